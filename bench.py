@@ -1,0 +1,340 @@
+"""Benchmark of the coupled LB-MPCD step on the 2D channel workload.
+
+Workload: D2Q9 2048 x 512 channel (tau 0.8, g 1e-7, FP32 deviation storage),
+MPCD on the central 256 LB columns at refinement 2 (512 x 1020 cells, 10
+particles per cell, 5,222,400 particles), SRD 130 degrees, kT 1e-4, 2-column
+coupling buffers with the windowed MPCD -> LB feedback (W = 100).  One step =
+LB stream-collide + particle pass + cell pass.  Synthetic data only.
+
+Prints one JSON line.  The device-timed value comes from CUDA events around
+lbmpcd_step(K) (graph replay) on the handle's stream, bracketed by a barrier
+and a synchronize; the per-kernel roofline from a second, per-kernel-event
+profiled run; e2e through the C ABI with host buffers.  --impl reference times
+the FP64 CPU oracle on the same workload (bounded sample) instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(
+    name="channel2d_2048x512_fp32",
+    params=dict(lattice=9, nx=2048, ny=512, nz=1, tau=0.8, force=(1e-7, 0.0, 0.0), refine=2,
+                ppc=10, alpha=math.radians(130.0), kT=1e-4, mass=1.0, coupling_width=2,
+                precision=1, feedback=1, window=100, resample_density=0, seed=2),
+    region=(896, 1152))
+
+METRIC = "coupled_steps_per_s"
+UNIT = "steps/s"
+PROFILE_NOTE = os.path.join(ROOT, "profiles", "ncu_particle_pass_channel2048x512.md")
+
+
+def algorithmic_bytes(p, region):
+    """Algorithmic HBM bytes per step of each kernel (FP32 storage, 2D)."""
+    nx, ny, r, ppc = p["nx"], p["ny"], p["refine"], p["ppc"]
+    fluid = nx * (ny - 2)
+    Wx, Hy = (region[1] - region[0]) * r, (ny - 2) * r
+    npart = Wx * Hy * ppc
+    ncell = Wx * (Hy + 1)
+    return dict(
+        lb_pull=72 * fluid,              # 9 populations read + 9 written, 4 B each
+        particle_pass=40 * npart,        # home 4 + offsets 8 + velocities 8, read and written
+        cell_pass=52 * ncell,            # accumulators read 12 + cleared 12, table written 16, read 12
+        fluid_nodes=fluid, particles=npart, cells=ncell)
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        rows = [ln.split(",") for ln in open(self.f.name).read().strip().splitlines() if ln.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except Exception:
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def ncu_traffic_per_launch():
+    """dram bytes per particle_pass launch from the committed ncu summary, if the
+    kernel source is unchanged since the capture (hash recorded in the summary)."""
+    import hashlib
+    try:
+        txt = open(PROFILE_NOTE).read()
+    except Exception:
+        return None
+    src = open(os.path.join(ROOT, "paper_2004_00304_gb300", "csrc", "mpcd.cu"), "rb").read()
+    h = hashlib.sha256(src).hexdigest()[:16]
+    vals = {}
+    for ln in txt.splitlines():
+        if ":" in ln and ln.strip().startswith("- "):
+            k, v = ln.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("mpcd.cu sha256[:16]") != h:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+def cpu_baseline(seconds: float = 12.0):
+    """The FP64 oracle, as it stands, on a bounded sample of the same workload:
+    a few full coupled steps of the whole 2048 x 512 system, single-threaded."""
+    import oracle
+    s = oracle.OracleSim(WORKLOAD["params"])
+    s.set_region(*WORKLOAD["region"])
+    s.step(1)                       # warm-up
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        s.step(1)
+        n += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} full coupled steps of the 2048x512 / 5.2M-particle workload after 1 warm-up step, "
+                      f"FP64, single thread, {dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    s = oracle.OracleSim(WORKLOAD["params"])
+    s.set_region(*WORKLOAD["region"])
+    t = time.perf_counter()
+    s.step(1)
+    t_step = time.perf_counter() - t
+    budget = 90.0
+    nwarm = min(args.warmup, max(0, int(10.0 / t_step)))
+    s.step(nwarm)
+    ntimed = max(1, min(args.steps, int(budget / max(t_step, 1e-6))))
+    t0 = time.perf_counter()
+    s.step(ntimed)
+    dt = time.perf_counter() - t0
+    v = ntimed / dt
+    sample = (f"{ntimed} timed full coupled steps (of {args.steps} requested) after {nwarm + 1} warm-up "
+              f"steps, FP64 oracle, single thread")
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": ntimed, "warmup": nwarm + 1, "ms_per_step": 1e3 * dt / ntimed,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": WORKLOAD["name"]},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    import __graft_entry__
+    import paper_2004_00304_gb300 as lb
+
+    __graft_entry__.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.Stream(device=dev)
+    params = dict(WORKLOAD["params"], seed=WORKLOAD["params"]["seed"] + 1000 * rank)
+    p = WORKLOAD["params"]
+    ab = algorithmic_bytes(p, WORKLOAD["region"])
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    with torch.cuda.stream(stream):
+        sim = lb.Lbmpcd(params, stream=stream)
+        sim.set_region(0, *WORKLOAD["region"])
+        # keep a copy of the initial state on the host (pinned) for the e2e leg
+        names = ("POPS", "PART_POS", "PART_VEL", "PART_HOME")
+        host_in = {}
+        for nm in names:
+            n = lb.lbmpcd_field_size(sim._h, 0, nm)
+            t = torch.empty(n, dtype=torch.int32 if nm in lb.INT_FIELDS else torch.float64, pin_memory=True)
+            sim.get(nm, out=t.numpy())
+            host_in[nm] = t
+        sim.step(args.warmup)
+        stream.synchronize()
+
+        # ---- device-timed region: K steps of graph replay -----------------
+        sampler = ClockSampler(local_rank) if rank == 0 else None
+        time.sleep(0.3 if sampler else 0)
+        barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        clocks = sampler.stop() if sampler else None
+        ms = e0.elapsed_time(e1)
+        launches = 3 * args.steps + (args.steps + 31) // 32
+        t_max = torch.tensor([ms], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+        ms = float(t_max.item())
+
+        # ---- per-kernel durations (events around every launch) ------------
+        kprof = min(args.steps, 640)
+        phase_ms, nlaunch = sim.step_profiled(kprof)
+        per_launch = {k: phase_ms[k] / kprof for k in ("lb_pull", "particle_pass", "cell_pass")}
+
+        # ---- e2e through the C ABI with host buffers ----------------------
+        e2e = None
+        if not args.no_e2e:
+            out_u = torch.empty(lb.lbmpcd_field_size(sim._h, 0, "U"), dtype=torch.float64, pin_memory=True)
+            out_v = torch.empty(lb.lbmpcd_field_size(sim._h, 0, "PART_VEL"), dtype=torch.float64,
+                                pin_memory=True)
+            sim2 = lb.Lbmpcd(params, stream=stream)
+            sim2.set_region(0, *WORKLOAD["region"])
+            sim2.step(args.warmup)
+            torch.cuda.synchronize()
+            barrier()
+            t0 = time.perf_counter()
+            for nm in names:
+                sim2.set(nm, host_in[nm])
+            sim2.step(args.steps)
+            sim2.get("U", out=out_u.numpy())
+            sim2.get("PART_VEL", out=out_v.numpy())
+            torch.cuda.synchronize()
+            t_e2e = time.perf_counter() - t0
+            barrier()
+            tt = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
+            if world > 1:
+                dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            h2d = sum(t.numel() * t.element_size() for t in host_in.values())
+            d2h = out_u.numel() * 8 + out_v.numel() * 8
+            e2e = {"value": world * args.steps / float(tt.item()), "unit": UNIT,
+                   "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+                   "note": "set_state of the full initial state from pinned host memory, K steps, "
+                           "get_fields of U and particle velocities to pinned host memory"}
+            sim2.close()
+        sim.close()
+
+    if rank != 0:
+        return
+    steps_per_s = world * args.steps / (ms * 1e-3)
+    peaks = measured_peaks()
+    hbm = float(peaks["hbm_gbs"]) if peaks else 6800.0
+    step_bytes = ab["lb_pull"] + ab["particle_pass"] + ab["cell_pass"]
+    dom = "particle_pass"
+    t_dom = per_launch[dom] * 1e-3
+    achieved = ab[dom] / t_dom / 1e9
+    traffic = ncu_traffic_per_launch()
+    kernels = {}
+    for k in ("lb_pull", "particle_pass", "cell_pass"):
+        t = per_launch[k] * 1e-3
+        kernels[k] = {"us_per_launch": per_launch[k] * 1e3, "algorithmic_bytes": ab[k],
+                      "achieved_gbs": ab[k] / t / 1e9 if t > 0 else None,
+                      "frac_of_measured_hbm": (ab[k] / t / 1e9) / hbm if t > 0 else None}
+    out = {
+        "metric": METRIC, "value": steps_per_s, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD["name"], "lb_nodes": f"{p['nx']}x{p['ny']}",
+                   "particles": ab["particles"], "collision_cells": ab["cells"],
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "working set ~300 MB per step > 129 MB L2 (no flush needed)"},
+        "lb_mlups": ab["fluid_nodes"] * steps_per_s / 1e6,
+        "mpcd_mparticle_upd_per_s": ab["particles"] * steps_per_s / 1e6,
+        "step_hbm": {"algorithmic_bytes_per_step": step_bytes,
+                     "achieved_gbs": step_bytes * steps_per_s / world / 1e9,
+                     "frac_of_measured": step_bytes * steps_per_s / world / 1e9 / hbm,
+                     "frac_of_nominal_7900": step_bytes * steps_per_s / world / 1e9 / 7900.0},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": traffic,
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s"},
+        "kernels": kernels,
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "e2e": e2e,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        out["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=100)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,159 @@
+/*
+ * lbmpcd.h -- C ABI of the GB300 (sm_103a) coupled lattice Boltzmann /
+ * multiparticle-collision-dynamics time stepper (liblbmpcd.so).
+ *
+ * The method is that of Montessori, Tiribocchi, Lauricella and Succi, "A
+ * coupled lattice Boltzmann-multiparticle collision method for
+ * multi-resolution hydrodynamics": the LB equation (Eq. 1) with the
+ * second-order equilibrium (Eq. 2) runs on the whole channel; MPCD particles
+ * (streaming Eq. 3, stochastic-rotation collision Eq. 4) run in a sub-region;
+ * a coupling buffer of whole LB columns on each side of the sub-region passes
+ * LB -> MPCD by redrawing particle velocities from a Maxwellian about the
+ * (interpolated) LB velocity (Sec. 2.3, Algorithms 1 and 2) and MPCD -> LB by
+ * imposing equilibrium populations built from windowed cell moments.
+ *
+ * Conventions shared by every entry point:
+ *  - return 0 on success, a negative LBMPCD_ERR_* code on failure; no C++
+ *    exception ever crosses this boundary; lbmpcd_last_error() gives text;
+ *  - the library owns all device memory it allocates; callers own every
+ *    pointer they pass in (params, region bounds, dst/src buffers);
+ *  - a handle is not thread-safe; all its work is ordered on the CUDA stream
+ *    given at creation (NULL = the legacy default stream);
+ *  - units are LB units: spacing 1, time step 1; MPCD cells have side 1/refine.
+ *
+ * Geometry: LB node (x,y,z) covers [x,x+1)x[y,y+1)x[z,z+1); rows y = 0 and
+ * y = ny-1 are solid (half-way bounce-back walls at y = 1 and y = ny-1),
+ * x and z are periodic.  The MPCD sub-region is a slab of LB columns
+ * [x0,x1) over all fluid rows and all z.
+ */
+#ifndef LBMPCD_H
+#define LBMPCD_H
+#include <stddef.h>
+#include <stdint.h>
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { LBMPCD_D2Q9 = 9, LBMPCD_D3Q19 = 19 };
+/* LB population storage / particle arithmetic.  FP64: binary64 everywhere.
+ * FP32: populations stored as binary32 deviations f_i - w_i rho0, particles
+ * as integer cell + binary32 offset.  FP16DEV: populations stored as scaled
+ * binary16 deviations, arithmetic in binary32, particles as for FP32. */
+enum { LBMPCD_FP64 = 0, LBMPCD_FP32 = 1, LBMPCD_FP16DEV = 2 };
+
+enum {
+  LBMPCD_OK = 0,
+  LBMPCD_ERR_INVALID_ARG = -1,
+  LBMPCD_ERR_OOM = -2,
+  LBMPCD_ERR_CUDA = -3,
+  LBMPCD_ERR_TIMEOUT = -4,
+  LBMPCD_ERR_STATE = -5,
+  LBMPCD_ERR_CAPACITY = -6
+};
+
+/* Field ids for lbmpcd_get_fields / lbmpcd_set_state.  Element type is
+ * double for floating-point fields and int32 for integer ones, whatever the
+ * storage precision; shapes are per replica:
+ *  RHO [nz][ny][nx], U [3][nz][ny][nx]    LB density / velocity of the last
+ *                                         step (moments of the streamed
+ *                                         populations, u with the half-force
+ *                                         shift); Eq. 1-2, Sec. 2.1
+ *  POPS [q][nz][ny][nx]                   stored post-collision populations f_i
+ *  PART_POS [np][3] (double)              offset of each particle in its cell, [0,1)
+ *  PART_VEL [np][3] (double)              particle velocities (LB units)
+ *  PART_CELL [np] (int32)                 collision cell of the last binning
+ *  SHIFT [3] (double)                     last random grid shift, cell units
+ *  CELL_COUNT [ncell] (int32)             particles per collision cell, last binning
+ *  WINDOW_MEAN [nbuf][4] (double)         rho_bar, u_bar of the inner buffer nodes
+ *  DIAG [9] (double)                      LB mass, LB momentum (3), particle count,
+ *                                         particle momentum (3), kinetic energy
+ *  PART_HOME [np][3] (int32)              integer home cell of each particle
+ *  CELL_VCM [ncell][3] (double)           centre-of-mass velocity of the last collision
+ *  PART_ID [np] (int32)                   identity: particle fields come back in id order
+ * Collision cells: ncell = Wx (Hy+1) Wz, id = cx + Wx (cy + (Hy+1) cz), with
+ * Wx = (x1-x0) refine, Hy = (ny-2) refine, Wz = nz refine (1 in 2D).
+ * Inner buffer nodes: nbuf = 2 * floor(cw/2) * (ny-2) * nz, index
+ * ((side * floor(cw/2) + col) * nz + z) * (ny-2) + (y-1). */
+enum {
+  LBMPCD_RHO = 0, LBMPCD_U = 1, LBMPCD_POPS = 2, LBMPCD_PART_POS = 3, LBMPCD_PART_VEL = 4,
+  LBMPCD_PART_CELL = 5, LBMPCD_SHIFT = 6, LBMPCD_CELL_COUNT = 7, LBMPCD_WINDOW_MEAN = 8,
+  LBMPCD_DIAG = 9, LBMPCD_PART_HOME = 10, LBMPCD_CELL_VCM = 11, LBMPCD_PART_ID = 12
+};
+
+typedef struct lbmpcd lbmpcd; /* opaque handle */
+
+/* Problem statement of one replica (Sec. 2-3 of the paper; Table 1 lists the
+ * same quantities).  All replicas of one handle share lattice and precision. */
+typedef struct {
+  int lattice;          /* LBMPCD_D2Q9 (nz must be 1) or LBMPCD_D3Q19 (Sec. 2.1) */
+  int nx, ny, nz;       /* LB nodes, walls included in ny */
+  double tau;           /* BGK relaxation time, nu = (tau - 1/2)/3 (Sec. 2.1) */
+  double force[3];      /* body acceleration g driving the flow (Sec. 3) */
+  int refine;           /* r = LB spacing / MPCD cell side a (Sec. 2.3, Algorithm 2) */
+  int ppc;              /* mean particles per MPCD cell (Table 1 "N") */
+  double alpha;         /* SRD rotation angle, radians (Eq. 4) */
+  double kT, mass;      /* MPCD thermal energy and particle mass (Eq. 4-5, Algorithm 1) */
+  int coupling_width;   /* LB columns of coupling buffer per side (2 in Sec. 2.3) */
+  int precision;        /* LBMPCD_FP64 | LBMPCD_FP32 | LBMPCD_FP16DEV */
+  int feedback;         /* 0: one-way LB -> MPCD as in the paper; 1: plus windowed MPCD -> LB */
+  int window;           /* samples in the averaging window (Table 1 N_s) */
+  int resample_density; /* must be 0 (velocity-only redraw, as in the paper) */
+  uint64_t seed;        /* Philox key */
+} lbmpcd_params;
+
+/* Create a handle holding n_replicas independent channels; params points to
+ * n_replicas structs (replica i uses params[i]).  cuda_stream is a
+ * cudaStream_t (NULL for the default stream).  LB populations start at
+ * f_eq(rho = 1, u = 0).  Errors: INVALID_ARG (bad sizes / mixed lattice or
+ * precision), OOM, CUDA.  On failure *out is NULL. */
+int lbmpcd_create(const lbmpcd_params* params, int n_replicas, void* cuda_stream, lbmpcd** out);
+
+/* Declare the MPCD sub-region of a replica: LB columns [lo[0], hi[0]) (half-open).
+ * lo[1..2] / hi[1..2] must span the channel (0..ny, 0..nz) -- only slabs of
+ * whole columns are supported.  Seeds ppc particles in every MPCD cell with
+ * offsets uniform in the cell and Maxwellian velocities (variance kT/m).
+ * Must precede the first lbmpcd_step (else ERR_STATE).  Errors: INVALID_ARG
+ * (region narrower than 2 coupling widths, cell index range too large), OOM, CUDA. */
+int lbmpcd_set_region(lbmpcd* h, int replica, const int lo[3], const int hi[3]);
+
+/* Advance every replica by nsteps coupled time steps (one step = LB
+ * stream-collide, interpolation + Maxwellian redraw in the outer buffer, MPCD
+ * streaming, inner-buffer sampling, random-shift binning, SRD collision,
+ * imposition).  A replica without a region runs the LB part only.
+ * Asynchronous on the handle's stream.  Errors: INVALID_ARG, CUDA. */
+int lbmpcd_step(lbmpcd* h, int nsteps);
+
+/* Same work as lbmpcd_step, launched without graph replay and with a CUDA
+ * event pair on the handle's stream around every kernel; adds each kernel
+ * family's elapsed milliseconds to phase_ms[0..3] = {prep, lb_pull,
+ * particle_pass, cell_pass} (caller-owned; not zeroed here) and the number of
+ * kernel launches to *launches (may be NULL).  Synchronises the stream.  For
+ * measurement only: the per-kernel events add small gaps between kernels.
+ * Errors: INVALID_ARG, CUDA. */
+int lbmpcd_step_profiled(lbmpcd* h, int nsteps, double* phase_ms, long long* launches);
+
+/* Copy one field of one replica (layouts above) to dst, which holds exactly
+ * `bytes` bytes (else INVALID_ARG); dst_on_device = 1 for device memory.
+ * Synchronises the handle's stream before returning. */
+int lbmpcd_get_fields(lbmpcd* h, int replica, int field, void* dst, size_t bytes, int dst_on_device);
+
+/* Load POPS, PART_POS, PART_VEL or PART_HOME of one replica from src (same
+ * layouts and element types as get_fields; particle arrays in id order).
+ * Positions must satisfy 0 <= offset < 1 and lie inside the region.  Errors:
+ * INVALID_ARG (field, size, values), STATE (particles before set_region). */
+int lbmpcd_set_state(lbmpcd* h, int replica, int field, const void* src, size_t bytes, int src_on_device);
+
+/* Element count of a field for a replica (or a negative error code). */
+long long lbmpcd_field_size(const lbmpcd* h, int replica, int field);
+
+/* Release every resource of the handle; NULL is accepted. */
+void lbmpcd_destroy(lbmpcd* h);
+
+/* Text of the last error on this handle (never NULL; "" when none).  With
+ * h == NULL, the last error of a failed lbmpcd_create on this thread. */
+const char* lbmpcd_last_error(const lbmpcd* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,216 @@
+"""GB300-native coupled lattice Boltzmann / MPCD time stepper.
+
+A thin ctypes binding over the C ABI of ``liblbmpcd.so`` (declared in
+``include/lbmpcd.h``).  Every step of the method runs in the library's CUDA
+kernels; this module only marshals arguments.  There is no CPU fallback:
+importing the binding without a built library, or creating a handle without a
+CUDA device, raises.
+
+The entry points keep the ABI's names: :func:`lbmpcd_create`,
+:func:`lbmpcd_set_region`, :func:`lbmpcd_step`, :func:`lbmpcd_get_fields`,
+:func:`lbmpcd_set_state`, :func:`lbmpcd_destroy`; :class:`Lbmpcd` wraps them.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "liblbmpcd.so")
+
+D2Q9, D3Q19 = 9, 19
+FP64, FP32, FP16DEV = 0, 1, 2
+FIELDS = dict(RHO=0, U=1, POPS=2, PART_POS=3, PART_VEL=4, PART_CELL=5, SHIFT=6,
+              CELL_COUNT=7, WINDOW_MEAN=8, DIAG=9, PART_HOME=10, CELL_VCM=11, PART_ID=12)
+INT_FIELDS = {"PART_CELL", "CELL_COUNT", "PART_HOME", "PART_ID"}
+ERRORS = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "TIMEOUT", -5: "STATE", -6: "CAPACITY"}
+
+
+class LbmpcdError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class lbmpcd_params(ctypes.Structure):
+    _fields_ = [("lattice", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("nz", ctypes.c_int), ("tau", ctypes.c_double), ("force", ctypes.c_double * 3),
+                ("refine", ctypes.c_int), ("ppc", ctypes.c_int), ("alpha", ctypes.c_double),
+                ("kT", ctypes.c_double), ("mass", ctypes.c_double),
+                ("coupling_width", ctypes.c_int), ("precision", ctypes.c_int),
+                ("feedback", ctypes.c_int), ("window", ctypes.c_int),
+                ("resample_density", ctypes.c_int), ("seed", ctypes.c_uint64)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load liblbmpcd.so (build it with ``paper_2004_00304_gb300.build.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"liblbmpcd.so not built ({path}); run __graft_entry__.build()")
+    L = ctypes.CDLL(path)
+    vp, ci, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+    L.lbmpcd_create.argtypes = [ctypes.POINTER(lbmpcd_params), ci, vp, ctypes.POINTER(vp)]
+    L.lbmpcd_set_region.argtypes = [vp, ci, ctypes.POINTER(ci), ctypes.POINTER(ci)]
+    L.lbmpcd_step.argtypes = [vp, ci]
+    L.lbmpcd_get_fields.argtypes = [vp, ci, ci, vp, sz, ci]
+    L.lbmpcd_set_state.argtypes = [vp, ci, ci, vp, sz, ci]
+    L.lbmpcd_field_size.argtypes = [vp, ci, ci]
+    L.lbmpcd_field_size.restype = ctypes.c_longlong
+    L.lbmpcd_step_profiled.argtypes = [vp, ci, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_longlong)]
+    L.lbmpcd_destroy.argtypes = [vp]
+    L.lbmpcd_destroy.restype = None
+    L.lbmpcd_last_error.argtypes = [vp]
+    L.lbmpcd_last_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+EXPORTED = ["lbmpcd_create", "lbmpcd_set_region", "lbmpcd_step", "lbmpcd_step_profiled",
+            "lbmpcd_get_fields", "lbmpcd_set_state", "lbmpcd_field_size", "lbmpcd_destroy",
+            "lbmpcd_last_error"]
+
+
+def make_params(d: dict) -> lbmpcd_params:
+    p = lbmpcd_params()
+    p.lattice = int(d.get("lattice", 9))
+    p.nx, p.ny, p.nz = int(d["nx"]), int(d["ny"]), int(d.get("nz", 1))
+    p.tau = float(d["tau"])
+    f = list(d.get("force", (0.0, 0.0, 0.0))) + [0.0, 0.0, 0.0]
+    p.force = (ctypes.c_double * 3)(*[float(x) for x in f[:3]])
+    p.refine = int(d.get("refine", 1))
+    p.ppc = int(d.get("ppc", 10))
+    p.alpha = float(d.get("alpha", math.radians(130.0)))
+    p.kT = float(d.get("kT", 1e-4))
+    p.mass = float(d.get("mass", 1.0))
+    p.coupling_width = int(d.get("coupling_width", 2))
+    p.precision = int(d.get("precision", FP32))
+    p.feedback = int(d.get("feedback", 0))
+    p.window = int(d.get("window", 100))
+    p.resample_density = int(d.get("resample_density", 0))
+    p.seed = int(d.get("seed", 1))
+    return p
+
+
+def _check(h, rc: int):
+    if rc != 0:
+        msg = load_library().lbmpcd_last_error(h)
+        raise LbmpcdError(rc, msg.decode() if msg else "")
+
+
+def lbmpcd_create(params, n_replicas: int = None, stream=None):
+    """Create a handle; ``params`` is a dict or a list of dicts (one per replica).
+    ``stream`` is a torch.cuda.Stream, a raw cudaStream_t integer, or None."""
+    L = load_library()
+    plist = params if isinstance(params, (list, tuple)) else [params]
+    n = len(plist) if n_replicas is None else int(n_replicas)
+    arr = (lbmpcd_params * n)(*[make_params(p) for p in plist[:n]])
+    sptr = getattr(stream, "cuda_stream", stream) or 0
+    h = ctypes.c_void_p()
+    rc = L.lbmpcd_create(arr, n, ctypes.c_void_p(int(sptr)), ctypes.byref(h))
+    _check(None, rc)
+    return h
+
+
+def lbmpcd_set_region(h, replica: int, lo, hi):
+    lo3 = (ctypes.c_int * 3)(*[int(v) for v in lo])
+    hi3 = (ctypes.c_int * 3)(*[int(v) for v in hi])
+    _check(h, load_library().lbmpcd_set_region(h, int(replica), lo3, hi3))
+
+
+def lbmpcd_step(h, nsteps: int):
+    _check(h, load_library().lbmpcd_step(h, int(nsteps)))
+
+
+def lbmpcd_step_profiled(h, nsteps: int):
+    """Run nsteps with a CUDA event pair around every kernel; returns
+    ({phase: milliseconds}, number of kernel launches)."""
+    ms = (ctypes.c_double * 4)()
+    nl = ctypes.c_longlong(0)
+    _check(h, load_library().lbmpcd_step_profiled(h, int(nsteps), ms, ctypes.byref(nl)))
+    return dict(zip(("prep", "lb_pull", "particle_pass", "cell_pass"), list(ms))), int(nl.value)
+
+
+def lbmpcd_field_size(h, replica: int, field: str) -> int:
+    n = load_library().lbmpcd_field_size(h, int(replica), FIELDS[field])
+    if n < 0:
+        _check(h, int(n))
+    return int(n)
+
+
+def lbmpcd_get_fields(h, replica: int, field: str, out=None):
+    """Copy a field out; ``out`` may be a numpy array (host) or a torch CUDA tensor
+    of the right size and dtype (float64 / int32); returns the filled array."""
+    n = lbmpcd_field_size(h, replica, field)
+    is_int = field in INT_FIELDS
+    if out is None:
+        out = np.empty(n, dtype=np.int32 if is_int else np.float64)
+    if isinstance(out, np.ndarray):
+        assert out.flags.c_contiguous and out.size == n
+        ptr, nbytes, on_dev = out.ctypes.data, out.nbytes, 0
+    else:   # torch tensor
+        assert out.is_contiguous() and out.numel() == n
+        ptr, nbytes, on_dev = out.data_ptr(), out.numel() * out.element_size(), int(out.is_cuda)
+    _check(h, load_library().lbmpcd_get_fields(h, int(replica), FIELDS[field], ctypes.c_void_p(ptr),
+                                               nbytes, on_dev))
+    return out
+
+
+def lbmpcd_set_state(h, replica: int, field: str, value):
+    is_int = field in INT_FIELDS
+    if isinstance(value, np.ndarray) or not hasattr(value, "data_ptr"):
+        arr = np.ascontiguousarray(value, dtype=np.int32 if is_int else np.float64).ravel()
+        ptr, nbytes, on_dev = arr.ctypes.data, arr.nbytes, 0
+    else:
+        arr = value.contiguous()
+        ptr, nbytes, on_dev = arr.data_ptr(), arr.numel() * arr.element_size(), int(arr.is_cuda)
+    _check(h, load_library().lbmpcd_set_state(h, int(replica), FIELDS[field], ctypes.c_void_p(ptr),
+                                              nbytes, on_dev))
+
+
+def lbmpcd_destroy(h):
+    if h:
+        load_library().lbmpcd_destroy(h)
+
+
+class Lbmpcd:
+    """Owning wrapper of one handle (all replicas)."""
+
+    def __init__(self, params, stream=None):
+        self.params = list(params) if isinstance(params, (list, tuple)) else [params]
+        self._h = lbmpcd_create(self.params, stream=stream)
+
+    def set_region(self, replica: int, x0: int, x1: int):
+        p = self.params[replica]
+        lbmpcd_set_region(self._h, replica, (x0, 0, 0), (x1, p["ny"], p.get("nz", 1)))
+
+    def step(self, n: int = 1):
+        lbmpcd_step(self._h, n)
+
+    def step_profiled(self, n: int):
+        return lbmpcd_step_profiled(self._h, n)
+
+    def get(self, field: str, replica: int = 0, out=None):
+        return lbmpcd_get_fields(self._h, replica, field, out)
+
+    def set(self, field: str, value, replica: int = 0):
+        lbmpcd_set_state(self._h, replica, field, value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lbmpcd_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

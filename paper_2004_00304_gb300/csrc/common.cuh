@@ -1,0 +1,174 @@
+// common.cuh -- device-side building blocks of the coupled LB-MPCD step:
+// the counter-based generator, uniform/normal maps, lattice tables, the
+// per-replica descriptor and the per-step record read by every kernel.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#define LBM_HD __host__ __device__ __forceinline__
+
+namespace lbm {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11).  Counter words: (id, step, replica,
+// tag), key: the 64-bit seed.  Same stream on host and device.
+enum : uint32_t { TAG_SHIFT = 1, TAG_SIGN = 2, TAG_AXIS = 3, TAG_VIRT = 4,
+                  TAG_RESAMPLE = 5, TAG_INIT_POS = 6, TAG_INIT_VEL = 7 };
+
+LBM_HD uint32_t mul_hi32(uint32_t a, uint32_t b) {
+#ifdef __CUDA_ARCH__
+  return __umulhi(a, b);
+#else
+  return (uint32_t)(((uint64_t)a * (uint64_t)b) >> 32);
+#endif
+}
+
+LBM_HD uint4 philox(uint32_t id, uint32_t step, uint32_t rep, uint32_t tag, uint32_t k0, uint32_t k1) {
+  uint32_t x = id, y = step, z = rep, w = tag;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t a = 0xD2511F53u * x, ah = mul_hi32(0xD2511F53u, x);
+    const uint32_t b = 0xCD9E8D57u * z, bh = mul_hi32(0xCD9E8D57u, z);
+    x = bh ^ y ^ k0;
+    y = b;
+    z = ah ^ w ^ k1;
+    w = a;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return make_uint4(x, y, z, w);
+}
+
+// 24-bit uniform in [0,1): exact in binary32 and binary64.
+LBM_HD double unit24(uint32_t w) { return (double)(w >> 8) * (1.0 / 16777216.0); }
+LBM_HD float unit24f(uint32_t w) { return (float)(w >> 8) * (1.0f / 16777216.0f); }
+
+// Box-Muller pair in binary64: u1 = (a+1) 2^-32 in (0,1], u2 = b 2^-32.
+__device__ __forceinline__ void normal_pair(uint32_t a, uint32_t b, double& z0, double& z1) {
+  const double u1 = ((double)a + 1.0) * (1.0 / 4294967296.0);
+  const double u2 = (double)b * (1.0 / 4294967296.0);
+  const double rad = sqrt(-2.0 * log(u1));
+  double s, c;
+  sincospi(2.0 * u2, &s, &c);
+  z0 = rad * c;
+  z1 = rad * s;
+}
+
+// ---------------------------------------------------------------------------
+// Lattices: D2Q9 (the paper's, Sec. 2.1) and D3Q19.
+template <int Q> struct Lattice;
+template <> struct Lattice<9> {
+  static constexpr int D = 2;
+  LBM_HD static constexpr int cx(int i) { constexpr int t[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1}; return t[i]; }
+  LBM_HD static constexpr int cy(int i) { constexpr int t[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1}; return t[i]; }
+  LBM_HD static constexpr int cz(int) { return 0; }
+  LBM_HD static constexpr int opp(int i) { constexpr int t[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6}; return t[i]; }
+  LBM_HD static constexpr double w(int i) { return i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0); }
+};
+template <> struct Lattice<19> {
+  static constexpr int D = 3;
+  LBM_HD static constexpr int cx(int i) {
+    constexpr int t[19] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+    return t[i];
+  }
+  LBM_HD static constexpr int cy(int i) {
+    constexpr int t[19] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+    return t[i];
+  }
+  LBM_HD static constexpr int cz(int i) {
+    constexpr int t[19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+    return t[i];
+  }
+  LBM_HD static constexpr int opp(int i) {
+    constexpr int t[19] = {0, 2, 1, 4, 3, 6, 5, 8, 7, 10, 9, 12, 11, 14, 13, 16, 15, 18, 17};
+    return t[i];
+  }
+  LBM_HD static constexpr double w(int i) { return i == 0 ? 1.0 / 3.0 : (i < 7 ? 1.0 / 18.0 : 1.0 / 36.0); }
+};
+
+// ---------------------------------------------------------------------------
+// Per-replica descriptor (device copy).  Every array of a replica is its own
+// allocation; the kernels of one launch walk all replicas through a block map.
+struct RepDev {
+  // LB lattice
+  int nx, ny, nz, q;
+  double omega;            // 1 / tau
+  double g[3];             // body acceleration
+  long long nnode;         // nx ny nz
+  float fp16_scale;        // binary16 deviation scale 2^k (1 for the other storages)
+  float fp16_inv;
+  void* f[2];              // populations [q][nnode], ping-pong by step parity
+  void* rho;               // [nnode]
+  void* u;                 // [3][nnode]
+  // MPCD region, cell units: [0,Wx) x [0,Hy) x [0,Wz)
+  int has_region, x0, x1, Wx, Hy, Wz, r, n_out, n_in, cw, ppc, feedback, window;
+  double kT, mass, sig;    // sig = sqrt(kT / m)
+  double cos_a, sin_a, alpha;
+  long long np;            // particles
+  long long ncell;         // collision cells: Wx (Hy+1) Wz
+  long long nbuf;          // inner-buffer LB nodes
+  uint32_t key0, key1, rep;
+  // particles (structure of arrays)
+  uint32_t* home;          // packed integer home cell
+  void* off[3];            // offsets in [0,1), storage precision
+  void* vel[3];            // velocities, storage precision
+  uint32_t* pid;           // particle id (Philox counter of the redraw)
+  // collision cells
+  uint32_t* acc_n;         // accumulators of the current binning
+  void* acc_v[3];
+  void* vcm[3];            // table of the last collision: v_cm
+  void* rot[3];            // 2D: signed sin(theta) in rot[0]; 3D: unit axis
+  int* count;              // particles per cell of the last binning
+  // inner buffer sampling window (binary64)
+  double* frame;           // [nbuf][4] this step's mass, momentum
+  double* ring;            // [window][nbuf][4]
+  double* wsum;            // [nbuf][4]
+  double* wmean;           // [nbuf][4] rho_bar, u_bar
+};
+
+// One record per (step of the chunk, replica), written by the prep kernel.
+struct StepInfo {
+  uint32_t n;              // global step index
+  int pending;             // collision of step n-1 not yet applied to particles
+  int write_moments;       // write rho/u on every node this step
+  int pad;
+  double shift[3], prev[3];
+};
+
+// packed home cell: 2D x | y << 16 ; 3D x | y << 10 | z << 21
+template <int D> struct HomePack;
+template <> struct HomePack<2> {
+  static constexpr int XMAX = 65535, YMAX = 65535, ZMAX = 1;
+  LBM_HD static uint32_t pack(int x, int y, int) { return (uint32_t)x | ((uint32_t)y << 16); }
+  LBM_HD static void unpack(uint32_t h, int& x, int& y, int& z) { x = h & 0xFFFF; y = h >> 16; z = 0; }
+};
+template <> struct HomePack<3> {
+  static constexpr int XMAX = 1023, YMAX = 2047, ZMAX = 2047;
+  LBM_HD static uint32_t pack(int x, int y, int z) {
+    return (uint32_t)x | ((uint32_t)y << 10) | ((uint32_t)z << 21);
+  }
+  LBM_HD static void unpack(uint32_t h, int& x, int& y, int& z) {
+    x = h & 0x3FF; y = (h >> 10) & 0x7FF; z = h >> 21;
+  }
+};
+
+// Storage of LB populations as deviations d_i = f_i - w_i (rho0 = 1).
+template <typename S> struct Store;
+template <> struct Store<double> {
+  using R = double;
+  __device__ static double ld(const double* p, float) { return *p; }
+  __device__ static void st(double* p, double v, float) { *p = v; }
+};
+template <> struct Store<float> {
+  using R = float;
+  __device__ static float ld(const float* p, float) { return *p; }
+  __device__ static void st(float* p, float v, float) { *p = v; }
+};
+template <> struct Store<__half> {
+  using R = float;   // binary16 holds d_i * scale; arithmetic in binary32
+  __device__ static float ld(const __half* p, float inv) { return __half2float(*p) * inv; }
+  __device__ static void st(__half* p, float v, float scale) { *p = __float2half_rn(v * scale); }
+};
+
+}  // namespace lbm

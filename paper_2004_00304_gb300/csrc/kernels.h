@@ -1,0 +1,50 @@
+// kernels.h -- host-side launchers of the device kernels (one translation
+// unit per kernel family, called by the C ABI in lbmpcd_api.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include "common.cuh"
+
+namespace lbm {
+
+// precision codes (match LBMPCD_FP64 / FP32 / FP16DEV)
+enum { P_FP64 = 0, P_FP32 = 1, P_FP16 = 2 };
+
+struct Launch {
+  const RepDev* reps;     // device descriptor table
+  int nrep;
+  const StepInfo* si;     // device [kcount][nrep]
+  cudaStream_t stream;
+};
+
+// a1: fused pull stream + BGK collide (+ Guo force, bounce-back walls).
+cudaError_t launch_lb(int q, int prec, const Launch& L, const int2* bmap, int nblocks, int k);
+
+// prep: per-step records (shift, pending flag) for kcount steps.
+cudaError_t launch_prep(int dim, const Launch& L, StepInfo* si, int kcount, uint32_t* d_step,
+                        int* d_pending, double* d_last_shift);
+
+// a7(n-1) + a2 + a3 + a4 + a6 + a5 over every particle.
+cudaError_t launch_particles(int dim, int prec, const Launch& L, const int2* bmap, int nblocks, int k);
+
+// a7 cell part (v_cm, virtual particles, rotation draw) + a8 imposition.
+cudaError_t launch_cells(int q, int prec, const Launch& L, const int2* bmap, int nblocks, int k);
+
+// apply the pending collision of the last step to every particle of a replica.
+cudaError_t launch_flush(int dim, int prec, const RepDev* rd_dev, const RepDev& rd, const double* last_shift,
+                         cudaStream_t st);
+
+// seed particles of a replica (ppc per cell, Maxwellian velocities).
+cudaError_t launch_init_particles(int dim, int prec, const RepDev* rd_dev, const RepDev& rd, cudaStream_t st);
+
+// copy-out / copy-in helpers (binary64 / int32 host-facing layouts).
+cudaError_t launch_pops_out(int q, int prec, const RepDev& rd, int parity, double* out, cudaStream_t st);
+cudaError_t launch_pops_in(int q, int prec, const RepDev& rd, const double* in, cudaStream_t st);
+cudaError_t launch_real_out(int prec, const void* src, long long n, double* out, cudaStream_t st);
+cudaError_t launch_part_out(int dim, int prec, const RepDev& rd, int field, const double* last_shift,
+                            void* out, cudaStream_t st);
+cudaError_t launch_part_in(int dim, int prec, const RepDev& rd, int field, const void* in, int* bad,
+                           cudaStream_t st);
+cudaError_t launch_diag_lb(int q, int prec, const RepDev& rd, int parity, double* out4, cudaStream_t st);
+cudaError_t launch_diag_particles(int dim, int prec, const RepDev& rd, double* out9, cudaStream_t st);
+
+}  // namespace lbm

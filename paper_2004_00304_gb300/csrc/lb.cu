@@ -1,0 +1,221 @@
+// lb.cu -- a1: the lattice Boltzmann update (Eq. 1 with the equilibrium of
+// Eq. 2) as one fused pull kernel per step.
+//
+// Each thread owns one fluid node.  It pulls f*_i(x - c_i) from the
+// post-collision buffer of the previous step (structure of arrays
+// f[i][z][y][x]: for a fixed i, a warp reads 32 consecutive x, one coalesced
+// segment), substitutes f*_{-i}(x) where x - c_i is a wall node (half-way
+// bounce-back), forms rho and u = (sum f c + F/2)/rho with F = rho g (Guo
+// forcing), relaxes to f_eq with rate 1/tau, adds the Guo source and writes
+// f*_i(x) to the other buffer.  Populations are kept as deviations
+// d_i = f_i - w_i (rho0 = 1) so that small body-force increments survive
+// binary32 / scaled binary16 storage.  HBM traffic: one read and one write of
+// q populations per node.
+#include "kernels.h"
+
+namespace lbm {
+
+template <int Q, typename S>
+__global__ void __launch_bounds__(256) lb_pull(const RepDev* __restrict__ reps, const int2* __restrict__ bmap,
+                                               const StepInfo* __restrict__ si, int k, int nrep) {
+  using L = Lattice<Q>;
+  using R = typename Store<S>::R;
+  const int2 bm = bmap[blockIdx.x];
+  const RepDev& rd = reps[bm.x];
+  const StepInfo& st = si[k * nrep + bm.x];
+  const int nx = rd.nx, ny = rd.ny, nz = rd.nz;
+  const int ntx = (nx + blockDim.x - 1) / blockDim.x;
+  const int tile = bm.y % ntx, yz = bm.y / ntx;
+  const int y = 1 + yz % (ny - 2), z = yz / (ny - 2);
+  const int x = tile * blockDim.x + threadIdx.x;
+  if (x >= nx) return;
+  const int par = st.n & 1;
+  const S* __restrict__ src = (const S*)rd.f[par];
+  S* __restrict__ dst = (S*)rd.f[par ^ 1];
+  const long long N = rd.nnode;
+  const long long here = x + (long long)nx * (y + (long long)ny * z);
+  const float inv = rd.fp16_inv, scale = rd.fp16_scale;
+
+  R d[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const int sy = y - L::cy(i);
+    if (sy == 0 || sy == ny - 1) {
+      d[i] = Store<S>::ld(src + L::opp(i) * N + here, inv);
+    } else {
+      int sx = x - L::cx(i);
+      sx = sx < 0 ? sx + nx : (sx >= nx ? sx - nx : sx);
+      int sz = z - L::cz(i);
+      sz = sz < 0 ? sz + nz : (sz >= nz ? sz - nz : sz);
+      d[i] = Store<S>::ld(src + i * N + sx + (long long)nx * (sy + (long long)ny * sz), inv);
+    }
+  }
+  R drho = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    drho += d[i];
+    if (L::cx(i)) jx += L::cx(i) * d[i];
+    if (L::cy(i)) jy += L::cy(i) * d[i];
+    if (L::cz(i)) jz += L::cz(i) * d[i];
+  }
+  const R rho = R(1) + drho;
+  const R irho = R(1) / rho;
+  const R gx = (R)rd.g[0], gy = (R)rd.g[1], gz = (R)rd.g[2];
+  const R ux = jx * irho + R(0.5) * gx, uy = jy * irho + R(0.5) * gy, uz = jz * irho + R(0.5) * gz;
+  const R uu = ux * ux + uy * uy + uz * uz;
+  const R Fx = rho * gx, Fy = rho * gy, Fz = rho * gz;
+  const R uF = ux * Fx + uy * Fy + uz * Fz;
+  const R om = (R)rd.omega;
+  const R cf = R(1) - R(0.5) * om;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const R w = (R)L::w(i);
+    const R cu = L::cx(i) * ux + L::cy(i) * uy + L::cz(i) * uz;
+    const R cF = L::cx(i) * Fx + L::cy(i) * Fy + L::cz(i) * Fz;
+    const R deq = w * (drho + rho * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu));
+    const R src_i = cf * w * (R(3) * (cF - uF) + R(9) * cu * cF);
+    Store<S>::st(dst + i * N + here, d[i] - om * (d[i] - deq) + src_i, scale);
+  }
+  // rho, u: every node on request; otherwise the columns the coarse->fine
+  // interpolation of the outer buffer reads.
+  bool want = st.write_moments;
+  if (!want && rd.has_region) {
+    // columns x0-1 .. x0+n_out and x1-n_out-1 .. x1 (periodic in x)
+    int da = x - (rd.x0 - 1), db = x - (rd.x1 - rd.n_out - 1);
+    da = da < 0 ? da + nx : (da >= nx ? da - nx : da);
+    db = db < 0 ? db + nx : (db >= nx ? db - nx : db);
+    want = da <= rd.n_out + 1 || db <= rd.n_out + 1;
+  }
+  if (want) {
+    R* rh = (R*)rd.rho;
+    R* uv = (R*)rd.u;
+    rh[here] = rho;
+    uv[here] = ux;
+    uv[N + here] = uy;
+    uv[2 * N + here] = uz;
+  }
+}
+
+template <int Q, typename S>
+static cudaError_t go_lb(const Launch& L, const int2* bmap, int nblocks, int k) {
+  if (nblocks == 0) return cudaSuccess;
+  lb_pull<Q, S><<<nblocks, 256, 0, L.stream>>>(L.reps, bmap, L.si, k, L.nrep);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lb(int q, int prec, const Launch& L, const int2* bmap, int nblocks, int k) {
+  if (q == 9) {
+    if (prec == P_FP64) return go_lb<9, double>(L, bmap, nblocks, k);
+    if (prec == P_FP32) return go_lb<9, float>(L, bmap, nblocks, k);
+    return go_lb<9, __half>(L, bmap, nblocks, k);
+  }
+  if (prec == P_FP64) return go_lb<19, double>(L, bmap, nblocks, k);
+  if (prec == P_FP32) return go_lb<19, float>(L, bmap, nblocks, k);
+  return go_lb<19, __half>(L, bmap, nblocks, k);
+}
+
+// ---- copy-out / copy-in of populations and LB-side diagnostics ------------
+template <int Q, typename S>
+__global__ void pops_out(const S* __restrict__ f, long long N, float inv, double* __restrict__ out) {
+  using L = Lattice<Q>;
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= Q * N) return;
+  const int i = (int)(idx / N);
+  double w = 0;
+#pragma unroll
+  for (int j = 0; j < Q; ++j) if (j == i) w = L::w(j);
+  out[idx] = w + (double)Store<S>::ld(f + idx, inv);
+}
+
+template <int Q, typename S>
+__global__ void pops_in(S* __restrict__ f0, S* __restrict__ f1, long long N, float scale,
+                        const double* __restrict__ in) {
+  using L = Lattice<Q>;
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= Q * N) return;
+  const int i = (int)(idx / N);
+  double w = 0;
+#pragma unroll
+  for (int j = 0; j < Q; ++j) if (j == i) w = L::w(j);
+  const double d = in[idx] - w;
+  Store<S>::st(f0 + idx, (typename Store<S>::R)d, scale);
+  Store<S>::st(f1 + idx, (typename Store<S>::R)d, scale);
+}
+
+// LB mass and momentum of the stored populations over fluid nodes (binary64).
+template <int Q, typename S>
+__global__ void lb_diag(const S* __restrict__ f, int nx, int ny, int nz, float inv, double* out) {
+  using L = Lattice<Q>;
+  const long long N = (long long)nx * ny * nz;
+  double m = 0, px = 0, py = 0, pz = 0;
+  for (long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x; node < N;
+       node += (long long)gridDim.x * blockDim.x) {
+    const int y = (int)((node / nx) % ny);
+    if (y == 0 || y == ny - 1) continue;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const double fv = L::w(i) + (double)Store<S>::ld(f + i * N + node, inv);
+      m += fv; px += L::cx(i) * fv; py += L::cy(i) * fv; pz += L::cz(i) * fv;
+    }
+  }
+  double v[4] = {m, px, py, pz};
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    double t = v[a];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&out[a], t);
+  }
+}
+
+template <int Q, typename S>
+static cudaError_t go_pops(const RepDev& rd, int parity, double* out, const double* in, double* diag,
+                           cudaStream_t st) {
+  const long long n = Q * rd.nnode;
+  const int nb = (int)((n + 255) / 256);
+  if (out) pops_out<Q, S><<<nb, 256, 0, st>>>((const S*)rd.f[parity], rd.nnode, rd.fp16_inv, out);
+  if (in) pops_in<Q, S><<<nb, 256, 0, st>>>((S*)rd.f[0], (S*)rd.f[1], rd.nnode, rd.fp16_scale, in);
+  if (diag) {
+    const int g = (int)((rd.nnode + 255) / 256);
+    lb_diag<Q, S><<<g < 1024 ? g : 1024, 256, 0, st>>>((const S*)rd.f[parity], rd.nx, rd.ny, rd.nz,
+                                                       rd.fp16_inv, diag);
+  }
+  return cudaGetLastError();
+}
+
+static cudaError_t dispatch_pops(int q, int prec, const RepDev& rd, int parity, double* out, const double* in,
+                                 double* diag, cudaStream_t st) {
+  if (q == 9) {
+    if (prec == P_FP64) return go_pops<9, double>(rd, parity, out, in, diag, st);
+    if (prec == P_FP32) return go_pops<9, float>(rd, parity, out, in, diag, st);
+    return go_pops<9, __half>(rd, parity, out, in, diag, st);
+  }
+  if (prec == P_FP64) return go_pops<19, double>(rd, parity, out, in, diag, st);
+  if (prec == P_FP32) return go_pops<19, float>(rd, parity, out, in, diag, st);
+  return go_pops<19, __half>(rd, parity, out, in, diag, st);
+}
+
+cudaError_t launch_pops_out(int q, int prec, const RepDev& rd, int parity, double* out, cudaStream_t st) {
+  return dispatch_pops(q, prec, rd, parity, out, nullptr, nullptr, st);
+}
+cudaError_t launch_pops_in(int q, int prec, const RepDev& rd, const double* in, cudaStream_t st) {
+  return dispatch_pops(q, prec, rd, 0, nullptr, in, nullptr, st);
+}
+cudaError_t launch_diag_lb(int q, int prec, const RepDev& rd, int parity, double* out4, cudaStream_t st) {
+  return dispatch_pops(q, prec, rd, parity, nullptr, nullptr, out4, st);
+}
+
+template <typename R>
+__global__ void real_out(const R* __restrict__ src, long long n, double* __restrict__ out) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (double)src[i];
+}
+
+cudaError_t launch_real_out(int prec, const void* src, long long n, double* out, cudaStream_t st) {
+  const int nb = (int)((n + 255) / 256);
+  if (n == 0) return cudaSuccess;
+  if (prec == P_FP64) real_out<double><<<nb, 256, 0, st>>>((const double*)src, n, out);
+  else real_out<float><<<nb, 256, 0, st>>>((const float*)src, n, out);
+  return cudaGetLastError();
+}
+
+}  // namespace lbm

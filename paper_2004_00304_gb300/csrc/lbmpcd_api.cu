@@ -1,0 +1,516 @@
+// lbmpcd_api.cu -- the C ABI declared in include/lbmpcd.h.
+//
+// A handle owns R replicas.  Every replica's arrays are separate device
+// allocations described by a RepDev record; one device table of these records
+// plus a block map per kernel family lets a single launch of each kernel
+// cover all replicas.  lbmpcd_step runs the per-step sequence
+//     lb_pull -> particle_pass -> cell_pass
+// in chunks of KCHUNK steps; each full chunk (a prep kernel plus the 3 kernels
+// per step) is captured once into a CUDA graph and replayed.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/lbmpcd.h"
+#include "kernels.h"
+
+using namespace lbm;
+
+namespace {
+constexpr int KCHUNK = 32;   // steps per captured graph
+thread_local std::string g_create_error;
+}  // namespace
+
+struct lbmpcd {
+  std::vector<lbmpcd_params> P;
+  int nrep = 0, q = 9, dim = 2, prec = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<RepDev> rd;
+  std::vector<std::vector<void*>> rep_allocs;   // per replica, region arrays
+  std::vector<void*> allocs;                    // handle-wide
+  RepDev* d_reps = nullptr;
+  int2 *bm_lb = nullptr, *bm_p = nullptr, *bm_c = nullptr;
+  int nb_lb = 0, nb_p = 0, nb_c = 0;
+  StepInfo* d_si = nullptr;
+  uint32_t* d_step = nullptr;
+  int* d_pending = nullptr;
+  double* d_last_shift = nullptr;
+  int* d_flag = nullptr;
+  long long nstep = 0;
+  bool maps_dirty = true;
+  std::vector<char> pending;                    // host mirror of d_pending
+  cudaGraphExec_t graph = nullptr;
+  std::string err;
+};
+
+static int fail(lbmpcd* h, int code, const std::string& msg) {
+  if (h) h->err = msg; else g_create_error = msg;
+  return code;
+}
+static int cuda_fail(lbmpcd* h, cudaError_t e, const char* where) {
+  return fail(h, LBMPCD_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+#define CK(h, call)                                            \
+  do {                                                         \
+    cudaError_t e_ = (call);                                   \
+    if (e_ != cudaSuccess) return cuda_fail((h), e_, #call);   \
+  } while (0)
+
+static size_t real_size(int prec) { return prec == P_FP64 ? 8 : 4; }
+static size_t store_size(int prec) { return prec == P_FP64 ? 8 : (prec == P_FP32 ? 4 : 2); }
+
+static cudaError_t dalloc(std::vector<void*>& list, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) return cudaSuccess;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) { *p = nullptr; return e; }
+  list.push_back(*p);
+  return cudaMemset(*p, 0, bytes);
+}
+
+static void free_list(std::vector<void*>& list) {
+  for (void* p : list) cudaFree(p);
+  list.clear();
+}
+
+extern "C" void lbmpcd_destroy(lbmpcd* h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream); else cudaDeviceSynchronize();
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  for (auto& l : h->rep_allocs) free_list(l);
+  free_list(h->allocs);
+  delete h;
+}
+
+extern "C" const char* lbmpcd_last_error(const lbmpcd* h) {
+  return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+static int validate(const lbmpcd_params& p, std::string& why) {
+  if (p.lattice != LBMPCD_D2Q9 && p.lattice != LBMPCD_D3Q19) { why = "lattice must be 9 or 19"; return 0; }
+  if (p.nx < 1 || p.ny < 3 || p.nz < 1) { why = "need nx >= 1, ny >= 3, nz >= 1"; return 0; }
+  if (p.lattice == LBMPCD_D2Q9 && p.nz != 1) { why = "D2Q9 needs nz == 1"; return 0; }
+  if ((long long)p.nx * p.ny * p.nz > (1LL << 31)) { why = "lattice too large"; return 0; }
+  if (!(p.tau > 0.5)) { why = "tau must exceed 1/2"; return 0; }
+  if (p.refine < 1 || p.refine > 16) { why = "refine must be in [1,16]"; return 0; }
+  if (p.ppc < 1) { why = "ppc must be >= 1"; return 0; }
+  if (!(p.kT >= 0) || !(p.mass > 0)) { why = "need kT >= 0, mass > 0"; return 0; }
+  if (p.coupling_width < 0) { why = "coupling_width must be >= 0"; return 0; }
+  if (p.precision < 0 || p.precision > 2) { why = "precision must be 0, 1 or 2"; return 0; }
+  if (p.feedback < 0 || p.feedback > 1) { why = "feedback must be 0 or 1"; return 0; }
+  if (p.window < 1) { why = "window must be >= 1"; return 0; }
+  if (p.resample_density != 0) { why = "resample_density = 1 is not supported"; return 0; }
+  return 1;
+}
+
+extern "C" int lbmpcd_create(const lbmpcd_params* params, int n_replicas, void* cuda_stream, lbmpcd** out) {
+  if (out) *out = nullptr;
+  if (!params || !out || n_replicas < 1 || n_replicas > 65535)
+    return fail(nullptr, LBMPCD_ERR_INVALID_ARG, "null argument or bad replica count");
+  std::string why;
+  for (int r = 0; r < n_replicas; ++r) {
+    if (!validate(params[r], why)) return fail(nullptr, LBMPCD_ERR_INVALID_ARG, "replica " + std::to_string(r) + ": " + why);
+    if (params[r].lattice != params[0].lattice || params[r].precision != params[0].precision)
+      return fail(nullptr, LBMPCD_ERR_INVALID_ARG, "all replicas must share lattice and precision");
+  }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(nullptr, LBMPCD_ERR_CUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
+  lbmpcd* h = new (std::nothrow) lbmpcd();
+  if (!h) return fail(nullptr, LBMPCD_ERR_OOM, "host allocation failed");
+  h->P.assign(params, params + n_replicas);
+  h->nrep = n_replicas;
+  h->q = params[0].lattice;
+  h->dim = h->q == 9 ? 2 : 3;
+  h->prec = params[0].precision;
+  h->stream = (cudaStream_t)cuda_stream;
+  h->rd.resize(n_replicas);
+  h->rep_allocs.resize(n_replicas);
+  h->pending.assign(n_replicas, 0);
+  const size_t ss = store_size(h->prec), rs = real_size(h->prec);
+  for (int r = 0; r < n_replicas; ++r) {
+    const lbmpcd_params& p = params[r];
+    RepDev& d = h->rd[r];
+    memset(&d, 0, sizeof(d));
+    d.nx = p.nx; d.ny = p.ny; d.nz = p.nz; d.q = h->q;
+    d.omega = 1.0 / p.tau;
+    for (int a = 0; a < 3; ++a) d.g[a] = p.force[a];
+    if (h->dim == 2) d.g[2] = 0.0;
+    d.nnode = (long long)p.nx * p.ny * p.nz;
+    d.fp16_scale = 1.0f; d.fp16_inv = 1.0f;
+    d.r = p.refine; d.ppc = p.ppc; d.cw = p.coupling_width;
+    d.n_out = (p.coupling_width + 1) / 2; d.n_in = p.coupling_width / 2;
+    d.feedback = p.feedback; d.window = p.window;
+    d.kT = p.kT; d.mass = p.mass; d.sig = sqrt(p.kT / p.mass);
+    d.alpha = p.alpha; d.cos_a = cos(p.alpha); d.sin_a = sin(p.alpha);
+    d.key0 = (uint32_t)(p.seed & 0xFFFFFFFFu); d.key1 = (uint32_t)(p.seed >> 32); d.rep = (uint32_t)r;
+    std::vector<void*>& L = h->allocs;
+    e = dalloc(L, &d.f[0], h->q * d.nnode * ss);
+    if (e == cudaSuccess) e = dalloc(L, &d.f[1], h->q * d.nnode * ss);
+    if (e == cudaSuccess) e = dalloc(L, &d.rho, d.nnode * rs);
+    if (e == cudaSuccess) e = dalloc(L, &d.u, 3 * d.nnode * rs);
+    if (e != cudaSuccess) {
+      int code = e == cudaErrorMemoryAllocation ? LBMPCD_ERR_OOM : LBMPCD_ERR_CUDA;
+      std::string m = std::string("allocating LB arrays: ") + cudaGetErrorString(e);
+      lbmpcd_destroy(h);
+      return fail(nullptr, code, m);
+    }
+  }
+  void* tmp = nullptr;
+  e = dalloc(h->allocs, &tmp, sizeof(RepDev) * n_replicas); h->d_reps = (RepDev*)tmp;
+  if (e == cudaSuccess) { e = dalloc(h->allocs, &tmp, sizeof(StepInfo) * KCHUNK * n_replicas); h->d_si = (StepInfo*)tmp; }
+  if (e == cudaSuccess) { e = dalloc(h->allocs, &tmp, sizeof(uint32_t)); h->d_step = (uint32_t*)tmp; }
+  if (e == cudaSuccess) { e = dalloc(h->allocs, &tmp, sizeof(int) * n_replicas); h->d_pending = (int*)tmp; }
+  if (e == cudaSuccess) { e = dalloc(h->allocs, &tmp, sizeof(double) * 3 * n_replicas); h->d_last_shift = (double*)tmp; }
+  if (e == cudaSuccess) { e = dalloc(h->allocs, &tmp, sizeof(int) * 16); h->d_flag = (int*)tmp; }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    std::string m = std::string("allocating handle arrays: ") + cudaGetErrorString(e);
+    lbmpcd_destroy(h);
+    return fail(nullptr, LBMPCD_ERR_CUDA, m);
+  }
+  *out = h;
+  return LBMPCD_OK;
+}
+
+// Block maps: (replica, local block) per block of each kernel family.
+static int build_maps(lbmpcd* h) {
+  std::vector<int2> lb, pp, cc;
+  for (int r = 0; r < h->nrep; ++r) {
+    const RepDev& d = h->rd[r];
+    const int ntx = (d.nx + 255) / 256;
+    const long long nlb = (long long)ntx * (d.ny - 2) * d.nz;
+    for (long long b = 0; b < nlb; ++b) lb.push_back(make_int2(r, (int)b));
+    if (!d.has_region) continue;
+    const long long npb = (d.np + 255) / 256, ncb = (d.ncell + 255) / 256, nbb = (d.nbuf + 255) / 256;
+    for (long long b = 0; b < npb; ++b) pp.push_back(make_int2(r, (int)b));
+    for (long long b = 0; b < ncb; ++b) cc.push_back(make_int2(r, (int)b));
+    for (long long b = 0; b < nbb; ++b) cc.push_back(make_int2(r, (int)(-1 - b)));
+  }
+  int2** dst[3] = {&h->bm_lb, &h->bm_p, &h->bm_c};
+  int* cnt[3] = {&h->nb_lb, &h->nb_p, &h->nb_c};
+  std::vector<int2>* src[3] = {&lb, &pp, &cc};
+  for (int i = 0; i < 3; ++i) {
+    if (*dst[i]) {
+      cudaFree(*dst[i]);
+      for (auto it = h->allocs.begin(); it != h->allocs.end(); ++it)
+        if (*it == *dst[i]) { h->allocs.erase(it); break; }
+      *dst[i] = nullptr;
+    }
+    *cnt[i] = (int)src[i]->size();
+    if (src[i]->empty()) continue;
+    void* p = nullptr;
+    CK(h, dalloc(h->allocs, &p, sizeof(int2) * src[i]->size()));
+    *dst[i] = (int2*)p;
+    CK(h, cudaMemcpy(p, src[i]->data(), sizeof(int2) * src[i]->size(), cudaMemcpyHostToDevice));
+  }
+  CK(h, cudaMemcpy(h->d_reps, h->rd.data(), sizeof(RepDev) * h->nrep, cudaMemcpyHostToDevice));
+  if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
+  h->maps_dirty = false;
+  return LBMPCD_OK;
+}
+
+extern "C" int lbmpcd_set_region(lbmpcd* h, int replica, const int lo[3], const int hi[3]) {
+  if (!h) return LBMPCD_ERR_INVALID_ARG;
+  if (replica < 0 || replica >= h->nrep || !lo || !hi) return fail(h, LBMPCD_ERR_INVALID_ARG, "bad replica or null bounds");
+  if (h->nstep > 0) return fail(h, LBMPCD_ERR_STATE, "set_region must precede the first step");
+  RepDev& d = h->rd[replica];
+  const lbmpcd_params& p = h->P[replica];
+  if (d.has_region) return fail(h, LBMPCD_ERR_STATE, "region already set for this replica");
+  const int x0 = lo[0], x1 = hi[0];
+  if (!(lo[1] <= 1 && hi[1] >= p.ny - 1 && lo[2] <= 0 && hi[2] >= p.nz))
+    return fail(h, LBMPCD_ERR_INVALID_ARG, "region must span all fluid rows and all z (slab of whole columns)");
+  if (x0 < 0 || x1 > p.nx || x1 - x0 < 2 * p.coupling_width || x1 <= x0)
+    return fail(h, LBMPCD_ERR_INVALID_ARG, "region columns out of range or narrower than two coupling widths");
+  d.x0 = x0; d.x1 = x1;
+  d.Wx = (x1 - x0) * p.refine; d.Hy = (p.ny - 2) * p.refine; d.Wz = h->dim == 3 ? p.nz * p.refine : 1;
+  const bool fits = h->dim == 2 ? (d.Wx <= HomePack<2>::XMAX && d.Hy <= HomePack<2>::YMAX)
+                                : (d.Wx <= HomePack<3>::XMAX + 1 && d.Hy <= HomePack<3>::YMAX + 1 &&
+                                   d.Wz <= HomePack<3>::ZMAX + 1);
+  if (!fits) return fail(h, LBMPCD_ERR_INVALID_ARG, "region has more cells per axis than the packed home index holds");
+  d.np = (long long)d.Wx * d.Hy * d.Wz * p.ppc;
+  if (d.np >= (1LL << 32) - 1) return fail(h, LBMPCD_ERR_INVALID_ARG, "too many particles");
+  d.ncell = (long long)d.Wx * (d.Hy + 1) * d.Wz;
+  d.nbuf = 2LL * d.n_in * (p.ny - 2) * p.nz;
+  const size_t rs = real_size(h->prec);
+  std::vector<void*>& L = h->rep_allocs[replica];
+  void* t = nullptr;
+  cudaError_t e = cudaSuccess;
+#define A(ptr, bytes) if (e == cudaSuccess) { e = dalloc(L, &t, (bytes)); ptr = t; }
+  A(*(void**)&d.home, d.np * 4);
+  A(*(void**)&d.pid, d.np * 4);
+  for (int a = 0; a < h->dim; ++a) { A(d.off[a], d.np * rs); A(d.vel[a], d.np * rs); }
+  A(*(void**)&d.acc_n, d.ncell * 4);
+  A(*(void**)&d.count, d.ncell * 4);
+  for (int a = 0; a < h->dim; ++a) { A(d.acc_v[a], d.ncell * rs); A(d.vcm[a], d.ncell * rs); A(d.rot[a], d.ncell * rs); }
+  const long long nb4 = (d.nbuf > 0 ? d.nbuf : 1) * 4;
+  A(*(void**)&d.frame, nb4 * 8);
+  A(*(void**)&d.ring, nb4 * 8 * (long long)p.window);
+  A(*(void**)&d.wsum, nb4 * 8);
+  A(*(void**)&d.wmean, nb4 * 8);
+#undef A
+  if (e != cudaSuccess) {
+    free_list(L);
+    return fail(h, e == cudaErrorMemoryAllocation ? LBMPCD_ERR_OOM : LBMPCD_ERR_CUDA,
+                std::string("allocating region arrays: ") + cudaGetErrorString(e));
+  }
+  d.has_region = 1;
+  int rc = build_maps(h);
+  if (rc) return rc;
+  CK(h, launch_init_particles(h->dim, h->prec, h->d_reps + replica, d, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  return LBMPCD_OK;
+}
+
+static int run_chunk(lbmpcd* h, int kcount) {
+  Launch L{h->d_reps, h->nrep, h->d_si, h->stream};
+  CK(h, launch_prep(h->dim, L, h->d_si, kcount, h->d_step, h->d_pending, h->d_last_shift));
+  for (int k = 0; k < kcount; ++k) {
+    CK(h, launch_lb(h->q, h->prec, L, h->bm_lb, h->nb_lb, k));
+    CK(h, launch_particles(h->dim, h->prec, L, h->bm_p, h->nb_p, k));
+    CK(h, launch_cells(h->q, h->prec, L, h->bm_c, h->nb_c, k));
+  }
+  return LBMPCD_OK;
+}
+
+extern "C" int lbmpcd_step(lbmpcd* h, int nsteps) {
+  if (!h) return LBMPCD_ERR_INVALID_ARG;
+  if (nsteps < 0) return fail(h, LBMPCD_ERR_INVALID_ARG, "nsteps < 0");
+  if (h->maps_dirty) { int rc = build_maps(h); if (rc) return rc; }
+  int left = nsteps;
+  while (left >= KCHUNK) {
+    if (!h->graph) {
+      cudaGraph_t g = nullptr;
+      cudaStream_t cap = h->stream;
+      bool own = false;
+      if (!cap) { CK(h, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking)); own = true; }
+      if (own) CK(h, cudaDeviceSynchronize());
+      CK(h, cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+      cudaStream_t keep = h->stream;
+      h->stream = cap;
+      int rc = run_chunk(h, KCHUNK);
+      h->stream = keep;
+      cudaError_t e = cudaStreamEndCapture(cap, &g);
+      if (rc) { if (g) cudaGraphDestroy(g); if (own) cudaStreamDestroy(cap); return rc; }
+      if (e != cudaSuccess) { if (own) cudaStreamDestroy(cap); return cuda_fail(h, e, "graph capture"); }
+      e = cudaGraphInstantiate(&h->graph, g, 0);
+      cudaGraphDestroy(g);
+      if (own) cudaStreamDestroy(cap);
+      if (e != cudaSuccess) { h->graph = nullptr; return cuda_fail(h, e, "graph instantiate"); }
+    }
+    CK(h, cudaGraphLaunch(h->graph, h->stream));
+    left -= KCHUNK;
+    h->nstep += KCHUNK;
+  }
+  if (left > 0) {
+    int rc = run_chunk(h, left);
+    if (rc) return rc;
+    h->nstep += left;
+  }
+  if (nsteps > 0)
+    for (int r = 0; r < h->nrep; ++r) h->pending[r] = h->rd[r].has_region ? 1 : 0;
+  return LBMPCD_OK;
+}
+
+extern "C" int lbmpcd_step_profiled(lbmpcd* h, int nsteps, double* phase_ms, long long* launches) {
+  if (!h) return LBMPCD_ERR_INVALID_ARG;
+  if (nsteps < 0 || !phase_ms) return fail(h, LBMPCD_ERR_INVALID_ARG, "nsteps < 0 or null phase_ms");
+  if (h->maps_dirty) { int rc = build_maps(h); if (rc) return rc; }
+  const int nev = 2 * (1 + 3 * KCHUNK);
+  std::vector<cudaEvent_t> ev(nev, nullptr);
+  for (auto& x : ev) CK(h, cudaEventCreate(&x));
+  Launch L{h->d_reps, h->nrep, h->d_si, h->stream};
+  int rc = LBMPCD_OK;
+  long long nl = 0;
+  int left = nsteps;
+  cudaError_t e = cudaSuccess;
+  while (left > 0 && e == cudaSuccess) {
+    const int kc = left < KCHUNK ? left : KCHUNK;
+    int ie = 0;
+    std::vector<int> phase;
+    auto bracket = [&](int ph, auto&& fn) {
+      if (e != cudaSuccess) return;
+      e = cudaEventRecord(ev[ie++], h->stream);
+      if (e == cudaSuccess) e = fn();
+      if (e == cudaSuccess) e = cudaEventRecord(ev[ie++], h->stream);
+      phase.push_back(ph);
+      ++nl;
+    };
+    bracket(0, [&] { return launch_prep(h->dim, L, h->d_si, kc, h->d_step, h->d_pending, h->d_last_shift); });
+    for (int k = 0; k < kc; ++k) {
+      bracket(1, [&] { return launch_lb(h->q, h->prec, L, h->bm_lb, h->nb_lb, k); });
+      if (h->nb_p) bracket(2, [&] { return launch_particles(h->dim, h->prec, L, h->bm_p, h->nb_p, k); });
+      if (h->nb_c) bracket(3, [&] { return launch_cells(h->q, h->prec, L, h->bm_c, h->nb_c, k); });
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    for (size_t i = 0; i < phase.size() && e == cudaSuccess; ++i) {
+      float ms = 0;
+      e = cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]);
+      phase_ms[phase[i]] += ms;
+    }
+    left -= kc;
+    h->nstep += kc;
+  }
+  for (auto& x : ev) cudaEventDestroy(x);
+  if (e != cudaSuccess) rc = cuda_fail(h, e, "step_profiled");
+  if (nsteps > 0)
+    for (int r = 0; r < h->nrep; ++r) h->pending[r] = h->rd[r].has_region ? 1 : 0;
+  if (launches) *launches += nl;
+  return rc;
+}
+
+static long long field_elems(const lbmpcd* h, int r, int field) {
+  const RepDev& d = h->rd[r];
+  switch (field) {
+    case LBMPCD_RHO: return d.nnode;
+    case LBMPCD_U: return 3 * d.nnode;
+    case LBMPCD_POPS: return (long long)h->q * d.nnode;
+    case LBMPCD_PART_POS: case LBMPCD_PART_VEL: case LBMPCD_PART_HOME: return d.has_region ? 3 * d.np : -1;
+    case LBMPCD_PART_CELL: case LBMPCD_PART_ID: return d.has_region ? d.np : -1;
+    case LBMPCD_SHIFT: return 3;
+    case LBMPCD_CELL_COUNT: return d.has_region ? d.ncell : -1;
+    case LBMPCD_CELL_VCM: return d.has_region ? 3 * d.ncell : -1;
+    case LBMPCD_WINDOW_MEAN: return d.has_region ? 4 * d.nbuf : -1;
+    case LBMPCD_DIAG: return 9;
+  }
+  return -1;
+}
+static bool int_field(int f) {
+  return f == LBMPCD_PART_CELL || f == LBMPCD_CELL_COUNT || f == LBMPCD_PART_HOME || f == LBMPCD_PART_ID;
+}
+
+extern "C" long long lbmpcd_field_size(const lbmpcd* h, int replica, int field) {
+  if (!h || replica < 0 || replica >= h->nrep) return LBMPCD_ERR_INVALID_ARG;
+  long long n = field_elems(h, replica, field);
+  return n < 0 ? LBMPCD_ERR_INVALID_ARG : n;
+}
+
+static int flush_if_pending(lbmpcd* h, int r) {
+  if (!h->pending[r] || !h->rd[r].has_region) return LBMPCD_OK;
+  double ls[3];
+  CK(h, cudaMemcpyAsync(ls, h->d_last_shift + 3 * r, sizeof(ls), cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  CK(h, launch_flush(h->dim, h->prec, h->d_reps + r, h->rd[r], ls, h->stream));
+  CK(h, cudaMemsetAsync(h->d_pending + r, 0, sizeof(int), h->stream));
+  h->pending[r] = 0;
+  return LBMPCD_OK;
+}
+
+extern "C" int lbmpcd_get_fields(lbmpcd* h, int replica, int field, void* dst, size_t bytes, int dst_on_device) {
+  if (!h) return LBMPCD_ERR_INVALID_ARG;
+  if (replica < 0 || replica >= h->nrep || !dst) return fail(h, LBMPCD_ERR_INVALID_ARG, "bad replica or null dst");
+  const long long n = field_elems(h, replica, field);
+  if (n < 0) return fail(h, LBMPCD_ERR_INVALID_ARG, "unknown field (or no region set)");
+  const size_t esz = int_field(field) ? 4 : 8;
+  if (bytes != (size_t)n * esz) return fail(h, LBMPCD_ERR_INVALID_ARG, "dst size does not match the field");
+  if (h->maps_dirty) { int rc = build_maps(h); if (rc) return rc; }
+  const RepDev& d = h->rd[replica];
+  void* buf = dst;
+  void* tmp = nullptr;
+  if (!dst_on_device && n > 0) {
+    CK(h, cudaMalloc(&tmp, bytes));
+    buf = tmp;
+  }
+  int rc = LBMPCD_OK;
+  cudaError_t e = cudaSuccess;
+  const int parity = (int)(h->nstep & 1);
+  double ls[3] = {0, 0, 0};
+  switch (field) {
+    case LBMPCD_RHO: e = launch_real_out(h->prec, d.rho, d.nnode, (double*)buf, h->stream); break;
+    case LBMPCD_U: e = launch_real_out(h->prec, d.u, 3 * d.nnode, (double*)buf, h->stream); break;
+    case LBMPCD_POPS: e = launch_pops_out(h->q, h->prec, d, parity, (double*)buf, h->stream); break;
+    case LBMPCD_PART_POS: case LBMPCD_PART_VEL: case LBMPCD_PART_HOME: case LBMPCD_PART_CELL:
+    case LBMPCD_PART_ID:
+      rc = flush_if_pending(h, replica);
+      if (rc) break;
+      e = cudaMemcpyAsync(ls, h->d_last_shift + 3 * replica, sizeof(ls), cudaMemcpyDeviceToHost, h->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+      if (e == cudaSuccess) e = launch_part_out(h->dim, h->prec, d, field, ls, buf, h->stream);
+      break;
+    case LBMPCD_SHIFT:
+      e = cudaMemcpyAsync(buf, h->d_last_shift + 3 * replica, 3 * sizeof(double),
+                          dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToDevice, h->stream);
+      break;
+    case LBMPCD_CELL_COUNT:
+      e = cudaMemcpyAsync(buf, d.count, d.ncell * 4, cudaMemcpyDeviceToDevice, h->stream);
+      break;
+    case LBMPCD_CELL_VCM: {
+      double* o = (double*)buf;
+      e = cudaMemsetAsync(o, 0, 3 * d.ncell * 8, h->stream);
+      // [ncell][3] from three structure-of-arrays columns
+      std::vector<double> host;
+      for (int a = 0; a < h->dim && e == cudaSuccess; ++a) {
+        double* col = nullptr;
+        e = cudaMalloc(&col, d.ncell * 8);
+        if (e != cudaSuccess) break;
+        e = launch_real_out(h->prec, d.vcm[a], d.ncell, col, h->stream);
+        if (e == cudaSuccess)
+          e = cudaMemcpy2DAsync(o + a, 3 * 8, col, 8, 8, d.ncell, cudaMemcpyDeviceToDevice, h->stream);
+        cudaError_t e2 = cudaStreamSynchronize(h->stream);
+        cudaFree(col);
+        if (e == cudaSuccess) e = e2;
+      }
+      break;
+    }
+    case LBMPCD_WINDOW_MEAN:
+      e = cudaMemcpyAsync(buf, d.wmean, d.nbuf * 4 * 8, cudaMemcpyDeviceToDevice, h->stream);
+      break;
+    case LBMPCD_DIAG: {
+      double* o = (double*)buf;
+      e = cudaMemsetAsync(o, 0, 9 * 8, h->stream);
+      if (e == cudaSuccess) e = launch_diag_lb(h->q, h->prec, d, parity, o, h->stream);
+      if (e == cudaSuccess && d.has_region) {
+        rc = flush_if_pending(h, replica);
+        if (!rc) e = launch_diag_particles(h->dim, h->prec, d, o, h->stream);
+      }
+      break;
+    }
+  }
+  if (rc == LBMPCD_OK && e == cudaSuccess && tmp) e = cudaMemcpyAsync(dst, tmp, bytes, cudaMemcpyDeviceToHost, h->stream);
+  if (rc == LBMPCD_OK && e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (tmp) cudaFree(tmp);
+  if (rc) return rc;
+  if (e != cudaSuccess) return cuda_fail(h, e, "get_fields");
+  return LBMPCD_OK;
+}
+
+extern "C" int lbmpcd_set_state(lbmpcd* h, int replica, int field, const void* src, size_t bytes, int src_on_device) {
+  if (!h) return LBMPCD_ERR_INVALID_ARG;
+  if (replica < 0 || replica >= h->nrep || !src) return fail(h, LBMPCD_ERR_INVALID_ARG, "bad replica or null src");
+  if (field != LBMPCD_POPS && field != LBMPCD_PART_POS && field != LBMPCD_PART_VEL && field != LBMPCD_PART_HOME)
+    return fail(h, LBMPCD_ERR_INVALID_ARG, "only POPS, PART_POS, PART_VEL and PART_HOME can be set");
+  const RepDev& d = h->rd[replica];
+  if (field != LBMPCD_POPS && !d.has_region) return fail(h, LBMPCD_ERR_STATE, "particles need a region first");
+  const long long n = field_elems(h, replica, field);
+  const size_t esz = int_field(field) ? 4 : 8;
+  if (bytes != (size_t)n * esz) return fail(h, LBMPCD_ERR_INVALID_ARG, "src size does not match the field");
+  if (h->maps_dirty) { int rc = build_maps(h); if (rc) return rc; }
+  if (field != LBMPCD_POPS) { int rc = flush_if_pending(h, replica); if (rc) return rc; }
+  const void* buf = src;
+  void* tmp = nullptr;
+  if (!src_on_device) {
+    CK(h, cudaMalloc(&tmp, bytes));
+    cudaError_t e = cudaMemcpyAsync(tmp, src, bytes, cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) { cudaFree(tmp); return cuda_fail(h, e, "set_state copy"); }
+    buf = tmp;
+  }
+  cudaError_t e = cudaSuccess;
+  if (field == LBMPCD_POPS) {
+    e = launch_pops_in(h->q, h->prec, d, (const double*)buf, h->stream);
+  } else {
+    e = cudaMemsetAsync(h->d_flag, 0, sizeof(int), h->stream);
+    if (e == cudaSuccess) e = launch_part_in(h->dim, h->prec, d, field, buf, h->d_flag, h->stream);
+  }
+  int bad = 0;
+  if (e == cudaSuccess && field != LBMPCD_POPS)
+    e = cudaMemcpyAsync(&bad, h->d_flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (tmp) cudaFree(tmp);
+  if (e != cudaSuccess) return cuda_fail(h, e, "set_state");
+  if (bad) return fail(h, LBMPCD_ERR_INVALID_ARG, "particle positions out of range (state partly written)");
+  return LBMPCD_OK;
+}

@@ -1,0 +1,616 @@
+// mpcd.cu -- the MPCD half of the coupled step and both coupling directions.
+//
+// Per step n the handle runs   lb_pull(n) -> particle_pass(n) -> cell_pass(n):
+//   particle_pass  one thread per particle, structure-of-arrays state
+//                  (packed integer home cell, offsets, velocities):
+//                    a7(n-1)  rotate v about the v_cm of its collision cell
+//                             of step n-1 (table written by cell_pass(n-1)),
+//                    a2+a3    outer-buffer particles: v = u_fine + sqrt(kT/m) xi,
+//                             u_fine by bilinear/trilinear interpolation of
+//                             the LB velocity (Algorithms 1-2, Sec. 2.3),
+//                    a4       kick-drift streaming (Eq. 3), bounce-back walls,
+//                             periodic wrap in the region,
+//                    a6       inner-buffer particles add m, m v to the frame,
+//                    a5       binning under the step's random shift and a
+//                             warp-aggregated reduction (__match_any_sync
+//                             groups, one atomic per group and cell);
+//   cell_pass      one thread per collision cell: v_cm with virtual wall
+//                  particles, rotation draw (Eq. 4), accumulators cleared;
+//                  extra blocks run a8: windowed moments of the inner buffer
+//                  -> f_eq populations written into the LB buffer.
+// The collision of the last step is applied lazily (flush) before particle
+// state is read out, so the visible state is always post-collision.
+//
+// This translation unit is compiled with -fmad=false: streaming and binning
+// then perform exactly the IEEE operations their comments describe, so FP64
+// runs bin every particle into the same cell as a binary64 reference would.
+#include "kernels.h"
+
+namespace lbm {
+
+template <typename R> struct Num;
+template <> struct Num<double> { static constexpr double one_minus = 1.0 - 1.0 / 9007199254740992.0; };
+template <> struct Num<float> { static constexpr float one_minus = 1.0f - 1.0f / 16777216.0f; };
+
+__device__ __forceinline__ int wrap(int a, int m) { a %= m; return a < 0 ? a + m : a; }
+
+// ---------------------------------------------------------------------------
+// prep: one block; per (step k of the chunk, replica) the global step index,
+// the random shift of that step and of the previous one, and whether the
+// previous collision is still pending.
+__global__ void prep_steps(const RepDev* __restrict__ reps, int nrep, int dim, int kcount,
+                           StepInfo* __restrict__ si, uint32_t* d_step, int* d_pending,
+                           double* d_last_shift) {
+  const uint32_t n0 = *d_step;
+  for (int idx = threadIdx.x; idx < kcount * nrep; idx += blockDim.x) {
+    const int k = idx / nrep, r = idx % nrep;
+    const RepDev& rd = reps[r];
+    StepInfo s;
+    s.n = n0 + k;
+    s.pending = (k == 0) ? d_pending[r] : 1;
+    s.write_moments = (k == kcount - 1);
+    s.pad = 0;
+    const uint4 w = philox(0u, s.n, rd.rep, TAG_SHIFT, rd.key0, rd.key1);
+    s.shift[0] = unit24(w.x);
+    s.shift[1] = unit24(w.y);
+    s.shift[2] = dim == 3 ? unit24(w.z) : 0.0;
+    if (k == 0) {
+      for (int a = 0; a < 3; ++a) s.prev[a] = d_last_shift[3 * r + a];
+    } else {
+      const uint4 p = philox(0u, s.n - 1, rd.rep, TAG_SHIFT, rd.key0, rd.key1);
+      s.prev[0] = unit24(p.x);
+      s.prev[1] = unit24(p.y);
+      s.prev[2] = dim == 3 ? unit24(p.z) : 0.0;
+    }
+    si[idx] = s;
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < nrep; r += blockDim.x) {
+    const StepInfo& last = si[(kcount - 1) * nrep + r];
+    for (int a = 0; a < 3; ++a) d_last_shift[3 * r + a] = last.shift[a];
+    d_pending[r] = reps[r].has_region ? 1 : 0;
+  }
+  if (threadIdx.x == 0) *d_step = n0 + kcount;
+}
+
+cudaError_t launch_prep(int dim, const Launch& L, StepInfo* si, int kcount, uint32_t* d_step, int* d_pending,
+                        double* d_last_shift) {
+  prep_steps<<<1, 256, 0, L.stream>>>(L.reps, L.nrep, dim, kcount, si, d_step, d_pending, d_last_shift);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// a5: the collision cell of a particle under shift s: per axis the home
+// index plus one when offset + s >= 1 (the sum rounded in storage precision),
+// wrapped in x and z.  id = cx + Wx (cy + (Hy+1) cz).
+template <int D, typename R>
+__device__ __forceinline__ uint32_t collision_cell(const RepDev& rd, int X, int Y, int Z, const R* o,
+                                                   const double* s) {
+  int cx = X + ((o[0] + (R)s[0]) >= R(1) ? 1 : 0);
+  if (cx >= rd.Wx) cx -= rd.Wx;
+  const int cy = Y + ((o[1] + (R)s[1]) >= R(1) ? 1 : 0);
+  int cz = 0;
+  if (D == 3) {
+    cz = Z + ((o[2] + (R)s[2]) >= R(1) ? 1 : 0);
+    if (cz >= rd.Wz) cz -= rd.Wz;
+  }
+  return (uint32_t)(cx + rd.Wx * (cy + (rd.Hy + 1) * cz));
+}
+
+// a7, particle side: v <- v_cm + R (v - v_cm).  2D: R = rotation by theta
+// with sin(theta) stored per cell; 3D: Rodrigues' formula about the cell axis.
+template <int D, typename R>
+__device__ __forceinline__ void rotate(const RepDev& rd, uint32_t c, R* v) {
+  const R ca = (R)rd.cos_a;
+  if (D == 2) {
+    const R vcx = ((const R*)rd.vcm[0])[c], vcy = ((const R*)rd.vcm[1])[c];
+    const R sn = ((const R*)rd.rot[0])[c];
+    const R wx = v[0] - vcx, wy = v[1] - vcy;
+    v[0] = vcx + (ca * wx - sn * wy);
+    v[1] = vcy + (sn * wx + ca * wy);
+  } else {
+    const R sa = (R)rd.sin_a;
+    R vc[3], n[3], w[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      vc[a] = ((const R*)rd.vcm[a])[c];
+      n[a] = ((const R*)rd.rot[a])[c];
+      w[a] = v[a] - vc[a];
+    }
+    const R cr[3] = {n[1] * w[2] - n[2] * w[1], n[2] * w[0] - n[0] * w[2], n[0] * w[1] - n[1] * w[0]};
+    const R nw = n[0] * w[0] + n[1] * w[1] + n[2] * w[2];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) v[a] = vc[a] + (w[a] * ca + cr[a] * sa + n[a] * nw * (R(1) - ca));
+  }
+}
+
+// LB velocity at node (x,y,z) with periodic x, z and the wall ghost
+// u(0) = -u(1), u(ny-1) = -u(ny-2) that puts u = 0 on the half-way walls.
+template <typename R>
+__device__ __forceinline__ double u_node(const RepDev& rd, int a, int x, int y, int z) {
+  x = wrap(x, rd.nx);
+  z = wrap(z, rd.nz);
+  double sgn = 1.0;
+  if (y <= 0) { y = 1; sgn = -1.0; }
+  if (y >= rd.ny - 1) { y = rd.ny - 2; sgn = -1.0; }
+  const R* u = (const R*)rd.u;
+  return sgn * (double)u[a * rd.nnode + x + (long long)rd.nx * (y + (long long)rd.ny * z)];
+}
+
+// a2: bilinear (2D) / trilinear (3D) interpolation of the LB velocity, known
+// at node centres, to the centre of MPCD cell (X,Y,Z) (Algorithm 2).
+template <int D, typename R>
+__device__ void u_fine(const RepDev& rd, int X, int Y, int Z, double* out) {
+  const double r = rd.r;
+  const double px = rd.x0 + (X + 0.5) / r - 0.5;
+  const double py = 1.0 + (Y + 0.5) / r - 0.5;
+  const double pz = (D == 3) ? (Z + 0.5) / r - 0.5 : 0.0;
+  const int i0 = (int)floor(px), j0 = (int)floor(py), k0 = (int)floor(pz);
+  const double tx = px - i0, ty = py - j0, tz = pz - k0;
+  for (int a = 0; a < D; ++a) {
+    double acc = 0;
+    for (int di = 0; di < 2; ++di)
+      for (int dj = 0; dj < 2; ++dj)
+        for (int dk = 0; dk < (D == 3 ? 2 : 1); ++dk) {
+          double wgt = (di ? tx : 1 - tx) * (dj ? ty : 1 - ty);
+          if (D == 3) wgt *= (dk ? tz : 1 - tz);
+          acc += wgt * u_node<R>(rd, a, i0 + di, j0 + dj, k0 + dk);
+        }
+    out[a] = acc;
+  }
+}
+
+// a4: kick (v += g) then drift r += v dt (Eq. 3, dt = 1, r in cell units so the
+// displacement is v r); a wall crossing reverses v and retraces the rest of
+// the step; x (and z) wrap periodically in the region.
+template <int D, typename R>
+__device__ __forceinline__ void stream(const RepDev& rd, int& X, int& Y, int& Z, R* o, R* v) {
+  v[0] += (R)rd.g[0];
+  v[1] += (R)rd.g[1];
+  if (D == 3) v[2] += (R)rd.g[2];
+  const R rr = (R)rd.r;
+  const R dx = v[0] * rr, dy = v[1] * rr, dz = (D == 3) ? v[2] * rr : R(0);
+  const R ty = o[1] + dy;
+  const int ky = (int)floor(ty);
+  const int nyc = Y + ky;
+  R dxe = dx, dze = dz;
+  if (nyc < 0 || nyc >= rd.Hy) {
+    const R Lw = (nyc < 0) ? (R)(-Y) : (R)(rd.Hy - Y);   // wall, local units
+    const R ts = (Lw - o[1]) / dy;                       // fraction before the hit
+    const R tr = Lw - (ty - Lw);                         // mirrored end point
+#pragma unroll
+    for (int a = 0; a < D; ++a) v[a] = -v[a];
+    dxe = dx * ts - dx * (R(1) - ts);
+    dze = dz * ts - dz * (R(1) - ts);
+    const int kr = (int)floor(tr);
+    Y += kr;
+    o[1] = tr - (R)kr;
+    if (Y >= rd.Hy) { Y = rd.Hy - 1; o[1] = Num<R>::one_minus; }
+    if (Y < 0) { Y = 0; o[1] = R(0); }
+  } else {
+    Y = nyc;
+    o[1] = ty - (R)ky;
+  }
+  if (o[1] >= R(1)) {
+    o[1] -= R(1);
+    Y += 1;
+    if (Y >= rd.Hy) { Y = rd.Hy - 1; o[1] = Num<R>::one_minus; }
+  }
+  const R tx = o[0] + dxe;
+  int kx = (int)floor(tx);
+  o[0] = tx - (R)kx;
+  if (o[0] >= R(1)) { o[0] -= R(1); kx += 1; }
+  X = wrap(X + kx, rd.Wx);
+  if (D == 3) {
+    const R tz = o[2] + dze;
+    int kz = (int)floor(tz);
+    o[2] = tz - (R)kz;
+    if (o[2] >= R(1)) { o[2] -= R(1); kz += 1; }
+    Z = wrap(Z + kz, rd.Wz);
+  }
+}
+
+template <int D, typename R>
+__global__ void __launch_bounds__(256) particle_pass(const RepDev* __restrict__ reps, const int2* __restrict__ bmap,
+                                                     const StepInfo* __restrict__ si, int k, int nrep) {
+  __shared__ R sv[D][256];
+  const int2 bm = bmap[blockIdx.x];
+  const RepDev& rd = reps[bm.x];
+  const StepInfo& st = si[k * nrep + bm.x];
+  const long long j = (long long)bm.y * blockDim.x + threadIdx.x;
+  const bool active = j < rd.np;
+  int X = 0, Y = 0, Z = 0;
+  R o[3] = {R(0), R(0), R(0)}, v[3] = {R(0), R(0), R(0)};
+  uint32_t cid = 0xFFFFFFFFu;
+  if (active) {
+    HomePack<D>::unpack(rd.home[j], X, Y, Z);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      o[a] = ((const R*)rd.off[a])[j];
+      v[a] = ((const R*)rd.vel[a])[j];
+    }
+    // a7 of step n-1
+    if (st.pending) rotate<D, R>(rd, collision_cell<D, R>(rd, X, Y, Z, o, st.prev), v);
+    // a2 + a3: Maxwellian redraw in the outer buffer columns
+    const int xl = X / rd.r, wcols = rd.x1 - rd.x0;
+    if (xl < rd.n_out || xl >= wcols - rd.n_out) {
+      double uf[3] = {0, 0, 0};
+      u_fine<D, R>(rd, X, Y, Z, uf);
+      const uint4 w = philox(rd.pid[j], st.n, rd.rep, TAG_RESAMPLE, rd.key0, rd.key1);
+      double z0, z1, z2, z3;
+      normal_pair(w.x, w.y, z0, z1);
+      normal_pair(w.z, w.w, z2, z3);
+      v[0] = (R)(uf[0] + rd.sig * z0);
+      v[1] = (R)(uf[1] + rd.sig * z1);
+      if (D == 3) v[2] = (R)(uf[2] + rd.sig * z2);
+    }
+    // a4
+    stream<D, R>(rd, X, Y, Z, o, v);
+    // a6: inner-buffer sample (unshifted cells), binary64 atomics
+    if (rd.n_in > 0) {
+      const int xn = X / rd.r;
+      int side = -1, col = 0;
+      if (xn >= rd.n_out && xn < rd.cw) { side = 0; col = xn - rd.n_out; }
+      else if (xn < wcols - rd.n_out && xn >= wcols - rd.cw) { side = 1; col = wcols - 1 - rd.n_out - xn; }
+      if (side >= 0) {
+        const int zl = (D == 3) ? Z / rd.r : 0;
+        const long long b = (((long long)side * rd.n_in + col) * rd.nz + zl) * (rd.ny - 2) + Y / rd.r;
+        double* fr = rd.frame + 4 * b;
+        atomicAdd(fr, rd.mass);
+#pragma unroll
+        for (int a = 0; a < D; ++a) atomicAdd(fr + 1 + a, rd.mass * (double)v[a]);
+      }
+    }
+    // a5: binning under this step's shift
+    cid = collision_cell<D, R>(rd, X, Y, Z, o, st.shift);
+    rd.home[j] = HomePack<D>::pack(X, Y, Z);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      ((R*)rd.off[a])[j] = o[a];
+      ((R*)rd.vel[a])[j] = v[a];
+    }
+  }
+  // warp-aggregated reduction: lanes sharing a collision cell are summed by
+  // their lowest lane, which issues one atomic per accumulator.
+  const unsigned grp = __match_any_sync(0xFFFFFFFFu, cid);
+  const int lane = threadIdx.x & 31, wbase = threadIdx.x & ~31;
+#pragma unroll
+  for (int a = 0; a < D; ++a) sv[a][threadIdx.x] = v[a];
+  __syncwarp();
+  if (active && lane == __ffs(grp) - 1) {
+    R acc[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) acc[a] = R(0);
+    unsigned m = grp;
+    while (m) {
+      const int l = __ffs(m) - 1;
+      m &= m - 1;
+#pragma unroll
+      for (int a = 0; a < D; ++a) acc[a] += sv[a][wbase + l];
+    }
+    atomicAdd(rd.acc_n + cid, (uint32_t)__popc(grp));
+#pragma unroll
+    for (int a = 0; a < D; ++a) atomicAdd((R*)rd.acc_v[a] + cid, acc[a]);
+  }
+}
+
+cudaError_t launch_particles(int dim, int prec, const Launch& L, const int2* bmap, int nblocks, int k) {
+  if (nblocks == 0) return cudaSuccess;
+  if (dim == 2) {
+    if (prec == P_FP64) particle_pass<2, double><<<nblocks, 256, 0, L.stream>>>(L.reps, bmap, L.si, k, L.nrep);
+    else particle_pass<2, float><<<nblocks, 256, 0, L.stream>>>(L.reps, bmap, L.si, k, L.nrep);
+  } else {
+    if (prec == P_FP64) particle_pass<3, double><<<nblocks, 256, 0, L.stream>>>(L.reps, bmap, L.si, k, L.nrep);
+    else particle_pass<3, float><<<nblocks, 256, 0, L.stream>>>(L.reps, bmap, L.si, k, L.nrep);
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// cell_pass: a7 cell part and a8.
+template <int Q, typename S>
+__global__ void __launch_bounds__(256) cell_pass(const RepDev* __restrict__ reps, const int2* __restrict__ bmap,
+                                                 const StepInfo* __restrict__ si, int k, int nrep) {
+  using R = typename Store<S>::R;
+  using L = Lattice<Q>;
+  constexpr int D = L::D;
+  const int2 bm = bmap[blockIdx.x];
+  const RepDev& rd = reps[bm.x];
+  const StepInfo& st = si[k * nrep + bm.x];
+  if (bm.y >= 0) {
+    const long long c = (long long)bm.y * blockDim.x + threadIdx.x;
+    if (c >= rd.ncell) return;
+    const uint32_t n = rd.acc_n[c];
+    R vc[3] = {R(0), R(0), R(0)}, rt[3] = {R(0), R(0), R(0)};
+    if (n > 0) {
+      const int cy = (int)((c / rd.Wx) % (rd.Hy + 1));
+      const bool cut = (cy == 0 || cy == rd.Hy) && st.shift[1] > 0.0;
+      if (cut && (int)n < rd.ppc) {
+        // Lamura-type wall: ppc - n virtual particles at rest, summed momentum
+        // drawn from N(0, (ppc - n) m kT) per component.
+        const int nv = rd.ppc - (int)n;
+        const uint4 w = philox((uint32_t)c, st.n, rd.rep, TAG_VIRT, rd.key0, rd.key1);
+        double z[4];
+        normal_pair(w.x, w.y, z[0], z[1]);
+        normal_pair(w.z, w.w, z[2], z[3]);
+        const double sd = sqrt((double)nv * rd.kT / rd.mass);
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+          vc[a] = (R)(((double)((const R*)rd.acc_v[a])[c] + sd * z[a]) / (double)(rd.ppc));
+      } else {
+#pragma unroll
+        for (int a = 0; a < D; ++a) vc[a] = ((const R*)rd.acc_v[a])[c] / (R)n;
+      }
+      if (D == 2) {
+        const uint4 w = philox((uint32_t)c, st.n, rd.rep, TAG_SIGN, rd.key0, rd.key1);
+        rt[0] = (w.x >> 31) ? (R)rd.sin_a : -(R)rd.sin_a;
+      } else {
+        const uint4 w = philox((uint32_t)c, st.n, rd.rep, TAG_AXIS, rd.key0, rd.key1);
+        if (sizeof(R) == 8) {
+          const double zc = 2.0 * unit24(w.x) - 1.0;
+          double sp, cp;
+          sincospi(2.0 * unit24(w.y), &sp, &cp);
+          const double rh = sqrt(1.0 - zc * zc);
+          rt[0] = (R)(rh * cp); rt[1] = (R)(rh * sp); rt[2] = (R)zc;
+        } else {
+          const float zc = 2.0f * unit24f(w.x) - 1.0f;
+          float sp, cp;
+          sincospif(2.0f * unit24f(w.y), &sp, &cp);
+          const float rh = sqrtf(1.0f - zc * zc);
+          rt[0] = (R)(rh * cp); rt[1] = (R)(rh * sp); rt[2] = (R)zc;
+        }
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      ((R*)rd.vcm[a])[c] = vc[a];
+      ((R*)rd.rot[a])[c] = rt[a];
+      ((R*)rd.acc_v[a])[c] = R(0);
+    }
+    rd.count[c] = (int)n;
+    rd.acc_n[c] = 0u;
+    return;
+  }
+  // a8: one thread per inner-buffer LB node
+  const long long b = (long long)(-1 - bm.y) * blockDim.x + threadIdx.x;
+  if (b >= rd.nbuf) return;
+  double* fr = rd.frame + 4 * b;
+  double* ws = rd.wsum + 4 * b;
+  double* rg = rd.ring + 4 * ((long long)(st.n % (uint32_t)rd.window) * rd.nbuf + b);
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const double x = fr[a];
+    ws[a] += x - rg[a];
+    rg[a] = x;
+    fr[a] = 0.0;
+  }
+  const double nf = (double)min((long long)st.n + 1, (long long)rd.window);
+  const double rdim = (D == 3) ? (double)rd.r * rd.r * rd.r : (double)rd.r * rd.r;
+  const double M = ws[0];
+  const double rho = M / ((double)rd.ppc * rd.mass * rdim * nf);
+  double u[3] = {0, 0, 0};
+  if (M > 0) { u[0] = ws[1] / M; u[1] = ws[2] / M; u[2] = ws[3] / M; }
+  double* wm = rd.wmean + 4 * b;
+  wm[0] = rho; wm[1] = u[0]; wm[2] = u[1]; wm[3] = u[2];
+  if (!(rd.feedback == 1 && st.n >= 1 && M > 0)) return;
+  long long t = b;
+  const int y = 1 + (int)(t % (rd.ny - 2)); t /= (rd.ny - 2);
+  const int z = (int)(t % rd.nz); t /= rd.nz;
+  const int col = (int)(t % rd.n_in), side = (int)(t / rd.n_in);
+  const int x = side == 0 ? rd.x0 + rd.n_out + col : rd.x1 - 1 - rd.n_out - col;
+  S* dst = (S*)rd.f[(st.n & 1) ^ 1];
+  const long long node = x + (long long)rd.nx * (y + (long long)rd.ny * z);
+  const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const double cu = L::cx(i) * u[0] + L::cy(i) * u[1] + L::cz(i) * u[2];
+    const double dev = L::w(i) * ((rho - 1.0) + rho * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu));
+    Store<S>::st(dst + i * rd.nnode + node, (R)dev, rd.fp16_scale);
+  }
+}
+
+cudaError_t launch_cells(int q, int prec, const Launch& L, const int2* bmap, int nblocks, int k) {
+  if (nblocks == 0) return cudaSuccess;
+#define LBM_CELLS(QQ, SS) cell_pass<QQ, SS><<<nblocks, 256, 0, L.stream>>>(L.reps, bmap, L.si, k, L.nrep)
+  if (q == 9) {
+    if (prec == P_FP64) LBM_CELLS(9, double);
+    else if (prec == P_FP32) LBM_CELLS(9, float);
+    else LBM_CELLS(9, __half);
+  } else {
+    if (prec == P_FP64) LBM_CELLS(19, double);
+    else if (prec == P_FP32) LBM_CELLS(19, float);
+    else LBM_CELLS(19, __half);
+  }
+#undef LBM_CELLS
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// flush: a7 of the last step for every particle of one replica.
+template <int D, typename R>
+__global__ void flush_collision(const RepDev* __restrict__ rdp, double s0, double s1, double s2) {
+  const RepDev& rd = *rdp;
+  const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (j >= rd.np) return;
+  const double s[3] = {s0, s1, s2};
+  int X, Y, Z;
+  HomePack<D>::unpack(rd.home[j], X, Y, Z);
+  R o[3] = {R(0), R(0), R(0)}, v[3] = {R(0), R(0), R(0)};
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    o[a] = ((const R*)rd.off[a])[j];
+    v[a] = ((const R*)rd.vel[a])[j];
+  }
+  rotate<D, R>(rd, collision_cell<D, R>(rd, X, Y, Z, o, s), v);
+#pragma unroll
+  for (int a = 0; a < D; ++a) ((R*)rd.vel[a])[j] = v[a];
+}
+
+cudaError_t launch_flush(int dim, int prec, const RepDev* rd_dev, const RepDev& rd, const double* ls,
+                         cudaStream_t st) {
+  const int nb = (int)((rd.np + 255) / 256);
+  if (nb == 0) return cudaSuccess;
+  if (dim == 2) {
+    if (prec == P_FP64) flush_collision<2, double><<<nb, 256, 0, st>>>(rd_dev, ls[0], ls[1], ls[2]);
+    else flush_collision<2, float><<<nb, 256, 0, st>>>(rd_dev, ls[0], ls[1], ls[2]);
+  } else {
+    if (prec == P_FP64) flush_collision<3, double><<<nb, 256, 0, st>>>(rd_dev, ls[0], ls[1], ls[2]);
+    else flush_collision<3, float><<<nb, 256, 0, st>>>(rd_dev, ls[0], ls[1], ls[2]);
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// initial particles: ppc per cell in cell order, offsets from 24-bit Philox
+// uniforms, Maxwellian velocities (variance kT/m) from Box-Muller pairs.
+template <int D, typename R>
+__global__ void init_particles(const RepDev* __restrict__ rdp) {
+  const RepDev& rd = *rdp;
+  const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (j >= rd.np) return;
+  const long long cell = j / rd.ppc;
+  const int X = (int)(cell % rd.Wx), Y = (int)((cell / rd.Wx) % rd.Hy), Z = (int)(cell / ((long long)rd.Wx * rd.Hy));
+  const uint4 wp = philox((uint32_t)j, 0u, rd.rep, TAG_INIT_POS, rd.key0, rd.key1);
+  const uint4 wv = philox((uint32_t)j, 0u, rd.rep, TAG_INIT_VEL, rd.key0, rd.key1);
+  double z[4];
+  normal_pair(wv.x, wv.y, z[0], z[1]);
+  normal_pair(wv.z, wv.w, z[2], z[3]);
+  const uint32_t wo[3] = {wp.x, wp.y, wp.z};
+  rd.home[j] = HomePack<D>::pack(X, Y, Z);
+  rd.pid[j] = (uint32_t)j;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    ((R*)rd.off[a])[j] = (R)unit24(wo[a]);
+    ((R*)rd.vel[a])[j] = (R)(rd.sig * z[a]);
+  }
+}
+
+cudaError_t launch_init_particles(int dim, int prec, const RepDev* rd_dev, const RepDev& rd, cudaStream_t st) {
+  const int nb = (int)((rd.np + 255) / 256);
+  if (nb == 0) return cudaSuccess;
+  if (dim == 2) {
+    if (prec == P_FP64) init_particles<2, double><<<nb, 256, 0, st>>>(rd_dev);
+    else init_particles<2, float><<<nb, 256, 0, st>>>(rd_dev);
+  } else {
+    if (prec == P_FP64) init_particles<3, double><<<nb, 256, 0, st>>>(rd_dev);
+    else init_particles<3, float><<<nb, 256, 0, st>>>(rd_dev);
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// particle fields in id order (binary64 / int32) and back.
+enum { F_POS = 3, F_VEL = 4, F_CELL = 5, F_HOME = 10, F_ID = 12 };
+
+template <int D, typename R>
+__global__ void part_out(RepDev rd, int field, double s0, double s1, double s2, void* out) {
+  const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (j >= rd.np) return;
+  const long long id = rd.pid[j];
+  int X, Y, Z;
+  HomePack<D>::unpack(rd.home[j], X, Y, Z);
+  if (field == F_POS || field == F_VEL) {
+    double* o = (double*)out;
+    for (int a = 0; a < 3; ++a)
+      o[3 * id + a] = a < D ? (double)((const R*)(field == F_POS ? rd.off[a] : rd.vel[a]))[j] : 0.0;
+  } else if (field == F_HOME) {
+    int* o = (int*)out;
+    o[3 * id] = X; o[3 * id + 1] = Y; o[3 * id + 2] = Z;
+  } else if (field == F_CELL) {
+    R of[3] = {R(0), R(0), R(0)};
+    for (int a = 0; a < D; ++a) of[a] = ((const R*)rd.off[a])[j];
+    const double s[3] = {s0, s1, s2};
+    ((int*)out)[id] = (int)collision_cell<D, R>(rd, X, Y, Z, of, s);
+  } else {
+    ((int*)out)[id] = (int)id;
+  }
+}
+
+template <int D, typename R>
+__global__ void part_in(RepDev rd, int field, const void* in, int* bad) {
+  const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (j >= rd.np) return;
+  const long long id = rd.pid[j];
+  if (field == F_POS || field == F_VEL) {
+    const double* s = (const double*)in;
+    for (int a = 0; a < D; ++a) {
+      const double x = s[3 * id + a];
+      if (field == F_POS && !(x >= 0.0 && x < 1.0)) atomicExch(bad, 1);
+      const R xr = (R)x;
+      ((R*)(field == F_POS ? rd.off[a] : rd.vel[a]))[j] = (field == F_POS && xr >= R(1)) ? Num<R>::one_minus : xr;
+    }
+  } else {
+    const int* s = (const int*)in;
+    const int X = s[3 * id], Y = s[3 * id + 1], Z = D == 3 ? s[3 * id + 2] : 0;
+    if (X < 0 || X >= rd.Wx || Y < 0 || Y >= rd.Hy || Z < 0 || Z >= rd.Wz) {
+      atomicExch(bad, 1);
+      return;
+    }
+    rd.home[j] = HomePack<D>::pack(X, Y, Z);
+  }
+}
+
+cudaError_t launch_part_out(int dim, int prec, const RepDev& rd, int field, const double* ls, void* out,
+                            cudaStream_t st) {
+  const int nb = (int)((rd.np + 255) / 256);
+  if (nb == 0) return cudaSuccess;
+  if (dim == 2) {
+    if (prec == P_FP64) part_out<2, double><<<nb, 256, 0, st>>>(rd, field, ls[0], ls[1], ls[2], out);
+    else part_out<2, float><<<nb, 256, 0, st>>>(rd, field, ls[0], ls[1], ls[2], out);
+  } else {
+    if (prec == P_FP64) part_out<3, double><<<nb, 256, 0, st>>>(rd, field, ls[0], ls[1], ls[2], out);
+    else part_out<3, float><<<nb, 256, 0, st>>>(rd, field, ls[0], ls[1], ls[2], out);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_part_in(int dim, int prec, const RepDev& rd, int field, const void* in, int* bad,
+                           cudaStream_t st) {
+  const int nb = (int)((rd.np + 255) / 256);
+  if (nb == 0) return cudaSuccess;
+  if (dim == 2) {
+    if (prec == P_FP64) part_in<2, double><<<nb, 256, 0, st>>>(rd, field, in, bad);
+    else part_in<2, float><<<nb, 256, 0, st>>>(rd, field, in, bad);
+  } else {
+    if (prec == P_FP64) part_in<3, double><<<nb, 256, 0, st>>>(rd, field, in, bad);
+    else part_in<3, float><<<nb, 256, 0, st>>>(rd, field, in, bad);
+  }
+  return cudaGetLastError();
+}
+
+// particle count, momentum and kinetic energy (binary64) into out[4..8].
+template <int D, typename R>
+__global__ void part_diag(RepDev rd, double* out) {
+  double p[3] = {0, 0, 0}, e = 0;
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < rd.np;
+       j += (long long)gridDim.x * blockDim.x) {
+    for (int a = 0; a < D; ++a) {
+      const double v = (double)((const R*)rd.vel[a])[j];
+      p[a] += rd.mass * v;
+      e += 0.5 * rd.mass * v * v;
+    }
+  }
+  double vals[4] = {p[0], p[1], p[2], e};
+  for (int a = 0; a < 4; ++a) {
+    double t = vals[a];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&out[5 + a], t);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&out[4], (double)rd.np);
+}
+
+cudaError_t launch_diag_particles(int dim, int prec, const RepDev& rd, double* out9, cudaStream_t st) {
+  if (rd.np == 0) return cudaSuccess;
+  long long g = (rd.np + 255) / 256;
+  const int nb = (int)(g < 1024 ? g : 1024);
+  if (dim == 2) {
+    if (prec == P_FP64) part_diag<2, double><<<nb, 256, 0, st>>>(rd, out9);
+    else part_diag<2, float><<<nb, 256, 0, st>>>(rd, out9);
+  } else {
+    if (prec == P_FP64) part_diag<3, double><<<nb, 256, 0, st>>>(rd, out9);
+    else part_diag<3, float><<<nb, 256, 0, st>>>(rd, out9);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace lbm

@@ -1,0 +1,256 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle, element
+by element on the same seeded inputs.  Tolerances: FP64 1e-12 relative, FP32
+1e-5 relative, where "relative" is |a - b| <= rtol max(|b|, rms(b)); integer
+and index results bit-exact (binning, cell counts, home cells, shifts)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from tests import inputs
+
+pytestmark = pytest.mark.gpu
+
+RTOL = {0: 1e-12, 1: 1e-5}
+
+
+@pytest.fixture(scope="module")
+def lb():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2004_00304_gb300 as mod
+    return mod
+
+
+def rel_err(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    if b.size == 0:
+        return 0.0
+    scale = max(float(np.sqrt(np.mean(b * b))), 1e-300)
+    return float(np.max(np.abs(a - b) / np.maximum(np.abs(b), scale)))
+
+
+def pair(lb, cfg, region=True):
+    g = lb.Lbmpcd(cfg["params"])
+    o = O.OracleSim(cfg["params"])
+    if region:
+        g.set_region(0, *cfg["region"])
+        o.set_region(*cfg["region"])
+    return g, o
+
+
+def compare_lb(g, o, rtol, fields=("POPS", "RHO", "U")):
+    for f in fields:
+        e = rel_err(g.get(f), o.get(f))
+        assert e <= rtol, (f, e)
+
+
+def ambiguous_particles(o, prec, eps):
+    """Particles whose binning or home cell could flip under a perturbation of
+    size eps (positions within eps of a cell edge or of a shifted edge)."""
+    off = o.get("PART_POS").reshape(-1, 3)
+    sh = o.get("SHIFT")
+    t = off + sh[None, :]
+    near = (np.abs(t - 1.0) < eps) | (off < eps) | (off > 1.0 - eps)
+    return near.any(axis=1)
+
+
+# ---------------------------------------------------------------------------
+# LB alone
+@pytest.mark.parametrize("case,prec", [("2d", 0), ("3d", 0), ("2d", 1), ("3d", 1)])
+def test_lb_stream_collide_parity(lb, case, prec):
+    """a1 on perturbed populations with walls, periodic x/z, force, ragged tiles."""
+    cfg = inputs.small_2d(precision=prec) if case == "2d" else inputs.small_3d(precision=prec)
+    p = cfg["params"]
+    g, o = pair(lb, cfg, region=False)
+    c, w = O.lattice(p["lattice"])
+    f0 = inputs.perturbed_populations(len(w), (p["nz"], p["ny"], p["nx"]), w, seed=21, amp=0.05)
+    g.set("POPS", f0)
+    o.set("POPS", f0)
+    compare_lb(g, o, RTOL[prec], fields=("POPS",))
+    for n in (1, 4):
+        g.step(n)
+        o.step(n)
+        compare_lb(g, o, RTOL[prec] * (1 if prec == 0 else 4))
+
+
+def test_lb_long_run_graph_chunks(lb):
+    """70 steps (two captured 32-step graphs plus a remainder) stay at FP64 parity."""
+    cfg = inputs.small_2d(precision=0)
+    g, o = pair(lb, cfg, region=False)
+    g.step(70)
+    o.step(70)
+    compare_lb(g, o, 1e-12)
+
+
+# ---------------------------------------------------------------------------
+# initial state and random numbers
+@pytest.mark.parametrize("case", ["2d", "3d"])
+def test_initial_particles_match(lb, case):
+    """Seeding (Philox offsets, Box-Muller velocities) is identical on both sides."""
+    cfg = inputs.small_2d() if case == "2d" else inputs.small_3d()
+    g, o = pair(lb, cfg)
+    assert np.array_equal(g.get("PART_HOME"), o.get("PART_HOME"))
+    assert np.array_equal(g.get("PART_POS"), o.get("PART_POS"))
+    assert rel_err(g.get("PART_VEL"), o.get("PART_VEL")) <= 1e-15
+    assert np.array_equal(g.get("PART_ID"), np.arange(o.num_particles))
+
+
+# ---------------------------------------------------------------------------
+# full coupled step, FP64
+@pytest.mark.parametrize("case", ["2d", "3d", "2d_r1", "2d_r4", "2d_oneway"])
+def test_coupled_step_parity_fp64(lb, case):
+    over = dict(precision=0)
+    if case == "2d_r1":
+        over["refine"] = 1
+    if case == "2d_r4":
+        over["refine"] = 4
+    if case == "2d_oneway":
+        over["feedback"] = 0
+    cfg = inputs.small_3d(**over) if case == "3d" else inputs.small_2d(**over)
+    g, o = pair(lb, cfg)
+    for n in (1, 1, 3):
+        g.step(n)
+        o.step(n)
+        assert np.array_equal(g.get("SHIFT"), o.get("SHIFT"))
+        assert np.array_equal(g.get("PART_HOME"), o.get("PART_HOME"))
+        assert np.array_equal(g.get("PART_CELL"), o.get("PART_CELL"))
+        assert np.array_equal(g.get("CELL_COUNT"), o.get("CELL_COUNT"))
+        for f in ("PART_POS", "PART_VEL", "CELL_VCM", "WINDOW_MEAN", "POPS", "RHO", "U"):
+            e = rel_err(g.get(f), o.get(f))
+            assert e <= 1e-12, (f, e)
+        np.testing.assert_allclose(g.get("DIAG"), o.get("DIAG"), rtol=1e-12, atol=1e-13)
+
+
+def test_coupled_step_parity_fp32(lb):
+    """FP32 storage against the FP64 oracle: 1e-5; binning exact away from edges."""
+    cfg = inputs.small_2d(precision=1)
+    g, o = pair(lb, cfg)
+    for n in (1, 2):
+        g.step(n)
+        o.step(n)
+        amb = ambiguous_particles(o, 1, 1e-5)
+        cells_o, cells_g = o.get("PART_CELL"), g.get("PART_CELL")
+        bad = set(cells_o[amb]) | set(cells_g[amb])
+        ok = ~np.isin(cells_o, list(bad)) & ~amb
+        assert ok.mean() > 0.95
+        assert np.array_equal(cells_g[ok], cells_o[ok])
+        vg = g.get("PART_VEL").reshape(-1, 3)[ok]
+        vo = o.get("PART_VEL").reshape(-1, 3)[ok]
+        assert rel_err(vg, vo) <= 1e-5
+        for f in ("POPS", "RHO", "U"):
+            assert rel_err(g.get(f), o.get(f)) <= 1e-5, f
+
+
+def test_binning_fp32_bit_exact_at_rest(lb):
+    """Particles at rest: FP32 binning under every step's shift is bit-exact."""
+    cfg = inputs.small_2d(precision=1, kT=0.0, force=(0, 0, 0))
+    g, o = pair(lb, cfg)
+    n = o.num_particles
+    off = inputs.grid_offsets(n, 2, seed=5)
+    for s in (g, o):
+        s.set("PART_VEL", np.zeros(3 * n))
+        s.set("PART_POS", off)
+    for _ in range(5):
+        g.step(1)
+        o.step(1)
+        assert np.array_equal(g.get("PART_CELL"), o.get("PART_CELL"))
+        assert np.array_equal(g.get("CELL_COUNT"), o.get("CELL_COUNT"))
+
+
+def test_set_state_round_trip_and_step(lb):
+    """State loaded through set_state steps identically on both sides."""
+    cfg = inputs.small_2d(precision=0)
+    g, o = pair(lb, cfg)
+    n = o.num_particles
+    v = inputs.random_velocities(n, 2, 0.02, seed=8)
+    off = inputs.grid_offsets(n, 2, seed=9)
+    for s in (g, o):
+        s.set("PART_VEL", v)
+        s.set("PART_POS", off)
+    assert np.array_equal(g.get("PART_VEL"), o.get("PART_VEL"))
+    g.step(2)
+    o.step(2)
+    assert np.array_equal(g.get("PART_HOME"), o.get("PART_HOME"))
+    assert rel_err(g.get("PART_VEL"), o.get("PART_VEL")) <= 1e-12
+
+
+def test_replicas_in_one_handle(lb):
+    """Three uneven replicas in one handle match three separate oracles."""
+    cfgs = [inputs.small_2d(precision=0, seed=31),
+            inputs.small_2d(precision=0, seed=32, nx=40, ny=14, refine=1, ppc=5),
+            inputs.small_2d(precision=0, seed=33, nx=90, ny=30, refine=4, ppc=3)]
+    cfgs[1]["region"] = (4, 20)
+    cfgs[2]["region"] = (30, 50)
+    g = lb.Lbmpcd([c["params"] for c in cfgs])
+    os_ = []
+    for r, c in enumerate(cfgs):
+        g.set_region(r, *c["region"])
+        o = O.OracleSim(c["params"], replica=r)
+        o.set_region(*c["region"])
+        os_.append(o)
+    g.step(3)
+    for r, o in enumerate(os_):
+        o.step(3)
+        assert np.array_equal(g.get("PART_CELL", r), o.get("PART_CELL"))
+        assert rel_err(g.get("PART_VEL", r), o.get("PART_VEL")) <= 1e-12
+        assert rel_err(g.get("POPS", r), o.get("POPS")) <= 1e-12
+
+
+def test_edge_cases(lb):
+    """Degenerate configurations: no coupling buffer, one particle per cell,
+    region spanning the whole periodic channel, a 1-column-wide lattice."""
+    cases = [inputs.small_2d(precision=0, coupling_width=0),
+             inputs.small_2d(precision=0, ppc=1),
+             dict(inputs.small_2d(precision=0), region=(0, 70)),
+             dict(inputs.small_2d(precision=0, nx=6, ny=5), region=(0, 6))]
+    for cfg in cases:
+        g, o = pair(lb, cfg)
+        g.step(2)
+        o.step(2)
+        assert np.array_equal(g.get("PART_CELL"), o.get("PART_CELL"))
+        assert rel_err(g.get("PART_VEL"), o.get("PART_VEL")) <= 1e-12
+        assert rel_err(g.get("POPS"), o.get("POPS")) <= 1e-12
+
+
+def test_errors_are_reported(lb):
+    with pytest.raises(lb.LbmpcdError) as ei:
+        lb.Lbmpcd(dict(nx=8, ny=8, tau=0.4))
+    assert ei.value.code == -1
+    g = lb.Lbmpcd(inputs.small_2d()["params"])
+    with pytest.raises(lb.LbmpcdError):
+        g.set_region(0, 10, 12)          # narrower than two coupling widths
+    g.set_region(0, 20, 43)
+    g.step(1)
+    with pytest.raises(lb.LbmpcdError) as ei:
+        g.set_region(0, 20, 43)
+    assert ei.value.code == -5
+    with pytest.raises(lb.LbmpcdError):
+        g.set("PART_POS", np.full(3 * lb.lbmpcd_field_size(g._h, 0, "PART_VEL") // 3, 1.5))
+
+
+# ---------------------------------------------------------------------------
+# full-size workload, one step, in the benchmark's launch configuration
+@pytest.mark.parametrize("name", ["CHANNEL_64x32_FP64", "CHANNEL_2048x512_FP32"])
+def test_full_size_single_step(lb, name):
+    cfg = getattr(inputs, name)
+    prec = cfg["params"]["precision"]
+    g, o = pair(lb, cfg)
+    g.step(1)
+    o.step(1)
+    compare_lb(g, o, RTOL[prec])
+    amb = ambiguous_particles(o, prec, 1e-5 if prec else 0.0)
+    cells_o, cells_g = o.get("PART_CELL"), g.get("PART_CELL")
+    if prec == 0:
+        assert np.array_equal(cells_g, cells_o)
+    bad = set(cells_o[amb]) | set(cells_g[amb])
+    ok = ~np.isin(cells_o, list(bad)) & ~amb
+    assert np.array_equal(cells_g[ok], cells_o[ok])
+    assert rel_err(g.get("PART_VEL").reshape(-1, 3)[ok], o.get("PART_VEL").reshape(-1, 3)[ok]) <= RTOL[prec]
+    e = rel_err(g.get("WINDOW_MEAN"), o.get("WINDOW_MEAN"))
+    assert e <= RTOL[prec] * 10, e
