@@ -39,6 +39,7 @@ cudaError_t launch_init_particles(int dim, int prec, const RepDev* rd_dev, const
 // copy-out / copy-in helpers (binary64 / int32 host-facing layouts).
 cudaError_t launch_pops_out(int q, int prec, const RepDev& rd, int parity, double* out, cudaStream_t st);
 cudaError_t launch_pops_in(int q, int prec, const RepDev& rd, const double* in, cudaStream_t st);
+cudaError_t launch_fill_real(int prec, void* dst, long long n, double value, cudaStream_t st);
 cudaError_t launch_real_out(int prec, const void* src, long long n, double* out, cudaStream_t st);
 cudaError_t launch_part_out(int dim, int prec, const RepDev& rd, int field, const double* last_shift,
                             void* out, cudaStream_t st);

@@ -210,6 +210,20 @@ __global__ void real_out(const R* __restrict__ src, long long n, double* __restr
   if (i < n) out[i] = (double)src[i];
 }
 
+template <typename R>
+__global__ void fill_real(R* __restrict__ dst, long long n, double value) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = (R)value;
+}
+
+cudaError_t launch_fill_real(int prec, void* dst, long long n, double value, cudaStream_t st) {
+  const int nb = (int)((n + 255) / 256);
+  if (n == 0) return cudaSuccess;
+  if (prec == P_FP64) fill_real<double><<<nb, 256, 0, st>>>((double*)dst, n, value);
+  else fill_real<float><<<nb, 256, 0, st>>>((float*)dst, n, value);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_real_out(int prec, const void* src, long long n, double* out, cudaStream_t st) {
   const int nb = (int)((n + 255) / 256);
   if (n == 0) return cudaSuccess;

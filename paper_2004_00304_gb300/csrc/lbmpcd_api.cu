@@ -153,6 +153,7 @@ extern "C" int lbmpcd_create(const lbmpcd_params* params, int n_replicas, void* 
     if (e == cudaSuccess) e = dalloc(L, &d.f[1], h->q * d.nnode * ss);
     if (e == cudaSuccess) e = dalloc(L, &d.rho, d.nnode * rs);
     if (e == cudaSuccess) e = dalloc(L, &d.u, 3 * d.nnode * rs);
+    if (e == cudaSuccess) e = launch_fill_real(h->prec, d.rho, d.nnode, 1.0, nullptr);   // rho0 = 1
     if (e != cudaSuccess) {
       int code = e == cudaErrorMemoryAllocation ? LBMPCD_ERR_OOM : LBMPCD_ERR_CUDA;
       std::string m = std::string("allocating LB arrays: ") + cudaGetErrorString(e);

@@ -26,12 +26,19 @@ def lb():
     return mod
 
 
-def rel_err(a, b):
+# The LB velocity is a difference of O(0.1) populations divided by rho: either
+# implementation carries an absolute rounding error of about q eps max(f_i),
+# ~5e-16 in binary64, whatever the size of u.  Its relative comparison
+# therefore uses a floor of 1e-3 lattice units next to the field's rms.
+FLOOR = {"U": 1e-3}
+
+
+def rel_err(a, b, floor=0.0):
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
     if b.size == 0:
         return 0.0
-    scale = max(float(np.sqrt(np.mean(b * b))), 1e-300)
+    scale = max(float(np.sqrt(np.mean(b * b))), floor, 1e-300)
     return float(np.max(np.abs(a - b) / np.maximum(np.abs(b), scale)))
 
 
@@ -46,15 +53,15 @@ def pair(lb, cfg, region=True):
 
 def compare_lb(g, o, rtol, fields=("POPS", "RHO", "U")):
     for f in fields:
-        e = rel_err(g.get(f), o.get(f))
+        e = rel_err(g.get(f), o.get(f), FLOOR.get(f, 0.0))
         assert e <= rtol, (f, e)
 
 
-def ambiguous_particles(o, prec, eps):
+def ambiguous_particles(o, dim, eps):
     """Particles whose binning or home cell could flip under a perturbation of
     size eps (positions within eps of a cell edge or of a shifted edge)."""
-    off = o.get("PART_POS").reshape(-1, 3)
-    sh = o.get("SHIFT")
+    off = o.get("PART_POS").reshape(-1, 3)[:, :dim]
+    sh = o.get("SHIFT")[:dim]
     t = off + sh[None, :]
     near = (np.abs(t - 1.0) < eps) | (off < eps) | (off > 1.0 - eps)
     return near.any(axis=1)
@@ -97,7 +104,7 @@ def test_initial_particles_match(lb, case):
     g, o = pair(lb, cfg)
     assert np.array_equal(g.get("PART_HOME"), o.get("PART_HOME"))
     assert np.array_equal(g.get("PART_POS"), o.get("PART_POS"))
-    assert rel_err(g.get("PART_VEL"), o.get("PART_VEL")) <= 1e-15
+    assert rel_err(g.get("PART_VEL"), o.get("PART_VEL")) <= 1e-13
     assert np.array_equal(g.get("PART_ID"), np.arange(o.num_particles))
 
 
@@ -122,7 +129,7 @@ def test_coupled_step_parity_fp64(lb, case):
         assert np.array_equal(g.get("PART_CELL"), o.get("PART_CELL"))
         assert np.array_equal(g.get("CELL_COUNT"), o.get("CELL_COUNT"))
         for f in ("PART_POS", "PART_VEL", "CELL_VCM", "WINDOW_MEAN", "POPS", "RHO", "U"):
-            e = rel_err(g.get(f), o.get(f))
+            e = rel_err(g.get(f), o.get(f), FLOOR.get(f, 0.0))
             assert e <= 1e-12, (f, e)
         np.testing.assert_allclose(g.get("DIAG"), o.get("DIAG"), rtol=1e-12, atol=1e-13)
 
@@ -134,7 +141,7 @@ def test_coupled_step_parity_fp32(lb):
     for n in (1, 2):
         g.step(n)
         o.step(n)
-        amb = ambiguous_particles(o, 1, 1e-5)
+        amb = ambiguous_particles(o, 2, 1e-5)
         cells_o, cells_g = o.get("PART_CELL"), g.get("PART_CELL")
         bad = set(cells_o[amb]) | set(cells_g[amb])
         ok = ~np.isin(cells_o, list(bad)) & ~amb
@@ -144,7 +151,7 @@ def test_coupled_step_parity_fp32(lb):
         vo = o.get("PART_VEL").reshape(-1, 3)[ok]
         assert rel_err(vg, vo) <= 1e-5
         for f in ("POPS", "RHO", "U"):
-            assert rel_err(g.get(f), o.get(f)) <= 1e-5, f
+            assert rel_err(g.get(f), o.get(f), FLOOR.get(f, 0.0)) <= 1e-5, f
 
 
 def test_binning_fp32_bit_exact_at_rest(lb):
@@ -244,7 +251,7 @@ def test_full_size_single_step(lb, name):
     g.step(1)
     o.step(1)
     compare_lb(g, o, RTOL[prec])
-    amb = ambiguous_particles(o, prec, 1e-5 if prec else 0.0)
+    amb = ambiguous_particles(o, 2 if cfg["params"]["lattice"] == 9 else 3, 1e-5 if prec else 0.0)
     cells_o, cells_g = o.get("PART_CELL"), g.get("PART_CELL")
     if prec == 0:
         assert np.array_equal(cells_g, cells_o)
