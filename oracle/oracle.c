@@ -527,8 +527,12 @@ static void collide(orc_sim* s) {
 
 /* a8: on each inner-buffer LB node, rho_bar = rho0 M_W / (ppc m r^d W_n) and
  * u_bar = P_W / M_W from the last W_n = min(n+1, W) frames; the stored
- * post-collision populations become f_eq(rho_bar, u_bar) (Eq. 2).  No
- * imposition at the first step (n = 0). */
+ * post-collision populations become f_eq(rho_LB, u_bar) (Eq. 2), rho_LB being
+ * the node's LB density of this step.  The MPCD density is reported, not
+ * imposed: the two fluids have different equations of state (LB pressure
+ * rho/3, MPCD pressure n kT), so MPCD density fluctuations imposed on the LB
+ * become pressure gradients thousands of times too strong and the coupled
+ * step diverges.  No imposition at the first step (n = 0). */
 static void impose(orc_sim* s) {
   const orc_params* p = &s->p;
   if (s->nbuf == 0) return;
@@ -553,7 +557,7 @@ static void impose(orc_sim* s) {
     int col = (int)(t % s->n_in); int side = (int)(t / s->n_in);
     int x = side == 0 ? s->x0 + s->n_out + col : s->x1 - 1 - s->n_out - col;
     double feq[19];
-    orc_feq(p->lattice, rho, u, feq);
+    orc_feq(p->lattice, s->rho[nidx(s, x, y, z)], u, feq);
     for (int i = 0; i < s->q; ++i) s->f[i * s->nnode + nidx(s, x, y, z)] = feq[i];
   }
 }

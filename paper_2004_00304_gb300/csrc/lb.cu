@@ -80,11 +80,13 @@ __global__ void __launch_bounds__(256) lb_pull(const RepDev* __restrict__ reps, 
   // interpolation of the outer buffer reads.
   bool want = st.write_moments;
   if (!want && rd.has_region) {
-    // columns x0-1 .. x0+n_out and x1-n_out-1 .. x1 (periodic in x)
-    int da = x - (rd.x0 - 1), db = x - (rd.x1 - rd.n_out - 1);
+    // columns x0-1 .. x0+cw and x1-cw-1 .. x1 (periodic in x): the outer
+    // columns and their neighbours for the interpolation, the inner columns
+    // for the density kept by the imposition
+    int da = x - (rd.x0 - 1), db = x - (rd.x1 - rd.cw - 1);
     da = da < 0 ? da + nx : (da >= nx ? da - nx : da);
     db = db < 0 ? db + nx : (db >= nx ? db - nx : db);
-    want = da <= rd.n_out + 1 || db <= rd.n_out + 1;
+    want = da <= rd.cw + 1 || db <= rd.cw + 1;
   }
   if (want) {
     R* rh = (R*)rd.rho;

@@ -16,8 +16,8 @@
 //                             groups, one atomic per group and cell);
 //   cell_pass      one thread per collision cell: v_cm with virtual wall
 //                  particles, rotation draw (Eq. 4), accumulators cleared;
-//                  extra blocks run a8: windowed moments of the inner buffer
-//                  -> f_eq populations written into the LB buffer.
+//                  extra blocks run a8: window-mean MPCD velocity of the
+//                  inner buffer -> f_eq(rho_LB, u_bar) written into the LB buffer.
 // The collision of the last step is applied lazily (flush) before particle
 // state is read out, so the visible state is always post-collision.
 //
@@ -400,11 +400,15 @@ __global__ void __launch_bounds__(256) cell_pass(const RepDev* __restrict__ reps
   const int x = side == 0 ? rd.x0 + rd.n_out + col : rd.x1 - 1 - rd.n_out - col;
   S* dst = (S*)rd.f[(st.n & 1) ^ 1];
   const long long node = x + (long long)rd.nx * (y + (long long)rd.ny * z);
+  // equilibrium at the node's own LB density (this step's moment) and the
+  // window-mean MPCD velocity: the MPCD density is reported, not imposed,
+  // because the two fluids' equations of state differ (rho/3 versus n kT).
+  const double rl = (double)((const R*)rd.rho)[node];
   const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const double cu = L::cx(i) * u[0] + L::cy(i) * u[1] + L::cz(i) * u[2];
-    const double dev = L::w(i) * ((rho - 1.0) + rho * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu));
+    const double dev = L::w(i) * ((rl - 1.0) + rl * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu));
     Store<S>::st(dst + i * rd.nnode + node, (R)dev, rd.fp16_scale);
   }
 }

@@ -126,8 +126,9 @@ def test_window_is_mean_of_last_W_frames():
 
 
 def test_imposition_writes_equilibrium_of_window_mean():
-    """From the second step on, the inner-buffer populations are f_eq of the
-    window moments (Eq. 2): zeroth and first moments equal rho_bar, rho_bar u_bar."""
+    """From the second step on, the inner-buffer populations are f_eq (Eq. 2)
+    at the node's LB density and the window-mean MPCD velocity: zeroth and
+    first moments equal rho_LB and rho_LB u_bar."""
     cfg = inputs.small_2d(feedback=1, window=3)
     p = cfg["params"]
     s = _sim(cfg)
@@ -137,10 +138,15 @@ def test_imposition_writes_equilibrium_of_window_mean():
         s.step(1)
         f = s.get("POPS").reshape(9, ny, nx)
         wm = s.get("WINDOW_MEAN").reshape(-1, 4)
+        rho = s.get("RHO").reshape(ny, nx)
+        c, _ = O.lattice(9)
         k = 0
         for xc in (x0 + 1, x1 - 2):
             for yy in range(1, ny - 1):
-                want = O.feq(9, wm[k, 0], wm[k, 1:3])
+                want = O.feq(9, rho[yy, xc], wm[k, 1:3])
+                if n > 0:
+                    assert abs(f[:, yy, xc].sum() - rho[yy, xc]) < 1e-14
+                    np.testing.assert_allclose(f[:, yy, xc] @ c[:, :2], rho[yy, xc] * wm[k, 1:3], atol=1e-16)
                 if n == 0:
                     assert np.max(np.abs(f[:, yy, xc] - want)) > 1e-6
                 else:
@@ -176,3 +182,19 @@ def test_particle_count_and_bounds_conserved():
     assert home[:, 1].min() >= 0 and home[:, 1].max() < (p["ny"] - 2) * r
     assert home[:, 2].min() >= 0 and home[:, 2].max() < p["nz"] * r
     assert off.min() >= 0 and off.max() < 1
+
+
+@pytest.mark.slow
+def test_two_way_coupling_stays_bounded():
+    """With the windowed feedback the coupled channel stays at the noise level:
+    over 1500 steps the LB speed stays below 1e-2 and rho within 1 %."""
+    cfg = inputs.small_2d(refine=2, ppc=10, tau=0.8, force=(1e-7, 0, 0), kT=1e-4, window=100,
+                          nx=128, ny=34)
+    cfg["region"] = (48, 80)
+    s = _sim(cfg)
+    for _ in range(3):
+        s.step(500)
+        u = s.get("U")
+        rho = s.get("RHO").reshape(34, 128)[1:-1]
+        assert np.all(np.isfinite(u)) and np.abs(u).max() < 1e-2
+        assert np.abs(rho - 1).max() < 1e-2
