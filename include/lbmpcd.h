@@ -125,9 +125,9 @@ int lbmpcd_step(lbmpcd* h, int nsteps);
 
 /* Same work as lbmpcd_step, launched without graph replay and with a CUDA
  * event pair on the handle's stream around every kernel; adds each kernel
- * family's elapsed milliseconds to phase_ms[0..3] = {prep, lb_pull,
- * particle_pass, cell_pass} (caller-owned; not zeroed here) and the number of
- * kernel launches to *launches (may be NULL).  Synchronises the stream.  For
+ * family's elapsed milliseconds to phase_ms[0..4] = {prep, lb_pull,
+ * particle_pass, cell_pass, particle sort} (caller-owned, 5 entries; not
+ * zeroed here) and the number of kernel launches to *launches (may be NULL).  Synchronises the stream.  For
  * measurement only: the per-kernel events add small gaps between kernels.
  * Errors: INVALID_ARG, CUDA. */
 int lbmpcd_step_profiled(lbmpcd* h, int nsteps, double* phase_ms, long long* launches);

@@ -133,10 +133,10 @@ def lbmpcd_step(h, nsteps: int):
 def lbmpcd_step_profiled(h, nsteps: int):
     """Run nsteps with a CUDA event pair around every kernel; returns
     ({phase: milliseconds}, number of kernel launches)."""
-    ms = (ctypes.c_double * 4)()
+    ms = (ctypes.c_double * 5)()
     nl = ctypes.c_longlong(0)
     _check(h, load_library().lbmpcd_step_profiled(h, int(nsteps), ms, ctypes.byref(nl)))
-    return dict(zip(("prep", "lb_pull", "particle_pass", "cell_pass"), list(ms))), int(nl.value)
+    return dict(zip(("prep", "lb_pull", "particle_pass", "cell_pass", "sort"), list(ms))), int(nl.value)
 
 
 def lbmpcd_field_size(h, replica: int, field: str) -> int:

@@ -1,8 +1,8 @@
 """Build liblbmpcd.so in-tree with nvcc for sm_103a (no torch extension machinery).
 
-Each translation unit is compiled in parallel; mpcd.cu is compiled with
--fmad=false so that particle streaming and binning perform exactly the
-IEEE operations written in the source.
+Each translation unit is compiled in parallel.  Particle streaming and
+binning spell out their binary64 operations with non-contractible
+intrinsics, so no translation unit needs -fmad=false.
 """
 from __future__ import annotations
 
@@ -22,7 +22,7 @@ COMMON = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", 
 SOURCES = {
     "lbmpcd_api.cu": [],
     "lb.cu": [],
-    "mpcd.cu": ["-fmad=false"],
+    "mpcd.cu": [],
 }
 HEADERS = ["common.cuh", "kernels.h"]
 

@@ -109,17 +109,31 @@ struct RepDev {
   long long ncell;         // collision cells: Wx (Hy+1) Wz
   long long nbuf;          // inner-buffer LB nodes
   uint32_t key0, key1, rep;
-  // particles (structure of arrays)
+  // coupling columns in cell units: outer X < xo_lo or X >= xo_hi; inner
+  // [xi_lo0, xi_hi0) (left side) and [xi_lo1, xi_hi1) (right side)
+  int xo_lo, xo_hi, xi_lo0, xi_hi0, xi_lo1, xi_hi1;
+  // particles (structure of arrays); *_alt receive the sorted copy
   uint32_t* home;          // packed integer home cell
   void* off[3];            // offsets in [0,1), storage precision
   void* vel[3];            // velocities, storage precision
   uint32_t* pid;           // particle id (Philox counter of the redraw)
+  uint32_t* home_alt;
+  void* off_alt[3];
+  void* vel_alt[3];
+  uint32_t* pid_alt;
+  // counting sort by home cell
+  long long nhome;         // Wx Hy Wz
+  int ntile;               // ceil(nhome / SORT_TILE)
+  uint32_t* hcount;        // [nhome] particles per home cell (zero between sorts)
+  uint32_t* hoff;          // [nhome] exclusive prefix inside the tile
+  uint32_t* tsum;          // [ntile] tile totals -> exclusive tile offsets
+  uint32_t* rank;          // [np] rank of the particle inside its home cell
   // collision cells
   uint32_t* acc_n;         // accumulators of the current binning
   void* acc_v[3];
-  void* vcm[3];            // table of the last collision: v_cm
-  void* rot[3];            // 2D: signed sin(theta) in rot[0]; 3D: unit axis
-  int* count;              // particles per cell of the last binning
+  void* tab;               // table of the last collision, vec4 of the storage
+                           // precision: 2D {vcm.x, vcm.y, sin(theta), n};
+                           // 3D {vcm.x, vcm.y, vcm.z, n}, {axis.x, axis.y, axis.z, 0}
   // inner buffer sampling window (binary64)
   double* frame;           // [nbuf][4] this step's mass, momentum
   double* ring;            // [window][nbuf][4]
@@ -127,12 +141,18 @@ struct RepDev {
   double* wmean;           // [nbuf][4] rho_bar, u_bar
 };
 
+constexpr int SORT_TILE = 1024;
+
+template <typename R> struct Vec4;
+template <> struct Vec4<float> { using T = float4; };
+template <> struct Vec4<double> { using T = double4; };
+
 // One record per (step of the chunk, replica), written by the prep kernel.
 struct StepInfo {
   uint32_t n;              // global step index
   int pending;             // collision of step n-1 not yet applied to particles
   int write_moments;       // write rho/u on every node this step
-  int pad;
+  int src_alt;             // particle state of this step is in the *_alt (sorted) arrays
   double shift[3], prev[3];
 };
 
@@ -170,5 +190,20 @@ template <> struct Store<__half> {
   __device__ static float ld(const __half* p, float inv) { return __half2float(*p) * inv; }
   __device__ static void st(__half* p, float v, float scale) { *p = __float2half_rn(v * scale); }
 };
+
+// Copy a block's descriptor and step record to shared memory (all threads
+// call it; it ends with a barrier).  si == nullptr skips the step record.
+__device__ __forceinline__ void load_block_records(RepDev& srd, StepInfo& sst, const RepDev* reps,
+                                                   const StepInfo* si, int rep, int k, int nrep) {
+  const int* a = (const int*)(reps + rep);
+  int* b = (int*)&srd;
+  for (int i = threadIdx.x; i < (int)(sizeof(RepDev) / 4); i += blockDim.x) b[i] = a[i];
+  if (si) {
+    const int* c = (const int*)(si + (long long)k * nrep + rep);
+    int* d = (int*)&sst;
+    for (int i = threadIdx.x; i < (int)(sizeof(StepInfo) / 4); i += blockDim.x) d[i] = c[i];
+  }
+  __syncthreads();
+}
 
 }  // namespace lbm

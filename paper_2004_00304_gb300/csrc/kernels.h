@@ -17,11 +17,20 @@ struct Launch {
 };
 
 // a1: fused pull stream + BGK collide (+ Guo force, bounce-back walls).
-cudaError_t launch_lb(int q, int prec, const Launch& L, const int2* bmap, int nblocks, int k);
+// vec = nodes per thread (lb_vector_width); one vec for all replicas of a handle.
+int lb_vector_width(int prec, int nx);
+cudaError_t launch_lb(int q, int prec, int vec, const Launch& L, const int2* bmap, int nblocks, int k);
 
 // prep: per-step records (shift, pending flag) for kcount steps.
-cudaError_t launch_prep(int dim, const Launch& L, StepInfo* si, int kcount, uint32_t* d_step,
+cudaError_t launch_prep(int dim, const Launch& L, StepInfo* si, int kcount, int sorted, uint32_t* d_step,
                         int* d_pending, double* d_last_shift);
+
+// counting sort of the particles by home cell into the *_alt arrays.
+cudaError_t launch_sort(int dim, int prec, const Launch& L, const int2* bmap_p, int nb_p, const int2* bmap_t,
+                        int nb_t);
+
+// collision-cell table -> CELL_COUNT (field 7, int32) or CELL_VCM (field 11, [ncell][3] binary64).
+cudaError_t launch_tab_out(int dim, int prec, const RepDev& rd, int field, void* out, cudaStream_t st);
 
 // a7(n-1) + a2 + a3 + a4 + a6 + a5 over every particle.
 cudaError_t launch_particles(int dim, int prec, const Launch& L, const int2* bmap, int nblocks, int k);

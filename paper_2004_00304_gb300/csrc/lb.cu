@@ -15,105 +15,198 @@
 
 namespace lbm {
 
-template <int Q, typename S>
-__global__ void __launch_bounds__(256) lb_pull(const RepDev* __restrict__ reps, const int2* __restrict__ bmap,
+// V consecutive populations of one row: aligned vector load/store (V = 4 for
+// binary32 and scaled binary16 rows whose length is a multiple of 4), scalar
+// otherwise.
+template <typename S, int V> struct Row;
+template <typename S> struct Row<S, 1> {
+  using R = typename Store<S>::R;
+  __device__ static void ld(const S* p, R* o, float inv) { o[0] = Store<S>::ld(p, inv); }
+  __device__ static void st(S* p, const R* v, float sc) { Store<S>::st(p, v[0], sc); }
+};
+template <> struct Row<float, 4> {
+  __device__ static void ld(const float* p, float* o, float) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+  }
+  __device__ static void st(float* p, const float* v, float) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+};
+template <> struct Row<__half, 4> {
+  __device__ static void ld(const __half* p, float* o, float inv) {
+    const uint2 t = *reinterpret_cast<const uint2*>(p);
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&t.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&t.y));
+    o[0] = a.x * inv; o[1] = a.y * inv; o[2] = b.x * inv; o[3] = b.y * inv;
+  }
+  __device__ static void st(__half* p, const float* v, float sc) {
+    const __half2 a = __floats2half2_rn(v[0] * sc, v[1] * sc), b = __floats2half2_rn(v[2] * sc, v[3] * sc);
+    uint2 t;
+    t.x = *reinterpret_cast<const uint32_t*>(&a);
+    t.y = *reinterpret_cast<const uint32_t*>(&b);
+    *reinterpret_cast<uint2*>(p) = t;
+  }
+};
+
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+
+// One thread owns V consecutive nodes x0 .. x0+V-1 of one row (y, z).
+template <int Q, typename S, int V>
+__global__ void __launch_bounds__(128) lb_pull(const RepDev* __restrict__ reps, const int2* __restrict__ bmap,
                                                const StepInfo* __restrict__ si, int k, int nrep) {
   using L = Lattice<Q>;
   using R = typename Store<S>::R;
+  __shared__ RepDev rd;
+  __shared__ StepInfo st;
+  __shared__ int srow[3];
   const int2 bm = bmap[blockIdx.x];
-  const RepDev& rd = reps[bm.x];
-  const StepInfo& st = si[k * nrep + bm.x];
+  if (threadIdx.x == 0) {
+    const RepDev& g = reps[bm.x];
+    const int tpr = g.nx / V, ntx = (tpr + blockDim.x - 1) / blockDim.x;
+    const int tile = bm.y % ntx, yz = bm.y / ntx;
+    srow[0] = tile; srow[1] = 1 + yz % (g.ny - 2); srow[2] = yz / (g.ny - 2);
+  }
+  load_block_records(rd, st, reps, si, bm.x, k, nrep);
   const int nx = rd.nx, ny = rd.ny, nz = rd.nz;
-  const int ntx = (nx + blockDim.x - 1) / blockDim.x;
-  const int tile = bm.y % ntx, yz = bm.y / ntx;
-  const int y = 1 + yz % (ny - 2), z = yz / (ny - 2);
-  const int x = tile * blockDim.x + threadIdx.x;
-  if (x >= nx) return;
+  const int y = srow[1], z = srow[2];
+  const int tpr = nx / V;
+  const int tx = srow[0] * blockDim.x + threadIdx.x;
+  const bool active = tx < tpr;
+  const int lane = threadIdx.x & 31;
+  const int x0 = tx * V;
   const int par = st.n & 1;
   const S* __restrict__ src = (const S*)rd.f[par];
   S* __restrict__ dst = (S*)rd.f[par ^ 1];
-  const long long N = rd.nnode;
-  const long long here = x + (long long)nx * (y + (long long)ny * z);
+  const int N = (int)rd.nnode;
+  const int row = nx * (y + ny * z);
   const float inv = rd.fp16_inv, scale = rd.fp16_scale;
 
-  R d[Q];
+  R d[Q][V];
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const int sy = y - L::cy(i);
-    if (sy == 0 || sy == ny - 1) {
-      d[i] = Store<S>::ld(src + L::opp(i) * N + here, inv);
-    } else {
-      int sx = x - L::cx(i);
+    if (sy == 0 || sy == ny - 1) {           // half-way bounce-back: f*_{-i} of this node
+      if (active) Row<S, V>::ld(src + L::opp(i) * N + row + x0, d[i], inv);
+      continue;
+    }
+    int sz = z - L::cz(i);
+    sz = sz < 0 ? sz + nz : (sz >= nz ? sz - nz : sz);
+    const S* srow_i = src + i * N + nx * (sy + ny * sz);
+    R a[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) a[v] = R(0);
+    if (active) Row<S, V>::ld(srow_i + x0, a, inv);
+    if (L::cx(i) == 0) {
+#pragma unroll
+      for (int v = 0; v < V; ++v) d[i][v] = a[v];
+    } else if (V == 1) {
+      int sx = x0 - L::cx(i);
       sx = sx < 0 ? sx + nx : (sx >= nx ? sx - nx : sx);
-      int sz = z - L::cz(i);
-      sz = sz < 0 ? sz + nz : (sz >= nz ? sz - nz : sz);
-      d[i] = Store<S>::ld(src + i * N + sx + (long long)nx * (sy + (long long)ny * sz), inv);
+      if (active) d[i][0] = Store<S>::ld(srow_i + sx, inv);
+    } else if (L::cx(i) > 0) {               // source x - 1: previous lane's last node
+      R prev = __shfl_up_sync(0xFFFFFFFFu, a[V - 1], 1);
+      if (active && lane == 0) prev = Store<S>::ld(srow_i + (x0 == 0 ? nx - 1 : x0 - 1), inv);
+      d[i][0] = prev;
+#pragma unroll
+      for (int v = 1; v < V; ++v) d[i][v] = a[v - 1];
+    } else {                                 // source x + 1: next lane's first node
+      R next = __shfl_down_sync(0xFFFFFFFFu, a[0], 1);
+      if (active && (lane == 31 || tx + 1 >= tpr)) next = Store<S>::ld(srow_i + (x0 + V >= nx ? 0 : x0 + V), inv);
+#pragma unroll
+      for (int v = 0; v < V - 1; ++v) d[i][v] = a[v + 1];
+      d[i][V - 1] = next;
     }
   }
-  R drho = 0, jx = 0, jy = 0, jz = 0;
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    drho += d[i];
-    if (L::cx(i)) jx += L::cx(i) * d[i];
-    if (L::cy(i)) jy += L::cy(i) * d[i];
-    if (L::cz(i)) jz += L::cz(i) * d[i];
-  }
-  const R rho = R(1) + drho;
-  const R irho = R(1) / rho;
+  if (!active) return;
+
+  const R om = (R)rd.omega, om1 = R(1) - om, cf = R(1) - R(0.5) * om;
   const R gx = (R)rd.g[0], gy = (R)rd.g[1], gz = (R)rd.g[2];
-  const R ux = jx * irho + R(0.5) * gx, uy = jy * irho + R(0.5) * gy, uz = jz * irho + R(0.5) * gz;
-  const R uu = ux * ux + uy * uy + uz * uz;
-  const R Fx = rho * gx, Fy = rho * gy, Fz = rho * gz;
-  const R uF = ux * Fx + uy * Fy + uz * Fz;
-  const R om = (R)rd.omega;
-  const R cf = R(1) - R(0.5) * om;
+  R out[Q][V];
+  R mr[V], mu[3][V];
 #pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    const R w = (R)L::w(i);
-    const R cu = L::cx(i) * ux + L::cy(i) * uy + L::cz(i) * uz;
-    const R cF = L::cx(i) * Fx + L::cy(i) * Fy + L::cz(i) * Fz;
-    const R deq = w * (drho + rho * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu));
-    const R src_i = cf * w * (R(3) * (cF - uF) + R(9) * cu * cF);
-    Store<S>::st(dst + i * N + here, d[i] - om * (d[i] - deq) + src_i, scale);
+  for (int v = 0; v < V; ++v) {
+    R drho = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      drho += d[i][v];
+      if (L::cx(i) > 0) jx += d[i][v]; else if (L::cx(i) < 0) jx -= d[i][v];
+      if (L::cy(i) > 0) jy += d[i][v]; else if (L::cy(i) < 0) jy -= d[i][v];
+      if (L::cz(i) > 0) jz += d[i][v]; else if (L::cz(i) < 0) jz -= d[i][v];
+    }
+    const R rho = R(1) + drho;
+    const R ir = recip(rho);
+    const R ux = jx * ir + R(0.5) * gx, uy = jy * ir + R(0.5) * gy, uz = jz * ir + R(0.5) * gz;
+    const R Gx = rho * gx, Gy = rho * gy, Gz = rho * gz;              // F = rho g
+    const R uu = ux * ux + uy * uy + uz * uz;
+    const R uF = ux * Gx + uy * Gy + uz * Gz;
+    // f*_i = (1-om) d_i + w_i (E_i + O_i): E even, O odd in c_i
+    //   E = om drho - 1.5 om rho u.u - 3 cf u.F + cu (4.5 om rho cu + 9 cf cF)
+    //   O = 3 (om rho cu + cf cF)
+    const R K0 = om * drho - R(1.5) * om * rho * uu - R(3) * cf * uF;
+    const R A = R(4.5) * om * rho, B = om * rho, C9 = R(9) * cf;
+    out[0][v] = om1 * d[0][v] + (R)L::w(0) * K0;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      const int o = L::opp(i);
+      if (o < i) continue;
+      const R cu = L::cx(i) * ux + L::cy(i) * uy + L::cz(i) * uz;
+      const R cF = L::cx(i) * Gx + L::cy(i) * Gy + L::cz(i) * Gz;
+      const R cfF = cf * cF;
+      const R E = K0 + cu * (A * cu + C9 * cF);
+      const R Od = R(3) * (B * cu + cfF);
+      const R w = (R)L::w(i);
+      const R pe = w * E, po = w * Od;
+      out[i][v] = om1 * d[i][v] + (pe + po);
+      out[o][v] = om1 * d[o][v] + (pe - po);
+    }
+    mr[v] = rho; mu[0][v] = ux; mu[1][v] = uy; mu[2][v] = uz;
   }
-  // rho, u: every node on request; otherwise the columns the coarse->fine
-  // interpolation of the outer buffer reads.
-  bool want = st.write_moments;
-  if (!want && rd.has_region) {
-    // columns x0-1 .. x0+cw and x1-cw-1 .. x1 (periodic in x): the outer
-    // columns and their neighbours for the interpolation, the inner columns
-    // for the density kept by the imposition
-    int da = x - (rd.x0 - 1), db = x - (rd.x1 - rd.cw - 1);
-    da = da < 0 ? da + nx : (da >= nx ? da - nx : da);
-    db = db < 0 ? db + nx : (db >= nx ? db - nx : db);
-    want = da <= rd.cw + 1 || db <= rd.cw + 1;
-  }
-  if (want) {
-    R* rh = (R*)rd.rho;
-    R* uv = (R*)rd.u;
-    rh[here] = rho;
-    uv[here] = ux;
-    uv[N + here] = uy;
-    uv[2 * N + here] = uz;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) Row<S, V>::st(dst + i * N + row + x0, out[i], scale);
+
+  // rho, u: every node on request; otherwise the columns the coupling reads
+  // (x0-1 .. x0+cw and x1-cw-1 .. x1, periodic in x).
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    const int x = x0 + v;
+    bool want = st.write_moments;
+    if (!want && rd.has_region) {
+      int da = x - (rd.x0 - 1), db = x - (rd.x1 - rd.cw - 1);
+      da = da < 0 ? da + nx : (da >= nx ? da - nx : da);
+      db = db < 0 ? db + nx : (db >= nx ? db - nx : db);
+      want = da <= rd.cw + 1 || db <= rd.cw + 1;
+    }
+    if (want) {
+      R* rh = (R*)rd.rho;
+      R* uv = (R*)rd.u;
+      rh[row + x] = mr[v];
+      uv[row + x] = mu[0][v];
+      uv[N + row + x] = mu[1][v];
+      uv[2 * N + row + x] = mu[2][v];
+    }
   }
 }
 
-template <int Q, typename S>
+template <int Q, typename S, int V>
 static cudaError_t go_lb(const Launch& L, const int2* bmap, int nblocks, int k) {
   if (nblocks == 0) return cudaSuccess;
-  lb_pull<Q, S><<<nblocks, 256, 0, L.stream>>>(L.reps, bmap, L.si, k, L.nrep);
+  lb_pull<Q, S, V><<<nblocks, 128, 0, L.stream>>>(L.reps, bmap, L.si, k, L.nrep);
   return cudaGetLastError();
 }
 
-cudaError_t launch_lb(int q, int prec, const Launch& L, const int2* bmap, int nblocks, int k) {
+int lb_vector_width(int prec, int nx) { return (prec != P_FP64 && nx % 4 == 0) ? 4 : 1; }
+
+cudaError_t launch_lb(int q, int prec, int vec, const Launch& L, const int2* bmap, int nblocks, int k) {
   if (q == 9) {
-    if (prec == P_FP64) return go_lb<9, double>(L, bmap, nblocks, k);
-    if (prec == P_FP32) return go_lb<9, float>(L, bmap, nblocks, k);
-    return go_lb<9, __half>(L, bmap, nblocks, k);
+    if (prec == P_FP64) return go_lb<9, double, 1>(L, bmap, nblocks, k);
+    if (prec == P_FP32) return vec == 4 ? go_lb<9, float, 4>(L, bmap, nblocks, k) : go_lb<9, float, 1>(L, bmap, nblocks, k);
+    return vec == 4 ? go_lb<9, __half, 4>(L, bmap, nblocks, k) : go_lb<9, __half, 1>(L, bmap, nblocks, k);
   }
-  if (prec == P_FP64) return go_lb<19, double>(L, bmap, nblocks, k);
-  if (prec == P_FP32) return go_lb<19, float>(L, bmap, nblocks, k);
-  return go_lb<19, __half>(L, bmap, nblocks, k);
+  if (prec == P_FP64) return go_lb<19, double, 1>(L, bmap, nblocks, k);
+  if (prec == P_FP32) return vec == 4 ? go_lb<19, float, 4>(L, bmap, nblocks, k) : go_lb<19, float, 1>(L, bmap, nblocks, k);
+  return vec == 4 ? go_lb<19, __half, 4>(L, bmap, nblocks, k) : go_lb<19, __half, 1>(L, bmap, nblocks, k);
 }
 
 // ---- copy-out / copy-in of populations and LB-side diagnostics ------------

@@ -11,6 +11,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <string>
 #include <vector>
@@ -27,14 +28,14 @@ thread_local std::string g_create_error;
 
 struct lbmpcd {
   std::vector<lbmpcd_params> P;
-  int nrep = 0, q = 9, dim = 2, prec = 0;
+  int nrep = 0, q = 9, dim = 2, prec = 0, lbvec = 1;
   cudaStream_t stream = nullptr;
   std::vector<RepDev> rd;
   std::vector<std::vector<void*>> rep_allocs;   // per replica, region arrays
   std::vector<void*> allocs;                    // handle-wide
   RepDev* d_reps = nullptr;
-  int2 *bm_lb = nullptr, *bm_p = nullptr, *bm_c = nullptr;
-  int nb_lb = 0, nb_p = 0, nb_c = 0;
+  int2 *bm_lb = nullptr, *bm_p = nullptr, *bm_c = nullptr, *bm_t = nullptr;
+  int nb_lb = 0, nb_p = 0, nb_c = 0, nb_t = 0;
   StepInfo* d_si = nullptr;
   uint32_t* d_step = nullptr;
   int* d_pending = nullptr;
@@ -132,6 +133,8 @@ extern "C" int lbmpcd_create(const lbmpcd_params* params, int n_replicas, void* 
   h->rep_allocs.resize(n_replicas);
   h->pending.assign(n_replicas, 0);
   const size_t ss = store_size(h->prec), rs = real_size(h->prec);
+  h->lbvec = 4;
+  for (int r = 0; r < n_replicas; ++r) h->lbvec = std::min(h->lbvec, lb_vector_width(h->prec, params[r].nx));
   for (int r = 0; r < n_replicas; ++r) {
     const lbmpcd_params& p = params[r];
     RepDev& d = h->rd[r];
@@ -180,10 +183,10 @@ extern "C" int lbmpcd_create(const lbmpcd_params* params, int n_replicas, void* 
 
 // Block maps: (replica, local block) per block of each kernel family.
 static int build_maps(lbmpcd* h) {
-  std::vector<int2> lb, pp, cc;
+  std::vector<int2> lb, pp, cc, tt;
   for (int r = 0; r < h->nrep; ++r) {
     const RepDev& d = h->rd[r];
-    const int ntx = (d.nx + 255) / 256;
+    const int ntx = (d.nx / h->lbvec + 127) / 128;
     const long long nlb = (long long)ntx * (d.ny - 2) * d.nz;
     for (long long b = 0; b < nlb; ++b) lb.push_back(make_int2(r, (int)b));
     if (!d.has_region) continue;
@@ -191,11 +194,12 @@ static int build_maps(lbmpcd* h) {
     for (long long b = 0; b < npb; ++b) pp.push_back(make_int2(r, (int)b));
     for (long long b = 0; b < ncb; ++b) cc.push_back(make_int2(r, (int)b));
     for (long long b = 0; b < nbb; ++b) cc.push_back(make_int2(r, (int)(-1 - b)));
+    for (int b = 0; b < d.ntile; ++b) tt.push_back(make_int2(r, b));
   }
-  int2** dst[3] = {&h->bm_lb, &h->bm_p, &h->bm_c};
-  int* cnt[3] = {&h->nb_lb, &h->nb_p, &h->nb_c};
-  std::vector<int2>* src[3] = {&lb, &pp, &cc};
-  for (int i = 0; i < 3; ++i) {
+  int2** dst[4] = {&h->bm_lb, &h->bm_p, &h->bm_c, &h->bm_t};
+  int* cnt[4] = {&h->nb_lb, &h->nb_p, &h->nb_c, &h->nb_t};
+  std::vector<int2>* src[4] = {&lb, &pp, &cc, &tt};
+  for (int i = 0; i < 4; ++i) {
     if (*dst[i]) {
       cudaFree(*dst[i]);
       for (auto it = h->allocs.begin(); it != h->allocs.end(); ++it)
@@ -233,7 +237,15 @@ extern "C" int lbmpcd_set_region(lbmpcd* h, int replica, const int lo[3], const 
                                 : (d.Wx <= HomePack<3>::XMAX + 1 && d.Hy <= HomePack<3>::YMAX + 1 &&
                                    d.Wz <= HomePack<3>::ZMAX + 1);
   if (!fits) return fail(h, LBMPCD_ERR_INVALID_ARG, "region has more cells per axis than the packed home index holds");
-  d.np = (long long)d.Wx * d.Hy * d.Wz * p.ppc;
+  d.nhome = (long long)d.Wx * d.Hy * d.Wz;
+  d.ntile = (int)((d.nhome + SORT_TILE - 1) / SORT_TILE);
+  d.np = d.nhome * p.ppc;
+  {
+    const int r = p.refine, w = x1 - x0;
+    d.xo_lo = d.n_out * r; d.xo_hi = (w - d.n_out) * r;
+    d.xi_lo0 = d.n_out * r; d.xi_hi0 = p.coupling_width * r;
+    d.xi_lo1 = (w - p.coupling_width) * r; d.xi_hi1 = (w - d.n_out) * r;
+  }
   if (d.np >= (1LL << 32) - 1) return fail(h, LBMPCD_ERR_INVALID_ARG, "too many particles");
   d.ncell = (long long)d.Wx * (d.Hy + 1) * d.Wz;
   d.nbuf = 2LL * d.n_in * (p.ny - 2) * p.nz;
@@ -244,10 +256,19 @@ extern "C" int lbmpcd_set_region(lbmpcd* h, int replica, const int lo[3], const 
 #define A(ptr, bytes) if (e == cudaSuccess) { e = dalloc(L, &t, (bytes)); ptr = t; }
   A(*(void**)&d.home, d.np * 4);
   A(*(void**)&d.pid, d.np * 4);
-  for (int a = 0; a < h->dim; ++a) { A(d.off[a], d.np * rs); A(d.vel[a], d.np * rs); }
+  A(*(void**)&d.home_alt, d.np * 4);
+  A(*(void**)&d.pid_alt, d.np * 4);
+  for (int a = 0; a < h->dim; ++a) {
+    A(d.off[a], d.np * rs); A(d.vel[a], d.np * rs);
+    A(d.off_alt[a], d.np * rs); A(d.vel_alt[a], d.np * rs);
+  }
+  A(*(void**)&d.rank, d.np * 4);
+  A(*(void**)&d.hcount, d.nhome * 4);
+  A(*(void**)&d.hoff, d.nhome * 4);
+  A(*(void**)&d.tsum, (long long)d.ntile * 4);
   A(*(void**)&d.acc_n, d.ncell * 4);
-  A(*(void**)&d.count, d.ncell * 4);
-  for (int a = 0; a < h->dim; ++a) { A(d.acc_v[a], d.ncell * rs); A(d.vcm[a], d.ncell * rs); A(d.rot[a], d.ncell * rs); }
+  for (int a = 0; a < h->dim; ++a) A(d.acc_v[a], d.ncell * rs);
+  A(d.tab, d.ncell * rs * 4 * (h->dim == 2 ? 1 : 2));
   const long long nb4 = (d.nbuf > 0 ? d.nbuf : 1) * 4;
   A(*(void**)&d.frame, nb4 * 8);
   A(*(void**)&d.ring, nb4 * 8 * (long long)p.window);
@@ -267,11 +288,15 @@ extern "C" int lbmpcd_set_region(lbmpcd* h, int replica, const int lo[3], const 
   return LBMPCD_OK;
 }
 
-static int run_chunk(lbmpcd* h, int kcount) {
+// One chunk of kcount steps.  Full (graph) chunks start with the counting
+// sort of the particles; the chunk's first particle pass reads the sorted copy.
+static int run_chunk(lbmpcd* h, int kcount, bool sort) {
   Launch L{h->d_reps, h->nrep, h->d_si, h->stream};
-  CK(h, launch_prep(h->dim, L, h->d_si, kcount, h->d_step, h->d_pending, h->d_last_shift));
+  sort = sort && h->nb_p > 0;
+  if (sort) CK(h, launch_sort(h->dim, h->prec, L, h->bm_p, h->nb_p, h->bm_t, h->nb_t));
+  CK(h, launch_prep(h->dim, L, h->d_si, kcount, sort ? 1 : 0, h->d_step, h->d_pending, h->d_last_shift));
   for (int k = 0; k < kcount; ++k) {
-    CK(h, launch_lb(h->q, h->prec, L, h->bm_lb, h->nb_lb, k));
+    CK(h, launch_lb(h->q, h->prec, h->lbvec, L, h->bm_lb, h->nb_lb, k));
     CK(h, launch_particles(h->dim, h->prec, L, h->bm_p, h->nb_p, k));
     CK(h, launch_cells(h->q, h->prec, L, h->bm_c, h->nb_c, k));
   }
@@ -293,7 +318,7 @@ extern "C" int lbmpcd_step(lbmpcd* h, int nsteps) {
       CK(h, cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
       cudaStream_t keep = h->stream;
       h->stream = cap;
-      int rc = run_chunk(h, KCHUNK);
+      int rc = run_chunk(h, KCHUNK, true);
       h->stream = keep;
       cudaError_t e = cudaStreamEndCapture(cap, &g);
       if (rc) { if (g) cudaGraphDestroy(g); if (own) cudaStreamDestroy(cap); return rc; }
@@ -308,7 +333,7 @@ extern "C" int lbmpcd_step(lbmpcd* h, int nsteps) {
     h->nstep += KCHUNK;
   }
   if (left > 0) {
-    int rc = run_chunk(h, left);
+    int rc = run_chunk(h, left, false);
     if (rc) return rc;
     h->nstep += left;
   }
@@ -321,7 +346,7 @@ extern "C" int lbmpcd_step_profiled(lbmpcd* h, int nsteps, double* phase_ms, lon
   if (!h) return LBMPCD_ERR_INVALID_ARG;
   if (nsteps < 0 || !phase_ms) return fail(h, LBMPCD_ERR_INVALID_ARG, "nsteps < 0 or null phase_ms");
   if (h->maps_dirty) { int rc = build_maps(h); if (rc) return rc; }
-  const int nev = 2 * (1 + 3 * KCHUNK);
+  const int nev = 2 * (2 + 3 * KCHUNK);
   std::vector<cudaEvent_t> ev(nev, nullptr);
   for (auto& x : ev) CK(h, cudaEventCreate(&x));
   Launch L{h->d_reps, h->nrep, h->d_si, h->stream};
@@ -341,9 +366,12 @@ extern "C" int lbmpcd_step_profiled(lbmpcd* h, int nsteps, double* phase_ms, lon
       phase.push_back(ph);
       ++nl;
     };
-    bracket(0, [&] { return launch_prep(h->dim, L, h->d_si, kc, h->d_step, h->d_pending, h->d_last_shift); });
+    const bool sort = kc == KCHUNK && h->nb_p > 0;
+    if (sort) bracket(4, [&] { return launch_sort(h->dim, h->prec, L, h->bm_p, h->nb_p, h->bm_t, h->nb_t); });
+    bracket(0, [&] { return launch_prep(h->dim, L, h->d_si, kc, sort ? 1 : 0, h->d_step, h->d_pending,
+                                        h->d_last_shift); });
     for (int k = 0; k < kc; ++k) {
-      bracket(1, [&] { return launch_lb(h->q, h->prec, L, h->bm_lb, h->nb_lb, k); });
+      bracket(1, [&] { return launch_lb(h->q, h->prec, h->lbvec, L, h->bm_lb, h->nb_lb, k); });
       if (h->nb_p) bracket(2, [&] { return launch_particles(h->dim, h->prec, L, h->bm_p, h->nb_p, k); });
       if (h->nb_c) bracket(3, [&] { return launch_cells(h->q, h->prec, L, h->bm_c, h->nb_c, k); });
     }
@@ -352,6 +380,7 @@ extern "C" int lbmpcd_step_profiled(lbmpcd* h, int nsteps, double* phase_ms, lon
       float ms = 0;
       e = cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]);
       phase_ms[phase[i]] += ms;
+      if (phase[i] == 4) nl += 3;   // the sort is four kernels
     }
     left -= kc;
     h->nstep += kc;
@@ -437,26 +466,9 @@ extern "C" int lbmpcd_get_fields(lbmpcd* h, int replica, int field, void* dst, s
                           dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToDevice, h->stream);
       break;
     case LBMPCD_CELL_COUNT:
-      e = cudaMemcpyAsync(buf, d.count, d.ncell * 4, cudaMemcpyDeviceToDevice, h->stream);
+    case LBMPCD_CELL_VCM:
+      e = launch_tab_out(h->dim, h->prec, d, field, buf, h->stream);
       break;
-    case LBMPCD_CELL_VCM: {
-      double* o = (double*)buf;
-      e = cudaMemsetAsync(o, 0, 3 * d.ncell * 8, h->stream);
-      // [ncell][3] from three structure-of-arrays columns
-      std::vector<double> host;
-      for (int a = 0; a < h->dim && e == cudaSuccess; ++a) {
-        double* col = nullptr;
-        e = cudaMalloc(&col, d.ncell * 8);
-        if (e != cudaSuccess) break;
-        e = launch_real_out(h->prec, d.vcm[a], d.ncell, col, h->stream);
-        if (e == cudaSuccess)
-          e = cudaMemcpy2DAsync(o + a, 3 * 8, col, 8, 8, d.ncell, cudaMemcpyDeviceToDevice, h->stream);
-        cudaError_t e2 = cudaStreamSynchronize(h->stream);
-        cudaFree(col);
-        if (e == cudaSuccess) e = e2;
-      }
-      break;
-    }
     case LBMPCD_WINDOW_MEAN:
       e = cudaMemcpyAsync(buf, d.wmean, d.nbuf * 4 * 8, cudaMemcpyDeviceToDevice, h->stream);
       break;

@@ -20,10 +20,16 @@
 //                  inner buffer -> f_eq(rho_LB, u_bar) written into the LB buffer.
 // The collision of the last step is applied lazily (flush) before particle
 // state is read out, so the visible state is always post-collision.
+// Every graph chunk starts with a counting sort of the particles by home cell
+// (sort_count -> sort_scan_tiles -> sort_scan_top -> sort_scatter into the
+// *_alt arrays; the chunk's first particle_pass reads them back), which keeps
+// the particles of a warp in a few neighbouring cells so that the warp-level
+// aggregation and the cell-table reads stay local.
 //
-// This translation unit is compiled with -fmad=false: streaming and binning
-// then perform exactly the IEEE operations their comments describe, so FP64
-// runs bin every particle into the same cell as a binary64 reference would.
+// Streaming and binning use the add/mul helpers below: in binary64 they are
+// the non-contractible __dadd_rn/__dmul_rn, so FP64 runs bin every particle
+// into the same cell as a binary64 reference would; in binary32 the compiler
+// may fuse them.
 #include "kernels.h"
 
 namespace lbm {
@@ -34,11 +40,18 @@ template <> struct Num<float> { static constexpr float one_minus = 1.0f - 1.0f /
 
 __device__ __forceinline__ int wrap(int a, int m) { a %= m; return a < 0 ? a + m : a; }
 
+__device__ __forceinline__ double xadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double xsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double xmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float xadd(float a, float b) { return a + b; }
+__device__ __forceinline__ float xsub(float a, float b) { return a - b; }
+__device__ __forceinline__ float xmul(float a, float b) { return a * b; }
+
 // ---------------------------------------------------------------------------
 // prep: one block; per (step k of the chunk, replica) the global step index,
 // the random shift of that step and of the previous one, and whether the
 // previous collision is still pending.
-__global__ void prep_steps(const RepDev* __restrict__ reps, int nrep, int dim, int kcount,
+__global__ void prep_steps(const RepDev* __restrict__ reps, int nrep, int dim, int kcount, int sorted,
                            StepInfo* __restrict__ si, uint32_t* d_step, int* d_pending,
                            double* d_last_shift) {
   const uint32_t n0 = *d_step;
@@ -49,7 +62,7 @@ __global__ void prep_steps(const RepDev* __restrict__ reps, int nrep, int dim, i
     s.n = n0 + k;
     s.pending = (k == 0) ? d_pending[r] : 1;
     s.write_moments = (k == kcount - 1);
-    s.pad = 0;
+    s.src_alt = (k == 0) && sorted && rd.has_region;
     const uint4 w = philox(0u, s.n, rd.rep, TAG_SHIFT, rd.key0, rd.key1);
     s.shift[0] = unit24(w.x);
     s.shift[1] = unit24(w.y);
@@ -73,9 +86,9 @@ __global__ void prep_steps(const RepDev* __restrict__ reps, int nrep, int dim, i
   if (threadIdx.x == 0) *d_step = n0 + kcount;
 }
 
-cudaError_t launch_prep(int dim, const Launch& L, StepInfo* si, int kcount, uint32_t* d_step, int* d_pending,
-                        double* d_last_shift) {
-  prep_steps<<<1, 256, 0, L.stream>>>(L.reps, L.nrep, dim, kcount, si, d_step, d_pending, d_last_shift);
+cudaError_t launch_prep(int dim, const Launch& L, StepInfo* si, int kcount, int sorted, uint32_t* d_step,
+                        int* d_pending, double* d_last_shift) {
+  prep_steps<<<1, 256, 0, L.stream>>>(L.reps, L.nrep, dim, kcount, sorted, si, d_step, d_pending, d_last_shift);
   return cudaGetLastError();
 }
 
@@ -86,12 +99,12 @@ cudaError_t launch_prep(int dim, const Launch& L, StepInfo* si, int kcount, uint
 template <int D, typename R>
 __device__ __forceinline__ uint32_t collision_cell(const RepDev& rd, int X, int Y, int Z, const R* o,
                                                    const double* s) {
-  int cx = X + ((o[0] + (R)s[0]) >= R(1) ? 1 : 0);
+  int cx = X + (xadd(o[0], (R)s[0]) >= R(1) ? 1 : 0);
   if (cx >= rd.Wx) cx -= rd.Wx;
-  const int cy = Y + ((o[1] + (R)s[1]) >= R(1) ? 1 : 0);
+  const int cy = Y + (xadd(o[1], (R)s[1]) >= R(1) ? 1 : 0);
   int cz = 0;
   if (D == 3) {
-    cz = Z + ((o[2] + (R)s[2]) >= R(1) ? 1 : 0);
+    cz = Z + (xadd(o[2], (R)s[2]) >= R(1) ? 1 : 0);
     if (cz >= rd.Wz) cz -= rd.Wz;
   }
   return (uint32_t)(cx + rd.Wx * (cy + (rd.Hy + 1) * cz));
@@ -101,22 +114,19 @@ __device__ __forceinline__ uint32_t collision_cell(const RepDev& rd, int X, int 
 // with sin(theta) stored per cell; 3D: Rodrigues' formula about the cell axis.
 template <int D, typename R>
 __device__ __forceinline__ void rotate(const RepDev& rd, uint32_t c, R* v) {
+  using T4 = typename Vec4<R>::T;
   const R ca = (R)rd.cos_a;
+  const T4* tab = (const T4*)rd.tab;
   if (D == 2) {
-    const R vcx = ((const R*)rd.vcm[0])[c], vcy = ((const R*)rd.vcm[1])[c];
-    const R sn = ((const R*)rd.rot[0])[c];
-    const R wx = v[0] - vcx, wy = v[1] - vcy;
-    v[0] = vcx + (ca * wx - sn * wy);
-    v[1] = vcy + (sn * wx + ca * wy);
+    const T4 t = tab[c];
+    const R wx = v[0] - t.x, wy = v[1] - t.y;
+    v[0] = t.x + (ca * wx - t.z * wy);
+    v[1] = t.y + (t.z * wx + ca * wy);
   } else {
     const R sa = (R)rd.sin_a;
-    R vc[3], n[3], w[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      vc[a] = ((const R*)rd.vcm[a])[c];
-      n[a] = ((const R*)rd.rot[a])[c];
-      w[a] = v[a] - vc[a];
-    }
+    const T4 t0 = tab[2 * (size_t)c], t1 = tab[2 * (size_t)c + 1];
+    const R vc[3] = {t0.x, t0.y, t0.z}, n[3] = {t1.x, t1.y, t1.z};
+    const R w[3] = {v[0] - vc[0], v[1] - vc[1], v[2] - vc[2]};
     const R cr[3] = {n[1] * w[2] - n[2] * w[1], n[2] * w[0] - n[0] * w[2], n[0] * w[1] - n[1] * w[0]};
     const R nw = n[0] * w[0] + n[1] * w[1] + n[2] * w[2];
 #pragma unroll
@@ -165,78 +175,81 @@ __device__ void u_fine(const RepDev& rd, int X, int Y, int Z, double* out) {
 // the step; x (and z) wrap periodically in the region.
 template <int D, typename R>
 __device__ __forceinline__ void stream(const RepDev& rd, int& X, int& Y, int& Z, R* o, R* v) {
-  v[0] += (R)rd.g[0];
-  v[1] += (R)rd.g[1];
-  if (D == 3) v[2] += (R)rd.g[2];
+  v[0] = xadd(v[0], (R)rd.g[0]);
+  v[1] = xadd(v[1], (R)rd.g[1]);
+  if (D == 3) v[2] = xadd(v[2], (R)rd.g[2]);
   const R rr = (R)rd.r;
-  const R dx = v[0] * rr, dy = v[1] * rr, dz = (D == 3) ? v[2] * rr : R(0);
-  const R ty = o[1] + dy;
+  const R dx = xmul(v[0], rr), dy = xmul(v[1], rr), dz = (D == 3) ? xmul(v[2], rr) : R(0);
+  const R ty = xadd(o[1], dy);
   const int ky = (int)floor(ty);
   const int nyc = Y + ky;
   R dxe = dx, dze = dz;
   if (nyc < 0 || nyc >= rd.Hy) {
     const R Lw = (nyc < 0) ? (R)(-Y) : (R)(rd.Hy - Y);   // wall, local units
     const R ts = (Lw - o[1]) / dy;                       // fraction before the hit
-    const R tr = Lw - (ty - Lw);                         // mirrored end point
+    const R tr = xsub(Lw, xsub(ty, Lw));                 // mirrored end point
 #pragma unroll
     for (int a = 0; a < D; ++a) v[a] = -v[a];
-    dxe = dx * ts - dx * (R(1) - ts);
-    dze = dz * ts - dz * (R(1) - ts);
+    dxe = xsub(xmul(dx, ts), xmul(dx, xsub(R(1), ts)));
+    dze = xsub(xmul(dz, ts), xmul(dz, xsub(R(1), ts)));
     const int kr = (int)floor(tr);
     Y += kr;
-    o[1] = tr - (R)kr;
+    o[1] = xsub(tr, (R)kr);
     if (Y >= rd.Hy) { Y = rd.Hy - 1; o[1] = Num<R>::one_minus; }
     if (Y < 0) { Y = 0; o[1] = R(0); }
   } else {
     Y = nyc;
-    o[1] = ty - (R)ky;
+    o[1] = xsub(ty, (R)ky);
   }
   if (o[1] >= R(1)) {
-    o[1] -= R(1);
+    o[1] = xsub(o[1], R(1));
     Y += 1;
     if (Y >= rd.Hy) { Y = rd.Hy - 1; o[1] = Num<R>::one_minus; }
   }
-  const R tx = o[0] + dxe;
+  const R tx = xadd(o[0], dxe);
   int kx = (int)floor(tx);
-  o[0] = tx - (R)kx;
-  if (o[0] >= R(1)) { o[0] -= R(1); kx += 1; }
-  X = wrap(X + kx, rd.Wx);
+  o[0] = xsub(tx, (R)kx);
+  if (o[0] >= R(1)) { o[0] = xsub(o[0], R(1)); kx += 1; }
+  X += kx;
+  if (X < 0 || X >= rd.Wx) X = wrap(X, rd.Wx);
   if (D == 3) {
-    const R tz = o[2] + dze;
+    const R tz = xadd(o[2], dze);
     int kz = (int)floor(tz);
-    o[2] = tz - (R)kz;
-    if (o[2] >= R(1)) { o[2] -= R(1); kz += 1; }
-    Z = wrap(Z + kz, rd.Wz);
+    o[2] = xsub(tz, (R)kz);
+    if (o[2] >= R(1)) { o[2] = xsub(o[2], R(1)); kz += 1; }
+    Z += kz;
+    if (Z < 0 || Z >= rd.Wz) Z = wrap(Z, rd.Wz);
   }
 }
 
 template <int D, typename R>
 __global__ void __launch_bounds__(256) particle_pass(const RepDev* __restrict__ reps, const int2* __restrict__ bmap,
                                                      const StepInfo* __restrict__ si, int k, int nrep) {
+  __shared__ RepDev rd;
+  __shared__ StepInfo st;
   __shared__ R sv[D][256];
   const int2 bm = bmap[blockIdx.x];
-  const RepDev& rd = reps[bm.x];
-  const StepInfo& st = si[k * nrep + bm.x];
+  load_block_records(rd, st, reps, si, bm.x, k, nrep);
   const long long j = (long long)bm.y * blockDim.x + threadIdx.x;
   const bool active = j < rd.np;
   int X = 0, Y = 0, Z = 0;
   R o[3] = {R(0), R(0), R(0)}, v[3] = {R(0), R(0), R(0)};
   uint32_t cid = 0xFFFFFFFFu;
   if (active) {
-    HomePack<D>::unpack(rd.home[j], X, Y, Z);
+    const bool alt = st.src_alt;
+    HomePack<D>::unpack((alt ? rd.home_alt : rd.home)[j], X, Y, Z);
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-      o[a] = ((const R*)rd.off[a])[j];
-      v[a] = ((const R*)rd.vel[a])[j];
+      o[a] = ((const R*)(alt ? rd.off_alt[a] : rd.off[a]))[j];
+      v[a] = ((const R*)(alt ? rd.vel_alt[a] : rd.vel[a]))[j];
     }
     // a7 of step n-1
     if (st.pending) rotate<D, R>(rd, collision_cell<D, R>(rd, X, Y, Z, o, st.prev), v);
     // a2 + a3: Maxwellian redraw in the outer buffer columns
-    const int xl = X / rd.r, wcols = rd.x1 - rd.x0;
-    if (xl < rd.n_out || xl >= wcols - rd.n_out) {
+    if (X < rd.xo_lo || X >= rd.xo_hi) {
       double uf[3] = {0, 0, 0};
       u_fine<D, R>(rd, X, Y, Z, uf);
-      const uint4 w = philox(rd.pid[j], st.n, rd.rep, TAG_RESAMPLE, rd.key0, rd.key1);
+      const uint4 w = philox((alt ? rd.pid_alt : rd.pid)[j], st.n, rd.rep, TAG_RESAMPLE, rd.key0, rd.key1);
       double z0, z1, z2, z3;
       normal_pair(w.x, w.y, z0, z1);
       normal_pair(w.z, w.w, z2, z3);
@@ -244,22 +257,20 @@ __global__ void __launch_bounds__(256) particle_pass(const RepDev* __restrict__ 
       v[1] = (R)(uf[1] + rd.sig * z1);
       if (D == 3) v[2] = (R)(uf[2] + rd.sig * z2);
     }
+    if (alt) rd.pid[j] = rd.pid_alt[j];
     // a4
     stream<D, R>(rd, X, Y, Z, o, v);
     // a6: inner-buffer sample (unshifted cells), binary64 atomics
-    if (rd.n_in > 0) {
-      const int xn = X / rd.r;
-      int side = -1, col = 0;
-      if (xn >= rd.n_out && xn < rd.cw) { side = 0; col = xn - rd.n_out; }
-      else if (xn < wcols - rd.n_out && xn >= wcols - rd.cw) { side = 1; col = wcols - 1 - rd.n_out - xn; }
-      if (side >= 0) {
-        const int zl = (D == 3) ? Z / rd.r : 0;
-        const long long b = (((long long)side * rd.n_in + col) * rd.nz + zl) * (rd.ny - 2) + Y / rd.r;
-        double* fr = rd.frame + 4 * b;
-        atomicAdd(fr, rd.mass);
+    const bool left = X >= rd.xi_lo0 && X < rd.xi_hi0, right = X >= rd.xi_lo1 && X < rd.xi_hi1;
+    if (left || right) {
+      const int xn = X / rd.r, wcols = rd.x1 - rd.x0;
+      const int col = left ? xn - rd.n_out : wcols - 1 - rd.n_out - xn;
+      const int zl = (D == 3) ? Z / rd.r : 0;
+      const long long b = (((long long)(right ? 1 : 0) * rd.n_in + col) * rd.nz + zl) * (rd.ny - 2) + Y / rd.r;
+      double* fr = rd.frame + 4 * b;
+      atomicAdd(fr, rd.mass);
 #pragma unroll
-        for (int a = 0; a < D; ++a) atomicAdd(fr + 1 + a, rd.mass * (double)v[a]);
-      }
+      for (int a = 0; a < D; ++a) atomicAdd(fr + 1 + a, rd.mass * (double)v[a]);
     }
     // a5: binning under this step's shift
     cid = collision_cell<D, R>(rd, X, Y, Z, o, st.shift);
@@ -312,11 +323,13 @@ template <int Q, typename S>
 __global__ void __launch_bounds__(256) cell_pass(const RepDev* __restrict__ reps, const int2* __restrict__ bmap,
                                                  const StepInfo* __restrict__ si, int k, int nrep) {
   using R = typename Store<S>::R;
+  using T4 = typename Vec4<R>::T;
   using L = Lattice<Q>;
   constexpr int D = L::D;
+  __shared__ RepDev rd;
+  __shared__ StepInfo st;
   const int2 bm = bmap[blockIdx.x];
-  const RepDev& rd = reps[bm.x];
-  const StepInfo& st = si[k * nrep + bm.x];
+  load_block_records(rd, st, reps, si, bm.x, k, nrep);
   if (bm.y >= 0) {
     const long long c = (long long)bm.y * blockDim.x + threadIdx.x;
     if (c >= rd.ncell) return;
@@ -361,13 +374,19 @@ __global__ void __launch_bounds__(256) cell_pass(const RepDev* __restrict__ reps
         }
       }
     }
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-      ((R*)rd.vcm[a])[c] = vc[a];
-      ((R*)rd.rot[a])[c] = rt[a];
-      ((R*)rd.acc_v[a])[c] = R(0);
+    T4* tab = (T4*)rd.tab;
+    if (D == 2) {
+      T4 t; t.x = vc[0]; t.y = vc[1]; t.z = rt[0]; t.w = (R)n;
+      tab[c] = t;
+    } else {
+      T4 t0, t1;
+      t0.x = vc[0]; t0.y = vc[1]; t0.z = vc[2]; t0.w = (R)n;
+      t1.x = rt[0]; t1.y = rt[1]; t1.z = rt[2]; t1.w = R(0);
+      tab[2 * c] = t0;
+      tab[2 * c + 1] = t1;
     }
-    rd.count[c] = (int)n;
+#pragma unroll
+    for (int a = 0; a < D; ++a) ((R*)rd.acc_v[a])[c] = R(0);
     rd.acc_n[c] = 0u;
     return;
   }
@@ -613,6 +632,161 @@ cudaError_t launch_diag_particles(int dim, int prec, const RepDev& rd, double* o
   } else {
     if (prec == P_FP64) part_diag<3, double><<<nb, 256, 0, st>>>(rd, out9);
     else part_diag<3, float><<<nb, 256, 0, st>>>(rd, out9);
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Counting sort of the particles by home cell (row-major X fastest).
+// sort_count: rank of every particle inside its home cell (warp-aggregated
+// atomics on the per-cell counters); sort_scan_tiles: exclusive prefix of the
+// counters inside tiles of SORT_TILE cells, tile totals, counters cleared;
+// sort_scan_top: exclusive prefix of the tile totals (one block per replica);
+// sort_scatter: every particle copied to its sorted slot in the *_alt arrays.
+template <int D>
+__device__ __forceinline__ uint32_t home_index(const RepDev& rd, uint32_t packed) {
+  int X, Y, Z;
+  HomePack<D>::unpack(packed, X, Y, Z);
+  return (uint32_t)(X + rd.Wx * (Y + rd.Hy * Z));
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) sort_count(const RepDev* __restrict__ reps, const int2* __restrict__ bmap) {
+  __shared__ RepDev rd;
+  __shared__ StepInfo unused;
+  const int2 bm = bmap[blockIdx.x];
+  load_block_records(rd, unused, reps, nullptr, bm.x, 0, 0);
+  const long long j = (long long)bm.y * blockDim.x + threadIdx.x;
+  const bool active = j < rd.np;
+  const uint32_t h = active ? home_index<D>(rd, rd.home[j]) : 0xFFFFFFFFu;
+  const unsigned grp = __match_any_sync(0xFFFFFFFFu, h);
+  const int lane = threadIdx.x & 31, leader = __ffs(grp) - 1;
+  uint32_t base = 0;
+  if (active && lane == leader) base = atomicAdd(rd.hcount + h, (uint32_t)__popc(grp));
+  base = __shfl_sync(0xFFFFFFFFu, base, leader);
+  if (active) rd.rank[j] = base + (uint32_t)__popc(grp & ((1u << lane) - 1u));
+}
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t* warp_tot, uint32_t& total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint32_t inc = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) warp_tot[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    uint32_t t = lane < nw ? warp_tot[lane] : 0u, ti = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t u = __shfl_up_sync(0xFFFFFFFFu, ti, o);
+      if (lane >= o) ti += u;
+    }
+    if (lane < nw) warp_tot[lane] = ti - t;
+    if (lane == 31) warp_tot[32] = ti;
+  }
+  __syncthreads();
+  total = warp_tot[32];
+  return inc - x + warp_tot[w];
+}
+
+__global__ void __launch_bounds__(SORT_TILE) sort_scan_tiles(const RepDev* __restrict__ reps, const int2* __restrict__ bmap) {
+  __shared__ RepDev rd;
+  __shared__ StepInfo unused;
+  __shared__ uint32_t wt[33];
+  const int2 bm = bmap[blockIdx.x];
+  load_block_records(rd, unused, reps, nullptr, bm.x, 0, 0);
+  const long long c = (long long)bm.y * SORT_TILE + threadIdx.x;
+  const uint32_t x = c < rd.nhome ? rd.hcount[c] : 0u;
+  uint32_t total;
+  const uint32_t ex = block_exclusive_scan(x, wt, total);
+  if (c < rd.nhome) { rd.hoff[c] = ex; rd.hcount[c] = 0u; }
+  if (threadIdx.x == 0) rd.tsum[bm.y] = total;
+}
+
+__global__ void __launch_bounds__(1024) sort_scan_top(const RepDev* __restrict__ reps) {
+  __shared__ RepDev rd;
+  __shared__ StepInfo unused;
+  __shared__ uint32_t wt[33];
+  load_block_records(rd, unused, reps, nullptr, blockIdx.x, 0, 0);
+  if (!rd.has_region) return;
+  uint32_t carry = 0;
+  for (int base = 0; base < rd.ntile; base += blockDim.x) {
+    const int t = base + threadIdx.x;
+    const uint32_t x = t < rd.ntile ? rd.tsum[t] : 0u;
+    uint32_t total;
+    const uint32_t ex = block_exclusive_scan(x, wt, total);
+    if (t < rd.ntile) rd.tsum[t] = carry + ex;
+    carry += total;
+    __syncthreads();
+  }
+}
+
+template <int D, typename R>
+__global__ void __launch_bounds__(256) sort_scatter(const RepDev* __restrict__ reps, const int2* __restrict__ bmap) {
+  __shared__ RepDev rd;
+  __shared__ StepInfo unused;
+  const int2 bm = bmap[blockIdx.x];
+  load_block_records(rd, unused, reps, nullptr, bm.x, 0, 0);
+  const long long j = (long long)bm.y * blockDim.x + threadIdx.x;
+  if (j >= rd.np) return;
+  const uint32_t hp = rd.home[j];
+  const uint32_t h = home_index<D>(rd, hp);
+  const long long dst = (long long)rd.tsum[h / SORT_TILE] + rd.hoff[h] + rd.rank[j];
+  rd.home_alt[dst] = hp;
+  rd.pid_alt[dst] = rd.pid[j];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    ((R*)rd.off_alt[a])[dst] = ((const R*)rd.off[a])[j];
+    ((R*)rd.vel_alt[a])[dst] = ((const R*)rd.vel[a])[j];
+  }
+}
+
+cudaError_t launch_sort(int dim, int prec, const Launch& L, const int2* bmap_p, int nb_p, const int2* bmap_t,
+                        int nb_t) {
+  if (nb_p == 0) return cudaSuccess;
+  if (dim == 2) sort_count<2><<<nb_p, 256, 0, L.stream>>>(L.reps, bmap_p);
+  else sort_count<3><<<nb_p, 256, 0, L.stream>>>(L.reps, bmap_p);
+  sort_scan_tiles<<<nb_t, SORT_TILE, 0, L.stream>>>(L.reps, bmap_t);
+  sort_scan_top<<<L.nrep, 1024, 0, L.stream>>>(L.reps);
+  if (dim == 2) {
+    if (prec == P_FP64) sort_scatter<2, double><<<nb_p, 256, 0, L.stream>>>(L.reps, bmap_p);
+    else sort_scatter<2, float><<<nb_p, 256, 0, L.stream>>>(L.reps, bmap_p);
+  } else {
+    if (prec == P_FP64) sort_scatter<3, double><<<nb_p, 256, 0, L.stream>>>(L.reps, bmap_p);
+    else sort_scatter<3, float><<<nb_p, 256, 0, L.stream>>>(L.reps, bmap_p);
+  }
+  return cudaGetLastError();
+}
+
+// collision-cell table -> CELL_COUNT (int32) or CELL_VCM ([ncell][3] binary64)
+template <int D, typename R>
+__global__ void tab_out(RepDev rd, int field, void* out) {
+  using T4 = typename Vec4<R>::T;
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= rd.ncell) return;
+  const T4 t = ((const T4*)rd.tab)[(D == 2 ? 1 : 2) * c];
+  if (field == 7) {
+    ((int*)out)[c] = (int)t.w;
+  } else {
+    double* o = (double*)out;
+    o[3 * c] = (double)t.x;
+    o[3 * c + 1] = (double)t.y;
+    o[3 * c + 2] = D == 3 ? (double)t.z : 0.0;
+  }
+}
+
+cudaError_t launch_tab_out(int dim, int prec, const RepDev& rd, int field, void* out, cudaStream_t st) {
+  const int nb = (int)((rd.ncell + 255) / 256);
+  if (nb == 0) return cudaSuccess;
+  if (dim == 2) {
+    if (prec == P_FP64) tab_out<2, double><<<nb, 256, 0, st>>>(rd, field, out);
+    else tab_out<2, float><<<nb, 256, 0, st>>>(rd, field, out);
+  } else {
+    if (prec == P_FP64) tab_out<3, double><<<nb, 256, 0, st>>>(rd, field, out);
+    else tab_out<3, float><<<nb, 256, 0, st>>>(rd, field, out);
   }
   return cudaGetLastError();
 }
