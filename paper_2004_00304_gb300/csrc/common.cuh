@@ -206,4 +206,41 @@ __device__ __forceinline__ void load_block_records(RepDev& srd, StepInfo& sst, c
   __syncthreads();
 }
 
+// Grid-stride walk over a block map: a block processes work items blockIdx.x,
+// blockIdx.x + gridDim.x, ...; the replica's records are reloaded into shared
+// memory only when the replica changes (the map lists each replica's items
+// contiguously).  The body runs with the records of its item's replica.
+template <typename Item, typename Body>
+__device__ __forceinline__ void for_each_item(const Item* __restrict__ bmap, int nwork, const RepDev* reps,
+                                              const StepInfo* si, int k, int nrep, RepDev& rd, StepInfo& st,
+                                              Body&& body) {
+  int cur = -1;
+  for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
+    const Item bm = bmap[wi];
+    if (bm.x != cur) {
+      __syncthreads();
+      load_block_records(rd, st, reps, si, bm.x, k, nrep);
+      cur = bm.x;
+    }
+    body(bm);
+  }
+}
+
+// Blocks to launch for nwork items: enough to fill every SM at the kernel's
+// occupancy, never more than the items.
+template <typename K>
+inline int grid_for(K kernel, int threads, int nwork) {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, 0) != cudaSuccess || occ < 1) occ = 1;
+  const long long cap = (long long)occ * sms;
+  return (int)(nwork < cap ? nwork : cap);
+}
+
 }  // namespace lbm

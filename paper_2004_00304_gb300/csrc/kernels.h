@@ -19,7 +19,7 @@ struct Launch {
 // a1: fused pull stream + BGK collide (+ Guo force, bounce-back walls).
 // vec = nodes per thread (lb_vector_width); one vec for all replicas of a handle.
 int lb_vector_width(int prec, int nx);
-cudaError_t launch_lb(int q, int prec, int vec, const Launch& L, const int2* bmap, int nblocks, int k);
+cudaError_t launch_lb(int q, int prec, int vec, const Launch& L, const int4* bmap, int nblocks, int k);
 
 // prep: per-step records (shift, pending flag) for kcount steps.
 cudaError_t launch_prep(int dim, const Launch& L, StepInfo* si, int kcount, int sorted, uint32_t* d_step,

@@ -52,27 +52,16 @@ template <> struct Row<__half, 4> {
 __device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 
-// One thread owns V consecutive nodes x0 .. x0+V-1 of one row (y, z).
+// One thread owns V consecutive nodes x0 .. x0+V-1 of one row (y, z); a
+// work item (replica, tile, y, z) is one block-wide tile of a row.
 template <int Q, typename S, int V>
-__global__ void __launch_bounds__(128) lb_pull(const RepDev* __restrict__ reps, const int2* __restrict__ bmap,
-                                               const StepInfo* __restrict__ si, int k, int nrep) {
+__device__ __forceinline__ void lb_row(const RepDev& rd, const StepInfo& st, const int4 bm) {
   using L = Lattice<Q>;
   using R = typename Store<S>::R;
-  __shared__ RepDev rd;
-  __shared__ StepInfo st;
-  __shared__ int srow[3];
-  const int2 bm = bmap[blockIdx.x];
-  if (threadIdx.x == 0) {
-    const RepDev& g = reps[bm.x];
-    const int tpr = g.nx / V, ntx = (tpr + blockDim.x - 1) / blockDim.x;
-    const int tile = bm.y % ntx, yz = bm.y / ntx;
-    srow[0] = tile; srow[1] = 1 + yz % (g.ny - 2); srow[2] = yz / (g.ny - 2);
-  }
-  load_block_records(rd, st, reps, si, bm.x, k, nrep);
   const int nx = rd.nx, ny = rd.ny, nz = rd.nz;
-  const int y = srow[1], z = srow[2];
+  const int y = bm.z, z = bm.w;
   const int tpr = nx / V;
-  const int tx = srow[0] * blockDim.x + threadIdx.x;
+  const int tx = bm.y * blockDim.x + threadIdx.x;
   const bool active = tx < tpr;
   const int lane = threadIdx.x & 31;
   const int x0 = tx * V;
@@ -189,16 +178,26 @@ __global__ void __launch_bounds__(128) lb_pull(const RepDev* __restrict__ reps, 
   }
 }
 
+
 template <int Q, typename S, int V>
-static cudaError_t go_lb(const Launch& L, const int2* bmap, int nblocks, int k) {
-  if (nblocks == 0) return cudaSuccess;
-  lb_pull<Q, S, V><<<nblocks, 128, 0, L.stream>>>(L.reps, bmap, L.si, k, L.nrep);
+__global__ void __launch_bounds__(128) lb_pull(const RepDev* __restrict__ reps, const int4* __restrict__ bmap,
+                                               int nwork, const StepInfo* __restrict__ si, int k, int nrep) {
+  __shared__ RepDev rd;
+  __shared__ StepInfo st;
+  for_each_item(bmap, nwork, reps, si, k, nrep, rd, st, [&](const int4 bm) { lb_row<Q, S, V>(rd, st, bm); });
+}
+
+template <int Q, typename S, int V>
+static cudaError_t go_lb(const Launch& L, const int4* bmap, int nwork, int k) {
+  if (nwork == 0) return cudaSuccess;
+  static const int g = grid_for(lb_pull<Q, S, V>, 128, 1 << 30);
+  lb_pull<Q, S, V><<<g < nwork ? g : nwork, 128, 0, L.stream>>>(L.reps, bmap, nwork, L.si, k, L.nrep);
   return cudaGetLastError();
 }
 
 int lb_vector_width(int prec, int nx) { return (prec != P_FP64 && nx % 4 == 0) ? 4 : 1; }
 
-cudaError_t launch_lb(int q, int prec, int vec, const Launch& L, const int2* bmap, int nblocks, int k) {
+cudaError_t launch_lb(int q, int prec, int vec, const Launch& L, const int4* bmap, int nblocks, int k) {
   if (q == 9) {
     if (prec == P_FP64) return go_lb<9, double, 1>(L, bmap, nblocks, k);
     if (prec == P_FP32) return vec == 4 ? go_lb<9, float, 4>(L, bmap, nblocks, k) : go_lb<9, float, 1>(L, bmap, nblocks, k);

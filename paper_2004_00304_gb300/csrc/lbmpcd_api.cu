@@ -34,7 +34,8 @@ struct lbmpcd {
   std::vector<std::vector<void*>> rep_allocs;   // per replica, region arrays
   std::vector<void*> allocs;                    // handle-wide
   RepDev* d_reps = nullptr;
-  int2 *bm_lb = nullptr, *bm_p = nullptr, *bm_c = nullptr, *bm_t = nullptr;
+  int4* bm_lb = nullptr;
+  int2 *bm_p = nullptr, *bm_c = nullptr, *bm_t = nullptr;
   int nb_lb = 0, nb_p = 0, nb_c = 0, nb_t = 0;
   StepInfo* d_si = nullptr;
   uint32_t* d_step = nullptr;
@@ -181,14 +182,36 @@ extern "C" int lbmpcd_create(const lbmpcd_params* params, int n_replicas, void* 
   return LBMPCD_OK;
 }
 
-// Block maps: (replica, local block) per block of each kernel family.
+// Block maps, one work item per entry, each replica's items contiguous:
+// LB (replica, tile, y, z); particles / sort (replica, block of 256
+// particles); cells (replica, block of 256 cells, or -1-b for block b of the
+// inner-buffer nodes); sort tiles (replica, tile of SORT_TILE home cells).
+template <typename T>
+static int upload_map(lbmpcd* h, T** dst, int* cnt, const std::vector<T>& src) {
+  if (*dst) {
+    cudaFree(*dst);
+    for (auto it = h->allocs.begin(); it != h->allocs.end(); ++it)
+      if (*it == (void*)*dst) { h->allocs.erase(it); break; }
+    *dst = nullptr;
+  }
+  *cnt = (int)src.size();
+  if (src.empty()) return LBMPCD_OK;
+  void* p = nullptr;
+  CK(h, dalloc(h->allocs, &p, sizeof(T) * src.size()));
+  *dst = (T*)p;
+  CK(h, cudaMemcpy(p, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice));
+  return LBMPCD_OK;
+}
+
 static int build_maps(lbmpcd* h) {
-  std::vector<int2> lb, pp, cc, tt;
+  std::vector<int4> lb;
+  std::vector<int2> pp, cc, tt;
   for (int r = 0; r < h->nrep; ++r) {
     const RepDev& d = h->rd[r];
     const int ntx = (d.nx / h->lbvec + 127) / 128;
-    const long long nlb = (long long)ntx * (d.ny - 2) * d.nz;
-    for (long long b = 0; b < nlb; ++b) lb.push_back(make_int2(r, (int)b));
+    for (int z = 0; z < d.nz; ++z)
+      for (int y = 1; y < d.ny - 1; ++y)
+        for (int t = 0; t < ntx; ++t) lb.push_back(make_int4(r, t, y, z));
     if (!d.has_region) continue;
     const long long npb = (d.np + 255) / 256, ncb = (d.ncell + 255) / 256, nbb = (d.nbuf + 255) / 256;
     for (long long b = 0; b < npb; ++b) pp.push_back(make_int2(r, (int)b));
@@ -196,23 +219,11 @@ static int build_maps(lbmpcd* h) {
     for (long long b = 0; b < nbb; ++b) cc.push_back(make_int2(r, (int)(-1 - b)));
     for (int b = 0; b < d.ntile; ++b) tt.push_back(make_int2(r, b));
   }
-  int2** dst[4] = {&h->bm_lb, &h->bm_p, &h->bm_c, &h->bm_t};
-  int* cnt[4] = {&h->nb_lb, &h->nb_p, &h->nb_c, &h->nb_t};
-  std::vector<int2>* src[4] = {&lb, &pp, &cc, &tt};
-  for (int i = 0; i < 4; ++i) {
-    if (*dst[i]) {
-      cudaFree(*dst[i]);
-      for (auto it = h->allocs.begin(); it != h->allocs.end(); ++it)
-        if (*it == *dst[i]) { h->allocs.erase(it); break; }
-      *dst[i] = nullptr;
-    }
-    *cnt[i] = (int)src[i]->size();
-    if (src[i]->empty()) continue;
-    void* p = nullptr;
-    CK(h, dalloc(h->allocs, &p, sizeof(int2) * src[i]->size()));
-    *dst[i] = (int2*)p;
-    CK(h, cudaMemcpy(p, src[i]->data(), sizeof(int2) * src[i]->size(), cudaMemcpyHostToDevice));
-  }
+  int rc = upload_map(h, &h->bm_lb, &h->nb_lb, lb);
+  if (!rc) rc = upload_map(h, &h->bm_p, &h->nb_p, pp);
+  if (!rc) rc = upload_map(h, &h->bm_c, &h->nb_c, cc);
+  if (!rc) rc = upload_map(h, &h->bm_t, &h->nb_t, tt);
+  if (rc) return rc;
   CK(h, cudaMemcpy(h->d_reps, h->rd.data(), sizeof(RepDev) * h->nrep, cudaMemcpyHostToDevice));
   if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
   h->maps_dirty = false;

@@ -223,13 +223,7 @@ __device__ __forceinline__ void stream(const RepDev& rd, int& X, int& Y, int& Z,
 }
 
 template <int D, typename R>
-__global__ void __launch_bounds__(256) particle_pass(const RepDev* __restrict__ reps, const int2* __restrict__ bmap,
-                                                     const StepInfo* __restrict__ si, int k, int nrep) {
-  __shared__ RepDev rd;
-  __shared__ StepInfo st;
-  __shared__ R sv[D][256];
-  const int2 bm = bmap[blockIdx.x];
-  load_block_records(rd, st, reps, si, bm.x, k, nrep);
+__device__ __forceinline__ void particle_item(const RepDev& rd, const StepInfo& st, const int2 bm, R (*sv)[256]) {
   const long long j = (long long)bm.y * blockDim.x + threadIdx.x;
   const bool active = j < rd.np;
   int X = 0, Y = 0, Z = 0;
@@ -285,6 +279,7 @@ __global__ void __launch_bounds__(256) particle_pass(const RepDev* __restrict__ 
   // their lowest lane, which issues one atomic per accumulator.
   const unsigned grp = __match_any_sync(0xFFFFFFFFu, cid);
   const int lane = threadIdx.x & 31, wbase = threadIdx.x & ~31;
+  __syncwarp();
 #pragma unroll
   for (int a = 0; a < D; ++a) sv[a][threadIdx.x] = v[a];
   __syncwarp();
@@ -305,14 +300,29 @@ __global__ void __launch_bounds__(256) particle_pass(const RepDev* __restrict__ 
   }
 }
 
-cudaError_t launch_particles(int dim, int prec, const Launch& L, const int2* bmap, int nblocks, int k) {
-  if (nblocks == 0) return cudaSuccess;
+template <int D, typename R>
+__global__ void __launch_bounds__(256) particle_pass(const RepDev* __restrict__ reps, const int2* __restrict__ bmap,
+                                                     int nwork, const StepInfo* __restrict__ si, int k, int nrep) {
+  __shared__ RepDev rd;
+  __shared__ StepInfo st;
+  __shared__ R sv[D][256];
+  for_each_item(bmap, nwork, reps, si, k, nrep, rd, st, [&](const int2 bm) { particle_item<D, R>(rd, st, bm, sv); });
+}
+
+template <int D, typename R>
+static void go_particles(const Launch& L, const int2* bmap, int nwork, int k) {
+  static const int g = grid_for(particle_pass<D, R>, 256, 1 << 30);
+  particle_pass<D, R><<<g < nwork ? g : nwork, 256, 0, L.stream>>>(L.reps, bmap, nwork, L.si, k, L.nrep);
+}
+
+cudaError_t launch_particles(int dim, int prec, const Launch& L, const int2* bmap, int nwork, int k) {
+  if (nwork == 0) return cudaSuccess;
   if (dim == 2) {
-    if (prec == P_FP64) particle_pass<2, double><<<nblocks, 256, 0, L.stream>>>(L.reps, bmap, L.si, k, L.nrep);
-    else particle_pass<2, float><<<nblocks, 256, 0, L.stream>>>(L.reps, bmap, L.si, k, L.nrep);
+    if (prec == P_FP64) go_particles<2, double>(L, bmap, nwork, k);
+    else go_particles<2, float>(L, bmap, nwork, k);
   } else {
-    if (prec == P_FP64) particle_pass<3, double><<<nblocks, 256, 0, L.stream>>>(L.reps, bmap, L.si, k, L.nrep);
-    else particle_pass<3, float><<<nblocks, 256, 0, L.stream>>>(L.reps, bmap, L.si, k, L.nrep);
+    if (prec == P_FP64) go_particles<3, double>(L, bmap, nwork, k);
+    else go_particles<3, float>(L, bmap, nwork, k);
   }
   return cudaGetLastError();
 }
@@ -320,16 +330,11 @@ cudaError_t launch_particles(int dim, int prec, const Launch& L, const int2* bma
 // ---------------------------------------------------------------------------
 // cell_pass: a7 cell part and a8.
 template <int Q, typename S>
-__global__ void __launch_bounds__(256) cell_pass(const RepDev* __restrict__ reps, const int2* __restrict__ bmap,
-                                                 const StepInfo* __restrict__ si, int k, int nrep) {
+__device__ __forceinline__ void cell_item(const RepDev& rd, const StepInfo& st, const int2 bm) {
   using R = typename Store<S>::R;
   using T4 = typename Vec4<R>::T;
   using L = Lattice<Q>;
   constexpr int D = L::D;
-  __shared__ RepDev rd;
-  __shared__ StepInfo st;
-  const int2 bm = bmap[blockIdx.x];
-  load_block_records(rd, st, reps, si, bm.x, k, nrep);
   if (bm.y >= 0) {
     const long long c = (long long)bm.y * blockDim.x + threadIdx.x;
     if (c >= rd.ncell) return;
@@ -432,9 +437,23 @@ __global__ void __launch_bounds__(256) cell_pass(const RepDev* __restrict__ reps
   }
 }
 
+template <int Q, typename S>
+__global__ void __launch_bounds__(256) cell_pass(const RepDev* __restrict__ reps, const int2* __restrict__ bmap,
+                                                 int nwork, const StepInfo* __restrict__ si, int k, int nrep) {
+  __shared__ RepDev rd;
+  __shared__ StepInfo st;
+  for_each_item(bmap, nwork, reps, si, k, nrep, rd, st, [&](const int2 bm) { cell_item<Q, S>(rd, st, bm); });
+}
+
+template <int Q, typename S>
+static void go_cells(const Launch& L, const int2* bmap, int nwork, int k) {
+  static const int g = grid_for(cell_pass<Q, S>, 256, 1 << 30);
+  cell_pass<Q, S><<<g < nwork ? g : nwork, 256, 0, L.stream>>>(L.reps, bmap, nwork, L.si, k, L.nrep);
+}
+
 cudaError_t launch_cells(int q, int prec, const Launch& L, const int2* bmap, int nblocks, int k) {
   if (nblocks == 0) return cudaSuccess;
-#define LBM_CELLS(QQ, SS) cell_pass<QQ, SS><<<nblocks, 256, 0, L.stream>>>(L.reps, bmap, L.si, k, L.nrep)
+#define LBM_CELLS(QQ, SS) go_cells<QQ, SS>(L, bmap, nblocks, k)
   if (q == 9) {
     if (prec == P_FP64) LBM_CELLS(9, double);
     else if (prec == P_FP32) LBM_CELLS(9, float);
@@ -651,11 +670,7 @@ __device__ __forceinline__ uint32_t home_index(const RepDev& rd, uint32_t packed
 }
 
 template <int D>
-__global__ void __launch_bounds__(256) sort_count(const RepDev* __restrict__ reps, const int2* __restrict__ bmap) {
-  __shared__ RepDev rd;
-  __shared__ StepInfo unused;
-  const int2 bm = bmap[blockIdx.x];
-  load_block_records(rd, unused, reps, nullptr, bm.x, 0, 0);
+__device__ __forceinline__ void sort_count_item(const RepDev& rd, const int2 bm) {
   const long long j = (long long)bm.y * blockDim.x + threadIdx.x;
   const bool active = j < rd.np;
   const uint32_t h = active ? home_index<D>(rd, rd.home[j]) : 0xFFFFFFFFu;
@@ -665,6 +680,15 @@ __global__ void __launch_bounds__(256) sort_count(const RepDev* __restrict__ rep
   if (active && lane == leader) base = atomicAdd(rd.hcount + h, (uint32_t)__popc(grp));
   base = __shfl_sync(0xFFFFFFFFu, base, leader);
   if (active) rd.rank[j] = base + (uint32_t)__popc(grp & ((1u << lane) - 1u));
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) sort_count(const RepDev* __restrict__ reps, const int2* __restrict__ bmap,
+                                                  int nwork) {
+  __shared__ RepDev rd;
+  __shared__ StepInfo unused;
+  for_each_item(bmap, nwork, reps, (const StepInfo*)nullptr, 0, 0, rd, unused,
+                [&](const int2 bm) { sort_count_item<D>(rd, bm); });
 }
 
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t* warp_tot, uint32_t& total) {
@@ -725,11 +749,7 @@ __global__ void __launch_bounds__(1024) sort_scan_top(const RepDev* __restrict__
 }
 
 template <int D, typename R>
-__global__ void __launch_bounds__(256) sort_scatter(const RepDev* __restrict__ reps, const int2* __restrict__ bmap) {
-  __shared__ RepDev rd;
-  __shared__ StepInfo unused;
-  const int2 bm = bmap[blockIdx.x];
-  load_block_records(rd, unused, reps, nullptr, bm.x, 0, 0);
+__device__ __forceinline__ void sort_scatter_item(const RepDev& rd, const int2 bm) {
   const long long j = (long long)bm.y * blockDim.x + threadIdx.x;
   if (j >= rd.np) return;
   const uint32_t hp = rd.home[j];
@@ -744,19 +764,30 @@ __global__ void __launch_bounds__(256) sort_scatter(const RepDev* __restrict__ r
   }
 }
 
+template <int D, typename R>
+__global__ void __launch_bounds__(256) sort_scatter(const RepDev* __restrict__ reps, const int2* __restrict__ bmap,
+                                                    int nwork) {
+  __shared__ RepDev rd;
+  __shared__ StepInfo unused;
+  for_each_item(bmap, nwork, reps, (const StepInfo*)nullptr, 0, 0, rd, unused,
+                [&](const int2 bm) { sort_scatter_item<D, R>(rd, bm); });
+}
+
 cudaError_t launch_sort(int dim, int prec, const Launch& L, const int2* bmap_p, int nb_p, const int2* bmap_t,
                         int nb_t) {
   if (nb_p == 0) return cudaSuccess;
-  if (dim == 2) sort_count<2><<<nb_p, 256, 0, L.stream>>>(L.reps, bmap_p);
-  else sort_count<3><<<nb_p, 256, 0, L.stream>>>(L.reps, bmap_p);
+  static const int gc2 = grid_for(sort_count<2>, 256, 1 << 30), gc3 = grid_for(sort_count<3>, 256, 1 << 30);
+  if (dim == 2) sort_count<2><<<gc2 < nb_p ? gc2 : nb_p, 256, 0, L.stream>>>(L.reps, bmap_p, nb_p);
+  else sort_count<3><<<gc3 < nb_p ? gc3 : nb_p, 256, 0, L.stream>>>(L.reps, bmap_p, nb_p);
   sort_scan_tiles<<<nb_t, SORT_TILE, 0, L.stream>>>(L.reps, bmap_t);
   sort_scan_top<<<L.nrep, 1024, 0, L.stream>>>(L.reps);
+  const int gs = nb_p < 16384 ? nb_p : 16384;
   if (dim == 2) {
-    if (prec == P_FP64) sort_scatter<2, double><<<nb_p, 256, 0, L.stream>>>(L.reps, bmap_p);
-    else sort_scatter<2, float><<<nb_p, 256, 0, L.stream>>>(L.reps, bmap_p);
+    if (prec == P_FP64) sort_scatter<2, double><<<gs, 256, 0, L.stream>>>(L.reps, bmap_p, nb_p);
+    else sort_scatter<2, float><<<gs, 256, 0, L.stream>>>(L.reps, bmap_p, nb_p);
   } else {
-    if (prec == P_FP64) sort_scatter<3, double><<<nb_p, 256, 0, L.stream>>>(L.reps, bmap_p);
-    else sort_scatter<3, float><<<nb_p, 256, 0, L.stream>>>(L.reps, bmap_p);
+    if (prec == P_FP64) sort_scatter<3, double><<<gs, 256, 0, L.stream>>>(L.reps, bmap_p, nb_p);
+    else sort_scatter<3, float><<<gs, 256, 0, L.stream>>>(L.reps, bmap_p, nb_p);
   }
   return cudaGetLastError();
 }

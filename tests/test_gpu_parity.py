@@ -69,10 +69,20 @@ def ambiguous_particles(o, dim, eps):
 
 # ---------------------------------------------------------------------------
 # LB alone
-@pytest.mark.parametrize("case,prec", [("2d", 0), ("3d", 0), ("2d", 1), ("3d", 1)])
+@pytest.mark.parametrize("case,prec", [("2d", 0), ("3d", 0), ("2d", 1), ("3d", 1), ("2d_vec", 1),
+                                       ("3d_vec", 1), ("2d_vec_wide", 1)])
 def test_lb_stream_collide_parity(lb, case, prec):
-    """a1 on perturbed populations with walls, periodic x/z, force, ragged tiles."""
-    cfg = inputs.small_2d(precision=prec) if case == "2d" else inputs.small_3d(precision=prec)
+    """a1 on perturbed populations with walls, periodic x/z, force, ragged tiles;
+    *_vec rows (nx a multiple of 4) take the 4-nodes-per-thread path, the wide
+    one spans several blocks per row with a partial last block."""
+    if case == "2d_vec":
+        cfg = inputs.small_2d(precision=prec, nx=72)
+    elif case == "2d_vec_wide":
+        cfg = inputs.small_2d(precision=prec, nx=1100, ny=7)
+    elif case == "3d_vec":
+        cfg = inputs.small_3d(precision=prec, nx=24)
+    else:
+        cfg = inputs.small_2d(precision=prec) if case == "2d" else inputs.small_3d(precision=prec)
     p = cfg["params"]
     g, o = pair(lb, cfg, region=False)
     c, w = O.lattice(p["lattice"])
@@ -132,6 +142,22 @@ def test_coupled_step_parity_fp64(lb, case):
             e = rel_err(g.get(f), o.get(f), FLOOR.get(f, 0.0))
             assert e <= 1e-12, (f, e)
         np.testing.assert_allclose(g.get("DIAG"), o.get("DIAG"), rtol=1e-12, atol=1e-13)
+
+
+@pytest.mark.parametrize("case", ["2d", "3d"])
+def test_coupled_run_with_sorting_fp64(lb, case):
+    """100 steps = three 32-step graph chunks, each opening with the particle
+    sort, plus a remainder: state still matches the oracle (ids followed)."""
+    cfg = inputs.small_2d(precision=0, nx=72) if case == "2d" else inputs.small_3d(precision=0, nx=24)
+    g, o = pair(lb, cfg)
+    g.step(100)
+    o.step(100)
+    assert np.array_equal(g.get("PART_HOME"), o.get("PART_HOME"))
+    assert np.array_equal(g.get("PART_CELL"), o.get("PART_CELL"))
+    assert np.array_equal(g.get("CELL_COUNT"), o.get("CELL_COUNT"))
+    for f in ("PART_POS", "PART_VEL", "CELL_VCM", "WINDOW_MEAN", "POPS", "U"):
+        e = rel_err(g.get(f), o.get(f), FLOOR.get(f, 0.0))
+        assert e <= 1e-12, (f, e)
 
 
 def test_coupled_step_parity_fp32(lb):
