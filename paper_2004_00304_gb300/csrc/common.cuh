@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 #include <stdint.h>
+#include <stdlib.h>
 
 #define LBM_HD __host__ __device__ __forceinline__
 
@@ -105,6 +106,9 @@ struct RepDev {
   int has_region, x0, x1, Wx, Hy, Wz, r, n_out, n_in, cw, ppc, feedback, window;
   double kT, mass, sig;    // sig = sqrt(kT / m)
   double cos_a, sin_a, alpha;
+  // binary32 copies of the constants the binary32 kernels use (binary64
+  // arithmetic, conversions included, is slow on this GPU)
+  float omega_f, g_f[3], r_f, cos_f, sin_f;
   long long np;            // particles
   long long ncell;         // collision cells: Wx (Hy+1) Wz
   long long nbuf;          // inner-buffer LB nodes
@@ -154,6 +158,28 @@ struct StepInfo {
   int write_moments;       // write rho/u on every node this step
   int src_alt;             // particle state of this step is in the *_alt (sorted) arrays
   double shift[3], prev[3];
+  float shift_f[3], prev_f[3];   // the same shifts (exact in binary32)
+};
+
+// The per-replica and per-step constants in the kernel's precision.
+template <typename R> struct Cst;
+template <> struct Cst<double> {
+  __device__ static double omega(const RepDev& d) { return d.omega; }
+  __device__ static double g(const RepDev& d, int a) { return d.g[a]; }
+  __device__ static double r(const RepDev& d) { return (double)d.r; }
+  __device__ static double cos_a(const RepDev& d) { return d.cos_a; }
+  __device__ static double sin_a(const RepDev& d) { return d.sin_a; }
+  __device__ static const double* shift(const StepInfo& s) { return s.shift; }
+  __device__ static const double* prev(const StepInfo& s) { return s.prev; }
+};
+template <> struct Cst<float> {
+  __device__ static float omega(const RepDev& d) { return d.omega_f; }
+  __device__ static float g(const RepDev& d, int a) { return d.g_f[a]; }
+  __device__ static float r(const RepDev& d) { return d.r_f; }
+  __device__ static float cos_a(const RepDev& d) { return d.cos_f; }
+  __device__ static float sin_a(const RepDev& d) { return d.sin_f; }
+  __device__ static const float* shift(const StepInfo& s) { return s.shift_f; }
+  __device__ static const float* prev(const StepInfo& s) { return s.prev_f; }
 };
 
 // packed home cell: 2D x | y << 16 ; 3D x | y << 10 | z << 21
@@ -224,6 +250,18 @@ __device__ __forceinline__ void for_each_item(const Item* __restrict__ bmap, int
     }
     body(bm);
   }
+}
+
+// Resident-grid size for a kernel; LBMPCD_GRID_BLOCKS_PER_ITEM=1 in the
+// environment switches every kernel to one block per work item instead
+// (for measurement).
+inline int grid_cap(int resident) {
+  static int mode = -1;
+  if (mode < 0) {
+    const char* e = getenv("LBMPCD_GRID_BLOCKS_PER_ITEM");
+    mode = (e && e[0] == '1') ? 1 : 0;
+  }
+  return mode ? (1 << 30) : resident;
 }
 
 // Blocks to launch for nwork items: enough to fill every SM at the kernel's

@@ -9,6 +9,10 @@ namespace lbm {
 // precision codes (match LBMPCD_FP64 / FP32 / FP16DEV)
 enum { P_FP64 = 0, P_FP32 = 1, P_FP16 = 2 };
 
+constexpr int PPT = 4;                       // particles per thread in particle_pass
+constexpr int PP_ITEM = 256 * PPT;           // particles per work item
+constexpr int CPT = 4;                       // collision cells per thread in cell_pass
+
 struct Launch {
   const RepDev* reps;     // device descriptor table
   int nrep;
@@ -18,7 +22,7 @@ struct Launch {
 
 // a1: fused pull stream + BGK collide (+ Guo force, bounce-back walls).
 // vec = nodes per thread (lb_vector_width); one vec for all replicas of a handle.
-int lb_vector_width(int prec, int nx);
+int lb_vector_width(int q, int prec, int nx);
 cudaError_t launch_lb(int q, int prec, int vec, const Launch& L, const int4* bmap, int nblocks, int k);
 
 // prep: per-step records (shift, pending flag) for kcount steps.

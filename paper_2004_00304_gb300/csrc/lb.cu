@@ -33,6 +33,24 @@ template <> struct Row<float, 4> {
     *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
   }
 };
+template <> struct Row<float, 2> {
+  __device__ static void ld(const float* p, float* o, float) {
+    const float2 t = *reinterpret_cast<const float2*>(p);
+    o[0] = t.x; o[1] = t.y;
+  }
+  __device__ static void st(float* p, const float* v, float) {
+    *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+  }
+};
+template <> struct Row<__half, 2> {
+  __device__ static void ld(const __half* p, float* o, float inv) {
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(p));
+    o[0] = a.x * inv; o[1] = a.y * inv;
+  }
+  __device__ static void st(__half* p, const float* v, float sc) {
+    *reinterpret_cast<__half2*>(p) = __floats2half2_rn(v[0] * sc, v[1] * sc);
+  }
+};
 template <> struct Row<__half, 4> {
   __device__ static void ld(const __half* p, float* o, float inv) {
     const uint2 t = *reinterpret_cast<const uint2*>(p);
@@ -72,48 +90,59 @@ __device__ __forceinline__ void lb_row(const RepDev& rd, const StepInfo& st, con
   const int row = nx * (y + ny * z);
   const float inv = rd.fp16_inv, scale = rd.fp16_scale;
 
-  R d[Q][V];
+  // phase 1: every load of the thread (Q aligned rows plus the scalar edge
+  // values at warp boundaries), branch-free so that all of them are in flight
+  // together: inactive tail lanes read a clamped, valid position and discard it,
+  // bounce-back rows are selected, not branched to.
+  const int xa = active ? x0 : (tpr - 1) * V;
+  const int xprev = xa == 0 ? nx - 1 : xa - 1;
+  const int xnext = xa + V >= nx ? 0 : xa + V;
+  R d[Q][V], edge[Q];
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const int sy = y - L::cy(i);
-    if (sy == 0 || sy == ny - 1) {           // half-way bounce-back: f*_{-i} of this node
-      if (active) Row<S, V>::ld(src + L::opp(i) * N + row + x0, d[i], inv);
-      continue;
-    }
+    const bool bounce = (sy == 0) | (sy == ny - 1);
     int sz = z - L::cz(i);
     sz = sz < 0 ? sz + nz : (sz >= nz ? sz - nz : sz);
     const S* srow_i = src + i * N + nx * (sy + ny * sz);
-    R a[V];
-#pragma unroll
-    for (int v = 0; v < V; ++v) a[v] = R(0);
-    if (active) Row<S, V>::ld(srow_i + x0, a, inv);
-    if (L::cx(i) == 0) {
-#pragma unroll
-      for (int v = 0; v < V; ++v) d[i][v] = a[v];
-    } else if (V == 1) {
-      int sx = x0 - L::cx(i);
+    const S* rp = bounce ? src + L::opp(i) * N + row : srow_i;
+    if (V == 1) {
+      int sx = xa - L::cx(i);
       sx = sx < 0 ? sx + nx : (sx >= nx ? sx - nx : sx);
-      if (active) d[i][0] = Store<S>::ld(srow_i + sx, inv);
-    } else if (L::cx(i) > 0) {               // source x - 1: previous lane's last node
-      R prev = __shfl_up_sync(0xFFFFFFFFu, a[V - 1], 1);
-      if (active && lane == 0) prev = Store<S>::ld(srow_i + (x0 == 0 ? nx - 1 : x0 - 1), inv);
-      d[i][0] = prev;
+      d[i][0] = Store<S>::ld(rp + (bounce ? xa : sx), inv);
+    } else {
+      Row<S, V>::ld(rp + xa, d[i], inv);
+    }
+    edge[i] = R(0);
+    if (V > 1 && L::cx(i) > 0) edge[i] = Store<S>::ld(rp + xprev, inv);
+    if (V > 1 && L::cx(i) < 0) edge[i] = Store<S>::ld(rp + xnext, inv);
+  }
+  // phase 2: shift the rows with cx != 0 by one node through the neighbour lanes
+  if (V > 1) {
 #pragma unroll
-      for (int v = 1; v < V; ++v) d[i][v] = a[v - 1];
-    } else {                                 // source x + 1: next lane's first node
-      R next = __shfl_down_sync(0xFFFFFFFFu, a[0], 1);
-      if (active && (lane == 31 || tx + 1 >= tpr)) next = Store<S>::ld(srow_i + (x0 + V >= nx ? 0 : x0 + V), inv);
+    for (int i = 0; i < Q; ++i) {
+      const int sy = y - L::cy(i);
+      if (L::cx(i) == 0 || sy == 0 || sy == ny - 1) continue;
+      if (L::cx(i) > 0) {                    // source x - 1: previous lane's last node
+        R prev = __shfl_up_sync(0xFFFFFFFFu, d[i][V - 1], 1);
+        if (lane == 0) prev = edge[i];
 #pragma unroll
-      for (int v = 0; v < V - 1; ++v) d[i][v] = a[v + 1];
-      d[i][V - 1] = next;
+        for (int v = V - 1; v > 0; --v) d[i][v] = d[i][v - 1];
+        d[i][0] = prev;
+      } else {                               // source x + 1: next lane's first node
+        R next = __shfl_down_sync(0xFFFFFFFFu, d[i][0], 1);
+        if (lane == 31 || tx + 1 >= tpr) next = edge[i];
+#pragma unroll
+        for (int v = 0; v < V - 1; ++v) d[i][v] = d[i][v + 1];
+        d[i][V - 1] = next;
+      }
     }
   }
   if (!active) return;
 
-  const R om = (R)rd.omega, om1 = R(1) - om, cf = R(1) - R(0.5) * om;
-  const R gx = (R)rd.g[0], gy = (R)rd.g[1], gz = (R)rd.g[2];
-  R out[Q][V];
-  R mr[V], mu[3][V];
+  const R om = Cst<R>::omega(rd), om1 = R(1) - om, cf = R(1) - R(0.5) * om;
+  const R gx = Cst<R>::g(rd, 0), gy = Cst<R>::g(rd, 1), gz = Cst<R>::g(rd, 2);
+  R mr[V], mu[3][V];   // post-collision values overwrite d in place
 #pragma unroll
   for (int v = 0; v < V; ++v) {
     R drho = 0, jx = 0, jy = 0, jz = 0;
@@ -135,7 +164,7 @@ __device__ __forceinline__ void lb_row(const RepDev& rd, const StepInfo& st, con
     //   O = 3 (om rho cu + cf cF)
     const R K0 = om * drho - R(1.5) * om * rho * uu - R(3) * cf * uF;
     const R A = R(4.5) * om * rho, B = om * rho, C9 = R(9) * cf;
-    out[0][v] = om1 * d[0][v] + (R)L::w(0) * K0;
+    d[0][v] = om1 * d[0][v] + (R)L::w(0) * K0;
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
       const int o = L::opp(i);
@@ -147,13 +176,15 @@ __device__ __forceinline__ void lb_row(const RepDev& rd, const StepInfo& st, con
       const R Od = R(3) * (B * cu + cfF);
       const R w = (R)L::w(i);
       const R pe = w * E, po = w * Od;
-      out[i][v] = om1 * d[i][v] + (pe + po);
-      out[o][v] = om1 * d[o][v] + (pe - po);
+      const R fi = om1 * d[i][v] + (pe + po);
+      const R fo = om1 * d[o][v] + (pe - po);
+      d[i][v] = fi;
+      d[o][v] = fo;
     }
     mr[v] = rho; mu[0][v] = ux; mu[1][v] = uy; mu[2][v] = uz;
   }
 #pragma unroll
-  for (int i = 0; i < Q; ++i) Row<S, V>::st(dst + i * N + row + x0, out[i], scale);
+  for (int i = 0; i < Q; ++i) Row<S, V>::st(dst + i * N + row + x0, d[i], scale);
 
   // rho, u: every node on request; otherwise the columns the coupling reads
   // (x0-1 .. x0+cw and x1-cw-1 .. x1, periodic in x).
@@ -190,12 +221,18 @@ __global__ void __launch_bounds__(128) lb_pull(const RepDev* __restrict__ reps, 
 template <int Q, typename S, int V>
 static cudaError_t go_lb(const Launch& L, const int4* bmap, int nwork, int k) {
   if (nwork == 0) return cudaSuccess;
-  static const int g = grid_for(lb_pull<Q, S, V>, 128, 1 << 30);
+  static const int g = grid_cap(grid_for(lb_pull<Q, S, V>, 128, 1 << 30));
   lb_pull<Q, S, V><<<g < nwork ? g : nwork, 128, 0, L.stream>>>(L.reps, bmap, nwork, L.si, k, L.nrep);
   return cudaGetLastError();
 }
 
-int lb_vector_width(int prec, int nx) { return (prec != P_FP64 && nx % 4 == 0) ? 4 : 1; }
+// Nodes per thread: 4 for D2Q9 rows, 2 for D3Q19 rows (19 populations per
+// node), 1 in binary64 or when the row length is not a multiple.
+int lb_vector_width(int q, int prec, int nx) {
+  if (prec == P_FP64) return 1;
+  const int v = q == 9 ? 4 : 2;
+  return nx % v == 0 ? v : 1;
+}
 
 cudaError_t launch_lb(int q, int prec, int vec, const Launch& L, const int4* bmap, int nblocks, int k) {
   if (q == 9) {
@@ -204,8 +241,8 @@ cudaError_t launch_lb(int q, int prec, int vec, const Launch& L, const int4* bma
     return vec == 4 ? go_lb<9, __half, 4>(L, bmap, nblocks, k) : go_lb<9, __half, 1>(L, bmap, nblocks, k);
   }
   if (prec == P_FP64) return go_lb<19, double, 1>(L, bmap, nblocks, k);
-  if (prec == P_FP32) return vec == 4 ? go_lb<19, float, 4>(L, bmap, nblocks, k) : go_lb<19, float, 1>(L, bmap, nblocks, k);
-  return vec == 4 ? go_lb<19, __half, 4>(L, bmap, nblocks, k) : go_lb<19, __half, 1>(L, bmap, nblocks, k);
+  if (prec == P_FP32) return vec == 2 ? go_lb<19, float, 2>(L, bmap, nblocks, k) : go_lb<19, float, 1>(L, bmap, nblocks, k);
+  return vec == 2 ? go_lb<19, __half, 2>(L, bmap, nblocks, k) : go_lb<19, __half, 1>(L, bmap, nblocks, k);
 }
 
 // ---- copy-out / copy-in of populations and LB-side diagnostics ------------

@@ -135,7 +135,7 @@ extern "C" int lbmpcd_create(const lbmpcd_params* params, int n_replicas, void* 
   h->pending.assign(n_replicas, 0);
   const size_t ss = store_size(h->prec), rs = real_size(h->prec);
   h->lbvec = 4;
-  for (int r = 0; r < n_replicas; ++r) h->lbvec = std::min(h->lbvec, lb_vector_width(h->prec, params[r].nx));
+  for (int r = 0; r < n_replicas; ++r) h->lbvec = std::min(h->lbvec, lb_vector_width(h->q, h->prec, params[r].nx));
   for (int r = 0; r < n_replicas; ++r) {
     const lbmpcd_params& p = params[r];
     RepDev& d = h->rd[r];
@@ -151,6 +151,9 @@ extern "C" int lbmpcd_create(const lbmpcd_params* params, int n_replicas, void* 
     d.feedback = p.feedback; d.window = p.window;
     d.kT = p.kT; d.mass = p.mass; d.sig = sqrt(p.kT / p.mass);
     d.alpha = p.alpha; d.cos_a = cos(p.alpha); d.sin_a = sin(p.alpha);
+    d.omega_f = (float)d.omega; d.r_f = (float)p.refine;
+    d.cos_f = (float)d.cos_a; d.sin_f = (float)d.sin_a;
+    for (int a = 0; a < 3; ++a) d.g_f[a] = (float)d.g[a];
     d.key0 = (uint32_t)(p.seed & 0xFFFFFFFFu); d.key1 = (uint32_t)(p.seed >> 32); d.rep = (uint32_t)r;
     std::vector<void*>& L = h->allocs;
     e = dalloc(L, &d.f[0], h->q * d.nnode * ss);
@@ -183,8 +186,8 @@ extern "C" int lbmpcd_create(const lbmpcd_params* params, int n_replicas, void* 
 }
 
 // Block maps, one work item per entry, each replica's items contiguous:
-// LB (replica, tile, y, z); particles / sort (replica, block of 256
-// particles); cells (replica, block of 256 cells, or -1-b for block b of the
+// LB (replica, tile, y, z); particles / sort (replica, block of PP_ITEM
+// particles); cells (replica, block of 256 CPT cells, or -1-b for block b of 256
 // inner-buffer nodes); sort tiles (replica, tile of SORT_TILE home cells).
 template <typename T>
 static int upload_map(lbmpcd* h, T** dst, int* cnt, const std::vector<T>& src) {
@@ -213,7 +216,7 @@ static int build_maps(lbmpcd* h) {
       for (int y = 1; y < d.ny - 1; ++y)
         for (int t = 0; t < ntx; ++t) lb.push_back(make_int4(r, t, y, z));
     if (!d.has_region) continue;
-    const long long npb = (d.np + 255) / 256, ncb = (d.ncell + 255) / 256, nbb = (d.nbuf + 255) / 256;
+    const long long npb = (d.np + PP_ITEM - 1) / PP_ITEM, ncb = (d.ncell + 256 * CPT - 1) / (256 * CPT), nbb = (d.nbuf + 255) / 256;
     for (long long b = 0; b < npb; ++b) pp.push_back(make_int2(r, (int)b));
     for (long long b = 0; b < ncb; ++b) cc.push_back(make_int2(r, (int)b));
     for (long long b = 0; b < nbb; ++b) cc.push_back(make_int2(r, (int)(-1 - b)));

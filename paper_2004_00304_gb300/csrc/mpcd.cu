@@ -75,6 +75,7 @@ __global__ void prep_steps(const RepDev* __restrict__ reps, int nrep, int dim, i
       s.prev[1] = unit24(p.y);
       s.prev[2] = dim == 3 ? unit24(p.z) : 0.0;
     }
+    for (int a = 0; a < 3; ++a) { s.shift_f[a] = (float)s.shift[a]; s.prev_f[a] = (float)s.prev[a]; }
     si[idx] = s;
   }
   __syncthreads();
@@ -98,13 +99,13 @@ cudaError_t launch_prep(int dim, const Launch& L, StepInfo* si, int kcount, int 
 // wrapped in x and z.  id = cx + Wx (cy + (Hy+1) cz).
 template <int D, typename R>
 __device__ __forceinline__ uint32_t collision_cell(const RepDev& rd, int X, int Y, int Z, const R* o,
-                                                   const double* s) {
-  int cx = X + (xadd(o[0], (R)s[0]) >= R(1) ? 1 : 0);
+                                                   const R* s) {
+  int cx = X + (xadd(o[0], s[0]) >= R(1) ? 1 : 0);
   if (cx >= rd.Wx) cx -= rd.Wx;
-  const int cy = Y + (xadd(o[1], (R)s[1]) >= R(1) ? 1 : 0);
+  const int cy = Y + (xadd(o[1], s[1]) >= R(1) ? 1 : 0);
   int cz = 0;
   if (D == 3) {
-    cz = Z + (xadd(o[2], (R)s[2]) >= R(1) ? 1 : 0);
+    cz = Z + (xadd(o[2], s[2]) >= R(1) ? 1 : 0);
     if (cz >= rd.Wz) cz -= rd.Wz;
   }
   return (uint32_t)(cx + rd.Wx * (cy + (rd.Hy + 1) * cz));
@@ -115,7 +116,7 @@ __device__ __forceinline__ uint32_t collision_cell(const RepDev& rd, int X, int 
 template <int D, typename R>
 __device__ __forceinline__ void rotate(const RepDev& rd, uint32_t c, R* v) {
   using T4 = typename Vec4<R>::T;
-  const R ca = (R)rd.cos_a;
+  const R ca = Cst<R>::cos_a(rd);
   const T4* tab = (const T4*)rd.tab;
   if (D == 2) {
     const T4 t = tab[c];
@@ -123,7 +124,7 @@ __device__ __forceinline__ void rotate(const RepDev& rd, uint32_t c, R* v) {
     v[0] = t.x + (ca * wx - t.z * wy);
     v[1] = t.y + (t.z * wx + ca * wy);
   } else {
-    const R sa = (R)rd.sin_a;
+    const R sa = Cst<R>::sin_a(rd);
     const T4 t0 = tab[2 * (size_t)c], t1 = tab[2 * (size_t)c + 1];
     const R vc[3] = {t0.x, t0.y, t0.z}, n[3] = {t1.x, t1.y, t1.z};
     const R w[3] = {v[0] - vc[0], v[1] - vc[1], v[2] - vc[2]};
@@ -175,10 +176,10 @@ __device__ void u_fine(const RepDev& rd, int X, int Y, int Z, double* out) {
 // the step; x (and z) wrap periodically in the region.
 template <int D, typename R>
 __device__ __forceinline__ void stream(const RepDev& rd, int& X, int& Y, int& Z, R* o, R* v) {
-  v[0] = xadd(v[0], (R)rd.g[0]);
-  v[1] = xadd(v[1], (R)rd.g[1]);
-  if (D == 3) v[2] = xadd(v[2], (R)rd.g[2]);
-  const R rr = (R)rd.r;
+  v[0] = xadd(v[0], Cst<R>::g(rd, 0));
+  v[1] = xadd(v[1], Cst<R>::g(rd, 1));
+  if (D == 3) v[2] = xadd(v[2], Cst<R>::g(rd, 2));
+  const R rr = Cst<R>::r(rd);
   const R dx = xmul(v[0], rr), dy = xmul(v[1], rr), dz = (D == 3) ? xmul(v[2], rr) : R(0);
   const R ty = xadd(o[1], dy);
   const int ky = (int)floor(ty);
@@ -222,81 +223,138 @@ __device__ __forceinline__ void stream(const RepDev& rd, int& X, int& Y, int& Z,
   }
 }
 
+// One work item = PP_ITEM consecutive particles; thread t handles particles
+// t, t + 256, t + 512, t + 768 of the item, so that every round of the warp
+// covers 32 consecutive particles.  All state loads of the four particles are
+// issued first, then their four cell-table loads, before any arithmetic:
+// each thread keeps ~100 bytes in flight instead of one dependent chain.
 template <int D, typename R>
 __device__ __forceinline__ void particle_item(const RepDev& rd, const StepInfo& st, const int2 bm, R (*sv)[256]) {
-  const long long j = (long long)bm.y * blockDim.x + threadIdx.x;
-  const bool active = j < rd.np;
-  int X = 0, Y = 0, Z = 0;
-  R o[3] = {R(0), R(0), R(0)}, v[3] = {R(0), R(0), R(0)};
-  uint32_t cid = 0xFFFFFFFFu;
-  if (active) {
-    const bool alt = st.src_alt;
-    HomePack<D>::unpack((alt ? rd.home_alt : rd.home)[j], X, Y, Z);
+  using T4 = typename Vec4<R>::T;
+  const long long j0 = (long long)bm.y * PP_ITEM + threadIdx.x;
+  const bool alt = st.src_alt;
+  const uint32_t* __restrict__ hsrc = alt ? rd.home_alt : rd.home;
+  int X[PPT], Y[PPT], Z[PPT];
+  R o[PPT][3], v[PPT][3];
+  bool act[PPT];
+  // branch-free loads: a lane past the end reads the last particle and discards it
+  const R* offs[3];
+  const R* vels[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    offs[a] = (const R*)(alt ? rd.off_alt[a] : rd.off[a]);
+    vels[a] = (const R*)(alt ? rd.vel_alt[a] : rd.vel[a]);
+  }
+#pragma unroll
+  for (int p = 0; p < PPT; ++p) {
+    const long long j = j0 + 256 * p;
+    act[p] = j < rd.np;
+    const long long jl = act[p] ? j : rd.np - 1;
+    HomePack<D>::unpack(hsrc[jl], X[p], Y[p], Z[p]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) { o[p][a] = R(0); v[p][a] = R(0); }
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-      o[a] = ((const R*)(alt ? rd.off_alt[a] : rd.off[a]))[j];
-      v[a] = ((const R*)(alt ? rd.vel_alt[a] : rd.vel[a]))[j];
+      o[p][a] = offs[a][jl];
+      v[p][a] = vels[a][jl];
     }
-    // a7 of step n-1
-    if (st.pending) rotate<D, R>(rd, collision_cell<D, R>(rd, X, Y, Z, o, st.prev), v);
+  }
+  // a7 of step n-1: cell-table loads for all four, then the rotations
+  if (st.pending) {
+    const T4* tab = (const T4*)rd.tab;
+    T4 t0[PPT], t1[PPT];
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) {
+      const uint32_t c = collision_cell<D, R>(rd, X[p], Y[p], Z[p], o[p], Cst<R>::prev(st));
+      if (D == 2) t0[p] = tab[c];
+      else { t0[p] = tab[2 * (size_t)c]; t1[p] = tab[2 * (size_t)c + 1]; }
+    }
+    const R ca = Cst<R>::cos_a(rd), sa = Cst<R>::sin_a(rd);
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) {
+      if (D == 2) {
+        const T4 t = t0[p];
+        const R wx = v[p][0] - t.x, wy = v[p][1] - t.y;
+        v[p][0] = t.x + (ca * wx - t.z * wy);
+        v[p][1] = t.y + (t.z * wx + ca * wy);
+      } else {
+        const R vc[3] = {t0[p].x, t0[p].y, t0[p].z}, n[3] = {t1[p].x, t1[p].y, t1[p].z};
+        const R w[3] = {v[p][0] - vc[0], v[p][1] - vc[1], v[p][2] - vc[2]};
+        const R cr[3] = {n[1] * w[2] - n[2] * w[1], n[2] * w[0] - n[0] * w[2], n[0] * w[1] - n[1] * w[0]};
+        const R nw = n[0] * w[0] + n[1] * w[1] + n[2] * w[2];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) v[p][a] = vc[a] + (w[a] * ca + cr[a] * sa + n[a] * nw * (R(1) - ca));
+      }
+    }
+  }
+  uint32_t cid[PPT];
+#pragma unroll
+  for (int p = 0; p < PPT; ++p) {
+    const long long j = j0 + 256 * p;
+    cid[p] = 0xFFFFFFFFu;
+    if (!act[p]) continue;
     // a2 + a3: Maxwellian redraw in the outer buffer columns
-    if (X < rd.xo_lo || X >= rd.xo_hi) {
+    if (X[p] < rd.xo_lo || X[p] >= rd.xo_hi) {
       double uf[3] = {0, 0, 0};
-      u_fine<D, R>(rd, X, Y, Z, uf);
+      u_fine<D, R>(rd, X[p], Y[p], Z[p], uf);
       const uint4 w = philox((alt ? rd.pid_alt : rd.pid)[j], st.n, rd.rep, TAG_RESAMPLE, rd.key0, rd.key1);
       double z0, z1, z2, z3;
       normal_pair(w.x, w.y, z0, z1);
       normal_pair(w.z, w.w, z2, z3);
-      v[0] = (R)(uf[0] + rd.sig * z0);
-      v[1] = (R)(uf[1] + rd.sig * z1);
-      if (D == 3) v[2] = (R)(uf[2] + rd.sig * z2);
+      v[p][0] = (R)(uf[0] + rd.sig * z0);
+      v[p][1] = (R)(uf[1] + rd.sig * z1);
+      if (D == 3) v[p][2] = (R)(uf[2] + rd.sig * z2);
     }
     if (alt) rd.pid[j] = rd.pid_alt[j];
     // a4
-    stream<D, R>(rd, X, Y, Z, o, v);
+    stream<D, R>(rd, X[p], Y[p], Z[p], o[p], v[p]);
     // a6: inner-buffer sample (unshifted cells), binary64 atomics
-    const bool left = X >= rd.xi_lo0 && X < rd.xi_hi0, right = X >= rd.xi_lo1 && X < rd.xi_hi1;
+    const bool left = X[p] >= rd.xi_lo0 && X[p] < rd.xi_hi0, right = X[p] >= rd.xi_lo1 && X[p] < rd.xi_hi1;
     if (left || right) {
-      const int xn = X / rd.r, wcols = rd.x1 - rd.x0;
+      const int xn = X[p] / rd.r, wcols = rd.x1 - rd.x0;
       const int col = left ? xn - rd.n_out : wcols - 1 - rd.n_out - xn;
-      const int zl = (D == 3) ? Z / rd.r : 0;
-      const long long b = (((long long)(right ? 1 : 0) * rd.n_in + col) * rd.nz + zl) * (rd.ny - 2) + Y / rd.r;
+      const int zl = (D == 3) ? Z[p] / rd.r : 0;
+      const long long b = (((long long)(right ? 1 : 0) * rd.n_in + col) * rd.nz + zl) * (rd.ny - 2) + Y[p] / rd.r;
       double* fr = rd.frame + 4 * b;
       atomicAdd(fr, rd.mass);
 #pragma unroll
-      for (int a = 0; a < D; ++a) atomicAdd(fr + 1 + a, rd.mass * (double)v[a]);
+      for (int a = 0; a < D; ++a) atomicAdd(fr + 1 + a, rd.mass * (double)v[p][a]);
     }
     // a5: binning under this step's shift
-    cid = collision_cell<D, R>(rd, X, Y, Z, o, st.shift);
-    rd.home[j] = HomePack<D>::pack(X, Y, Z);
+    cid[p] = collision_cell<D, R>(rd, X[p], Y[p], Z[p], o[p], Cst<R>::shift(st));
+    rd.home[j] = HomePack<D>::pack(X[p], Y[p], Z[p]);
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-      ((R*)rd.off[a])[j] = o[a];
-      ((R*)rd.vel[a])[j] = v[a];
+      ((R*)rd.off[a])[j] = o[p][a];
+      ((R*)rd.vel[a])[j] = v[p][a];
     }
   }
-  // warp-aggregated reduction: lanes sharing a collision cell are summed by
-  // their lowest lane, which issues one atomic per accumulator.
-  const unsigned grp = __match_any_sync(0xFFFFFFFFu, cid);
+  // warp-aggregated reduction, one round per particle slot: lanes sharing a
+  // collision cell are summed by their lowest lane, which issues one atomic
+  // per accumulator.
   const int lane = threadIdx.x & 31, wbase = threadIdx.x & ~31;
-  __syncwarp();
 #pragma unroll
-  for (int a = 0; a < D; ++a) sv[a][threadIdx.x] = v[a];
-  __syncwarp();
-  if (active && lane == __ffs(grp) - 1) {
-    R acc[D];
+  for (int p = 0; p < PPT; ++p) {
+    const unsigned grp = __match_any_sync(0xFFFFFFFFu, cid[p]);
+    __syncwarp();
 #pragma unroll
-    for (int a = 0; a < D; ++a) acc[a] = R(0);
-    unsigned m = grp;
-    while (m) {
-      const int l = __ffs(m) - 1;
-      m &= m - 1;
+    for (int a = 0; a < D; ++a) sv[a][threadIdx.x] = v[p][a];
+    __syncwarp();
+    if (act[p] && lane == __ffs(grp) - 1) {
+      R acc[D];
 #pragma unroll
-      for (int a = 0; a < D; ++a) acc[a] += sv[a][wbase + l];
+      for (int a = 0; a < D; ++a) acc[a] = R(0);
+      unsigned m = grp;
+      while (m) {
+        const int l = __ffs(m) - 1;
+        m &= m - 1;
+#pragma unroll
+        for (int a = 0; a < D; ++a) acc[a] += sv[a][wbase + l];
+      }
+      atomicAdd(rd.acc_n + cid[p], (uint32_t)__popc(grp));
+#pragma unroll
+      for (int a = 0; a < D; ++a) atomicAdd((R*)rd.acc_v[a] + cid[p], acc[a]);
     }
-    atomicAdd(rd.acc_n + cid, (uint32_t)__popc(grp));
-#pragma unroll
-    for (int a = 0; a < D; ++a) atomicAdd((R*)rd.acc_v[a] + cid, acc[a]);
   }
 }
 
@@ -311,7 +369,7 @@ __global__ void __launch_bounds__(256) particle_pass(const RepDev* __restrict__ 
 
 template <int D, typename R>
 static void go_particles(const Launch& L, const int2* bmap, int nwork, int k) {
-  static const int g = grid_for(particle_pass<D, R>, 256, 1 << 30);
+  static const int g = grid_cap(grid_for(particle_pass<D, R>, 256, 1 << 30));
   particle_pass<D, R><<<g < nwork ? g : nwork, 256, 0, L.stream>>>(L.reps, bmap, nwork, L.si, k, L.nrep);
 }
 
@@ -336,63 +394,79 @@ __device__ __forceinline__ void cell_item(const RepDev& rd, const StepInfo& st, 
   using L = Lattice<Q>;
   constexpr int D = L::D;
   if (bm.y >= 0) {
-    const long long c = (long long)bm.y * blockDim.x + threadIdx.x;
-    if (c >= rd.ncell) return;
-    const uint32_t n = rd.acc_n[c];
-    R vc[3] = {R(0), R(0), R(0)}, rt[3] = {R(0), R(0), R(0)};
-    if (n > 0) {
-      const int cy = (int)((c / rd.Wx) % (rd.Hy + 1));
-      const bool cut = (cy == 0 || cy == rd.Hy) && st.shift[1] > 0.0;
-      if (cut && (int)n < rd.ppc) {
-        // Lamura-type wall: ppc - n virtual particles at rest, summed momentum
-        // drawn from N(0, (ppc - n) m kT) per component.
-        const int nv = rd.ppc - (int)n;
-        const uint4 w = philox((uint32_t)c, st.n, rd.rep, TAG_VIRT, rd.key0, rd.key1);
-        double z[4];
-        normal_pair(w.x, w.y, z[0], z[1]);
-        normal_pair(w.z, w.w, z[2], z[3]);
-        const double sd = sqrt((double)nv * rd.kT / rd.mass);
+    // CPT cells per thread (c0 + 256 p): all accumulator loads first
+    const long long c0 = (long long)bm.y * (256 * CPT) + threadIdx.x;
+    uint32_t nn[CPT];
+    R V[CPT][3];
 #pragma unroll
-        for (int a = 0; a < D; ++a)
-          vc[a] = (R)(((double)((const R*)rd.acc_v[a])[c] + sd * z[a]) / (double)(rd.ppc));
-      } else {
+    for (int p = 0; p < CPT; ++p) {
+      const long long c = c0 + 256 * p;
+      const long long cl = c < rd.ncell ? c : rd.ncell - 1;
+      nn[p] = rd.acc_n[cl];
 #pragma unroll
-        for (int a = 0; a < D; ++a) vc[a] = ((const R*)rd.acc_v[a])[c] / (R)n;
-      }
-      if (D == 2) {
-        const uint4 w = philox((uint32_t)c, st.n, rd.rep, TAG_SIGN, rd.key0, rd.key1);
-        rt[0] = (w.x >> 31) ? (R)rd.sin_a : -(R)rd.sin_a;
-      } else {
-        const uint4 w = philox((uint32_t)c, st.n, rd.rep, TAG_AXIS, rd.key0, rd.key1);
-        if (sizeof(R) == 8) {
-          const double zc = 2.0 * unit24(w.x) - 1.0;
-          double sp, cp;
-          sincospi(2.0 * unit24(w.y), &sp, &cp);
-          const double rh = sqrt(1.0 - zc * zc);
-          rt[0] = (R)(rh * cp); rt[1] = (R)(rh * sp); rt[2] = (R)zc;
+      for (int a = 0; a < 3; ++a) V[p][a] = a < D ? ((const R*)rd.acc_v[a])[cl] : R(0);
+    }
+#pragma unroll
+    for (int p = 0; p < CPT; ++p) {
+      const long long c = c0 + 256 * p;
+      if (c >= rd.ncell) break;
+      const uint32_t n = nn[p];
+      R vc[3] = {R(0), R(0), R(0)}, rt[3] = {R(0), R(0), R(0)};
+      if (n > 0) {
+        const uint32_t ci = (uint32_t)c, row = ci / (uint32_t)rd.Wx;
+        const uint32_t cy = D == 2 ? row : row % (uint32_t)(rd.Hy + 1);
+        const bool cut = (cy == 0 || cy == (uint32_t)rd.Hy) && st.shift_f[1] > 0.0f;
+        if (cut && (int)n < rd.ppc) {
+          // Lamura-type wall: ppc - n virtual particles at rest, summed momentum
+          // drawn from N(0, (ppc - n) m kT) per component.
+          const int nv = rd.ppc - (int)n;
+          const uint4 w = philox((uint32_t)c, st.n, rd.rep, TAG_VIRT, rd.key0, rd.key1);
+          double z[4];
+          normal_pair(w.x, w.y, z[0], z[1]);
+          normal_pair(w.z, w.w, z[2], z[3]);
+          const double sd = sqrt((double)nv * rd.kT / rd.mass);
+#pragma unroll
+          for (int a = 0; a < D; ++a) vc[a] = (R)(((double)V[p][a] + sd * z[a]) / (double)(rd.ppc));
         } else {
-          const float zc = 2.0f * unit24f(w.x) - 1.0f;
-          float sp, cp;
-          sincospif(2.0f * unit24f(w.y), &sp, &cp);
-          const float rh = sqrtf(1.0f - zc * zc);
-          rt[0] = (R)(rh * cp); rt[1] = (R)(rh * sp); rt[2] = (R)zc;
+          const R inv_n = R(1) / (R)n;
+#pragma unroll
+          for (int a = 0; a < D; ++a) vc[a] = V[p][a] * inv_n;
+        }
+        if (D == 2) {
+          const uint4 w = philox((uint32_t)c, st.n, rd.rep, TAG_SIGN, rd.key0, rd.key1);
+          rt[0] = (w.x >> 31) ? Cst<R>::sin_a(rd) : -Cst<R>::sin_a(rd);
+        } else {
+          const uint4 w = philox((uint32_t)c, st.n, rd.rep, TAG_AXIS, rd.key0, rd.key1);
+          if (sizeof(R) == 8) {
+            const double zc = 2.0 * unit24(w.x) - 1.0;
+            double sp, cp;
+            sincospi(2.0 * unit24(w.y), &sp, &cp);
+            const double rh = sqrt(1.0 - zc * zc);
+            rt[0] = (R)(rh * cp); rt[1] = (R)(rh * sp); rt[2] = (R)zc;
+          } else {
+            const float zc = 2.0f * unit24f(w.x) - 1.0f;
+            float sp, cp;
+            sincospif(2.0f * unit24f(w.y), &sp, &cp);
+            const float rh = sqrtf(1.0f - zc * zc);
+            rt[0] = (R)(rh * cp); rt[1] = (R)(rh * sp); rt[2] = (R)zc;
+          }
         }
       }
-    }
-    T4* tab = (T4*)rd.tab;
-    if (D == 2) {
-      T4 t; t.x = vc[0]; t.y = vc[1]; t.z = rt[0]; t.w = (R)n;
-      tab[c] = t;
-    } else {
-      T4 t0, t1;
-      t0.x = vc[0]; t0.y = vc[1]; t0.z = vc[2]; t0.w = (R)n;
-      t1.x = rt[0]; t1.y = rt[1]; t1.z = rt[2]; t1.w = R(0);
-      tab[2 * c] = t0;
-      tab[2 * c + 1] = t1;
-    }
+      T4* tab = (T4*)rd.tab;
+      if (D == 2) {
+        T4 t; t.x = vc[0]; t.y = vc[1]; t.z = rt[0]; t.w = (R)n;
+        tab[c] = t;
+      } else {
+        T4 t0, t1;
+        t0.x = vc[0]; t0.y = vc[1]; t0.z = vc[2]; t0.w = (R)n;
+        t1.x = rt[0]; t1.y = rt[1]; t1.z = rt[2]; t1.w = R(0);
+        tab[2 * c] = t0;
+        tab[2 * c + 1] = t1;
+      }
 #pragma unroll
-    for (int a = 0; a < D; ++a) ((R*)rd.acc_v[a])[c] = R(0);
-    rd.acc_n[c] = 0u;
+      for (int a = 0; a < D; ++a) ((R*)rd.acc_v[a])[c] = R(0);
+      rd.acc_n[c] = 0u;
+    }
     return;
   }
   // a8: one thread per inner-buffer LB node
@@ -447,7 +521,7 @@ __global__ void __launch_bounds__(256) cell_pass(const RepDev* __restrict__ reps
 
 template <int Q, typename S>
 static void go_cells(const Launch& L, const int2* bmap, int nwork, int k) {
-  static const int g = grid_for(cell_pass<Q, S>, 256, 1 << 30);
+  static const int g = grid_cap(grid_for(cell_pass<Q, S>, 256, 1 << 30));
   cell_pass<Q, S><<<g < nwork ? g : nwork, 256, 0, L.stream>>>(L.reps, bmap, nwork, L.si, k, L.nrep);
 }
 
@@ -474,7 +548,7 @@ __global__ void flush_collision(const RepDev* __restrict__ rdp, double s0, doubl
   const RepDev& rd = *rdp;
   const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (j >= rd.np) return;
-  const double s[3] = {s0, s1, s2};
+  const R s[3] = {(R)s0, (R)s1, (R)s2};     // shifts are exact in binary32
   int X, Y, Z;
   HomePack<D>::unpack(rd.home[j], X, Y, Z);
   R o[3] = {R(0), R(0), R(0)}, v[3] = {R(0), R(0), R(0)};
@@ -561,7 +635,7 @@ __global__ void part_out(RepDev rd, int field, double s0, double s1, double s2, 
   } else if (field == F_CELL) {
     R of[3] = {R(0), R(0), R(0)};
     for (int a = 0; a < D; ++a) of[a] = ((const R*)rd.off[a])[j];
-    const double s[3] = {s0, s1, s2};
+    const R s[3] = {(R)s0, (R)s1, (R)s2};
     ((int*)out)[id] = (int)collision_cell<D, R>(rd, X, Y, Z, of, s);
   } else {
     ((int*)out)[id] = (int)id;
@@ -670,8 +744,7 @@ __device__ __forceinline__ uint32_t home_index(const RepDev& rd, uint32_t packed
 }
 
 template <int D>
-__device__ __forceinline__ void sort_count_item(const RepDev& rd, const int2 bm) {
-  const long long j = (long long)bm.y * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void sort_count_one(const RepDev& rd, const long long j) {
   const bool active = j < rd.np;
   const uint32_t h = active ? home_index<D>(rd, rd.home[j]) : 0xFFFFFFFFu;
   const unsigned grp = __match_any_sync(0xFFFFFFFFu, h);
@@ -680,6 +753,12 @@ __device__ __forceinline__ void sort_count_item(const RepDev& rd, const int2 bm)
   if (active && lane == leader) base = atomicAdd(rd.hcount + h, (uint32_t)__popc(grp));
   base = __shfl_sync(0xFFFFFFFFu, base, leader);
   if (active) rd.rank[j] = base + (uint32_t)__popc(grp & ((1u << lane) - 1u));
+}
+
+template <int D>
+__device__ __forceinline__ void sort_count_item(const RepDev& rd, const int2 bm) {
+#pragma unroll
+  for (int p = 0; p < PPT; ++p) sort_count_one<D>(rd, (long long)bm.y * PP_ITEM + 256 * p + threadIdx.x);
 }
 
 template <int D>
@@ -749,8 +828,7 @@ __global__ void __launch_bounds__(1024) sort_scan_top(const RepDev* __restrict__
 }
 
 template <int D, typename R>
-__device__ __forceinline__ void sort_scatter_item(const RepDev& rd, const int2 bm) {
-  const long long j = (long long)bm.y * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void sort_scatter_one(const RepDev& rd, const long long j) {
   if (j >= rd.np) return;
   const uint32_t hp = rd.home[j];
   const uint32_t h = home_index<D>(rd, hp);
@@ -765,6 +843,12 @@ __device__ __forceinline__ void sort_scatter_item(const RepDev& rd, const int2 b
 }
 
 template <int D, typename R>
+__device__ __forceinline__ void sort_scatter_item(const RepDev& rd, const int2 bm) {
+#pragma unroll
+  for (int p = 0; p < PPT; ++p) sort_scatter_one<D, R>(rd, (long long)bm.y * PP_ITEM + 256 * p + threadIdx.x);
+}
+
+template <int D, typename R>
 __global__ void __launch_bounds__(256) sort_scatter(const RepDev* __restrict__ reps, const int2* __restrict__ bmap,
                                                     int nwork) {
   __shared__ RepDev rd;
@@ -776,12 +860,13 @@ __global__ void __launch_bounds__(256) sort_scatter(const RepDev* __restrict__ r
 cudaError_t launch_sort(int dim, int prec, const Launch& L, const int2* bmap_p, int nb_p, const int2* bmap_t,
                         int nb_t) {
   if (nb_p == 0) return cudaSuccess;
-  static const int gc2 = grid_for(sort_count<2>, 256, 1 << 30), gc3 = grid_for(sort_count<3>, 256, 1 << 30);
+  static const int gc2 = grid_cap(grid_for(sort_count<2>, 256, 1 << 30)), gc3 = grid_cap(grid_for(sort_count<3>, 256, 1 << 30));
   if (dim == 2) sort_count<2><<<gc2 < nb_p ? gc2 : nb_p, 256, 0, L.stream>>>(L.reps, bmap_p, nb_p);
   else sort_count<3><<<gc3 < nb_p ? gc3 : nb_p, 256, 0, L.stream>>>(L.reps, bmap_p, nb_p);
   sort_scan_tiles<<<nb_t, SORT_TILE, 0, L.stream>>>(L.reps, bmap_t);
   sort_scan_top<<<L.nrep, 1024, 0, L.stream>>>(L.reps);
-  const int gs = nb_p < 16384 ? nb_p : 16384;
+  static const int gs2 = grid_cap(grid_for(sort_scatter<2, float>, 256, 1 << 30));
+  const int gs = nb_p < gs2 ? nb_p : gs2;
   if (dim == 2) {
     if (prec == P_FP64) sort_scatter<2, double><<<gs, 256, 0, L.stream>>>(L.reps, bmap_p, nb_p);
     else sort_scatter<2, float><<<gs, 256, 0, L.stream>>>(L.reps, bmap_p, nb_p);
