@@ -45,13 +45,27 @@ LBM_HD uint4 philox(uint32_t id, uint32_t step, uint32_t rep, uint32_t tag, uint
 LBM_HD double unit24(uint32_t w) { return (double)(w >> 8) * (1.0 / 16777216.0); }
 LBM_HD float unit24f(uint32_t w) { return (float)(w >> 8) * (1.0f / 16777216.0f); }
 
-// Box-Muller pair in binary64: u1 = (a+1) 2^-32 in (0,1], u2 = b 2^-32.
+// Box-Muller pair: u1 = (a+1) 2^-32 in (0,1], u2 = b 2^-32,
+// z0 = sqrt(-2 ln u1) cos(2 pi u2), z1 = sqrt(-2 ln u1) sin(2 pi u2).
+// binary64 version:
 __device__ __forceinline__ void normal_pair(uint32_t a, uint32_t b, double& z0, double& z1) {
   const double u1 = ((double)a + 1.0) * (1.0 / 4294967296.0);
   const double u2 = (double)b * (1.0 / 4294967296.0);
   const double rad = sqrt(-2.0 * log(u1));
   double s, c;
   sincospi(2.0 * u2, &s, &c);
+  z0 = rad * c;
+  z1 = rad * s;
+}
+// binary32 version, within ~1e-6 of the binary64 outputs: ln u1 is logf(u1)
+// for u1 < 1/2 and log1pf(-m 2^-32), m = 2^32 - 1 - a, for u1 >= 1/2, so that
+// neither tail loses the bits that rounding the 32-bit word to binary32 drops.
+__device__ __forceinline__ void normal_pair(uint32_t a, uint32_t b, float& z0, float& z1) {
+  const float lnu = a < 0x80000000u ? logf((float)(a + 1u) * (1.0f / 4294967296.0f))
+                                    : log1pf(-(float)(0xFFFFFFFFu - a) * (1.0f / 4294967296.0f));
+  const float rad = sqrtf(-2.0f * lnu);
+  float s, c;
+  sincospif(2.0f * ((float)b * (1.0f / 4294967296.0f)), &s, &c);
   z0 = rad * c;
   z1 = rad * s;
 }
@@ -108,7 +122,7 @@ struct RepDev {
   double cos_a, sin_a, alpha;
   // binary32 copies of the constants the binary32 kernels use (binary64
   // arithmetic, conversions included, is slow on this GPU)
-  float omega_f, g_f[3], r_f, cos_f, sin_f;
+  float omega_f, g_f[3], r_f, cos_f, sin_f, kT_f, mass_f, sig_f;
   long long np;            // particles
   long long ncell;         // collision cells: Wx (Hy+1) Wz
   long long nbuf;          // inner-buffer LB nodes
@@ -169,6 +183,8 @@ template <> struct Cst<double> {
   __device__ static double r(const RepDev& d) { return (double)d.r; }
   __device__ static double cos_a(const RepDev& d) { return d.cos_a; }
   __device__ static double sin_a(const RepDev& d) { return d.sin_a; }
+  __device__ static double sig(const RepDev& d) { return d.sig; }
+  __device__ static double kT_over_m(const RepDev& d) { return d.kT / d.mass; }
   __device__ static const double* shift(const StepInfo& s) { return s.shift; }
   __device__ static const double* prev(const StepInfo& s) { return s.prev; }
 };
@@ -178,6 +194,8 @@ template <> struct Cst<float> {
   __device__ static float r(const RepDev& d) { return d.r_f; }
   __device__ static float cos_a(const RepDev& d) { return d.cos_f; }
   __device__ static float sin_a(const RepDev& d) { return d.sin_f; }
+  __device__ static float sig(const RepDev& d) { return d.sig_f; }
+  __device__ static float kT_over_m(const RepDev& d) { return d.kT_f / d.mass_f; }
   __device__ static const float* shift(const StepInfo& s) { return s.shift_f; }
   __device__ static const float* prev(const StepInfo& s) { return s.prev_f; }
 };

@@ -153,6 +153,7 @@ extern "C" int lbmpcd_create(const lbmpcd_params* params, int n_replicas, void* 
     d.alpha = p.alpha; d.cos_a = cos(p.alpha); d.sin_a = sin(p.alpha);
     d.omega_f = (float)d.omega; d.r_f = (float)p.refine;
     d.cos_f = (float)d.cos_a; d.sin_f = (float)d.sin_a;
+    d.kT_f = (float)p.kT; d.mass_f = (float)p.mass; d.sig_f = (float)d.sig;
     for (int a = 0; a < 3; ++a) d.g_f[a] = (float)d.g[a];
     d.key0 = (uint32_t)(p.seed & 0xFFFFFFFFu); d.key1 = (uint32_t)(p.seed >> 32); d.rep = (uint32_t)r;
     std::vector<void*>& L = h->allocs;

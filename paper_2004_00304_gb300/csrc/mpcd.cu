@@ -138,33 +138,35 @@ __device__ __forceinline__ void rotate(const RepDev& rd, uint32_t c, R* v) {
 // LB velocity at node (x,y,z) with periodic x, z and the wall ghost
 // u(0) = -u(1), u(ny-1) = -u(ny-2) that puts u = 0 on the half-way walls.
 template <typename R>
-__device__ __forceinline__ double u_node(const RepDev& rd, int a, int x, int y, int z) {
+__device__ __forceinline__ R u_node(const RepDev& rd, int a, int x, int y, int z) {
   x = wrap(x, rd.nx);
   z = wrap(z, rd.nz);
-  double sgn = 1.0;
-  if (y <= 0) { y = 1; sgn = -1.0; }
-  if (y >= rd.ny - 1) { y = rd.ny - 2; sgn = -1.0; }
+  R sgn = R(1);
+  if (y <= 0) { y = 1; sgn = R(-1); }
+  if (y >= rd.ny - 1) { y = rd.ny - 2; sgn = R(-1); }
   const R* u = (const R*)rd.u;
-  return sgn * (double)u[a * rd.nnode + x + (long long)rd.nx * (y + (long long)rd.ny * z)];
+  return sgn * u[a * rd.nnode + x + (long long)rd.nx * (y + (long long)rd.ny * z)];
 }
 
 // a2: bilinear (2D) / trilinear (3D) interpolation of the LB velocity, known
-// at node centres, to the centre of MPCD cell (X,Y,Z) (Algorithm 2).
+// at node centres, to the centre of MPCD cell (X,Y,Z) (Algorithm 2).  In the
+// kernel's precision: for refinement ratios that are powers of two the
+// positions and weights are exact in binary32.
 template <int D, typename R>
-__device__ void u_fine(const RepDev& rd, int X, int Y, int Z, double* out) {
-  const double r = rd.r;
-  const double px = rd.x0 + (X + 0.5) / r - 0.5;
-  const double py = 1.0 + (Y + 0.5) / r - 0.5;
-  const double pz = (D == 3) ? (Z + 0.5) / r - 0.5 : 0.0;
+__device__ void u_fine(const RepDev& rd, int X, int Y, int Z, R* out) {
+  const R r = Cst<R>::r(rd);
+  const R px = (R)rd.x0 + ((R)X + R(0.5)) / r - R(0.5);
+  const R py = R(1) + ((R)Y + R(0.5)) / r - R(0.5);
+  const R pz = (D == 3) ? ((R)Z + R(0.5)) / r - R(0.5) : R(0);
   const int i0 = (int)floor(px), j0 = (int)floor(py), k0 = (int)floor(pz);
-  const double tx = px - i0, ty = py - j0, tz = pz - k0;
+  const R tx = px - (R)i0, ty = py - (R)j0, tz = pz - (R)k0;
   for (int a = 0; a < D; ++a) {
-    double acc = 0;
+    R acc = R(0);
     for (int di = 0; di < 2; ++di)
       for (int dj = 0; dj < 2; ++dj)
         for (int dk = 0; dk < (D == 3 ? 2 : 1); ++dk) {
-          double wgt = (di ? tx : 1 - tx) * (dj ? ty : 1 - ty);
-          if (D == 3) wgt *= (dk ? tz : 1 - tz);
+          R wgt = (di ? tx : R(1) - tx) * (dj ? ty : R(1) - ty);
+          if (D == 3) wgt *= (dk ? tz : R(1) - tz);
           acc += wgt * u_node<R>(rd, a, i0 + di, j0 + dj, k0 + dk);
         }
     out[a] = acc;
@@ -295,15 +297,16 @@ __device__ __forceinline__ void particle_item(const RepDev& rd, const StepInfo& 
     if (!act[p]) continue;
     // a2 + a3: Maxwellian redraw in the outer buffer columns
     if (X[p] < rd.xo_lo || X[p] >= rd.xo_hi) {
-      double uf[3] = {0, 0, 0};
+      R uf[3] = {R(0), R(0), R(0)};
       u_fine<D, R>(rd, X[p], Y[p], Z[p], uf);
       const uint4 w = philox((alt ? rd.pid_alt : rd.pid)[j], st.n, rd.rep, TAG_RESAMPLE, rd.key0, rd.key1);
-      double z0, z1, z2, z3;
+      R z0, z1, z2, z3;
       normal_pair(w.x, w.y, z0, z1);
       normal_pair(w.z, w.w, z2, z3);
-      v[p][0] = (R)(uf[0] + rd.sig * z0);
-      v[p][1] = (R)(uf[1] + rd.sig * z1);
-      if (D == 3) v[p][2] = (R)(uf[2] + rd.sig * z2);
+      const R sg = Cst<R>::sig(rd);
+      v[p][0] = uf[0] + sg * z0;
+      v[p][1] = uf[1] + sg * z1;
+      if (D == 3) v[p][2] = uf[2] + sg * z2;
     }
     if (alt) rd.pid[j] = rd.pid_alt[j];
     // a4
@@ -421,12 +424,12 @@ __device__ __forceinline__ void cell_item(const RepDev& rd, const StepInfo& st, 
           // drawn from N(0, (ppc - n) m kT) per component.
           const int nv = rd.ppc - (int)n;
           const uint4 w = philox((uint32_t)c, st.n, rd.rep, TAG_VIRT, rd.key0, rd.key1);
-          double z[4];
+          R z[4];
           normal_pair(w.x, w.y, z[0], z[1]);
           normal_pair(w.z, w.w, z[2], z[3]);
-          const double sd = sqrt((double)nv * rd.kT / rd.mass);
+          const R sd = sqrt((R)nv * Cst<R>::kT_over_m(rd));
 #pragma unroll
-          for (int a = 0; a < D; ++a) vc[a] = (R)(((double)V[p][a] + sd * z[a]) / (double)(rd.ppc));
+          for (int a = 0; a < D; ++a) vc[a] = (V[p][a] + sd * z[a]) / (R)rd.ppc;
         } else {
           const R inv_n = R(1) / (R)n;
 #pragma unroll
