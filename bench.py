@@ -116,8 +116,8 @@ def ncu_traffic_per_launch():
     h = hashlib.sha256(src).hexdigest()[:16]
     vals = {}
     for ln in txt.splitlines():
-        if ":" in ln and ln.strip().startswith("- "):
-            k, v = ln.strip()[2:].split(":", 1)
+        if ": " in ln and ln.strip().startswith("- "):
+            k, v = ln.strip()[2:].split(": ", 1)
             vals[k.strip()] = v.strip()
     if vals.get("mpcd.cu sha256[:16]") != h:
         return None
