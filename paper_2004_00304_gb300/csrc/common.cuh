@@ -185,6 +185,7 @@ template <> struct Cst<double> {
   __device__ static double sin_a(const RepDev& d) { return d.sin_a; }
   __device__ static double sig(const RepDev& d) { return d.sig; }
   __device__ static double kT_over_m(const RepDev& d) { return d.kT / d.mass; }
+  __device__ static double mass(const RepDev& d) { return d.mass; }
   __device__ static const double* shift(const StepInfo& s) { return s.shift; }
   __device__ static const double* prev(const StepInfo& s) { return s.prev; }
 };
@@ -196,6 +197,7 @@ template <> struct Cst<float> {
   __device__ static float sin_a(const RepDev& d) { return d.sin_f; }
   __device__ static float sig(const RepDev& d) { return d.sig_f; }
   __device__ static float kT_over_m(const RepDev& d) { return d.kT_f / d.mass_f; }
+  __device__ static float mass(const RepDev& d) { return d.mass_f; }
   __device__ static const float* shift(const StepInfo& s) { return s.shift_f; }
   __device__ static const float* prev(const StepInfo& s) { return s.prev_f; }
 };

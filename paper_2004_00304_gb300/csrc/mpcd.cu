@@ -184,7 +184,8 @@ __device__ __forceinline__ void stream(const RepDev& rd, int& X, int& Y, int& Z,
   const R rr = Cst<R>::r(rd);
   const R dx = xmul(v[0], rr), dy = xmul(v[1], rr), dz = (D == 3) ? xmul(v[2], rr) : R(0);
   const R ty = xadd(o[1], dy);
-  const int ky = (int)floor(ty);
+  int ky = (ty >= R(1) ? 1 : 0) - (ty < R(0) ? 1 : 0);      // floor(ty) for ty in [-1, 2)
+  if (ty < R(-1) || ty >= R(2)) ky = (int)floor(ty);
   const int nyc = Y + ky;
   R dxe = dx, dze = dz;
   if (nyc < 0 || nyc >= rd.Hy) {
@@ -210,14 +211,16 @@ __device__ __forceinline__ void stream(const RepDev& rd, int& X, int& Y, int& Z,
     if (Y >= rd.Hy) { Y = rd.Hy - 1; o[1] = Num<R>::one_minus; }
   }
   const R tx = xadd(o[0], dxe);
-  int kx = (int)floor(tx);
+  int kx = (tx >= R(1) ? 1 : 0) - (tx < R(0) ? 1 : 0);
+  if (tx < R(-1) || tx >= R(2)) kx = (int)floor(tx);
   o[0] = xsub(tx, (R)kx);
   if (o[0] >= R(1)) { o[0] = xsub(o[0], R(1)); kx += 1; }
   X += kx;
   if (X < 0 || X >= rd.Wx) X = wrap(X, rd.Wx);
   if (D == 3) {
     const R tz = xadd(o[2], dze);
-    int kz = (int)floor(tz);
+    int kz = (tz >= R(1) ? 1 : 0) - (tz < R(0) ? 1 : 0);
+    if (tz < R(-1) || tz >= R(2)) kz = (int)floor(tz);
     o[2] = xsub(tz, (R)kz);
     if (o[2] >= R(1)) { o[2] = xsub(o[2], R(1)); kz += 1; }
     Z += kz;
@@ -230,8 +233,14 @@ __device__ __forceinline__ void stream(const RepDev& rd, int& X, int& Y, int& Z,
 // covers 32 consecutive particles.  All state loads of the four particles are
 // issued first, then their four cell-table loads, before any arithmetic:
 // each thread keeps ~100 bytes in flight instead of one dependent chain.
+// shared memory of particle_pass: staging of the warp-aggregated reduction
+template <int D, typename R> struct PassShared {
+  R sv[D][256];
+};
+
 template <int D, typename R>
-__device__ __forceinline__ void particle_item(const RepDev& rd, const StepInfo& st, const int2 bm, R (*sv)[256]) {
+__device__ __forceinline__ void particle_item(const RepDev& rd, const StepInfo& st, const int2 bm,
+                                              PassShared<D, R>& red) {
   using T4 = typename Vec4<R>::T;
   const long long j0 = (long long)bm.y * PP_ITEM + threadIdx.x;
   const bool alt = st.src_alt;
@@ -341,7 +350,7 @@ __device__ __forceinline__ void particle_item(const RepDev& rd, const StepInfo& 
     const unsigned grp = __match_any_sync(0xFFFFFFFFu, cid[p]);
     __syncwarp();
 #pragma unroll
-    for (int a = 0; a < D; ++a) sv[a][threadIdx.x] = v[p][a];
+    for (int a = 0; a < D; ++a) red.sv[a][threadIdx.x] = v[p][a];
     __syncwarp();
     if (act[p] && lane == __ffs(grp) - 1) {
       R acc[D];
@@ -352,7 +361,7 @@ __device__ __forceinline__ void particle_item(const RepDev& rd, const StepInfo& 
         const int l = __ffs(m) - 1;
         m &= m - 1;
 #pragma unroll
-        for (int a = 0; a < D; ++a) acc[a] += sv[a][wbase + l];
+        for (int a = 0; a < D; ++a) acc[a] += red.sv[a][wbase + l];
       }
       atomicAdd(rd.acc_n + cid[p], (uint32_t)__popc(grp));
 #pragma unroll
@@ -366,8 +375,8 @@ __global__ void __launch_bounds__(256) particle_pass(const RepDev* __restrict__ 
                                                      int nwork, const StepInfo* __restrict__ si, int k, int nrep) {
   __shared__ RepDev rd;
   __shared__ StepInfo st;
-  __shared__ R sv[D][256];
-  for_each_item(bmap, nwork, reps, si, k, nrep, rd, st, [&](const int2 bm) { particle_item<D, R>(rd, st, bm, sv); });
+  __shared__ PassShared<D, R> red;
+  for_each_item(bmap, nwork, reps, si, k, nrep, rd, st, [&](const int2 bm) { particle_item<D, R>(rd, st, bm, red); });
 }
 
 template <int D, typename R>
@@ -472,28 +481,34 @@ __device__ __forceinline__ void cell_item(const RepDev& rd, const StepInfo& st, 
     }
     return;
   }
-  // a8: one thread per inner-buffer LB node
+  // a8: one thread per inner-buffer LB node.  The window sums are binary64;
+  // the equilibrium is evaluated in the kernel's precision.
   const long long b = (long long)(-1 - bm.y) * blockDim.x + threadIdx.x;
   if (b >= rd.nbuf) return;
   double* fr = rd.frame + 4 * b;
   double* ws = rd.wsum + 4 * b;
   double* rg = rd.ring + 4 * ((long long)(st.n % (uint32_t)rd.window) * rd.nbuf + b);
+  double W4[4];
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
     const double x = fr[a];
-    ws[a] += x - rg[a];
+    W4[a] = ws[a] + (x - rg[a]);
+    ws[a] = W4[a];
     rg[a] = x;
     fr[a] = 0.0;
   }
-  const double nf = (double)min((long long)st.n + 1, (long long)rd.window);
-  const double rdim = (D == 3) ? (double)rd.r * rd.r * rd.r : (double)rd.r * rd.r;
-  const double M = ws[0];
-  const double rho = M / ((double)rd.ppc * rd.mass * rdim * nf);
-  double u[3] = {0, 0, 0};
-  if (M > 0) { u[0] = ws[1] / M; u[1] = ws[2] / M; u[2] = ws[3] / M; }
+  const uint32_t nf = min(st.n + 1u, (uint32_t)rd.window);
+  const R rdim = (D == 3) ? (R)(rd.r * rd.r * rd.r) : (R)(rd.r * rd.r);
+  const R M = (R)W4[0];
+  const R rho = M / ((R)rd.ppc * (R)Cst<R>::mass(rd) * rdim * (R)nf);
+  R u[3] = {R(0), R(0), R(0)};
+  if (M > R(0)) {
+    const R iM = R(1) / M;
+    u[0] = (R)W4[1] * iM; u[1] = (R)W4[2] * iM; u[2] = (R)W4[3] * iM;
+  }
   double* wm = rd.wmean + 4 * b;
-  wm[0] = rho; wm[1] = u[0]; wm[2] = u[1]; wm[3] = u[2];
-  if (!(rd.feedback == 1 && st.n >= 1 && M > 0)) return;
+  wm[0] = (double)rho; wm[1] = (double)u[0]; wm[2] = (double)u[1]; wm[3] = (double)u[2];
+  if (!(rd.feedback == 1 && st.n >= 1 && M > R(0))) return;
   long long t = b;
   const int y = 1 + (int)(t % (rd.ny - 2)); t /= (rd.ny - 2);
   const int z = (int)(t % rd.nz); t /= rd.nz;
@@ -504,13 +519,13 @@ __device__ __forceinline__ void cell_item(const RepDev& rd, const StepInfo& st, 
   // equilibrium at the node's own LB density (this step's moment) and the
   // window-mean MPCD velocity: the MPCD density is reported, not imposed,
   // because the two fluids' equations of state differ (rho/3 versus n kT).
-  const double rl = (double)((const R*)rd.rho)[node];
-  const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  const R rl = ((const R*)rd.rho)[node];
+  const R uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
-    const double cu = L::cx(i) * u[0] + L::cy(i) * u[1] + L::cz(i) * u[2];
-    const double dev = L::w(i) * ((rl - 1.0) + rl * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu));
-    Store<S>::st(dst + i * rd.nnode + node, (R)dev, rd.fp16_scale);
+    const R cu = L::cx(i) * u[0] + L::cy(i) * u[1] + L::cz(i) * u[2];
+    const R dev = (R)L::w(i) * ((rl - R(1)) + rl * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu));
+    Store<S>::st(dst + i * rd.nnode + node, dev, rd.fp16_scale);
   }
 }
 
