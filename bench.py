@@ -222,7 +222,7 @@ def run_ours(args, rank, world, local_rank):
         barrier()
         clocks = sampler.stop() if sampler else None
         ms = e0.elapsed_time(e1)
-        launches = 3 * args.steps + (args.steps + 31) // 32
+        launches = 3 * args.steps + 5 * (args.steps // 64) + (1 if args.steps % 64 else 0)
         t_max = torch.tensor([ms], dtype=torch.float64, device=dev)
         if world > 1:
             dist.all_reduce(t_max, op=dist.ReduceOp.MAX)

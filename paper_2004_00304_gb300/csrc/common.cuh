@@ -132,8 +132,8 @@ struct RepDev {
   int xo_lo, xo_hi, xi_lo0, xi_hi0, xi_lo1, xi_hi1;
   // particles (structure of arrays); *_alt receive the sorted copy
   uint32_t* home;          // packed integer home cell
-  void* off[3];            // offsets in [0,1), storage precision
-  void* vel[3];            // velocities, storage precision
+  void* off[3];            // offsets in [0,1), storage precision (2D: off[0] holds (x,y) pairs)
+  void* vel[3];            // velocities, storage precision (2D: vel[0] holds (x,y) pairs)
   uint32_t* pid;           // particle id (Philox counter of the redraw)
   uint32_t* home_alt;
   void* off_alt[3];
@@ -147,7 +147,11 @@ struct RepDev {
   uint32_t* tsum;          // [ntile] tile totals -> exclusive tile offsets
   uint32_t* rank;          // [np] rank of the particle inside its home cell
   // collision cells
-  uint32_t* acc_n;         // accumulators of the current binning
+  // accumulators of the current binning: binary32 storage keeps one float4
+  // {n, sum vx, sum vy, sum vz} per cell in acc4 (one vector atomic per group
+  // of particles); binary64 keeps acc_n and acc_v[d]
+  float4* acc4;
+  uint32_t* acc_n;
   void* acc_v[3];
   void* tab;               // table of the last collision, vec4 of the storage
                            // precision: 2D {vcm.x, vcm.y, sin(theta), n};
@@ -163,7 +167,7 @@ constexpr int SORT_TILE = 1024;
 
 template <typename R> struct Vec4;
 template <> struct Vec4<float> { using T = float4; };
-template <> struct Vec4<double> { using T = double4; };
+template <> struct Vec4<double> { using T = double4_32a; };
 
 // One record per (step of the chunk, replica), written by the prep kernel.
 struct StepInfo {

@@ -211,7 +211,7 @@ __device__ __forceinline__ void lb_row(const RepDev& rd, const StepInfo& st, con
 
 
 template <int Q, typename S, int V>
-__global__ void __launch_bounds__(128) lb_pull(const RepDev* __restrict__ reps, const int4* __restrict__ bmap,
+__global__ void __launch_bounds__(128, 5) lb_pull(const RepDev* __restrict__ reps, const int4* __restrict__ bmap,
                                                int nwork, const StepInfo* __restrict__ si, int k, int nrep) {
   __shared__ RepDev rd;
   __shared__ StepInfo st;

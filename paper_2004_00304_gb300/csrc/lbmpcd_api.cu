@@ -22,7 +22,7 @@
 using namespace lbm;
 
 namespace {
-constexpr int KCHUNK = 32;   // steps per captured graph
+constexpr int KCHUNK = 64;   // steps per captured graph (and per particle sort)
 thread_local std::string g_create_error;
 }  // namespace
 
@@ -273,16 +273,25 @@ extern "C" int lbmpcd_set_region(lbmpcd* h, int replica, const int lo[3], const 
   A(*(void**)&d.pid, d.np * 4);
   A(*(void**)&d.home_alt, d.np * 4);
   A(*(void**)&d.pid_alt, d.np * 4);
-  for (int a = 0; a < h->dim; ++a) {
-    A(d.off[a], d.np * rs); A(d.vel[a], d.np * rs);
-    A(d.off_alt[a], d.np * rs); A(d.vel_alt[a], d.np * rs);
+  if (h->dim == 2) {   // interleaved (x, y) pairs
+    A(d.off[0], d.np * 2 * rs); A(d.vel[0], d.np * 2 * rs);
+    A(d.off_alt[0], d.np * 2 * rs); A(d.vel_alt[0], d.np * 2 * rs);
+  } else {
+    for (int a = 0; a < 3; ++a) {
+      A(d.off[a], d.np * rs); A(d.vel[a], d.np * rs);
+      A(d.off_alt[a], d.np * rs); A(d.vel_alt[a], d.np * rs);
+    }
   }
   A(*(void**)&d.rank, d.np * 4);
   A(*(void**)&d.hcount, d.nhome * 4);
   A(*(void**)&d.hoff, d.nhome * 4);
   A(*(void**)&d.tsum, (long long)d.ntile * 4);
-  A(*(void**)&d.acc_n, d.ncell * 4);
-  for (int a = 0; a < h->dim; ++a) A(d.acc_v[a], d.ncell * rs);
+  if (h->prec == P_FP64) {
+    A(*(void**)&d.acc_n, d.ncell * 4);
+    for (int a = 0; a < h->dim; ++a) A(d.acc_v[a], d.ncell * rs);
+  } else {
+    A(*(void**)&d.acc4, d.ncell * 16);
+  }
   A(d.tab, d.ncell * rs * 4 * (h->dim == 2 ? 1 : 2));
   const long long nb4 = (d.nbuf > 0 ? d.nbuf : 1) * 4;
   A(*(void**)&d.frame, nb4 * 8);

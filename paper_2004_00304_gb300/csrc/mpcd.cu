@@ -47,6 +47,34 @@ __device__ __forceinline__ float xadd(float a, float b) { return a + b; }
 __device__ __forceinline__ float xsub(float a, float b) { return a - b; }
 __device__ __forceinline__ float xmul(float a, float b) { return a * b; }
 
+// Particle offsets and velocities: in 2D each is one array of interleaved
+// (x, y) pairs (one 8- or 16-byte access per particle), in 3D one array per axis.
+template <typename R> struct Pair;
+template <> struct Pair<float> { using T = float2; };
+template <> struct Pair<double> { using T = double2; };
+template <int D, typename R> struct PState;
+template <typename R> struct PState<2, R> {
+  using T2 = typename Pair<R>::T;
+  __device__ static void ld(void* const* base, uint32_t j, R* x) {
+    const T2 t = ((const T2*)base[0])[j];
+    x[0] = t.x; x[1] = t.y;
+  }
+  __device__ static void st(void* const* base, uint32_t j, const R* x) {
+    T2 t; t.x = x[0]; t.y = x[1];
+    ((T2*)base[0])[j] = t;
+  }
+};
+template <typename R> struct PState<3, R> {
+  __device__ static void ld(void* const* base, uint32_t j, R* x) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) x[a] = ((const R*)base[a])[j];
+  }
+  __device__ static void st(void* const* base, uint32_t j, const R* x) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) ((R*)base[a])[j] = x[a];
+  }
+};
+
 // ---------------------------------------------------------------------------
 // prep: one block; per (step k of the chunk, replica) the global step index,
 // the random shift of that step and of the previous one, and whether the
@@ -242,33 +270,26 @@ template <int D, typename R>
 __device__ __forceinline__ void particle_item(const RepDev& rd, const StepInfo& st, const int2 bm,
                                               PassShared<D, R>& red) {
   using T4 = typename Vec4<R>::T;
-  const long long j0 = (long long)bm.y * PP_ITEM + threadIdx.x;
+  const uint32_t j0 = (uint32_t)bm.y * PP_ITEM + threadIdx.x;
   const bool alt = st.src_alt;
   const uint32_t* __restrict__ hsrc = alt ? rd.home_alt : rd.home;
   int X[PPT], Y[PPT], Z[PPT];
   R o[PPT][3], v[PPT][3];
   bool act[PPT];
   // branch-free loads: a lane past the end reads the last particle and discards it
-  const R* offs[3];
-  const R* vels[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    offs[a] = (const R*)(alt ? rd.off_alt[a] : rd.off[a]);
-    vels[a] = (const R*)(alt ? rd.vel_alt[a] : rd.vel[a]);
-  }
+  void* const* offs = alt ? rd.off_alt : rd.off;
+  void* const* vels = alt ? rd.vel_alt : rd.vel;
+  const uint32_t np32 = (uint32_t)rd.np;
 #pragma unroll
   for (int p = 0; p < PPT; ++p) {
-    const long long j = j0 + 256 * p;
-    act[p] = j < rd.np;
-    const long long jl = act[p] ? j : rd.np - 1;
+    const uint32_t j = j0 + 256u * p;
+    act[p] = j < np32;
+    const uint32_t jl = act[p] ? j : np32 - 1u;
     HomePack<D>::unpack(hsrc[jl], X[p], Y[p], Z[p]);
 #pragma unroll
     for (int a = 0; a < 3; ++a) { o[p][a] = R(0); v[p][a] = R(0); }
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-      o[p][a] = offs[a][jl];
-      v[p][a] = vels[a][jl];
-    }
+    PState<D, R>::ld(offs, jl, o[p]);
+    PState<D, R>::ld(vels, jl, v[p]);
   }
   // a7 of step n-1: cell-table loads for all four, then the rotations
   if (st.pending) {
@@ -301,7 +322,7 @@ __device__ __forceinline__ void particle_item(const RepDev& rd, const StepInfo& 
   uint32_t cid[PPT];
 #pragma unroll
   for (int p = 0; p < PPT; ++p) {
-    const long long j = j0 + 256 * p;
+    const uint32_t j = j0 + 256u * p;
     cid[p] = 0xFFFFFFFFu;
     if (!act[p]) continue;
     // a2 + a3: Maxwellian redraw in the outer buffer columns
@@ -335,11 +356,8 @@ __device__ __forceinline__ void particle_item(const RepDev& rd, const StepInfo& 
     // a5: binning under this step's shift
     cid[p] = collision_cell<D, R>(rd, X[p], Y[p], Z[p], o[p], Cst<R>::shift(st));
     rd.home[j] = HomePack<D>::pack(X[p], Y[p], Z[p]);
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-      ((R*)rd.off[a])[j] = o[p][a];
-      ((R*)rd.vel[a])[j] = v[p][a];
-    }
+    PState<D, R>::st(rd.off, j, o[p]);
+    PState<D, R>::st(rd.vel, j, v[p]);
   }
   // warp-aggregated reduction, one round per particle slot: lanes sharing a
   // collision cell are summed by their lowest lane, which issues one atomic
@@ -363,9 +381,18 @@ __device__ __forceinline__ void particle_item(const RepDev& rd, const StepInfo& 
 #pragma unroll
         for (int a = 0; a < D; ++a) acc[a] += red.sv[a][wbase + l];
       }
-      atomicAdd(rd.acc_n + cid[p], (uint32_t)__popc(grp));
+      if (sizeof(R) == 4) {
+        float4 g4;
+        g4.x = (float)__popc(grp);
+        g4.y = (float)acc[0];
+        g4.z = (float)acc[1];
+        g4.w = D == 3 ? (float)acc[D - 1] : 0.0f;
+        atomicAdd(rd.acc4 + cid[p], g4);
+      } else {
+        atomicAdd(rd.acc_n + cid[p], (uint32_t)__popc(grp));
 #pragma unroll
-      for (int a = 0; a < D; ++a) atomicAdd((R*)rd.acc_v[a] + cid[p], acc[a]);
+        for (int a = 0; a < D; ++a) atomicAdd((R*)rd.acc_v[a] + cid[p], acc[a]);
+      }
     }
   }
 }
@@ -414,9 +441,15 @@ __device__ __forceinline__ void cell_item(const RepDev& rd, const StepInfo& st, 
     for (int p = 0; p < CPT; ++p) {
       const long long c = c0 + 256 * p;
       const long long cl = c < rd.ncell ? c : rd.ncell - 1;
-      nn[p] = rd.acc_n[cl];
+      if (sizeof(R) == 4) {
+        const float4 g4 = rd.acc4[cl];
+        nn[p] = (uint32_t)g4.x;
+        V[p][0] = (R)g4.y; V[p][1] = (R)g4.z; V[p][2] = (R)g4.w;
+      } else {
+        nn[p] = rd.acc_n[cl];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) V[p][a] = a < D ? ((const R*)rd.acc_v[a])[cl] : R(0);
+        for (int a = 0; a < 3; ++a) V[p][a] = a < D ? ((const R*)rd.acc_v[a])[cl] : R(0);
+      }
     }
 #pragma unroll
     for (int p = 0; p < CPT; ++p) {
@@ -475,9 +508,13 @@ __device__ __forceinline__ void cell_item(const RepDev& rd, const StepInfo& st, 
         tab[2 * c] = t0;
         tab[2 * c + 1] = t1;
       }
+      if (sizeof(R) == 4) {
+        rd.acc4[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+      } else {
 #pragma unroll
-      for (int a = 0; a < D; ++a) ((R*)rd.acc_v[a])[c] = R(0);
-      rd.acc_n[c] = 0u;
+        for (int a = 0; a < D; ++a) ((R*)rd.acc_v[a])[c] = R(0);
+        rd.acc_n[c] = 0u;
+      }
     }
     return;
   }
@@ -570,14 +607,10 @@ __global__ void flush_collision(const RepDev* __restrict__ rdp, double s0, doubl
   int X, Y, Z;
   HomePack<D>::unpack(rd.home[j], X, Y, Z);
   R o[3] = {R(0), R(0), R(0)}, v[3] = {R(0), R(0), R(0)};
-#pragma unroll
-  for (int a = 0; a < D; ++a) {
-    o[a] = ((const R*)rd.off[a])[j];
-    v[a] = ((const R*)rd.vel[a])[j];
-  }
+  PState<D, R>::ld(rd.off, (uint32_t)j, o);
+  PState<D, R>::ld(rd.vel, (uint32_t)j, v);
   rotate<D, R>(rd, collision_cell<D, R>(rd, X, Y, Z, o, s), v);
-#pragma unroll
-  for (int a = 0; a < D; ++a) ((R*)rd.vel[a])[j] = v[a];
+  PState<D, R>::st(rd.vel, (uint32_t)j, v);
 }
 
 cudaError_t launch_flush(int dim, int prec, const RepDev* rd_dev, const RepDev& rd, const double* ls,
@@ -612,11 +645,14 @@ __global__ void init_particles(const RepDev* __restrict__ rdp) {
   const uint32_t wo[3] = {wp.x, wp.y, wp.z};
   rd.home[j] = HomePack<D>::pack(X, Y, Z);
   rd.pid[j] = (uint32_t)j;
+  R o[3], v[3];
 #pragma unroll
-  for (int a = 0; a < D; ++a) {
-    ((R*)rd.off[a])[j] = (R)unit24(wo[a]);
-    ((R*)rd.vel[a])[j] = (R)(rd.sig * z[a]);
+  for (int a = 0; a < 3; ++a) {
+    o[a] = (R)unit24(wo[a]);
+    v[a] = (R)(rd.sig * z[a]);
   }
+  PState<D, R>::st(rd.off, (uint32_t)j, o);
+  PState<D, R>::st(rd.vel, (uint32_t)j, v);
 }
 
 cudaError_t launch_init_particles(int dim, int prec, const RepDev* rd_dev, const RepDev& rd, cudaStream_t st) {
@@ -645,14 +681,15 @@ __global__ void part_out(RepDev rd, int field, double s0, double s1, double s2, 
   HomePack<D>::unpack(rd.home[j], X, Y, Z);
   if (field == F_POS || field == F_VEL) {
     double* o = (double*)out;
-    for (int a = 0; a < 3; ++a)
-      o[3 * id + a] = a < D ? (double)((const R*)(field == F_POS ? rd.off[a] : rd.vel[a]))[j] : 0.0;
+    R x[3] = {R(0), R(0), R(0)};
+    PState<D, R>::ld(field == F_POS ? rd.off : rd.vel, (uint32_t)j, x);
+    for (int a = 0; a < 3; ++a) o[3 * id + a] = (double)x[a];
   } else if (field == F_HOME) {
     int* o = (int*)out;
     o[3 * id] = X; o[3 * id + 1] = Y; o[3 * id + 2] = Z;
   } else if (field == F_CELL) {
     R of[3] = {R(0), R(0), R(0)};
-    for (int a = 0; a < D; ++a) of[a] = ((const R*)rd.off[a])[j];
+    PState<D, R>::ld(rd.off, (uint32_t)j, of);
     const R s[3] = {(R)s0, (R)s1, (R)s2};
     ((int*)out)[id] = (int)collision_cell<D, R>(rd, X, Y, Z, of, s);
   } else {
@@ -667,12 +704,14 @@ __global__ void part_in(RepDev rd, int field, const void* in, int* bad) {
   const long long id = rd.pid[j];
   if (field == F_POS || field == F_VEL) {
     const double* s = (const double*)in;
+    R x3[3] = {R(0), R(0), R(0)};
     for (int a = 0; a < D; ++a) {
       const double x = s[3 * id + a];
       if (field == F_POS && !(x >= 0.0 && x < 1.0)) atomicExch(bad, 1);
       const R xr = (R)x;
-      ((R*)(field == F_POS ? rd.off[a] : rd.vel[a]))[j] = (field == F_POS && xr >= R(1)) ? Num<R>::one_minus : xr;
+      x3[a] = (field == F_POS && xr >= R(1)) ? Num<R>::one_minus : xr;
     }
+    PState<D, R>::st(field == F_POS ? rd.off : rd.vel, (uint32_t)j, x3);
   } else {
     const int* s = (const int*)in;
     const int X = s[3 * id], Y = s[3 * id + 1], Z = D == 3 ? s[3 * id + 2] : 0;
@@ -718,8 +757,10 @@ __global__ void part_diag(RepDev rd, double* out) {
   double p[3] = {0, 0, 0}, e = 0;
   for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < rd.np;
        j += (long long)gridDim.x * blockDim.x) {
+    R vv[3] = {R(0), R(0), R(0)};
+    PState<D, R>::ld(rd.vel, (uint32_t)j, vv);
     for (int a = 0; a < D; ++a) {
-      const double v = (double)((const R*)rd.vel[a])[j];
+      const double v = (double)vv[a];
       p[a] += rd.mass * v;
       e += 0.5 * rd.mass * v * v;
     }
@@ -853,11 +894,11 @@ __device__ __forceinline__ void sort_scatter_one(const RepDev& rd, const long lo
   const long long dst = (long long)rd.tsum[h / SORT_TILE] + rd.hoff[h] + rd.rank[j];
   rd.home_alt[dst] = hp;
   rd.pid_alt[dst] = rd.pid[j];
-#pragma unroll
-  for (int a = 0; a < D; ++a) {
-    ((R*)rd.off_alt[a])[dst] = ((const R*)rd.off[a])[j];
-    ((R*)rd.vel_alt[a])[dst] = ((const R*)rd.vel[a])[j];
-  }
+  R o[3], v[3];
+  PState<D, R>::ld(rd.off, (uint32_t)j, o);
+  PState<D, R>::ld(rd.vel, (uint32_t)j, v);
+  PState<D, R>::st(rd.off_alt, (uint32_t)dst, o);
+  PState<D, R>::st(rd.vel_alt, (uint32_t)dst, v);
 }
 
 template <int D, typename R>

@@ -97,11 +97,11 @@ def test_lb_stream_collide_parity(lb, case, prec):
 
 
 def test_lb_long_run_graph_chunks(lb):
-    """70 steps (two captured 32-step graphs plus a remainder) stay at FP64 parity."""
+    """140 steps (two captured 64-step graphs plus a remainder) stay at FP64 parity."""
     cfg = inputs.small_2d(precision=0)
     g, o = pair(lb, cfg, region=False)
-    g.step(70)
-    o.step(70)
+    g.step(140)
+    o.step(140)
     compare_lb(g, o, 1e-12)
 
 
@@ -146,12 +146,12 @@ def test_coupled_step_parity_fp64(lb, case):
 
 @pytest.mark.parametrize("case", ["2d", "3d"])
 def test_coupled_run_with_sorting_fp64(lb, case):
-    """100 steps = three 32-step graph chunks, each opening with the particle
+    """150 steps = two 64-step graph chunks, each opening with the particle
     sort, plus a remainder: state still matches the oracle (ids followed)."""
     cfg = inputs.small_2d(precision=0, nx=72) if case == "2d" else inputs.small_3d(precision=0, nx=24)
     g, o = pair(lb, cfg)
-    g.step(100)
-    o.step(100)
+    g.step(150)
+    o.step(150)
     assert np.array_equal(g.get("PART_HOME"), o.get("PART_HOME"))
     assert np.array_equal(g.get("PART_CELL"), o.get("PART_CELL"))
     assert np.array_equal(g.get("CELL_COUNT"), o.get("CELL_COUNT"))
