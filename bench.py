@@ -34,6 +34,15 @@ WORKLOAD = dict(
                 precision=1, feedback=1, window=100, resample_density=0, seed=2),
     region=(896, 1152))
 
+def ensemble_workload():
+    """The 64-replica uneven ensemble of tests/inputs.py (Ny in {16,32,64,128},
+    Nx = 4 Ny, r in {1,2,4}, tau ~ U[0.6,1.2], g ~ U[1e-7,1e-6], 5..20 particles
+    per cell, MPCD on the central Nx/4 columns): 29,056,224 particles and
+    1,626,112 LB nodes in one handle."""
+    from tests import inputs
+    return inputs.ensemble_replicas()
+
+
 METRIC = "coupled_steps_per_s"
 UNIT = "steps/s"
 PROFILE_NOTE = os.path.join(ROOT, "profiles", "ncu_particle_pass_channel2048x512.md")
@@ -308,6 +317,53 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(out), flush=True)
 
 
+def run_ensemble(args):
+    """Secondary measurement: the 64-replica uneven ensemble in one handle
+    (one launch per kernel and step covering every replica, 64-step graphs)."""
+    import torch
+    import __graft_entry__
+    import paper_2004_00304_gb300 as lb
+    __graft_entry__.build()
+    reps = ensemble_workload()
+    if args.fp16:
+        for r in reps:
+            r["params"] = dict(r["params"], precision=2)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        sim = lb.Lbmpcd([r["params"] for r in reps], stream=stream)
+        for k, r in enumerate(reps):
+            sim.set_region(k, *r["region"])
+        sim.step(args.warmup)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        sim.close()
+    sps = args.steps / (ms * 1e-3)
+    nodes = sum(r["params"]["nx"] * (r["params"]["ny"] - 2) for r in reps)
+    parts = sum((r["region"][1] - r["region"][0]) * r["params"]["refine"] * (r["params"]["ny"] - 2) * r["params"]["refine"]
+                * r["params"]["ppc"] for r in reps)
+    cells = sum((r["region"][1] - r["region"][0]) * r["params"]["refine"] * ((r["params"]["ny"] - 2) * r["params"]["refine"] + 1)
+                for r in reps)
+    pop_b = 36 if args.fp16 else 72
+    step_bytes = pop_b * nodes + 40 * parts + 52 * cells
+    peaks = measured_peaks()
+    hbm = float(peaks["hbm_gbs"]) if peaks else 6800.0
+    out = {"metric": METRIC, "value": sps, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f16-storage/f32" if args.fp16 else "f32", "data": "synthetic",
+           "config": {"workload": "ensemble64_uneven_" + ("fp16dev" if args.fp16 else "fp32"), "replicas": len(reps),
+                      "lb_nodes": nodes, "particles": parts},
+           "lb_mlups": nodes * sps / 1e6, "mpcd_mparticle_upd_per_s": parts * sps / 1e6,
+           "step_hbm": {"algorithmic_bytes_per_step": step_bytes, "achieved_gbs": step_bytes * sps / 1e9,
+                        "frac_of_measured": step_bytes * sps / 1e9 / hbm}}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -316,6 +372,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="channel", choices=["channel", "ensemble"],
+                    help="channel: the 2048x512 headline workload; ensemble: the 64-replica ensemble (extra line)")
+    ap.add_argument("--fp16", action="store_true", help="ensemble only: FP16 deviation storage")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -324,6 +383,9 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "ensemble":
+        run_ensemble(args)
         return
     if world > 1:
         import torch

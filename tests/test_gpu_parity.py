@@ -287,3 +287,34 @@ def test_full_size_single_step(lb, name):
     assert rel_err(g.get("PART_VEL").reshape(-1, 3)[ok], o.get("PART_VEL").reshape(-1, 3)[ok]) <= RTOL[prec]
     e = rel_err(g.get("WINDOW_MEAN"), o.get("WINDOW_MEAN"))
     assert e <= RTOL[prec] * 10, e
+
+
+def test_ensemble_64_uneven_replicas_fp32(lb):
+    """The 64-replica uneven ensemble (Ny in {16..128}, Nx = 4 Ny, r in {1,2,4},
+    5..20 particles per cell, distinct seeds) runs in one handle, one launch
+    per kernel and step; a spread of replicas matches independent oracles."""
+    reps = inputs.ensemble_replicas()
+    g = lb.Lbmpcd([r["params"] for r in reps])
+    for k, r in enumerate(reps):
+        g.set_region(k, *r["region"])
+    g.step(2)
+    # the smallest and the largest replica, and one of each (Ny, r) corner
+    picks = {1, 4}
+    for want in ((16, 4), (128, 1), (32, 2), (64, 4)):
+        picks.add(next(k for k, r in enumerate(reps) if (r["params"]["ny"], r["params"]["refine"]) == want))
+    for k in sorted(picks):
+        o = O.OracleSim(reps[k]["params"], replica=k)
+        o.set_region(*reps[k]["region"])
+        o.step(2)
+        dim = 2
+        amb = ambiguous_particles(o, dim, 1e-5)
+        cells_o, cells_g = o.get("PART_CELL"), g.get("PART_CELL", k)
+        bad = set(cells_o[amb]) | set(cells_g[amb])
+        ok = ~np.isin(cells_o, list(bad)) & ~amb
+        assert ok.mean() > 0.95
+        assert np.array_equal(cells_g[ok], cells_o[ok]), k
+        vg = g.get("PART_VEL", k).reshape(-1, 3)[ok]
+        vo = o.get("PART_VEL").reshape(-1, 3)[ok]
+        assert rel_err(vg, vo) <= 1e-5, k
+        for f in ("POPS", "U"):
+            assert rel_err(g.get(f, k), o.get(f), FLOOR.get(f, 0.0)) <= 1e-5, (k, f)
