@@ -225,20 +225,41 @@ template <> struct HomePack<3> {
 
 // Storage of LB populations as deviations d_i = f_i - w_i (rho0 = 1).
 template <typename S> struct Store;
+// 32-bit integer mix (the MurmurHash3 finaliser): the random bits of the
+// stochastic rounding below; not part of the method's random numbers.
+LBM_HD uint32_t mix32(uint32_t x) {
+  x ^= x >> 16; x *= 0x85EBCA6Bu;
+  x ^= x >> 13; x *= 0xC2B2AE35u;
+  x ^= x >> 16;
+  return x;
+}
+
+// binary32 -> binary16 with stochastic rounding: round up with probability
+// (y - down) / (up - down), so that the stored value is unbiased and updates
+// far below one binary16 ulp (the per-step body-force increments) still
+// accumulate.  h = 0 selects round-to-nearest (used when loading a state).
+__device__ __forceinline__ __half sr_half(float y, uint32_t h) {
+  if (h == 0u) return __float2half_rn(y);
+  const __half lo = __float2half_rd(y), hi = __float2half_ru(y);
+  const float flo = __half2float(lo), gap = __half2float(hi) - flo;
+  const float u = (float)(h >> 8) * (1.0f / 16777216.0f);
+  return (gap > 0.0f && u * gap < y - flo) ? hi : lo;
+}
+
 template <> struct Store<double> {
   using R = double;
   __device__ static double ld(const double* p, float) { return *p; }
-  __device__ static void st(double* p, double v, float) { *p = v; }
+  __device__ static void st(double* p, double v, float, uint32_t = 0) { *p = v; }
 };
 template <> struct Store<float> {
   using R = float;
   __device__ static float ld(const float* p, float) { return *p; }
-  __device__ static void st(float* p, float v, float) { *p = v; }
+  __device__ static void st(float* p, float v, float, uint32_t = 0) { *p = v; }
 };
 template <> struct Store<__half> {
   using R = float;   // binary16 holds d_i * scale; arithmetic in binary32
   __device__ static float ld(const __half* p, float inv) { return __half2float(*p) * inv; }
-  __device__ static void st(__half* p, float v, float scale) { *p = __float2half_rn(v * scale); }
+  __device__ static void st(__half* p, float v, float scale, uint32_t h = 0) { *p = sr_half(v * scale, h); }
 };
 
 // Copy a block's descriptor and step record to shared memory (all threads

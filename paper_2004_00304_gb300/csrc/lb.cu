@@ -22,14 +22,14 @@ template <typename S, int V> struct Row;
 template <typename S> struct Row<S, 1> {
   using R = typename Store<S>::R;
   __device__ static void ld(const S* p, R* o, float inv) { o[0] = Store<S>::ld(p, inv); }
-  __device__ static void st(S* p, const R* v, float sc) { Store<S>::st(p, v[0], sc); }
+  __device__ static void st(S* p, const R* v, float sc, uint32_t h) { Store<S>::st(p, v[0], sc, h); }
 };
 template <> struct Row<float, 4> {
   __device__ static void ld(const float* p, float* o, float) {
     const float4 t = *reinterpret_cast<const float4*>(p);
     o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
   }
-  __device__ static void st(float* p, const float* v, float) {
+  __device__ static void st(float* p, const float* v, float, uint32_t) {
     *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
   }
 };
@@ -38,7 +38,7 @@ template <> struct Row<float, 2> {
     const float2 t = *reinterpret_cast<const float2*>(p);
     o[0] = t.x; o[1] = t.y;
   }
-  __device__ static void st(float* p, const float* v, float) {
+  __device__ static void st(float* p, const float* v, float, uint32_t) {
     *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
   }
 };
@@ -47,8 +47,11 @@ template <> struct Row<__half, 2> {
     const float2 a = __half22float2(*reinterpret_cast<const __half2*>(p));
     o[0] = a.x * inv; o[1] = a.y * inv;
   }
-  __device__ static void st(__half* p, const float* v, float sc) {
-    *reinterpret_cast<__half2*>(p) = __floats2half2_rn(v[0] * sc, v[1] * sc);
+  __device__ static void st(__half* p, const float* v, float sc, uint32_t h) {
+    __half2 t;
+    t.x = sr_half(v[0] * sc, h);
+    t.y = sr_half(v[1] * sc, h ? mix32(h + 1u) : 0u);
+    *reinterpret_cast<__half2*>(p) = t;
   }
 };
 template <> struct Row<__half, 4> {
@@ -58,8 +61,12 @@ template <> struct Row<__half, 4> {
     const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&t.y));
     o[0] = a.x * inv; o[1] = a.y * inv; o[2] = b.x * inv; o[3] = b.y * inv;
   }
-  __device__ static void st(__half* p, const float* v, float sc) {
-    const __half2 a = __floats2half2_rn(v[0] * sc, v[1] * sc), b = __floats2half2_rn(v[2] * sc, v[3] * sc);
+  __device__ static void st(__half* p, const float* v, float sc, uint32_t h) {
+    __half2 a, b;
+    a.x = sr_half(v[0] * sc, h);
+    a.y = sr_half(v[1] * sc, h ? mix32(h + 1u) : 0u);
+    b.x = sr_half(v[2] * sc, h ? mix32(h + 2u) : 0u);
+    b.y = sr_half(v[3] * sc, h ? mix32(h + 3u) : 0u);
     uint2 t;
     t.x = *reinterpret_cast<const uint32_t*>(&a);
     t.y = *reinterpret_cast<const uint32_t*>(&b);
@@ -183,8 +190,11 @@ __device__ __forceinline__ void lb_row(const RepDev& rd, const StepInfo& st, con
     }
     mr[v] = rho; mu[0][v] = ux; mu[1][v] = uy; mu[2][v] = uz;
   }
+  // random bits of the binary16 stochastic rounding: per node, population, step
+  const uint32_t hb = sizeof(S) == 2 ? mix32((uint32_t)(row + x0) * 0x9E3779B1u ^ (st.n * 0x632BE5ABu + rd.rep)) : 0u;
 #pragma unroll
-  for (int i = 0; i < Q; ++i) Row<S, V>::st(dst + i * N + row + x0, d[i], scale);
+  for (int i = 0; i < Q; ++i)
+    Row<S, V>::st(dst + i * N + row + x0, d[i], scale, hb ? (mix32(hb + 0x27D4EB2Fu * (uint32_t)i) | 1u) : 0u);
 
   // rho, u: every node on request; otherwise the columns the coupling reads
   // (x0-1 .. x0+cw and x1-cw-1 .. x1, periodic in x).

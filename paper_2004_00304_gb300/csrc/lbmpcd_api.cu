@@ -145,7 +145,10 @@ extern "C" int lbmpcd_create(const lbmpcd_params* params, int n_replicas, void* 
     for (int a = 0; a < 3; ++a) d.g[a] = p.force[a];
     if (h->dim == 2) d.g[2] = 0.0;
     d.nnode = (long long)p.nx * p.ny * p.nz;
-    d.fp16_scale = 1.0f; d.fp16_inv = 1.0f;
+    // binary16 deviations are stored times 2^14: |d| up to ~0.5 stays below the
+    // binary16 maximum and increments down to ~1e-8 stay in its normal range
+    d.fp16_scale = h->prec == P_FP16 ? 16384.0f : 1.0f;
+    d.fp16_inv = 1.0f / d.fp16_scale;
     d.r = p.refine; d.ppc = p.ppc; d.cw = p.coupling_width;
     d.n_out = (p.coupling_width + 1) / 2; d.n_in = p.coupling_width / 2;
     d.feedback = p.feedback; d.window = p.window;

@@ -562,7 +562,8 @@ __device__ __forceinline__ void cell_item(const RepDev& rd, const StepInfo& st, 
   for (int i = 0; i < Q; ++i) {
     const R cu = L::cx(i) * u[0] + L::cy(i) * u[1] + L::cz(i) * u[2];
     const R dev = (R)L::w(i) * ((rl - R(1)) + rl * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu));
-    Store<S>::st(dst + i * rd.nnode + node, dev, rd.fp16_scale);
+    Store<S>::st(dst + i * rd.nnode + node, dev, rd.fp16_scale,
+                 sizeof(S) == 2 ? (mix32((uint32_t)node * 19u + (uint32_t)i + st.n * 0x632BE5ABu) | 1u) : 0u);
   }
 }
 

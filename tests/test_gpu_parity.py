@@ -318,3 +318,47 @@ def test_ensemble_64_uneven_replicas_fp32(lb):
         assert rel_err(vg, vo) <= 1e-5, k
         for f in ("POPS", "U"):
             assert rel_err(g.get(f, k), o.get(f), FLOOR.get(f, 0.0)) <= 1e-5, (k, f)
+
+
+@pytest.mark.parametrize("prec,tol", [(1, 1e-4), (2, 1e-2)])
+def test_steady_poiseuille_reduced_precision(lb, prec, tol):
+    """Binary32 and binary16 deviation storage reach the FP64 oracle's steady
+    Poiseuille profile (g = 1e-6, the ensemble's upper force) within tol
+    (relative L2 of the x-averaged u_x).  Binary16 needs its stochastic
+    rounding here: the per-step force increment w 3 g ~ 3e-7 is below half a
+    binary16 ulp of the deviations, so round-to-nearest would stall the flow."""
+    p = dict(lattice=9, nx=8, ny=18, nz=1, tau=1.0, force=(1e-6, 0.0, 0.0), precision=prec, seed=5)
+    g = lb.Lbmpcd(p)
+    o = O.OracleSim(dict(p, precision=0))
+    g.step(8000)
+    o.step(8000)
+    ug = g.get("U").reshape(3, 18, 8)[0, 1:-1].mean(axis=1)
+    uo = o.get("U").reshape(3, 18, 8)[0, 1:-1].mean(axis=1)
+    err = float(np.linalg.norm(ug - uo) / np.linalg.norm(uo))
+    print(f"precision {prec}: steady-profile relative L2 error {err:.2e}")
+    assert err < tol
+
+
+def test_fp16_coupled_steps(lb):
+    """Binary16 deviation storage (binary32 arithmetic and particles): after
+    three coupled steps the populations are within two binary16 ulps of the
+    largest deviation of the FP64 oracle.  Particle velocities are within 1e-5
+    of their rms plus four binary16 ulps of that deviation: the outer-buffer
+    redraw reads the LB velocity next to the imposed column, whose deviations
+    carry the binary16 rounding."""
+    cfg = inputs.small_2d(precision=2)
+    g, o = pair(lb, cfg)
+    for n in (1, 2):
+        g.step(n)
+        o.step(n)
+        c, w = O.lattice(9)
+        fo = o.get("POPS").reshape(9, -1)
+        dev = np.abs(fo - w[:, None]).max()
+        assert np.abs(g.get("POPS").reshape(9, -1) - fo).max() <= 2.0 ** -9 * dev + 1e-12
+        amb = ambiguous_particles(o, 2, 1e-5)
+        cells_o, cells_g = o.get("PART_CELL"), g.get("PART_CELL")
+        bad = set(cells_o[amb]) | set(cells_g[amb])
+        ok = ~np.isin(cells_o, list(bad)) & ~amb
+        vg = g.get("PART_VEL").reshape(-1, 3)[ok]
+        vo = o.get("PART_VEL").reshape(-1, 3)[ok]
+        assert np.abs(vg - vo).max() <= 1e-5 * np.sqrt(np.mean(vo * vo)) + 2.0 ** -8 * dev
