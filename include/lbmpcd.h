@@ -143,6 +143,15 @@ int lbmpcd_get_fields(lbmpcd* h, int replica, int field, void* dst, size_t bytes
  * INVALID_ARG (field, size, values), STATE (particles before set_region). */
 int lbmpcd_set_state(lbmpcd* h, int replica, int field, const void* src, size_t bytes, int src_on_device);
 
+/* Tensor-core GEMM of the learned closure (not a step of the paper's method):
+ * C[M][N] = alpha * A[M][K] B[N][K]^T + beta * C, A and B bf16 with K
+ * contiguous, C fp32 with row stride N; all device pointers, launched on
+ * `stream` (a cudaStream_t, may be NULL).  M a multiple of 128, N of 16
+ * (<= 4096), K of 64, else INVALID_ARG.  err_dev is a device int set to 1 if
+ * a bounded wait inside the kernel gave up (C then invalid).  Asynchronous. */
+int lbmpcd_tc_gemm_bf16(const void* A, const void* B, float* C, int M, int N, int K, float alpha, float beta,
+                        int* err_dev, void* stream);
+
 /* Element count of a field for a replica (or a negative error code). */
 long long lbmpcd_field_size(const lbmpcd* h, int replica, int field);
 

@@ -66,6 +66,7 @@ def load_library(path: str = LIB_PATH):
     L.lbmpcd_field_size.restype = ctypes.c_longlong
     L.lbmpcd_step_profiled.argtypes = [vp, ci, ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_longlong)]
+    L.lbmpcd_tc_gemm_bf16.argtypes = [vp, vp, vp, ci, ci, ci, ctypes.c_float, ctypes.c_float, vp, vp]
     L.lbmpcd_destroy.argtypes = [vp]
     L.lbmpcd_destroy.restype = None
     L.lbmpcd_last_error.argtypes = [vp]
@@ -76,7 +77,7 @@ def load_library(path: str = LIB_PATH):
 
 EXPORTED = ["lbmpcd_create", "lbmpcd_set_region", "lbmpcd_step", "lbmpcd_step_profiled",
             "lbmpcd_get_fields", "lbmpcd_set_state", "lbmpcd_field_size", "lbmpcd_destroy",
-            "lbmpcd_last_error"]
+            "lbmpcd_last_error", "lbmpcd_tc_gemm_bf16"]
 
 
 def make_params(d: dict) -> lbmpcd_params:
@@ -174,6 +175,19 @@ def lbmpcd_set_state(h, replica: int, field: str, value):
         ptr, nbytes, on_dev = arr.data_ptr(), arr.numel() * arr.element_size(), int(arr.is_cuda)
     _check(h, load_library().lbmpcd_set_state(h, int(replica), FIELDS[field], ctypes.c_void_p(ptr),
                                               nbytes, on_dev))
+
+
+def lbmpcd_tc_gemm_bf16(A, B, C, alpha=1.0, beta=0.0, err=None, stream=None):
+    """C = alpha A B^T + beta C on the tensor cores; A (M, K) and B (N, K) bf16
+    CUDA tensors, C (M, N) float32 CUDA tensor, err an int32 CUDA tensor."""
+    M, K = A.shape
+    N = B.shape[0]
+    sptr = getattr(stream, "cuda_stream", stream) or 0
+    rc = load_library().lbmpcd_tc_gemm_bf16(ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(B.data_ptr()),
+                                             ctypes.c_void_p(C.data_ptr()), M, N, K, float(alpha), float(beta),
+                                             ctypes.c_void_p(err.data_ptr()), ctypes.c_void_p(int(sptr)))
+    if rc != 0:
+        raise LbmpcdError(rc, "tc_gemm_bf16")
 
 
 def lbmpcd_destroy(h):

@@ -23,8 +23,9 @@ SOURCES = {
     "lbmpcd_api.cu": [],
     "lb.cu": [],
     "mpcd.cu": [],
+    "closure.cu": [],
 }
-HEADERS = ["common.cuh", "kernels.h"]
+HEADERS = ["common.cuh", "kernels.h", "tc_gemm.cuh"]
 
 
 def _nvcc() -> str:
