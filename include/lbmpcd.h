@@ -152,6 +152,31 @@ int lbmpcd_set_state(lbmpcd* h, int replica, int field, const void* src, size_t 
 int lbmpcd_tc_gemm_bf16(const void* A, const void* B, float* C, int M, int N, int K, float alpha, float beta,
                         int* err_dev, void* stream);
 
+/* The learned closure network (not in the paper; the MPCD->LB feedback of
+ * the coupled step may use it in place of the long averaging window): a
+ * 3x3 convolutional net 24 -> 64 -> 64 -> 64 -> 3 channels on 16 x 16 patches
+ * of MPCD cells, ReLU between layers, plus the mean of its 8 input frames;
+ * bf16 weights and activations, fp32 accumulation, every contraction on the
+ * tcgen05 tensor cores.  Tensors are fp32, NHWC, device pointers: input
+ * x[P][16][16][24] (frame f, field c at channel 3f + c: density deviation
+ * n/ppc - 1, u_x / sqrt(kT/m), u_y / sqrt(kT/m)), output / target
+ * [P][16][16][3].  Parameters: one fp32 vector, per layer W[cout][3][3][cin]
+ * then b[cout].  All calls synchronise the net's stream; a bounded wait that
+ * gave up inside a kernel returns ERR_TIMEOUT. */
+typedef struct lbmpcd_net lbmpcd_net;
+long long lbmpcd_net_num_params(void);
+int lbmpcd_net_create(int max_patches, void* cuda_stream, lbmpcd_net** out);
+/* which = 0 parameters, 1 gradient of the last backward / train step */
+int lbmpcd_net_get_params(lbmpcd_net* net, float* dst, long long count, int which, int dst_on_device);
+int lbmpcd_net_set_params(lbmpcd_net* net, const float* src, long long count, int src_on_device);
+int lbmpcd_net_forward(lbmpcd_net* net, const float* x_dev, int patches, float* y_dev);
+/* forward, then the MSE loss against t and its parameter gradient */
+int lbmpcd_net_backward(lbmpcd_net* net, const float* x_dev, const float* t_dev, int patches, float* loss_host);
+/* backward plus one Adam step (beta 0.9, 0.999, eps 1e-8) with rate lr */
+int lbmpcd_net_train_step(lbmpcd_net* net, const float* x_dev, const float* t_dev, int patches, float lr,
+                          float* loss_host);
+void lbmpcd_net_destroy(lbmpcd_net* net);
+
 /* Element count of a field for a replica (or a negative error code). */
 long long lbmpcd_field_size(const lbmpcd* h, int replica, int field);
 

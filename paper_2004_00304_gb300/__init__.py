@@ -67,6 +67,17 @@ def load_library(path: str = LIB_PATH):
     L.lbmpcd_step_profiled.argtypes = [vp, ci, ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_longlong)]
     L.lbmpcd_tc_gemm_bf16.argtypes = [vp, vp, vp, ci, ci, ci, ctypes.c_float, ctypes.c_float, vp, vp]
+    ll, fp = ctypes.c_longlong, ctypes.POINTER(ctypes.c_float)
+    L.lbmpcd_net_num_params.restype = ll
+    L.lbmpcd_net_num_params.argtypes = []
+    L.lbmpcd_net_create.argtypes = [ci, vp, ctypes.POINTER(vp)]
+    L.lbmpcd_net_get_params.argtypes = [vp, vp, ll, ci, ci]
+    L.lbmpcd_net_set_params.argtypes = [vp, vp, ll, ci]
+    L.lbmpcd_net_forward.argtypes = [vp, vp, ci, vp]
+    L.lbmpcd_net_backward.argtypes = [vp, vp, vp, ci, fp]
+    L.lbmpcd_net_train_step.argtypes = [vp, vp, vp, ci, ctypes.c_float, fp]
+    L.lbmpcd_net_destroy.argtypes = [vp]
+    L.lbmpcd_net_destroy.restype = None
     L.lbmpcd_destroy.argtypes = [vp]
     L.lbmpcd_destroy.restype = None
     L.lbmpcd_last_error.argtypes = [vp]
@@ -77,7 +88,9 @@ def load_library(path: str = LIB_PATH):
 
 EXPORTED = ["lbmpcd_create", "lbmpcd_set_region", "lbmpcd_step", "lbmpcd_step_profiled",
             "lbmpcd_get_fields", "lbmpcd_set_state", "lbmpcd_field_size", "lbmpcd_destroy",
-            "lbmpcd_last_error", "lbmpcd_tc_gemm_bf16"]
+            "lbmpcd_last_error", "lbmpcd_tc_gemm_bf16", "lbmpcd_net_num_params", "lbmpcd_net_create",
+            "lbmpcd_net_get_params", "lbmpcd_net_set_params", "lbmpcd_net_forward", "lbmpcd_net_backward",
+            "lbmpcd_net_train_step", "lbmpcd_net_destroy"]
 
 
 def make_params(d: dict) -> lbmpcd_params:
@@ -193,6 +206,63 @@ def lbmpcd_tc_gemm_bf16(A, B, C, alpha=1.0, beta=0.0, err=None, stream=None):
 def lbmpcd_destroy(h):
     if h:
         load_library().lbmpcd_destroy(h)
+
+
+class Net:
+    """The learned closure network (device tensors are torch CUDA tensors)."""
+
+    def __init__(self, max_patches: int, stream=None):
+        L = load_library()
+        h = ctypes.c_void_p()
+        sptr = getattr(stream, "cuda_stream", stream) or 0
+        rc = L.lbmpcd_net_create(int(max_patches), ctypes.c_void_p(int(sptr)), ctypes.byref(h))
+        if rc != 0:
+            raise LbmpcdError(rc, "net_create")
+        self._h = h
+        self.n = int(L.lbmpcd_net_num_params())
+
+    def _rc(self, rc, what):
+        if rc != 0:
+            raise LbmpcdError(rc, what)
+
+    def set_params(self, theta):
+        arr = np.ascontiguousarray(theta, dtype=np.float32)
+        self._rc(load_library().lbmpcd_net_set_params(self._h, arr.ctypes.data, arr.size, 0), "set_params")
+
+    def get_params(self, which: int = 0) -> np.ndarray:
+        out = np.empty(self.n, dtype=np.float32)
+        self._rc(load_library().lbmpcd_net_get_params(self._h, out.ctypes.data, out.size, which, 0), "get_params")
+        return out
+
+    def forward(self, x, y):
+        P = x.shape[0]
+        self._rc(load_library().lbmpcd_net_forward(self._h, ctypes.c_void_p(x.data_ptr()), P,
+                                                   ctypes.c_void_p(y.data_ptr())), "forward")
+
+    def backward(self, x, t) -> float:
+        loss = ctypes.c_float()
+        self._rc(load_library().lbmpcd_net_backward(self._h, ctypes.c_void_p(x.data_ptr()),
+                                                    ctypes.c_void_p(t.data_ptr()), x.shape[0],
+                                                    ctypes.byref(loss)), "backward")
+        return float(loss.value)
+
+    def train_step(self, x, t, lr: float) -> float:
+        loss = ctypes.c_float()
+        self._rc(load_library().lbmpcd_net_train_step(self._h, ctypes.c_void_p(x.data_ptr()),
+                                                      ctypes.c_void_p(t.data_ptr()), x.shape[0], float(lr),
+                                                      ctypes.byref(loss)), "train_step")
+        return float(loss.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load_library().lbmpcd_net_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Lbmpcd:
