@@ -177,6 +177,33 @@ int lbmpcd_net_train_step(lbmpcd_net* net, const float* x_dev, const float* t_de
                           float* loss_host);
 void lbmpcd_net_destroy(lbmpcd_net* net);
 
+/* Allocation-free network forward (no counterpart in the paper): the same
+ * output as lbmpcd_net_forward for parameters theta_dev (device fp32, the
+ * layout above), input x_dev and output y_dev (device fp32), with every piece
+ * of scratch in one device array of the library (about 4 MiB) reserved when
+ * the module loads.  No call allocates or frees device or host memory, which
+ * is what a caller needs that already holds nearly all of the GPU's memory in
+ * its own pool (a PyTorch caching allocator, a solver that reserves HBM up
+ * front) and so cannot risk a hidden cudaMalloc failing, or that steps in a
+ * loop where cudaMalloc / cudaFree may synchronise the device.
+ *  - patches in [1, LBMPCD_NET_STATIC_MAX_PATCHES], else ERR_CAPACITY (larger
+ *    batches: call once per slice of at most that many patches); NULL
+ *    pointers or patches < 1: ERR_INVALID_ARG.
+ *  - Runs on `stream` (a cudaStream_t, may be NULL) and synchronises it
+ *    before returning; a bounded wait that gave up returns ERR_TIMEOUT.
+ *  - The scratch's error word must be zero when the GEMMs start: each call
+ *    clears it itself, first on its stream.  Nothing else in the scratch is
+ *    read before the call writes it, so no state carries between calls.
+ *  - The first call on a device looks up the scratch address
+ *    (cudaGetSymbolAddress) and sets the GEMM kernels' shared-memory limit:
+ *    make it with that device current, before any stream capture begins.
+ *  - One scratch per device: calls that overlap in time on the same device
+ *    (two host threads, or two streams) race on it and give wrong results;
+ *    serialise them. */
+#define LBMPCD_NET_STATIC_MAX_PATCHES 8
+int lbmpcd_net_forward_noalloc(const float* theta_dev, const float* x_dev, int patches, float* y_dev,
+                               void* cuda_stream);
+
 /* Element count of a field for a replica (or a negative error code). */
 long long lbmpcd_field_size(const lbmpcd* h, int replica, int field);
 

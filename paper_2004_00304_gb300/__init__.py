@@ -77,6 +77,7 @@ def load_library(path: str = LIB_PATH):
     L.lbmpcd_net_backward.argtypes = [vp, vp, vp, ci, fp]
     L.lbmpcd_net_train_step.argtypes = [vp, vp, vp, ci, ctypes.c_float, fp]
     L.lbmpcd_net_destroy.argtypes = [vp]
+    L.lbmpcd_net_forward_noalloc.argtypes = [vp, vp, ci, vp, vp]
     L.lbmpcd_net_destroy.restype = None
     L.lbmpcd_destroy.argtypes = [vp]
     L.lbmpcd_destroy.restype = None
@@ -90,7 +91,7 @@ EXPORTED = ["lbmpcd_create", "lbmpcd_set_region", "lbmpcd_step", "lbmpcd_step_pr
             "lbmpcd_get_fields", "lbmpcd_set_state", "lbmpcd_field_size", "lbmpcd_destroy",
             "lbmpcd_last_error", "lbmpcd_tc_gemm_bf16", "lbmpcd_net_num_params", "lbmpcd_net_create",
             "lbmpcd_net_get_params", "lbmpcd_net_set_params", "lbmpcd_net_forward", "lbmpcd_net_backward",
-            "lbmpcd_net_train_step", "lbmpcd_net_destroy"]
+            "lbmpcd_net_train_step", "lbmpcd_net_destroy", "lbmpcd_net_forward_noalloc"]
 
 
 def make_params(d: dict) -> lbmpcd_params:
@@ -201,6 +202,21 @@ def lbmpcd_tc_gemm_bf16(A, B, C, alpha=1.0, beta=0.0, err=None, stream=None):
                                              ctypes.c_void_p(err.data_ptr()), ctypes.c_void_p(int(sptr)))
     if rc != 0:
         raise LbmpcdError(rc, "tc_gemm_bf16")
+
+
+NET_STATIC_MAX_PATCHES = 8   # LBMPCD_NET_STATIC_MAX_PATCHES
+
+
+def lbmpcd_net_forward_noalloc(theta, x, y, stream=None):
+    """Network forward with the library's static scratch (no allocation):
+    theta (n_params,) float32, x (P, 16, 16, 24) and y (P, 16, 16, 3) float32
+    CUDA tensors, P <= NET_STATIC_MAX_PATCHES."""
+    sptr = getattr(stream, "cuda_stream", stream) or 0
+    rc = load_library().lbmpcd_net_forward_noalloc(ctypes.c_void_p(theta.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                                                    int(x.shape[0]), ctypes.c_void_p(y.data_ptr()),
+                                                    ctypes.c_void_p(int(sptr)))
+    if rc != 0:
+        raise LbmpcdError(rc, "net_forward_noalloc")
 
 
 def lbmpcd_destroy(h):

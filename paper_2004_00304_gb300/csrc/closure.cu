@@ -6,6 +6,7 @@
 #include <cuda_bf16.h>
 #include <math.h>
 
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -397,4 +398,99 @@ extern "C" int lbmpcd_net_train_step(lbmpcd_net* n, const float* x_dev, const fl
   n->weights_dirty = true;
   if (loss && cudaMemcpyAsync(loss, n->loss, 4, cudaMemcpyDeviceToHost, n->st) != cudaSuccess) return LBMPCD_ERR_CUDA;
   return net_check_err(n);
+}
+
+// ===========================================================================
+// Allocation-free network forward.  All scratch (bf16 weights, activations,
+// the im2col matrix, the fp32 GEMM output, the GEMM error word) lives in one
+// file-scope device array reserved when the module loads, so a call performs
+// no cudaMalloc / cudaFree.  Layout, each slot a multiple of 256 bytes, for
+// Mp = NET_STATIC_MAX_PATCHES * 256 rows:
+//   err word (256) | per layer l: W npad x kpad, WT kpad x 64, act Mp x cin
+//   (bf16) | z Mp x 64 fp32 (reused by every layer) | col Mp x 576 bf16
+namespace lbm {
+constexpr int NET_STATIC_MAX_PATCHES = LBMPCD_NET_STATIC_MAX_PATCHES;
+constexpr long long NS_MP = (long long)NET_STATIC_MAX_PATCHES * 256;
+constexpr long long ns_round(long long b) { return (b + 255) / 256 * 256; }
+// layer widths as constants for sizing the array (the carve below checks them against layer())
+constexpr int NS_CIN[NL] = {24, 64, 64, 64}, NS_COUT[NL] = {64, 64, 64, 3};
+constexpr long long ns_kpad(int l) { return (9LL * NS_CIN[l] + 63) / 64 * 64; }
+constexpr long long ns_npad(int l) { return NS_COUT[l] < 16 ? 16 : NS_COUT[l]; }
+constexpr long long ns_layer_bytes(int l) {
+  return ns_round(ns_npad(l) * ns_kpad(l) * 2) + ns_round(ns_kpad(l) * 64 * 2) + ns_round(NS_MP * NS_CIN[l] * 2);
+}
+constexpr long long NS_Z_BYTES = ns_round(NS_MP * 64 * 4);
+constexpr long long NS_COL_BYTES = ns_round(NS_MP * 576 * 2);
+constexpr long long NS_BYTES = 256 + ns_layer_bytes(0) + ns_layer_bytes(1) + ns_layer_bytes(2) + ns_layer_bytes(3) +
+                               NS_Z_BYTES + NS_COL_BYTES;
+static_assert(NS_BYTES <= 5LL * 1024 * 1024, "static network scratch stays modest");
+
+static __device__ __align__(256) unsigned char g_net_scratch[NS_BYTES];
+
+// device address of g_net_scratch on the current device, looked up once per device
+static cudaError_t net_scratch_base(unsigned char** out) {
+  static std::mutex mu;
+  static unsigned char* base[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> g(mu);
+  if (!base[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_net_scratch);
+    if (e != cudaSuccess) return e;
+    base[dev] = (unsigned char*)p;
+  }
+  *out = base[dev];
+  return cudaSuccess;
+}
+}  // namespace lbm
+
+extern "C" int lbmpcd_net_forward_noalloc(const float* theta_dev, const float* x_dev, int patches, float* y_dev,
+                                          void* stream) {
+  using namespace lbm;
+  if (!theta_dev || !x_dev || !y_dev || patches < 1) return LBMPCD_ERR_INVALID_ARG;
+  if (patches > NET_STATIC_MAX_PATCHES) return LBMPCD_ERR_CAPACITY;
+  unsigned char* s = nullptr;
+  if (net_scratch_base(&s) != cudaSuccess) return LBMPCD_ERR_CUDA;
+  cudaStream_t st = (cudaStream_t)stream;
+  int* err = (int*)s;
+  unsigned char* q = s + 256;
+  __nv_bfloat16 *W[NL], *WT[NL], *act[NL];
+  for (int l = 0; l < NL; ++l) {
+    const NetLayer L = layer(l);
+    if (L.cin != NS_CIN[l] || L.cout != NS_COUT[l] || L.kpad != ns_kpad(l) || L.npad != ns_npad(l))
+      return LBMPCD_ERR_INVALID_ARG;   // the array was sized for another network
+    W[l] = (__nv_bfloat16*)q; q += ns_round(ns_npad(l) * ns_kpad(l) * 2);
+    WT[l] = (__nv_bfloat16*)q; q += ns_round(ns_kpad(l) * 64 * 2);
+    act[l] = (__nv_bfloat16*)q; q += ns_round(NS_MP * NS_CIN[l] * 2);
+  }
+  float* z = (float*)q;
+  q += NS_Z_BYTES;
+  __nv_bfloat16* col = (__nv_bfloat16*)q;
+
+  // the error word is the only scratch read before this call writes it
+  if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) return LBMPCD_ERR_CUDA;
+  const int M = patches * 256;   // a patch is two 128-row tiles: no padding rows
+  for (int l = 0; l < NL; ++l) {
+    const NetLayer L = layer(l);
+    k_cast_weights<<<nblk((long long)(L.npad > 64 ? L.npad : 64) * L.kpad), 256, 0, st>>>(theta_dev, L, W[l], WT[l]);
+  }
+  k_input<<<nblk((long long)M * 24), 256, 0, st>>>(x_dev, M, M, act[0]);
+  for (int l = 0; l < NL; ++l) {
+    const NetLayer L = layer(l);
+    const long long tq = (long long)M * (L.kpad / 8);
+    if (L.cin == 24) k_im2col<24><<<nblk(tq), 256, 0, st>>>(act[l], M, M, L.kpad, col);
+    else k_im2col<64><<<nblk(tq), 256, 0, st>>>(act[l], M, M, L.kpad, col);
+    if (tc_gemm(col, W[l], z, M, L.npad, L.kpad, L.npad, 1.0f, 0.0f, err, st) != cudaSuccess) return LBMPCD_ERR_CUDA;
+    const bool last = l == NL - 1;
+    k_epilogue<<<nblk((long long)M * L.cout), 256, 0, st>>>(z, theta_dev, L, M, last ? 1 : 0,
+                                                           last ? nullptr : act[l + 1], x_dev, y_dev);
+  }
+  if (cudaGetLastError() != cudaSuccess) return LBMPCD_ERR_CUDA;
+  int e = 0;
+  if (cudaMemcpyAsync(&e, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return LBMPCD_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return LBMPCD_ERR_CUDA;
+  return e ? LBMPCD_ERR_TIMEOUT : LBMPCD_OK;
 }
