@@ -24,7 +24,8 @@ _SO = os.path.join(_HERE, "_build", "liboracle.so")
 _lib = None
 
 FIELDS = dict(RHO=0, U=1, POPS=2, PART_POS=3, PART_VEL=4, PART_CELL=5, SHIFT=6,
-              CELL_COUNT=7, WINDOW_MEAN=8, DIAG=9, PART_HOME=10, CELL_VCM=11, PART_ID=12)
+              CELL_COUNT=7, WINDOW_MEAN=8, DIAG=9, PART_HOME=10, CELL_VCM=11, PART_ID=12,
+              CLOSURE_IN=13, CLOSURE_TARGET=15)
 _INT_FIELDS = {"PART_CELL", "CELL_COUNT", "PART_HOME", "PART_ID"}
 
 
@@ -81,6 +82,9 @@ def lib():
         L.orc_srd_rotate_3d.argtypes = [vp, vp, vp, ctypes.c_double, vp]
         L.orc_random_axis.argtypes = [ctypes.c_uint32, ctypes.c_uint32, vp]
         L.orc_u_fine.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp]
+        L.orc_closure_patches.restype = ctypes.c_long
+        L.orc_closure_patches.argtypes = [vp]
+        L.orc_closure_impose.argtypes = [vp, vp]
         _lib = L
     return _lib
 
@@ -148,6 +152,30 @@ class OracleSim:
         out = np.zeros(3)
         lib().orc_u_fine(self._h, int(X), int(Y), int(Z), out.ctypes.data)
         return out
+
+    @property
+    def closure_patches(self) -> int:
+        return int(lib().orc_closure_patches(self._h))
+
+    def closure_impose(self, y) -> None:
+        """a8 of the learned closure for the step just taken, from the network
+        output y of shape (P, 16, 16, 3)."""
+        arr = np.ascontiguousarray(y, dtype=np.float64).ravel()
+        if arr.size != self.closure_patches * 768:
+            raise ValueError("closure output has the wrong size")
+        if lib().orc_closure_impose(self._h, arr.ctypes.data) != 0:
+            raise ValueError("no closure sampling on this replica")
+
+    def step_with_closure(self, theta, n: int = 1) -> None:
+        """n steps with the learned closure in the loop: after each step the
+        network (oracle/closure.py, bf16 rounding emulated as on the GPU)
+        maps the step's input to the imposed fields."""
+        from . import closure
+        for _ in range(int(n)):
+            self.step(1)
+            x = self.get("CLOSURE_IN").reshape(-1, 16, 16, 24)
+            y, _ = closure.forward(np.asarray(theta, dtype=np.float64), x, emulate_bf16=True)
+            self.closure_impose(y)
 
     def set(self, field: str, value) -> None:
         fid = FIELDS[field]

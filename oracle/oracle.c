@@ -142,7 +142,19 @@ struct orc_sim {
   double *frames;                     /* [W][nbuf][4] ring of per-step samples */
   double *wmean;                      /* [nbuf][4] rho_bar, u_bar of last step */
   long nframes;                       /* frames written so far */
+  /* learned closure (feedback = 2): strips of CL_W fine columns per side */
+  int cl_on, cl_npy;                  /* patches per side: ceil(Hy / 16) */
+  long cl_ncell;                      /* 2 Hy CL_W strip cells */
+  double *cl_frame;                   /* [ncl][3] count, sum vx, sum vy of this step */
+  double *cl_hist;                    /* [8][ncl][3] fields of the last 8 steps, oldest first */
+  double *cl_ema;                     /* [ncl][3] exponential moving average */
+  double *cl_x;                       /* [P][16][16][24] network input */
+  long cl_nframes;
 };
+
+#define CL_W 16          /* strip width and patch side, fine cells */
+#define CL_FRAMES 8      /* frames in the network input */
+#define CL_EMA_T 500.0   /* moving-average time constant, steps */
 
 static void draw(const orc_sim* s, uint32_t id, uint32_t step, uint32_t tag, uint32_t w[4]) {
   uint32_t ctr[4] = {id, step, (uint32_t)s->replica, tag};
@@ -187,6 +199,7 @@ void orc_destroy(orc_sim* s) {
   free(s->f); free(s->fn); free(s->rho); free(s->u);
   free(s->home); free(s->off); free(s->vel); free(s->pcell);
   free(s->cnt); free(s->sumv); free(s->vcm); free(s->frames); free(s->wmean);
+  free(s->cl_frame); free(s->cl_hist); free(s->cl_ema); free(s->cl_x);
   free(s);
 }
 
@@ -218,6 +231,19 @@ int orc_set_region(orc_sim* s, int x0, int x1) {
   int W = p->window > 0 ? p->window : 1;
   s->frames = (double*)calloc((size_t)W * (s->nbuf > 0 ? s->nbuf : 1) * 4, sizeof(double));
   s->wmean = (double*)calloc((size_t)(s->nbuf > 0 ? s->nbuf : 1) * 4, sizeof(double));
+  if (p->feedback == 2) {
+    /* the closure needs two disjoint strips, 16 rows, an inner column inside
+       the strip and a thermal velocity to scale by */
+    if (s->dim != 2 || s->Wx < 2 * CL_W || s->Hy < CL_W || cw * s->r > CL_W || !(p->kT > 0)) return -1;
+    s->cl_on = 1;
+    s->cl_npy = (s->Hy + CL_W - 1) / CL_W;
+    s->cl_ncell = 2L * s->Hy * CL_W;
+    s->cl_frame = (double*)calloc((size_t)s->cl_ncell * 3, sizeof(double));
+    s->cl_hist = (double*)calloc((size_t)CL_FRAMES * s->cl_ncell * 3, sizeof(double));
+    s->cl_ema = (double*)calloc((size_t)s->cl_ncell * 3, sizeof(double));
+    s->cl_x = (double*)calloc((size_t)2 * s->cl_npy * CL_W * CL_W * 3 * CL_FRAMES, sizeof(double));
+    s->cl_nframes = 0;
+  }
   double sig = sqrt(p->kT / p->mass);
   for (long k = 0; k < s->np; ++k) {
     long cell = k / p->ppc;
@@ -562,6 +588,110 @@ static void impose(orc_sim* s) {
   }
 }
 
+/* ------------------------------------------------------------------------ */
+/* Learned closure (feedback = 2, D2Q9; not in the paper).
+ *
+ * Strips: on each x-side, the CL_W fine columns nearest the region's edge;
+ * xi = distance from the edge in fine cells (left: xi = X; right:
+ * xi = Wx - 1 - X, the right strip seen in a mirror, so its u_x changes sign).
+ * Strip cell c = (side Hy + Y) CL_W + xi.
+ * Fields of one step, per strip cell, from the particles whose (unshifted)
+ * home cell is c after streaming (the same instant as a6):
+ *   phi_0 = n / ppc - 1,  phi_1 = +-(sum v_x / n) / sqrt(kT/m),
+ *   phi_2 = (sum v_y / n) / sqrt(kT/m)   (velocities 0 in an empty cell).
+ * Patches: side-major, ceil(Hy/16) per side; patch py covers rows
+ * 16 py .. 16 py + 15, the last one rows Hy - 16 .. Hy - 1 (it may overlap the
+ * one before).  Input pixel (row, xi) of a patch, channel 3 f + k = phi_k of
+ * the f-th of the last 8 steps, oldest first (zeros for steps before 0).
+ * Target: exponential moving average e <- e + (phi - e) / 500, e = phi at the
+ * first frame (time constant 500 steps: the mean lag and the white-noise
+ * variance of a 1000-step trailing mean). */
+static long cl_row0(const orc_sim* s, int py) {
+  return py == s->cl_npy - 1 ? s->Hy - CL_W : (long)CL_W * py;
+}
+
+static void closure_sample(orc_sim* s) {
+  const long ncl = s->cl_ncell;
+  memset(s->cl_frame, 0, sizeof(double) * ncl * 3);
+  for (long k = 0; k < s->np; ++k) {
+    int X = s->home[3*k], Y = s->home[3*k+1], side, xi;
+    if (X < CL_W) { side = 0; xi = X; }
+    else if (X >= s->Wx - CL_W) { side = 1; xi = s->Wx - 1 - X; }
+    else continue;
+    long c = ((long)side * s->Hy + Y) * CL_W + xi;
+    s->cl_frame[3*c] += 1.0;
+    s->cl_frame[3*c+1] += s->vel[3*k];
+    s->cl_frame[3*c+2] += s->vel[3*k+1];
+  }
+  /* drop the oldest frame, append this one */
+  memmove(s->cl_hist, s->cl_hist + ncl * 3, sizeof(double) * (CL_FRAMES - 1) * ncl * 3);
+  double* nw = s->cl_hist + (size_t)(CL_FRAMES - 1) * ncl * 3;
+  double sig = sqrt(s->p.kT / s->p.mass);
+  for (long c = 0; c < ncl; ++c) {
+    double n = s->cl_frame[3*c];
+    double mirror = c >= (long)s->Hy * CL_W ? -1.0 : 1.0;
+    double phi[3];
+    phi[0] = n / (double)s->p.ppc - 1.0;
+    phi[1] = n > 0 ? mirror * ((s->cl_frame[3*c+1] / n) / sig) : 0.0;
+    phi[2] = n > 0 ? (s->cl_frame[3*c+2] / n) / sig : 0.0;
+    for (int k = 0; k < 3; ++k) {
+      nw[3*c+k] = phi[k];
+      if (s->cl_nframes == 0) s->cl_ema[3*c+k] = phi[k];
+      else s->cl_ema[3*c+k] += (phi[k] - s->cl_ema[3*c+k]) / CL_EMA_T;
+    }
+  }
+  s->cl_nframes++;
+  /* lay the history out as the network input */
+  for (int pch = 0; pch < 2 * s->cl_npy; ++pch) {
+    int side = pch / s->cl_npy, py = pch % s->cl_npy;
+    long row0 = cl_row0(s, py);
+    for (int y = 0; y < CL_W; ++y)
+      for (int x = 0; x < CL_W; ++x) {
+        long c = ((long)side * s->Hy + row0 + y) * CL_W + x;
+        double* px = s->cl_x + (((size_t)pch * CL_W + y) * CL_W + x) * 3 * CL_FRAMES;
+        for (int f = 0; f < CL_FRAMES; ++f)
+          for (int k = 0; k < 3; ++k) px[3*f+k] = s->cl_hist[((size_t)f * ncl + c) * 3 + k];
+      }
+  }
+}
+
+long orc_closure_patches(const orc_sim* s) { return s->cl_on ? 2L * s->cl_npy : 0; }
+
+/* Imposition from the network output: on each inner-buffer LB node, u_bar =
+ * sqrt(kT/m) times the mean predicted velocity over the node's r x r fine
+ * cells (u_x mirrored back on the right side); the stored post-collision
+ * populations become f_eq(rho_LB, u_bar), rho_LB the node's LB density of
+ * the step (the MPCD density is not imposed, as in a8).  Fine cell (row, xi)
+ * is read from patch min(row / 16, npy - 1) of its side. */
+int orc_closure_impose(orc_sim* s, const double* y) {
+  const orc_params* p = &s->p;
+  if (!s->cl_on) return -1;
+  if (s->cl_nframes < CL_FRAMES) return 0;
+  double sig = sqrt(p->kT / p->mass);
+  for (int side = 0; side < 2; ++side)
+    for (int col = 0; col < s->n_in; ++col)
+      for (int yn = 1; yn < p->ny - 1; ++yn) {
+        double su[2] = {0, 0};
+        for (int a = 0; a < s->r; ++a)
+          for (int b = 0; b < s->r; ++b) {
+            int row = (yn - 1) * s->r + a, xi = (s->n_out + col) * s->r + b;
+            int py = row / CL_W < s->cl_npy - 1 ? row / CL_W : s->cl_npy - 1;
+            long pch = (long)side * s->cl_npy + py;
+            long m = (pch * CL_W + (row - cl_row0(s, py))) * CL_W + xi;
+            su[0] += y[3*m+1]; su[1] += y[3*m+2];
+          }
+        double u[3];
+        u[0] = (side ? -1.0 : 1.0) * sig * su[0] / (double)(s->r * s->r);
+        u[1] = sig * su[1] / (double)(s->r * s->r);
+        u[2] = 0.0;
+        int x = side == 0 ? s->x0 + s->n_out + col : s->x1 - 1 - s->n_out - col;
+        double feq[19];
+        orc_feq(p->lattice, s->rho[nidx(s, x, yn, 0)], u, feq);
+        for (int i = 0; i < s->q; ++i) s->f[i * s->nnode + nidx(s, x, yn, 0)] = feq[i];
+      }
+  return 0;
+}
+
 void orc_u_fine(const orc_sim* s, int X, int Y, int Z, double out[3]) { u_fine(s, X, Y, Z, out); }
 
 int orc_step(orc_sim* s, int nsteps) {
@@ -571,6 +701,7 @@ int orc_step(orc_sim* s, int nsteps) {
       resample(s);                    /* a2 + a3 */
       stream(s);                      /* a4 */
       sample_inner(s);                /* a6 */
+      if (s->cl_on) closure_sample(s);  /* closure input of the same instant */
       shift_and_bin(s);               /* a5 */
       collide(s);                     /* a7 */
       impose(s);                      /* a8 */
@@ -593,6 +724,8 @@ long orc_field_size(const orc_sim* s, int field) {
     case ORC_CELL_VCM: return 3 * s->ncell;
     case ORC_WINDOW_MEAN: return 4 * s->nbuf;
     case ORC_DIAG: return 9;
+    case ORC_CLOSURE_IN: return s->cl_on ? 2L * s->cl_npy * CL_W * CL_W * 3 * CL_FRAMES : -1;
+    case ORC_CLOSURE_TARGET: return s->cl_on ? 2L * s->cl_npy * CL_W * CL_W * 3 : -1;
   }
   return -1;
 }
@@ -635,6 +768,17 @@ int orc_get_field(const orc_sim* s, int field, void* dst) {
     case ORC_CELL_VCM: memcpy(D, s->vcm, sizeof(double) * n); break;
     case ORC_WINDOW_MEAN: memcpy(D, s->wmean, sizeof(double) * n); break;
     case ORC_DIAG: diag(s, D); break;
+    case ORC_CLOSURE_IN: memcpy(D, s->cl_x, sizeof(double) * n); break;
+    case ORC_CLOSURE_TARGET:
+      for (int pch = 0; pch < 2 * s->cl_npy; ++pch) {
+        int side = pch / s->cl_npy, py = pch % s->cl_npy;
+        for (int y = 0; y < CL_W; ++y)
+          for (int x = 0; x < CL_W; ++x) {
+            long c = ((long)side * s->Hy + cl_row0(s, py) + y) * CL_W + x;
+            for (int k = 0; k < 3; ++k) D[(((long)pch * CL_W + y) * CL_W + x) * 3 + k] = s->cl_ema[3*c+k];
+          }
+      }
+      break;
     default: return -1;
   }
   return 0;

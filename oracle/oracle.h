@@ -21,6 +21,12 @@
  *       particles in wall-cut cells;
  *   a8  MPCD->LB imposition of equilibrium populations built from the
  *       windowed cell moments on the inner buffer column.
+ * With feedback = 2 (D2Q9 only; not in the paper) a8 is replaced by the
+ * learned closure: each step records the instantaneous fine-cell fields of
+ * the two 16-column strips at the region's x-edges, keeps the last 8 of them
+ * and their exponential moving average, and lays them out as the network's
+ * 16 x 16 patches; orc_closure_impose then imposes f_eq from a network
+ * output that the caller computes (oracle/closure.py).
  * All random numbers come from Philox4x32-10 keyed by (seed) with counter
  * (id, step, replica, tag); every floating-point step is IEEE binary64.
  */
@@ -43,7 +49,9 @@ typedef struct {
   double kT, mass;      /* thermal energy and particle mass (LB units) */
   int coupling_width;   /* LB columns of coupling buffer per side */
   int precision;        /* 0 FP64, 1 FP32, 2 FP16 deviations: decides binning precision only */
-  int feedback;         /* 0 one-way (the paper), 1 windowed MPCD->LB imposition */
+  int feedback;         /* 0 one-way (the paper), 1 windowed MPCD->LB imposition,
+                           2 learned closure (sampling here, imposition by
+                           orc_closure_impose) */
   int window;           /* averaging window W in steps */
   int resample_density; /* must be 0 in the oracle */
   uint64_t seed;
@@ -55,7 +63,9 @@ typedef struct orc_sim orc_sim;
 enum {
   ORC_RHO = 0, ORC_U = 1, ORC_POPS = 2, ORC_PART_POS = 3, ORC_PART_VEL = 4,
   ORC_PART_CELL = 5, ORC_SHIFT = 6, ORC_CELL_COUNT = 7, ORC_WINDOW_MEAN = 8,
-  ORC_DIAG = 9, ORC_PART_HOME = 10, ORC_CELL_VCM = 11, ORC_PART_ID = 12
+  ORC_DIAG = 9, ORC_PART_HOME = 10, ORC_CELL_VCM = 11, ORC_PART_ID = 12,
+  ORC_CLOSURE_IN = 13,      /* [P][16][16][24] network input of the last step */
+  ORC_CLOSURE_TARGET = 15   /* [P][16][16][3] moving averages, patch layout */
 };
 
 orc_sim* orc_create(const orc_params* p, int replica);
@@ -67,6 +77,12 @@ int  orc_set_field(orc_sim* s, int field, const void* src);
 void orc_destroy(orc_sim* s);
 long orc_num_particles(const orc_sim* s);
 long orc_step_count(const orc_sim* s);
+/* Closure patches per replica (0 unless feedback = 2 with a region). */
+long orc_closure_patches(const orc_sim* s);
+/* a8 of the learned closure for the step just completed: y [P][16][16][3]
+ * is the network output in patch layout.  No-op before 8 frames exist.
+ * Returns -1 if the replica has no closure sampling. */
+int  orc_closure_impose(orc_sim* s, const double* y);
 
 /* building blocks exposed for the pin tests */
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
