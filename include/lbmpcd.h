@@ -70,6 +70,11 @@ enum {
  *  PART_HOME [np][3] (int32)              integer home cell of each particle
  *  CELL_VCM [ncell][3] (double)           centre-of-mass velocity of the last collision
  *  PART_ID [np] (int32)                   identity: particle fields come back in id order
+ *  CLOSURE_IN [P][16][16][24] (double)    learned-closure network input of the last step
+ *  CLOSURE_OUT [P][16][16][3] (double)    network output of the last step (with parameters)
+ *  CLOSURE_TARGET [P][16][16][3] (double) moving averages of the strip fields (training target)
+ *                                         -- the three CLOSURE fields exist with feedback = 2;
+ *                                         P = 2 ceil(Hy/16) patches, see lbmpcd_set_closure
  * Collision cells: ncell = Wx (Hy+1) Wz, id = cx + Wx (cy + (Hy+1) cz), with
  * Wx = (x1-x0) refine, Hy = (ny-2) refine, Wz = nz refine (1 in 2D).
  * Inner buffer nodes: nbuf = 2 * floor(cw/2) * (ny-2) * nz, index
@@ -77,7 +82,8 @@ enum {
 enum {
   LBMPCD_RHO = 0, LBMPCD_U = 1, LBMPCD_POPS = 2, LBMPCD_PART_POS = 3, LBMPCD_PART_VEL = 4,
   LBMPCD_PART_CELL = 5, LBMPCD_SHIFT = 6, LBMPCD_CELL_COUNT = 7, LBMPCD_WINDOW_MEAN = 8,
-  LBMPCD_DIAG = 9, LBMPCD_PART_HOME = 10, LBMPCD_CELL_VCM = 11, LBMPCD_PART_ID = 12
+  LBMPCD_DIAG = 9, LBMPCD_PART_HOME = 10, LBMPCD_CELL_VCM = 11, LBMPCD_PART_ID = 12,
+  LBMPCD_CLOSURE_IN = 13, LBMPCD_CLOSURE_OUT = 14, LBMPCD_CLOSURE_TARGET = 15
 };
 
 typedef struct lbmpcd lbmpcd; /* opaque handle */
@@ -95,7 +101,8 @@ typedef struct {
   double kT, mass;      /* MPCD thermal energy and particle mass (Eq. 4-5, Algorithm 1) */
   int coupling_width;   /* LB columns of coupling buffer per side (2 in Sec. 2.3) */
   int precision;        /* LBMPCD_FP64 | LBMPCD_FP32 | LBMPCD_FP16DEV */
-  int feedback;         /* 0: one-way LB -> MPCD as in the paper; 1: plus windowed MPCD -> LB */
+  int feedback;         /* 0: one-way LB -> MPCD as in the paper; 1: plus windowed MPCD -> LB;
+                           2: plus MPCD -> LB from the learned closure (D2Q9; lbmpcd_set_closure) */
   int window;           /* samples in the averaging window (Table 1 N_s) */
   int resample_density; /* must be 0 (velocity-only redraw, as in the paper) */
   uint64_t seed;        /* Philox key */
@@ -125,9 +132,9 @@ int lbmpcd_step(lbmpcd* h, int nsteps);
 
 /* Same work as lbmpcd_step, launched without graph replay and with a CUDA
  * event pair on the handle's stream around every kernel; adds each kernel
- * family's elapsed milliseconds to phase_ms[0..4] = {prep, lb_pull,
- * particle_pass, cell_pass, particle sort} (caller-owned, 5 entries; not
- * zeroed here) and the number of kernel launches to *launches (may be NULL).  Synchronises the stream.  For
+ * family's elapsed milliseconds to phase_ms[0..5] = {prep, lb_pull,
+ * particle_pass, cell_pass, particle sort, learned closure} (caller-owned,
+ * 6 entries; not zeroed here) and the number of kernel launches to *launches (may be NULL).  Synchronises the stream.  For
  * measurement only: the per-kernel events add small gaps between kernels.
  * Errors: INVALID_ARG, CUDA. */
 int lbmpcd_step_profiled(lbmpcd* h, int nsteps, double* phase_ms, long long* launches);
@@ -203,6 +210,34 @@ void lbmpcd_net_destroy(lbmpcd_net* net);
 #define LBMPCD_NET_STATIC_MAX_PATCHES 8
 int lbmpcd_net_forward_noalloc(const float* theta_dev, const float* x_dev, int patches, float* y_dev,
                                void* cuda_stream);
+
+/* The learned closure in the coupled step (feedback = 2; not in the paper,
+ * which couples one way).  Every step, right after streaming (the instant of
+ * the inner-buffer sampling), the particles in the 16 fine columns nearest
+ * each x-edge of the region ("strips"; xi = distance from the edge, the right
+ * strip seen in a mirror so its u_x changes sign) give per fine cell
+ *     phi_0 = n/ppc - 1,  phi_1 = +-(sum v_x / n)/sqrt(kT/m),  phi_2 = (sum v_y / n)/sqrt(kT/m)
+ * (velocities 0 in an empty cell).  The fields of the last 8 steps (zeros
+ * before step 0), oldest first, are the 24 input channels of the network's
+ * 16 x 16 patches: side-major, ceil(Hy/16) per side, patch py covering fine
+ * rows 16 py .. 16 py + 15 except the last, which covers Hy-16 .. Hy-1.  The
+ * training target is the moving average e <- e + (phi - e)/500 (e = phi at
+ * step 0; the mean lag and white-noise variance of a 1000-step trailing mean).
+ * With parameters loaded, from step 7 on, each inner-buffer LB node gets
+ * f_eq(rho_LB, u_bar) with u_bar = sqrt(kT/m) times the network's mean
+ * predicted velocity over the node's r x r fine cells (fine row R read from
+ * patch min(R/16, ceil(Hy/16)-1)); the patches of all replicas are one batch.
+ * Needs >= 32 fine columns and >= 16 fine rows in the region and
+ * coupling_width * refine <= 16 (set_region returns INVALID_ARG otherwise).
+ *
+ * Load the network parameters (layout of lbmpcd_net_get_params, count =
+ * lbmpcd_net_num_params()) from host or device memory; theta = NULL unloads
+ * them, leaving the sampling only (one-way coupling plus the CLOSURE fields:
+ * the mode that records training data).  With parameters loaded,
+ * lbmpcd_step synchronises the stream at its end and returns ERR_TIMEOUT if a
+ * bounded wait inside the network's tensor-core kernels gave up.  Errors:
+ * STATE (no replica with feedback = 2 and a region), INVALID_ARG, CUDA. */
+int lbmpcd_set_closure(lbmpcd* h, const float* theta, long long count, int src_on_device);
 
 /* Element count of a field for a replica (or a negative error code). */
 long long lbmpcd_field_size(const lbmpcd* h, int replica, int field);

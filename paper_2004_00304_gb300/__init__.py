@@ -24,7 +24,8 @@ LIB_PATH = os.path.join(_HERE, "_build", "liblbmpcd.so")
 D2Q9, D3Q19 = 9, 19
 FP64, FP32, FP16DEV = 0, 1, 2
 FIELDS = dict(RHO=0, U=1, POPS=2, PART_POS=3, PART_VEL=4, PART_CELL=5, SHIFT=6,
-              CELL_COUNT=7, WINDOW_MEAN=8, DIAG=9, PART_HOME=10, CELL_VCM=11, PART_ID=12)
+              CELL_COUNT=7, WINDOW_MEAN=8, DIAG=9, PART_HOME=10, CELL_VCM=11, PART_ID=12,
+              CLOSURE_IN=13, CLOSURE_OUT=14, CLOSURE_TARGET=15)
 INT_FIELDS = {"PART_CELL", "CELL_COUNT", "PART_HOME", "PART_ID"}
 ERRORS = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "TIMEOUT", -5: "STATE", -6: "CAPACITY"}
 
@@ -78,6 +79,7 @@ def load_library(path: str = LIB_PATH):
     L.lbmpcd_net_train_step.argtypes = [vp, vp, vp, ci, ctypes.c_float, fp]
     L.lbmpcd_net_destroy.argtypes = [vp]
     L.lbmpcd_net_forward_noalloc.argtypes = [vp, vp, ci, vp, vp]
+    L.lbmpcd_set_closure.argtypes = [vp, vp, ll, ci]
     L.lbmpcd_net_destroy.restype = None
     L.lbmpcd_destroy.argtypes = [vp]
     L.lbmpcd_destroy.restype = None
@@ -91,7 +93,8 @@ EXPORTED = ["lbmpcd_create", "lbmpcd_set_region", "lbmpcd_step", "lbmpcd_step_pr
             "lbmpcd_get_fields", "lbmpcd_set_state", "lbmpcd_field_size", "lbmpcd_destroy",
             "lbmpcd_last_error", "lbmpcd_tc_gemm_bf16", "lbmpcd_net_num_params", "lbmpcd_net_create",
             "lbmpcd_net_get_params", "lbmpcd_net_set_params", "lbmpcd_net_forward", "lbmpcd_net_backward",
-            "lbmpcd_net_train_step", "lbmpcd_net_destroy", "lbmpcd_net_forward_noalloc"]
+            "lbmpcd_net_train_step", "lbmpcd_net_destroy", "lbmpcd_net_forward_noalloc",
+            "lbmpcd_set_closure"]
 
 
 def make_params(d: dict) -> lbmpcd_params:
@@ -148,10 +151,24 @@ def lbmpcd_step(h, nsteps: int):
 def lbmpcd_step_profiled(h, nsteps: int):
     """Run nsteps with a CUDA event pair around every kernel; returns
     ({phase: milliseconds}, number of kernel launches)."""
-    ms = (ctypes.c_double * 5)()
+    ms = (ctypes.c_double * 6)()
     nl = ctypes.c_longlong(0)
     _check(h, load_library().lbmpcd_step_profiled(h, int(nsteps), ms, ctypes.byref(nl)))
-    return dict(zip(("prep", "lb_pull", "particle_pass", "cell_pass", "sort"), list(ms))), int(nl.value)
+    return dict(zip(("prep", "lb_pull", "particle_pass", "cell_pass", "sort", "closure"), list(ms))), int(nl.value)
+
+
+def lbmpcd_set_closure(h, theta):
+    """Load the learned closure's parameters (numpy float32 vector or a
+    float32 CUDA tensor); None unloads them (sampling only)."""
+    L = load_library()
+    if theta is None:
+        _check(h, L.lbmpcd_set_closure(h, None, 0, 0))
+    elif hasattr(theta, "data_ptr"):
+        t = theta.contiguous()
+        _check(h, L.lbmpcd_set_closure(h, ctypes.c_void_p(t.data_ptr()), t.numel(), int(t.is_cuda)))
+    else:
+        arr = np.ascontiguousarray(theta, dtype=np.float32)
+        _check(h, L.lbmpcd_set_closure(h, ctypes.c_void_p(arr.ctypes.data), arr.size, 0))
 
 
 def lbmpcd_field_size(h, replica: int, field: str) -> int:
@@ -297,6 +314,9 @@ class Lbmpcd:
 
     def step_profiled(self, n: int):
         return lbmpcd_step_profiled(self._h, n)
+
+    def set_closure(self, theta):
+        lbmpcd_set_closure(self._h, theta)
 
     def get(self, field: str, replica: int = 0, out=None):
         return lbmpcd_get_fields(self._h, replica, field, out)

@@ -24,6 +24,7 @@ SOURCES = {
     "lb.cu": [],
     "mpcd.cu": [],
     "closure.cu": [],
+    "closure_coupling.cu": [],
 }
 HEADERS = ["common.cuh", "kernels.h", "tc_gemm.cuh"]
 

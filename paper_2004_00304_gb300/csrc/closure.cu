@@ -302,32 +302,64 @@ extern "C" int lbmpcd_net_get_params(lbmpcd_net* n, float* theta, long long coun
   return cudaStreamSynchronize(n->st) == cudaSuccess ? LBMPCD_OK : LBMPCD_ERR_CUDA;
 }
 
-namespace {
-int net_forward(lbmpcd_net* n, const float* x, int P) {
-  using namespace lbm;
-  cudaStream_t st = n->st;
-  const int M = P * 256, Mp = P * 256;   // one patch is two 128-row tiles: no padding rows needed
-  if (n->weights_dirty) {
-    for (int l = 0; l < NL; ++l) {
-      const NetLayer L = layer(l);
-      k_cast_weights<<<nblk((long long)(L.npad > 64 ? L.npad : 64) * L.kpad), 256, 0, st>>>(n->theta, L, n->W[l], n->WT[l]);
-    }
-    n->weights_dirty = false;
+namespace lbm {
+float* net_input(lbmpcd_net* n) { return n->x32; }
+const float* net_output(lbmpcd_net* n) { return n->y; }
+int net_capacity(lbmpcd_net* n) { return n->cap; }
+
+static void cast_weights(lbmpcd_net* n, cudaStream_t st) {
+  for (int l = 0; l < NL; ++l) {
+    const NetLayer L = layer(l);
+    k_cast_weights<<<nblk((long long)(L.npad > 64 ? L.npad : 64) * L.kpad), 256, 0, st>>>(n->theta, L, n->W[l], n->WT[l]);
   }
-  if (cudaMemcpyAsync(n->x32, x, (size_t)M * 24 * 4, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return LBMPCD_ERR_CUDA;
+  n->weights_dirty = false;
+}
+
+// parameters for in-loop inference: loaded, cast to bf16 and synchronised
+int net_load_params(lbmpcd_net* n, const float* theta, int on_device) {
+  if (cudaMemcpyAsync(n->theta, theta, n->nparam * 4, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                      n->st) != cudaSuccess)
+    return LBMPCD_ERR_CUDA;
+  cast_weights(n, n->st);
+  return cudaStreamSynchronize(n->st) == cudaSuccess ? LBMPCD_OK : LBMPCD_ERR_CUDA;
+}
+
+// forward pass of P patches already in net_input(n), weights already cast
+cudaError_t net_forward_resident(lbmpcd_net* n, int P, cudaStream_t st) {
+  const int M = P * 256, Mp = P * 256;   // one patch is two 128-row tiles: no padding rows needed
   k_input<<<nblk((long long)Mp * 24), 256, 0, st>>>(n->x32, M, Mp, n->act[0]);
   for (int l = 0; l < NL; ++l) {
     const NetLayer L = layer(l);
     const long long tq = (long long)Mp * (L.kpad / 8);
     if (L.cin == 24) k_im2col<24><<<nblk(tq), 256, 0, st>>>(n->act[l], M, Mp, L.kpad, n->col);
     else k_im2col<64><<<nblk(tq), 256, 0, st>>>(n->act[l], M, Mp, L.kpad, n->col);
-    if (tc_gemm(n->col, n->W[l], n->z[l], Mp, L.npad, L.kpad, L.npad, 1.0f, 0.0f, n->err, st) != cudaSuccess)
-      return LBMPCD_ERR_CUDA;
+    const cudaError_t e = tc_gemm(n->col, n->W[l], n->z[l], Mp, L.npad, L.kpad, L.npad, 1.0f, 0.0f, n->err, st);
+    if (e != cudaSuccess) return e;
     const bool last = l == NL - 1;
     k_epilogue<<<nblk((long long)M * L.cout), 256, 0, st>>>(n->z[l], n->theta, L, M, last ? 1 : 0,
                                                             last ? nullptr : n->act[l + 1], n->x32, n->y);
   }
-  return cudaGetLastError() == cudaSuccess ? LBMPCD_OK : LBMPCD_ERR_CUDA;
+  return cudaGetLastError();
+}
+
+// the GEMMs' error word (a bounded wait gave up): read and cleared
+int net_error(lbmpcd_net* n, cudaStream_t st) {
+  int e = 0;
+  if (cudaMemcpyAsync(&e, n->err, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) return LBMPCD_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return LBMPCD_ERR_CUDA;
+  if (e && cudaMemset(n->err, 0, 4) != cudaSuccess) return LBMPCD_ERR_CUDA;
+  return e ? LBMPCD_ERR_TIMEOUT : LBMPCD_OK;
+}
+}  // namespace lbm
+
+namespace {
+int net_forward(lbmpcd_net* n, const float* x, int P) {
+  using namespace lbm;
+  cudaStream_t st = n->st;
+  if (n->weights_dirty) cast_weights(n, st);
+  if (cudaMemcpyAsync(n->x32, x, (size_t)P * 256 * 24 * 4, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return LBMPCD_ERR_CUDA;
+  return net_forward_resident(n, P, st) == cudaSuccess ? LBMPCD_OK : LBMPCD_ERR_CUDA;
 }
 
 int net_backward(lbmpcd_net* n, const float* t, int P) {

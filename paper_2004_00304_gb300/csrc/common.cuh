@@ -161,6 +161,17 @@ struct RepDev {
   double* ring;            // [window][nbuf][4]
   double* wsum;            // [nbuf][4]
   double* wmean;           // [nbuf][4] rho_bar, u_bar
+  // learned closure (feedback = 2, 2D): strips of 16 fine columns per side,
+  // strip cell c = (side Hy + row) 16 + xi
+  int cl_on;               // strip sampling active
+  int cl_npy;              // patches per side, ceil(Hy / 16)
+  int cl_p0;               // first patch of this replica in the handle's batch
+  int cl_pad;
+  double* cframe;          // [2 Hy 16][4] count, sum vx, sum vy of this step (binary64 atomics)
+  float* cring;            // [8][2 Hy 16][3] fields of the last 8 steps
+  double* cema;            // [2 Hy 16][3] moving averages (training target)
+  float* cl_x;             // network input of the handle's batch [P][16][16][24]
+  const float* cl_y;       // network output [P][16][16][3]
 };
 
 constexpr int SORT_TILE = 1024;

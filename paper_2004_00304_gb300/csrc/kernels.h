@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include "common.cuh"
 
+typedef struct lbmpcd_net lbmpcd_net;
+
 namespace lbm {
 
 // precision codes (match LBMPCD_FP64 / FP32 / FP16DEV)
@@ -41,6 +43,22 @@ cudaError_t launch_particles(int dim, int prec, const Launch& L, const int2* bma
 
 // a7 cell part (v_cm, virtual particles, rotation draw) + a8 imposition.
 cudaError_t launch_cells(int q, int prec, const Launch& L, const int2* bmap, int nblocks, int k);
+
+// learned closure (feedback = 2): strip fields -> ring, moving average and
+// network input; imposition of the network's prediction; target readout.
+cudaError_t launch_closure_in(const Launch& L, const int2* bmap, int nwork, int k);
+cudaError_t launch_closure_impose(int prec, const Launch& L, const int2* bmap, int nwork, int k);
+cudaError_t launch_closure_target_out(const RepDev& rd, double* out, cudaStream_t st);
+
+// the closure network (closure.cu) as the coupled step uses it: input and
+// output buffers of the handle's batch, weights cast once per parameter load,
+// and the forward pass of P resident patches on a given stream.
+float* net_input(lbmpcd_net* n);
+const float* net_output(lbmpcd_net* n);
+int net_capacity(lbmpcd_net* n);
+int net_load_params(lbmpcd_net* n, const float* theta, int on_device);
+cudaError_t net_forward_resident(lbmpcd_net* n, int P, cudaStream_t st);
+int net_error(lbmpcd_net* n, cudaStream_t st);
 
 // apply the pending collision of the last step to every particle of a replica.
 cudaError_t launch_flush(int dim, int prec, const RepDev* rd_dev, const RepDev& rd, const double* last_shift,

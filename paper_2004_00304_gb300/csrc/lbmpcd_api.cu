@@ -6,7 +6,10 @@
 // cover all replicas.  lbmpcd_step runs the per-step sequence
 //     lb_pull -> particle_pass -> cell_pass
 // in chunks of KCHUNK steps; each full chunk (a prep kernel plus the 3 kernels
-// per step) is captured once into a CUDA graph and replayed.
+// per step) is captured once into a CUDA graph and replayed.  With the learned
+// closure (feedback = 2) each step adds closure_in, and once parameters are
+// loaded the network's forward pass over the patches of all replicas and
+// closure_impose.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>
@@ -35,8 +38,12 @@ struct lbmpcd {
   std::vector<void*> allocs;                    // handle-wide
   RepDev* d_reps = nullptr;
   int4* bm_lb = nullptr;
-  int2 *bm_p = nullptr, *bm_c = nullptr, *bm_t = nullptr;
-  int nb_lb = 0, nb_p = 0, nb_c = 0, nb_t = 0;
+  int2 *bm_p = nullptr, *bm_c = nullptr, *bm_t = nullptr, *bm_cl = nullptr, *bm_ci = nullptr;
+  int nb_lb = 0, nb_p = 0, nb_c = 0, nb_t = 0, nb_cl = 0, nb_ci = 0;
+  lbmpcd_net* net = nullptr;                    // learned closure, batch of all replicas' patches
+  int cl_P = 0;                                 // patches in the batch
+  bool cl_params = false;                       // parameters loaded: impose from the network
+  std::vector<float> cl_theta;                  // host copy of the parameters
   StepInfo* d_si = nullptr;
   uint32_t* d_step = nullptr;
   int* d_pending = nullptr;
@@ -83,6 +90,7 @@ extern "C" void lbmpcd_destroy(lbmpcd* h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream); else cudaDeviceSynchronize();
   if (h->graph) cudaGraphExecDestroy(h->graph);
+  if (h->net) lbmpcd_net_destroy(h->net);
   for (auto& l : h->rep_allocs) free_list(l);
   free_list(h->allocs);
   delete h;
@@ -103,7 +111,9 @@ static int validate(const lbmpcd_params& p, std::string& why) {
   if (!(p.kT >= 0) || !(p.mass > 0)) { why = "need kT >= 0, mass > 0"; return 0; }
   if (p.coupling_width < 0) { why = "coupling_width must be >= 0"; return 0; }
   if (p.precision < 0 || p.precision > 2) { why = "precision must be 0, 1 or 2"; return 0; }
-  if (p.feedback < 0 || p.feedback > 1) { why = "feedback must be 0 or 1"; return 0; }
+  if (p.feedback < 0 || p.feedback > 2) { why = "feedback must be 0, 1 or 2"; return 0; }
+  if (p.feedback == 2 && (p.lattice != LBMPCD_D2Q9 || !(p.kT > 0)))
+    { why = "feedback = 2 (learned closure) needs D2Q9 and kT > 0"; return 0; }
   if (p.window < 1) { why = "window must be >= 1"; return 0; }
   if (p.resample_density != 0) { why = "resample_density = 1 is not supported"; return 0; }
   return 1;
@@ -210,9 +220,41 @@ static int upload_map(lbmpcd* h, T** dst, int* cnt, const std::vector<T>& src) {
   return LBMPCD_OK;
 }
 
+// The closure network holds the patches of every replica with strip sampling
+// in one batch; it is (re)created when the batch outgrows it.
+static int closure_batch(lbmpcd* h) {
+  int P = 0;
+  for (int r = 0; r < h->nrep; ++r) {
+    RepDev& d = h->rd[r];
+    if (!d.cl_on) continue;
+    d.cl_p0 = P;
+    P += 2 * d.cl_npy;
+  }
+  h->cl_P = P;
+  if (P == 0) return LBMPCD_OK;
+  if (!h->net || net_capacity(h->net) < P) {
+    if (h->net) { CK(h, cudaStreamSynchronize(h->stream)); lbmpcd_net_destroy(h->net); h->net = nullptr; }
+    const int rc = lbmpcd_net_create(P, h->stream, &h->net);
+    if (rc) return fail(h, rc, "creating the closure network");
+    if (h->cl_params) {
+      const int rc2 = net_load_params(h->net, h->cl_theta.data(), 0);
+      if (rc2) return fail(h, rc2, "loading the closure parameters");
+    }
+  }
+  for (int r = 0; r < h->nrep; ++r) {
+    RepDev& d = h->rd[r];
+    if (!d.cl_on) continue;
+    d.cl_x = net_input(h->net);
+    d.cl_y = net_output(h->net);
+  }
+  return LBMPCD_OK;
+}
+
 static int build_maps(lbmpcd* h) {
+  int rc0 = closure_batch(h);
+  if (rc0) return rc0;
   std::vector<int4> lb;
-  std::vector<int2> pp, cc, tt;
+  std::vector<int2> pp, cc, tt, cl, ci;
   for (int r = 0; r < h->nrep; ++r) {
     const RepDev& d = h->rd[r];
     const int ntx = (d.nx / h->lbvec + 127) / 128;
@@ -225,11 +267,18 @@ static int build_maps(lbmpcd* h) {
     for (long long b = 0; b < ncb; ++b) cc.push_back(make_int2(r, (int)b));
     for (long long b = 0; b < nbb; ++b) cc.push_back(make_int2(r, (int)(-1 - b)));
     for (int b = 0; b < d.ntile; ++b) tt.push_back(make_int2(r, b));
+    if (d.cl_on) {
+      const long long ncl = 2LL * d.Hy * 16;
+      for (long long b = 0; b < (ncl + 255) / 256; ++b) cl.push_back(make_int2(r, (int)b));
+      for (long long b = 0; b < nbb; ++b) ci.push_back(make_int2(r, (int)b));
+    }
   }
   int rc = upload_map(h, &h->bm_lb, &h->nb_lb, lb);
   if (!rc) rc = upload_map(h, &h->bm_p, &h->nb_p, pp);
   if (!rc) rc = upload_map(h, &h->bm_c, &h->nb_c, cc);
   if (!rc) rc = upload_map(h, &h->bm_t, &h->nb_t, tt);
+  if (!rc) rc = upload_map(h, &h->bm_cl, &h->nb_cl, cl);
+  if (!rc) rc = upload_map(h, &h->bm_ci, &h->nb_ci, ci);
   if (rc) return rc;
   CK(h, cudaMemcpy(h->d_reps, h->rd.data(), sizeof(RepDev) * h->nrep, cudaMemcpyHostToDevice));
   if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
@@ -265,6 +314,9 @@ extern "C" int lbmpcd_set_region(lbmpcd* h, int replica, const int lo[3], const 
     d.xi_lo1 = (w - p.coupling_width) * r; d.xi_hi1 = (w - d.n_out) * r;
   }
   if (d.np >= (1LL << 32) - 1) return fail(h, LBMPCD_ERR_INVALID_ARG, "too many particles");
+  if (p.feedback == 2 && (d.Wx < 32 || d.Hy < 16 || p.coupling_width * p.refine > 16))
+    return fail(h, LBMPCD_ERR_INVALID_ARG,
+                "learned closure needs >= 32 fine columns, >= 16 fine rows and coupling_width * refine <= 16");
   d.ncell = (long long)d.Wx * (d.Hy + 1) * d.Wz;
   d.nbuf = 2LL * d.n_in * (p.ny - 2) * p.nz;
   const size_t rs = real_size(h->prec);
@@ -301,6 +353,12 @@ extern "C" int lbmpcd_set_region(lbmpcd* h, int replica, const int lo[3], const 
   A(*(void**)&d.ring, nb4 * 8 * (long long)p.window);
   A(*(void**)&d.wsum, nb4 * 8);
   A(*(void**)&d.wmean, nb4 * 8);
+  if (p.feedback == 2) {
+    const long long ncl = 2LL * d.Hy * 16;
+    A(*(void**)&d.cframe, ncl * 4 * 8);
+    A(*(void**)&d.cring, 8 * ncl * 3 * 4);
+    A(*(void**)&d.cema, ncl * 3 * 8);
+  }
 #undef A
   if (e != cudaSuccess) {
     free_list(L);
@@ -308,6 +366,7 @@ extern "C" int lbmpcd_set_region(lbmpcd* h, int replica, const int lo[3], const 
                 std::string("allocating region arrays: ") + cudaGetErrorString(e));
   }
   d.has_region = 1;
+  if (p.feedback == 2) { d.cl_on = 1; d.cl_npy = (d.Hy + 15) / 16; }
   int rc = build_maps(h);
   if (rc) return rc;
   CK(h, launch_init_particles(h->dim, h->prec, h->d_reps + replica, d, h->stream));
@@ -326,6 +385,13 @@ static int run_chunk(lbmpcd* h, int kcount, bool sort) {
     CK(h, launch_lb(h->q, h->prec, h->lbvec, L, h->bm_lb, h->nb_lb, k));
     CK(h, launch_particles(h->dim, h->prec, L, h->bm_p, h->nb_p, k));
     CK(h, launch_cells(h->q, h->prec, L, h->bm_c, h->nb_c, k));
+    if (h->nb_cl) {
+      CK(h, launch_closure_in(L, h->bm_cl, h->nb_cl, k));
+      if (h->cl_params) {
+        CK(h, net_forward_resident(h->net, h->cl_P, h->stream));
+        CK(h, launch_closure_impose(h->prec, L, h->bm_ci, h->nb_ci, k));
+      }
+    }
   }
   return LBMPCD_OK;
 }
@@ -366,6 +432,10 @@ extern "C" int lbmpcd_step(lbmpcd* h, int nsteps) {
   }
   if (nsteps > 0)
     for (int r = 0; r < h->nrep; ++r) h->pending[r] = h->rd[r].has_region ? 1 : 0;
+  if (nsteps > 0 && h->cl_params) {   // a bounded wait inside a closure GEMM gave up
+    const int rc = net_error(h->net, h->stream);
+    if (rc) return fail(h, rc, "closure network: a tensor-core wait timed out");
+  }
   return LBMPCD_OK;
 }
 
@@ -373,7 +443,7 @@ extern "C" int lbmpcd_step_profiled(lbmpcd* h, int nsteps, double* phase_ms, lon
   if (!h) return LBMPCD_ERR_INVALID_ARG;
   if (nsteps < 0 || !phase_ms) return fail(h, LBMPCD_ERR_INVALID_ARG, "nsteps < 0 or null phase_ms");
   if (h->maps_dirty) { int rc = build_maps(h); if (rc) return rc; }
-  const int nev = 2 * (2 + 3 * KCHUNK);
+  const int nev = 2 * (2 + 4 * KCHUNK);
   std::vector<cudaEvent_t> ev(nev, nullptr);
   for (auto& x : ev) CK(h, cudaEventCreate(&x));
   Launch L{h->d_reps, h->nrep, h->d_si, h->stream};
@@ -401,6 +471,13 @@ extern "C" int lbmpcd_step_profiled(lbmpcd* h, int nsteps, double* phase_ms, lon
       bracket(1, [&] { return launch_lb(h->q, h->prec, h->lbvec, L, h->bm_lb, h->nb_lb, k); });
       if (h->nb_p) bracket(2, [&] { return launch_particles(h->dim, h->prec, L, h->bm_p, h->nb_p, k); });
       if (h->nb_c) bracket(3, [&] { return launch_cells(h->q, h->prec, L, h->bm_c, h->nb_c, k); });
+      if (h->nb_cl)
+        bracket(5, [&] {
+          cudaError_t e2 = launch_closure_in(L, h->bm_cl, h->nb_cl, k);
+          if (e2 == cudaSuccess && h->cl_params) e2 = net_forward_resident(h->net, h->cl_P, h->stream);
+          if (e2 == cudaSuccess && h->cl_params) e2 = launch_closure_impose(h->prec, L, h->bm_ci, h->nb_ci, k);
+          return e2;
+        });
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     for (size_t i = 0; i < phase.size() && e == cudaSuccess; ++i) {
@@ -408,6 +485,7 @@ extern "C" int lbmpcd_step_profiled(lbmpcd* h, int nsteps, double* phase_ms, lon
       e = cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]);
       phase_ms[phase[i]] += ms;
       if (phase[i] == 4) nl += 3;   // the sort is four kernels
+      if (phase[i] == 5 && h->cl_params) nl += 14;   // network: input + 4 x (im2col, GEMM, epilogue); impose
     }
     left -= kc;
     h->nstep += kc;
@@ -433,6 +511,8 @@ static long long field_elems(const lbmpcd* h, int r, int field) {
     case LBMPCD_CELL_VCM: return d.has_region ? 3 * d.ncell : -1;
     case LBMPCD_WINDOW_MEAN: return d.has_region ? 4 * d.nbuf : -1;
     case LBMPCD_DIAG: return 9;
+    case LBMPCD_CLOSURE_IN: return d.cl_on ? 2LL * d.cl_npy * 256 * 24 : -1;
+    case LBMPCD_CLOSURE_OUT: case LBMPCD_CLOSURE_TARGET: return d.cl_on ? 2LL * d.cl_npy * 256 * 3 : -1;
   }
   return -1;
 }
@@ -499,6 +579,15 @@ extern "C" int lbmpcd_get_fields(lbmpcd* h, int replica, int field, void* dst, s
     case LBMPCD_WINDOW_MEAN:
       e = cudaMemcpyAsync(buf, d.wmean, d.nbuf * 4 * 8, cudaMemcpyDeviceToDevice, h->stream);
       break;
+    case LBMPCD_CLOSURE_IN:
+      e = launch_real_out(P_FP32, net_input(h->net) + (long long)d.cl_p0 * 256 * 24, n, (double*)buf, h->stream);
+      break;
+    case LBMPCD_CLOSURE_OUT:
+      e = launch_real_out(P_FP32, net_output(h->net) + (long long)d.cl_p0 * 256 * 3, n, (double*)buf, h->stream);
+      break;
+    case LBMPCD_CLOSURE_TARGET:
+      e = launch_closure_target_out(d, (double*)buf, h->stream);
+      break;
     case LBMPCD_DIAG: {
       double* o = (double*)buf;
       e = cudaMemsetAsync(o, 0, 9 * 8, h->stream);
@@ -552,5 +641,28 @@ extern "C" int lbmpcd_set_state(lbmpcd* h, int replica, int field, const void* s
   if (tmp) cudaFree(tmp);
   if (e != cudaSuccess) return cuda_fail(h, e, "set_state");
   if (bad) return fail(h, LBMPCD_ERR_INVALID_ARG, "particle positions out of range (state partly written)");
+  return LBMPCD_OK;
+}
+
+extern "C" int lbmpcd_set_closure(lbmpcd* h, const float* theta, long long count, int src_on_device) {
+  if (!h) return LBMPCD_ERR_INVALID_ARG;
+  bool any = false;
+  for (int r = 0; r < h->nrep; ++r) any = any || h->rd[r].cl_on;
+  if (!any) return fail(h, LBMPCD_ERR_STATE, "no replica has a region with feedback = 2");
+  if (theta && count != lbmpcd_net_num_params())
+    return fail(h, LBMPCD_ERR_INVALID_ARG, "parameter count does not match the closure network");
+  if (h->maps_dirty) { int rc = build_maps(h); if (rc) return rc; }
+  if (!theta) {
+    h->cl_params = false;
+  } else {
+    h->cl_theta.resize((size_t)count);
+    CK(h, cudaMemcpyAsync(h->cl_theta.data(), theta, (size_t)count * 4,
+                          src_on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    const int rc = net_load_params(h->net, h->cl_theta.data(), 0);
+    if (rc) return fail(h, rc, "loading the closure parameters");
+    h->cl_params = true;
+  }
+  if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }   // the step's kernels changed
   return LBMPCD_OK;
 }

@@ -10,7 +10,9 @@
 //                             the LB velocity (Algorithms 1-2, Sec. 2.3),
 //                    a4       kick-drift streaming (Eq. 3), bounce-back walls,
 //                             periodic wrap in the region,
-//                    a6       inner-buffer particles add m, m v to the frame,
+//                    a6       inner-buffer particles add m, m v to the frame
+//                             (with the learned closure, strip particles add
+//                             1, v to their fine cell's closure frame),
 //                    a5       binning under the step's random shift and a
 //                             warp-aggregated reduction (__match_any_sync
 //                             groups, one atomic per group and cell);
@@ -352,6 +354,17 @@ __device__ __forceinline__ void particle_item(const RepDev& rd, const StepInfo& 
       atomicAdd(fr, rd.mass);
 #pragma unroll
       for (int a = 0; a < D; ++a) atomicAdd(fr + 1 + a, rd.mass * (double)v[p][a]);
+    }
+    // learned-closure strips (feedback = 2): count and momentum per fine cell
+    // of the 16 columns at each x-edge, same instant as a6
+    if (D == 2 && rd.cl_on) {
+      const int xs = X[p] < 16 ? X[p] : rd.Wx - 1 - X[p];
+      if (xs < 16) {
+        double* fr = rd.cframe + 4 * (((long long)(X[p] < 16 ? 0 : 1) * rd.Hy + Y[p]) * 16 + xs);
+        atomicAdd(fr, 1.0);
+        atomicAdd(fr + 1, (double)v[p][0]);
+        atomicAdd(fr + 2, (double)v[p][1]);
+      }
     }
     // a5: binning under this step's shift
     cid[p] = collision_cell<D, R>(rd, X[p], Y[p], Z[p], o[p], Cst<R>::shift(st));

@@ -1,0 +1,137 @@
+"""The learned closure inside the coupled step (feedback = 2) against the
+FP64 oracle (GPU).
+
+Sampling (strip fields, 8-frame input, moving-average target) is compared
+with the oracle's directly.  For the in-loop imposition the network output
+the GPU computed is handed to the oracle's imposition, so that both sides
+impose the same velocities and stay comparable element by element; the
+output itself is checked against the oracle's network forward of the GPU's
+input at the network tolerance of the closure tests."""
+import numpy as np
+import pytest
+
+from tests import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lb():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2004_00304_gb300 as mod
+    return mod
+
+
+def _pair(lb, cfg):
+    import oracle as O
+    g = lb.Lbmpcd(cfg["params"])
+    g.set_region(0, *cfg["region"])
+    o = O.OracleSim(cfg["params"])
+    o.set_region(*cfg["region"])
+    return g, o
+
+
+def _theta(seed=3):
+    from oracle import closure as C
+    rng = np.random.default_rng(seed)
+    th = C.init_params(seed) + rng.normal(0, 0.01, size=C.n_params())
+    return th.astype(np.float32)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.mark.parametrize("steps", [20, 70])
+def test_sampling_matches_oracle(lb, steps):
+    """Without parameters feedback = 2 samples only: the input frames (binary32
+    ring) and the moving-average target (binary64) match the oracle; 70 steps
+    cover one captured 64-step chunk with its particle sort."""
+    cfg = inputs.small_2d(feedback=2)
+    g, o = _pair(lb, cfg)
+    g.step(steps)
+    o.step(steps)
+    xg, xo = g.get("CLOSURE_IN"), o.get("CLOSURE_IN")
+    assert xg.shape == xo.shape
+    assert np.max(np.abs(xg - xo)) < 1e-6 * max(1.0, np.max(np.abs(xo)))
+    tg, to = g.get("CLOSURE_TARGET"), o.get("CLOSURE_TARGET")
+    assert np.max(np.abs(tg - to)) < 1e-12
+    assert np.max(np.abs(g.get("POPS") - o.get("POPS"))) < 1e-12
+    g.close()
+
+
+def test_in_loop_imposition_matches_oracle(lb):
+    """Ten steps with parameters loaded (imposition from step 7 on), FP64."""
+    from oracle import closure as C
+    cfg = inputs.small_2d(feedback=2)
+    th = _theta()
+    g, o = _pair(lb, cfg)
+    g.set_closure(th)
+    for n in range(10):
+        g.step(1)
+        o.step(1)
+        xg = g.get("CLOSURE_IN")
+        assert np.max(np.abs(xg - o.get("CLOSURE_IN"))) < 1e-6 * max(1.0, np.max(np.abs(xg)))
+        yg = g.get("CLOSURE_OUT").reshape(-1, 16, 16, 3)
+        ye, _ = C.forward(th.astype(np.float64), xg.reshape(-1, 16, 16, 24), emulate_bf16=True)
+        assert _rel(yg, ye) < 2e-3, n
+        o.closure_impose(yg)
+        pg, po = g.get("POPS"), o.get("POPS")
+        err = np.max(np.abs(pg - po))
+        assert err < 1e-12, (n, err)
+    # the imposition did change the inner columns relative to one-way coupling
+    one = lb.Lbmpcd(cfg["params"])
+    one.set_region(0, *cfg["region"])
+    one.step(10)
+    assert np.max(np.abs(one.get("POPS") - g.get("POPS"))) > 1e-6
+    g.close()
+    one.close()
+
+
+def test_in_loop_closure_fp32_graph(lb):
+    """FP32 with the closure in captured graphs (two 64-step chunks): the run
+    stays finite and the network output still matches the oracle's forward
+    of the GPU's input."""
+    from oracle import closure as C
+    cfg = inputs.small_2d(feedback=2, precision=1)
+    th = _theta(5)
+    g = lb.Lbmpcd(cfg["params"])
+    g.set_region(0, *cfg["region"])
+    g.set_closure(th)
+    g.step(128)
+    xg = g.get("CLOSURE_IN").reshape(-1, 16, 16, 24)
+    yg = g.get("CLOSURE_OUT").reshape(-1, 16, 16, 3)
+    ye, _ = C.forward(th.astype(np.float64), xg, emulate_bf16=True)
+    assert _rel(yg, ye) < 2e-3
+    assert np.all(np.isfinite(g.get("POPS")))
+    assert np.all(np.isfinite(g.get("PART_VEL")))
+    # unloading the parameters leaves sampling only
+    g.set_closure(None)
+    g.step(3)
+    g.close()
+
+
+def test_closure_argument_errors(lb):
+    cfg = inputs.small_2d(feedback=1)
+    g = lb.Lbmpcd(cfg["params"])
+    g.set_region(0, *cfg["region"])
+    with pytest.raises(lb.LbmpcdError) as ei:
+        g.set_closure(_theta())
+    assert ei.value.code == -5                        # STATE: no closure replica
+    g.close()
+    cfg = inputs.small_2d(feedback=2)
+    g = lb.Lbmpcd(cfg["params"])
+    with pytest.raises(lb.LbmpcdError) as ei:
+        g.set_region(0, 20, 34)                       # 28 fine columns < 32
+    assert ei.value.code == -1
+    g.set_region(0, *cfg["region"])
+    with pytest.raises(lb.LbmpcdError) as ei:
+        g.set_closure(np.zeros(10, np.float32))
+    assert ei.value.code == -1
+    g.close()
+    with pytest.raises(lb.LbmpcdError):
+        lb.Lbmpcd(inputs.small_3d(feedback=2)["params"])
