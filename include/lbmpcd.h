@@ -145,7 +145,9 @@ int lbmpcd_step_profiled(lbmpcd* h, int nsteps, double* phase_ms, long long* lau
 int lbmpcd_get_fields(lbmpcd* h, int replica, int field, void* dst, size_t bytes, int dst_on_device);
 
 /* Load POPS, PART_POS, PART_VEL or PART_HOME of one replica from src (same
- * layouts and element types as get_fields; particle arrays in id order).
+ * layouts and element types as get_fields; particle arrays in id order), or
+ * start the LB from a velocity field: U [3][nz][ny][nx] sets the populations
+ * of every node to f_eq(rho0 = 1, u) (Eq. 2).
  * Positions must satisfy 0 <= offset < 1 and lie inside the region.  Errors:
  * INVALID_ARG (field, size, values), STATE (particles before set_region). */
 int lbmpcd_set_state(lbmpcd* h, int replica, int field, const void* src, size_t bytes, int src_on_device);

@@ -26,7 +26,7 @@ SOURCES = {
     "closure.cu": [],
     "closure_coupling.cu": [],
 }
-HEADERS = ["common.cuh", "kernels.h", "tc_gemm.cuh"]
+HEADERS = ["common.cuh", "kernels.h", "tc_gemm.cuh", "net_fused.cuh"]
 
 
 def _nvcc() -> str:

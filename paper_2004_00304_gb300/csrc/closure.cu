@@ -12,6 +12,7 @@
 
 #include "../../include/lbmpcd.h"
 #include "kernels.h"
+#include "net_fused.cuh"
 #include "tc_gemm.cuh"
 
 namespace lbm {
@@ -228,6 +229,7 @@ struct lbmpcd_net {
   __nv_bfloat16 *col = nullptr, *colT = nullptr, *dC = nullptr, *dCT = nullptr;
   float *dcol = nullptr, *d = nullptr, *dW = nullptr, *loss = nullptr;
   int* err = nullptr;
+  __nv_bfloat16* img = nullptr;   // weight images of the fused in-loop forward
   bool weights_dirty = true;
   std::vector<void*> allocs;
 };
@@ -276,6 +278,7 @@ extern "C" int lbmpcd_net_create(int max_patches, void* stream, lbmpcd_net** out
   NA(n->dcol, Mp * 576 * 4); NA(n->d, Mp * 64 * 4);
   NA(n->dC, Mp * 64 * 2); NA(n->dCT, Mp * 128 * 2);
   NA(n->dW, 128LL * 576 * 4); NA(n->loss, 4); NA(n->err, 4);
+  NA(n->img, lbm::fz::IMG_TOTAL);
 #undef NA
   if (rc) { lbmpcd_net_destroy(n); return rc; }
   *out = n;
@@ -315,13 +318,30 @@ static void cast_weights(lbmpcd_net* n, cudaStream_t st) {
   n->weights_dirty = false;
 }
 
-// parameters for in-loop inference: loaded, cast to bf16 and synchronised
+static fz::Meta fused_meta() {
+  fz::Meta m;
+  for (int l = 0; l < NL; ++l) { const NetLayer L = layer(l); m.woff[l] = L.woff; m.boff[l] = L.boff; }
+  return m;
+}
+
+// parameters for in-loop inference: loaded, cast to bf16, packed into the
+// fused kernel's weight images and synchronised
 int net_load_params(lbmpcd_net* n, const float* theta, int on_device) {
   if (cudaMemcpyAsync(n->theta, theta, n->nparam * 4, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                       n->st) != cudaSuccess)
     return LBMPCD_ERR_CUDA;
   cast_weights(n, n->st);
+  k_pack_fused<<<nblk(fz::IMG_TOTAL / 2), 256, 0, n->st>>>(n->theta, fused_meta(), n->img);
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(net_fused_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, fz::SMEM);
+  if (attr != cudaSuccess || cudaGetLastError() != cudaSuccess) return LBMPCD_ERR_CUDA;
   return cudaStreamSynchronize(n->st) == cudaSuccess ? LBMPCD_OK : LBMPCD_ERR_CUDA;
+}
+
+// the whole forward pass of P resident patches in one launch (net_fused.cuh)
+cudaError_t net_forward_fused(lbmpcd_net* n, int P, cudaStream_t st) {
+  net_fused_fwd<<<P, 128, fz::SMEM, st>>>(n->x32, n->img, n->theta, fused_meta(), n->y, n->err);
+  return cudaGetLastError();
 }
 
 // forward pass of P patches already in net_input(n), weights already cast

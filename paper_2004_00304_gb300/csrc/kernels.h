@@ -58,6 +58,7 @@ const float* net_output(lbmpcd_net* n);
 int net_capacity(lbmpcd_net* n);
 int net_load_params(lbmpcd_net* n, const float* theta, int on_device);
 cudaError_t net_forward_resident(lbmpcd_net* n, int P, cudaStream_t st);
+cudaError_t net_forward_fused(lbmpcd_net* n, int P, cudaStream_t st);
 int net_error(lbmpcd_net* n, cudaStream_t st);
 
 // apply the pending collision of the last step to every particle of a replica.
@@ -70,6 +71,7 @@ cudaError_t launch_init_particles(int dim, int prec, const RepDev* rd_dev, const
 // copy-out / copy-in helpers (binary64 / int32 host-facing layouts).
 cudaError_t launch_pops_out(int q, int prec, const RepDev& rd, int parity, double* out, cudaStream_t st);
 cudaError_t launch_pops_in(int q, int prec, const RepDev& rd, const double* in, cudaStream_t st);
+cudaError_t launch_pops_from_u(int q, int prec, const RepDev& rd, const double* u, cudaStream_t st);
 cudaError_t launch_fill_real(int prec, void* dst, long long n, double value, cudaStream_t st);
 cudaError_t launch_real_out(int prec, const void* src, long long n, double* out, cudaStream_t st);
 cudaError_t launch_part_out(int dim, int prec, const RepDev& rd, int field, const double* last_shift,

@@ -338,6 +338,38 @@ static cudaError_t dispatch_pops(int q, int prec, const RepDev& rd, int parity, 
 cudaError_t launch_pops_out(int q, int prec, const RepDev& rd, int parity, double* out, cudaStream_t st) {
   return dispatch_pops(q, prec, rd, parity, out, nullptr, nullptr, st);
 }
+// populations at equilibrium f_eq(rho0 = 1, u) (Eq. 2) from a velocity field
+// u [3][nnode], written to both buffers: the way a flow is started from a
+// prescribed velocity profile
+template <int Q, typename S>
+__global__ void pops_from_u(S* __restrict__ f0, S* __restrict__ f1, long long N, float scale,
+                            const double* __restrict__ u) {
+  using L = Lattice<Q>;
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const double ux = u[n], uy = u[N + n], uz = u[2 * N + n];
+  const double uu = ux * ux + uy * uy + uz * uz;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const double cu = L::cx(i) * ux + L::cy(i) * uy + L::cz(i) * uz;
+    const double d = L::w(i) * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+    Store<S>::st(f0 + i * N + n, (typename Store<S>::R)d, scale);
+    Store<S>::st(f1 + i * N + n, (typename Store<S>::R)d, scale);
+  }
+}
+
+cudaError_t launch_pops_from_u(int q, int prec, const RepDev& rd, const double* u, cudaStream_t st) {
+  const int nb = (int)((rd.nnode + 255) / 256);
+#define LBM_PFU(QQ, SS) pops_from_u<QQ, SS><<<nb, 256, 0, st>>>((SS*)rd.f[0], (SS*)rd.f[1], rd.nnode, rd.fp16_scale, u)
+  if (q == 9) {
+    if (prec == P_FP64) LBM_PFU(9, double); else if (prec == P_FP32) LBM_PFU(9, float); else LBM_PFU(9, __half);
+  } else {
+    if (prec == P_FP64) LBM_PFU(19, double); else if (prec == P_FP32) LBM_PFU(19, float); else LBM_PFU(19, __half);
+  }
+#undef LBM_PFU
+  return cudaGetLastError();
+}
+
 cudaError_t launch_pops_in(int q, int prec, const RepDev& rd, const double* in, cudaStream_t st) {
   return dispatch_pops(q, prec, rd, 0, nullptr, in, nullptr, st);
 }

@@ -9,7 +9,8 @@
 // per step) is captured once into a CUDA graph and replayed.  With the learned
 // closure (feedback = 2) each step adds closure_in, and once parameters are
 // loaded the network's forward pass over the patches of all replicas and
-// closure_impose.
+// closure_impose.  In the loop the network runs as one fused kernel per
+// step (net_fused.cuh).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>
@@ -388,7 +389,7 @@ static int run_chunk(lbmpcd* h, int kcount, bool sort) {
     if (h->nb_cl) {
       CK(h, launch_closure_in(L, h->bm_cl, h->nb_cl, k));
       if (h->cl_params) {
-        CK(h, net_forward_resident(h->net, h->cl_P, h->stream));
+        CK(h, net_forward_fused(h->net, h->cl_P, h->stream));
         CK(h, launch_closure_impose(h->prec, L, h->bm_ci, h->nb_ci, k));
       }
     }
@@ -474,7 +475,7 @@ extern "C" int lbmpcd_step_profiled(lbmpcd* h, int nsteps, double* phase_ms, lon
       if (h->nb_cl)
         bracket(5, [&] {
           cudaError_t e2 = launch_closure_in(L, h->bm_cl, h->nb_cl, k);
-          if (e2 == cudaSuccess && h->cl_params) e2 = net_forward_resident(h->net, h->cl_P, h->stream);
+          if (e2 == cudaSuccess && h->cl_params) e2 = net_forward_fused(h->net, h->cl_P, h->stream);
           if (e2 == cudaSuccess && h->cl_params) e2 = launch_closure_impose(h->prec, L, h->bm_ci, h->nb_ci, k);
           return e2;
         });
@@ -485,7 +486,7 @@ extern "C" int lbmpcd_step_profiled(lbmpcd* h, int nsteps, double* phase_ms, lon
       e = cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]);
       phase_ms[phase[i]] += ms;
       if (phase[i] == 4) nl += 3;   // the sort is four kernels
-      if (phase[i] == 5 && h->cl_params) nl += 14;   // network: input + 4 x (im2col, GEMM, epilogue); impose
+      if (phase[i] == 5 && h->cl_params) nl += 2;    // fused network forward, imposition
     }
     left -= kc;
     h->nstep += kc;
@@ -610,15 +611,17 @@ extern "C" int lbmpcd_get_fields(lbmpcd* h, int replica, int field, void* dst, s
 extern "C" int lbmpcd_set_state(lbmpcd* h, int replica, int field, const void* src, size_t bytes, int src_on_device) {
   if (!h) return LBMPCD_ERR_INVALID_ARG;
   if (replica < 0 || replica >= h->nrep || !src) return fail(h, LBMPCD_ERR_INVALID_ARG, "bad replica or null src");
-  if (field != LBMPCD_POPS && field != LBMPCD_PART_POS && field != LBMPCD_PART_VEL && field != LBMPCD_PART_HOME)
-    return fail(h, LBMPCD_ERR_INVALID_ARG, "only POPS, PART_POS, PART_VEL and PART_HOME can be set");
+  if (field != LBMPCD_POPS && field != LBMPCD_U && field != LBMPCD_PART_POS && field != LBMPCD_PART_VEL &&
+      field != LBMPCD_PART_HOME)
+    return fail(h, LBMPCD_ERR_INVALID_ARG, "only POPS, U, PART_POS, PART_VEL and PART_HOME can be set");
   const RepDev& d = h->rd[replica];
-  if (field != LBMPCD_POPS && !d.has_region) return fail(h, LBMPCD_ERR_STATE, "particles need a region first");
+  const bool lbf = field == LBMPCD_POPS || field == LBMPCD_U;
+  if (!lbf && !d.has_region) return fail(h, LBMPCD_ERR_STATE, "particles need a region first");
   const long long n = field_elems(h, replica, field);
   const size_t esz = int_field(field) ? 4 : 8;
   if (bytes != (size_t)n * esz) return fail(h, LBMPCD_ERR_INVALID_ARG, "src size does not match the field");
   if (h->maps_dirty) { int rc = build_maps(h); if (rc) return rc; }
-  if (field != LBMPCD_POPS) { int rc = flush_if_pending(h, replica); if (rc) return rc; }
+  if (!lbf) { int rc = flush_if_pending(h, replica); if (rc) return rc; }
   const void* buf = src;
   void* tmp = nullptr;
   if (!src_on_device) {
@@ -630,12 +633,14 @@ extern "C" int lbmpcd_set_state(lbmpcd* h, int replica, int field, const void* s
   cudaError_t e = cudaSuccess;
   if (field == LBMPCD_POPS) {
     e = launch_pops_in(h->q, h->prec, d, (const double*)buf, h->stream);
+  } else if (field == LBMPCD_U) {
+    e = launch_pops_from_u(h->q, h->prec, d, (const double*)buf, h->stream);
   } else {
     e = cudaMemsetAsync(h->d_flag, 0, sizeof(int), h->stream);
     if (e == cudaSuccess) e = launch_part_in(h->dim, h->prec, d, field, buf, h->d_flag, h->stream);
   }
   int bad = 0;
-  if (e == cudaSuccess && field != LBMPCD_POPS)
+  if (e == cudaSuccess && !lbf)
     e = cudaMemcpyAsync(&bad, h->d_flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (tmp) cudaFree(tmp);
