@@ -225,21 +225,25 @@ int lbmpcd_net_forward_noalloc(const float* theta_dev, const float* x_dev, int p
  * rows 16 py .. 16 py + 15 except the last, which covers Hy-16 .. Hy-1.  The
  * training target is the moving average e <- e + (phi - e)/500 (e = phi at
  * step 0; the mean lag and white-noise variance of a 1000-step trailing mean).
- * With parameters loaded, from step 7 on, each inner-buffer LB node gets
- * f_eq(rho_LB, u_bar) with u_bar = sqrt(kT/m) times the network's mean
- * predicted velocity over the node's r x r fine cells (fine row R read from
- * patch min(R/16, ceil(Hy/16)-1)); the patches of all replicas are one batch.
- * Needs >= 32 fine columns and >= 16 fine rows in the region and
- * coupling_width * refine <= 16 (set_region returns INVALID_ARG otherwise).
+ * With parameters loaded, the network runs on steps n0, n0 + K, n0 + 2K, ...
+ * (K = interval >= 1, n0 = max(7, the step count at the load)), the patches of
+ * all replicas as one batch; from n0 on every step gives each inner-buffer LB
+ * node f_eq(rho_LB, u_bar), u_bar = sqrt(kT/m) times the latest prediction's
+ * mean velocity over the node's r x r fine cells (fine row R read from patch
+ * min(R/16, ceil(Hy/16)-1)).  K = 1 evaluates every step; K = 8 once per
+ * window of 8 input frames.  Needs >= 32 fine columns and >= 16 fine rows in
+ * the region, refine in {1, 2, 4, 8} and coupling_width * refine <= 16
+ * (set_region returns INVALID_ARG otherwise).
  *
  * Load the network parameters (layout of lbmpcd_net_get_params, count =
  * lbmpcd_net_num_params()) from host or device memory; theta = NULL unloads
  * them, leaving the sampling only (one-way coupling plus the CLOSURE fields:
- * the mode that records training data).  With parameters loaded,
+ * the mode that records training data).  CLOSURE_OUT holds the latest
+ * prediction.  With parameters loaded,
  * lbmpcd_step synchronises the stream at its end and returns ERR_TIMEOUT if a
  * bounded wait inside the network's tensor-core kernels gave up.  Errors:
  * STATE (no replica with feedback = 2 and a region), INVALID_ARG, CUDA. */
-int lbmpcd_set_closure(lbmpcd* h, const float* theta, long long count, int src_on_device);
+int lbmpcd_set_closure(lbmpcd* h, const float* theta, long long count, int src_on_device, int interval);
 
 /* Element count of a field for a replica (or a negative error code). */
 long long lbmpcd_field_size(const lbmpcd* h, int replica, int field);

@@ -166,16 +166,27 @@ class OracleSim:
         if lib().orc_closure_impose(self._h, arr.ctypes.data) != 0:
             raise ValueError("no closure sampling on this replica")
 
-    def step_with_closure(self, theta, n: int = 1) -> None:
-        """n steps with the learned closure in the loop: after each step the
-        network (oracle/closure.py, bf16 rounding emulated as on the GPU)
-        maps the step's input to the imposed fields."""
+    def set_closure(self, theta, interval: int = 1) -> None:
+        """Network parameters for step_with_closure: the network runs on steps
+        n0, n0 + interval, ... with n0 = max(7, the current step count)."""
+        self._cl = (np.asarray(theta, dtype=np.float64), int(interval), max(7, self.step_count))
+        self._cl_y = None
+
+    def step_with_closure(self, n: int = 1) -> None:
+        """n steps with the learned closure in the loop: on evaluation steps the
+        network (oracle/closure.py, bf16 rounding emulated as on the GPU) maps
+        the step's input to the predicted fields; from the first evaluation on
+        every step imposes the latest prediction."""
         from . import closure
+        theta, K, first = self._cl
         for _ in range(int(n)):
+            s = self.step_count
             self.step(1)
-            x = self.get("CLOSURE_IN").reshape(-1, 16, 16, 24)
-            y, _ = closure.forward(np.asarray(theta, dtype=np.float64), x, emulate_bf16=True)
-            self.closure_impose(y)
+            if s >= first and (s - first) % K == 0:
+                x = self.get("CLOSURE_IN").reshape(-1, 16, 16, 24)
+                self._cl_y, _ = closure.forward(theta, x, emulate_bf16=True)
+            if s >= first:
+                self.closure_impose(self._cl_y)
 
     def set(self, field: str, value) -> None:
         fid = FIELDS[field]

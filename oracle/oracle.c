@@ -233,8 +233,10 @@ int orc_set_region(orc_sim* s, int x0, int x1) {
   s->wmean = (double*)calloc((size_t)(s->nbuf > 0 ? s->nbuf : 1) * 4, sizeof(double));
   if (p->feedback == 2) {
     /* the closure needs two disjoint strips, 16 rows, an inner column inside
-       the strip and a thermal velocity to scale by */
-    if (s->dim != 2 || s->Wx < 2 * CL_W || s->Hy < CL_W || cw * s->r > CL_W || !(p->kT > 0)) return -1;
+       the strip, LB nodes that do not straddle patches (r divides 16)
+       and a thermal velocity to scale by */
+    if (s->dim != 2 || s->Wx < 2 * CL_W || s->Hy < CL_W || cw * s->r > CL_W || CL_W % s->r || !(p->kT > 0))
+      return -1;
     s->cl_on = 1;
     s->cl_npy = (s->Hy + CL_W - 1) / CL_W;
     s->cl_ncell = 2L * s->Hy * CL_W;

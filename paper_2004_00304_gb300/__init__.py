@@ -79,7 +79,7 @@ def load_library(path: str = LIB_PATH):
     L.lbmpcd_net_train_step.argtypes = [vp, vp, vp, ci, ctypes.c_float, fp]
     L.lbmpcd_net_destroy.argtypes = [vp]
     L.lbmpcd_net_forward_noalloc.argtypes = [vp, vp, ci, vp, vp]
-    L.lbmpcd_set_closure.argtypes = [vp, vp, ll, ci]
+    L.lbmpcd_set_closure.argtypes = [vp, vp, ll, ci, ci]
     L.lbmpcd_net_destroy.restype = None
     L.lbmpcd_destroy.argtypes = [vp]
     L.lbmpcd_destroy.restype = None
@@ -157,18 +157,19 @@ def lbmpcd_step_profiled(h, nsteps: int):
     return dict(zip(("prep", "lb_pull", "particle_pass", "cell_pass", "sort", "closure"), list(ms))), int(nl.value)
 
 
-def lbmpcd_set_closure(h, theta):
+def lbmpcd_set_closure(h, theta, interval: int = 1):
     """Load the learned closure's parameters (numpy float32 vector or a
-    float32 CUDA tensor); None unloads them (sampling only)."""
+    float32 CUDA tensor) with the network evaluated every ``interval`` steps;
+    None unloads them (sampling only)."""
     L = load_library()
     if theta is None:
-        _check(h, L.lbmpcd_set_closure(h, None, 0, 0))
+        _check(h, L.lbmpcd_set_closure(h, None, 0, 0, 1))
     elif hasattr(theta, "data_ptr"):
         t = theta.contiguous()
-        _check(h, L.lbmpcd_set_closure(h, ctypes.c_void_p(t.data_ptr()), t.numel(), int(t.is_cuda)))
+        _check(h, L.lbmpcd_set_closure(h, ctypes.c_void_p(t.data_ptr()), t.numel(), int(t.is_cuda), int(interval)))
     else:
         arr = np.ascontiguousarray(theta, dtype=np.float32)
-        _check(h, L.lbmpcd_set_closure(h, ctypes.c_void_p(arr.ctypes.data), arr.size, 0))
+        _check(h, L.lbmpcd_set_closure(h, ctypes.c_void_p(arr.ctypes.data), arr.size, 0, int(interval)))
 
 
 def lbmpcd_field_size(h, replica: int, field: str) -> int:
@@ -315,8 +316,8 @@ class Lbmpcd:
     def step_profiled(self, n: int):
         return lbmpcd_step_profiled(self._h, n)
 
-    def set_closure(self, theta):
-        lbmpcd_set_closure(self._h, theta)
+    def set_closure(self, theta, interval: int = 1):
+        lbmpcd_set_closure(self._h, theta, interval)
 
     def get(self, field: str, replica: int = 0, out=None):
         return lbmpcd_get_fields(self._h, replica, field, out)

@@ -307,7 +307,7 @@ extern "C" int lbmpcd_net_get_params(lbmpcd_net* n, float* theta, long long coun
 
 namespace lbm {
 float* net_input(lbmpcd_net* n) { return n->x32; }
-const float* net_output(lbmpcd_net* n) { return n->y; }
+float* net_output(lbmpcd_net* n) { return n->y; }
 int net_capacity(lbmpcd_net* n) { return n->cap; }
 
 static void cast_weights(lbmpcd_net* n, cudaStream_t st) {
@@ -318,31 +318,46 @@ static void cast_weights(lbmpcd_net* n, cudaStream_t st) {
   n->weights_dirty = false;
 }
 
-static fz::Meta fused_meta() {
-  fz::Meta m;
+// weight images of the four layers, bf16, core-matrix layout:
+// element (n, k) of layer l at ((n/8 * KB + k/8) * 8 + n%8) * 8 + k%8,
+// KB = 9 cinp / 8, k = tap * cinp + channel
+__global__ void k_pack_fused(const float* __restrict__ theta, fz::Meta meta, __nv_bfloat16* __restrict__ img) {
+  using namespace fz;
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= IMG_TOTAL / 2) return;
+  int l = 0;
+  while (l < 3 && i >= img_off(l + 1) / 2) ++l;
+  const long long e = i - img_off(l) / 2;
+  const int KB = 9 * cinp(l) / 8;
+  const int q = (int)(e & 7), r = (int)((e >> 3) & 7);
+  const long long rest = e >> 6;
+  const int c = (int)(rest % KB), g = (int)(rest / KB);
+  const int n = 8 * g + r, k = 8 * c + q;
+  const int tap = k / cinp(l), ci = k % cinp(l);
+  float v = 0.0f;
+  if (n < coutr(l) && ci < cinr(l)) v = theta[meta.woff[l] + ((long long)n * 9 + tap) * cinr(l) + ci];
+  img[i] = __float2bfloat16_rn(v);
+}
+
+static NetMeta fused_meta() {
+  NetMeta m;
   for (int l = 0; l < NL; ++l) { const NetLayer L = layer(l); m.woff[l] = L.woff; m.boff[l] = L.boff; }
   return m;
 }
 
 // parameters for in-loop inference: loaded, cast to bf16, packed into the
-// fused kernel's weight images and synchronised
+// weight images of the fused in-loop network and synchronised
 int net_load_params(lbmpcd_net* n, const float* theta, int on_device) {
   if (cudaMemcpyAsync(n->theta, theta, n->nparam * 4, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                       n->st) != cudaSuccess)
     return LBMPCD_ERR_CUDA;
   cast_weights(n, n->st);
   k_pack_fused<<<nblk(fz::IMG_TOTAL / 2), 256, 0, n->st>>>(n->theta, fused_meta(), n->img);
-  static const cudaError_t attr =
-      cudaFuncSetAttribute(net_fused_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, fz::SMEM);
-  if (attr != cudaSuccess || cudaGetLastError() != cudaSuccess) return LBMPCD_ERR_CUDA;
+  if (cudaGetLastError() != cudaSuccess) return LBMPCD_ERR_CUDA;
   return cudaStreamSynchronize(n->st) == cudaSuccess ? LBMPCD_OK : LBMPCD_ERR_CUDA;
 }
 
-// the whole forward pass of P resident patches in one launch (net_fused.cuh)
-cudaError_t net_forward_fused(lbmpcd_net* n, int P, cudaStream_t st) {
-  net_fused_fwd<<<P, 128, fz::SMEM, st>>>(n->x32, n->img, n->theta, fused_meta(), n->y, n->err);
-  return cudaGetLastError();
-}
+ClosureNet net_closure(lbmpcd_net* n) { return ClosureNet{n->img, n->theta, fused_meta(), n->err}; }
 
 // forward pass of P patches already in net_input(n), weights already cast
 cudaError_t net_forward_resident(lbmpcd_net* n, int P, cudaStream_t st) {

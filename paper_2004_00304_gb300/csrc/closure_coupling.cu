@@ -1,79 +1,79 @@
 // closure_coupling.cu -- the learned closure inside the coupled step
 // (feedback = 2, D2Q9; not in the paper, which couples one way).
 //
-// Per step n, after cell_pass(n):
-//   closure_in      one thread per strip cell: this step's count and momentum
-//                   (sampled by particle_pass right after streaming, the
-//                   instant of a6) -> the three fields
-//                       phi_0 = n / ppc - 1,
-//                       phi_1 = +-(sum v_x / n) / sqrt(kT/m)   (- on the right strip),
-//                       phi_2 = (sum v_y / n) / sqrt(kT/m),
-//                   stored in an 8-slot ring (binary32); the moving average
-//                   e <- e + (phi - e) / 500 (binary64, e = phi at n = 0) is
-//                   the training target; the last 8 frames, oldest first, are
-//                   written as the network's 24 input channels of every patch
-//                   holding the cell;
-//   network forward (closure.cu) over the patches of all replicas at once;
-//   closure_impose  one thread per inner-buffer LB node: u_bar = sqrt(kT/m)
-//                   times the mean predicted velocity of its r x r fine cells,
-//                   f_eq(rho_LB, u_bar) written into the buffer lb_pull(n+1)
-//                   reads, from step 7 on (8 frames present).
-// Strips: the 16 fine columns nearest each x-edge of the region, xi = distance
-// from the edge.  Patches: side-major, ceil(Hy/16) per side, patch py covers
-// rows 16 py .. 16 py + 15 except the last, which covers Hy - 16 .. Hy - 1.
+// particle_pass(n) adds 1 and v of every particle whose home cell lies in a
+// strip (the 16 fine columns nearest each x-edge of the region, xi = distance
+// from the edge) to that cell's frame, half n & 1 of a double buffer.  After
+// cell_pass(n), per strip cell, the fields of step n are
+//     phi_0 = n / ppc - 1,
+//     phi_1 = +-(sum v_x / n) / sqrt(kT/m)   (- on the right strip, seen in a mirror),
+//     phi_2 = (sum v_y / n) / sqrt(kT/m)     (velocities 0 in an empty cell);
+// they go into slot n mod 8 of a ring of the last 8 steps (binary32) and the
+// moving average e <- e + (phi - e) / 500 (binary64, e = phi at n = 0), the
+// training target.  Patches: side-major, ceil(Hy/16) per side; patch py covers
+// rows 16 py .. 16 py + 15 except the last, which covers Hy - 16 .. Hy - 1 and
+// "owns" (updates, imposes) only its rows from 16 (npy - 1) on.
+//
+// Without network parameters closure_in does the per-cell update.  With
+// parameters closure_step does everything in one launch, one CTA per patch of
+// the batch: the update of the cells it owns and, on evaluation steps (n = n0,
+// n0 + K, n0 + 2K, ... for the inference interval K, n0 = max(7, the step at
+// which the parameters were loaded)), the network input built
+// from the ring straight into shared memory, the network (the tcgen05 layers
+// of net_fused.cuh), the output and u_bar = sqrt(kT/m) times the mean
+// predicted velocity over each inner-buffer node's r x r cells; from n0 on
+// every step imposes f_eq(rho_LB, u_bar) with the latest u_bar on the
+// inner-buffer LB nodes whose rows the patch owns.
 #include "kernels.h"
+#include "net_fused.cuh"
 
 namespace lbm {
 
-constexpr int CL_W = 16;          // strip width and patch side, fine cells
-constexpr int CL_F = 8;           // frames in the network input
-constexpr double CL_EMA_T = 500.0;
+constexpr int CL_W = 16;                 // strip width and patch side, fine cells
+constexpr int CL_F = 8;                  // frames in the network input
+constexpr double CL_EMA_A = 1.0 / 500.0; // moving-average weight of the newest frame
 
 __device__ __forceinline__ int cl_row0(const RepDev& rd, int py) {
   return py == rd.cl_npy - 1 ? rd.Hy - CL_W : CL_W * py;
 }
 
-// the 24 channels of one pixel: 6 float4 stores into a 96-byte run
-__device__ __forceinline__ void cl_put(const RepDev& rd, int patch, int yy, int xi, const float* v) {
-  float4* dst = (float4*)(rd.cl_x + (((long long)patch * CL_W + yy) * CL_W + xi) * (3 * CL_F));
-#pragma unroll
-  for (int q = 0; q < 6; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+// this step's fields of one strip cell from its frame {count, sum vx, sum vy}
+__device__ __forceinline__ void cl_phi(const RepDev& rd, const double* fr, int side, double phi[3]) {
+  const double n = fr[0];
+  phi[0] = n * rd.cl_inv_ppc - 1.0;
+  phi[1] = 0.0;
+  phi[2] = 0.0;
+  if (n > 0) {
+    const double s = rd.cl_inv_sig / n;
+    phi[1] = (side ? -fr[1] : fr[1]) * s;
+    phi[2] = fr[2] * s;
+  }
 }
 
-__device__ __forceinline__ void closure_in_item(const RepDev& rd, const StepInfo& st, const int2 bm) {
-  const long long ncl = 2LL * rd.Hy * CL_W;
-  const long long c = (long long)bm.y * blockDim.x + threadIdx.x;
-  if (c >= ncl) return;
-  const int side = (int)(c / ((long long)rd.Hy * CL_W));
-  const int row = (int)((c / CL_W) % rd.Hy), xi = (int)(c % CL_W);
-  double* fr = rd.cframe + 4 * c;
-  const double n = fr[0], px = fr[1], py = fr[2];
-  fr[0] = 0.0; fr[1] = 0.0; fr[2] = 0.0;
-  double phi[3];
-  phi[0] = n / (double)rd.ppc - 1.0;
-  phi[1] = n > 0 ? (side ? -1.0 : 1.0) * ((px / n) / rd.sig) : 0.0;
-  phi[2] = n > 0 ? (py / n) / rd.sig : 0.0;
+// ring slot n mod 8 and moving average of strip cell c
+__device__ __forceinline__ void cl_update(const RepDev& rd, uint32_t n, long long c, const double phi[3]) {
+  const long long ncl = 32LL * rd.Hy;
+  float* ring = rd.cring + ((long long)(n & (CL_F - 1)) * ncl + c) * 3;
   double* e = rd.cema + 3 * c;
-  float* ring = rd.cring;
-  const uint32_t slot = st.n & (CL_F - 1);
-  float v[3 * CL_F];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    ring[((long long)slot * ncl + c) * 3 + k] = (float)phi[k];
-    e[k] = st.n == 0 ? phi[k] : e[k] + (phi[k] - e[k]) / CL_EMA_T;
-    v[3 * (CL_F - 1) + k] = (float)phi[k];
+    ring[k] = (float)phi[k];
+    e[k] = n == 0 ? phi[k] : e[k] + (phi[k] - e[k]) * CL_EMA_A;
   }
-  // frame f (oldest first) of step n - 7 + f sits in slot (n + 1 + f) mod 8
-#pragma unroll
-  for (int f = 0; f < CL_F - 1; ++f) {
-    const uint32_t s = (st.n + 1u + (uint32_t)f) & (CL_F - 1);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) v[3 * f + k] = ring[((long long)s * ncl + c) * 3 + k];
-  }
-  const int pa = min(row / CL_W, rd.cl_npy - 1);
-  cl_put(rd, rd.cl_p0 + side * rd.cl_npy + pa, row - cl_row0(rd, pa), xi, v);
-  if (pa != rd.cl_npy - 1 && row >= rd.Hy - CL_W)   // also in the (overlapping) last patch
-    cl_put(rd, rd.cl_p0 + side * rd.cl_npy + rd.cl_npy - 1, row - (rd.Hy - CL_W), xi, v);
+}
+
+// sampling only (no parameters): one thread per strip cell
+__device__ __forceinline__ void closure_in_item(const RepDev& rd, const StepInfo& st, const int2 bm) {
+  const long long ncl = 32LL * rd.Hy;
+  const long long c = (long long)bm.y * blockDim.x + threadIdx.x;
+  if (c >= ncl) return;
+  double* fr = rd.cframe + 4 * ((st.n & 1) * ncl + c);
+  double phi[3];
+  cl_phi(rd, fr, (int)(c / (16LL * rd.Hy)), phi);
+  cl_update(rd, st.n, c, phi);
+  fr[0] = 0.0; fr[1] = 0.0; fr[2] = 0.0;
+  double* fo = rd.cframe + 4 * (((st.n + 1) & 1) * ncl + c);
+  fo[0] = 0.0; fo[1] = 0.0; fo[2] = 0.0;
 }
 
 __global__ void __launch_bounds__(256) closure_in(const RepDev* __restrict__ reps, const int2* __restrict__ bmap,
@@ -83,64 +83,264 @@ __global__ void __launch_bounds__(256) closure_in(const RepDev* __restrict__ rep
   for_each_item(bmap, nwork, reps, si, k, nrep, rd, st, [&](const int2 bm) { closure_in_item(rd, st, bm); });
 }
 
-template <typename S>
-__device__ __forceinline__ void closure_impose_item(const RepDev& rd, const StepInfo& st, const int2 bm) {
-  using R = typename Store<S>::R;
-  using L = Lattice<9>;
-  const long long b = (long long)bm.y * blockDim.x + threadIdx.x;
-  if (b >= rd.nbuf || st.n < (uint32_t)(CL_F - 1)) return;
-  long long t = b;
-  const int yn = 1 + (int)(t % (rd.ny - 2));
-  t /= (rd.ny - 2);
-  const int col = (int)(t % rd.n_in), side = (int)(t / rd.n_in);
-  double su0 = 0.0, su1 = 0.0;
-  for (int a = 0; a < rd.r; ++a)
-    for (int bb = 0; bb < rd.r; ++bb) {
-      const int row = (yn - 1) * rd.r + a, xi = (rd.n_out + col) * rd.r + bb;
-      const int py = min(row / CL_W, rd.cl_npy - 1);
-      const long long p = rd.cl_p0 + side * rd.cl_npy + py;
-      const long long m = (p * CL_W + (row - cl_row0(rd, py))) * CL_W + xi;
-      su0 += (double)rd.cl_y[3 * m + 1];
-      su1 += (double)rd.cl_y[3 * m + 2];
-    }
-  const double rr = (double)(rd.r * rd.r);
-  R u[3];
-  u[0] = (R)((side ? -1.0 : 1.0) * rd.sig * su0 / rr);
-  u[1] = (R)(rd.sig * su1 / rr);
-  u[2] = R(0);
-  const int x = side == 0 ? rd.x0 + rd.n_out + col : rd.x1 - 1 - rd.n_out - col;
-  const long long node = x + (long long)rd.nx * yn;
-  S* dst = (S*)rd.f[(st.n & 1) ^ 1];
-  const R rl = ((const R*)rd.rho)[node];
-  const R uu = u[0] * u[0] + u[1] * u[1];
+// network input of one replica's patches after step n, [P][16][16][24]
+// binary64: frame f (oldest first) of step n - 7 + f is ring slot (n + 1 + f) mod 8
+__global__ void closure_in_out(RepDev rd, uint32_t n, double* __restrict__ out) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= 2LL * rd.cl_npy * CL_W * CL_W) return;
+  const int p = (int)(i / (CL_W * CL_W)), yy = (int)((i / CL_W) % CL_W), xi = (int)(i % CL_W);
+  const int side = p / rd.cl_npy, py = p % rd.cl_npy;
+  const long long ncl = 32LL * rd.Hy;
+  const long long c = ((long long)side * rd.Hy + cl_row0(rd, py) + yy) * CL_W + xi;
 #pragma unroll
-  for (int i = 0; i < 9; ++i) {
-    const R cu = L::cx(i) * u[0] + L::cy(i) * u[1];
-    const R dev = (R)L::w(i) * ((rl - R(1)) + rl * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu));
-    Store<S>::st(dst + i * rd.nnode + node, dev, rd.fp16_scale,
-                 sizeof(S) == 2 ? (mix32((uint32_t)node * 19u + (uint32_t)i + st.n * 0x632BE5ABu) | 1u) : 0u);
+  for (int f = 0; f < CL_F; ++f) {
+    const float* r = rd.cring + ((long long)((n + 1u + (uint32_t)f) & (CL_F - 1)) * ncl + c) * 3;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) out[24 * i + 3 * f + k] = (double)r[k];
   }
-}
-
-template <typename S>
-__global__ void __launch_bounds__(256) closure_impose(const RepDev* __restrict__ reps,
-                                                      const int2* __restrict__ bmap, int nwork,
-                                                      const StepInfo* __restrict__ si, int k, int nrep) {
-  __shared__ RepDev rd;
-  __shared__ StepInfo st;
-  for_each_item(bmap, nwork, reps, si, k, nrep, rd, st, [&](const int2 bm) { closure_impose_item<S>(rd, st, bm); });
 }
 
 // moving averages of one replica in patch layout [P][16][16][3], binary64
 __global__ void closure_target_out(RepDev rd, double* __restrict__ out) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const long long npx = 2LL * rd.cl_npy * CL_W * CL_W;
-  if (i >= npx) return;
+  if (i >= 2LL * rd.cl_npy * CL_W * CL_W) return;
   const int p = (int)(i / (CL_W * CL_W)), yy = (int)((i / CL_W) % CL_W), xi = (int)(i % CL_W);
   const int side = p / rd.cl_npy, py = p % rd.cl_npy;
   const long long c = ((long long)side * rd.Hy + cl_row0(rd, py) + yy) * CL_W + xi;
 #pragma unroll
   for (int k = 0; k < 3; ++k) out[3 * i + k] = rd.cema[3 * c + k];
+}
+
+// f_eq(rho_LB, u) on one inner-buffer node, in the kernel's precision
+template <typename S>
+__device__ __forceinline__ void cl_impose_node(const RepDev& rd, uint32_t n, int x, int yn,
+                                               typename Store<S>::R ux, typename Store<S>::R uy) {
+  using R = typename Store<S>::R;
+  using L = Lattice<9>;
+  const long long node = x + (long long)rd.nx * yn;
+  S* dst = (S*)rd.f[(n & 1) ^ 1];
+  const R rl = ((const R*)rd.rho)[node];
+  const R uu = ux * ux + uy * uy;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const R cu = L::cx(i) * ux + L::cy(i) * uy;
+    const R dev = (R)L::w(i) * ((rl - R(1)) + rl * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu));
+    Store<S>::st(dst + i * rd.nnode + node, dev, rd.fp16_scale,
+                 sizeof(S) == 2 ? (mix32((uint32_t)node * 19u + (uint32_t)i + n * 0x632BE5ABu) | 1u) : 0u);
+  }
+}
+
+// One CTA per patch of the batch (ptab: replica, side, py), 128 threads,
+// fz::SMEM bytes of dynamic shared memory.  Thread (warp w, lane) handles the
+// pixels m = 128 t + 32 w + lane, t = 0, 1, both for the input and for the
+// output.  Every mbarrier wait is bounded; a timeout sets *err, and the CTA
+// releases its TMEM and returns.
+template <typename S>
+__global__ void __launch_bounds__(128, 1) closure_step(const RepDev* __restrict__ reps,
+                                                       const StepInfo* __restrict__ si, int k, int nrep,
+                                                       const int4* __restrict__ ptab,
+                                                       const __nv_bfloat16* __restrict__ img,
+                                                       const float* __restrict__ theta, fz::Meta meta, int* err) {
+  using namespace fz;
+  using namespace tc;
+  using R = typename Store<S>::R;
+  extern __shared__ __align__(1024) unsigned char sm[];
+  __shared__ RepDev rd;
+  __shared__ StepInfo st;
+  __shared__ __align__(8) uint64_t mbar;   // MMAs of a layer complete
+  __shared__ __align__(8) uint64_t wbar;   // weight image of a layer arrived
+  __shared__ float s_bias[4][64];
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_fail;
+  unsigned char* cp = sm;   // copies for dx = -1, 0, +1 at cp + (dx + 1) COPY_BYTES
+  unsigned char* wsm = sm + 3 * COPY_BYTES;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int4 pt = ptab[blockIdx.x];
+  const int side = pt.y, py = pt.z;
+  load_block_records(rd, st, reps, si, pt.x, k, nrep);   // ends with a barrier
+  const uint32_t n = st.n;
+  const long long ncl = 32LL * rd.Hy;
+  const int row0 = cl_row0(rd, py), own0 = py == rd.cl_npy - 1 ? CL_W * py : row0;
+  const int rows_end = py == rd.cl_npy - 1 ? rd.Hy : own0 + CL_W;
+  const int nodes = (rows_end - own0) / rd.r;   // inner-buffer nodes per column whose rows this patch owns
+  const uint32_t first = (uint32_t)rd.cl_first;
+  const bool eval = n >= first && (n - first) % (uint32_t)rd.cl_interval == 0u;
+  if (!eval) {
+    // between evaluations: update the owned cells, impose the last prediction
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const int m = 128 * t + 32 * warp + lane, row = row0 + (m >> 4);
+      if (row < own0) continue;
+      const long long c = ((long long)side * rd.Hy + row) * CL_W + (m & 15);
+      double phi[3];
+      cl_phi(rd, rd.cframe + 4 * ((n & 1) * ncl + c), side, phi);
+      cl_update(rd, n, c, phi);
+      double* fo = rd.cframe + 4 * (((n + 1) & 1) * ncl + c);
+      fo[0] = 0.0; fo[1] = 0.0; fo[2] = 0.0;
+    }
+    if (n > first)   // a prediction exists
+      for (int i = tid; i < nodes * rd.n_in; i += blockDim.x) {
+        const int col = i / nodes, yn = 1 + own0 / rd.r + i % nodes;
+        const double* u = rd.cl_u + 2 * (((long long)side * rd.n_in + col) * (rd.ny - 2) + (yn - 1));
+        const int x = side == 0 ? rd.x0 + rd.n_out + col : rd.x1 - 1 - rd.n_out - col;
+        cl_impose_node<S>(rd, n, x, yn, (R)u[0], (R)u[1]);
+      }
+    return;
+  }
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s_addr(&tmem_base)),
+                 "r"(128u)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    mbar_init(&mbar, 1);
+    mbar_init(&wbar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_fail = 0;
+    bulk_weights(wsm, img, (uint32_t)img_bytes(0), &wbar);
+  }
+  if (tid < 64) {
+#pragma unroll
+    for (int l = 0; l < 4; ++l) s_bias[l][tid] = tid < coutr(l) ? theta[meta.boff[l] + tid] : 0.0f;
+  }
+  zero_unwritten(cp, 4);
+  __syncthreads();   // zeros and barrier initialisation before anyone writes or waits
+
+  // input: the 8 frames of this thread's two pixels (all loads first, so that
+  // they are in flight together); the owner of a cell also updates its ring
+  // slot and moving average and clears its next frame
+  float mean8[2][3];
+  float v[2][3 * CL_F + 8];
+  double fr[2][3];
+  long long cc[2];
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    const int m = 128 * t + 32 * warp + lane;
+    cc[t] = ((long long)side * rd.Hy + row0 + (m >> 4)) * CL_W + (m & 15);
+#pragma unroll
+    for (int f = 0; f < CL_F - 1; ++f) {
+      const float* r = rd.cring + ((long long)((n + 1u + (uint32_t)f) & (CL_F - 1)) * ncl + cc[t]) * 3;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) v[t][3 * f + q] = r[q];
+    }
+    const double* fp = rd.cframe + 4 * ((n & 1) * ncl + cc[t]);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) fr[t][q] = fp[q];
+  }
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    const int m = 128 * t + 32 * warp + lane;
+    double phi[3];
+    cl_phi(rd, fr[t], side, phi);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) v[t][3 * (CL_F - 1) + q] = (float)phi[q];
+#pragma unroll
+    for (int q = 24; q < 32; ++q) v[t][q] = 0.0f;
+    if (row0 + (m >> 4) >= own0) {
+      cl_update(rd, n, cc[t], phi);
+      double* fo = rd.cframe + 4 * (((n + 1) & 1) * ncl + cc[t]);
+      fo[0] = 0.0; fo[1] = 0.0; fo[2] = 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      float s = 0.0f;
+#pragma unroll
+      for (int f = 0; f < CL_F; ++f) s += v[t][3 * f + q];
+      mean8[t][q] = 0.125f * s;
+    }
+#pragma unroll
+    for (int g = 0; g < 4; ++g)
+      put3(cp, m, g, 4,
+           make_uint4(pack2(v[t][8 * g], v[t][8 * g + 1]), pack2(v[t][8 * g + 2], v[t][8 * g + 3]),
+                      pack2(v[t][8 * g + 4], v[t][8 * g + 5]), pack2(v[t][8 * g + 6], v[t][8 * g + 7])));
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+
+  for (int l = 0; l < 4; ++l) {
+    const bool wok = mbar_wait(&wbar, (uint32_t)(l & 1));   // this layer's weights are in
+    if (__syncthreads_or(!wok)) { s_fail = 1; break; }
+    if (tid == 0) {
+      const uint32_t a0 = s_addr(cp), b0 = s_addr(wsm);
+      if (l == 0) issue_layer<4, 64>(tmem, smem_desc(a0, 128, 4 * 128), smem_desc(b0, 128, 36 * 128));
+      else if (l < 3) issue_layer<8, 64>(tmem, smem_desc(a0, 128, 8 * 128), smem_desc(b0, 128, 72 * 128));
+      else issue_layer<8, 16>(tmem, smem_desc(a0, 128, 8 * 128), smem_desc(b0, 128, 72 * 128));
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       s_addr(&mbar))
+                   : "memory");
+    }
+    const bool mok = mbar_wait(&mbar, (uint32_t)(l & 1));
+    if (__syncthreads_or(!mok)) { s_fail = 1; break; }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // this layer's MMAs are complete: the next layer's weights may overwrite
+    // the staging buffer while the epilogue runs
+    if (l < 3 && tid == 0) bulk_weights(wsm, img + img_off(l + 1) / 2, (uint32_t)img_bytes(l + 1), &wbar);
+    if (l == 0) {   // the hidden layers use 8 channel groups: clear their unwritten positions
+      zero_unwritten(cp, 8);
+      __syncthreads();
+    }
+    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+    if (l < 3) {
+      epilogue_hidden(cp, trow, 32 * warp + lane, s_bias[l]);
+      epilogue_hidden(cp, trow + 64u, 128 + 32 * warp + lane, s_bias[l]);
+    } else {
+      // output: global (the CLOSURE_OUT field) and shared memory (the
+      // imposition below); the copies are free once the last MMAs are done
+      uint32_t v0[16], v1[16];
+      FZ_TMEM_LD16(v0, trow);
+      FZ_TMEM_LD16(v1, trow + 64u);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      float* s_y = reinterpret_cast<float*>(sm);
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        const int m = 128 * t + 32 * warp + lane;
+        float* yr = rd.cl_y + ((long long)blockIdx.x * 256 + m) * 3;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float yv = (__uint_as_float(t ? v1[c] : v0[c]) + s_bias[3][c]) + mean8[t][c];
+          yr[c] = yv;
+          s_y[3 * m + c] = yv;
+        }
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  }
+
+  // imposition on the inner-buffer nodes whose fine rows this patch owns
+  if (!s_fail) {
+    const float* s_y = reinterpret_cast<const float*>(sm);
+    for (int i = tid; i < nodes * rd.n_in; i += blockDim.x) {
+      const int col = i / nodes, yn = 1 + own0 / rd.r + i % nodes;
+      R su0 = R(0), su1 = R(0);
+      for (int a = 0; a < rd.r; ++a)
+        for (int b = 0; b < rd.r; ++b) {
+          const int m = ((yn - 1) * rd.r + a - row0) * CL_W + (rd.n_out + col) * rd.r + b;
+          su0 += (R)s_y[3 * m + 1];
+          su1 += (R)s_y[3 * m + 2];
+        }
+      const R scale = (R)rd.sig / (R)(rd.r * rd.r);
+      const R ux = (side ? -su0 : su0) * scale, uy = su1 * scale;
+      double* u = rd.cl_u + 2 * (((long long)side * rd.n_in + col) * (rd.ny - 2) + (yn - 1));
+      u[0] = (double)ux;   // imposed again until the next evaluation
+      u[1] = (double)uy;
+      const int x = side == 0 ? rd.x0 + rd.n_out + col : rd.x1 - 1 - rd.n_out - col;
+      cl_impose_node<S>(rd, n, x, yn, ux, uy);
+    }
+  }
+  if (s_fail && tid == 0) atomicExch(err, 1);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128u) : "memory");
+  }
 }
 
 cudaError_t launch_closure_in(const Launch& L, const int2* bmap, int nwork, int k) {
@@ -151,22 +351,31 @@ cudaError_t launch_closure_in(const Launch& L, const int2* bmap, int nwork, int 
 }
 
 template <typename S>
-static void go_impose(const Launch& L, const int2* bmap, int nwork, int k) {
-  static const int g = grid_cap(grid_for(closure_impose<S>, 256, 1 << 30));
-  closure_impose<S><<<g < nwork ? g : nwork, 256, 0, L.stream>>>(L.reps, bmap, nwork, L.si, k, L.nrep);
+static cudaError_t go_step(const Launch& L, const int4* ptab, int P, int k, const ClosureNet& cn) {
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(closure_step<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, fz::SMEM);
+  if (attr != cudaSuccess) return attr;
+  closure_step<S><<<P, 128, fz::SMEM, L.stream>>>(L.reps, L.si, k, L.nrep, ptab, cn.img, cn.theta, cn.meta,
+                                                 cn.err);
+  return cudaGetLastError();
 }
 
-cudaError_t launch_closure_impose(int prec, const Launch& L, const int2* bmap, int nwork, int k) {
-  if (nwork == 0) return cudaSuccess;
-  if (prec == P_FP64) go_impose<double>(L, bmap, nwork, k);
-  else if (prec == P_FP32) go_impose<float>(L, bmap, nwork, k);
-  else go_impose<__half>(L, bmap, nwork, k);
+cudaError_t launch_closure_step(int prec, const Launch& L, const int4* ptab, int P, int k, const ClosureNet& cn) {
+  if (P == 0) return cudaSuccess;
+  if (prec == P_FP64) return go_step<double>(L, ptab, P, k, cn);
+  if (prec == P_FP32) return go_step<float>(L, ptab, P, k, cn);
+  return go_step<__half>(L, ptab, P, k, cn);
+}
+
+cudaError_t launch_closure_in_out(const RepDev& rd, uint32_t n, double* out, cudaStream_t st) {
+  const long long np = 2LL * rd.cl_npy * CL_W * CL_W;
+  closure_in_out<<<(int)((np + 255) / 256), 256, 0, st>>>(rd, n, out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_closure_target_out(const RepDev& rd, double* out, cudaStream_t st) {
-  const long long n = 2LL * rd.cl_npy * CL_W * CL_W;
-  closure_target_out<<<(int)((n + 255) / 256), 256, 0, st>>>(rd, out);
+  const long long np = 2LL * rd.cl_npy * CL_W * CL_W;
+  closure_target_out<<<(int)((np + 255) / 256), 256, 0, st>>>(rd, out);
   return cudaGetLastError();
 }
 

@@ -167,11 +167,15 @@ struct RepDev {
   int cl_npy;              // patches per side, ceil(Hy / 16)
   int cl_p0;               // first patch of this replica in the handle's batch
   int cl_pad;
-  double* cframe;          // [2 Hy 16][4] count, sum vx, sum vy of this step (binary64 atomics)
+  double cl_inv_ppc, cl_inv_sig;   // 1 / ppc, 1 / sqrt(kT/m)
+  int cl_interval;                 // steps between network evaluations
+  int cl_first;                    // first evaluation: max(7, step of the parameter load)
+  double* cl_u;                    // [nbuf][2] velocity imposed from the latest evaluation
+  double* cframe;          // [2][2 Hy 16][4] count, sum vx, sum vy of step n in half n & 1
+                           // (binary64 atomics; the other half is cleared for step n + 1)
   float* cring;            // [8][2 Hy 16][3] fields of the last 8 steps
   double* cema;            // [2 Hy 16][3] moving averages (training target)
-  float* cl_x;             // network input of the handle's batch [P][16][16][24]
-  const float* cl_y;       // network output [P][16][16][3]
+  float* cl_y;             // network output of the handle's batch [P][16][16][3]
 };
 
 constexpr int SORT_TILE = 1024;

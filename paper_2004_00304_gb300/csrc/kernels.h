@@ -2,6 +2,7 @@
 // unit per kernel family, called by the C ABI in lbmpcd_api.cu).
 #pragma once
 #include <cuda_runtime.h>
+#include <cuda_bf16.h>
 #include "common.cuh"
 
 typedef struct lbmpcd_net lbmpcd_net;
@@ -44,21 +45,30 @@ cudaError_t launch_particles(int dim, int prec, const Launch& L, const int2* bma
 // a7 cell part (v_cm, virtual particles, rotation draw) + a8 imposition.
 cudaError_t launch_cells(int q, int prec, const Launch& L, const int2* bmap, int nblocks, int k);
 
-// learned closure (feedback = 2): strip fields -> ring, moving average and
-// network input; imposition of the network's prediction; target readout.
+// learned closure (feedback = 2): closure_in updates the strip ring and
+// moving averages (no parameters); closure_step does that, the network and
+// the imposition in one launch per step; readouts of input and target.
+struct NetMeta { long long woff[4], boff[4]; };
+struct ClosureNet {                 // what closure_step reads of the network
+  const __nv_bfloat16* img;         // weight images (net_fused.cuh layout)
+  const float* theta;               // fp32 parameters (biases)
+  NetMeta meta;
+  int* err;                         // set when a bounded wait gave up
+};
 cudaError_t launch_closure_in(const Launch& L, const int2* bmap, int nwork, int k);
-cudaError_t launch_closure_impose(int prec, const Launch& L, const int2* bmap, int nwork, int k);
+cudaError_t launch_closure_step(int prec, const Launch& L, const int4* ptab, int P, int k, const ClosureNet& cn);
+cudaError_t launch_closure_in_out(const RepDev& rd, uint32_t n, double* out, cudaStream_t st);
 cudaError_t launch_closure_target_out(const RepDev& rd, double* out, cudaStream_t st);
 
 // the closure network (closure.cu) as the coupled step uses it: input and
 // output buffers of the handle's batch, weights cast once per parameter load,
 // and the forward pass of P resident patches on a given stream.
 float* net_input(lbmpcd_net* n);
-const float* net_output(lbmpcd_net* n);
+float* net_output(lbmpcd_net* n);
 int net_capacity(lbmpcd_net* n);
 int net_load_params(lbmpcd_net* n, const float* theta, int on_device);
 cudaError_t net_forward_resident(lbmpcd_net* n, int P, cudaStream_t st);
-cudaError_t net_forward_fused(lbmpcd_net* n, int P, cudaStream_t st);
+ClosureNet net_closure(lbmpcd_net* n);
 int net_error(lbmpcd_net* n, cudaStream_t st);
 
 // apply the pending collision of the last step to every particle of a replica.

@@ -7,10 +7,9 @@
 //     lb_pull -> particle_pass -> cell_pass
 // in chunks of KCHUNK steps; each full chunk (a prep kernel plus the 3 kernels
 // per step) is captured once into a CUDA graph and replayed.  With the learned
-// closure (feedback = 2) each step adds closure_in, and once parameters are
-// loaded the network's forward pass over the patches of all replicas and
-// closure_impose.  In the loop the network runs as one fused kernel per
-// step (net_fused.cuh).
+// closure (feedback = 2) each step adds one kernel: closure_in (sampling only)
+// or, with parameters loaded, closure_step (sampling, the network over the
+// patches of all replicas, imposition).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>
@@ -39,8 +38,9 @@ struct lbmpcd {
   std::vector<void*> allocs;                    // handle-wide
   RepDev* d_reps = nullptr;
   int4* bm_lb = nullptr;
-  int2 *bm_p = nullptr, *bm_c = nullptr, *bm_t = nullptr, *bm_cl = nullptr, *bm_ci = nullptr;
-  int nb_lb = 0, nb_p = 0, nb_c = 0, nb_t = 0, nb_cl = 0, nb_ci = 0;
+  int2 *bm_p = nullptr, *bm_c = nullptr, *bm_t = nullptr, *bm_cl = nullptr;
+  int4* ptab = nullptr;                         // closure patches of the batch: (replica, side, py)
+  int nb_lb = 0, nb_p = 0, nb_c = 0, nb_t = 0, nb_cl = 0, n_ptab = 0;
   lbmpcd_net* net = nullptr;                    // learned closure, batch of all replicas' patches
   int cl_P = 0;                                 // patches in the batch
   bool cl_params = false;                       // parameters loaded: impose from the network
@@ -245,7 +245,6 @@ static int closure_batch(lbmpcd* h) {
   for (int r = 0; r < h->nrep; ++r) {
     RepDev& d = h->rd[r];
     if (!d.cl_on) continue;
-    d.cl_x = net_input(h->net);
     d.cl_y = net_output(h->net);
   }
   return LBMPCD_OK;
@@ -255,7 +254,8 @@ static int build_maps(lbmpcd* h) {
   int rc0 = closure_batch(h);
   if (rc0) return rc0;
   std::vector<int4> lb;
-  std::vector<int2> pp, cc, tt, cl, ci;
+  std::vector<int2> pp, cc, tt, cl;
+  std::vector<int4> pt;
   for (int r = 0; r < h->nrep; ++r) {
     const RepDev& d = h->rd[r];
     const int ntx = (d.nx / h->lbvec + 127) / 128;
@@ -271,7 +271,8 @@ static int build_maps(lbmpcd* h) {
     if (d.cl_on) {
       const long long ncl = 2LL * d.Hy * 16;
       for (long long b = 0; b < (ncl + 255) / 256; ++b) cl.push_back(make_int2(r, (int)b));
-      for (long long b = 0; b < nbb; ++b) ci.push_back(make_int2(r, (int)b));
+      for (int side = 0; side < 2; ++side)
+        for (int py = 0; py < d.cl_npy; ++py) pt.push_back(make_int4(r, side, py, 0));   // batch order
     }
   }
   int rc = upload_map(h, &h->bm_lb, &h->nb_lb, lb);
@@ -279,7 +280,7 @@ static int build_maps(lbmpcd* h) {
   if (!rc) rc = upload_map(h, &h->bm_c, &h->nb_c, cc);
   if (!rc) rc = upload_map(h, &h->bm_t, &h->nb_t, tt);
   if (!rc) rc = upload_map(h, &h->bm_cl, &h->nb_cl, cl);
-  if (!rc) rc = upload_map(h, &h->bm_ci, &h->nb_ci, ci);
+  if (!rc) rc = upload_map(h, &h->ptab, &h->n_ptab, pt);
   if (rc) return rc;
   CK(h, cudaMemcpy(h->d_reps, h->rd.data(), sizeof(RepDev) * h->nrep, cudaMemcpyHostToDevice));
   if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
@@ -315,9 +316,10 @@ extern "C" int lbmpcd_set_region(lbmpcd* h, int replica, const int lo[3], const 
     d.xi_lo1 = (w - p.coupling_width) * r; d.xi_hi1 = (w - d.n_out) * r;
   }
   if (d.np >= (1LL << 32) - 1) return fail(h, LBMPCD_ERR_INVALID_ARG, "too many particles");
-  if (p.feedback == 2 && (d.Wx < 32 || d.Hy < 16 || p.coupling_width * p.refine > 16))
+  if (p.feedback == 2 && (d.Wx < 32 || d.Hy < 16 || p.coupling_width * p.refine > 16 || 16 % p.refine))
     return fail(h, LBMPCD_ERR_INVALID_ARG,
-                "learned closure needs >= 32 fine columns, >= 16 fine rows and coupling_width * refine <= 16");
+                "learned closure needs >= 32 fine columns, >= 16 fine rows, refine in {1, 2, 4, 8} and "
+                "coupling_width * refine <= 16");
   d.ncell = (long long)d.Wx * (d.Hy + 1) * d.Wz;
   d.nbuf = 2LL * d.n_in * (p.ny - 2) * p.nz;
   const size_t rs = real_size(h->prec);
@@ -356,9 +358,10 @@ extern "C" int lbmpcd_set_region(lbmpcd* h, int replica, const int lo[3], const 
   A(*(void**)&d.wmean, nb4 * 8);
   if (p.feedback == 2) {
     const long long ncl = 2LL * d.Hy * 16;
-    A(*(void**)&d.cframe, ncl * 4 * 8);
+    A(*(void**)&d.cframe, 2 * ncl * 4 * 8);
     A(*(void**)&d.cring, 8 * ncl * 3 * 4);
     A(*(void**)&d.cema, ncl * 3 * 8);
+    A(*(void**)&d.cl_u, (d.nbuf > 0 ? d.nbuf : 1) * 2 * 8);
   }
 #undef A
   if (e != cudaSuccess) {
@@ -367,7 +370,14 @@ extern "C" int lbmpcd_set_region(lbmpcd* h, int replica, const int lo[3], const 
                 std::string("allocating region arrays: ") + cudaGetErrorString(e));
   }
   d.has_region = 1;
-  if (p.feedback == 2) { d.cl_on = 1; d.cl_npy = (d.Hy + 15) / 16; }
+  if (p.feedback == 2) {
+    d.cl_on = 1;
+    d.cl_npy = (d.Hy + 15) / 16;
+    d.cl_inv_ppc = 1.0 / p.ppc;
+    d.cl_inv_sig = 1.0 / d.sig;
+    d.cl_interval = 1;
+    d.cl_first = 7;
+  }
   int rc = build_maps(h);
   if (rc) return rc;
   CK(h, launch_init_particles(h->dim, h->prec, h->d_reps + replica, d, h->stream));
@@ -387,11 +397,8 @@ static int run_chunk(lbmpcd* h, int kcount, bool sort) {
     CK(h, launch_particles(h->dim, h->prec, L, h->bm_p, h->nb_p, k));
     CK(h, launch_cells(h->q, h->prec, L, h->bm_c, h->nb_c, k));
     if (h->nb_cl) {
-      CK(h, launch_closure_in(L, h->bm_cl, h->nb_cl, k));
-      if (h->cl_params) {
-        CK(h, net_forward_fused(h->net, h->cl_P, h->stream));
-        CK(h, launch_closure_impose(h->prec, L, h->bm_ci, h->nb_ci, k));
-      }
+      if (h->cl_params) CK(h, launch_closure_step(h->prec, L, h->ptab, h->n_ptab, k, net_closure(h->net)));
+      else CK(h, launch_closure_in(L, h->bm_cl, h->nb_cl, k));
     }
   }
   return LBMPCD_OK;
@@ -474,10 +481,8 @@ extern "C" int lbmpcd_step_profiled(lbmpcd* h, int nsteps, double* phase_ms, lon
       if (h->nb_c) bracket(3, [&] { return launch_cells(h->q, h->prec, L, h->bm_c, h->nb_c, k); });
       if (h->nb_cl)
         bracket(5, [&] {
-          cudaError_t e2 = launch_closure_in(L, h->bm_cl, h->nb_cl, k);
-          if (e2 == cudaSuccess && h->cl_params) e2 = net_forward_fused(h->net, h->cl_P, h->stream);
-          if (e2 == cudaSuccess && h->cl_params) e2 = launch_closure_impose(h->prec, L, h->bm_ci, h->nb_ci, k);
-          return e2;
+          return h->cl_params ? launch_closure_step(h->prec, L, h->ptab, h->n_ptab, k, net_closure(h->net))
+                              : launch_closure_in(L, h->bm_cl, h->nb_cl, k);
         });
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -486,7 +491,6 @@ extern "C" int lbmpcd_step_profiled(lbmpcd* h, int nsteps, double* phase_ms, lon
       e = cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]);
       phase_ms[phase[i]] += ms;
       if (phase[i] == 4) nl += 3;   // the sort is four kernels
-      if (phase[i] == 5 && h->cl_params) nl += 2;    // fused network forward, imposition
     }
     left -= kc;
     h->nstep += kc;
@@ -581,7 +585,7 @@ extern "C" int lbmpcd_get_fields(lbmpcd* h, int replica, int field, void* dst, s
       e = cudaMemcpyAsync(buf, d.wmean, d.nbuf * 4 * 8, cudaMemcpyDeviceToDevice, h->stream);
       break;
     case LBMPCD_CLOSURE_IN:
-      e = launch_real_out(P_FP32, net_input(h->net) + (long long)d.cl_p0 * 256 * 24, n, (double*)buf, h->stream);
+      e = launch_closure_in_out(d, (uint32_t)(h->nstep - 1), (double*)buf, h->stream);
       break;
     case LBMPCD_CLOSURE_OUT:
       e = launch_real_out(P_FP32, net_output(h->net) + (long long)d.cl_p0 * 256 * 3, n, (double*)buf, h->stream);
@@ -649,13 +653,21 @@ extern "C" int lbmpcd_set_state(lbmpcd* h, int replica, int field, const void* s
   return LBMPCD_OK;
 }
 
-extern "C" int lbmpcd_set_closure(lbmpcd* h, const float* theta, long long count, int src_on_device) {
+extern "C" int lbmpcd_set_closure(lbmpcd* h, const float* theta, long long count, int src_on_device, int interval) {
   if (!h) return LBMPCD_ERR_INVALID_ARG;
   bool any = false;
   for (int r = 0; r < h->nrep; ++r) any = any || h->rd[r].cl_on;
   if (!any) return fail(h, LBMPCD_ERR_STATE, "no replica has a region with feedback = 2");
   if (theta && count != lbmpcd_net_num_params())
     return fail(h, LBMPCD_ERR_INVALID_ARG, "parameter count does not match the closure network");
+  if (theta && interval < 1) return fail(h, LBMPCD_ERR_INVALID_ARG, "interval must be >= 1");
+  if (theta)
+    for (int r = 0; r < h->nrep; ++r)
+      if (h->rd[r].cl_on) {
+        h->rd[r].cl_interval = interval;
+        h->rd[r].cl_first = (int)std::max<long long>(7, h->nstep);
+        h->maps_dirty = true;
+      }
   if (h->maps_dirty) { int rc = build_maps(h); if (rc) return rc; }
   if (!theta) {
     h->cl_params = false;

@@ -360,7 +360,8 @@ __device__ __forceinline__ void particle_item(const RepDev& rd, const StepInfo& 
     if (D == 2 && rd.cl_on) {
       const int xs = X[p] < 16 ? X[p] : rd.Wx - 1 - X[p];
       if (xs < 16) {
-        double* fr = rd.cframe + 4 * (((long long)(X[p] < 16 ? 0 : 1) * rd.Hy + Y[p]) * 16 + xs);
+        const long long ncl = 32LL * rd.Hy;
+        double* fr = rd.cframe + 4 * ((st.n & 1) * ncl + ((long long)(X[p] < 16 ? 0 : 1) * rd.Hy + Y[p]) * 16 + xs);
         atomicAdd(fr, 1.0);
         atomicAdd(fr + 1, (double)v[p][0]);
         atomicAdd(fr + 2, (double)v[p][1]);

@@ -15,11 +15,14 @@
 // already in the same layout ([n][tap][channel], zero padded), the two M tiles
 // accumulate in TMEM columns 0..63 and 64..127, and the epilogue (bias, ReLU,
 // bf16) writes the next layer's three copies; the last layer (3 outputs,
-// padded to N = 16) adds the mean of the 8 input frames and writes y.
+// padded to N = 16) adds the mean of the 8 input frames.  The kernel that
+// runs these layers inside the coupled step is closure_step
+// (closure_coupling.cu).
 #pragma once
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include "kernels.h"
 #include "tc_gemm.cuh"
 
 namespace lbm {
@@ -40,7 +43,7 @@ __host__ __device__ constexpr long long img_off(int l) {
 }
 constexpr long long IMG_TOTAL = img_off(4);
 
-struct Meta { long long woff[4], boff[4]; };
+using Meta = NetMeta;   // parameter offsets of each layer's weights and biases
 
 // byte offset of (row j in [-16, 272), channel group c) in a copy with KC groups
 __device__ __forceinline__ uint32_t cp_off(int j, int c, int KC) {
@@ -48,11 +51,45 @@ __device__ __forceinline__ uint32_t cp_off(int j, int c, int KC) {
   return (uint32_t)((((jj >> 3) * KC + c) << 7) + ((jj & 7) << 4));
 }
 
-// one 16-byte channel group of pixel p into the three shifted copies
-__device__ __forceinline__ void put3(unsigned char* const* cp, int p, int c, int KC, uint4 v) {
-  *reinterpret_cast<uint4*>(cp[1] + cp_off(p, c, KC)) = v;                            // dx = 0
-  if ((p & 15) >= 1) *reinterpret_cast<uint4*>(cp[2] + cp_off(p - 1, c, KC)) = v;     // dx = +1
-  if ((p & 15) <= 14) *reinterpret_cast<uint4*>(cp[0] + cp_off(p + 1, c, KC)) = v;    // dx = -1
+// one 16-byte channel group of pixel p into the three shifted copies, which
+// sit at cp + (dx + 1) COPY_BYTES
+__device__ __forceinline__ void put3(unsigned char* cp, int p, int c, int KC, uint4 v) {
+  *reinterpret_cast<uint4*>(cp + COPY_BYTES + cp_off(p, c, KC)) = v;                              // dx = 0
+  if ((p & 15) >= 1) *reinterpret_cast<uint4*>(cp + 2 * COPY_BYTES + cp_off(p - 1, c, KC)) = v;   // dx = +1
+  if ((p & 15) <= 14) *reinterpret_cast<uint4*>(cp + cp_off(p + 1, c, KC)) = v;                   // dx = -1
+}
+
+// weight image of one layer -> shared memory by one bulk (TMA) copy that
+// completes on mbarrier wb; issued by one thread
+__device__ __forceinline__ void bulk_weights(unsigned char* wsm, const __nv_bfloat16* src, uint32_t bytes,
+                                             uint64_t* wb) {
+  const uint32_t b = (uint32_t)__cvta_generic_to_shared(wb);
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(b),
+               "r"(bytes)
+               : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(wsm)),
+               "l"(src), "r"(bytes), "r"(b)
+               : "memory");
+}
+
+// Clear the positions of the three copies that no write of a layer input
+// covers, for a layout of KC channel groups: the 16 halo rows above and below
+// (all copies), the rows whose x + dx leaves the patch (x = 15 in the dx = +1
+// copy, x = 0 in the dx = -1 copy).  Every other position is written.
+__device__ __forceinline__ void zero_unwritten(unsigned char* cp, int KC) {
+  const uint4 z = make_uint4(0, 0, 0, 0);
+  const int halo = 2 * KC * 8;   // 16-byte units in the 16 halo rows of one side
+  for (int i = threadIdx.x; i < 3 * 2 * halo; i += blockDim.x) {
+    const int k = i / (2 * halo), r = i % (2 * halo);
+    const int off = r < halo ? r : (34 * KC * 8) + (r - halo);   // groups 0-1 and 34-35
+    reinterpret_cast<uint4*>(cp + k * COPY_BYTES)[off] = z;
+  }
+  for (int i = threadIdx.x; i < 2 * 16 * KC; i += blockDim.x) {
+    const int side = i / (16 * KC), r = (i / KC) % 16, c = i % KC;
+    const int j = 16 * r + (side ? 15 : 0);   // dx = +1 copy: x = 15; dx = -1 copy: x = 0
+    *reinterpret_cast<uint4*>(cp + (side ? 2 : 0) * COPY_BYTES + cp_off(j, c, KC)) = z;
+  }
 }
 
 __device__ __forceinline__ uint32_t pack2(float a, float b) {
@@ -62,165 +99,68 @@ __device__ __forceinline__ uint32_t pack2(float a, float b) {
 
 }  // namespace fz
 
-// weight images of the four layers, bf16, core-matrix layout:
-// element (n, k) of layer l at ((n/8 * KB + k/8) * 8 + n%8) * 8 + k%8,
-// KB = 9 cinp / 8, k = tap * cinp + channel
-__global__ void k_pack_fused(const float* __restrict__ theta, fz::Meta meta, __nv_bfloat16* __restrict__ img) {
-  using namespace fz;
-  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= IMG_TOTAL / 2) return;
-  int l = 0;
-  while (l < 3 && i >= img_off(l + 1) / 2) ++l;
-  const long long e = i - img_off(l) / 2;
-  const int KB = 9 * cinp(l) / 8;
-  const int q = (int)(e & 7), r = (int)((e >> 3) & 7);
-  const long long rest = e >> 6;
-  const int c = (int)(rest % KB), g = (int)(rest / KB);
-  const int n = 8 * g + r, k = 8 * c + q;
-  const int tap = k / cinp(l), ci = k % cinp(l);
-  float v = 0.0f;
-  if (n < coutr(l) && ci < cinr(l)) v = theta[meta.woff[l] + ((long long)n * 9 + tap) * cinr(l) + ci];
-  img[i] = __float2bfloat16_rn(v);
+
+namespace fz {
+
+__device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
 }
 
-// y[P][256][3] = network(x[P][256][24]); grid = P, 128 threads, fz::SMEM bytes
-// of dynamic shared memory.  Every mbarrier wait is bounded; a timeout sets
-// *err, and the CTA releases its TMEM and returns.
-__global__ void __launch_bounds__(128, 1) net_fused_fwd(const float* __restrict__ x,
-                                                        const __nv_bfloat16* __restrict__ img,
-                                                        const float* __restrict__ theta, fz::Meta meta,
-                                                        float* __restrict__ y, int* err) {
-  using namespace fz;
-  using namespace tc;
-  extern __shared__ __align__(1024) unsigned char sm[];
-  __shared__ __align__(8) uint64_t mbar;
-  __shared__ uint32_t tmem_base;
-  __shared__ int s_fail;
-  unsigned char* cp[3] = {sm, sm + COPY_BYTES, sm + 2 * COPY_BYTES};   // dx = -1, 0, +1
-  unsigned char* wsm = sm + 3 * COPY_BYTES;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const float* xp = x + (long long)blockIdx.x * 256 * 24;
-
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s_addr(&tmem_base)),
-                 "r"(128u)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  if (tid == 0) {
-    mbar_init(&mbar, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    s_fail = 0;
-  }
-  const uint4 z4 = make_uint4(0, 0, 0, 0);
-  for (int i = tid; i < 3 * COPY_BYTES / 16; i += 128) reinterpret_cast<uint4*>(sm)[i] = z4;
-  __syncthreads();
-  // layer-0 input: 24 fp32 channels -> bf16, padded to 32 (4 groups of 8)
-  for (int it = tid; it < 256 * 4; it += 128) {
-    const int p = it >> 2, c = it & 3;
-    float v[8];
+// All MMAs of one layer: tile t (rows 128 t .. 128 t + 127) accumulates in
+// TMEM columns 64 t.., over 9 taps x KC/2 K-steps of 16.  dA / dB are the
+// descriptors of the first copy / the weight image; a descriptor's start
+// field is the byte address / 16, so an offset is added as offset / 16.
+template <int KC, int N>
+__device__ __forceinline__ void issue_layer(uint32_t tmem, uint64_t dA, uint64_t dB) {
+  constexpr uint32_t idesc = tc::instr_desc(128, N);
 #pragma unroll
-    for (int e = 0; e < 8; ++e) v[e] = (c < 3) ? xp[p * 24 + 8 * c + e] : 0.0f;
-    put3(cp, p, c, 4, make_uint4(pack2(v[0], v[1]), pack2(v[2], v[3]), pack2(v[4], v[5]), pack2(v[6], v[7])));
-  }
-  for (int i = tid; i < (int)(img_bytes(0) / 16); i += 128)
-    reinterpret_cast<uint4*>(wsm)[i] = reinterpret_cast<const uint4*>(img)[i];
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t tmem = tmem_base;
-
-  for (int l = 0; l < 4 && !s_fail; ++l) {
-    const int KC = cinp(l) / 8, N = nout(l);
-    const uint32_t sbo_a = (uint32_t)KC * 128u, sbo_b = (uint32_t)(9 * KC) * 128u;
-    if (tid == 0) {
-      const uint32_t idesc = instr_desc(128, N);
-      for (int t = 0; t < 2; ++t) {
-        uint32_t acc = 0;
-        for (int tap = 0; tap < 9; ++tap) {
-          const int dy = tap / 3 - 1, dx = tap % 3 - 1;
-          const uint32_t a0 = s_addr(cp[dx + 1]) + (uint32_t)((16 + 128 * t + 16 * dy) >> 3) * sbo_a;
-          const uint32_t b0 = s_addr(wsm) + (uint32_t)(tap * KC) * 128u;
-          for (int s = 0; s < KC / 2; ++s) {
-            const uint64_t ad = smem_desc(a0 + s * 256, 128, sbo_a);
-            const uint64_t bd = smem_desc(b0 + s * 256, 128, sbo_b);
-            asm volatile(
-                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + 64u * t),
-                "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-                : "memory");
-            acc = 1;
-          }
-        }
-      }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                       s_addr(&mbar))
-                   : "memory");
-    }
-    const bool ok = mbar_wait(&mbar, (uint32_t)(l & 1));
-    if (__syncthreads_or(!ok)) {
-      if (tid == 0) { atomicExch(err, 1); s_fail = 1; }
-      __syncthreads();
-      break;
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (l == 0) {   // the hidden layers use 8 channel groups: clear the 4-group layout first
-      for (int i = tid; i < 3 * COPY_BYTES / 16; i += 128) reinterpret_cast<uint4*>(sm)[i] = z4;
-      __syncthreads();
-    }
-    const float* bias = theta + meta.boff[l];
-#pragma unroll 1
-    for (int t = 0; t < 2; ++t) {
-      const int m = 128 * t + 32 * warp + lane;
-#pragma unroll 1
-      for (int c0 = 0; c0 < N; c0 += 16) {
-        uint32_t v[16];
-        const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + 64u * t + (uint32_t)c0;
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-            : "r"(ta)
-            : "memory");
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (l < 3) {
-          float a[16];
+  for (int t = 0; t < 2; ++t) {
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const float s = __uint_as_float(v[j]) + bias[c0 + j];
-            a[j] = s > 0.0f ? s : 0.0f;
-          }
-          put3(cp, m, c0 / 8, 8, make_uint4(pack2(a[0], a[1]), pack2(a[2], a[3]), pack2(a[4], a[5]), pack2(a[6], a[7])));
-          put3(cp, m, c0 / 8 + 1, 8,
-               make_uint4(pack2(a[8], a[9]), pack2(a[10], a[11]), pack2(a[12], a[13]), pack2(a[14], a[15])));
-        } else {
-          float* yr = y + ((long long)blockIdx.x * 256 + m) * 3;
-          const float* xr = xp + (long long)m * 24;
+    for (int tap = 0; tap < 9; ++tap) {
+      const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+      const uint32_t a_off = (uint32_t)((dx + 1) * COPY_BYTES + ((16 + 128 * t + 16 * dy) >> 3) * KC * 128);
 #pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            float s = 0.0f;
-#pragma unroll
-            for (int f = 0; f < 8; ++f) s += xr[3 * f + c];
-            yr[c] = (__uint_as_float(v[c]) + bias[c]) + 0.125f * s;
-          }
-        }
-      }
+      for (int s = 0; s < KC / 2; ++s)
+        mma_f16(tmem + 64u * t, dA + ((a_off + 256u * s) >> 4), dB + ((uint32_t)(tap * KC * 128 + 256 * s) >> 4),
+                idesc, (tap | s) ? 1u : 0u);
     }
-    if (l < 3) {   // this layer's MMAs are complete: stage the next layer's weights
-      const uint4* src = reinterpret_cast<const uint4*>(img + img_off(l + 1) / 2);
-      for (int i = tid; i < (int)(img_bytes(l + 1) / 16); i += 128) reinterpret_cast<uint4*>(wsm)[i] = src[i];
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  if (warp == 0) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128u) : "memory");
   }
 }
+
+// 16 consecutive fp32 accumulator columns of this warp's 32 lanes
+#define FZ_TMEM_LD16(v, addr)                                                                                  \
+  asm volatile(                                                                                                \
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];" \
+      : "=r"((v)[0]), "=r"((v)[1]), "=r"((v)[2]), "=r"((v)[3]), "=r"((v)[4]), "=r"((v)[5]), "=r"((v)[6]),    \
+        "=r"((v)[7]), "=r"((v)[8]), "=r"((v)[9]), "=r"((v)[10]), "=r"((v)[11]), "=r"((v)[12]),               \
+        "=r"((v)[13]), "=r"((v)[14]), "=r"((v)[15])                                                          \
+      : "r"(addr)                                                                                              \
+      : "memory")
+
+// hidden-layer epilogue of one tile: bias, ReLU, bf16 into the next layer's copies
+__device__ __forceinline__ void epilogue_hidden(unsigned char* cp, uint32_t ta, int m, const float* bias) {
+  uint32_t v[64];
+  FZ_TMEM_LD16(v, ta);
+  FZ_TMEM_LD16(v + 16, ta + 16);
+  FZ_TMEM_LD16(v + 32, ta + 32);
+  FZ_TMEM_LD16(v + 48, ta + 48);
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int g = 0; g < 8; ++g) {
+    float a[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const float s = __uint_as_float(v[8 * g + j]) + bias[8 * g + j];
+      a[j] = s > 0.0f ? s : 0.0f;
+    }
+    put3(cp, m, g, 8, make_uint4(pack2(a[0], a[1]), pack2(a[2], a[3]), pack2(a[4], a[5]), pack2(a[6], a[7])));
+  }
+}
+
+}  // namespace fz
 
 }  // namespace lbm

@@ -64,44 +64,55 @@ def test_sampling_matches_oracle(lb, steps):
     g.close()
 
 
-def test_in_loop_imposition_matches_oracle(lb):
-    """Ten steps with parameters loaded (imposition from step 7 on), FP64."""
+@pytest.mark.parametrize("interval,before", [(1, 0), (3, 0), (4, 10)])
+def test_in_loop_imposition_matches_oracle(lb, interval, before):
+    """FP64, steps one at a time, the parameters loaded after `before`
+    sampling-only steps: the network runs on steps n0, n0 + K, ... with
+    n0 = max(7, before); from n0 on every step imposes the latest prediction."""
     from oracle import closure as C
     cfg = inputs.small_2d(feedback=2)
     th = _theta()
     g, o = _pair(lb, cfg)
-    g.set_closure(th)
-    for n in range(10):
+    g.step(before)
+    o.step(before)
+    g.set_closure(th, interval=interval)
+    first = max(7, before)
+    y_last = None
+    for n in range(before, first + 3 * interval + 2):
         g.step(1)
         o.step(1)
         xg = g.get("CLOSURE_IN")
         assert np.max(np.abs(xg - o.get("CLOSURE_IN"))) < 1e-6 * max(1.0, np.max(np.abs(xg)))
         yg = g.get("CLOSURE_OUT").reshape(-1, 16, 16, 3)
-        ye, _ = C.forward(th.astype(np.float64), xg.reshape(-1, 16, 16, 24), emulate_bf16=True)
-        assert _rel(yg, ye) < 2e-3, n
-        o.closure_impose(yg)
-        pg, po = g.get("POPS"), o.get("POPS")
-        err = np.max(np.abs(pg - po))
+        if n >= first and (n - first) % interval == 0:
+            ye, _ = C.forward(th.astype(np.float64), xg.reshape(-1, 16, 16, 24), emulate_bf16=True)
+            assert _rel(yg, ye) < 2e-3, n
+            y_last = yg
+        elif y_last is not None:
+            np.testing.assert_array_equal(yg, y_last)      # held between evaluations
+        if n >= first:
+            o.closure_impose(yg)
+        err = np.max(np.abs(g.get("POPS") - o.get("POPS")))
         assert err < 1e-12, (n, err)
     # the imposition did change the inner columns relative to one-way coupling
     one = lb.Lbmpcd(cfg["params"])
     one.set_region(0, *cfg["region"])
-    one.step(10)
+    one.step(n + 1)
     assert np.max(np.abs(one.get("POPS") - g.get("POPS"))) > 1e-6
     g.close()
     one.close()
 
 
 def test_in_loop_closure_fp32_graph(lb):
-    """FP32 with the closure in captured graphs (two 64-step chunks): the run
-    stays finite and the network output still matches the oracle's forward
-    of the GPU's input."""
+    """FP32 with the closure evaluated every 8 steps in captured graphs (two
+    64-step chunks): the run stays finite and the last evaluation (step 127)
+    still matches the oracle's forward of the GPU's input."""
     from oracle import closure as C
     cfg = inputs.small_2d(feedback=2, precision=1)
     th = _theta(5)
     g = lb.Lbmpcd(cfg["params"])
     g.set_region(0, *cfg["region"])
-    g.set_closure(th)
+    g.set_closure(th, interval=8)
     g.step(128)
     xg = g.get("CLOSURE_IN").reshape(-1, 16, 16, 24)
     yg = g.get("CLOSURE_OUT").reshape(-1, 16, 16, 3)
