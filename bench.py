@@ -364,6 +364,133 @@ def run_ensemble(args):
     print(json.dumps(out), flush=True)
 
 
+def run_closure(args):
+    """Secondary measurement: the learned closure.  The network is trained
+    here on data the coupled method generates (channels of the 2048 x 512
+    family at Ny in {64,...,512}, g in [1e-7, 1e-6]), its gain over the plain
+    8-frame mean is measured on held-out channels, and the 1024 x 256 channel
+    (MPCD on the central 128 LB columns at refinement 2) runs in the loop with
+    the plain windowed coupling (W = 100 and W = 8) and with the closure
+    (inference every step and every 8 steps).  Each run starts from the
+    steady Poiseuille profile; the imposed-profile error is the relative L2
+    distance of the velocity on the two inner-buffer columns (the imposed
+    f_eq(rho, u_bar)) from that profile, the LB-profile error that of the
+    x-averaged LB velocity profile, both averaged over 100 samples 10 steps
+    apart."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    import paper_2004_00304_gb300 as lb
+    from paper_2004_00304_gb300 import closure_train as CT
+    __graft_entry__.build()
+    t0 = time.time()
+    X, T = CT.generate(CT.training_channels(8, seed=1), spinup=1500, samples=100, every=10)
+    Xv, Tv = CT.generate(CT.training_channels(4, seed=2), spinup=1500, samples=20, every=25)
+    t1 = time.time()
+    train_steps, batch = 3000, 64
+    theta, losses = CT.train(X, T, steps=train_steps, batch=batch, lr=1e-3, seed=0)
+    torch.cuda.synchronize()
+    t2 = time.time()
+    ev = CT.evaluate(theta, Xv, Tv)
+    del X, T, Xv, Tv
+
+    cfg = CT.channel(256, 1e-7, seed=5, nx=1024, region_cols=128)
+    p0, (x0, x1) = cfg["params"], cfg["region"]
+    nx, ny = p0["nx"], p0["ny"]
+    cols = [x0 + 1, x1 - 2]                      # inner-buffer columns (coupling width 2)
+    yc = np.arange(1, ny - 1) + 0.5
+    u_ref = CT.poiseuille(yc, ny, p0["tau"], p0["force"][0])
+    cxs = torch.tensor([0, 1, 0, -1, 0, 1, -1, -1, 1], dtype=torch.float64, device="cuda")
+    pops = torch.empty(9 * ny * nx, dtype=torch.float64, device="cuda")
+    uf = torch.empty(3 * ny * nx, dtype=torch.float64, device="cuda")
+    modes = [("plain_W100", 1, 100, 0), ("plain_W8", 1, 8, 0), ("closure_K1", 2, 100, 1), ("closure_K8", 2, 100, 8)]
+    runs = {}
+    peaks = measured_peaks()
+    for name, fb, window, K in modes:
+        pm = dict(p0, feedback=fb, window=window)
+        sim = lb.Lbmpcd([pm])
+        sim.set_region(0, x0, x1)
+        CT.start_from_poiseuille(sim, 0, dict(cfg, params=pm))
+        if fb == 2:
+            sim.set_closure(theta, interval=K)
+        sim.step(max(args.warmup, 1000))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        sim.step(args.steps)
+        e1.record()
+        torch.cuda.synchronize()
+        sps = args.steps / (e0.elapsed_time(e1) * 1e-3)
+        errs, prof, lb_errs = [], [], []
+        for _ in range(100):
+            sim.step(10)
+            sim.get("U", 0, out=uf)
+            ux = uf.view(3, ny, nx)[0, 1:ny - 1, :].mean(dim=1).cpu().numpy()
+            lb_errs.append(float(np.linalg.norm(ux - u_ref) / np.linalg.norm(u_ref)))
+            sim.get("POPS", 0, out=pops)
+            f = pops.view(9, ny, nx)[:, 1:ny - 1, cols]
+            u = ((cxs[:, None, None] * f).sum(0) / f.sum(0)).cpu().numpy()
+            prof.append(u)
+            errs.append(float(np.linalg.norm(u - u_ref[:, None]) / np.linalg.norm(np.repeat(u_ref[:, None], 2, 1))))
+        mean_prof = np.mean(prof, axis=0)
+        run = {"steps_per_s": sps, "imposed_profile_l2_err": float(np.mean(errs)),
+               "lb_profile_l2_err": float(np.mean(lb_errs)),
+               "time_mean_profile_l2_err": float(np.linalg.norm(mean_prof - u_ref[:, None]) /
+                                                 np.linalg.norm(np.repeat(u_ref[:, None], 2, 1)))}
+        if fb == 2 and K == 1:
+            ph, _ = sim.step_profiled(64)
+            t_launch = ph["closure"] / 64 * 1e-3                 # one closure_step launch per step
+            P = 2 * (-(-((ny - 2) * p0["refine"]) // 16))
+            flops = P * 45.7e6
+            peak = float(peaks["bf16_tflops_sustained"]) if peaks else 1700.0   # timed inside the step
+            run["closure_step"] = {"patches": P, "us_per_launch": t_launch * 1e6,
+                                   "roofline": {"bound": "tensor", "achieved": flops / t_launch / 1e12, "peak": peak,
+                                                "unit": "TFLOP/s", "frac": flops / t_launch / 1e12 / peak}}
+        runs[name] = run
+        sim.close()
+    out = {"metric": METRIC, "value": runs["closure_K8"]["steps_per_s"], "unit": UNIT, "n_gpus": 1,
+           "steps": args.steps, "warmup": max(args.warmup, 1000),
+           "ms_per_step": 1e3 / runs["closure_K8"]["steps_per_s"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32 (network bf16/f32-acc)", "data": "synthetic",
+           "config": {"workload": "channel2d_1024x256_closure_fp32", "lb_nodes": f"{nx}x{ny}",
+                      "mpcd_region_cols": x1 - x0, "refine": p0["refine"], "ppc": p0["ppc"]},
+           "closure": {"training": {"patches": int(100 * 480), "steps": train_steps, "batch": batch,
+                                    "data_s": t1 - t0, "train_s": t2 - t1,
+                                    "patches_per_s": train_steps * batch / (t2 - t1),
+                                    "loss_first20": float(losses[:20].mean()), "loss_last100": float(losses[-100:].mean())},
+                       "heldout": {k: [float(v) for v in ev[k]] for k in ("rmse_net", "rmse_mean8", "gain")},
+                       "in_loop": runs,
+                       "surrogate_over_plain_W100": runs["closure_K8"]["steps_per_s"] / runs["plain_W100"]["steps_per_s"]}}
+    print(json.dumps(out), flush=True)
+
+
+def run_closure_kernel(args):
+    """The 1024 x 256 channel with the closure evaluated every step (network
+    parameters of the initial distribution: the kernels' cost does not depend
+    on their values); for kernel profiling."""
+    import torch
+    import __graft_entry__
+    import paper_2004_00304_gb300 as lb
+    from paper_2004_00304_gb300 import closure_train as CT
+    __graft_entry__.build()
+    cfg = CT.channel(256, 1e-7, seed=5, nx=1024, region_cols=128)
+    sim = lb.Lbmpcd([cfg["params"]])
+    sim.set_region(0, *cfg["region"])
+    sim.set_closure(CT.init_params(0), interval=1)
+    sim.step(args.warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    sim.step(args.steps)
+    e1.record()
+    torch.cuda.synchronize()
+    sps = args.steps / (e0.elapsed_time(e1) * 1e-3)
+    print(json.dumps({"metric": METRIC, "value": sps, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+                      "warmup": args.warmup, "higher_is_better": True, "data": "synthetic",
+                      "config": {"workload": "channel2d_1024x256_closure_every_step_fp32"}}), flush=True)
+    sim.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -372,8 +499,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="channel", choices=["channel", "ensemble"],
-                    help="channel: the 2048x512 headline workload; ensemble: the 64-replica ensemble (extra line)")
+    ap.add_argument("--workload", default="channel", choices=["channel", "ensemble", "closure", "closure_kernel"],
+                    help="channel: the 2048x512 headline workload; ensemble: the 64-replica ensemble; "
+                         "closure: training, gain and in-loop runs of the learned closure (extra lines)")
     ap.add_argument("--fp16", action="store_true", help="ensemble only: FP16 deviation storage")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -386,6 +514,12 @@ def main():
         return
     if args.workload == "ensemble":
         run_ensemble(args)
+        return
+    if args.workload == "closure":
+        run_closure(args)
+        return
+    if args.workload == "closure_kernel":
+        run_closure_kernel(args)
         return
     if world > 1:
         import torch
