@@ -206,6 +206,7 @@ def run_ours(args, rank, world, local_rank):
     with torch.cuda.stream(stream):
         sim = lb.Lbmpcd(params, stream=stream)
         sim.set_region(0, *WORKLOAD["region"])
+        launch = choose_launch(sim, args)
         # keep a copy of the initial state on the host (pinned) for the e2e leg
         names = ("POPS", "PART_POS", "PART_VEL", "PART_HOME")
         host_in = {}
@@ -231,7 +232,10 @@ def run_ours(args, rank, world, local_rank):
         barrier()
         clocks = sampler.stop() if sampler else None
         ms = e0.elapsed_time(e1)
-        launches = 3 * args.steps + 5 * (args.steps // 64) + (1 if args.steps % 64 else 0)
+        if launch["mode"] == 1:   # sort (4) + prep + one persistent kernel per chunk
+            launches = 6 * (args.steps // 64) + (2 if args.steps % 64 else 0)
+        else:
+            launches = 3 * args.steps + 5 * (args.steps // 64) + (1 if args.steps % 64 else 0)
         t_max = torch.tensor([ms], dtype=torch.float64, device=dev)
         if world > 1:
             dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
@@ -297,7 +301,7 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": WORKLOAD["name"], "lb_nodes": f"{p['nx']}x{p['ny']}",
                    "particles": ab["particles"], "collision_cells": ab["cells"],
                    "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "working set ~300 MB per step > 129 MB L2 (no flush needed)"},
+                   "l2": "working set ~300 MB per step > 129 MB L2 (no flush needed)", "launch": launch},
         "lb_mlups": ab["fluid_nodes"] * steps_per_s / 1e6,
         "mpcd_mparticle_upd_per_s": ab["particles"] * steps_per_s / 1e6,
         "step_hbm": {"algorithmic_bytes_per_step": step_bytes,
@@ -317,6 +321,16 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(out), flush=True)
 
 
+def choose_launch(sim, args) -> dict:
+    """The launch form of the step: autotuned on a copy of the handle (default),
+    or forced to per-kernel graphs / the persistent kernel."""
+    if args.launch == "auto":
+        return sim.autotune(steps=256)
+    mode = 1 if args.launch == "persistent" else 0
+    sim.set_launch_mode(mode)
+    return dict(mode=mode, blocks_per_sm=0, lb_nodes_per_thread=None, candidates=1)
+
+
 def run_ensemble(args):
     """Secondary measurement: the 64-replica uneven ensemble in one handle
     (one launch per kernel and step covering every replica, 64-step graphs)."""
@@ -333,6 +347,7 @@ def run_ensemble(args):
         sim = lb.Lbmpcd([r["params"] for r in reps], stream=stream)
         for k, r in enumerate(reps):
             sim.set_region(k, *r["region"])
+        launch = choose_launch(sim, args)
         sim.step(args.warmup)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -357,7 +372,7 @@ def run_ensemble(args):
            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f16-storage/f32" if args.fp16 else "f32", "data": "synthetic",
            "config": {"workload": "ensemble64_uneven_" + ("fp16dev" if args.fp16 else "fp32"), "replicas": len(reps),
-                      "lb_nodes": nodes, "particles": parts},
+                      "lb_nodes": nodes, "particles": parts, "launch": launch},
            "lb_mlups": nodes * sps / 1e6, "mpcd_mparticle_upd_per_s": parts * sps / 1e6,
            "step_hbm": {"algorithmic_bytes_per_step": step_bytes, "achieved_gbs": step_bytes * sps / 1e9,
                         "frac_of_measured": step_bytes * sps / 1e9 / hbm}}
@@ -503,6 +518,8 @@ def main():
                     help="channel: the 2048x512 headline workload; ensemble: the 64-replica ensemble; "
                          "closure: training, gain and in-loop runs of the learned closure (extra lines)")
     ap.add_argument("--fp16", action="store_true", help="ensemble only: FP16 deviation storage")
+    ap.add_argument("--launch", default="auto", choices=["auto", "graphs", "persistent"],
+                    help="launch form of the step: autotuned (default), per-kernel graphs, persistent kernel")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

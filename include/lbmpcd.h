@@ -245,6 +245,29 @@ int lbmpcd_net_forward_noalloc(const float* theta_dev, const float* x_dev, int p
  * STATE (no replica with feedback = 2 and a region), INVALID_ARG, CUDA. */
 int lbmpcd_set_closure(lbmpcd* h, const float* theta, long long count, int src_on_device, int interval);
 
+/* Launch form of the step (batching; not in the paper).  mode 0
+ * (default): each step is three kernels (lb_pull, particle_pass, cell_pass)
+ * over all replicas, 64 steps per captured CUDA graph.  mode 1: each chunk of
+ * steps is one persistent cooperative kernel running the three phases per
+ * step with a grid barrier between phases (bounded waits: a barrier that
+ * times out ends the launch and lbmpcd_step returns ERR_TIMEOUT), captured
+ * into the chunk's graph when the driver allows the capture, launched
+ * directly otherwise; lbmpcd_step then synchronises the stream at its end.
+ * blocks_per_sm: persistent blocks per SM (0 = the occupancy limit).  Results
+ * are those of mode 0 (same per-step records, same kernels' item code).  Mode 1
+ * is not available with the learned closure (INVALID_ARG); lbmpcd_step_profiled
+ * always launches per kernel. */
+int lbmpcd_set_launch_mode(lbmpcd* h, int mode, int blocks_per_sm);
+
+/* Time the launch forms {mode 0, mode 1 at the occupancy limit, mode 1 with
+ * one block per SM} x {the default LB row width, one node per thread} for
+ * `steps` steps each (after a 64-step warm-up) on a fresh copy of the handle
+ * built from the same parameters and regions -- the handle's own state is not
+ * touched -- and keep the fastest.  choice (may be NULL) receives {mode,
+ * blocks_per_sm, LB nodes per thread, candidates timed}.  Needs the memory of
+ * a second handle for the duration of the call.  Errors: INVALID_ARG, OOM, CUDA. */
+int lbmpcd_autotune(lbmpcd* h, int steps, int choice[4]);
+
 /* Element count of a field for a replica (or a negative error code). */
 long long lbmpcd_field_size(const lbmpcd* h, int replica, int field);
 

@@ -80,6 +80,8 @@ def load_library(path: str = LIB_PATH):
     L.lbmpcd_net_destroy.argtypes = [vp]
     L.lbmpcd_net_forward_noalloc.argtypes = [vp, vp, ci, vp, vp]
     L.lbmpcd_set_closure.argtypes = [vp, vp, ll, ci, ci]
+    L.lbmpcd_set_launch_mode.argtypes = [vp, ci, ci]
+    L.lbmpcd_autotune.argtypes = [vp, ci, ctypes.POINTER(ci)]
     L.lbmpcd_net_destroy.restype = None
     L.lbmpcd_destroy.argtypes = [vp]
     L.lbmpcd_destroy.restype = None
@@ -94,7 +96,7 @@ EXPORTED = ["lbmpcd_create", "lbmpcd_set_region", "lbmpcd_step", "lbmpcd_step_pr
             "lbmpcd_last_error", "lbmpcd_tc_gemm_bf16", "lbmpcd_net_num_params", "lbmpcd_net_create",
             "lbmpcd_net_get_params", "lbmpcd_net_set_params", "lbmpcd_net_forward", "lbmpcd_net_backward",
             "lbmpcd_net_train_step", "lbmpcd_net_destroy", "lbmpcd_net_forward_noalloc",
-            "lbmpcd_set_closure"]
+            "lbmpcd_set_closure", "lbmpcd_set_launch_mode", "lbmpcd_autotune"]
 
 
 def make_params(d: dict) -> lbmpcd_params:
@@ -318,6 +320,16 @@ class Lbmpcd:
 
     def set_closure(self, theta, interval: int = 1):
         lbmpcd_set_closure(self._h, theta, interval)
+
+    def set_launch_mode(self, mode: int, blocks_per_sm: int = 0):
+        """0: per-kernel launches in 64-step graphs; 1: one persistent kernel per chunk."""
+        _check(self._h, load_library().lbmpcd_set_launch_mode(self._h, int(mode), int(blocks_per_sm)))
+
+    def autotune(self, steps: int = 256) -> dict:
+        """Time the launch forms on a copy of this handle and keep the fastest."""
+        out = (ctypes.c_int * 4)()
+        _check(self._h, load_library().lbmpcd_autotune(self._h, int(steps), out))
+        return dict(mode=out[0], blocks_per_sm=out[1], lb_nodes_per_thread=out[2], candidates=out[3])
 
     def get(self, field: str, replica: int = 0, out=None):
         return lbmpcd_get_fields(self._h, replica, field, out)

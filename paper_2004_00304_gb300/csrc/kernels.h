@@ -71,6 +71,20 @@ cudaError_t net_forward_resident(lbmpcd_net* n, int P, cudaStream_t st);
 ClosureNet net_closure(lbmpcd_net* n);
 int net_error(lbmpcd_net* n, cudaStream_t st);
 
+// persistent form of a chunk: kcount steps of lb_pull -> particle_pass ->
+// cell_pass in one cooperative launch with bounded grid barriers between
+// phases (bar: two zeroed words, err: set on a barrier timeout).  The LB map
+// has 256-thread row tiles.  blocks_per_sm <= 0 takes the occupancy limit.
+struct PersistentMaps {
+  const int4* lb; int nb_lb;
+  const int2* p; int nb_p;
+  const int2* c; int nb_c;
+  unsigned* bar;
+  int* err;
+};
+cudaError_t launch_persistent(int q, int prec, int vec, const Launch& L, int kcount, const PersistentMaps& m,
+                              int blocks_per_sm, int* grid_out);
+
 // apply the pending collision of the last step to every particle of a replica.
 cudaError_t launch_flush(int dim, int prec, const RepDev* rd_dev, const RepDev& rd, const double* last_shift,
                          cudaStream_t st);

@@ -11,214 +11,9 @@
 // d_i = f_i - w_i (rho0 = 1) so that small body-force increments survive
 // binary32 / scaled binary16 storage.  HBM traffic: one read and one write of
 // q populations per node.
-#include "kernels.h"
+#include "lb_core.cuh"
 
 namespace lbm {
-
-// V consecutive populations of one row: aligned vector load/store (V = 4 for
-// binary32 and scaled binary16 rows whose length is a multiple of 4), scalar
-// otherwise.
-template <typename S, int V> struct Row;
-template <typename S> struct Row<S, 1> {
-  using R = typename Store<S>::R;
-  __device__ static void ld(const S* p, R* o, float inv) { o[0] = Store<S>::ld(p, inv); }
-  __device__ static void st(S* p, const R* v, float sc, uint32_t h) { Store<S>::st(p, v[0], sc, h); }
-};
-template <> struct Row<float, 4> {
-  __device__ static void ld(const float* p, float* o, float) {
-    const float4 t = *reinterpret_cast<const float4*>(p);
-    o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
-  }
-  __device__ static void st(float* p, const float* v, float, uint32_t) {
-    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
-  }
-};
-template <> struct Row<float, 2> {
-  __device__ static void ld(const float* p, float* o, float) {
-    const float2 t = *reinterpret_cast<const float2*>(p);
-    o[0] = t.x; o[1] = t.y;
-  }
-  __device__ static void st(float* p, const float* v, float, uint32_t) {
-    *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
-  }
-};
-template <> struct Row<__half, 2> {
-  __device__ static void ld(const __half* p, float* o, float inv) {
-    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(p));
-    o[0] = a.x * inv; o[1] = a.y * inv;
-  }
-  __device__ static void st(__half* p, const float* v, float sc, uint32_t h) {
-    __half2 t;
-    t.x = sr_half(v[0] * sc, h);
-    t.y = sr_half(v[1] * sc, h ? mix32(h + 1u) : 0u);
-    *reinterpret_cast<__half2*>(p) = t;
-  }
-};
-template <> struct Row<__half, 4> {
-  __device__ static void ld(const __half* p, float* o, float inv) {
-    const uint2 t = *reinterpret_cast<const uint2*>(p);
-    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&t.x));
-    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&t.y));
-    o[0] = a.x * inv; o[1] = a.y * inv; o[2] = b.x * inv; o[3] = b.y * inv;
-  }
-  __device__ static void st(__half* p, const float* v, float sc, uint32_t h) {
-    __half2 a, b;
-    a.x = sr_half(v[0] * sc, h);
-    a.y = sr_half(v[1] * sc, h ? mix32(h + 1u) : 0u);
-    b.x = sr_half(v[2] * sc, h ? mix32(h + 2u) : 0u);
-    b.y = sr_half(v[3] * sc, h ? mix32(h + 3u) : 0u);
-    uint2 t;
-    t.x = *reinterpret_cast<const uint32_t*>(&a);
-    t.y = *reinterpret_cast<const uint32_t*>(&b);
-    *reinterpret_cast<uint2*>(p) = t;
-  }
-};
-
-__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
-__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
-
-// One thread owns V consecutive nodes x0 .. x0+V-1 of one row (y, z); a
-// work item (replica, tile, y, z) is one block-wide tile of a row.
-template <int Q, typename S, int V>
-__device__ __forceinline__ void lb_row(const RepDev& rd, const StepInfo& st, const int4 bm) {
-  using L = Lattice<Q>;
-  using R = typename Store<S>::R;
-  const int nx = rd.nx, ny = rd.ny, nz = rd.nz;
-  const int y = bm.z, z = bm.w;
-  const int tpr = nx / V;
-  const int tx = bm.y * blockDim.x + threadIdx.x;
-  const bool active = tx < tpr;
-  const int lane = threadIdx.x & 31;
-  const int x0 = tx * V;
-  const int par = st.n & 1;
-  const S* __restrict__ src = (const S*)rd.f[par];
-  S* __restrict__ dst = (S*)rd.f[par ^ 1];
-  const int N = (int)rd.nnode;
-  const int row = nx * (y + ny * z);
-  const float inv = rd.fp16_inv, scale = rd.fp16_scale;
-
-  // phase 1: every load of the thread (Q aligned rows plus the scalar edge
-  // values at warp boundaries), branch-free so that all of them are in flight
-  // together: inactive tail lanes read a clamped, valid position and discard it,
-  // bounce-back rows are selected, not branched to.
-  const int xa = active ? x0 : (tpr - 1) * V;
-  const int xprev = xa == 0 ? nx - 1 : xa - 1;
-  const int xnext = xa + V >= nx ? 0 : xa + V;
-  R d[Q][V], edge[Q];
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    const int sy = y - L::cy(i);
-    const bool bounce = (sy == 0) | (sy == ny - 1);
-    int sz = z - L::cz(i);
-    sz = sz < 0 ? sz + nz : (sz >= nz ? sz - nz : sz);
-    const S* srow_i = src + i * N + nx * (sy + ny * sz);
-    const S* rp = bounce ? src + L::opp(i) * N + row : srow_i;
-    if (V == 1) {
-      int sx = xa - L::cx(i);
-      sx = sx < 0 ? sx + nx : (sx >= nx ? sx - nx : sx);
-      d[i][0] = Store<S>::ld(rp + (bounce ? xa : sx), inv);
-    } else {
-      Row<S, V>::ld(rp + xa, d[i], inv);
-    }
-    edge[i] = R(0);
-    if (V > 1 && L::cx(i) > 0) edge[i] = Store<S>::ld(rp + xprev, inv);
-    if (V > 1 && L::cx(i) < 0) edge[i] = Store<S>::ld(rp + xnext, inv);
-  }
-  // phase 2: shift the rows with cx != 0 by one node through the neighbour lanes
-  if (V > 1) {
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const int sy = y - L::cy(i);
-      if (L::cx(i) == 0 || sy == 0 || sy == ny - 1) continue;
-      if (L::cx(i) > 0) {                    // source x - 1: previous lane's last node
-        R prev = __shfl_up_sync(0xFFFFFFFFu, d[i][V - 1], 1);
-        if (lane == 0) prev = edge[i];
-#pragma unroll
-        for (int v = V - 1; v > 0; --v) d[i][v] = d[i][v - 1];
-        d[i][0] = prev;
-      } else {                               // source x + 1: next lane's first node
-        R next = __shfl_down_sync(0xFFFFFFFFu, d[i][0], 1);
-        if (lane == 31 || tx + 1 >= tpr) next = edge[i];
-#pragma unroll
-        for (int v = 0; v < V - 1; ++v) d[i][v] = d[i][v + 1];
-        d[i][V - 1] = next;
-      }
-    }
-  }
-  if (!active) return;
-
-  const R om = Cst<R>::omega(rd), om1 = R(1) - om, cf = R(1) - R(0.5) * om;
-  const R gx = Cst<R>::g(rd, 0), gy = Cst<R>::g(rd, 1), gz = Cst<R>::g(rd, 2);
-  R mr[V], mu[3][V];   // post-collision values overwrite d in place
-#pragma unroll
-  for (int v = 0; v < V; ++v) {
-    R drho = 0, jx = 0, jy = 0, jz = 0;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      drho += d[i][v];
-      if (L::cx(i) > 0) jx += d[i][v]; else if (L::cx(i) < 0) jx -= d[i][v];
-      if (L::cy(i) > 0) jy += d[i][v]; else if (L::cy(i) < 0) jy -= d[i][v];
-      if (L::cz(i) > 0) jz += d[i][v]; else if (L::cz(i) < 0) jz -= d[i][v];
-    }
-    const R rho = R(1) + drho;
-    const R ir = recip(rho);
-    const R ux = jx * ir + R(0.5) * gx, uy = jy * ir + R(0.5) * gy, uz = jz * ir + R(0.5) * gz;
-    const R Gx = rho * gx, Gy = rho * gy, Gz = rho * gz;              // F = rho g
-    const R uu = ux * ux + uy * uy + uz * uz;
-    const R uF = ux * Gx + uy * Gy + uz * Gz;
-    // f*_i = (1-om) d_i + w_i (E_i + O_i): E even, O odd in c_i
-    //   E = om drho - 1.5 om rho u.u - 3 cf u.F + cu (4.5 om rho cu + 9 cf cF)
-    //   O = 3 (om rho cu + cf cF)
-    const R K0 = om * drho - R(1.5) * om * rho * uu - R(3) * cf * uF;
-    const R A = R(4.5) * om * rho, B = om * rho, C9 = R(9) * cf;
-    d[0][v] = om1 * d[0][v] + (R)L::w(0) * K0;
-#pragma unroll
-    for (int i = 1; i < Q; ++i) {
-      const int o = L::opp(i);
-      if (o < i) continue;
-      const R cu = L::cx(i) * ux + L::cy(i) * uy + L::cz(i) * uz;
-      const R cF = L::cx(i) * Gx + L::cy(i) * Gy + L::cz(i) * Gz;
-      const R cfF = cf * cF;
-      const R E = K0 + cu * (A * cu + C9 * cF);
-      const R Od = R(3) * (B * cu + cfF);
-      const R w = (R)L::w(i);
-      const R pe = w * E, po = w * Od;
-      const R fi = om1 * d[i][v] + (pe + po);
-      const R fo = om1 * d[o][v] + (pe - po);
-      d[i][v] = fi;
-      d[o][v] = fo;
-    }
-    mr[v] = rho; mu[0][v] = ux; mu[1][v] = uy; mu[2][v] = uz;
-  }
-  // random bits of the binary16 stochastic rounding: per node, population, step
-  const uint32_t hb = sizeof(S) == 2 ? mix32((uint32_t)(row + x0) * 0x9E3779B1u ^ (st.n * 0x632BE5ABu + rd.rep)) : 0u;
-#pragma unroll
-  for (int i = 0; i < Q; ++i)
-    Row<S, V>::st(dst + i * N + row + x0, d[i], scale, hb ? (mix32(hb + 0x27D4EB2Fu * (uint32_t)i) | 1u) : 0u);
-
-  // rho, u: every node on request; otherwise the columns the coupling reads
-  // (x0-1 .. x0+cw and x1-cw-1 .. x1, periodic in x).
-#pragma unroll
-  for (int v = 0; v < V; ++v) {
-    const int x = x0 + v;
-    bool want = st.write_moments;
-    if (!want && rd.has_region) {
-      int da = x - (rd.x0 - 1), db = x - (rd.x1 - rd.cw - 1);
-      da = da < 0 ? da + nx : (da >= nx ? da - nx : da);
-      db = db < 0 ? db + nx : (db >= nx ? db - nx : db);
-      want = da <= rd.cw + 1 || db <= rd.cw + 1;
-    }
-    if (want) {
-      R* rh = (R*)rd.rho;
-      R* uv = (R*)rd.u;
-      rh[row + x] = mr[v];
-      uv[row + x] = mu[0][v];
-      uv[N + row + x] = mu[1][v];
-      uv[2 * N + row + x] = mu[2][v];
-    }
-  }
-}
-
 
 template <int Q, typename S, int V>
 __global__ void __launch_bounds__(128, 5) lb_pull(const RepDev* __restrict__ reps, const int4* __restrict__ bmap,

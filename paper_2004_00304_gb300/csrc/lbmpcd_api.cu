@@ -40,6 +40,12 @@ struct lbmpcd {
   int4* bm_lb = nullptr;
   int2 *bm_p = nullptr, *bm_c = nullptr, *bm_t = nullptr, *bm_cl = nullptr;
   int4* ptab = nullptr;                         // closure patches of the batch: (replica, side, py)
+  int4* bm_lb256 = nullptr;                     // LB map with 256-thread row tiles (persistent kernel)
+  int nb_lb256 = 0;
+  int mode = 0;                                 // 0: per-kernel launches in graphs, 1: persistent
+  int pers_bps = 0;                             // persistent blocks per SM (0: occupancy limit)
+  bool pers_graph = true;                       // the persistent launch captures into a graph
+  unsigned* d_bar = nullptr;                    // grid barrier: count, generation, error
   int nb_lb = 0, nb_p = 0, nb_c = 0, nb_t = 0, nb_cl = 0, n_ptab = 0;
   lbmpcd_net* net = nullptr;                    // learned closure, batch of all replicas' patches
   int cl_P = 0;                                 // patches in the batch
@@ -190,6 +196,7 @@ extern "C" int lbmpcd_create(const lbmpcd_params* params, int n_replicas, void* 
   if (e == cudaSuccess) { e = dalloc(h->allocs, &tmp, sizeof(int) * n_replicas); h->d_pending = (int*)tmp; }
   if (e == cudaSuccess) { e = dalloc(h->allocs, &tmp, sizeof(double) * 3 * n_replicas); h->d_last_shift = (double*)tmp; }
   if (e == cudaSuccess) { e = dalloc(h->allocs, &tmp, sizeof(int) * 16); h->d_flag = (int*)tmp; }
+  if (e == cudaSuccess) { e = dalloc(h->allocs, &tmp, sizeof(unsigned) * 4); h->d_bar = (unsigned*)tmp; }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     std::string m = std::string("allocating handle arrays: ") + cudaGetErrorString(e);
@@ -255,13 +262,17 @@ static int build_maps(lbmpcd* h) {
   if (rc0) return rc0;
   std::vector<int4> lb;
   std::vector<int2> pp, cc, tt, cl;
-  std::vector<int4> pt;
+  std::vector<int4> pt, lb256;
   for (int r = 0; r < h->nrep; ++r) {
     const RepDev& d = h->rd[r];
     const int ntx = (d.nx / h->lbvec + 127) / 128;
     for (int z = 0; z < d.nz; ++z)
       for (int y = 1; y < d.ny - 1; ++y)
         for (int t = 0; t < ntx; ++t) lb.push_back(make_int4(r, t, y, z));
+    const int ntx256 = (d.nx / h->lbvec + 255) / 256;
+    for (int z = 0; z < d.nz; ++z)
+      for (int y = 1; y < d.ny - 1; ++y)
+        for (int t = 0; t < ntx256; ++t) lb256.push_back(make_int4(r, t, y, z));
     if (!d.has_region) continue;
     const long long npb = (d.np + PP_ITEM - 1) / PP_ITEM, ncb = (d.ncell + 256 * CPT - 1) / (256 * CPT), nbb = (d.nbuf + 255) / 256;
     for (long long b = 0; b < npb; ++b) pp.push_back(make_int2(r, (int)b));
@@ -281,6 +292,7 @@ static int build_maps(lbmpcd* h) {
   if (!rc) rc = upload_map(h, &h->bm_t, &h->nb_t, tt);
   if (!rc) rc = upload_map(h, &h->bm_cl, &h->nb_cl, cl);
   if (!rc) rc = upload_map(h, &h->ptab, &h->n_ptab, pt);
+  if (!rc) rc = upload_map(h, &h->bm_lb256, &h->nb_lb256, lb256);
   if (rc) return rc;
   CK(h, cudaMemcpy(h->d_reps, h->rd.data(), sizeof(RepDev) * h->nrep, cudaMemcpyHostToDevice));
   if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
@@ -387,11 +399,19 @@ extern "C" int lbmpcd_set_region(lbmpcd* h, int replica, const int lo[3], const 
 
 // One chunk of kcount steps.  Full (graph) chunks start with the counting
 // sort of the particles; the chunk's first particle pass reads the sorted copy.
+static bool persistent(const lbmpcd* h) { return h->mode == 1 && h->nb_cl == 0; }
+
 static int run_chunk(lbmpcd* h, int kcount, bool sort) {
   Launch L{h->d_reps, h->nrep, h->d_si, h->stream};
   sort = sort && h->nb_p > 0;
   if (sort) CK(h, launch_sort(h->dim, h->prec, L, h->bm_p, h->nb_p, h->bm_t, h->nb_t));
   CK(h, launch_prep(h->dim, L, h->d_si, kcount, sort ? 1 : 0, h->d_step, h->d_pending, h->d_last_shift));
+  if (persistent(h)) {
+    const PersistentMaps m{h->bm_lb256, h->nb_lb256, h->bm_p, h->nb_p, h->bm_c, h->nb_c, h->d_bar,
+                           (int*)(h->d_bar + 2)};
+    CK(h, launch_persistent(h->q, h->prec, h->lbvec, L, kcount, m, h->pers_bps, nullptr));
+    return LBMPCD_OK;
+  }
   for (int k = 0; k < kcount; ++k) {
     CK(h, launch_lb(h->q, h->prec, h->lbvec, L, h->bm_lb, h->nb_lb, k));
     CK(h, launch_particles(h->dim, h->prec, L, h->bm_p, h->nb_p, k));
@@ -410,7 +430,8 @@ extern "C" int lbmpcd_step(lbmpcd* h, int nsteps) {
   if (h->maps_dirty) { int rc = build_maps(h); if (rc) return rc; }
   int left = nsteps;
   while (left >= KCHUNK) {
-    if (!h->graph) {
+    const bool use_graph = !persistent(h) || h->pers_graph;
+    if (use_graph && !h->graph) {
       cudaGraph_t g = nullptr;
       cudaStream_t cap = h->stream;
       bool own = false;
@@ -422,14 +443,27 @@ extern "C" int lbmpcd_step(lbmpcd* h, int nsteps) {
       int rc = run_chunk(h, KCHUNK, true);
       h->stream = keep;
       cudaError_t e = cudaStreamEndCapture(cap, &g);
-      if (rc) { if (g) cudaGraphDestroy(g); if (own) cudaStreamDestroy(cap); return rc; }
-      if (e != cudaSuccess) { if (own) cudaStreamDestroy(cap); return cuda_fail(h, e, "graph capture"); }
-      e = cudaGraphInstantiate(&h->graph, g, 0);
-      cudaGraphDestroy(g);
+      if (!rc && e == cudaSuccess) {
+        e = cudaGraphInstantiate(&h->graph, g, 0);
+        if (e != cudaSuccess) h->graph = nullptr;
+      }
+      if (g) cudaGraphDestroy(g);
       if (own) cudaStreamDestroy(cap);
-      if (e != cudaSuccess) { h->graph = nullptr; return cuda_fail(h, e, "graph instantiate"); }
+      if (rc || e != cudaSuccess || !h->graph) {
+        if (!persistent(h)) return rc ? rc : cuda_fail(h, e, "graph capture");
+        // the cooperative launch did not capture: launch the persistent chunks directly
+        cudaGetLastError();
+        h->pers_graph = false;
+        h->graph = nullptr;
+        continue;
+      }
     }
-    CK(h, cudaGraphLaunch(h->graph, h->stream));
+    if (use_graph) {
+      CK(h, cudaGraphLaunch(h->graph, h->stream));
+    } else {
+      int rc = run_chunk(h, KCHUNK, true);
+      if (rc) return rc;
+    }
     left -= KCHUNK;
     h->nstep += KCHUNK;
   }
@@ -443,6 +477,15 @@ extern "C" int lbmpcd_step(lbmpcd* h, int nsteps) {
   if (nsteps > 0 && h->cl_params) {   // a bounded wait inside a closure GEMM gave up
     const int rc = net_error(h->net, h->stream);
     if (rc) return fail(h, rc, "closure network: a tensor-core wait timed out");
+  }
+  if (nsteps > 0 && persistent(h)) {   // a bounded grid-barrier wait gave up
+    unsigned bar[4] = {0, 0, 0, 0};
+    CK(h, cudaMemcpyAsync(bar, h->d_bar, sizeof(bar), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (bar[2]) {
+      CK(h, cudaMemset(h->d_bar, 0, sizeof(bar)));
+      return fail(h, LBMPCD_ERR_TIMEOUT, "persistent step: a grid-barrier wait timed out");
+    }
   }
   return LBMPCD_OK;
 }
@@ -681,5 +724,82 @@ extern "C" int lbmpcd_set_closure(lbmpcd* h, const float* theta, long long count
     h->cl_params = true;
   }
   if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }   // the step's kernels changed
+  return LBMPCD_OK;
+}
+
+extern "C" int lbmpcd_set_launch_mode(lbmpcd* h, int mode, int blocks_per_sm) {
+  if (!h) return LBMPCD_ERR_INVALID_ARG;
+  if (mode < 0 || mode > 1 || blocks_per_sm < 0) return fail(h, LBMPCD_ERR_INVALID_ARG, "mode must be 0 or 1");
+  if (mode == 1)
+    for (int r = 0; r < h->nrep; ++r)
+      if (h->rd[r].cl_on) return fail(h, LBMPCD_ERR_INVALID_ARG, "the persistent form does not run the learned closure");
+  h->mode = mode;
+  h->pers_bps = blocks_per_sm;
+  h->pers_graph = true;
+  if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
+  return LBMPCD_OK;
+}
+
+// Time each candidate launch configuration on a fresh copy of the handle (same
+// parameters and regions, so the handle's own state is untouched) and keep the
+// fastest: {per-kernel graphs, persistent at the occupancy limit, persistent
+// with one block per SM} x {the default LB row width, one node per thread}.
+extern "C" int lbmpcd_autotune(lbmpcd* h, int steps, int* choice) {
+  if (!h) return LBMPCD_ERR_INVALID_ARG;
+  if (steps < 1) return fail(h, LBMPCD_ERR_INVALID_ARG, "steps must be >= 1");
+  bool closure = false;
+  for (int r = 0; r < h->nrep; ++r) closure = closure || h->rd[r].cl_on;
+  struct Cand { int mode, bps, vec; };
+  const int vdef = h->lbvec;
+  std::vector<Cand> cands = {{0, 0, vdef}};
+  if (vdef != 1) cands.push_back({0, 0, 1});
+  if (!closure) {
+    cands.push_back({1, 0, vdef});
+    cands.push_back({1, 1, vdef});
+  }
+  lbmpcd* c = nullptr;
+  int rc = lbmpcd_create(h->P.data(), h->nrep, h->stream, &c);
+  if (rc) return fail(h, rc, std::string("autotune copy: ") + g_create_error);
+  for (int r = 0; r < h->nrep && !rc; ++r) {
+    if (!h->rd[r].has_region) continue;
+    const int lo[3] = {h->rd[r].x0, 0, 0}, hi[3] = {h->rd[r].x1, h->P[r].ny, h->P[r].nz};
+    rc = lbmpcd_set_region(c, r, lo, hi);
+  }
+  std::vector<float> ms(cands.size(), 1e30f);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (!rc && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) rc = LBMPCD_ERR_CUDA;
+  for (size_t i = 0; i < cands.size() && !rc; ++i) {
+    c->lbvec = cands[i].vec;
+    c->maps_dirty = true;
+    rc = lbmpcd_set_launch_mode(c, cands[i].mode, cands[i].bps);
+    if (!rc) rc = lbmpcd_step(c, KCHUNK);   // warm-up, graph capture
+    if (!rc && cudaEventRecord(e0, c->stream) != cudaSuccess) rc = LBMPCD_ERR_CUDA;
+    if (!rc) rc = lbmpcd_step(c, steps);
+    if (!rc && cudaEventRecord(e1, c->stream) != cudaSuccess) rc = LBMPCD_ERR_CUDA;
+    if (!rc && cudaEventSynchronize(e1) != cudaSuccess) rc = LBMPCD_ERR_CUDA;
+    if (!rc) cudaEventElapsedTime(&ms[i], e0, e1);
+    if (rc == LBMPCD_ERR_TIMEOUT || (rc == LBMPCD_ERR_CUDA && cands[i].mode == 1)) {
+      rc = LBMPCD_OK;   // a candidate that cannot run is skipped
+      ms[i] = 1e30f;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  const std::string why = rc ? std::string(c->err) : std::string();
+  lbmpcd_destroy(c);
+  if (rc) return fail(h, rc, "autotune: " + why);
+  size_t best = 0;
+  for (size_t i = 1; i < cands.size(); ++i) if (ms[i] < ms[best]) best = i;
+  if (ms[best] >= 1e30f) return fail(h, LBMPCD_ERR_CUDA, "autotune: no candidate ran");
+  h->lbvec = cands[best].vec;
+  h->maps_dirty = true;
+  rc = lbmpcd_set_launch_mode(h, cands[best].mode, cands[best].bps);
+  if (rc) return rc;
+  if (choice) {
+    choice[0] = cands[best].mode;
+    choice[1] = cands[best].bps;
+    choice[2] = cands[best].vec;
+    choice[3] = (int)cands.size();
+  }
   return LBMPCD_OK;
 }

@@ -32,7 +32,9 @@
 // the non-contractible __dadd_rn/__dmul_rn, so FP64 runs bin every particle
 // into the same cell as a binary64 reference would; in binary32 the compiler
 // may fuse them.
-#include "kernels.h"
+#include <type_traits>
+
+#include "lb_core.cuh"
 
 namespace lbm {
 
@@ -274,7 +276,7 @@ __device__ __forceinline__ void particle_item(const RepDev& rd, const StepInfo& 
   using T4 = typename Vec4<R>::T;
   const uint32_t j0 = (uint32_t)bm.y * PP_ITEM + threadIdx.x;
   const bool alt = st.src_alt;
-  const uint32_t* __restrict__ hsrc = alt ? rd.home_alt : rd.home;
+  const uint32_t* hsrc = alt ? rd.home_alt : rd.home;   // plain loads (see lb_row)
   int X[PPT], Y[PPT], Z[PPT];
   R o[PPT][3], v[PPT][3];
   bool act[PPT];
@@ -609,6 +611,121 @@ cudaError_t launch_cells(int q, int prec, const Launch& L, const int2* bmap, int
   }
 #undef LBM_CELLS
   return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Persistent form of a chunk: one cooperative launch runs kcount steps, each
+// as the three phases lb_pull -> particle_pass -> cell_pass over the same
+// block maps (the LB map with 256-thread row tiles), separated by a grid
+// barrier.  The barrier is a counter and a generation word in global memory;
+// every wait is bounded: after PB_SPIN polls a block records the failure in
+// *err and leaves the launch, so a stuck barrier ends the kernel instead of
+// hanging the GPU.  Co-residency of all blocks comes from the cooperative launch.
+constexpr unsigned PB_SPIN = 1u << 24;
+
+__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, unsigned nblocks, int* err) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned g = atomicAdd(gen, 0u);
+    __threadfence();
+    int ok = 1;
+    if (atomicAdd(count, 1u) + 1u == nblocks) {
+      atomicExch(count, 0u);
+      __threadfence();
+      atomicAdd(gen, 1u);
+    } else {
+      unsigned it = 0;
+      const volatile unsigned* vg = gen;
+      const volatile int* ve = err;
+      while (*vg == g) {   // plain polling loads (L2), no atomic traffic on the word
+        if (++it >= PB_SPIN || *ve != 0) { ok = 0; break; }
+        __nanosleep(32);
+      }
+      if (!ok) atomicExch(err, 1);
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+template <int Q, typename S, int V>
+__global__ void __launch_bounds__(256, 2) step_persistent(const RepDev* __restrict__ reps, int nrep,
+                                                         const StepInfo* __restrict__ si, int kcount,
+                                                         const int4* __restrict__ bm_lb, int nb_lb,
+                                                         const int2* __restrict__ bm_p, int nb_p,
+                                                         const int2* __restrict__ bm_c, int nb_c,
+                                                         unsigned* bar, int* err) {
+  constexpr int D = Q == 9 ? 2 : 3;
+  using R = typename std::conditional<sizeof(S) == 8, double, float>::type;
+  __shared__ RepDev rd;
+  __shared__ StepInfo st;
+  __shared__ PassShared<D, R> red;
+  for (int k = 0; k < kcount; ++k) {
+    for_each_item(bm_lb, nb_lb, reps, si, k, nrep, rd, st, [&](const int4 bm) { lb_row<Q, S, V>(rd, st, bm); });
+    if (!grid_barrier(bar, bar + 1, gridDim.x, err)) return;
+    for_each_item(bm_p, nb_p, reps, si, k, nrep, rd, st, [&](const int2 bm) { particle_item<D, R>(rd, st, bm, red); });
+    if (!grid_barrier(bar, bar + 1, gridDim.x, err)) return;
+    for_each_item(bm_c, nb_c, reps, si, k, nrep, rd, st, [&](const int2 bm) { cell_item<Q, S>(rd, st, bm); });
+    if (!grid_barrier(bar, bar + 1, gridDim.x, err)) return;
+  }
+}
+
+template <int Q, typename S, int V>
+static cudaError_t go_persistent(const Launch& L, int kcount, const PersistentMaps& m, int blocks_per_sm,
+                                 int* grid_out) {
+  static int occ = -1, sms = 0;
+  if (occ < 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, step_persistent<Q, S, V>, 256, 0) != cudaSuccess) occ = 0;
+  }
+  if (occ < 1) return cudaErrorCooperativeLaunchTooLarge;
+  const int bps = blocks_per_sm > 0 && blocks_per_sm < occ ? blocks_per_sm : occ;
+  const int grid = bps * sms;
+  if (grid_out) *grid_out = grid;
+  const RepDev* reps = L.reps;
+  int nrep = L.nrep;
+  const StepInfo* si = L.si;
+  const int4* bl = m.lb;
+  const int2 *bp = m.p, *bc = m.c;
+  int nl = m.nb_lb, np = m.nb_p, nc = m.nb_c;
+  unsigned* bar = m.bar;
+  int* err = m.err;
+  void* args[] = {(void*)&reps, (void*)&nrep, (void*)&si, (void*)&kcount, (void*)&bl, (void*)&nl,
+                  (void*)&bp,   (void*)&np,   (void*)&bc, (void*)&nc,     (void*)&bar, (void*)&err};
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = L.stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelExC(&cfg, (const void*)step_persistent<Q, S, V>, args);
+}
+
+cudaError_t launch_persistent(int q, int prec, int vec, const Launch& L, int kcount, const PersistentMaps& m,
+                              int blocks_per_sm, int* grid_out) {
+  if (q == 9) {
+    if (prec == P_FP64) return go_persistent<9, double, 1>(L, kcount, m, blocks_per_sm, grid_out);
+    if (prec == P_FP32)
+      return vec == 4 ? go_persistent<9, float, 4>(L, kcount, m, blocks_per_sm, grid_out)
+                      : go_persistent<9, float, 1>(L, kcount, m, blocks_per_sm, grid_out);
+    return vec == 4 ? go_persistent<9, __half, 4>(L, kcount, m, blocks_per_sm, grid_out)
+                    : go_persistent<9, __half, 1>(L, kcount, m, blocks_per_sm, grid_out);
+  }
+  if (prec == P_FP64) return go_persistent<19, double, 1>(L, kcount, m, blocks_per_sm, grid_out);
+  if (prec == P_FP32)
+    return vec == 2 ? go_persistent<19, float, 2>(L, kcount, m, blocks_per_sm, grid_out)
+                    : go_persistent<19, float, 1>(L, kcount, m, blocks_per_sm, grid_out);
+  return vec == 2 ? go_persistent<19, __half, 2>(L, kcount, m, blocks_per_sm, grid_out)
+                  : go_persistent<19, __half, 1>(L, kcount, m, blocks_per_sm, grid_out);
 }
 
 // ---------------------------------------------------------------------------

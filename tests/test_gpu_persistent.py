@@ -1,0 +1,103 @@
+"""The persistent launch form (one cooperative kernel per chunk, grid barriers
+between the LB, particle and cell phases) and the autotuner, against the
+FP64 oracle (GPU).  Tolerances as in test_gpu_parity: 1e-12 relative in FP64,
+integer results bit-exact."""
+import numpy as np
+import pytest
+
+import oracle as O
+from tests import inputs
+from tests.test_gpu_parity import FLOOR, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lb():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2004_00304_gb300 as mod
+    return mod
+
+
+def _check(g, o):
+    assert np.array_equal(g.get("SHIFT"), o.get("SHIFT"))
+    assert np.array_equal(g.get("PART_HOME"), o.get("PART_HOME"))
+    assert np.array_equal(g.get("PART_CELL"), o.get("PART_CELL"))
+    assert np.array_equal(g.get("CELL_COUNT"), o.get("CELL_COUNT"))
+    for f in ("PART_POS", "PART_VEL", "CELL_VCM", "WINDOW_MEAN", "POPS", "U"):
+        e = rel_err(g.get(f), o.get(f), FLOOR.get(f, 0.0))
+        assert e <= 1e-12, (f, e)
+
+
+@pytest.mark.parametrize("case,bps", [("2d", 0), ("2d", 1), ("3d", 0)])
+def test_persistent_matches_oracle(lb, case, bps):
+    """70 steps = one 64-step chunk (sort + one persistent launch) and a
+    6-step remainder launch, then 3 more single steps."""
+    cfg = inputs.small_2d(precision=0, nx=72) if case == "2d" else inputs.small_3d(precision=0, nx=24)
+    g = lb.Lbmpcd(cfg["params"])
+    g.set_region(0, *cfg["region"])
+    g.set_launch_mode(1, bps)
+    o = O.OracleSim(cfg["params"])
+    o.set_region(*cfg["region"])
+    g.step(70)
+    o.step(70)
+    _check(g, o)
+    for _ in range(3):
+        g.step(1)
+        o.step(1)
+    _check(g, o)
+    g.close()
+
+
+def test_persistent_uneven_replicas(lb):
+    """Three uneven replicas (one without a region) in one persistent launch."""
+    reps = [inputs.small_2d(precision=0, seed=31, nx=72),
+            inputs.small_2d(precision=0, seed=32, nx=40, ny=14, refine=1, ppc=5),
+            inputs.small_2d(precision=0, seed=33, nx=36, ny=20)]
+    g = lb.Lbmpcd([r["params"] for r in reps])
+    g.set_region(0, *reps[0]["region"])
+    g.set_region(1, 10, 30)
+    g.set_launch_mode(1)
+    o = [O.OracleSim(r["params"], replica=k) for k, r in enumerate(reps)]
+    o[0].set_region(*reps[0]["region"])
+    o[1].set_region(10, 30)
+    g.step(66)
+    for k in range(3):
+        o[k].step(66)
+        e = rel_err(g.get("POPS", k), o[k].get("POPS"))
+        assert e <= 1e-12, (k, e)
+    for k in (0, 1):
+        assert np.array_equal(g.get("PART_HOME", k), o[k].get("PART_HOME"))
+        assert rel_err(g.get("PART_VEL", k), o[k].get("PART_VEL")) <= 1e-12
+    g.close()
+
+
+def test_autotune_keeps_the_state_and_the_results(lb):
+    """The autotuner times its candidates on a copy: afterwards the handle
+    still starts from step 0 and matches the oracle in whatever form it chose."""
+    cfg = inputs.small_2d(precision=0, nx=72)
+    g = lb.Lbmpcd(cfg["params"])
+    g.set_region(0, *cfg["region"])
+    choice = g.autotune(steps=64)
+    print("autotune choice", choice)
+    assert choice["mode"] in (0, 1) and choice["candidates"] >= 3
+    o = O.OracleSim(cfg["params"])
+    o.set_region(*cfg["region"])
+    g.step(67)
+    o.step(67)
+    _check(g, o)
+    g.close()
+
+
+def test_persistent_mode_rejects_the_closure(lb):
+    cfg = inputs.small_2d(feedback=2)
+    g = lb.Lbmpcd(cfg["params"])
+    g.set_region(0, *cfg["region"])
+    with pytest.raises(lb.LbmpcdError) as ei:
+        g.set_launch_mode(1)
+    assert ei.value.code == -1
+    g.close()
