@@ -12,7 +12,7 @@ namespace lbm {
 // precision codes (match LBMPCD_FP64 / FP32 / FP16DEV)
 enum { P_FP64 = 0, P_FP32 = 1, P_FP16 = 2 };
 
-constexpr int PPT = 4;                       // particles per thread in particle_pass
+constexpr int PPT = 2;                       // particles per thread in particle_pass (swept: 2, 4, 8)
 constexpr int PP_ITEM = 256 * PPT;           // particles per work item
 constexpr int CPT = 4;                       // collision cells per thread in cell_pass
 

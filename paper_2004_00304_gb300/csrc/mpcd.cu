@@ -261,10 +261,10 @@ __device__ __forceinline__ void stream(const RepDev& rd, int& X, int& Y, int& Z,
 }
 
 // One work item = PP_ITEM consecutive particles; thread t handles particles
-// t, t + 256, t + 512, t + 768 of the item, so that every round of the warp
-// covers 32 consecutive particles.  All state loads of the four particles are
-// issued first, then their four cell-table loads, before any arithmetic:
-// each thread keeps ~100 bytes in flight instead of one dependent chain.
+// t, t + 256, ... (PPT of them) of the item, so that every round of the warp
+// covers 32 consecutive particles.  All state loads of the thread's particles
+// are issued first, then their cell-table loads, before any arithmetic, so
+// they are in flight together instead of forming one dependent chain.
 // shared memory of particle_pass: staging of the warp-aggregated reduction
 template <int D, typename R> struct PassShared {
   R sv[D][256];
@@ -375,9 +375,19 @@ __device__ __forceinline__ void particle_item(const RepDev& rd, const StepInfo& 
     PState<D, R>::st(rd.off, j, o[p]);
     PState<D, R>::st(rd.vel, j, v[p]);
   }
-  // warp-aggregated reduction, one round per particle slot: lanes sharing a
+  // Cell sums.  Binary32: one vector atomic {1, v} per particle (measured as
+  // fast as the warp-aggregated form below at 4 particles per thread, and
+  // faster at 2, with fewer instructions and registers).  Binary64: warp-
+  // aggregated reduction, one round per particle slot: lanes sharing a
   // collision cell are summed by their lowest lane, which issues one atomic
   // per accumulator.
+  if (sizeof(R) == 4) {
+#pragma unroll
+    for (int p = 0; p < PPT; ++p)
+      if (act[p])
+        atomicAdd(rd.acc4 + cid[p], make_float4(1.0f, (float)v[p][0], (float)v[p][1], D == 3 ? (float)v[p][D - 1] : 0.0f));
+    return;
+  }
   const int lane = threadIdx.x & 31, wbase = threadIdx.x & ~31;
 #pragma unroll
   for (int p = 0; p < PPT; ++p) {
@@ -414,7 +424,7 @@ __device__ __forceinline__ void particle_item(const RepDev& rd, const StepInfo& 
 }
 
 template <int D, typename R>
-__global__ void __launch_bounds__(256) particle_pass(const RepDev* __restrict__ reps, const int2* __restrict__ bmap,
+__global__ void __launch_bounds__(256, 6) particle_pass(const RepDev* __restrict__ reps, const int2* __restrict__ bmap,
                                                      int nwork, const StepInfo* __restrict__ si, int k, int nrep) {
   __shared__ RepDev rd;
   __shared__ StepInfo st;
