@@ -327,8 +327,9 @@ def choose_launch(sim, args) -> dict:
     if args.launch == "auto":
         return sim.autotune(steps=256)
     mode = 1 if args.launch == "persistent" else 0
-    sim.set_launch_mode(mode)
-    return dict(mode=mode, blocks_per_sm=0, lb_nodes_per_thread=None, candidates=1)
+    tma = args.launch == "graphs_tma"
+    sim.set_launch_mode(mode, lb_tma=tma)
+    return dict(mode=mode, blocks_per_sm=0, lb_nodes_per_thread=None, lb_tma=tma, candidates=1)
 
 
 def run_ensemble(args):
@@ -518,7 +519,7 @@ def main():
                     help="channel: the 2048x512 headline workload; ensemble: the 64-replica ensemble; "
                          "closure: training, gain and in-loop runs of the learned closure (extra lines)")
     ap.add_argument("--fp16", action="store_true", help="ensemble only: FP16 deviation storage")
-    ap.add_argument("--launch", default="auto", choices=["auto", "graphs", "persistent"],
+    ap.add_argument("--launch", default="auto", choices=["auto", "graphs", "graphs_tma", "persistent"],
                     help="launch form of the step: autotuned (default), per-kernel graphs, persistent kernel")
     args = ap.parse_args()
     if args.warmup < 3:

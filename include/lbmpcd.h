@@ -256,17 +256,23 @@ int lbmpcd_set_closure(lbmpcd* h, const float* theta, long long count, int src_o
  * blocks_per_sm: persistent blocks per SM (0 = the occupancy limit).  Results
  * are those of mode 0 (same per-step records, same kernels' item code).  Mode 1
  * is not available with the learned closure (INVALID_ARG); lbmpcd_step_profiled
- * always launches per kernel. */
-int lbmpcd_set_launch_mode(lbmpcd* h, int mode, int blocks_per_sm);
+ * always launches per kernel.  flags: LBMPCD_LAUNCH_LB_TMA runs the LB update
+ * of D2Q9 binary32 channels (4 nodes per thread) with its source rows staged in
+ * shared memory by bulk (TMA) copies, three rows ahead per block; ignored for
+ * other lattices and precisions.  A bounded wait in that kernel that gives up
+ * is reported by the next lbmpcd_get_fields as ERR_TIMEOUT. */
+#define LBMPCD_LAUNCH_LB_TMA 1   /* flags: D2Q9 binary32 LB rows staged by bulk (TMA) copies */
+int lbmpcd_set_launch_mode(lbmpcd* h, int mode, int blocks_per_sm, int flags);
 
-/* Time the launch forms {mode 0, mode 1 at the occupancy limit, mode 1 with
- * one block per SM} x {the default LB row width, one node per thread} for
- * `steps` steps each (after a 64-step warm-up) on a fresh copy of the handle
- * built from the same parameters and regions -- the handle's own state is not
- * touched -- and keep the fastest.  choice (may be NULL) receives {mode,
- * blocks_per_sm, LB nodes per thread, candidates timed}.  Needs the memory of
- * a second handle for the duration of the call.  Errors: INVALID_ARG, OOM, CUDA. */
-int lbmpcd_autotune(lbmpcd* h, int steps, int choice[4]);
+/* Time the launch forms {mode 0 with the default LB row width, with TMA rows
+ * (where they apply), with one LB node per thread; mode 1 at the occupancy
+ * limit and with one block per SM} for `steps` steps each (after a 64-step
+ * warm-up) on a fresh copy of the handle built from the same parameters and
+ * regions -- the handle's own state is not touched -- and keep the fastest.
+ * choice (may be NULL) receives {mode, blocks_per_sm, LB nodes per thread,
+ * flags, candidates timed}.  Needs the memory of a second handle for the
+ * duration of the call.  Errors: INVALID_ARG, OOM, CUDA. */
+int lbmpcd_autotune(lbmpcd* h, int steps, int choice[5]);
 
 /* Element count of a field for a replica (or a negative error code). */
 long long lbmpcd_field_size(const lbmpcd* h, int replica, int field);

@@ -27,6 +27,7 @@ FIELDS = dict(RHO=0, U=1, POPS=2, PART_POS=3, PART_VEL=4, PART_CELL=5, SHIFT=6,
               CELL_COUNT=7, WINDOW_MEAN=8, DIAG=9, PART_HOME=10, CELL_VCM=11, PART_ID=12,
               CLOSURE_IN=13, CLOSURE_OUT=14, CLOSURE_TARGET=15)
 INT_FIELDS = {"PART_CELL", "CELL_COUNT", "PART_HOME", "PART_ID"}
+LAUNCH_LB_TMA = 1   # LBMPCD_LAUNCH_LB_TMA
 ERRORS = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "TIMEOUT", -5: "STATE", -6: "CAPACITY"}
 
 
@@ -80,7 +81,7 @@ def load_library(path: str = LIB_PATH):
     L.lbmpcd_net_destroy.argtypes = [vp]
     L.lbmpcd_net_forward_noalloc.argtypes = [vp, vp, ci, vp, vp]
     L.lbmpcd_set_closure.argtypes = [vp, vp, ll, ci, ci]
-    L.lbmpcd_set_launch_mode.argtypes = [vp, ci, ci]
+    L.lbmpcd_set_launch_mode.argtypes = [vp, ci, ci, ci]
     L.lbmpcd_autotune.argtypes = [vp, ci, ctypes.POINTER(ci)]
     L.lbmpcd_net_destroy.restype = None
     L.lbmpcd_destroy.argtypes = [vp]
@@ -321,15 +322,18 @@ class Lbmpcd:
     def set_closure(self, theta, interval: int = 1):
         lbmpcd_set_closure(self._h, theta, interval)
 
-    def set_launch_mode(self, mode: int, blocks_per_sm: int = 0):
-        """0: per-kernel launches in 64-step graphs; 1: one persistent kernel per chunk."""
-        _check(self._h, load_library().lbmpcd_set_launch_mode(self._h, int(mode), int(blocks_per_sm)))
+    def set_launch_mode(self, mode: int, blocks_per_sm: int = 0, lb_tma: bool = False):
+        """0: per-kernel launches in 64-step graphs; 1: one persistent kernel per
+        chunk.  lb_tma: TMA-staged LB rows (D2Q9 binary32)."""
+        _check(self._h, load_library().lbmpcd_set_launch_mode(self._h, int(mode), int(blocks_per_sm),
+                                                              LAUNCH_LB_TMA if lb_tma else 0))
 
     def autotune(self, steps: int = 256) -> dict:
         """Time the launch forms on a copy of this handle and keep the fastest."""
-        out = (ctypes.c_int * 4)()
+        out = (ctypes.c_int * 5)()
         _check(self._h, load_library().lbmpcd_autotune(self._h, int(steps), out))
-        return dict(mode=out[0], blocks_per_sm=out[1], lb_nodes_per_thread=out[2], candidates=out[3])
+        return dict(mode=out[0], blocks_per_sm=out[1], lb_nodes_per_thread=out[2], lb_tma=bool(out[3] & LAUNCH_LB_TMA),
+                    candidates=out[4])
 
     def get(self, field: str, replica: int = 0, out=None):
         return lbmpcd_get_fields(self._h, replica, field, out)

@@ -21,12 +21,16 @@ struct Launch {
   int nrep;
   const StepInfo* si;     // device [kcount][nrep]
   cudaStream_t stream;
+  int* err;               // set by a kernel whose bounded wait gave up
 };
 
 // a1: fused pull stream + BGK collide (+ Guo force, bounce-back walls).
 // vec = nodes per thread (lb_vector_width); one vec for all replicas of a handle.
+// tma: D2Q9 binary32 rows of 4 nodes per thread staged by bulk copies
+// (lb_tma_ok); same 512-node tiles as vec 4.
 int lb_vector_width(int q, int prec, int nx);
-cudaError_t launch_lb(int q, int prec, int vec, const Launch& L, const int4* bmap, int nblocks, int k);
+bool lb_tma_ok(int q, int prec, int vec);
+cudaError_t launch_lb(int q, int prec, int vec, bool tma, const Launch& L, const int4* bmap, int nblocks, int k);
 
 // prep: per-step records (shift, pending flag) for kcount steps.
 cudaError_t launch_prep(int dim, const Launch& L, StepInfo* si, int kcount, int sorted, uint32_t* d_step,

@@ -12,6 +12,7 @@
 // binary32 / scaled binary16 storage.  HBM traffic: one read and one write of
 // q populations per node.
 #include "lb_core.cuh"
+#include "tc_gemm.cuh"
 
 namespace lbm {
 
@@ -31,6 +32,134 @@ static cudaError_t go_lb(const Launch& L, const int4* bmap, int nwork, int k) {
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// a1 for D2Q9 binary32 rows with TMA staging.  A work item is a tile of up to
+// TL_W = 512 nodes of one row (128 threads x 4 nodes).  Its 9 source segments
+// (population i of row y - c_iy, or population opp(i) of row y where that row
+// is a wall: half-way bounce-back) are brought into shared memory by bulk
+// copies, each with a 4-node halo on both sides (wrapped periodically in x),
+// into a ring of TL_STAGES stages; one thread issues the copies of the item
+// TL_STAGES items ahead as soon as a stage is free, so that several rows per
+// block are in flight without holding registers.  The collision is lb_finish,
+// the same code as lb_pull.  Every mbarrier wait is bounded; a timeout sets
+// *err, and the block waits (bounded) for its copies in flight and returns.
+constexpr int TL_W = 512, TL_SEG = TL_W + 8, TL_STAGES = 3;
+constexpr int TL_SMEM = TL_STAGES * 9 * TL_SEG * 4;
+
+__device__ __forceinline__ void tl_copy(float* dst, const float* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(bytes), "r"((uint32_t)__cvta_generic_to_shared(bar))
+               : "memory");
+}
+
+// issue the copies of one item into one stage (one thread)
+__device__ __forceinline__ void tl_issue(const RepDev* __restrict__ reps, const StepInfo* __restrict__ si, int k,
+                                         int nrep, const int4 bm, float* stage, uint64_t* bar) {
+  using L = Lattice<9>;
+  const RepDev& r = reps[bm.x];
+  const int nx = r.nx, ny = r.ny, y = bm.z;
+  const long long N = r.nnode;
+  const float* src = (const float*)r.f[si[(long long)k * nrep + bm.x].n & 1];
+  const int x0 = bm.y * TL_W, len = min(TL_W, nx - x0);
+  const uint32_t b = (uint32_t)__cvta_generic_to_shared(bar);
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(b),
+               "r"((uint32_t)(9 * (len + 8) * 4))
+               : "memory");
+  const int xl = x0 == 0 ? nx - 4 : x0 - 4, xr = x0 + len == nx ? 0 : x0 + len;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const int sy = y - L::cy(i);
+    const bool bounce = (sy == 0) | (sy == ny - 1);
+    const float* row = bounce ? src + L::opp(i) * N + (long long)y * nx : src + i * N + (long long)sy * nx;
+    float* seg = stage + i * TL_SEG;
+    tl_copy(seg, row + xl, 16u, bar);
+    tl_copy(seg + 4, row + x0, (uint32_t)len * 4u, bar);
+    tl_copy(seg + 4 + len, row + xr, 16u, bar);
+  }
+}
+
+__global__ void __launch_bounds__(128) lb_pull_tma(const RepDev* __restrict__ reps, const int4* __restrict__ bmap,
+                                                   int nwork, const StepInfo* __restrict__ si, int k, int nrep,
+                                                   int* err) {
+  using L = Lattice<9>;
+  extern __shared__ __align__(16) float tsm[];
+  __shared__ __align__(8) uint64_t full[TL_STAGES];
+  __shared__ RepDev rd;
+  __shared__ StepInfo st;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    for (int s = 0; s < TL_STAGES; ++s) tc::mbar_init(&full[s], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    for (int j = 0; j < TL_STAGES; ++j) {
+      const int wi = blockIdx.x + j * gridDim.x;
+      if (wi < nwork) tl_issue(reps, si, k, nrep, bmap[wi], tsm + j * 9 * TL_SEG, &full[j]);
+    }
+  }
+  __syncthreads();
+  int cur = -1, it = 0;
+  for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x, ++it) {
+    const int s = it % TL_STAGES;
+    const int4 bm = bmap[wi];
+    if (bm.x != cur) {
+      __syncthreads();
+      load_block_records(rd, st, reps, si, bm.x, k, nrep);
+      cur = bm.x;
+    }
+    const bool ok = tc::mbar_wait(&full[s], (uint32_t)((it / TL_STAGES) & 1));
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        atomicExch(err, 1);
+        for (int q = 0; q < TL_STAGES; ++q) tc::mbar_wait(&full[q], (uint32_t)(((it + q) / TL_STAGES) & 1));
+      }
+      __syncthreads();
+      return;
+    }
+    const int x0 = bm.y * TL_W, len = min(TL_W, rd.nx - x0), xl = 4 * tid;
+    if (xl < len) {
+      const float* stage = tsm + s * 9 * TL_SEG;
+      const int y = bm.z;
+      float d[9][4];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        const int sy = y - L::cy(i);
+        const bool bounce = (sy == 0) | (sy == rd.ny - 1);
+        const float* seg = stage + i * TL_SEG + 4 + xl;   // node x0 + xl
+        const float4 c = *reinterpret_cast<const float4*>(seg);
+        if (L::cx(i) == 0 || bounce) {
+          d[i][0] = c.x; d[i][1] = c.y; d[i][2] = c.z; d[i][3] = c.w;
+        } else if (L::cx(i) > 0) {   // source x - 1
+          d[i][0] = seg[-1]; d[i][1] = c.x; d[i][2] = c.y; d[i][3] = c.z;
+        } else {                     // source x + 1
+          d[i][0] = c.y; d[i][1] = c.z; d[i][2] = c.w; d[i][3] = seg[4];
+        }
+      }
+      lb_finish<9, float, 4>(rd, st, d, x0 + xl, rd.nx * y);
+    }
+    __syncthreads();   // every thread is done with stage s
+    if (tid == 0) {
+      const int nxt = wi + TL_STAGES * gridDim.x;
+      if (nxt < nwork) tl_issue(reps, si, k, nrep, bmap[nxt], tsm + s * 9 * TL_SEG, &full[s]);
+    }
+  }
+}
+
+static cudaError_t go_lb_tma(const Launch& L, const int4* bmap, int nwork, int k) {
+  if (nwork == 0) return cudaSuccess;
+  static int g = 0;
+  if (!g) {
+    if (cudaFuncSetAttribute(lb_pull_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, TL_SMEM) != cudaSuccess)
+      return cudaErrorInvalidValue;
+    int dev = 0, sms = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lb_pull_tma, 128, TL_SMEM);
+    g = (occ > 0 ? occ : 1) * (sms > 0 ? sms : 1);
+  }
+  lb_pull_tma<<<g < nwork ? g : nwork, 128, TL_SMEM, L.stream>>>(L.reps, bmap, nwork, L.si, k, L.nrep, L.err);
+  return cudaGetLastError();
+}
+
 // Nodes per thread: 4 for D2Q9 rows, 2 for D3Q19 rows (19 populations per
 // node), 1 in binary64 or when the row length is not a multiple.
 int lb_vector_width(int q, int prec, int nx) {
@@ -39,7 +168,10 @@ int lb_vector_width(int q, int prec, int nx) {
   return nx % v == 0 ? v : 1;
 }
 
-cudaError_t launch_lb(int q, int prec, int vec, const Launch& L, const int4* bmap, int nblocks, int k) {
+bool lb_tma_ok(int q, int prec, int vec) { return q == 9 && prec == P_FP32 && vec == 4; }
+
+cudaError_t launch_lb(int q, int prec, int vec, bool tma, const Launch& L, const int4* bmap, int nblocks, int k) {
+  if (tma && lb_tma_ok(q, prec, vec)) return go_lb_tma(L, bmap, nblocks, k);
   if (q == 9) {
     if (prec == P_FP64) return go_lb<9, double, 1>(L, bmap, nblocks, k);
     if (prec == P_FP32) return vec == 4 ? go_lb<9, float, 4>(L, bmap, nblocks, k) : go_lb<9, float, 1>(L, bmap, nblocks, k);

@@ -67,78 +67,18 @@ template <> struct Row<__half, 4> {
 __device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 
-// One thread owns V consecutive nodes x0 .. x0+V-1 of one row (y, z); a
-// work item (replica, tile, y, z) is one block-wide tile of a row.
+// Collision (BGK + Guo source, Eq. 1-2) of V consecutive nodes x0.. of the
+// row starting at node index `row`, whose arrived populations are d[i][v]; the
+// post-collision values go to the other buffer, rho / u where requested.
 template <int Q, typename S, int V>
-__device__ __forceinline__ void lb_row(const RepDev& rd, const StepInfo& st, const int4 bm) {
+__device__ __forceinline__ void lb_finish(const RepDev& rd, const StepInfo& st, typename Store<S>::R (&d)[Q][V],
+                                          int x0, int row) {
   using L = Lattice<Q>;
   using R = typename Store<S>::R;
-  const int nx = rd.nx, ny = rd.ny, nz = rd.nz;
-  const int y = bm.z, z = bm.w;
-  const int tpr = nx / V;
-  const int tx = bm.y * blockDim.x + threadIdx.x;
-  const bool active = tx < tpr;
-  const int lane = threadIdx.x & 31;
-  const int x0 = tx * V;
-  const int par = st.n & 1;
-  // plain (coherent) loads: in the persistent kernel these buffers are
-  // written by other blocks of the same launch between grid barriers
-  const S* src = (const S*)rd.f[par];
-  S* dst = (S*)rd.f[par ^ 1];
+  const int nx = rd.nx;
   const int N = (int)rd.nnode;
-  const int row = nx * (y + ny * z);
-  const float inv = rd.fp16_inv, scale = rd.fp16_scale;
-
-  // phase 1: every load of the thread (Q aligned rows plus the scalar edge
-  // values at warp boundaries), branch-free so that all of them are in flight
-  // together: inactive tail lanes read a clamped, valid position and discard it,
-  // bounce-back rows are selected, not branched to.
-  const int xa = active ? x0 : (tpr - 1) * V;
-  const int xprev = xa == 0 ? nx - 1 : xa - 1;
-  const int xnext = xa + V >= nx ? 0 : xa + V;
-  R d[Q][V], edge[Q];
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    const int sy = y - L::cy(i);
-    const bool bounce = (sy == 0) | (sy == ny - 1);
-    int sz = z - L::cz(i);
-    sz = sz < 0 ? sz + nz : (sz >= nz ? sz - nz : sz);
-    const S* srow_i = src + i * N + nx * (sy + ny * sz);
-    const S* rp = bounce ? src + L::opp(i) * N + row : srow_i;
-    if (V == 1) {
-      int sx = xa - L::cx(i);
-      sx = sx < 0 ? sx + nx : (sx >= nx ? sx - nx : sx);
-      d[i][0] = Store<S>::ld(rp + (bounce ? xa : sx), inv);
-    } else {
-      Row<S, V>::ld(rp + xa, d[i], inv);
-    }
-    edge[i] = R(0);
-    if (V > 1 && L::cx(i) > 0) edge[i] = Store<S>::ld(rp + xprev, inv);
-    if (V > 1 && L::cx(i) < 0) edge[i] = Store<S>::ld(rp + xnext, inv);
-  }
-  // phase 2: shift the rows with cx != 0 by one node through the neighbour lanes
-  if (V > 1) {
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const int sy = y - L::cy(i);
-      if (L::cx(i) == 0 || sy == 0 || sy == ny - 1) continue;
-      if (L::cx(i) > 0) {                    // source x - 1: previous lane's last node
-        R prev = __shfl_up_sync(0xFFFFFFFFu, d[i][V - 1], 1);
-        if (lane == 0) prev = edge[i];
-#pragma unroll
-        for (int v = V - 1; v > 0; --v) d[i][v] = d[i][v - 1];
-        d[i][0] = prev;
-      } else {                               // source x + 1: next lane's first node
-        R next = __shfl_down_sync(0xFFFFFFFFu, d[i][0], 1);
-        if (lane == 31 || tx + 1 >= tpr) next = edge[i];
-#pragma unroll
-        for (int v = 0; v < V - 1; ++v) d[i][v] = d[i][v + 1];
-        d[i][V - 1] = next;
-      }
-    }
-  }
-  if (!active) return;
-
+  const float scale = rd.fp16_scale;
+  S* dst = (S*)rd.f[(st.n & 1) ^ 1];
   const R om = Cst<R>::omega(rd), om1 = R(1) - om, cf = R(1) - R(0.5) * om;
   const R gx = Cst<R>::g(rd, 0), gy = Cst<R>::g(rd, 1), gz = Cst<R>::g(rd, 2);
   R mr[V], mu[3][V];   // post-collision values overwrite d in place
@@ -209,6 +149,79 @@ __device__ __forceinline__ void lb_row(const RepDev& rd, const StepInfo& st, con
       uv[2 * N + row + x] = mu[2][v];
     }
   }
+}
+
+// One thread owns V consecutive nodes x0 .. x0+V-1 of one row (y, z); a
+// work item (replica, tile, y, z) is one block-wide tile of a row.
+template <int Q, typename S, int V>
+__device__ __forceinline__ void lb_row(const RepDev& rd, const StepInfo& st, const int4 bm) {
+  using L = Lattice<Q>;
+  using R = typename Store<S>::R;
+  const int nx = rd.nx, ny = rd.ny, nz = rd.nz;
+  const int y = bm.z, z = bm.w;
+  const int tpr = nx / V;
+  const int tx = bm.y * blockDim.x + threadIdx.x;
+  const bool active = tx < tpr;
+  const int lane = threadIdx.x & 31;
+  const int x0 = tx * V;
+  const int par = st.n & 1;
+  // plain (coherent) loads: in the persistent kernel this buffer is written
+  // by other blocks of the same launch between grid barriers
+  const S* src = (const S*)rd.f[par];
+  const int N = (int)rd.nnode;
+  const int row = nx * (y + ny * z);
+  const float inv = rd.fp16_inv;
+
+  // phase 1: every load of the thread (Q aligned rows plus the scalar edge
+  // values at warp boundaries), branch-free so that all of them are in flight
+  // together: inactive tail lanes read a clamped, valid position and discard it,
+  // bounce-back rows are selected, not branched to.
+  const int xa = active ? x0 : (tpr - 1) * V;
+  const int xprev = xa == 0 ? nx - 1 : xa - 1;
+  const int xnext = xa + V >= nx ? 0 : xa + V;
+  R d[Q][V], edge[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const int sy = y - L::cy(i);
+    const bool bounce = (sy == 0) | (sy == ny - 1);
+    int sz = z - L::cz(i);
+    sz = sz < 0 ? sz + nz : (sz >= nz ? sz - nz : sz);
+    const S* srow_i = src + i * N + nx * (sy + ny * sz);
+    const S* rp = bounce ? src + L::opp(i) * N + row : srow_i;
+    if (V == 1) {
+      int sx = xa - L::cx(i);
+      sx = sx < 0 ? sx + nx : (sx >= nx ? sx - nx : sx);
+      d[i][0] = Store<S>::ld(rp + (bounce ? xa : sx), inv);
+    } else {
+      Row<S, V>::ld(rp + xa, d[i], inv);
+    }
+    edge[i] = R(0);
+    if (V > 1 && L::cx(i) > 0) edge[i] = Store<S>::ld(rp + xprev, inv);
+    if (V > 1 && L::cx(i) < 0) edge[i] = Store<S>::ld(rp + xnext, inv);
+  }
+  // phase 2: shift the rows with cx != 0 by one node through the neighbour lanes
+  if (V > 1) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const int sy = y - L::cy(i);
+      if (L::cx(i) == 0 || sy == 0 || sy == ny - 1) continue;
+      if (L::cx(i) > 0) {                    // source x - 1: previous lane's last node
+        R prev = __shfl_up_sync(0xFFFFFFFFu, d[i][V - 1], 1);
+        if (lane == 0) prev = edge[i];
+#pragma unroll
+        for (int v = V - 1; v > 0; --v) d[i][v] = d[i][v - 1];
+        d[i][0] = prev;
+      } else {                               // source x + 1: next lane's first node
+        R next = __shfl_down_sync(0xFFFFFFFFu, d[i][0], 1);
+        if (lane == 31 || tx + 1 >= tpr) next = edge[i];
+#pragma unroll
+        for (int v = 0; v < V - 1; ++v) d[i][v] = d[i][v + 1];
+        d[i][V - 1] = next;
+      }
+    }
+  }
+  if (!active) return;
+  lb_finish<Q, S, V>(rd, st, d, x0, row);
 }
 
 }  // namespace lbm

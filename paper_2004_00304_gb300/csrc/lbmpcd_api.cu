@@ -43,6 +43,7 @@ struct lbmpcd {
   int4* bm_lb256 = nullptr;                     // LB map with 256-thread row tiles (persistent kernel)
   int nb_lb256 = 0;
   int mode = 0;                                 // 0: per-kernel launches in graphs, 1: persistent
+  bool lb_tma = false;                          // D2Q9 binary32 LB rows staged by bulk copies
   int pers_bps = 0;                             // persistent blocks per SM (0: occupancy limit)
   bool pers_graph = true;                       // the persistent launch captures into a graph
   unsigned* d_bar = nullptr;                    // grid barrier: count, generation, error
@@ -402,7 +403,7 @@ extern "C" int lbmpcd_set_region(lbmpcd* h, int replica, const int lo[3], const 
 static bool persistent(const lbmpcd* h) { return h->mode == 1 && h->nb_cl == 0; }
 
 static int run_chunk(lbmpcd* h, int kcount, bool sort) {
-  Launch L{h->d_reps, h->nrep, h->d_si, h->stream};
+  Launch L{h->d_reps, h->nrep, h->d_si, h->stream, h->d_flag + 8};
   sort = sort && h->nb_p > 0;
   if (sort) CK(h, launch_sort(h->dim, h->prec, L, h->bm_p, h->nb_p, h->bm_t, h->nb_t));
   CK(h, launch_prep(h->dim, L, h->d_si, kcount, sort ? 1 : 0, h->d_step, h->d_pending, h->d_last_shift));
@@ -413,7 +414,7 @@ static int run_chunk(lbmpcd* h, int kcount, bool sort) {
     return LBMPCD_OK;
   }
   for (int k = 0; k < kcount; ++k) {
-    CK(h, launch_lb(h->q, h->prec, h->lbvec, L, h->bm_lb, h->nb_lb, k));
+    CK(h, launch_lb(h->q, h->prec, h->lbvec, h->lb_tma, L, h->bm_lb, h->nb_lb, k));
     CK(h, launch_particles(h->dim, h->prec, L, h->bm_p, h->nb_p, k));
     CK(h, launch_cells(h->q, h->prec, L, h->bm_c, h->nb_c, k));
     if (h->nb_cl) {
@@ -497,7 +498,7 @@ extern "C" int lbmpcd_step_profiled(lbmpcd* h, int nsteps, double* phase_ms, lon
   const int nev = 2 * (2 + 4 * KCHUNK);
   std::vector<cudaEvent_t> ev(nev, nullptr);
   for (auto& x : ev) CK(h, cudaEventCreate(&x));
-  Launch L{h->d_reps, h->nrep, h->d_si, h->stream};
+  Launch L{h->d_reps, h->nrep, h->d_si, h->stream, h->d_flag + 8};
   int rc = LBMPCD_OK;
   long long nl = 0;
   int left = nsteps;
@@ -519,7 +520,7 @@ extern "C" int lbmpcd_step_profiled(lbmpcd* h, int nsteps, double* phase_ms, lon
     bracket(0, [&] { return launch_prep(h->dim, L, h->d_si, kc, sort ? 1 : 0, h->d_step, h->d_pending,
                                         h->d_last_shift); });
     for (int k = 0; k < kc; ++k) {
-      bracket(1, [&] { return launch_lb(h->q, h->prec, h->lbvec, L, h->bm_lb, h->nb_lb, k); });
+      bracket(1, [&] { return launch_lb(h->q, h->prec, h->lbvec, h->lb_tma, L, h->bm_lb, h->nb_lb, k); });
       if (h->nb_p) bracket(2, [&] { return launch_particles(h->dim, h->prec, L, h->bm_p, h->nb_p, k); });
       if (h->nb_c) bracket(3, [&] { return launch_cells(h->q, h->prec, L, h->bm_c, h->nb_c, k); });
       if (h->nb_cl)
@@ -648,7 +649,15 @@ extern "C" int lbmpcd_get_fields(lbmpcd* h, int replica, int field, void* dst, s
     }
   }
   if (rc == LBMPCD_OK && e == cudaSuccess && tmp) e = cudaMemcpyAsync(dst, tmp, bytes, cudaMemcpyDeviceToHost, h->stream);
+  int kerr = 0;   // a bounded wait inside a step kernel gave up (reported here, where the stream is synchronised)
+  if (rc == LBMPCD_OK && e == cudaSuccess && h->lb_tma)
+    e = cudaMemcpyAsync(&kerr, h->d_flag + 8, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
   if (rc == LBMPCD_OK && e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (rc == LBMPCD_OK && e == cudaSuccess && kerr) {
+    if (tmp) cudaFree(tmp);
+    cudaMemset(h->d_flag + 8, 0, sizeof(int));
+    return fail(h, LBMPCD_ERR_TIMEOUT, "a bounded wait in the TMA-staged LB kernel gave up; results invalid");
+  }
   if (tmp) cudaFree(tmp);
   if (rc) return rc;
   if (e != cudaSuccess) return cuda_fail(h, e, "get_fields");
@@ -727,14 +736,16 @@ extern "C" int lbmpcd_set_closure(lbmpcd* h, const float* theta, long long count
   return LBMPCD_OK;
 }
 
-extern "C" int lbmpcd_set_launch_mode(lbmpcd* h, int mode, int blocks_per_sm) {
+extern "C" int lbmpcd_set_launch_mode(lbmpcd* h, int mode, int blocks_per_sm, int flags) {
   if (!h) return LBMPCD_ERR_INVALID_ARG;
-  if (mode < 0 || mode > 1 || blocks_per_sm < 0) return fail(h, LBMPCD_ERR_INVALID_ARG, "mode must be 0 or 1");
+  if (mode < 0 || mode > 1 || blocks_per_sm < 0 || (flags & ~LBMPCD_LAUNCH_LB_TMA))
+    return fail(h, LBMPCD_ERR_INVALID_ARG, "mode must be 0 or 1, flags a set of LBMPCD_LAUNCH_*");
   if (mode == 1)
     for (int r = 0; r < h->nrep; ++r)
       if (h->rd[r].cl_on) return fail(h, LBMPCD_ERR_INVALID_ARG, "the persistent form does not run the learned closure");
   h->mode = mode;
   h->pers_bps = blocks_per_sm;
+  h->lb_tma = (flags & LBMPCD_LAUNCH_LB_TMA) && lb_tma_ok(h->q, h->prec, h->lbvec);
   h->pers_graph = true;
   if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
   return LBMPCD_OK;
@@ -742,20 +753,22 @@ extern "C" int lbmpcd_set_launch_mode(lbmpcd* h, int mode, int blocks_per_sm) {
 
 // Time each candidate launch configuration on a fresh copy of the handle (same
 // parameters and regions, so the handle's own state is untouched) and keep the
-// fastest: {per-kernel graphs, persistent at the occupancy limit, persistent
-// with one block per SM} x {the default LB row width, one node per thread}.
+// fastest: per-kernel graphs with the default LB row width, with TMA-staged LB
+// rows (D2Q9 binary32), with one LB node per thread; the persistent kernel at
+// the occupancy limit and at one block per SM.
 extern "C" int lbmpcd_autotune(lbmpcd* h, int steps, int* choice) {
   if (!h) return LBMPCD_ERR_INVALID_ARG;
   if (steps < 1) return fail(h, LBMPCD_ERR_INVALID_ARG, "steps must be >= 1");
   bool closure = false;
   for (int r = 0; r < h->nrep; ++r) closure = closure || h->rd[r].cl_on;
-  struct Cand { int mode, bps, vec; };
+  struct Cand { int mode, bps, vec, flags; };
   const int vdef = h->lbvec;
-  std::vector<Cand> cands = {{0, 0, vdef}};
-  if (vdef != 1) cands.push_back({0, 0, 1});
+  std::vector<Cand> cands = {{0, 0, vdef, 0}};
+  if (lb_tma_ok(h->q, h->prec, vdef)) cands.push_back({0, 0, vdef, LBMPCD_LAUNCH_LB_TMA});
+  if (vdef != 1) cands.push_back({0, 0, 1, 0});
   if (!closure) {
-    cands.push_back({1, 0, vdef});
-    cands.push_back({1, 1, vdef});
+    cands.push_back({1, 0, vdef, 0});
+    cands.push_back({1, 1, vdef, 0});
   }
   lbmpcd* c = nullptr;
   int rc = lbmpcd_create(h->P.data(), h->nrep, h->stream, &c);
@@ -771,7 +784,7 @@ extern "C" int lbmpcd_autotune(lbmpcd* h, int steps, int* choice) {
   for (size_t i = 0; i < cands.size() && !rc; ++i) {
     c->lbvec = cands[i].vec;
     c->maps_dirty = true;
-    rc = lbmpcd_set_launch_mode(c, cands[i].mode, cands[i].bps);
+    rc = lbmpcd_set_launch_mode(c, cands[i].mode, cands[i].bps, cands[i].flags);
     if (!rc) rc = lbmpcd_step(c, KCHUNK);   // warm-up, graph capture
     if (!rc && cudaEventRecord(e0, c->stream) != cudaSuccess) rc = LBMPCD_ERR_CUDA;
     if (!rc) rc = lbmpcd_step(c, steps);
@@ -793,13 +806,14 @@ extern "C" int lbmpcd_autotune(lbmpcd* h, int steps, int* choice) {
   if (ms[best] >= 1e30f) return fail(h, LBMPCD_ERR_CUDA, "autotune: no candidate ran");
   h->lbvec = cands[best].vec;
   h->maps_dirty = true;
-  rc = lbmpcd_set_launch_mode(h, cands[best].mode, cands[best].bps);
+  rc = lbmpcd_set_launch_mode(h, cands[best].mode, cands[best].bps, cands[best].flags);
   if (rc) return rc;
   if (choice) {
     choice[0] = cands[best].mode;
     choice[1] = cands[best].bps;
     choice[2] = cands[best].vec;
-    choice[3] = (int)cands.size();
+    choice[3] = cands[best].flags;
+    choice[4] = (int)cands.size();
   }
   return LBMPCD_OK;
 }
