@@ -31,6 +31,10 @@
 #define TAG_RESAMPLE 5u
 #define TAG_INIT_POS 6u
 #define TAG_INIT_VEL 7u
+#define TAG_DENSITY 8u
+#define TAG_SPAWN_POS 9u
+#define TAG_SPAWN_VEL 10u
+#define SPAWN_MAX 4     /* at most SPAWN_MAX * ppc new particles per cell and step */
 
 static const double PI = 3.14159265358979323846;
 
@@ -130,7 +134,7 @@ struct orc_sim {
   long step;                          /* global step counter n */
   /* MPCD */
   int has_region, x0, x1, Wx, Hy, Wz, r, n_out, n_in;
-  long np;
+  long np, cap;                       /* particles, allocated slots */
   int *home;                          /* [np][3] integer home cell */
   double *off, *vel;                  /* [np][3] offsets in [0,1), velocities */
   int *pcell;                         /* [np] collision cell of last binning */
@@ -171,7 +175,8 @@ orc_sim* orc_create(const orc_params* p, int replica) {
   if (!(p->lattice == 9 || p->lattice == 19)) return NULL;
   if (p->nx < 1 || p->ny < 3 || p->nz < 1) return NULL;
   if (p->lattice == 9 && p->nz != 1) return NULL;
-  if (p->tau <= 0.5 || p->refine < 1 || p->ppc < 1 || p->resample_density != 0) return NULL;
+  if (p->tau <= 0.5 || p->refine < 1 || p->ppc < 1 || p->resample_density < 0 || p->resample_density > 1)
+    return NULL;
   orc_sim* s = (orc_sim*)calloc(1, sizeof(orc_sim));
   s->p = *p; s->replica = replica;
   s->dim = p->lattice == 9 ? 2 : 3;
@@ -218,10 +223,12 @@ int orc_set_region(orc_sim* s, int x0, int x1) {
   s->n_out = (cw + 1) / 2; s->n_in = cw / 2;
   long ncell_home = (long)s->Wx * s->Hy * s->Wz;
   s->np = ncell_home * p->ppc;
-  s->home = (int*)malloc(sizeof(int) * 3 * s->np);
-  s->off = (double*)malloc(sizeof(double) * 3 * s->np);
-  s->vel = (double*)malloc(sizeof(double) * 3 * s->np);
-  s->pcell = (int*)malloc(sizeof(int) * s->np);
+  if (p->resample_density && (double)ncell_home * SPAWN_MAX * p->ppc >= 4294967296.0) return -1;
+  s->cap = s->np > 0 ? s->np : 1;
+  s->home = (int*)malloc(sizeof(int) * 3 * s->cap);
+  s->off = (double*)malloc(sizeof(double) * 3 * s->cap);
+  s->vel = (double*)malloc(sizeof(double) * 3 * s->cap);
+  s->pcell = (int*)malloc(sizeof(int) * s->cap);
   s->ncx = s->Wx; s->ncy = s->Hy + 1; s->ncz = s->Wz;
   s->ncell = (long)s->ncx * s->ncy * s->ncz;
   s->cnt = (int*)calloc(s->ncell, sizeof(int));
@@ -370,6 +377,75 @@ static long inner_node(const orc_sim* s, int X, int Y, int Z) {
   else return -1;
   int y = 1 + Y / s->r, z = (s->dim == 3) ? Z / s->r : 0;
   return (((long)side * s->n_in + col) * p->nz + z) * (p->ny - 2) + (y - 1);
+}
+
+/* a3' (resample_density = 1; the paper redraws velocities only and keeps the
+ * particles, Sec. 2.3, so this mode reads "resampling from the local LB
+ * density" literally): every particle whose home cell lies in an
+ * outer-buffer column is removed; then each outer-buffer cell c (home cell
+ * index c = X + Wx (Y + Hy Z), taken in increasing c) receives
+ *   N_c = floor(x) + [u < x - floor(x)],  x = ppc rho_LB / rho0 (rho0 = 1),
+ * rho_LB the density of the LB node holding the cell in this step and
+ * u = (w0 >> 8) 2^-24 of Philox(c, n, replica, TAG_DENSITY), capped at
+ * SPAWN_MAX ppc.  New particle k of cell c has the offsets (w >> 8) 2^-24 of
+ * the words of Philox(c SPAWN_MAX ppc + k, n, replica, TAG_SPAWN_POS) and the
+ * velocity u_fine + sqrt(kT/m) (z0, z1, z2) of the Box-Muller normals of
+ * Philox(c SPAWN_MAX ppc + k, n, replica, TAG_SPAWN_VEL), as in a3. */
+static void grow(orc_sim* s, long n) {
+  if (n <= s->cap) return;
+  long c = s->cap * 2 > n ? s->cap * 2 : n;
+  s->home = (int*)realloc(s->home, sizeof(int) * 3 * c);
+  s->off = (double*)realloc(s->off, sizeof(double) * 3 * c);
+  s->vel = (double*)realloc(s->vel, sizeof(double) * 3 * c);
+  s->pcell = (int*)realloc(s->pcell, sizeof(int) * c);
+  s->cap = c;
+}
+
+static void resample_density(orc_sim* s) {
+  const orc_params* p = &s->p;
+  long w = 0;
+  for (long k = 0; k < s->np; ++k) {
+    if (in_outer(s, s->home[3*k])) continue;
+    for (int a = 0; a < 3; ++a) {
+      s->home[3*w+a] = s->home[3*k+a]; s->off[3*w+a] = s->off[3*k+a]; s->vel[3*w+a] = s->vel[3*k+a];
+    }
+    s->pcell[w] = s->pcell[k];
+    ++w;
+  }
+  s->np = w;
+  double sig = sqrt(p->kT / p->mass);
+  long nmax = (long)SPAWN_MAX * p->ppc;
+  for (int Z = 0; Z < s->Wz; ++Z)
+    for (int Y = 0; Y < s->Hy; ++Y)
+      for (int X = 0; X < s->Wx; ++X) {
+        if (!in_outer(s, X)) continue;
+        long c = X + (long)s->Wx * (Y + (long)s->Hy * Z);
+        int lx = lb_column_of(s, X), ly = 1 + Y / s->r, lz = s->dim == 3 ? Z / s->r : 0;
+        double x = (double)p->ppc * s->rho[nidx(s, lx, ly, lz)];
+        uint32_t wd[4]; draw(s, (uint32_t)c, (uint32_t)s->step, TAG_DENSITY, wd);
+        double fl = floor(x);
+        long n = (long)fl + (u24(wd[0]) < x - fl ? 1 : 0);
+        if (n > nmax) n = nmax;
+        if (n < 0) n = 0;
+        double uf[3]; u_fine(s, X, Y, Z, uf);
+        grow(s, s->np + n);
+        for (long k = 0; k < n; ++k) {
+          uint32_t id = (uint32_t)(c * nmax + k), wp[4], wv[4];
+          draw(s, id, (uint32_t)s->step, TAG_SPAWN_POS, wp);
+          draw(s, id, (uint32_t)s->step, TAG_SPAWN_VEL, wv);
+          double z0, z1, z2, z3;
+          orc_box_muller(wv[0], wv[1], &z0, &z1);
+          orc_box_muller(wv[2], wv[3], &z2, &z3);
+          long j = s->np++;
+          s->home[3*j] = X; s->home[3*j+1] = Y; s->home[3*j+2] = Z;
+          s->off[3*j] = u24(wp[0]); s->off[3*j+1] = u24(wp[1]);
+          s->off[3*j+2] = s->dim == 3 ? u24(wp[2]) : 0.0;
+          s->vel[3*j] = uf[0] + sig * z0;
+          s->vel[3*j+1] = uf[1] + sig * z1;
+          s->vel[3*j+2] = s->dim == 3 ? uf[2] + sig * z2 : 0.0;
+          s->pcell[j] = -1;
+        }
+      }
 }
 
 /* a3 (Sec. 2.3, Algorithm 1): particles whose home cell is in an outer buffer
@@ -700,7 +776,8 @@ int orc_step(orc_sim* s, int nsteps) {
   for (int it = 0; it < nsteps; ++it) {
     lb_step(s);                       /* a1 */
     if (s->has_region) {
-      resample(s);                    /* a2 + a3 */
+      if (s->p.resample_density) resample_density(s);   /* a2 + a3' */
+      else resample(s);               /* a2 + a3 */
       stream(s);                      /* a4 */
       sample_inner(s);                /* a6 */
       if (s->cl_on) closure_sample(s);  /* closure input of the same instant */

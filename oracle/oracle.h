@@ -53,7 +53,8 @@ typedef struct {
                            2 learned closure (sampling here, imposition by
                            orc_closure_impose) */
   int window;           /* averaging window W in steps */
-  int resample_density; /* must be 0 in the oracle */
+  int resample_density; /* 0: outer-buffer velocities redrawn (the paper); 1: outer-buffer
+                           particles replaced, their number drawn from the LB density */
   uint64_t seed;
 } orc_params;
 
