@@ -70,6 +70,10 @@ enum {
  *  PART_HOME [np][3] (int32)              integer home cell of each particle
  *  CELL_VCM [ncell][3] (double)           centre-of-mass velocity of the last collision
  *  PART_ID [np] (int32)                   identity: particle fields come back in id order
+ *                                         (with resample_density = 1: the live particles
+ *                                         in pool order, the same for every field read
+ *                                         between two steps; PART_ID is the initial index
+ *                                         or -3 for particles created by the resampling)
  *  CLOSURE_IN [P][16][16][24] (double)    learned-closure network input of the last step
  *  CLOSURE_OUT [P][16][16][3] (double)    network output of the last step (with parameters)
  *  CLOSURE_TARGET [P][16][16][3] (double) moving averages of the strip fields (training target)
@@ -104,9 +108,26 @@ typedef struct {
   int feedback;         /* 0: one-way LB -> MPCD as in the paper; 1: plus windowed MPCD -> LB;
                            2: plus MPCD -> LB from the learned closure (D2Q9; lbmpcd_set_closure) */
   int window;           /* samples in the averaging window (Table 1 N_s) */
-  int resample_density; /* must be 0 (velocity-only redraw, as in the paper) */
+  int resample_density; /* 0: outer-buffer velocities redrawn, particles kept (the paper, Sec. 2.3);
+                           1: outer-buffer particles replaced each step by
+                           N = stochastic-round(ppc rho_LB) new ones (see below) */
   uint64_t seed;        /* Philox key */
 } lbmpcd_params;
+
+/* Density resampling (resample_density = 1; a reading of "resampling from the
+ * local LB density": the paper keeps its particles and redraws velocities):
+ * each step, before streaming, every particle whose home cell lies in an
+ * outer-buffer column is removed and each outer-buffer cell c (home-cell
+ * index X + Wx (Y + Hy Z)) receives N = floor(x) + [u < x - floor(x)] new
+ * particles, x = ppc rho_LB of the LB node holding the cell, u from
+ * Philox(c, n, replica, 8), at most 4 ppc; particle k has uniform offsets
+ * from Philox(c 4 ppc + k, n, replica, 9) and velocity u_fine + sqrt(kT/m) xi
+ * (Box-Muller of Philox(c 4 ppc + k, n, replica, 10)).  Particles live in a
+ * pool with room for 65 steps of new particles at twice the mean rate,
+ * compacted at the start of every call and graph chunk; lbmpcd_step returns
+ * ERR_CAPACITY (results invalid) if it ever fills, and synchronises the
+ * stream to check.  Particle state cannot be loaded (lbmpcd_set_state) and
+ * the persistent launch form is not available in this mode. */
 
 /* Create a handle holding n_replicas independent channels; params points to
  * n_replicas structs (replica i uses params[i]).  cuda_stream is a

@@ -15,7 +15,14 @@ namespace lbm {
 // Philox4x32-10 (Salmon et al., SC'11).  Counter words: (id, step, replica,
 // tag), key: the 64-bit seed.  Same stream on host and device.
 enum : uint32_t { TAG_SHIFT = 1, TAG_SIGN = 2, TAG_AXIS = 3, TAG_VIRT = 4,
-                  TAG_RESAMPLE = 5, TAG_INIT_POS = 6, TAG_INIT_VEL = 7 };
+                  TAG_RESAMPLE = 5, TAG_INIT_POS = 6, TAG_INIT_VEL = 7,
+                  TAG_DENSITY = 8, TAG_SPAWN_POS = 9, TAG_SPAWN_VEL = 10 };
+
+// density resampling of the outer buffer (resample_density = 1): a removed
+// particle's home is HOME_DEAD until the next sort compacts the pool; a new
+// particle carries PID_FRESH until its first particle pass, PID_SPAWNED after.
+constexpr uint32_t HOME_DEAD = 0xFFFFFFFFu, PID_FRESH = 0xFFFFFFFEu, PID_SPAWNED = 0xFFFFFFFDu;
+constexpr int SPAWN_MAX = 4;   // at most SPAWN_MAX ppc new particles per cell and step
 
 LBM_HD uint32_t mul_hi32(uint32_t a, uint32_t b) {
 #ifdef __CUDA_ARCH__
@@ -130,6 +137,13 @@ struct RepDev {
   // coupling columns in cell units: outer X < xo_lo or X >= xo_hi; inner
   // [xi_lo0, xi_hi0) (left side) and [xi_lo1, xi_hi1) (right side)
   int xo_lo, xo_hi, xi_lo0, xi_hi0, xi_lo1, xi_hi1;
+  // density resampling: particles live in a pool of cap slots; pool[0] is
+  // its end, pool[1] an overflow flag, pool[2] the live count of the last
+  // sort or compaction; ltile scratch of the readout compaction
+  int resample;
+  uint32_t cap;
+  uint32_t* pool;
+  uint32_t* ltile;
   // particles (structure of arrays); *_alt receive the sorted copy
   uint32_t* home;          // packed integer home cell
   void* off[3];            // offsets in [0,1), storage precision (2D: off[0] holds (x,y) pairs)
@@ -179,6 +193,14 @@ struct RepDev {
 };
 
 constexpr int SORT_TILE = 1024;
+
+// end of the particle slots in use: the pool end with density resampling,
+// the fixed count otherwise
+__device__ __forceinline__ uint32_t pool_end(const RepDev& rd) {
+  if (!rd.resample) return (uint32_t)rd.np;
+  const uint32_t e = *(volatile const uint32_t*)rd.pool;
+  return e < rd.cap ? e : rd.cap;
+}
 
 template <typename R> struct Vec4;
 template <> struct Vec4<float> { using T = float4; };

@@ -44,7 +44,7 @@ cudaError_t launch_sort(int dim, int prec, const Launch& L, const int2* bmap_p, 
 cudaError_t launch_tab_out(int dim, int prec, const RepDev& rd, int field, void* out, cudaStream_t st);
 
 // a7(n-1) + a2 + a3 + a4 + a6 + a5 over every particle.
-cudaError_t launch_particles(int dim, int prec, const Launch& L, const int2* bmap, int nblocks, int k);
+cudaError_t launch_particles(int dim, int prec, bool rs, const Launch& L, const int2* bmap, int nblocks, int k);
 
 // a7 cell part (v_cm, virtual particles, rotation draw) + a8 imposition.
 cudaError_t launch_cells(int q, int prec, const Launch& L, const int2* bmap, int nblocks, int k);
@@ -88,6 +88,12 @@ struct PersistentMaps {
 };
 cudaError_t launch_persistent(int q, int prec, int vec, const Launch& L, int kcount, const PersistentMaps& m,
                               int blocks_per_sm, int* grid_out);
+
+// a3' (density resampling): new particles of the outer-buffer cells, before
+// the particle pass of the same step; readout order of the pooled particles
+// (rank, pool[2] = live count).
+cudaError_t launch_spawn(int dim, int prec, const Launch& L, const int2* bmap, int nwork, int k);
+cudaError_t launch_live_index(const RepDev& rd, cudaStream_t st);
 
 // apply the pending collision of the last step to every particle of a replica.
 cudaError_t launch_flush(int dim, int prec, const RepDev* rd_dev, const RepDev& rd, const double* last_shift,

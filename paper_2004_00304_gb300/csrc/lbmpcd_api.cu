@@ -42,6 +42,8 @@ struct lbmpcd {
   int4* ptab = nullptr;                         // closure patches of the batch: (replica, side, py)
   int4* bm_lb256 = nullptr;                     // LB map with 256-thread row tiles (persistent kernel)
   int nb_lb256 = 0;
+  int2* bm_s = nullptr;                         // outer-buffer cells of the density resampling
+  int nb_s = 0;
   int mode = 0;                                 // 0: per-kernel launches in graphs, 1: persistent
   bool lb_tma = false;                          // D2Q9 binary32 LB rows staged by bulk copies
   int pers_bps = 0;                             // persistent blocks per SM (0: occupancy limit)
@@ -123,7 +125,7 @@ static int validate(const lbmpcd_params& p, std::string& why) {
   if (p.feedback == 2 && (p.lattice != LBMPCD_D2Q9 || !(p.kT > 0)))
     { why = "feedback = 2 (learned closure) needs D2Q9 and kT > 0"; return 0; }
   if (p.window < 1) { why = "window must be >= 1"; return 0; }
-  if (p.resample_density != 0) { why = "resample_density = 1 is not supported"; return 0; }
+  if (p.resample_density < 0 || p.resample_density > 1) { why = "resample_density must be 0 or 1"; return 0; }
   return 1;
 }
 
@@ -262,7 +264,7 @@ static int build_maps(lbmpcd* h) {
   int rc0 = closure_batch(h);
   if (rc0) return rc0;
   std::vector<int4> lb;
-  std::vector<int2> pp, cc, tt, cl;
+  std::vector<int2> pp, cc, tt, cl, sp;
   std::vector<int4> pt, lb256;
   for (int r = 0; r < h->nrep; ++r) {
     const RepDev& d = h->rd[r];
@@ -275,11 +277,16 @@ static int build_maps(lbmpcd* h) {
       for (int y = 1; y < d.ny - 1; ++y)
         for (int t = 0; t < ntx256; ++t) lb256.push_back(make_int4(r, t, y, z));
     if (!d.has_region) continue;
-    const long long npb = (d.np + PP_ITEM - 1) / PP_ITEM, ncb = (d.ncell + 256 * CPT - 1) / (256 * CPT), nbb = (d.nbuf + 255) / 256;
+    const long long nslot = d.resample ? (long long)d.cap : d.np;
+    const long long npb = (nslot + PP_ITEM - 1) / PP_ITEM, ncb = (d.ncell + 256 * CPT - 1) / (256 * CPT), nbb = (d.nbuf + 255) / 256;
     for (long long b = 0; b < npb; ++b) pp.push_back(make_int2(r, (int)b));
     for (long long b = 0; b < ncb; ++b) cc.push_back(make_int2(r, (int)b));
     for (long long b = 0; b < nbb; ++b) cc.push_back(make_int2(r, (int)(-1 - b)));
     for (int b = 0; b < d.ntile; ++b) tt.push_back(make_int2(r, b));
+    if (d.resample) {
+      const long long nouter = (long long)(d.xo_lo + (d.Wx - d.xo_hi)) * d.Hy * d.Wz;
+      for (long long b = 0; b < (nouter + 255) / 256; ++b) sp.push_back(make_int2(r, (int)b));
+    }
     if (d.cl_on) {
       const long long ncl = 2LL * d.Hy * 16;
       for (long long b = 0; b < (ncl + 255) / 256; ++b) cl.push_back(make_int2(r, (int)b));
@@ -294,6 +301,7 @@ static int build_maps(lbmpcd* h) {
   if (!rc) rc = upload_map(h, &h->bm_cl, &h->nb_cl, cl);
   if (!rc) rc = upload_map(h, &h->ptab, &h->n_ptab, pt);
   if (!rc) rc = upload_map(h, &h->bm_lb256, &h->nb_lb256, lb256);
+  if (!rc) rc = upload_map(h, &h->bm_s, &h->nb_s, sp);
   if (rc) return rc;
   CK(h, cudaMemcpy(h->d_reps, h->rd.data(), sizeof(RepDev) * h->nrep, cudaMemcpyHostToDevice));
   if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
@@ -329,6 +337,16 @@ extern "C" int lbmpcd_set_region(lbmpcd* h, int replica, const int lo[3], const 
     d.xi_lo1 = (w - p.coupling_width) * r; d.xi_hi1 = (w - d.n_out) * r;
   }
   if (d.np >= (1LL << 32) - 1) return fail(h, LBMPCD_ERR_INVALID_ARG, "too many particles");
+  // density resampling: a pool with room for KCHUNK + 1 steps of new particles
+  // at twice the mean rate (the pool is compacted at the start of every chunk)
+  long long cap = d.np;
+  if (p.resample_density) {
+    const long long nouter = (long long)(d.xo_lo + (d.Wx - d.xo_hi)) * d.Hy * d.Wz;
+    if ((double)d.nhome * SPAWN_MAX * p.ppc >= 4294967296.0)
+      return fail(h, LBMPCD_ERR_INVALID_ARG, "density resampling: region too large for 32-bit particle draws");
+    cap = d.np + (KCHUNK + 1) * nouter * 2LL * p.ppc;
+    if (cap >= (1LL << 32) - 8) return fail(h, LBMPCD_ERR_INVALID_ARG, "density resampling: pool too large");
+  }
   if (p.feedback == 2 && (d.Wx < 32 || d.Hy < 16 || p.coupling_width * p.refine > 16 || 16 % p.refine))
     return fail(h, LBMPCD_ERR_INVALID_ARG,
                 "learned closure needs >= 32 fine columns, >= 16 fine rows, refine in {1, 2, 4, 8} and "
@@ -340,20 +358,30 @@ extern "C" int lbmpcd_set_region(lbmpcd* h, int replica, const int lo[3], const 
   void* t = nullptr;
   cudaError_t e = cudaSuccess;
 #define A(ptr, bytes) if (e == cudaSuccess) { e = dalloc(L, &t, (bytes)); ptr = t; }
-  A(*(void**)&d.home, d.np * 4);
-  A(*(void**)&d.pid, d.np * 4);
-  A(*(void**)&d.home_alt, d.np * 4);
-  A(*(void**)&d.pid_alt, d.np * 4);
+  A(*(void**)&d.home, cap * 4);
+  A(*(void**)&d.pid, cap * 4);
+  A(*(void**)&d.home_alt, cap * 4);
+  A(*(void**)&d.pid_alt, cap * 4);
   if (h->dim == 2) {   // interleaved (x, y) pairs
-    A(d.off[0], d.np * 2 * rs); A(d.vel[0], d.np * 2 * rs);
-    A(d.off_alt[0], d.np * 2 * rs); A(d.vel_alt[0], d.np * 2 * rs);
+    A(d.off[0], cap * 2 * rs); A(d.vel[0], cap * 2 * rs);
+    A(d.off_alt[0], cap * 2 * rs); A(d.vel_alt[0], cap * 2 * rs);
   } else {
     for (int a = 0; a < 3; ++a) {
-      A(d.off[a], d.np * rs); A(d.vel[a], d.np * rs);
-      A(d.off_alt[a], d.np * rs); A(d.vel_alt[a], d.np * rs);
+      A(d.off[a], cap * rs); A(d.vel[a], cap * rs);
+      A(d.off_alt[a], cap * rs); A(d.vel_alt[a], cap * rs);
     }
   }
-  A(*(void**)&d.rank, d.np * 4);
+  A(*(void**)&d.rank, cap * 4);
+  if (p.resample_density) {
+    A(*(void**)&d.pool, 4 * 4);
+    A(*(void**)&d.ltile, ((cap + SORT_TILE - 1) / SORT_TILE) * 4);
+    d.resample = 1;
+    d.cap = (uint32_t)cap;
+    const uint32_t init[4] = {(uint32_t)d.np, 0u, (uint32_t)d.np, 0u};
+    if (e == cudaSuccess) e = cudaMemcpy(d.pool, init, sizeof(init), cudaMemcpyHostToDevice);
+  } else {
+    d.cap = (uint32_t)d.np;
+  }
   A(*(void**)&d.hcount, d.nhome * 4);
   A(*(void**)&d.hoff, d.nhome * 4);
   A(*(void**)&d.tsum, (long long)d.ntile * 4);
@@ -404,7 +432,8 @@ static bool persistent(const lbmpcd* h) { return h->mode == 1 && h->nb_cl == 0; 
 
 static int run_chunk(lbmpcd* h, int kcount, bool sort) {
   Launch L{h->d_reps, h->nrep, h->d_si, h->stream, h->d_flag + 8};
-  sort = sort && h->nb_p > 0;
+  // density resampling compacts its particle pool at the start of every chunk
+  sort = (sort || h->nb_s > 0) && h->nb_p > 0;
   if (sort) CK(h, launch_sort(h->dim, h->prec, L, h->bm_p, h->nb_p, h->bm_t, h->nb_t));
   CK(h, launch_prep(h->dim, L, h->d_si, kcount, sort ? 1 : 0, h->d_step, h->d_pending, h->d_last_shift));
   if (persistent(h)) {
@@ -415,7 +444,8 @@ static int run_chunk(lbmpcd* h, int kcount, bool sort) {
   }
   for (int k = 0; k < kcount; ++k) {
     CK(h, launch_lb(h->q, h->prec, h->lbvec, h->lb_tma, L, h->bm_lb, h->nb_lb, k));
-    CK(h, launch_particles(h->dim, h->prec, L, h->bm_p, h->nb_p, k));
+    if (h->nb_s) CK(h, launch_spawn(h->dim, h->prec, L, h->bm_s, h->nb_s, k));
+    CK(h, launch_particles(h->dim, h->prec, h->nb_s > 0, L, h->bm_p, h->nb_p, k));
     CK(h, launch_cells(h->q, h->prec, L, h->bm_c, h->nb_c, k));
     if (h->nb_cl) {
       if (h->cl_params) CK(h, launch_closure_step(h->prec, L, h->ptab, h->n_ptab, k, net_closure(h->net)));
@@ -479,6 +509,16 @@ extern "C" int lbmpcd_step(lbmpcd* h, int nsteps) {
     const int rc = net_error(h->net, h->stream);
     if (rc) return fail(h, rc, "closure network: a tensor-core wait timed out");
   }
+  if (nsteps > 0 && h->nb_s) {   // a density-resampling pool ran out of slots
+    for (int r = 0; r < h->nrep; ++r) {
+      if (!h->rd[r].resample) continue;
+      uint32_t pf[4];
+      CK(h, cudaMemcpyAsync(pf, h->rd[r].pool, sizeof(pf), cudaMemcpyDeviceToHost, h->stream));
+      CK(h, cudaStreamSynchronize(h->stream));
+      if (pf[1]) return fail(h, LBMPCD_ERR_CAPACITY, "density resampling: particle pool full (replica " +
+                                                         std::to_string(r) + "); results invalid");
+    }
+  }
   if (nsteps > 0 && persistent(h)) {   // a bounded grid-barrier wait gave up
     unsigned bar[4] = {0, 0, 0, 0};
     CK(h, cudaMemcpyAsync(bar, h->d_bar, sizeof(bar), cudaMemcpyDeviceToHost, h->stream));
@@ -495,7 +535,7 @@ extern "C" int lbmpcd_step_profiled(lbmpcd* h, int nsteps, double* phase_ms, lon
   if (!h) return LBMPCD_ERR_INVALID_ARG;
   if (nsteps < 0 || !phase_ms) return fail(h, LBMPCD_ERR_INVALID_ARG, "nsteps < 0 or null phase_ms");
   if (h->maps_dirty) { int rc = build_maps(h); if (rc) return rc; }
-  const int nev = 2 * (2 + 4 * KCHUNK);
+  const int nev = 2 * (2 + 5 * KCHUNK);
   std::vector<cudaEvent_t> ev(nev, nullptr);
   for (auto& x : ev) CK(h, cudaEventCreate(&x));
   Launch L{h->d_reps, h->nrep, h->d_si, h->stream, h->d_flag + 8};
@@ -515,13 +555,14 @@ extern "C" int lbmpcd_step_profiled(lbmpcd* h, int nsteps, double* phase_ms, lon
       phase.push_back(ph);
       ++nl;
     };
-    const bool sort = kc == KCHUNK && h->nb_p > 0;
+    const bool sort = (kc == KCHUNK || h->nb_s > 0) && h->nb_p > 0;
     if (sort) bracket(4, [&] { return launch_sort(h->dim, h->prec, L, h->bm_p, h->nb_p, h->bm_t, h->nb_t); });
     bracket(0, [&] { return launch_prep(h->dim, L, h->d_si, kc, sort ? 1 : 0, h->d_step, h->d_pending,
                                         h->d_last_shift); });
     for (int k = 0; k < kc; ++k) {
       bracket(1, [&] { return launch_lb(h->q, h->prec, h->lbvec, h->lb_tma, L, h->bm_lb, h->nb_lb, k); });
-      if (h->nb_p) bracket(2, [&] { return launch_particles(h->dim, h->prec, L, h->bm_p, h->nb_p, k); });
+      if (h->nb_s) bracket(2, [&] { return launch_spawn(h->dim, h->prec, L, h->bm_s, h->nb_s, k); });
+      if (h->nb_p) bracket(2, [&] { return launch_particles(h->dim, h->prec, h->nb_s > 0, L, h->bm_p, h->nb_p, k); });
       if (h->nb_c) bracket(3, [&] { return launch_cells(h->q, h->prec, L, h->bm_c, h->nb_c, k); });
       if (h->nb_cl)
         bracket(5, [&] {
@@ -547,8 +588,26 @@ extern "C" int lbmpcd_step_profiled(lbmpcd* h, int nsteps, double* phase_ms, lon
   return rc;
 }
 
+// live particles of a density-resampling replica; also leaves the readout
+// order of the pool in rank (valid until the next step)
+static long long live_particles(lbmpcd* h, int r) {
+  const RepDev& d = h->rd[r];
+  if (launch_live_index(d, h->stream) != cudaSuccess) return -1;
+  uint32_t n = 0;
+  if (cudaMemcpyAsync(&n, d.pool + 2, sizeof(n), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess) return -1;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return -1;
+  return n;
+}
+
 static long long field_elems(const lbmpcd* h, int r, int field) {
   const RepDev& d = h->rd[r];
+  const bool pf = field == LBMPCD_PART_POS || field == LBMPCD_PART_VEL || field == LBMPCD_PART_HOME ||
+                  field == LBMPCD_PART_CELL || field == LBMPCD_PART_ID;
+  if (pf && d.has_region && d.resample) {
+    const long long n = live_particles(const_cast<lbmpcd*>(h), r);
+    if (n < 0) return -1;
+    return (field == LBMPCD_PART_CELL || field == LBMPCD_PART_ID) ? n : 3 * n;
+  }
   switch (field) {
     case LBMPCD_RHO: return d.nnode;
     case LBMPCD_U: return 3 * d.nnode;
@@ -673,6 +732,8 @@ extern "C" int lbmpcd_set_state(lbmpcd* h, int replica, int field, const void* s
   const RepDev& d = h->rd[replica];
   const bool lbf = field == LBMPCD_POPS || field == LBMPCD_U;
   if (!lbf && !d.has_region) return fail(h, LBMPCD_ERR_STATE, "particles need a region first");
+  if (!lbf && d.resample)
+    return fail(h, LBMPCD_ERR_INVALID_ARG, "particle state cannot be loaded with density resampling");
   const long long n = field_elems(h, replica, field);
   const size_t esz = int_field(field) ? 4 : 8;
   if (bytes != (size_t)n * esz) return fail(h, LBMPCD_ERR_INVALID_ARG, "src size does not match the field");
@@ -742,7 +803,9 @@ extern "C" int lbmpcd_set_launch_mode(lbmpcd* h, int mode, int blocks_per_sm, in
     return fail(h, LBMPCD_ERR_INVALID_ARG, "mode must be 0 or 1, flags a set of LBMPCD_LAUNCH_*");
   if (mode == 1)
     for (int r = 0; r < h->nrep; ++r)
-      if (h->rd[r].cl_on) return fail(h, LBMPCD_ERR_INVALID_ARG, "the persistent form does not run the learned closure");
+      if (h->rd[r].cl_on || h->rd[r].resample)
+        return fail(h, LBMPCD_ERR_INVALID_ARG,
+                    "the persistent form runs neither the learned closure nor the density resampling");
   h->mode = mode;
   h->pers_bps = blocks_per_sm;
   h->lb_tma = (flags & LBMPCD_LAUNCH_LB_TMA) && lb_tma_ok(h->q, h->prec, h->lbvec);
@@ -760,7 +823,7 @@ extern "C" int lbmpcd_autotune(lbmpcd* h, int steps, int* choice) {
   if (!h) return LBMPCD_ERR_INVALID_ARG;
   if (steps < 1) return fail(h, LBMPCD_ERR_INVALID_ARG, "steps must be >= 1");
   bool closure = false;
-  for (int r = 0; r < h->nrep; ++r) closure = closure || h->rd[r].cl_on;
+  for (int r = 0; r < h->nrep; ++r) closure = closure || h->rd[r].cl_on || h->rd[r].resample;
   struct Cand { int mode, bps, vec, flags; };
   const int vdef = h->lbvec;
   std::vector<Cand> cands = {{0, 0, vdef, 0}};

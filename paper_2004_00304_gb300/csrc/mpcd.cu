@@ -112,6 +112,7 @@ __global__ void prep_steps(const RepDev* __restrict__ reps, int nrep, int dim, i
   }
   __syncthreads();
   for (int r = threadIdx.x; r < nrep; r += blockDim.x) {
+    if (sorted && reps[r].resample) reps[r].pool[0] = reps[r].pool[2];   // the sort compacted the pool
     const StepInfo& last = si[(kcount - 1) * nrep + r];
     for (int a = 0; a < 3; ++a) d_last_shift[3 * r + a] = last.shift[a];
     d_pending[r] = reps[r].has_region ? 1 : 0;
@@ -270,7 +271,7 @@ template <int D, typename R> struct PassShared {
   R sv[D][256];
 };
 
-template <int D, typename R>
+template <int D, typename R, bool RS>
 __device__ __forceinline__ void particle_item(const RepDev& rd, const StepInfo& st, const int2 bm,
                                               PassShared<D, R>& red) {
   using T4 = typename Vec4<R>::T;
@@ -283,13 +284,22 @@ __device__ __forceinline__ void particle_item(const RepDev& rd, const StepInfo& 
   // branch-free loads: a lane past the end reads the last particle and discards it
   void* const* offs = alt ? rd.off_alt : rd.off;
   void* const* vels = alt ? rd.vel_alt : rd.vel;
-  const uint32_t np32 = (uint32_t)rd.np;
+  const uint32_t np32 = RS ? pool_end(rd) : (uint32_t)rd.np, last = np32 ? np32 - 1u : 0u;
+  // density resampling: removed particles (HOME_DEAD) are skipped, particles
+  // created this step (PID_FRESH) are neither rotated nor removed
+  bool fresh[PPT];
 #pragma unroll
   for (int p = 0; p < PPT; ++p) {
     const uint32_t j = j0 + 256u * p;
     act[p] = j < np32;
-    const uint32_t jl = act[p] ? j : np32 - 1u;
-    HomePack<D>::unpack(hsrc[jl], X[p], Y[p], Z[p]);
+    fresh[p] = false;
+    const uint32_t jl = act[p] ? j : last;
+    uint32_t hp = hsrc[jl];
+    if (RS && rd.resample) {
+      if (hp == HOME_DEAD) { act[p] = false; hp = 0u; }
+      fresh[p] = act[p] && (alt ? rd.pid_alt : rd.pid)[jl] == PID_FRESH;
+    }
+    HomePack<D>::unpack(hp, X[p], Y[p], Z[p]);
 #pragma unroll
     for (int a = 0; a < 3; ++a) { o[p][a] = R(0); v[p][a] = R(0); }
     PState<D, R>::ld(offs, jl, o[p]);
@@ -308,6 +318,7 @@ __device__ __forceinline__ void particle_item(const RepDev& rd, const StepInfo& 
     const R ca = Cst<R>::cos_a(rd), sa = Cst<R>::sin_a(rd);
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
+      if (RS && fresh[p]) continue;
       if (D == 2) {
         const T4 t = t0[p];
         const R wx = v[p][0] - t.x, wy = v[p][1] - t.y;
@@ -329,8 +340,14 @@ __device__ __forceinline__ void particle_item(const RepDev& rd, const StepInfo& 
     const uint32_t j = j0 + 256u * p;
     cid[p] = 0xFFFFFFFFu;
     if (!act[p]) continue;
+    const bool outer = X[p] < rd.xo_lo || X[p] >= rd.xo_hi;
+    if (RS && rd.resample && outer && !fresh[p]) {   // a3': replaced by this step's spawn
+      rd.home[j] = HOME_DEAD;
+      act[p] = false;
+      continue;
+    }
     // a2 + a3: Maxwellian redraw in the outer buffer columns
-    if (X[p] < rd.xo_lo || X[p] >= rd.xo_hi) {
+    if (!(RS && rd.resample) && outer) {
       R uf[3] = {R(0), R(0), R(0)};
       u_fine<D, R>(rd, X[p], Y[p], Z[p], uf);
       const uint4 w = philox((alt ? rd.pid_alt : rd.pid)[j], st.n, rd.rep, TAG_RESAMPLE, rd.key0, rd.key1);
@@ -342,7 +359,8 @@ __device__ __forceinline__ void particle_item(const RepDev& rd, const StepInfo& 
       v[p][1] = uf[1] + sg * z1;
       if (D == 3) v[p][2] = uf[2] + sg * z2;
     }
-    if (alt) rd.pid[j] = rd.pid_alt[j];
+    if (RS && fresh[p]) rd.pid[j] = PID_SPAWNED;
+    else if (alt) rd.pid[j] = rd.pid_alt[j];
     // a4
     stream<D, R>(rd, X[p], Y[p], Z[p], o[p], v[p]);
     // a6: inner-buffer sample (unshifted cells), binary64 atomics
@@ -442,29 +460,110 @@ __device__ __forceinline__ void particle_item(const RepDev& rd, const StepInfo& 
   }
 }
 
-template <int D, typename R>
+template <int D, typename R, bool RS>
 __global__ void __launch_bounds__(256, 6) particle_pass(const RepDev* __restrict__ reps, const int2* __restrict__ bmap,
                                                      int nwork, const StepInfo* __restrict__ si, int k, int nrep) {
   __shared__ RepDev rd;
   __shared__ StepInfo st;
   __shared__ PassShared<D, R> red;
-  for_each_item(bmap, nwork, reps, si, k, nrep, rd, st, [&](const int2 bm) { particle_item<D, R>(rd, st, bm, red); });
+  for_each_item(bmap, nwork, reps, si, k, nrep, rd, st, [&](const int2 bm) { particle_item<D, R, RS>(rd, st, bm, red); });
+}
+
+template <int D, typename R, bool RS>
+static void go_particles(const Launch& L, const int2* bmap, int nwork, int k) {
+  static const int g = grid_cap(grid_for(particle_pass<D, R, RS>, 256, 1 << 30));
+  particle_pass<D, R, RS><<<g < nwork ? g : nwork, 256, 0, L.stream>>>(L.reps, bmap, nwork, L.si, k, L.nrep);
+}
+
+// rs: some replica of the handle uses density resampling (the pass then checks
+// each replica's mode; without it the resampling code is not compiled in)
+cudaError_t launch_particles(int dim, int prec, bool rs, const Launch& L, const int2* bmap, int nwork, int k) {
+  if (nwork == 0) return cudaSuccess;
+  if (dim == 2) {
+    if (prec == P_FP64) rs ? go_particles<2, double, true>(L, bmap, nwork, k) : go_particles<2, double, false>(L, bmap, nwork, k);
+    else rs ? go_particles<2, float, true>(L, bmap, nwork, k) : go_particles<2, float, false>(L, bmap, nwork, k);
+  } else {
+    if (prec == P_FP64) rs ? go_particles<3, double, true>(L, bmap, nwork, k) : go_particles<3, double, false>(L, bmap, nwork, k);
+    else rs ? go_particles<3, float, true>(L, bmap, nwork, k) : go_particles<3, float, false>(L, bmap, nwork, k);
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// a3' (resample_density = 1): one thread per outer-buffer cell, run before the
+// particle pass.  N = floor(x) + [u < x - floor(x)], x = ppc rho_LB of the LB
+// node holding the cell (rho0 = 1), u from Philox(c, n, replica,
+// TAG_DENSITY), capped at SPAWN_MAX ppc; new particle k gets 24-bit uniform
+// offsets from Philox(c SPAWN_MAX ppc + k, n, replica, TAG_SPAWN_POS) and the
+// velocity u_fine + sqrt(kT/m) xi from Philox(..., TAG_SPAWN_VEL), and is
+// appended to the pool (the arrays this step's particle pass reads) with
+// PID_FRESH.  c = X + Wx (Y + Hy Z) is the home-cell index.  The particle pass
+// removes the particles that were in these cells.  Past the pool capacity no
+// particle is written and pool[1] is set.
+template <int D, typename R>
+__device__ __forceinline__ void spawn_item(const RepDev& rd, const StepInfo& st, const int2 bm) {
+  const int nl = rd.xo_lo, nr = rd.Wx - rd.xo_hi, ncol = nl + nr;
+  const long long t = (long long)bm.y * blockDim.x + threadIdx.x;
+  if (t >= (long long)ncol * rd.Hy * rd.Wz) return;
+  const int xi = (int)(t % ncol);
+  const long long rest = t / ncol;
+  const int Y = (int)(rest % rd.Hy), Z = (int)(rest / rd.Hy);
+  const int X = xi < nl ? xi : rd.xo_hi + (xi - nl);
+  const uint32_t c = (uint32_t)(X + (long long)rd.Wx * (Y + (long long)rd.Hy * Z));
+  const long long node = (rd.x0 + X / rd.r) + (long long)rd.nx * ((1 + Y / rd.r) + (long long)rd.ny * (D == 3 ? Z / rd.r : 0));
+  const double x = (double)rd.ppc * (double)((const R*)rd.rho)[node];
+  const uint4 wd = philox(c, st.n, rd.rep, TAG_DENSITY, rd.key0, rd.key1);
+  const double fl = floor(x);
+  const uint32_t nmax = (uint32_t)(SPAWN_MAX * rd.ppc);
+  long long nn = (long long)fl + (unit24(wd.x) < x - fl ? 1 : 0);
+  if (nn < 0) nn = 0;
+  uint32_t n = nn > (long long)nmax ? nmax : (uint32_t)nn;
+  if (n == 0) return;
+  R uf[3] = {R(0), R(0), R(0)};
+  u_fine<D, R>(rd, X, Y, Z, uf);
+  const uint32_t base = atomicAdd(rd.pool, n);
+  const bool alt = st.src_alt;
+  uint32_t* home = alt ? rd.home_alt : rd.home;
+  uint32_t* pid = alt ? rd.pid_alt : rd.pid;
+  void* const* offs = alt ? rd.off_alt : rd.off;
+  void* const* vels = alt ? rd.vel_alt : rd.vel;
+  const R sg = Cst<R>::sig(rd);
+  const uint32_t hp = HomePack<D>::pack(X, Y, Z);
+  for (uint32_t k = 0; k < n; ++k) {
+    const uint32_t j = base + k;
+    if (j >= rd.cap) { atomicExch(rd.pool + 1, 1u); break; }
+    const uint32_t id = c * nmax + k;
+    const uint4 wp = philox(id, st.n, rd.rep, TAG_SPAWN_POS, rd.key0, rd.key1);
+    const uint4 wv = philox(id, st.n, rd.rep, TAG_SPAWN_VEL, rd.key0, rd.key1);
+    R z0, z1, z2, z3;
+    normal_pair(wv.x, wv.y, z0, z1);
+    normal_pair(wv.z, wv.w, z2, z3);
+    R o[3] = {(R)unit24(wp.x), (R)unit24(wp.y), D == 3 ? (R)unit24(wp.z) : R(0)};
+    R v[3] = {uf[0] + sg * z0, uf[1] + sg * z1, D == 3 ? uf[2] + sg * z2 : R(0)};
+    home[j] = hp;
+    pid[j] = PID_FRESH;
+    PState<D, R>::st(offs, j, o);
+    PState<D, R>::st(vels, j, v);
+  }
 }
 
 template <int D, typename R>
-static void go_particles(const Launch& L, const int2* bmap, int nwork, int k) {
-  static const int g = grid_cap(grid_for(particle_pass<D, R>, 256, 1 << 30));
-  particle_pass<D, R><<<g < nwork ? g : nwork, 256, 0, L.stream>>>(L.reps, bmap, nwork, L.si, k, L.nrep);
+__global__ void __launch_bounds__(256) spawn_pass(const RepDev* __restrict__ reps, const int2* __restrict__ bmap,
+                                                  int nwork, const StepInfo* __restrict__ si, int k, int nrep) {
+  __shared__ RepDev rd;
+  __shared__ StepInfo st;
+  for_each_item(bmap, nwork, reps, si, k, nrep, rd, st, [&](const int2 bm) { spawn_item<D, R>(rd, st, bm); });
 }
 
-cudaError_t launch_particles(int dim, int prec, const Launch& L, const int2* bmap, int nwork, int k) {
+cudaError_t launch_spawn(int dim, int prec, const Launch& L, const int2* bmap, int nwork, int k) {
   if (nwork == 0) return cudaSuccess;
+  const int g = nwork < 4096 ? nwork : 4096;
   if (dim == 2) {
-    if (prec == P_FP64) go_particles<2, double>(L, bmap, nwork, k);
-    else go_particles<2, float>(L, bmap, nwork, k);
+    if (prec == P_FP64) spawn_pass<2, double><<<g, 256, 0, L.stream>>>(L.reps, bmap, nwork, L.si, k, L.nrep);
+    else spawn_pass<2, float><<<g, 256, 0, L.stream>>>(L.reps, bmap, nwork, L.si, k, L.nrep);
   } else {
-    if (prec == P_FP64) go_particles<3, double>(L, bmap, nwork, k);
-    else go_particles<3, float>(L, bmap, nwork, k);
+    if (prec == P_FP64) spawn_pass<3, double><<<g, 256, 0, L.stream>>>(L.reps, bmap, nwork, L.si, k, L.nrep);
+    else spawn_pass<3, float><<<g, 256, 0, L.stream>>>(L.reps, bmap, nwork, L.si, k, L.nrep);
   }
   return cudaGetLastError();
 }
@@ -695,7 +794,7 @@ __global__ void __launch_bounds__(256, 2) step_persistent(const RepDev* __restri
   for (int k = 0; k < kcount; ++k) {
     for_each_item(bm_lb, nb_lb, reps, si, k, nrep, rd, st, [&](const int4 bm) { lb_row<Q, S, V>(rd, st, bm); });
     if (!grid_barrier(bar, bar + 1, gridDim.x, err)) return;
-    for_each_item(bm_p, nb_p, reps, si, k, nrep, rd, st, [&](const int2 bm) { particle_item<D, R>(rd, st, bm, red); });
+    for_each_item(bm_p, nb_p, reps, si, k, nrep, rd, st, [&](const int2 bm) { particle_item<D, R, false>(rd, st, bm, red); });
     if (!grid_barrier(bar, bar + 1, gridDim.x, err)) return;
     for_each_item(bm_c, nb_c, reps, si, k, nrep, rd, st, [&](const int2 bm) { cell_item<Q, S>(rd, st, bm); });
     if (!grid_barrier(bar, bar + 1, gridDim.x, err)) return;
@@ -763,10 +862,12 @@ template <int D, typename R>
 __global__ void flush_collision(const RepDev* __restrict__ rdp, double s0, double s1, double s2) {
   const RepDev& rd = *rdp;
   const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (j >= rd.np) return;
+  if (j >= pool_end(rd)) return;
   const R s[3] = {(R)s0, (R)s1, (R)s2};     // shifts are exact in binary32
   int X, Y, Z;
-  HomePack<D>::unpack(rd.home[j], X, Y, Z);
+  const uint32_t hp = rd.home[j];
+  if (hp == HOME_DEAD) return;
+  HomePack<D>::unpack(hp, X, Y, Z);
   R o[3] = {R(0), R(0), R(0)}, v[3] = {R(0), R(0), R(0)};
   PState<D, R>::ld(rd.off, (uint32_t)j, o);
   PState<D, R>::ld(rd.vel, (uint32_t)j, v);
@@ -776,7 +877,7 @@ __global__ void flush_collision(const RepDev* __restrict__ rdp, double s0, doubl
 
 cudaError_t launch_flush(int dim, int prec, const RepDev* rd_dev, const RepDev& rd, const double* ls,
                          cudaStream_t st) {
-  const int nb = (int)((rd.np + 255) / 256);
+  const int nb = (int)(((rd.resample ? (long long)rd.cap : rd.np) + 255) / 256);
   if (nb == 0) return cudaSuccess;
   if (dim == 2) {
     if (prec == P_FP64) flush_collision<2, double><<<nb, 256, 0, st>>>(rd_dev, ls[0], ls[1], ls[2]);
@@ -833,13 +934,18 @@ cudaError_t launch_init_particles(int dim, int prec, const RepDev* rd_dev, const
 // particle fields in id order (binary64 / int32) and back.
 enum { F_POS = 3, F_VEL = 4, F_CELL = 5, F_HOME = 10, F_ID = 12 };
 
+// With density resampling the live particles come out in pool order (rank =
+// compaction index from live_scan_*), PART_ID giving each one's id (initial
+// index, or PID_SPAWNED for particles created by the resampling).
 template <int D, typename R>
 __global__ void part_out(RepDev rd, int field, double s0, double s1, double s2, void* out) {
   const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (j >= rd.np) return;
-  const long long id = rd.pid[j];
+  if (j >= pool_end(rd)) return;
+  const uint32_t hp = rd.home[j];
+  if (rd.resample && hp == HOME_DEAD) return;
+  const long long id = rd.resample ? (long long)rd.rank[j] : (long long)rd.pid[j];
   int X, Y, Z;
-  HomePack<D>::unpack(rd.home[j], X, Y, Z);
+  HomePack<D>::unpack(hp, X, Y, Z);
   if (field == F_POS || field == F_VEL) {
     double* o = (double*)out;
     R x[3] = {R(0), R(0), R(0)};
@@ -854,7 +960,7 @@ __global__ void part_out(RepDev rd, int field, double s0, double s1, double s2, 
     const R s[3] = {(R)s0, (R)s1, (R)s2};
     ((int*)out)[id] = (int)collision_cell<D, R>(rd, X, Y, Z, of, s);
   } else {
-    ((int*)out)[id] = (int)id;
+    ((int*)out)[id] = rd.resample ? (int)rd.pid[j] : (int)id;
   }
 }
 
@@ -886,7 +992,7 @@ __global__ void part_in(RepDev rd, int field, const void* in, int* bad) {
 
 cudaError_t launch_part_out(int dim, int prec, const RepDev& rd, int field, const double* ls, void* out,
                             cudaStream_t st) {
-  const int nb = (int)((rd.np + 255) / 256);
+  const int nb = (int)(((rd.resample ? (long long)rd.cap : rd.np) + 255) / 256);
   if (nb == 0) return cudaSuccess;
   if (dim == 2) {
     if (prec == P_FP64) part_out<2, double><<<nb, 256, 0, st>>>(rd, field, ls[0], ls[1], ls[2], out);
@@ -915,9 +1021,12 @@ cudaError_t launch_part_in(int dim, int prec, const RepDev& rd, int field, const
 // particle count, momentum and kinetic energy (binary64) into out[4..8].
 template <int D, typename R>
 __global__ void part_diag(RepDev rd, double* out) {
-  double p[3] = {0, 0, 0}, e = 0;
-  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < rd.np;
+  double p[3] = {0, 0, 0}, e = 0, cnt = 0;
+  const long long end = pool_end(rd);
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < end;
        j += (long long)gridDim.x * blockDim.x) {
+    if (rd.resample && rd.home[j] == HOME_DEAD) continue;
+    cnt += 1.0;
     R vv[3] = {R(0), R(0), R(0)};
     PState<D, R>::ld(rd.vel, (uint32_t)j, vv);
     for (int a = 0; a < D; ++a) {
@@ -926,18 +1035,18 @@ __global__ void part_diag(RepDev rd, double* out) {
       e += 0.5 * rd.mass * v * v;
     }
   }
-  double vals[4] = {p[0], p[1], p[2], e};
-  for (int a = 0; a < 4; ++a) {
+  double vals[5] = {cnt, p[0], p[1], p[2], e};
+  for (int a = 0; a < 5; ++a) {
     double t = vals[a];
     for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(&out[5 + a], t);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&out[4 + a], t);
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&out[4], (double)rd.np);
 }
 
 cudaError_t launch_diag_particles(int dim, int prec, const RepDev& rd, double* out9, cudaStream_t st) {
-  if (rd.np == 0) return cudaSuccess;
-  long long g = (rd.np + 255) / 256;
+  const long long nslots = rd.resample ? (long long)rd.cap : rd.np;
+  if (nslots == 0) return cudaSuccess;
+  long long g = (nslots + 255) / 256;
   const int nb = (int)(g < 1024 ? g : 1024);
   if (dim == 2) {
     if (prec == P_FP64) part_diag<2, double><<<nb, 256, 0, st>>>(rd, out9);
@@ -965,8 +1074,9 @@ __device__ __forceinline__ uint32_t home_index(const RepDev& rd, uint32_t packed
 
 template <int D>
 __device__ __forceinline__ void sort_count_one(const RepDev& rd, const long long j) {
-  const bool active = j < rd.np;
-  const uint32_t h = active ? home_index<D>(rd, rd.home[j]) : 0xFFFFFFFFu;
+  const uint32_t hp = j < pool_end(rd) ? rd.home[j] : HOME_DEAD;
+  const bool active = hp != HOME_DEAD;   // removed particles are dropped (pool compaction)
+  const uint32_t h = active ? home_index<D>(rd, hp) : 0xFFFFFFFFu;
   const unsigned grp = __match_any_sync(0xFFFFFFFFu, h);
   const int lane = threadIdx.x & 31, leader = __ffs(grp) - 1;
   uint32_t base = 0;
@@ -1045,12 +1155,14 @@ __global__ void __launch_bounds__(1024) sort_scan_top(const RepDev* __restrict__
     carry += total;
     __syncthreads();
   }
+  if (threadIdx.x == 0 && rd.resample) rd.pool[2] = carry;   // live particles after the sort
 }
 
 template <int D, typename R>
 __device__ __forceinline__ void sort_scatter_one(const RepDev& rd, const long long j) {
-  if (j >= rd.np) return;
+  if (j >= pool_end(rd)) return;
   const uint32_t hp = rd.home[j];
+  if (hp == HOME_DEAD) return;
   const uint32_t h = home_index<D>(rd, hp);
   const long long dst = (long long)rd.tsum[h / SORT_TILE] + rd.hoff[h] + rd.rank[j];
   rd.home_alt[dst] = hp;
@@ -1094,6 +1206,50 @@ cudaError_t launch_sort(int dim, int prec, const Launch& L, const int2* bmap_p, 
     if (prec == P_FP64) sort_scatter<3, double><<<gs, 256, 0, L.stream>>>(L.reps, bmap_p, nb_p);
     else sort_scatter<3, float><<<gs, 256, 0, L.stream>>>(L.reps, bmap_p, nb_p);
   }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Readout order with density resampling: rank[j] = the number of live
+// particles in the pool slots below j (stable, so that separate readouts of
+// one state agree), ltile the per-tile totals of SORT_TILE slots, pool[2] the
+// live count.
+__global__ void __launch_bounds__(SORT_TILE) live_scan_tiles(RepDev rd) {
+  __shared__ uint32_t wt[33];
+  const long long j = (long long)blockIdx.x * SORT_TILE + threadIdx.x;
+  const bool live = j < pool_end(rd) && rd.home[j] != HOME_DEAD;
+  uint32_t total;
+  const uint32_t ex = block_exclusive_scan(live ? 1u : 0u, wt, total);
+  if (j < rd.cap) rd.rank[j] = ex;
+  if (threadIdx.x == 0) rd.ltile[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(1024) live_scan_top(RepDev rd, int ntile) {
+  __shared__ uint32_t wt[33];
+  uint32_t carry = 0;
+  for (int base = 0; base < ntile; base += blockDim.x) {
+    const int t = base + threadIdx.x;
+    const uint32_t x = t < ntile ? rd.ltile[t] : 0u;
+    uint32_t total;
+    const uint32_t ex = block_exclusive_scan(x, wt, total);
+    if (t < ntile) rd.ltile[t] = carry + ex;
+    carry += total;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) rd.pool[2] = carry;
+}
+
+__global__ void live_scan_add(RepDev rd) {
+  const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (j >= rd.cap) return;
+  rd.rank[j] += rd.ltile[j / SORT_TILE];
+}
+
+cudaError_t launch_live_index(const RepDev& rd, cudaStream_t st) {
+  const int ntile = (int)((rd.cap + SORT_TILE - 1) / SORT_TILE);
+  live_scan_tiles<<<ntile, SORT_TILE, 0, st>>>(rd);
+  live_scan_top<<<1, 1024, 0, st>>>(rd, ntile);
+  live_scan_add<<<(int)((rd.cap + 255) / 256), 256, 0, st>>>(rd);
   return cudaGetLastError();
 }
 
