@@ -34,6 +34,8 @@
 #define TAG_DENSITY 8u
 #define TAG_SPAWN_POS 9u
 #define TAG_SPAWN_VEL 10u
+#define TAG_AT 11u
+#define TAG_AT_VIRT 12u
 #define SPAWN_MAX 4     /* at most SPAWN_MAX * ppc new particles per cell and step */
 
 static const double PI = 3.14159265358979323846;
@@ -140,6 +142,7 @@ struct orc_sim {
   int *pcell;                         /* [np] collision cell of last binning */
   int ncx, ncy, ncz; long ncell;
   int *cnt; double *sumv, *vcm;      /* per collision cell */
+  double *vran, *ranm;               /* MPCD-AT: [np][3] random velocities, [ncell][3] their cell means */
   double shift[3];
   /* coupling */
   long nbuf;                          /* inner-buffer LB nodes */
@@ -177,6 +180,8 @@ orc_sim* orc_create(const orc_params* p, int replica) {
   if (p->lattice == 9 && p->nz != 1) return NULL;
   if (p->tau <= 0.5 || p->refine < 1 || p->ppc < 1 || p->resample_density < 0 || p->resample_density > 1)
     return NULL;
+  /* MPCD-AT draws by particle index, which density resampling renumbers */
+  if (p->collision < 0 || p->collision > 1 || (p->collision == 1 && p->resample_density)) return NULL;
   orc_sim* s = (orc_sim*)calloc(1, sizeof(orc_sim));
   s->p = *p; s->replica = replica;
   s->dim = p->lattice == 9 ? 2 : 3;
@@ -203,7 +208,7 @@ void orc_destroy(orc_sim* s) {
   if (!s) return;
   free(s->f); free(s->fn); free(s->rho); free(s->u);
   free(s->home); free(s->off); free(s->vel); free(s->pcell);
-  free(s->cnt); free(s->sumv); free(s->vcm); free(s->frames); free(s->wmean);
+  free(s->cnt); free(s->sumv); free(s->vcm); free(s->vran); free(s->ranm); free(s->frames); free(s->wmean);
   free(s->cl_frame); free(s->cl_hist); free(s->cl_ema); free(s->cl_x);
   free(s);
 }
@@ -234,6 +239,8 @@ int orc_set_region(orc_sim* s, int x0, int x1) {
   s->cnt = (int*)calloc(s->ncell, sizeof(int));
   s->sumv = (double*)calloc(3 * s->ncell, sizeof(double));
   s->vcm = (double*)calloc(3 * s->ncell, sizeof(double));
+  s->vran = (double*)calloc(3 * s->cap, sizeof(double));
+  s->ranm = (double*)calloc(3 * s->ncell, sizeof(double));
   s->nbuf = 2L * s->n_in * (p->ny - 2) * p->nz;
   int W = p->window > 0 ? p->window : 1;
   s->frames = (double*)calloc((size_t)W * (s->nbuf > 0 ? s->nbuf : 1) * 4, sizeof(double));
@@ -587,8 +594,10 @@ void orc_srd_rotate_3d(const double v[3], const double vcm[3], const double n[3]
  * nonzero shift) holding n_c < ppc particles gets ppc - n_c virtual wall
  * particles whose total momentum is drawn from N(0, (ppc - n_c) m kT) per
  * component (wall at rest); they enter v_cm only. */
+static void collide_at(orc_sim* s);
 static void collide(orc_sim* s) {
   const orc_params* p = &s->p;
+  if (p->collision == 1) { collide_at(s); return; }
   for (long c = 0; c < s->ncell; ++c) {
     int n = s->cnt[c];
     for (int a = 0; a < 3; ++a) s->vcm[3*c+a] = 0.0;
@@ -626,6 +635,61 @@ static void collide(orc_sim* s) {
       double out[3]; orc_srd_rotate_3d(v, vc, axis, p->alpha, out);
       v[0] = out[0]; v[1] = out[1]; v[2] = out[2];
     }
+  }
+}
+
+/* a7 with the Andersen thermostat, MPCD-AT (Eq. 6; collision = 1).  Every
+ * particle k draws a random velocity v_ran,k with components N(0, kT/m)
+ * (Box-Muller of Philox(k, n, replica, TAG_AT)) and leaves the collision with
+ * v_k = v_cm + v_ran,k - <v_ran>, the mean taken over its collision cell: the
+ * relative velocity is replaced, the cell momentum kept.  A wall-cut cell with
+ * n_c < ppc holds ppc - n_c virtual particles that take part like real ones:
+ * their velocity sum, N(0, (ppc - n_c) kT/m) per component from TAG_VIRT as for
+ * SRD, enters v_cm, the sum of their random velocities, drawn the same way from
+ * TAG_AT_VIRT, enters <v_ran>, and both means run over ppc particles. */
+static void collide_at(orc_sim* s) {
+  const orc_params* p = &s->p;
+  const double sig = sqrt(p->kT / p->mass);
+  for (long k = 0; k < s->np; ++k) {
+    uint32_t w[4]; draw(s, (uint32_t)k, (uint32_t)s->step, TAG_AT, w);
+    double z0, z1, z2, z3;
+    orc_box_muller(w[0], w[1], &z0, &z1);
+    orc_box_muller(w[2], w[3], &z2, &z3);
+    s->vran[3*k] = sig * z0;
+    s->vran[3*k+1] = sig * z1;
+    s->vran[3*k+2] = s->dim == 3 ? sig * z2 : 0.0;
+  }
+  for (long c = 0; c < 3 * s->ncell; ++c) s->ranm[c] = 0.0;
+  for (long k = 0; k < s->np; ++k)
+    for (int a = 0; a < 3; ++a) s->ranm[3 * (long)s->pcell[k] + a] += s->vran[3*k+a];
+  for (long c = 0; c < s->ncell; ++c) {
+    int n = s->cnt[c];
+    double P[3] = {s->sumv[3*c], s->sumv[3*c+1], s->sumv[3*c+2]};
+    double X[3] = {s->ranm[3*c], s->ranm[3*c+1], s->ranm[3*c+2]};
+    for (int a = 0; a < 3; ++a) { s->vcm[3*c+a] = 0.0; s->ranm[3*c+a] = 0.0; }
+    if (n == 0) continue;
+    int cy = (int)((c / s->ncx) % s->ncy);
+    int cut = (cy == 0 || cy == s->Hy) && s->shift[1] > 0.0;
+    int ntot = n;
+    if (cut && n < p->ppc) {
+      int nv = p->ppc - n;
+      double sd = sqrt((double)nv * p->kT / p->mass);
+      double z[4];
+      uint32_t w[4]; draw(s, (uint32_t)c, (uint32_t)s->step, TAG_VIRT, w);
+      orc_box_muller(w[0], w[1], &z[0], &z[1]);
+      orc_box_muller(w[2], w[3], &z[2], &z[3]);
+      for (int a = 0; a < s->dim; ++a) P[a] += sd * z[a];
+      draw(s, (uint32_t)c, (uint32_t)s->step, TAG_AT_VIRT, w);
+      orc_box_muller(w[0], w[1], &z[0], &z[1]);
+      orc_box_muller(w[2], w[3], &z[2], &z[3]);
+      for (int a = 0; a < s->dim; ++a) X[a] += sd * z[a];
+      ntot += nv;
+    }
+    for (int a = 0; a < 3; ++a) { s->vcm[3*c+a] = P[a] / (double)ntot; s->ranm[3*c+a] = X[a] / (double)ntot; }
+  }
+  for (long k = 0; k < s->np; ++k) {
+    long c = s->pcell[k];
+    for (int a = 0; a < 3; ++a) s->vel[3*k+a] = s->vcm[3*c+a] + s->vran[3*k+a] - s->ranm[3*c+a];
   }
 }
 
@@ -844,7 +908,10 @@ int orc_get_field(const orc_sim* s, int field, void* dst) {
     case ORC_PART_ID: for (long k = 0; k < n; ++k) I[k] = (int)k; break;
     case ORC_SHIFT: memcpy(D, s->shift, sizeof(double) * 3); break;
     case ORC_CELL_COUNT: memcpy(I, s->cnt, sizeof(int) * n); break;
-    case ORC_CELL_VCM: memcpy(D, s->vcm, sizeof(double) * n); break;
+    case ORC_CELL_VCM:   /* MPCD-AT: v_cm - <v_ran>, what each particle's own v_ran is added to */
+      if (s->p.collision == 1) { for (long i = 0; i < n; ++i) D[i] = s->vcm[i] - s->ranm[i]; }
+      else memcpy(D, s->vcm, sizeof(double) * n);
+      break;
     case ORC_WINDOW_MEAN: memcpy(D, s->wmean, sizeof(double) * n); break;
     case ORC_DIAG: diag(s, D); break;
     case ORC_CLOSURE_IN: memcpy(D, s->cl_x, sizeof(double) * n); break;

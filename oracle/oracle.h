@@ -17,8 +17,9 @@
  *       periodic wrap inside the MPCD region (Sec. 2.3);
  *   a6  inner-buffer sampling of mass and momentum into a per-step frame;
  *   a5  random grid shift and binning into collision cells;
- *   a7  SRD collision, Eq. 4 (2D +-alpha, 3D random axis), with virtual wall
- *       particles in wall-cut cells;
+ *   a7  SRD collision, Eq. 4 (2D +-alpha, 3D random axis), or the MPCD-AT
+ *       collision of Eq. 6 (collision = 1), with virtual wall particles in
+ *       wall-cut cells;
  *   a8  MPCD->LB imposition of equilibrium populations built from the
  *       windowed cell moments on the inner buffer column.
  * With feedback = 2 (D2Q9 only; not in the paper) a8 is replaced by the
@@ -56,6 +57,7 @@ typedef struct {
   int resample_density; /* 0: outer-buffer velocities redrawn (the paper); 1: outer-buffer
                            particles replaced, their number drawn from the LB density */
   uint64_t seed;
+  int collision;        /* 0: SRD (Eq. 4); 1: MPCD with the Andersen thermostat (MPCD-AT, Eq. 6) */
 } orc_params;
 
 typedef struct orc_sim orc_sim;
@@ -64,7 +66,9 @@ typedef struct orc_sim orc_sim;
 enum {
   ORC_RHO = 0, ORC_U = 1, ORC_POPS = 2, ORC_PART_POS = 3, ORC_PART_VEL = 4,
   ORC_PART_CELL = 5, ORC_SHIFT = 6, ORC_CELL_COUNT = 7, ORC_WINDOW_MEAN = 8,
-  ORC_DIAG = 9, ORC_PART_HOME = 10, ORC_CELL_VCM = 11, ORC_PART_ID = 12,
+  ORC_DIAG = 9, ORC_PART_HOME = 10,
+  ORC_CELL_VCM = 11,        /* [ncell][3] SRD: v_cm; MPCD-AT: v_cm minus the cell's mean random velocity */
+  ORC_PART_ID = 12,
   ORC_CLOSURE_IN = 13,      /* [P][16][16][24] network input of the last step */
   ORC_CLOSURE_TARGET = 15   /* [P][16][16][3] moving averages, patch layout */
 };

@@ -1,0 +1,57 @@
+"""The oracle's MPCD viscosity against the closed forms: a standalone MPCD
+Poiseuille flow (coupling width 0, so the region is a periodic channel with
+walls in y and no LB exchange) driven by g, time-averaged profile fitted to
+u(y) = g (y - 1)(ny - 1 - y) / (2 nu) with the walls fixed at the half-way
+positions.  SRD: the kinetic-theory form the paper cites for Eq. 5 (its
+printed Eq. 5 is garbled); MPCD-AT: Eq. 7.  Each case weights the kinetic
+and collisional parts differently, so a wrong variance, angle, cell size or
+wall treatment moves the fit.  Statistical (a few per cent); not GPU."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import transport as T
+
+DEG = math.pi / 180.0
+
+
+def poiseuille_viscosity(collision, kT, r, ppc=10, H=10, W=30, umax=0.15, spin=600, avg=4000, seed=3,
+                         alpha=130 * DEG):
+    a = 1.0 / r
+    kin, col = (T.at_viscosity(ppc, kT, a) if collision else T.srd_viscosity_2d(ppc, kT, alpha, a))
+    nu = kin + col
+    g = 8.0 * nu * umax / H ** 2
+    p = dict(lattice=9, nx=W, ny=H + 2, nz=1, tau=0.5 + 3.0 * nu, force=(g, 0.0, 0.0), refine=r, ppc=ppc,
+             alpha=alpha, kT=kT, mass=1.0, coupling_width=0, precision=0, feedback=0, window=1,
+             resample_density=0, seed=seed, collision=collision)
+    s = O.OracleSim(p)
+    s.set_region(0, W)
+    s.step(spin)
+    Hy = H * r
+    mom, cnt = np.zeros(Hy), np.zeros(Hy)
+    for _ in range(avg):
+        s.step(1)
+        h = s.get("PART_HOME").reshape(-1, 3)
+        v = s.get("PART_VEL").reshape(-1, 3)
+        mom += np.bincount(h[:, 1], weights=v[:, 0], minlength=Hy)
+        cnt += np.bincount(h[:, 1], minlength=Hy)
+    u = mom / cnt
+    y = 1.0 + (np.arange(Hy) + 0.5) / r
+    shape = (y - 1.0) * (H + 1.0 - y) / 2.0          # u = (g / nu) shape
+    return g * np.sum(shape * shape) / np.sum(shape * u), nu, kin, col
+
+
+@pytest.mark.parametrize("kT,r", [(0.25, 1), (0.05, 1), (0.05, 2)])
+def test_mpcd_at_viscosity_eq7(kT, r):
+    fit, nu, kin, col = poiseuille_viscosity(1, kT, r, W=30 if r == 1 else 20)
+    print(f"MPCD-AT kT {kT} a 1/{r}: Eq. 7 {nu:.4f} (kinetic {kin:.4f}, collisional {col:.4f}), fit {fit:.4f}")
+    assert abs(fit / nu - 1.0) < 0.05
+
+
+@pytest.mark.parametrize("kT", [1.0, 0.05])
+def test_srd_viscosity_kinetic_theory(kT):
+    fit, nu, kin, col = poiseuille_viscosity(0, kT, 1)
+    print(f"SRD kT {kT}: closed form {nu:.4f} (kinetic {kin:.4f}, collisional {col:.4f}), fit {fit:.4f}")
+    assert abs(fit / nu - 1.0) < 0.08
