@@ -60,7 +60,8 @@ PROFILE_NOTE = os.path.join(ROOT, "profiles", "ncu_particle_pass_channel2048x512
 
 
 def algorithmic_bytes(p, region):
-    """Algorithmic HBM bytes per step of each kernel (FP32 storage, 2D)."""
+    """Algorithmic HBM bytes per step of each kernel (FP32 storage, 2D).  MPCD-AT
+    reads each particle's id as well (its random velocity is keyed by it)."""
     nx, ny, r, ppc = p["nx"], p["ny"], p["refine"], p["ppc"]
     fluid = nx * (ny - 2)
     Wx, Hy = (region[1] - region[0]) * r, (ny - 2) * r
@@ -68,7 +69,8 @@ def algorithmic_bytes(p, region):
     ncell = Wx * (Hy + 1)
     return dict(
         lb_pull=72 * fluid,              # 9 populations read + 9 written, 4 B each
-        particle_pass=40 * npart,        # home 4 + offsets 8 + velocities 8, read and written
+        particle_pass=(44 if p.get("collision", 0) else 40) * npart,   # home 4 + offsets 8 + velocities 8,
+                                                                       # read and written (+ id 4 for MPCD-AT)
         cell_pass=52 * ncell,            # accumulators read 12 + cleared 12, table written 16, read 12
         fluid_nodes=fluid, particles=npart, cells=ncell)
 
@@ -163,7 +165,8 @@ def cpu_baseline(seconds: float = 12.0):
             break
     dt = time.perf_counter() - t0
     return {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{n} full coupled steps of the 2048x512 / 5.2M-particle workload after 1 warm-up step, "
+            "sample": f"{n} full coupled steps of the {WORKLOAD['name']} workload (5.2M particles) after 1 "
+                      "warm-up step, "
                       f"FP64, single thread, {dt:.1f} s"}
 
 
@@ -298,7 +301,7 @@ def run_ours(args, rank, world, local_rank):
     dom = "particle_pass"
     t_dom = per_launch[dom] * 1e-3
     achieved = ab[dom] / t_dom / 1e9
-    traffic = ncu_traffic_per_launch()
+    traffic = ncu_traffic_per_launch() if not p.get("collision", 0) else None
     kernels = {}
     for k in ("lb_pull", "particle_pass", "cell_pass"):
         t = per_launch[k] * 1e-3
@@ -582,6 +585,8 @@ def main():
                     help="channel: the 2048x512 headline workload; ensemble: the 64-replica ensemble; "
                          "closure: training, gain and in-loop runs of the learned closure (extra lines)")
     ap.add_argument("--fp16", action="store_true", help="ensemble only: FP16 deviation storage")
+    ap.add_argument("--collision", default="srd", choices=["srd", "at"],
+                    help="channel only: SRD (Eq. 4, default) or MPCD-AT (Eq. 6) collisions (extra line)")
     ap.add_argument("--launch", default="auto", choices=["auto", "graphs", "graphs_tma", "persistent"],
                     help="launch form of the step: autotuned (default), per-kernel graphs, persistent kernel")
     args = ap.parse_args()
@@ -590,6 +595,9 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.collision == "at":
+        global WORKLOAD
+        WORKLOAD = dict(WORKLOAD, name=WORKLOAD["name"] + "_mpcd_at", params=dict(WORKLOAD["params"], collision=1))
     if args.impl == "reference":
         run_reference(args, rank, world)
         return

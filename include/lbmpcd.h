@@ -68,7 +68,7 @@ enum {
  *  DIAG [9] (double)                      LB mass, LB momentum (3), particle count,
  *                                         particle momentum (3), kinetic energy
  *  PART_HOME [np][3] (int32)              integer home cell of each particle
- *  CELL_VCM [ncell][3] (double)           centre-of-mass velocity of the last collision
+ *  CELL_VCM [ncell][3] (double)           centre-of-mass velocity of the last collision (MPCD-AT: v_cm - <v_ran>)
  *  PART_ID [np] (int32)                   identity: particle fields come back in id order
  *                                         (with resample_density = 1: the live particles
  *                                         in pool order, the same for every field read
@@ -112,7 +112,19 @@ typedef struct {
                            1: outer-buffer particles replaced each step by
                            N = stochastic-round(ppc rho_LB) new ones (see below) */
   uint64_t seed;        /* Philox key */
+  int collision;        /* 0: SRD, stochastic rotation (Eq. 4); 1: MPCD-AT, Andersen thermostat
+                           (Eq. 6, the rule the paper's runs use; see below).  All replicas of a
+                           handle share it; 1 excludes resample_density = 1 */
 } lbmpcd_params;
+
+/* MPCD-AT (collision = 1): each particle leaves the collision with
+ * v_cm + v_ran - <v_ran>, v_ran a fresh Maxwellian velocity (variance kT/m per
+ * component, Box-Muller of Philox(particle id, n, replica, 11)), the mean over
+ * its collision cell.  In a wall-cut cell with n_c < ppc the ppc - n_c virtual
+ * particles are members of the cell: their velocity sum (Philox tag 4, as for
+ * SRD) enters v_cm and the sum of their random velocities (tag 12) enters
+ * <v_ran>.  Field CELL_VCM then holds v_cm - <v_ran>.  The persistent launch
+ * form is not available in this mode. */
 
 /* Density resampling (resample_density = 1; a reading of "resampling from the
  * local LB density": the paper keeps its particles and redraws velocities):

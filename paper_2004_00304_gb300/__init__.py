@@ -44,7 +44,8 @@ class lbmpcd_params(ctypes.Structure):
                 ("kT", ctypes.c_double), ("mass", ctypes.c_double),
                 ("coupling_width", ctypes.c_int), ("precision", ctypes.c_int),
                 ("feedback", ctypes.c_int), ("window", ctypes.c_int),
-                ("resample_density", ctypes.c_int), ("seed", ctypes.c_uint64)]
+                ("resample_density", ctypes.c_int), ("seed", ctypes.c_uint64),
+                ("collision", ctypes.c_int)]
 
 
 _lib = None
@@ -118,6 +119,7 @@ def make_params(d: dict) -> lbmpcd_params:
     p.window = int(d.get("window", 100))
     p.resample_density = int(d.get("resample_density", 0))
     p.seed = int(d.get("seed", 1))
+    p.collision = int(d.get("collision", 0))
     return p
 
 

@@ -16,7 +16,8 @@ namespace lbm {
 // tag), key: the 64-bit seed.  Same stream on host and device.
 enum : uint32_t { TAG_SHIFT = 1, TAG_SIGN = 2, TAG_AXIS = 3, TAG_VIRT = 4,
                   TAG_RESAMPLE = 5, TAG_INIT_POS = 6, TAG_INIT_VEL = 7,
-                  TAG_DENSITY = 8, TAG_SPAWN_POS = 9, TAG_SPAWN_VEL = 10 };
+                  TAG_DENSITY = 8, TAG_SPAWN_POS = 9, TAG_SPAWN_VEL = 10,
+                  TAG_AT = 11, TAG_AT_VIRT = 12 };
 
 // density resampling of the outer buffer (resample_density = 1): a removed
 // particle's home is HOME_DEAD until the next sort compacts the pool; a new
@@ -141,6 +142,8 @@ struct RepDev {
   // its end, pool[1] an overflow flag, pool[2] the live count of the last
   // sort or compaction; ltile scratch of the readout compaction
   int resample;
+  // collision rule: 0 SRD (Eq. 4), 1 MPCD-AT (Eq. 6)
+  int collision;
   uint32_t cap;
   uint32_t* pool;
   uint32_t* ltile;

@@ -146,11 +146,20 @@ __device__ __forceinline__ uint32_t collision_cell(const RepDev& rd, int X, int 
 
 // a7, particle side: v <- v_cm + R (v - v_cm).  2D: R = rotation by theta
 // with sin(theta) stored per cell; 3D: Rodrigues' formula about the cell axis.
+// MPCD-AT: v holds the particle's random velocity and the table v_cm minus the
+// cell's mean random velocity, so the collision is their sum.
 template <int D, typename R>
 __device__ __forceinline__ void rotate(const RepDev& rd, uint32_t c, R* v) {
   using T4 = typename Vec4<R>::T;
   const R ca = Cst<R>::cos_a(rd);
   const T4* tab = (const T4*)rd.tab;
+  if (rd.collision == 1) {
+    const T4 t = tab[D == 2 ? (size_t)c : 2 * (size_t)c];
+    v[0] += t.x;
+    v[1] += t.y;
+    if (D == 3) v[2] += t.z;
+    return;
+  }
   if (D == 2) {
     const T4 t = tab[c];
     const R wx = v[0] - t.x, wy = v[1] - t.y;
@@ -271,7 +280,15 @@ template <int D, typename R> struct PassShared {
   R sv[D][256];
 };
 
-template <int D, typename R, bool RS>
+// RS: density resampling compiled in; AT: MPCD-AT collision (Eq. 6) instead of
+// SRD.  MPCD-AT needs the cell mean of the particles' random velocities
+// before any particle can leave the collision; as the old relative velocity
+// plays no part in it, the binning pass draws each particle's random velocity
+// v_ran, adds v - v_ran to its cell sum and stores v_ran in place of v.  The
+// cell pass turns the sums into v_cm - <v_ran>, and the next pass adds that to
+// the stored v_ran: v_cm + v_ran - <v_ran> (virtual wall particles enter the
+// cell pass).
+template <int D, typename R, bool RS, bool AT>
 __device__ __forceinline__ void particle_item(const RepDev& rd, const StepInfo& st, const int2 bm,
                                               PassShared<D, R>& red) {
   using T4 = typename Vec4<R>::T;
@@ -313,13 +330,17 @@ __device__ __forceinline__ void particle_item(const RepDev& rd, const StepInfo& 
     for (int p = 0; p < PPT; ++p) {
       const uint32_t c = collision_cell<D, R>(rd, X[p], Y[p], Z[p], o[p], Cst<R>::prev(st));
       if (D == 2) t0[p] = tab[c];
-      else { t0[p] = tab[2 * (size_t)c]; t1[p] = tab[2 * (size_t)c + 1]; }
+      else { t0[p] = tab[2 * (size_t)c]; if (!AT) t1[p] = tab[2 * (size_t)c + 1]; }
     }
     const R ca = Cst<R>::cos_a(rd), sa = Cst<R>::sin_a(rd);
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
       if (RS && fresh[p]) continue;
-      if (D == 2) {
+      if (AT) {
+        v[p][0] += t0[p].x;
+        v[p][1] += t0[p].y;
+        if (D == 3) v[p][2] += t0[p].z;
+      } else if (D == 2) {
         const T4 t = t0[p];
         const R wx = v[p][0] - t.x, wy = v[p][1] - t.y;
         v[p][0] = t.x + (ca * wx - t.z * wy);
@@ -391,7 +412,20 @@ __device__ __forceinline__ void particle_item(const RepDev& rd, const StepInfo& 
     cid[p] = collision_cell<D, R>(rd, X[p], Y[p], Z[p], o[p], Cst<R>::shift(st));
     rd.home[j] = HomePack<D>::pack(X[p], Y[p], Z[p]);
     PState<D, R>::st(rd.off, j, o[p]);
-    PState<D, R>::st(rd.vel, j, v[p]);
+    if (AT) {
+      // a7 (MPCD-AT), first half: v_ran from Philox(id, n, replica, TAG_AT)
+      const uint4 w = philox((alt ? rd.pid_alt : rd.pid)[j], st.n, rd.rep, TAG_AT, rd.key0, rd.key1);
+      R z[4];
+      normal_pair(w.x, w.y, z[0], z[1]);
+      if (D == 3) normal_pair(w.z, w.w, z[2], z[3]);
+      const R sg = Cst<R>::sig(rd);
+      R xi[3] = {sg * z[0], sg * z[1], D == 3 ? sg * z[2] : R(0)};
+      PState<D, R>::st(rd.vel, j, xi);
+#pragma unroll
+      for (int a = 0; a < D; ++a) v[p][a] -= xi[a];
+    } else {
+      PState<D, R>::st(rd.vel, j, v[p]);
+    }
   }
   // Cell sums.  Binary32: one vector atomic {n, sum v} per group of lanes;
   // lanes are first merged with their xor-1 and then xor-2 neighbours when
@@ -460,31 +494,41 @@ __device__ __forceinline__ void particle_item(const RepDev& rd, const StepInfo& 
   }
 }
 
-template <int D, typename R, bool RS>
+template <int D, typename R, bool RS, bool AT>
 __global__ void __launch_bounds__(256, 6) particle_pass(const RepDev* __restrict__ reps, const int2* __restrict__ bmap,
                                                      int nwork, const StepInfo* __restrict__ si, int k, int nrep) {
   __shared__ RepDev rd;
   __shared__ StepInfo st;
   __shared__ PassShared<D, R> red;
-  for_each_item(bmap, nwork, reps, si, k, nrep, rd, st, [&](const int2 bm) { particle_item<D, R, RS>(rd, st, bm, red); });
+  for_each_item(bmap, nwork, reps, si, k, nrep, rd, st,
+                [&](const int2 bm) { particle_item<D, R, RS, AT>(rd, st, bm, red); });
 }
 
-template <int D, typename R, bool RS>
+template <int D, typename R, bool RS, bool AT>
 static void go_particles(const Launch& L, const int2* bmap, int nwork, int k) {
-  static const int g = grid_cap(grid_for(particle_pass<D, R, RS>, 256, 1 << 30));
-  particle_pass<D, R, RS><<<g < nwork ? g : nwork, 256, 0, L.stream>>>(L.reps, bmap, nwork, L.si, k, L.nrep);
+  static const int g = grid_cap(grid_for(particle_pass<D, R, RS, AT>, 256, 1 << 30));
+  particle_pass<D, R, RS, AT><<<g < nwork ? g : nwork, 256, 0, L.stream>>>(L.reps, bmap, nwork, L.si, k, L.nrep);
+}
+
+template <int D, typename R>
+static void go_particles_mode(bool rs, bool at, const Launch& L, const int2* bmap, int nwork, int k) {
+  if (at) go_particles<D, R, false, true>(L, bmap, nwork, k);
+  else if (rs) go_particles<D, R, true, false>(L, bmap, nwork, k);
+  else go_particles<D, R, false, false>(L, bmap, nwork, k);
 }
 
 // rs: some replica of the handle uses density resampling (the pass then checks
-// each replica's mode; without it the resampling code is not compiled in)
-cudaError_t launch_particles(int dim, int prec, bool rs, const Launch& L, const int2* bmap, int nwork, int k) {
+// each replica's mode; without it the resampling code is not compiled in);
+// at: the handle's replicas collide by MPCD-AT (never together with rs)
+cudaError_t launch_particles(int dim, int prec, bool rs, bool at, const Launch& L, const int2* bmap, int nwork,
+                             int k) {
   if (nwork == 0) return cudaSuccess;
   if (dim == 2) {
-    if (prec == P_FP64) rs ? go_particles<2, double, true>(L, bmap, nwork, k) : go_particles<2, double, false>(L, bmap, nwork, k);
-    else rs ? go_particles<2, float, true>(L, bmap, nwork, k) : go_particles<2, float, false>(L, bmap, nwork, k);
+    if (prec == P_FP64) go_particles_mode<2, double>(rs, at, L, bmap, nwork, k);
+    else go_particles_mode<2, float>(rs, at, L, bmap, nwork, k);
   } else {
-    if (prec == P_FP64) rs ? go_particles<3, double, true>(L, bmap, nwork, k) : go_particles<3, double, false>(L, bmap, nwork, k);
-    else rs ? go_particles<3, float, true>(L, bmap, nwork, k) : go_particles<3, float, false>(L, bmap, nwork, k);
+    if (prec == P_FP64) go_particles_mode<3, double>(rs, at, L, bmap, nwork, k);
+    else go_particles_mode<3, float>(rs, at, L, bmap, nwork, k);
   }
   return cudaGetLastError();
 }
@@ -607,7 +651,9 @@ __device__ __forceinline__ void cell_item(const RepDev& rd, const StepInfo& st, 
         const bool cut = (cy == 0 || cy == (uint32_t)rd.Hy) && st.shift_f[1] > 0.0f;
         if (cut && (int)n < rd.ppc) {
           // Lamura-type wall: ppc - n virtual particles at rest, summed momentum
-          // drawn from N(0, (ppc - n) m kT) per component.
+          // drawn from N(0, (ppc - n) m kT) per component.  MPCD-AT: they are
+          // members of the cell, so the sum of their random velocities (same
+          // law, TAG_AT_VIRT) is taken off as well: the sums hold v - v_ran.
           const int nv = rd.ppc - (int)n;
           const uint4 w = philox((uint32_t)c, st.n, rd.rep, TAG_VIRT, rd.key0, rd.key1);
           R z[4];
@@ -615,13 +661,24 @@ __device__ __forceinline__ void cell_item(const RepDev& rd, const StepInfo& st, 
           normal_pair(w.z, w.w, z[2], z[3]);
           const R sd = sqrt((R)nv * Cst<R>::kT_over_m(rd));
 #pragma unroll
-          for (int a = 0; a < D; ++a) vc[a] = (V[p][a] + sd * z[a]) / (R)rd.ppc;
+          for (int a = 0; a < D; ++a) V[p][a] += sd * z[a];
+          if (rd.collision == 1) {
+            const uint4 wa = philox((uint32_t)c, st.n, rd.rep, TAG_AT_VIRT, rd.key0, rd.key1);
+            normal_pair(wa.x, wa.y, z[0], z[1]);
+            normal_pair(wa.z, wa.w, z[2], z[3]);
+#pragma unroll
+            for (int a = 0; a < D; ++a) V[p][a] -= sd * z[a];
+          }
+#pragma unroll
+          for (int a = 0; a < D; ++a) vc[a] = V[p][a] / (R)rd.ppc;
         } else {
           const R inv_n = R(1) / (R)n;
 #pragma unroll
           for (int a = 0; a < D; ++a) vc[a] = V[p][a] * inv_n;
         }
-        if (D == 2) {
+        if (rd.collision == 1) {
+          // MPCD-AT: no rotation; the table holds v_cm - <v_ran>
+        } else if (D == 2) {
           const uint4 w = philox((uint32_t)c, st.n, rd.rep, TAG_SIGN, rd.key0, rd.key1);
           rt[0] = (w.x >> 31) ? Cst<R>::sin_a(rd) : -Cst<R>::sin_a(rd);
         } else {
@@ -794,7 +851,7 @@ __global__ void __launch_bounds__(256, 2) step_persistent(const RepDev* __restri
   for (int k = 0; k < kcount; ++k) {
     for_each_item(bm_lb, nb_lb, reps, si, k, nrep, rd, st, [&](const int4 bm) { lb_row<Q, S, V>(rd, st, bm); });
     if (!grid_barrier(bar, bar + 1, gridDim.x, err)) return;
-    for_each_item(bm_p, nb_p, reps, si, k, nrep, rd, st, [&](const int2 bm) { particle_item<D, R, false>(rd, st, bm, red); });
+    for_each_item(bm_p, nb_p, reps, si, k, nrep, rd, st, [&](const int2 bm) { particle_item<D, R, false, false>(rd, st, bm, red); });
     if (!grid_barrier(bar, bar + 1, gridDim.x, err)) return;
     for_each_item(bm_c, nb_c, reps, si, k, nrep, rd, st, [&](const int2 bm) { cell_item<Q, S>(rd, st, bm); });
     if (!grid_barrier(bar, bar + 1, gridDim.x, err)) return;
