@@ -22,6 +22,7 @@ struct Launch {
   const StepInfo* si;     // device [kcount][nrep]
   cudaStream_t stream;
   int* err;               // set by a kernel whose bounded wait gave up
+  const RepDev* host;     // host copy of the table (single-replica kernels take it by value)
 };
 
 // a1: fused pull stream + BGK collide (+ Guo force, bounce-back walls).

@@ -439,7 +439,7 @@ extern "C" int lbmpcd_set_region(lbmpcd* h, int replica, const int lo[3], const 
 static bool persistent(const lbmpcd* h) { return h->mode == 1 && h->nb_cl == 0; }
 
 static int run_chunk(lbmpcd* h, int kcount, bool sort) {
-  Launch L{h->d_reps, h->nrep, h->d_si, h->stream, h->d_flag + 8};
+  Launch L{h->d_reps, h->nrep, h->d_si, h->stream, h->d_flag + 8, h->rd.data()};
   // density resampling compacts its particle pool at the start of every chunk
   sort = (sort || h->nb_s > 0) && h->nb_p > 0;
   if (sort) CK(h, launch_sort(h->dim, h->prec, L, h->bm_p, h->nb_p, h->bm_t, h->nb_t));
@@ -546,7 +546,7 @@ extern "C" int lbmpcd_step_profiled(lbmpcd* h, int nsteps, double* phase_ms, lon
   const int nev = 2 * (2 + 5 * KCHUNK);
   std::vector<cudaEvent_t> ev(nev, nullptr);
   for (auto& x : ev) CK(h, cudaEventCreate(&x));
-  Launch L{h->d_reps, h->nrep, h->d_si, h->stream, h->d_flag + 8};
+  Launch L{h->d_reps, h->nrep, h->d_si, h->stream, h->d_flag + 8, h->rd.data()};
   int rc = LBMPCD_OK;
   long long nl = 0;
   int left = nsteps;
