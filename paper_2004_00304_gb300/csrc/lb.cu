@@ -24,9 +24,22 @@ __global__ void __launch_bounds__(128, 5) lb_pull(const RepDev* __restrict__ rep
   for_each_item(bmap, nwork, reps, si, k, nrep, rd, st, [&](const int4 bm) { lb_row<Q, S, V>(rd, st, bm); });
 }
 
+// single-replica form (see for_each_item_one)
+template <int Q, typename S, int V>
+__global__ void __launch_bounds__(128, 5) lb_pull_one(const __grid_constant__ RepDev rd, const int4* __restrict__ bmap,
+                                                   int nwork, const StepInfo* __restrict__ si, int k) {
+  __shared__ StepInfo st;
+  for_each_item_one(bmap, nwork, si, k, st, [&](const int4 bm) { lb_row<Q, S, V>(rd, st, bm); });
+}
+
 template <int Q, typename S, int V>
 static cudaError_t go_lb(const Launch& L, const int4* bmap, int nwork, int k) {
   if (nwork == 0) return cudaSuccess;
+  if (L.nrep == 1 && L.host) {
+    static const int g1 = grid_cap(grid_for(lb_pull_one<Q, S, V>, 128, 1 << 30));
+    lb_pull_one<Q, S, V><<<g1 < nwork ? g1 : nwork, 128, 0, L.stream>>>(*L.host, bmap, nwork, L.si, k);
+    return cudaGetLastError();
+  }
   static const int g = grid_cap(grid_for(lb_pull<Q, S, V>, 128, 1 << 30));
   lb_pull<Q, S, V><<<g < nwork ? g : nwork, 128, 0, L.stream>>>(L.reps, bmap, nwork, L.si, k, L.nrep);
   return cudaGetLastError();

@@ -504,22 +504,14 @@ __global__ void __launch_bounds__(256, 6) particle_pass(const RepDev* __restrict
                 [&](const int2 bm) { particle_item<D, R, RS, AT>(rd, st, bm, red); });
 }
 
-// Single-replica form: the replica record is a __grid_constant__ kernel
-// parameter, so the pass reads its fields as constant-bank operands instead of
-// shared-memory loads (the record is fixed between graph rebuilds).
+// single-replica form (see for_each_item_one)
 template <int D, typename R, bool RS, bool AT>
 __global__ void __launch_bounds__(256, 6) particle_pass_one(const __grid_constant__ RepDev rd,
                                                          const int2* __restrict__ bmap, int nwork,
                                                          const StepInfo* __restrict__ si, int k) {
   __shared__ StepInfo st;
   __shared__ PassShared<D, R> red;
-  {
-    const int* c = (const int*)(si + k);
-    int* d = (int*)&st;
-    for (int i = threadIdx.x; i < (int)(sizeof(StepInfo) / 4); i += blockDim.x) d[i] = c[i];
-    __syncthreads();
-  }
-  for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) particle_item<D, R, RS, AT>(rd, st, bmap[wi], red);
+  for_each_item_one(bmap, nwork, si, k, st, [&](const int2 bm) { particle_item<D, R, RS, AT>(rd, st, bm, red); });
 }
 
 template <int D, typename R, bool RS, bool AT>
@@ -800,7 +792,19 @@ __global__ void __launch_bounds__(256) cell_pass(const RepDev* __restrict__ reps
 }
 
 template <int Q, typename S>
+__global__ void __launch_bounds__(256) cell_pass_one(const __grid_constant__ RepDev rd, const int2* __restrict__ bmap,
+                                                     int nwork, const StepInfo* __restrict__ si, int k) {
+  __shared__ StepInfo st;
+  for_each_item_one(bmap, nwork, si, k, st, [&](const int2 bm) { cell_item<Q, S>(rd, st, bm); });
+}
+
+template <int Q, typename S>
 static void go_cells(const Launch& L, const int2* bmap, int nwork, int k) {
+  if (L.nrep == 1 && L.host) {
+    static const int g1 = grid_cap(grid_for(cell_pass_one<Q, S>, 256, 1 << 30));
+    cell_pass_one<Q, S><<<g1 < nwork ? g1 : nwork, 256, 0, L.stream>>>(*L.host, bmap, nwork, L.si, k);
+    return;
+  }
   static const int g = grid_cap(grid_for(cell_pass<Q, S>, 256, 1 << 30));
   cell_pass<Q, S><<<g < nwork ? g : nwork, 256, 0, L.stream>>>(L.reps, bmap, nwork, L.si, k, L.nrep);
 }
