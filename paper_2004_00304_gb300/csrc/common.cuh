@@ -341,14 +341,16 @@ __device__ __forceinline__ void for_each_item(const Item* __restrict__ bmap, int
 // value (a __grid_constant__ kernel parameter, read as constant-bank operands
 // instead of shared-memory loads); only the step record is staged in shared
 // memory.  The record is fixed between graph rebuilds.
-template <typename Item, typename Body>
-__device__ __forceinline__ void for_each_item_one(const Item* __restrict__ bmap, int nwork, const StepInfo* si,
-                                                  int k, StepInfo& st, Body&& body) {
+// The items of a single replica are computed from their index (item_of)
+// rather than read from the block map, which saves a dependent load.
+template <typename ItemOf, typename Body>
+__device__ __forceinline__ void for_each_item_one(ItemOf&& item_of, int nwork, const StepInfo* si, int k,
+                                                  StepInfo& st, Body&& body) {
   const int* c = (const int*)(si + k);
   int* d = (int*)&st;
   for (int i = threadIdx.x; i < (int)(sizeof(StepInfo) / 4); i += blockDim.x) d[i] = c[i];
   __syncthreads();
-  for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) body(bmap[wi]);
+  for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) body(item_of(wi));
 }
 
 // Resident-grid size for a kernel; LBMPCD_GRID_BLOCKS_PER_ITEM=1 in the

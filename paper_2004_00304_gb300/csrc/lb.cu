@@ -25,11 +25,14 @@ __global__ void __launch_bounds__(128, 5) lb_pull(const RepDev* __restrict__ rep
 }
 
 // single-replica form (see for_each_item_one)
+// items from the block map (computing (tile, y, z) from the index takes
+// integer divisions that cost more than the load)
 template <int Q, typename S, int V>
 __global__ void __launch_bounds__(128, 5) lb_pull_one(const __grid_constant__ RepDev rd, const int4* __restrict__ bmap,
                                                    int nwork, const StepInfo* __restrict__ si, int k) {
   __shared__ StepInfo st;
-  for_each_item_one(bmap, nwork, si, k, st, [&](const int4 bm) { lb_row<Q, S, V>(rd, st, bm); });
+  for_each_item_one([bmap](int wi) { return bmap[wi]; }, nwork, si, k, st,
+                    [&](const int4 bm) { lb_row<Q, S, V>(rd, st, bm); });
 }
 
 template <int Q, typename S, int V>

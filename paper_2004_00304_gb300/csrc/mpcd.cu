@@ -437,25 +437,27 @@ __device__ __forceinline__ void particle_item(const RepDev& rd, const StepInfo& 
   // per particle slot: lanes sharing a collision cell are summed by their
   // lowest lane, which issues one atomic per accumulator.
   if (sizeof(R) == 4) {
+    // a lane with nothing to add (inactive, or merged into its partner) holds
+    // the cell id NONE, which matches no partner; in 2D the fourth component
+    // is zero and is not exchanged
+    constexpr uint32_t NONE = 0xFFFFFFFFu;
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
-      uint32_t c = act[p] ? cid[p] : 0xFFFFFFFFu;
-      float4 a = make_float4(act[p] ? 1.0f : 0.0f, (float)v[p][0], (float)v[p][1], D == 3 ? (float)v[p][D - 1] : 0.0f);
-      bool live = act[p];
+      uint32_t c = act[p] ? cid[p] : NONE;
+      float4 a = make_float4(1.0f, (float)v[p][0], (float)v[p][1], D == 3 ? (float)v[p][D - 1] : 0.0f);
 #pragma unroll
       for (int r = 0; r < 2; ++r) {
         const int m = 1 << r;
         const uint32_t co = __shfl_xor_sync(0xFFFFFFFFu, c, m);
         const float ax = __shfl_xor_sync(0xFFFFFFFFu, a.x, m), ay = __shfl_xor_sync(0xFFFFFFFFu, a.y, m);
-        const float az = __shfl_xor_sync(0xFFFFFFFFu, a.z, m), aw = __shfl_xor_sync(0xFFFFFFFFu, a.w, m);
-        const bool lo = (lane & m) == 0;
-        const bool olive = __shfl_xor_sync(0xFFFFFFFFu, (int)live, m) != 0;
-        if (live && olive && co == c) {
-          if (lo) { a.x += ax; a.y += ay; a.z += az; a.w += aw; } else live = false;
+        const float az = __shfl_xor_sync(0xFFFFFFFFu, a.z, m);
+        const float aw = D == 3 ? __shfl_xor_sync(0xFFFFFFFFu, a.w, m) : 0.0f;
+        if (c != NONE && co == c) {
+          if ((lane & m) == 0) { a.x += ax; a.y += ay; a.z += az; if (D == 3) a.w += aw; } else c = NONE;
         }
       }
-      if (live) atomicAdd(rd.acc4 + c, a);
+      if (c != NONE) atomicAdd(rd.acc4 + c, a);
     }
     return;
   }
@@ -506,19 +508,19 @@ __global__ void __launch_bounds__(256, 6) particle_pass(const RepDev* __restrict
 
 // single-replica form (see for_each_item_one)
 template <int D, typename R, bool RS, bool AT>
-__global__ void __launch_bounds__(256, 6) particle_pass_one(const __grid_constant__ RepDev rd,
-                                                         const int2* __restrict__ bmap, int nwork,
+__global__ void __launch_bounds__(256, 6) particle_pass_one(const __grid_constant__ RepDev rd, int nwork,
                                                          const StepInfo* __restrict__ si, int k) {
   __shared__ StepInfo st;
   __shared__ PassShared<D, R> red;
-  for_each_item_one(bmap, nwork, si, k, st, [&](const int2 bm) { particle_item<D, R, RS, AT>(rd, st, bm, red); });
+  for_each_item_one([](int wi) { return make_int2(0, wi); }, nwork, si, k, st,
+                    [&](const int2 bm) { particle_item<D, R, RS, AT>(rd, st, bm, red); });
 }
 
 template <int D, typename R, bool RS, bool AT>
 static void go_particles(const Launch& L, const int2* bmap, int nwork, int k) {
   if (L.nrep == 1 && L.host) {
     static const int g1 = grid_cap(grid_for(particle_pass_one<D, R, RS, AT>, 256, 1 << 30));
-    particle_pass_one<D, R, RS, AT><<<g1 < nwork ? g1 : nwork, 256, 0, L.stream>>>(*L.host, bmap, nwork, L.si, k);
+    particle_pass_one<D, R, RS, AT><<<g1 < nwork ? g1 : nwork, 256, 0, L.stream>>>(*L.host, nwork, L.si, k);
     return;
   }
   static const int g = grid_cap(grid_for(particle_pass<D, R, RS, AT>, 256, 1 << 30));
@@ -791,18 +793,21 @@ __global__ void __launch_bounds__(256) cell_pass(const RepDev* __restrict__ reps
   for_each_item(bmap, nwork, reps, si, k, nrep, rd, st, [&](const int2 bm) { cell_item<Q, S>(rd, st, bm); });
 }
 
+// items: the cell blocks (0, b) of the replica, then its a8 blocks (0, -1 - b)
 template <int Q, typename S>
-__global__ void __launch_bounds__(256) cell_pass_one(const __grid_constant__ RepDev rd, const int2* __restrict__ bmap,
-                                                     int nwork, const StepInfo* __restrict__ si, int k) {
+__global__ void __launch_bounds__(256) cell_pass_one(const __grid_constant__ RepDev rd, int nwork,
+                                                     const StepInfo* __restrict__ si, int k) {
   __shared__ StepInfo st;
-  for_each_item_one(bmap, nwork, si, k, st, [&](const int2 bm) { cell_item<Q, S>(rd, st, bm); });
+  const int ncb = (int)((rd.ncell + 256 * CPT - 1) / (256 * CPT));
+  for_each_item_one([ncb](int wi) { return make_int2(0, wi < ncb ? wi : -1 - (wi - ncb)); }, nwork, si, k, st,
+                    [&](const int2 bm) { cell_item<Q, S>(rd, st, bm); });
 }
 
 template <int Q, typename S>
 static void go_cells(const Launch& L, const int2* bmap, int nwork, int k) {
   if (L.nrep == 1 && L.host) {
     static const int g1 = grid_cap(grid_for(cell_pass_one<Q, S>, 256, 1 << 30));
-    cell_pass_one<Q, S><<<g1 < nwork ? g1 : nwork, 256, 0, L.stream>>>(*L.host, bmap, nwork, L.si, k);
+    cell_pass_one<Q, S><<<g1 < nwork ? g1 : nwork, 256, 0, L.stream>>>(*L.host, nwork, L.si, k);
     return;
   }
   static const int g = grid_cap(grid_for(cell_pass<Q, S>, 256, 1 << 30));
