@@ -62,6 +62,7 @@ def lib():
         L.orc_create.restype = vp
         L.orc_create.argtypes = [ctypes.POINTER(Params), ctypes.c_int]
         L.orc_set_region.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+        L.orc_set_strip.argtypes = [vp, ctypes.c_int]
         L.orc_step.argtypes = [vp, ctypes.c_int]
         L.orc_field_size.restype = ctypes.c_long
         L.orc_field_size.argtypes = [vp, ctypes.c_int]
@@ -131,6 +132,11 @@ class OracleSim:
     def set_region(self, x0: int, x1: int) -> None:
         if lib().orc_set_region(self._h, int(x0), int(x1)) != 0:
             raise ValueError("bad region")
+
+    def set_strip(self, y1: int) -> None:
+        """Near-wall strip (Sec. 3.3): all columns, LB rows [1, y1), buffer along y1."""
+        if lib().orc_set_strip(self._h, int(y1)) != 0:
+            raise ValueError("bad strip")
 
     def step(self, n: int = 1) -> None:
         lib().orc_step(self._h, int(n))

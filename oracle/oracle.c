@@ -18,6 +18,15 @@
  * Each x-side has a coupling buffer of coupling_width LB columns: the outer
  * ceil(cw/2) columns take the LB->MPCD redraw, the inner floor(cw/2) columns
  * give the MPCD->LB imposition.
+ *
+ * Near-wall strip (orc_set_strip; the two-level geometry of Sec. 3.3): the
+ * MPCD region spans all columns (periodic in x) and the LB rows [1, y1) next
+ * to the bottom wall, Hy = (y1-1) r; the coupling buffer lies along its top
+ * edge: the outer ceil(cw/2) LB rows below y1 take the redraw, the inner
+ * floor(cw/2) rows under them the imposition.  The top edge is not a wall: a
+ * particle that reaches it is turned back by specular reflection (v_y -> -v_y,
+ * x and z motion kept), and cells cut by it get no virtual particles (they hold
+ * outer-buffer particles only, whose velocities are redrawn before they move).
  */
 #include "oracle.h"
 #include <math.h>
@@ -136,6 +145,7 @@ struct orc_sim {
   long step;                          /* global step counter n */
   /* MPCD */
   int has_region, x0, x1, Wx, Hy, Wz, r, n_out, n_in;
+  int strip, y1;                      /* near-wall strip: rows [1, y1), buffer along y1 */
   long np, cap;                       /* particles, allocated slots */
   int *home;                          /* [np][3] integer home cell */
   double *off, *vel;                  /* [np][3] offsets in [0,1), velocities */
@@ -219,12 +229,28 @@ long orc_step_count(const orc_sim* s) { return s->step; }
 /* Seed the MPCD region: exactly ppc particles in every cell, offsets uniform
  * in the cell (24-bit Philox uniforms), velocities Maxwellian with variance
  * kT/m per component and zero mean (Box-Muller). */
+static int setup_region(orc_sim* s, int x0, int x1, int strip, int y1);
 int orc_set_region(orc_sim* s, int x0, int x1) {
   const orc_params* p = &s->p;
+  if (x0 < 0 || x1 > p->nx || x1 - x0 < 2 * p->coupling_width || p->coupling_width < 0) return -1;
+  return setup_region(s, x0, x1, 0, p->ny - 1);
+}
+
+/* the near-wall strip: all columns, LB rows [1, y1), buffer rows below y1;
+ * needs interior rows under the buffer and y1 below the top wall */
+int orc_set_strip(orc_sim* s, int y1) {
+  const orc_params* p = &s->p;
+  if (p->coupling_width < 0 || y1 - 1 <= p->coupling_width || y1 >= p->ny - 1) return -1;
+  if (p->feedback == 2 || p->resample_density) return -1;
+  return setup_region(s, 0, p->nx, 1, y1);
+}
+
+static int setup_region(orc_sim* s, int x0, int x1, int strip, int y1) {
+  const orc_params* p = &s->p;
   int cw = p->coupling_width;
-  if (x0 < 0 || x1 > p->nx || x1 - x0 < 2 * cw || cw < 0) return -1;
   s->has_region = 1; s->x0 = x0; s->x1 = x1; s->r = p->refine;
-  s->Wx = (x1 - x0) * s->r; s->Hy = (p->ny - 2) * s->r; s->Wz = s->dim == 3 ? p->nz * s->r : 1;
+  s->strip = strip; s->y1 = y1;
+  s->Wx = (x1 - x0) * s->r; s->Hy = (y1 - 1) * s->r; s->Wz = s->dim == 3 ? p->nz * s->r : 1;
   s->n_out = (cw + 1) / 2; s->n_in = cw / 2;
   long ncell_home = (long)s->Wx * s->Hy * s->Wz;
   s->np = ncell_home * p->ppc;
@@ -241,7 +267,7 @@ int orc_set_region(orc_sim* s, int x0, int x1) {
   s->vcm = (double*)calloc(3 * s->ncell, sizeof(double));
   s->vran = (double*)calloc(3 * s->cap, sizeof(double));
   s->ranm = (double*)calloc(3 * s->ncell, sizeof(double));
-  s->nbuf = 2L * s->n_in * (p->ny - 2) * p->nz;
+  s->nbuf = strip ? (long)s->n_in * p->nx * p->nz : 2L * s->n_in * (p->ny - 2) * p->nz;
   int W = p->window > 0 ? p->window : 1;
   s->frames = (double*)calloc((size_t)W * (s->nbuf > 0 ? s->nbuf : 1) * 4, sizeof(double));
   s->wmean = (double*)calloc((size_t)(s->nbuf > 0 ? s->nbuf : 1) * 4, sizeof(double));
@@ -370,13 +396,23 @@ static void u_fine(const orc_sim* s, int X, int Y, int Z, double out[3]) {
 }
 
 static int lb_column_of(const orc_sim* s, int X) { return s->x0 + X / s->r; }
-static int in_outer(const orc_sim* s, int X) {
+/* outer buffer: the n_out LB columns at each x-end of the region, or the n_out
+ * LB rows under the top edge of a near-wall strip */
+static int in_outer(const orc_sim* s, int X, int Y) {
+  if (s->strip) return 1 + Y / s->r >= s->y1 - s->n_out;
   int x = lb_column_of(s, X);
   return x < s->x0 + s->n_out || x >= s->x1 - s->n_out;
 }
-/* index of the inner-buffer LB node holding MPCD cell (X,Y,Z), or -1 */
+/* index of the inner-buffer LB node holding MPCD cell (X,Y,Z), or -1.
+ * Strip: b = (row nz + z) nx + x, row counted down from the buffer's top. */
 static long inner_node(const orc_sim* s, int X, int Y, int Z) {
   const orc_params* p = &s->p;
+  if (s->strip) {
+    int y = 1 + Y / s->r;
+    if (y < s->y1 - p->coupling_width || y >= s->y1 - s->n_out) return -1;
+    int row = s->y1 - 1 - s->n_out - y, z = (s->dim == 3) ? Z / s->r : 0;
+    return ((long)row * p->nz + z) * p->nx + X / s->r;
+  }
   int x = lb_column_of(s, X);
   int side, col;
   if (x >= s->x0 + s->n_out && x < s->x0 + p->coupling_width) { side = 0; col = x - s->x0 - s->n_out; }
@@ -412,7 +448,7 @@ static void resample_density(orc_sim* s) {
   const orc_params* p = &s->p;
   long w = 0;
   for (long k = 0; k < s->np; ++k) {
-    if (in_outer(s, s->home[3*k])) continue;
+    if (in_outer(s, s->home[3*k], s->home[3*k+1])) continue;
     for (int a = 0; a < 3; ++a) {
       s->home[3*w+a] = s->home[3*k+a]; s->off[3*w+a] = s->off[3*k+a]; s->vel[3*w+a] = s->vel[3*k+a];
     }
@@ -425,7 +461,7 @@ static void resample_density(orc_sim* s) {
   for (int Z = 0; Z < s->Wz; ++Z)
     for (int Y = 0; Y < s->Hy; ++Y)
       for (int X = 0; X < s->Wx; ++X) {
-        if (!in_outer(s, X)) continue;
+        if (!in_outer(s, X, Y)) continue;
         long c = X + (long)s->Wx * (Y + (long)s->Hy * Z);
         int lx = lb_column_of(s, X), ly = 1 + Y / s->r, lz = s->dim == 3 ? Z / s->r : 0;
         double x = (double)p->ppc * s->rho[nidx(s, lx, ly, lz)];
@@ -461,7 +497,7 @@ static void resample(orc_sim* s) {
   double sig = sqrt(s->p.kT / s->p.mass);
   for (long k = 0; k < s->np; ++k) {
     int X = s->home[3*k], Y = s->home[3*k+1], Z = s->home[3*k+2];
-    if (!in_outer(s, X)) continue;
+    if (!in_outer(s, X, Y)) continue;
     double uf[3]; u_fine(s, X, Y, Z, uf);
     uint32_t w[4]; draw(s, (uint32_t)k, (uint32_t)s->step, TAG_RESAMPLE, w);
     double z0, z1, z2, z3;
@@ -496,9 +532,13 @@ static void stream(orc_sim* s) {
       double L = (ny_ < 0) ? (double)(-h[1]) : (double)(s->Hy - h[1]); /* wall, local units */
       double ts = (L - o[1]) / dy;          /* fraction of the step before the hit */
       double tr = L - (ty - L);             /* mirrored end point */
-      v[0] = -v[0]; v[1] = -v[1]; v[2] = -v[2];
-      dxe = dx * ts - dx * (1.0 - ts);
-      dze = dz * ts - dz * (1.0 - ts);
+      if (s->strip && ny_ >= s->Hy) {       /* top edge of a strip: specular */
+        v[1] = -v[1];
+      } else {
+        v[0] = -v[0]; v[1] = -v[1]; v[2] = -v[2];
+        dxe = dx * ts - dx * (1.0 - ts);
+        dze = dz * ts - dz * (1.0 - ts);
+      }
       int kr = (int)floor(tr);
       h[1] += kr; o[1] = tr - (double)kr;
       if (h[1] >= s->Hy) { h[1] = s->Hy - 1; o[1] = one_minus; }
@@ -603,7 +643,7 @@ static void collide(orc_sim* s) {
     for (int a = 0; a < 3; ++a) s->vcm[3*c+a] = 0.0;
     if (n == 0) continue;
     int cy = (int)((c / s->ncx) % s->ncy);
-    int cut = (cy == 0 || cy == s->Hy) && s->shift[1] > 0.0;
+    int cut = (cy == 0 || (cy == s->Hy && !s->strip)) && s->shift[1] > 0.0;
     double P[3] = {s->sumv[3*c], s->sumv[3*c+1], s->sumv[3*c+2]};
     int ntot = n;
     if (cut && n < p->ppc) {
@@ -669,7 +709,7 @@ static void collide_at(orc_sim* s) {
     for (int a = 0; a < 3; ++a) { s->vcm[3*c+a] = 0.0; s->ranm[3*c+a] = 0.0; }
     if (n == 0) continue;
     int cy = (int)((c / s->ncx) % s->ncy);
-    int cut = (cy == 0 || cy == s->Hy) && s->shift[1] > 0.0;
+    int cut = (cy == 0 || (cy == s->Hy && !s->strip)) && s->shift[1] > 0.0;
     int ntot = n;
     if (cut && n < p->ppc) {
       int nv = p->ppc - n;
@@ -720,10 +760,17 @@ static void impose(orc_sim* s) {
     if (!(p->feedback == 1 && s->step >= 1 && M > 0)) continue;
     /* node coordinates of buffer entry b */
     long t = b;
-    int y = 1 + (int)(t % (p->ny - 2)); t /= (p->ny - 2);
-    int z = (int)(t % p->nz); t /= p->nz;
-    int col = (int)(t % s->n_in); int side = (int)(t / s->n_in);
-    int x = side == 0 ? s->x0 + s->n_out + col : s->x1 - 1 - s->n_out - col;
+    int x, y, z;
+    if (s->strip) {
+      x = (int)(t % p->nx); t /= p->nx;
+      z = (int)(t % p->nz); t /= p->nz;
+      y = s->y1 - 1 - s->n_out - (int)t;
+    } else {
+      y = 1 + (int)(t % (p->ny - 2)); t /= (p->ny - 2);
+      z = (int)(t % p->nz); t /= p->nz;
+      int col = (int)(t % s->n_in), side = (int)(t / s->n_in);
+      x = side == 0 ? s->x0 + s->n_out + col : s->x1 - 1 - s->n_out - col;
+    }
     double feq[19];
     orc_feq(p->lattice, s->rho[nidx(s, x, y, z)], u, feq);
     for (int i = 0; i < s->q; ++i) s->f[i * s->nnode + nidx(s, x, y, z)] = feq[i];

@@ -75,6 +75,8 @@ enum {
 
 orc_sim* orc_create(const orc_params* p, int replica);
 int  orc_set_region(orc_sim* s, int x0, int x1);
+/* near-wall strip (Sec. 3.3): all columns, LB rows [1, y1), coupling buffer along y1 */
+int  orc_set_strip(orc_sim* s, int y1);
 int  orc_step(orc_sim* s, int nsteps);
 long orc_field_size(const orc_sim* s, int field);   /* element count */
 int  orc_get_field(const orc_sim* s, int field, void* dst); /* double or int32 */
