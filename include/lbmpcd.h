@@ -148,12 +148,24 @@ typedef struct {
  * precision), OOM, CUDA.  On failure *out is NULL. */
 int lbmpcd_create(const lbmpcd_params* params, int n_replicas, void* cuda_stream, lbmpcd** out);
 
-/* Declare the MPCD sub-region of a replica: LB columns [lo[0], hi[0]) (half-open).
- * lo[1..2] / hi[1..2] must span the channel (0..ny, 0..nz) -- only slabs of
- * whole columns are supported.  Seeds ppc particles in every MPCD cell with
- * offsets uniform in the cell and Maxwellian velocities (variance kT/m).
- * Must precede the first lbmpcd_step (else ERR_STATE).  Errors: INVALID_ARG
- * (region narrower than 2 coupling widths, cell index range too large), OOM, CUDA. */
+/* Declare the MPCD sub-region of a replica (LB node bounds, half-open).  Two
+ * forms (lo[1] <= 1 and z spanning 0..nz in both):
+ *  - slab of whole columns, hi[1] >= ny - 1: LB columns [lo[0], hi[0]), all
+ *    fluid rows; periodic in x inside the region; coupling buffers of
+ *    coupling_width columns at both x-ends (Sec. 2.3);
+ *  - near-wall strip, hi[1] = y1 < ny - 1 (the two-level geometry of Sec. 3.3):
+ *    all columns (lo[0] = 0, hi[0] = nx, periodic in x) and LB rows [1, y1);
+ *    the coupling buffer lies along the top edge: the outer ceil(cw/2) rows
+ *    below y1 are redrawn from the LB, the inner floor(cw/2) rows under them
+ *    are sampled and (feedback = 1) imposed, WINDOW_MEAN entries ordered
+ *    (row from the buffer's top, z, x).  The top edge is not a wall: particles
+ *    reaching it are reflected specularly (v_y -> -v_y) and its cut cells get
+ *    no virtual particles.  Needs y1 - 1 > coupling_width; not with
+ *    feedback = 2 or resample_density = 1.
+ * Seeds ppc particles in every MPCD cell with offsets uniform in the cell and
+ * Maxwellian velocities (variance kT/m).  Must precede the first lbmpcd_step
+ * (else ERR_STATE).  Errors: INVALID_ARG (bounds of neither form, region
+ * narrower than 2 coupling widths, cell index range too large), OOM, CUDA. */
 int lbmpcd_set_region(lbmpcd* h, int replica, const int lo[3], const int hi[3]);
 
 /* Advance every replica by nsteps coupled time steps (one step = LB

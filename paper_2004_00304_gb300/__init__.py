@@ -315,6 +315,12 @@ class Lbmpcd:
         p = self.params[replica]
         lbmpcd_set_region(self._h, replica, (x0, 0, 0), (x1, p["ny"], p.get("nz", 1)))
 
+    def set_strip(self, replica: int, y1: int):
+        """Near-wall strip (Sec. 3.3): all columns, LB rows [1, y1), coupling
+        buffer along y1."""
+        p = self.params[replica]
+        lbmpcd_set_region(self._h, replica, (0, 0, 0), (p["nx"], y1, p.get("nz", 1)))
+
     def step(self, n: int = 1):
         lbmpcd_step(self._h, n)
 

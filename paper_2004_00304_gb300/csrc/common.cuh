@@ -138,6 +138,9 @@ struct RepDev {
   // coupling columns in cell units: outer X < xo_lo or X >= xo_hi; inner
   // [xi_lo0, xi_hi0) (left side) and [xi_lo1, xi_hi1) (right side)
   int xo_lo, xo_hi, xi_lo0, xi_hi0, xi_lo1, xi_hi1;
+  // near-wall strip (Sec. 3.3): region = all columns x LB rows [1, y1); outer
+  // buffer rows Y >= yo (Hy when there is no strip), inner rows [yi_lo, yi_hi)
+  int strip, y1, yo, yi_lo, yi_hi;
   // density resampling: particles live in a pool of cap slots; pool[0] is
   // its end, pool[1] an overflow flag, pool[2] the live count of the last
   // sort or compaction; ltile scratch of the readout compaction

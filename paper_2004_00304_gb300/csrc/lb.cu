@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(128) lb_pull_tma(const RepDev* __restrict__ re
           d[i][0] = c.y; d[i][1] = c.z; d[i][2] = c.w; d[i][3] = seg[4];
         }
       }
-      lb_finish<9, float, 4>(rd, st, d, x0 + xl, rd.nx * y);
+      lb_finish<9, float, 4>(rd, st, d, x0 + xl, rd.nx * y, y);
     }
     __syncthreads();   // every thread is done with stage s
     if (tid == 0) {

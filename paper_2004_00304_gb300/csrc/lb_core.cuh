@@ -72,7 +72,7 @@ __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 // post-collision values go to the other buffer, rho / u where requested.
 template <int Q, typename S, int V>
 __device__ __forceinline__ void lb_finish(const RepDev& rd, const StepInfo& st, typename Store<S>::R (&d)[Q][V],
-                                          int x0, int row) {
+                                          int x0, int row, int y) {
   using L = Lattice<Q>;
   using R = typename Store<S>::R;
   const int nx = rd.nx;
@@ -129,12 +129,13 @@ __device__ __forceinline__ void lb_finish(const RepDev& rd, const StepInfo& st, 
     Row<S, V>::st(dst + i * N + row + x0, d[i], scale, hb ? (mix32(hb + 0x27D4EB2Fu * (uint32_t)i) | 1u) : 0u);
 
   // rho, u: every node on request; otherwise the columns the coupling reads
-  // (x0-1 .. x0+cw and x1-cw-1 .. x1, periodic in x).
+  // (x0-1 .. x0+cw and x1-cw-1 .. x1, periodic in x), or for a near-wall strip
+  // the rows y1-cw-1 .. y1.
 #pragma unroll
   for (int v = 0; v < V; ++v) {
     const int x = x0 + v;
-    bool want = st.write_moments;
-    if (!want && rd.has_region) {
+    bool want = st.write_moments || (rd.strip && y >= rd.y1 - rd.cw - 1 && y <= rd.y1);
+    if (!want && rd.has_region && !rd.strip) {
       int da = x - (rd.x0 - 1), db = x - (rd.x1 - rd.cw - 1);
       da = da < 0 ? da + nx : (da >= nx ? da - nx : da);
       db = db < 0 ? db + nx : (db >= nx ? db - nx : db);
@@ -221,7 +222,7 @@ __device__ __forceinline__ void lb_row(const RepDev& rd, const StepInfo& st, con
     }
   }
   if (!active) return;
-  lb_finish<Q, S, V>(rd, st, d, x0, row);
+  lb_finish<Q, S, V>(rd, st, d, x0, row, y);
 }
 
 }  // namespace lbm

@@ -325,12 +325,25 @@ extern "C" int lbmpcd_set_region(lbmpcd* h, int replica, const int lo[3], const 
   const lbmpcd_params& p = h->P[replica];
   if (d.has_region) return fail(h, LBMPCD_ERR_STATE, "region already set for this replica");
   const int x0 = lo[0], x1 = hi[0];
-  if (!(lo[1] <= 1 && hi[1] >= p.ny - 1 && lo[2] <= 0 && hi[2] >= p.nz))
-    return fail(h, LBMPCD_ERR_INVALID_ARG, "region must span all fluid rows and all z (slab of whole columns)");
-  if (x0 < 0 || x1 > p.nx || x1 - x0 < 2 * p.coupling_width || x1 <= x0)
+  if (!(lo[1] <= 1 && lo[2] <= 0 && hi[2] >= p.nz))
+    return fail(h, LBMPCD_ERR_INVALID_ARG, "region must start at the bottom wall and span all z");
+  // hi[1] below the top wall: the near-wall strip of Sec. 3.3 (all columns,
+  // LB rows [1, hi[1]), coupling buffer along its top edge)
+  const bool strip = hi[1] < p.ny - 1;
+  const int y1 = strip ? hi[1] : p.ny - 1;
+  if (strip) {
+    if (x0 != 0 || x1 != p.nx)
+      return fail(h, LBMPCD_ERR_INVALID_ARG, "a near-wall strip spans all columns");
+    if (y1 - 1 <= p.coupling_width)
+      return fail(h, LBMPCD_ERR_INVALID_ARG, "near-wall strip not taller than its coupling buffer");
+    if (p.feedback == 2 || p.resample_density)
+      return fail(h, LBMPCD_ERR_INVALID_ARG, "a near-wall strip runs neither the learned closure nor density resampling");
+  } else if (x0 < 0 || x1 > p.nx || x1 - x0 < 2 * p.coupling_width || x1 <= x0) {
     return fail(h, LBMPCD_ERR_INVALID_ARG, "region columns out of range or narrower than two coupling widths");
+  }
   d.x0 = x0; d.x1 = x1;
-  d.Wx = (x1 - x0) * p.refine; d.Hy = (p.ny - 2) * p.refine; d.Wz = h->dim == 3 ? p.nz * p.refine : 1;
+  d.strip = strip ? 1 : 0; d.y1 = y1;
+  d.Wx = (x1 - x0) * p.refine; d.Hy = (y1 - 1) * p.refine; d.Wz = h->dim == 3 ? p.nz * p.refine : 1;
   const bool fits = h->dim == 2 ? (d.Wx <= HomePack<2>::XMAX && d.Hy <= HomePack<2>::YMAX)
                                 : (d.Wx <= HomePack<3>::XMAX + 1 && d.Hy <= HomePack<3>::YMAX + 1 &&
                                    d.Wz <= HomePack<3>::ZMAX + 1);
@@ -340,9 +353,18 @@ extern "C" int lbmpcd_set_region(lbmpcd* h, int replica, const int lo[3], const 
   d.np = d.nhome * p.ppc;
   {
     const int r = p.refine, w = x1 - x0;
-    d.xo_lo = d.n_out * r; d.xo_hi = (w - d.n_out) * r;
-    d.xi_lo0 = d.n_out * r; d.xi_hi0 = p.coupling_width * r;
-    d.xi_lo1 = (w - p.coupling_width) * r; d.xi_hi1 = (w - d.n_out) * r;
+    if (strip) {   // buffer rows under the top edge; no buffer columns
+      d.xo_lo = 0; d.xo_hi = d.Wx;
+      d.xi_lo0 = d.xi_hi0 = d.xi_lo1 = d.xi_hi1 = 0;
+      d.yo = d.Hy - d.n_out * r;
+      d.yi_lo = d.Hy - p.coupling_width * r; d.yi_hi = d.yo;
+    } else {
+      d.xo_lo = d.n_out * r; d.xo_hi = (w - d.n_out) * r;
+      d.xi_lo0 = d.n_out * r; d.xi_hi0 = p.coupling_width * r;
+      d.xi_lo1 = (w - p.coupling_width) * r; d.xi_hi1 = (w - d.n_out) * r;
+      d.yo = d.Hy;
+      d.yi_lo = d.yi_hi = 0;
+    }
   }
   if (d.np >= (1LL << 32) - 1) return fail(h, LBMPCD_ERR_INVALID_ARG, "too many particles");
   // density resampling: a pool with room for KCHUNK + 1 steps of new particles
@@ -360,7 +382,7 @@ extern "C" int lbmpcd_set_region(lbmpcd* h, int replica, const int lo[3], const 
                 "learned closure needs >= 32 fine columns, >= 16 fine rows, refine in {1, 2, 4, 8} and "
                 "coupling_width * refine <= 16");
   d.ncell = (long long)d.Wx * (d.Hy + 1) * d.Wz;
-  d.nbuf = 2LL * d.n_in * (p.ny - 2) * p.nz;
+  d.nbuf = strip ? (long long)d.n_in * p.nx * p.nz : 2LL * d.n_in * (p.ny - 2) * p.nz;
   const size_t rs = real_size(h->prec);
   std::vector<void*>& L = h->rep_allocs[replica];
   void* t = nullptr;

@@ -232,12 +232,16 @@ __device__ __forceinline__ void stream(const RepDev& rd, int& X, int& Y, int& Z,
   R dxe = dx, dze = dz;
   if (nyc < 0 || nyc >= rd.Hy) {
     const R Lw = (nyc < 0) ? (R)(-Y) : (R)(rd.Hy - Y);   // wall, local units
-    const R ts = (Lw - o[1]) / dy;                       // fraction before the hit
     const R tr = xsub(Lw, xsub(ty, Lw));                 // mirrored end point
+    if (rd.strip && nyc >= rd.Hy) {                      // top edge of a near-wall strip: specular
+      v[1] = -v[1];
+    } else {
+      const R ts = (Lw - o[1]) / dy;                     // fraction before the hit
 #pragma unroll
-    for (int a = 0; a < D; ++a) v[a] = -v[a];
-    dxe = xsub(xmul(dx, ts), xmul(dx, xsub(R(1), ts)));
-    dze = xsub(xmul(dz, ts), xmul(dz, xsub(R(1), ts)));
+      for (int a = 0; a < D; ++a) v[a] = -v[a];
+      dxe = xsub(xmul(dx, ts), xmul(dx, xsub(R(1), ts)));
+      dze = xsub(xmul(dz, ts), xmul(dz, xsub(R(1), ts)));
+    }
     const int kr = (int)floor(tr);
     Y += kr;
     o[1] = xsub(tr, (R)kr);
@@ -361,7 +365,7 @@ __device__ __forceinline__ void particle_item(const RepDev& rd, const StepInfo& 
     const uint32_t j = j0 + 256u * p;
     cid[p] = 0xFFFFFFFFu;
     if (!act[p]) continue;
-    const bool outer = X[p] < rd.xo_lo || X[p] >= rd.xo_hi;
+    const bool outer = X[p] < rd.xo_lo || X[p] >= rd.xo_hi || Y[p] >= rd.yo;
     if (RS && rd.resample && outer && !fresh[p]) {   // a3': replaced by this step's spawn
       rd.home[j] = HOME_DEAD;
       act[p] = false;
@@ -386,11 +390,18 @@ __device__ __forceinline__ void particle_item(const RepDev& rd, const StepInfo& 
     stream<D, R>(rd, X[p], Y[p], Z[p], o[p], v[p]);
     // a6: inner-buffer sample (unshifted cells), binary64 atomics
     const bool left = X[p] >= rd.xi_lo0 && X[p] < rd.xi_hi0, right = X[p] >= rd.xi_lo1 && X[p] < rd.xi_hi1;
-    if (left || right) {
+    const bool row_in = Y[p] >= rd.yi_lo && Y[p] < rd.yi_hi;   // inner rows of a near-wall strip
+    if (left || right || row_in) {
       const int xn = X[p] / rd.r, wcols = rd.x1 - rd.x0;
-      const int col = left ? xn - rd.n_out : wcols - 1 - rd.n_out - xn;
       const int zl = (D == 3) ? Z[p] / rd.r : 0;
-      const long long b = (((long long)(right ? 1 : 0) * rd.n_in + col) * rd.nz + zl) * (rd.ny - 2) + Y[p] / rd.r;
+      long long b;
+      if (row_in) {   // b = (row nz + z) nx + x, row counted down from the buffer's top
+        const int row = rd.y1 - 2 - rd.n_out - Y[p] / rd.r;
+        b = ((long long)row * rd.nz + zl) * rd.nx + xn;
+      } else {
+        const int col = left ? xn - rd.n_out : wcols - 1 - rd.n_out - xn;
+        b = (((long long)(right ? 1 : 0) * rd.n_in + col) * rd.nz + zl) * (rd.ny - 2) + Y[p] / rd.r;
+      }
       double* fr = rd.frame + 4 * b;
       atomicAdd(fr, rd.mass);
 #pragma unroll
@@ -665,7 +676,7 @@ __device__ __forceinline__ void cell_item(const RepDev& rd, const StepInfo& st, 
       if (n > 0) {
         const uint32_t ci = (uint32_t)c, row = ci / (uint32_t)rd.Wx;
         const uint32_t cy = D == 2 ? row : row % (uint32_t)(rd.Hy + 1);
-        const bool cut = (cy == 0 || cy == (uint32_t)rd.Hy) && st.shift_f[1] > 0.0f;
+        const bool cut = (cy == 0 || (cy == (uint32_t)rd.Hy && !rd.strip)) && st.shift_f[1] > 0.0f;
         if (cut && (int)n < rd.ppc) {
           // Lamura-type wall: ppc - n virtual particles at rest, summed momentum
           // drawn from N(0, (ppc - n) m kT) per component.  MPCD-AT: they are
@@ -765,10 +776,17 @@ __device__ __forceinline__ void cell_item(const RepDev& rd, const StepInfo& st, 
   wm[0] = (double)rho; wm[1] = (double)u[0]; wm[2] = (double)u[1]; wm[3] = (double)u[2];
   if (!(rd.feedback == 1 && st.n >= 1 && M > R(0))) return;
   long long t = b;
-  const int y = 1 + (int)(t % (rd.ny - 2)); t /= (rd.ny - 2);
-  const int z = (int)(t % rd.nz); t /= rd.nz;
-  const int col = (int)(t % rd.n_in), side = (int)(t / rd.n_in);
-  const int x = side == 0 ? rd.x0 + rd.n_out + col : rd.x1 - 1 - rd.n_out - col;
+  int x, y, z;
+  if (rd.strip) {
+    x = (int)(t % rd.nx); t /= rd.nx;
+    z = (int)(t % rd.nz); t /= rd.nz;
+    y = rd.y1 - 1 - rd.n_out - (int)t;
+  } else {
+    y = 1 + (int)(t % (rd.ny - 2)); t /= (rd.ny - 2);
+    z = (int)(t % rd.nz); t /= rd.nz;
+    const int col = (int)(t % rd.n_in), side = (int)(t / rd.n_in);
+    x = side == 0 ? rd.x0 + rd.n_out + col : rd.x1 - 1 - rd.n_out - col;
+  }
   S* dst = (S*)rd.f[(st.n & 1) ^ 1];
   const long long node = x + (long long)rd.nx * (y + (long long)rd.ny * z);
   // equilibrium at the node's own LB density (this step's moment) and the

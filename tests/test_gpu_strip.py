@@ -1,0 +1,126 @@
+"""The near-wall strip (Sec. 3.3 geometry: MPCD on all columns and the LB
+rows [1, y1) at the bottom wall, coupling buffer along its top edge) on the
+GPU: parity with the FP64 oracle (single steps 2D/3D, SRD and MPCD-AT,
+sorted chunks, FP32), and the near-wall Poiseuille profile of Sec. 3.3 at
+Table 1 row 3's a = 1/2 and kT from Eq. 7, in binary32."""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import transport as T
+from tests import inputs
+from tests.test_gpu_parity import FLOOR, ambiguous_particles, lb, rel_err  # noqa: F401
+
+pytestmark = pytest.mark.gpu
+
+
+def _pair(lb, cfg, y1):
+    g = lb.Lbmpcd(cfg["params"])
+    g.set_strip(0, y1)
+    o = O.OracleSim(cfg["params"])
+    o.set_strip(y1)
+    return g, o
+
+
+@pytest.mark.parametrize("case", ["2d", "3d", "2d_at", "2d_r1_oneway", "3d_at"])
+def test_strip_step_parity_fp64(lb, case):
+    over = dict(precision=0)
+    if "at" in case:
+        over["collision"] = 1
+    if "r1" in case:
+        over.update(refine=1, feedback=0)
+    cfg = inputs.small_3d(**over) if case.startswith("3d") else inputs.small_2d(**over)
+    y1 = 6 if case.startswith("3d") else 9
+    g, o = _pair(lb, cfg, y1)
+    for n in (1, 1, 3):
+        g.step(n)
+        o.step(n)
+        assert np.array_equal(g.get("SHIFT"), o.get("SHIFT"))
+        assert np.array_equal(g.get("PART_HOME"), o.get("PART_HOME"))
+        assert np.array_equal(g.get("PART_CELL"), o.get("PART_CELL"))
+        assert np.array_equal(g.get("CELL_COUNT"), o.get("CELL_COUNT"))
+        for f in ("PART_POS", "PART_VEL", "CELL_VCM", "WINDOW_MEAN", "POPS", "RHO", "U"):
+            e = rel_err(g.get(f), o.get(f), FLOOR.get(f, 0.0))
+            assert e <= 1e-12, (f, e)
+        np.testing.assert_allclose(g.get("DIAG"), o.get("DIAG"), rtol=1e-12, atol=1e-13)
+    g.close()
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_strip_run_with_sorting_fp64(lb, dim):
+    cfg = inputs.small_2d(precision=0) if dim == 2 else inputs.small_3d(precision=0)
+    g, o = _pair(lb, cfg, 8 if dim == 2 else 6)
+    g.step(150)
+    o.step(150)
+    assert np.array_equal(g.get("PART_HOME"), o.get("PART_HOME"))
+    for f in ("PART_POS", "PART_VEL", "CELL_VCM", "WINDOW_MEAN", "POPS", "U"):
+        e = rel_err(g.get(f), o.get(f), FLOOR.get(f, 0.0))
+        assert e <= 1e-12, (f, e)
+    g.close()
+
+
+def test_strip_step_parity_fp32(lb):
+    cfg = inputs.small_2d(precision=1)
+    g, o = _pair(lb, cfg, 9)
+    for n in (1, 2):
+        g.step(n)
+        o.step(n)
+        amb = ambiguous_particles(o, 2, 1e-5)
+        cells_o, cells_g = o.get("PART_CELL"), g.get("PART_CELL")
+        bad = set(cells_o[amb]) | set(cells_g[amb])
+        ok = ~np.isin(cells_o, list(bad)) & ~amb
+        assert ok.mean() > 0.9
+        assert np.array_equal(cells_g[ok], cells_o[ok])
+        assert rel_err(g.get("PART_VEL").reshape(-1, 3)[ok], o.get("PART_VEL").reshape(-1, 3)[ok]) <= 1e-5
+        for f in ("POPS", "RHO", "U"):
+            assert rel_err(g.get(f), o.get(f), FLOOR.get(f, 0.0)) <= 1e-5, f
+    g.close()
+
+
+def test_strip_arguments(lb):
+    p = inputs.small_2d()["params"]
+    g = lb.Lbmpcd(p)
+    with pytest.raises(lb.LbmpcdError):
+        lb.lbmpcd_set_region(g._h, 0, (2, 0, 0), (p["nx"], 9, 1))      # not all columns
+    with pytest.raises(lb.LbmpcdError):
+        g.set_strip(0, 3)                                              # not taller than the buffer
+    g.close()
+    g = lb.Lbmpcd(inputs.small_2d(feedback=2)["params"])
+    with pytest.raises(lb.LbmpcdError):
+        g.set_strip(0, 9)
+    g.close()
+
+
+def test_near_wall_poiseuille_fp32(lb):
+    """Sec. 3.3 with Table 1 row 3's resolution: LB 20 x 32 (nu = 0.167,
+    tau = 1.0), MPCD-AT strip of 7 LB rows at a = 1/2 (14 fine rows), 1000
+    particles per cell, kT from Eq. 7 (0.29, Table 1's ~0.3), one-way coupled;
+    g = 1e-4 (Table 1's 5e-4 would put the LB centreline at Mach 0.6).  LB
+    started on the steady profile; the strip's profile, averaged over 2000
+    steps after 500, follows the analytic parabola within 2% L2."""
+    nx, ny, y1, r, ppc, g_, nu = 20, 32, 8, 2, 1000, 1e-4, 0.167
+    kT = T.at_kT_for_viscosity(nu, ppc, 1.0 / r)
+    assert abs(kT - 0.29) < 0.01
+    p = dict(lattice=9, nx=nx, ny=ny, nz=1, tau=0.5 + 3 * nu, force=(g_, 0, 0), refine=r, ppc=ppc, alpha=0.0,
+             kT=kT, mass=1.0, coupling_width=2, precision=1, feedback=0, window=1, seed=7, collision=1)
+    sim = lb.Lbmpcd(p)
+    sim.set_strip(0, y1)
+    yc = np.arange(ny) + 0.5
+    u = np.where((yc > 1) & (yc < ny - 1), g_ * (yc - 1) * (ny - 1 - yc) / (2 * nu), 0.0)
+    f = np.stack([O.feq(9, 1.0, [ui, 0.0, 0.0]) for ui in u])
+    sim.set("POPS", np.repeat(f.T[:, :, None], nx, axis=2).ravel())
+    sim.step(500)
+    Hs = (y1 - 1) * r
+    mom, cnt = np.zeros(Hs), np.zeros(Hs)
+    for _ in range(200):
+        sim.step(10)
+        h = sim.get("PART_HOME").reshape(-1, 3)
+        v = sim.get("PART_VEL").reshape(-1, 3)
+        mom += np.bincount(h[:, 1], weights=v[:, 0], minlength=Hs)
+        cnt += np.bincount(h[:, 1], minlength=Hs)
+    y = 1.0 + (np.arange(Hs) + 0.5) / r
+    ua = g_ * (y - 1) * (ny - 1 - y) / (2 * nu)
+    err = np.linalg.norm(mom / cnt - ua) / np.linalg.norm(ua)
+    print(f"near-wall strip, a = 1/2, N = 1000: rel. L2 against the analytic profile {err:.4f}")
+    assert err < 0.02
+    sim.close()
