@@ -25,7 +25,7 @@ _lib = None
 
 FIELDS = dict(RHO=0, U=1, POPS=2, PART_POS=3, PART_VEL=4, PART_CELL=5, SHIFT=6,
               CELL_COUNT=7, WINDOW_MEAN=8, DIAG=9, PART_HOME=10, CELL_VCM=11, PART_ID=12,
-              CLOSURE_IN=13, CLOSURE_TARGET=15)
+              CLOSURE_IN=13, CLOSURE_TARGET=15, PI=16)
 _INT_FIELDS = {"PART_CELL", "CELL_COUNT", "PART_HOME", "PART_ID"}
 
 
@@ -50,7 +50,7 @@ class Params(ctypes.Structure):
                 ("coupling_width", ctypes.c_int), ("precision", ctypes.c_int),
                 ("feedback", ctypes.c_int), ("window", ctypes.c_int),
                 ("resample_density", ctypes.c_int), ("seed", ctypes.c_uint64),
-                ("collision", ctypes.c_int)]
+                ("collision", ctypes.c_int), ("redraw", ctypes.c_int)]
 
 
 def lib():
@@ -110,6 +110,7 @@ def make_params(d: dict) -> Params:
     p.resample_density = int(d.get("resample_density", 0))
     p.seed = int(d.get("seed", 1))
     p.collision = int(d.get("collision", 0))
+    p.redraw = int(d.get("redraw", 0))
     return p
 
 

@@ -45,6 +45,8 @@
 #define TAG_SPAWN_VEL 10u
 #define TAG_AT 11u
 #define TAG_AT_VIRT 12u
+#define TAG_CE 13u       /* attempt k uses tag TAG_CE + 16 k (and TAG_CE + 1 + 16 k in 3D) */
+#define CE_TRIES 64
 #define SPAWN_MAX 4     /* at most SPAWN_MAX * ppc new particles per cell and step */
 
 static const double PI = 3.14159265358979323846;
@@ -142,6 +144,7 @@ struct orc_sim {
   int c[19*3]; double w[19]; int opp[19];
   long nnode;
   double *f, *fn, *rho, *u;          /* f[q][nz][ny][nx]; u[3][...] */
+  double *pi;                         /* redraw = 1: [6][nz][ny][nx] traceless pi' (xx yy zz xy xz yz) */
   long step;                          /* global step counter n */
   /* MPCD */
   int has_region, x0, x1, Wx, Hy, Wz, r, n_out, n_in;
@@ -192,6 +195,7 @@ orc_sim* orc_create(const orc_params* p, int replica) {
     return NULL;
   /* MPCD-AT draws by particle index, which density resampling renumbers */
   if (p->collision < 0 || p->collision > 1 || (p->collision == 1 && p->resample_density)) return NULL;
+  if (p->redraw < 0 || p->redraw > 1 || (p->redraw == 1 && p->resample_density)) return NULL;
   orc_sim* s = (orc_sim*)calloc(1, sizeof(orc_sim));
   s->p = *p; s->replica = replica;
   s->dim = p->lattice == 9 ? 2 : 3;
@@ -205,6 +209,7 @@ orc_sim* orc_create(const orc_params* p, int replica) {
   s->fn = (double*)malloc(sizeof(double) * s->q * s->nnode);
   s->rho = (double*)malloc(sizeof(double) * s->nnode);
   s->u = (double*)calloc(3 * s->nnode, sizeof(double));
+  s->pi = (double*)calloc(6 * s->nnode, sizeof(double));
   /* initial state: f = f_eq(rho0 = 1, u = 0) everywhere (walls included). */
   double feq[19], zero[3] = {0, 0, 0};
   orc_feq(p->lattice, 1.0, zero, feq);
@@ -216,7 +221,7 @@ orc_sim* orc_create(const orc_params* p, int replica) {
 
 void orc_destroy(orc_sim* s) {
   if (!s) return;
-  free(s->f); free(s->fn); free(s->rho); free(s->u);
+  free(s->f); free(s->fn); free(s->rho); free(s->u); free(s->pi);
   free(s->home); free(s->off); free(s->vel); free(s->pcell);
   free(s->cnt); free(s->sumv); free(s->vcm); free(s->vran); free(s->ranm); free(s->frames); free(s->wmean);
   free(s->cl_frame); free(s->cl_hist); free(s->cl_ema); free(s->cl_x);
@@ -351,6 +356,21 @@ static void lb_step(orc_sim* s) {
         }
         s->rho[here] = rho;
         s->u[here] = u[0]; s->u[s->nnode + here] = u[1]; s->u[2*s->nnode + here] = u[2];
+        if (p->redraw == 1) {
+          /* pi = (1 - 1/(2 tau)) Pi_neq / rho, Pi_neq = sum_i (f_i - f_i^eq) c_i c_i of the
+             populations after streaming; its traceless part over the MPCD dimensions */
+          const int ab[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+          double pv[6];
+          for (int m = 0; m < 6; ++m) {
+            double acc = 0;
+            for (int i = 0; i < s->q; ++i) acc += (fi[i] - feq[i]) * s->c[3*i+ab[m][0]] * s->c[3*i+ab[m][1]];
+            pv[m] = (1.0 - 1.0 / (2.0 * tau)) * acc / rho;
+          }
+          double tr = (pv[0] + pv[1] + (s->dim == 3 ? pv[2] : 0.0)) / s->dim;
+          pv[0] -= tr; pv[1] -= tr;
+          if (s->dim == 3) pv[2] -= tr; else { pv[2] = pv[4] = pv[5] = 0.0; }
+          for (int m = 0; m < 6; ++m) s->pi[m * s->nnode + here] = pv[m];
+        }
       }
   double* t = s->f; s->f = s->fn; s->fn = t;
   /* keep the (unused) wall rows identical in both buffers */
@@ -491,14 +511,61 @@ static void resample_density(orc_sim* s) {
       }
 }
 
+/* a3 with the Chapman-Enskog distribution (redraw = 1; Sec. 2.3 names Enskog
+ * sampling for flows whose gradients the Maxwellian redraw misses).  The new
+ * peculiar velocity C = v - u_fine follows f_MB(C; kT/m) (1 + b : zz), z = C /
+ * sqrt(kT/m), b = pi' / (2 kT/m), pi' the traceless non-equilibrium momentum
+ * flux of the LB node holding the cell, so that <C C> = (kT/m) I + pi'.  It is
+ * drawn by acceptance-rejection: attempt t takes z from the Box-Muller normals
+ * of Philox(id, n, replica, TAG_CE + 16 t) (3D: z0, z1 from words 0, 1 and z2
+ * from words 2, 3) and U = (w >> 8) 2^-24 of word 2 (3D: word 0 of
+ * Philox(id, n, replica, TAG_CE + 1 + 16 t)), and is accepted when
+ * A U <= 1 + b : zz with A = 1 + 30 max |b_ab|; after CE_TRIES rejections the
+ * last candidate is kept. */
+static void ce_peculiar(const orc_sim* s, uint32_t id, long node, double sig, double C[3]) {
+  const int ab[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+  double b[3][3] = {{0}}, bmax = 0.0;
+  for (int m = 0; m < 6; ++m) {
+    double v = s->pi[m * s->nnode + node] / (2.0 * sig * sig);
+    b[ab[m][0]][ab[m][1]] = v; b[ab[m][1]][ab[m][0]] = v;
+    if (fabs(v) > bmax) bmax = fabs(v);
+  }
+  double A = 1.0 + 30.0 * bmax, z[3] = {0, 0, 0};
+  for (int t = 0; t < CE_TRIES; ++t) {
+    uint32_t w[4]; draw(s, id, (uint32_t)s->step, TAG_CE + 16u * (uint32_t)t, w);
+    double z3, U;
+    orc_box_muller(w[0], w[1], &z[0], &z[1]);
+    if (s->dim == 3) {
+      orc_box_muller(w[2], w[3], &z[2], &z3);
+      uint32_t w2[4]; draw(s, id, (uint32_t)s->step, TAG_CE + 1u + 16u * (uint32_t)t, w2);
+      U = u24(w2[0]);
+    } else {
+      z[2] = 0.0;
+      U = u24(w[2]);
+    }
+    double q = 0.0;
+    for (int a = 0; a < s->dim; ++a)
+      for (int c = 0; c < s->dim; ++c) q += b[a][c] * z[a] * z[c];
+    if (A * U <= 1.0 + q) break;
+  }
+  for (int a = 0; a < 3; ++a) C[a] = sig * z[a];
+}
+
 /* a3 (Sec. 2.3, Algorithm 1): particles whose home cell is in an outer buffer
- * column get v = u_fine + sqrt(kT/m) xi, xi ~ N(0, I) by Box-Muller. */
+ * column get v = u_fine + sqrt(kT/m) xi, xi ~ N(0, I) by Box-Muller (or the
+ * Chapman-Enskog draw above with redraw = 1). */
 static void resample(orc_sim* s) {
   double sig = sqrt(s->p.kT / s->p.mass);
   for (long k = 0; k < s->np; ++k) {
     int X = s->home[3*k], Y = s->home[3*k+1], Z = s->home[3*k+2];
     if (!in_outer(s, X, Y)) continue;
     double uf[3]; u_fine(s, X, Y, Z, uf);
+    if (s->p.redraw == 1) {
+      long node = nidx(s, lb_column_of(s, X), 1 + Y / s->r, (s->dim == 3) ? Z / s->r : 0);
+      double C[3]; ce_peculiar(s, (uint32_t)k, node, sig, C);
+      for (int a = 0; a < 3; ++a) s->vel[3*k+a] = (a < s->dim) ? uf[a] + C[a] : 0.0;
+      continue;
+    }
     uint32_t w[4]; draw(s, (uint32_t)k, (uint32_t)s->step, TAG_RESAMPLE, w);
     double z0, z1, z2, z3;
     orc_box_muller(w[0], w[1], &z0, &z1);
@@ -916,6 +983,7 @@ long orc_field_size(const orc_sim* s, int field) {
     case ORC_DIAG: return 9;
     case ORC_CLOSURE_IN: return s->cl_on ? 2L * s->cl_npy * CL_W * CL_W * 3 * CL_FRAMES : -1;
     case ORC_CLOSURE_TARGET: return s->cl_on ? 2L * s->cl_npy * CL_W * CL_W * 3 : -1;
+    case ORC_PI: return 6 * s->nnode;
   }
   return -1;
 }
@@ -960,6 +1028,7 @@ int orc_get_field(const orc_sim* s, int field, void* dst) {
       else memcpy(D, s->vcm, sizeof(double) * n);
       break;
     case ORC_WINDOW_MEAN: memcpy(D, s->wmean, sizeof(double) * n); break;
+    case ORC_PI: memcpy(D, s->pi, sizeof(double) * n); break;
     case ORC_DIAG: diag(s, D); break;
     case ORC_CLOSURE_IN: memcpy(D, s->cl_x, sizeof(double) * n); break;
     case ORC_CLOSURE_TARGET:

@@ -58,6 +58,8 @@ typedef struct {
                            particles replaced, their number drawn from the LB density */
   uint64_t seed;
   int collision;        /* 0: SRD (Eq. 4); 1: MPCD with the Andersen thermostat (MPCD-AT, Eq. 6) */
+  int redraw;           /* 0: Maxwellian redraw (Algorithm 1); 1: Chapman-Enskog redraw carrying the
+                           LB's non-equilibrium momentum flux (the Enskog sampling of Sec. 2.3) */
 } orc_params;
 
 typedef struct orc_sim orc_sim;
@@ -70,7 +72,9 @@ enum {
   ORC_CELL_VCM = 11,        /* [ncell][3] SRD: v_cm; MPCD-AT: v_cm minus the cell's mean random velocity */
   ORC_PART_ID = 12,
   ORC_CLOSURE_IN = 13,      /* [P][16][16][24] network input of the last step */
-  ORC_CLOSURE_TARGET = 15   /* [P][16][16][3] moving averages, patch layout */
+  ORC_CLOSURE_TARGET = 15,  /* [P][16][16][3] moving averages, patch layout */
+  ORC_PI = 16               /* [6][nz][ny][nx] traceless kinematic non-equilibrium momentum flux
+                               (xx, yy, zz, xy, xz, yz) of the last LB step (redraw = 1) */
 };
 
 orc_sim* orc_create(const orc_params* p, int replica);
