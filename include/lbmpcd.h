@@ -115,7 +115,23 @@ typedef struct {
   int collision;        /* 0: SRD, stochastic rotation (Eq. 4); 1: MPCD-AT, Andersen thermostat
                            (Eq. 6, the rule the paper's runs use; see below).  All replicas of a
                            handle share it; 1 excludes resample_density = 1 */
+  int redraw;           /* 0: Maxwellian redraw of the outer buffer (Algorithm 1); 1: Chapman-Enskog
+                           redraw carrying the LB's non-equilibrium momentum flux (the Enskog
+                           sampling Sec. 2.3 names for strong gradients; see below).  1 excludes
+                           resample_density = 1 and LBMPCD_FP16DEV */
 } lbmpcd_params;
+
+/* Chapman-Enskog redraw (redraw = 1): the peculiar velocity C = v - u_fine of a
+ * redrawn particle follows f_MB(C; kT/m) (1 + b : zz), z = C / sqrt(kT/m),
+ * b = pi' / (2 kT/m), where pi' is the traceless part (over the MPCD
+ * dimensions) of (1 - 1/(2 tau)) Pi_neq / rho and Pi_neq = sum_i (f_i - f_i^eq)
+ * c_i c_i over the populations of the LB node holding the cell after this
+ * step's streaming, so that <C C> = (kT/m) I + pi'.  Acceptance-rejection:
+ * attempt t takes z from the Box-Muller normals of Philox(particle id, n,
+ * replica, 13 + 16 t) (3D: z2 from words 2, 3) and U = (w >> 8) 2^-24 of
+ * word 2 (3D: word 0 of Philox(..., 14 + 16 t)), accepted when
+ * A U <= 1 + b : zz, A = 1 + 30 max |b_ab|; after 64 rejections the last
+ * candidate is kept. */
 
 /* MPCD-AT (collision = 1): each particle leaves the collision with
  * v_cm + v_ran - <v_ran>, v_ran a fresh Maxwellian velocity (variance kT/m per

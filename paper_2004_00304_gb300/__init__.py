@@ -45,7 +45,7 @@ class lbmpcd_params(ctypes.Structure):
                 ("coupling_width", ctypes.c_int), ("precision", ctypes.c_int),
                 ("feedback", ctypes.c_int), ("window", ctypes.c_int),
                 ("resample_density", ctypes.c_int), ("seed", ctypes.c_uint64),
-                ("collision", ctypes.c_int)]
+                ("collision", ctypes.c_int), ("redraw", ctypes.c_int)]
 
 
 _lib = None
@@ -120,6 +120,7 @@ def make_params(d: dict) -> lbmpcd_params:
     p.resample_density = int(d.get("resample_density", 0))
     p.seed = int(d.get("seed", 1))
     p.collision = int(d.get("collision", 0))
+    p.redraw = int(d.get("redraw", 0))
     return p
 
 

@@ -17,7 +17,8 @@ namespace lbm {
 enum : uint32_t { TAG_SHIFT = 1, TAG_SIGN = 2, TAG_AXIS = 3, TAG_VIRT = 4,
                   TAG_RESAMPLE = 5, TAG_INIT_POS = 6, TAG_INIT_VEL = 7,
                   TAG_DENSITY = 8, TAG_SPAWN_POS = 9, TAG_SPAWN_VEL = 10,
-                  TAG_AT = 11, TAG_AT_VIRT = 12 };
+                  TAG_AT = 11, TAG_AT_VIRT = 12, TAG_CE = 13 };
+constexpr int CE_TRIES = 64;   // Chapman-Enskog redraw: attempts before the last candidate is kept
 
 // density resampling of the outer buffer (resample_density = 1): a removed
 // particle's home is HOME_DEAD until the next sort compacts the pool; a new
@@ -147,6 +148,8 @@ struct RepDev {
   int resample;
   // collision rule: 0 SRD (Eq. 4), 1 MPCD-AT (Eq. 6)
   int collision;
+  // outer-buffer redraw: 0 Maxwellian, 1 Chapman-Enskog
+  int redraw;
   uint32_t cap;
   uint32_t* pool;
   uint32_t* ltile;

@@ -45,8 +45,8 @@ cudaError_t launch_sort(int dim, int prec, const Launch& L, const int2* bmap_p, 
 cudaError_t launch_tab_out(int dim, int prec, const RepDev& rd, int field, void* out, cudaStream_t st);
 
 // a7(n-1) + a2 + a3 + a4 + a6 + a5 over every particle.
-cudaError_t launch_particles(int dim, int prec, bool rs, bool at, const Launch& L, const int2* bmap, int nblocks,
-                             int k);
+cudaError_t launch_particles(int dim, int prec, bool rs, bool at, bool ce, const Launch& L, const int2* bmap,
+                             int nblocks, int k);
 
 // a7 cell part (v_cm, virtual particles, rotation draw) + a8 imposition.
 cudaError_t launch_cells(int q, int prec, const Launch& L, const int2* bmap, int nblocks, int k);

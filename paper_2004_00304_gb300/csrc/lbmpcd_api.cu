@@ -46,6 +46,7 @@ struct lbmpcd {
   int nb_s = 0;
   int mode = 0;                                 // 0: per-kernel launches in graphs, 1: persistent
   bool at = false;                              // replicas collide by MPCD-AT (Eq. 6)
+  bool ce = false;                              // some replica redraws by Chapman-Enskog
   bool lb_tma = false;                          // D2Q9 binary32 LB rows staged by bulk copies
   int pers_bps = 0;                             // persistent blocks per SM (0: occupancy limit)
   bool pers_graph = true;                       // the persistent launch captures into a graph
@@ -131,6 +132,9 @@ static int validate(const lbmpcd_params& p, std::string& why) {
   // MPCD-AT draws by particle id, and density resampling gives new particles no id
   if (p.collision == 1 && p.resample_density)
     { why = "collision = 1 (MPCD-AT) cannot be combined with resample_density = 1"; return 0; }
+  if (p.redraw < 0 || p.redraw > 1) { why = "redraw must be 0 (Maxwellian) or 1 (Chapman-Enskog)"; return 0; }
+  if (p.redraw == 1 && (p.resample_density || p.precision == LBMPCD_FP16DEV))
+    { why = "redraw = 1 (Chapman-Enskog) needs resample_density = 0 and FP64 or FP32 storage"; return 0; }
   return 1;
 }
 
@@ -156,6 +160,7 @@ extern "C" int lbmpcd_create(const lbmpcd_params* params, int n_replicas, void* 
   h->dim = h->q == 9 ? 2 : 3;
   h->prec = params[0].precision;
   h->at = params[0].collision == 1;
+  for (int r = 0; r < n_replicas; ++r) h->ce = h->ce || params[r].redraw == 1;
   h->stream = (cudaStream_t)cuda_stream;
   h->rd.resize(n_replicas);
   h->rep_allocs.resize(n_replicas);
@@ -180,6 +185,7 @@ extern "C" int lbmpcd_create(const lbmpcd_params* params, int n_replicas, void* 
     d.n_out = (p.coupling_width + 1) / 2; d.n_in = p.coupling_width / 2;
     d.feedback = p.feedback; d.window = p.window;
     d.collision = p.collision;
+    d.redraw = p.redraw;
     d.kT = p.kT; d.mass = p.mass; d.sig = sqrt(p.kT / p.mass);
     d.alpha = p.alpha; d.cos_a = cos(p.alpha); d.sin_a = sin(p.alpha);
     d.omega_f = (float)d.omega; d.r_f = (float)p.refine;
@@ -475,7 +481,7 @@ static int run_chunk(lbmpcd* h, int kcount, bool sort) {
   for (int k = 0; k < kcount; ++k) {
     CK(h, launch_lb(h->q, h->prec, h->lbvec, h->lb_tma, L, h->bm_lb, h->nb_lb, k));
     if (h->nb_s) CK(h, launch_spawn(h->dim, h->prec, L, h->bm_s, h->nb_s, k));
-    CK(h, launch_particles(h->dim, h->prec, h->nb_s > 0, h->at, L, h->bm_p, h->nb_p, k));
+    CK(h, launch_particles(h->dim, h->prec, h->nb_s > 0, h->at, h->ce, L, h->bm_p, h->nb_p, k));
     CK(h, launch_cells(h->q, h->prec, L, h->bm_c, h->nb_c, k));
     if (h->nb_cl) {
       if (h->cl_params) CK(h, launch_closure_step(h->prec, L, h->ptab, h->n_ptab, k, net_closure(h->net)));
@@ -592,7 +598,7 @@ extern "C" int lbmpcd_step_profiled(lbmpcd* h, int nsteps, double* phase_ms, lon
     for (int k = 0; k < kc; ++k) {
       bracket(1, [&] { return launch_lb(h->q, h->prec, h->lbvec, h->lb_tma, L, h->bm_lb, h->nb_lb, k); });
       if (h->nb_s) bracket(2, [&] { return launch_spawn(h->dim, h->prec, L, h->bm_s, h->nb_s, k); });
-      if (h->nb_p) bracket(2, [&] { return launch_particles(h->dim, h->prec, h->nb_s > 0, h->at, L, h->bm_p, h->nb_p, k); });
+      if (h->nb_p) bracket(2, [&] { return launch_particles(h->dim, h->prec, h->nb_s > 0, h->at, h->ce, L, h->bm_p, h->nb_p, k); });
       if (h->nb_c) bracket(3, [&] { return launch_cells(h->q, h->prec, L, h->bm_c, h->nb_c, k); });
       if (h->nb_cl)
         bracket(5, [&] {
@@ -833,9 +839,10 @@ extern "C" int lbmpcd_set_launch_mode(lbmpcd* h, int mode, int blocks_per_sm, in
     return fail(h, LBMPCD_ERR_INVALID_ARG, "mode must be 0 or 1, flags a set of LBMPCD_LAUNCH_*");
   if (mode == 1)
     for (int r = 0; r < h->nrep; ++r)
-      if (h->rd[r].cl_on || h->rd[r].resample || h->at)
+      if (h->rd[r].cl_on || h->rd[r].resample || h->at || h->ce)
         return fail(h, LBMPCD_ERR_INVALID_ARG,
-                    "the persistent form runs neither the learned closure, the density resampling nor MPCD-AT");
+                    "the persistent form runs neither the learned closure, the density resampling, MPCD-AT "
+                    "nor the Chapman-Enskog redraw");
   h->mode = mode;
   h->pers_bps = blocks_per_sm;
   h->lb_tma = (flags & LBMPCD_LAUNCH_LB_TMA) && lb_tma_ok(h->q, h->prec, h->lbvec);
@@ -853,7 +860,7 @@ extern "C" int lbmpcd_autotune(lbmpcd* h, int steps, int* choice) {
   if (!h) return LBMPCD_ERR_INVALID_ARG;
   if (steps < 1) return fail(h, LBMPCD_ERR_INVALID_ARG, "steps must be >= 1");
   bool closure = false;
-  for (int r = 0; r < h->nrep; ++r) closure = closure || h->rd[r].cl_on || h->rd[r].resample || h->at;
+  for (int r = 0; r < h->nrep; ++r) closure = closure || h->rd[r].cl_on || h->rd[r].resample || h->at || h->ce;
   struct Cand { int mode, bps, vec, flags; };
   const int vdef = h->lbvec;
   std::vector<Cand> cands = {{0, 0, vdef, 0}};

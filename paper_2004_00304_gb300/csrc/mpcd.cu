@@ -215,6 +215,78 @@ __device__ void u_fine(const RepDev& rd, int X, int Y, int Z, R* out) {
   }
 }
 
+// a3, Chapman-Enskog form (redraw = 1): the peculiar velocity C of a redrawn
+// particle in cell (X,Y,Z) follows f_MB(C; kT/m) (1 + b : zz), z = C / sigma,
+// b = pi' / (2 sigma^2), pi' the traceless part of (1 - 1/(2 tau)) Pi_neq / rho
+// of the LB node holding the cell, Pi_neq = sum_i (f_i - f_i^eq) c_i c_i over
+// the populations after this step's streaming.  Those are pulled again here
+// from the buffer the LB step read (its sources, with the half-way
+// bounce-back rule), in the storage precision (binary64 or binary32
+// deviations).  Acceptance-rejection keyed by (particle id, step, replica,
+// TAG_CE + 16 t), as the oracle draws it.
+template <int D, typename R>
+__device__ __noinline__ void ce_peculiar(const RepDev& rd, const StepInfo& st, int X, int Y, int Z, uint32_t id,
+                                         R* C) {
+  constexpr int Q = D == 2 ? 9 : 19;
+  using L = Lattice<Q>;
+  const int x = rd.x0 + X / rd.r, y = 1 + Y / rd.r, z = D == 3 ? Z / rd.r : 0;
+  const R* src = (const R*)rd.f[st.n & 1];
+  const long long N = rd.nnode, here = x + (long long)rd.nx * (y + (long long)rd.ny * z);
+  R drho = R(0), j[3] = {R(0), R(0), R(0)}, P[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const int sy = y - L::cy(i);
+    R d;
+    if (sy == 0 || sy == rd.ny - 1) {
+      d = src[L::opp(i) * N + here];
+    } else {
+      const int sx = wrap(x - L::cx(i), rd.nx), sz = wrap(z - L::cz(i), rd.nz);
+      d = src[i * N + sx + (long long)rd.nx * (sy + (long long)rd.ny * sz)];
+    }
+    drho += d;
+    j[0] += L::cx(i) * d; j[1] += L::cy(i) * d; j[2] += L::cz(i) * d;
+    P[0] += L::cx(i) * L::cx(i) * d; P[1] += L::cy(i) * L::cy(i) * d; P[2] += L::cz(i) * L::cz(i) * d;
+    P[3] += L::cx(i) * L::cy(i) * d; P[4] += L::cx(i) * L::cz(i) * d; P[5] += L::cy(i) * L::cz(i) * d;
+  }
+  // deviations d_i = f_i - w_i: sum f c c = sum d c c + cs^2 I, and the
+  // equilibrium's second moment is rho cs^2 I + rho u u
+  const R rho = R(1) + drho, ir = R(1) / rho;
+  const R u[3] = {j[0] * ir + R(0.5) * Cst<R>::g(rd, 0), j[1] * ir + R(0.5) * Cst<R>::g(rd, 1),
+                  j[2] * ir + R(0.5) * Cst<R>::g(rd, 2)};
+  const int ia[6] = {0, 1, 2, 0, 0, 1}, ib[6] = {0, 1, 2, 1, 2, 2};
+  const R fac = (R(1) - R(0.5) * Cst<R>::omega(rd)) * ir;
+  R pi[6];
+#pragma unroll
+  for (int m = 0; m < 6; ++m)
+    pi[m] = fac * (P[m] - (m < 3 ? drho / R(3) : R(0)) - rho * u[ia[m]] * u[ib[m]]);
+  const R tr = (pi[0] + pi[1] + (D == 3 ? pi[2] : R(0))) / R(D);
+  pi[0] -= tr; pi[1] -= tr;
+  if (D == 3) pi[2] -= tr; else pi[2] = pi[4] = pi[5] = R(0);
+  const R sg = Cst<R>::sig(rd), i2s = R(1) / (R(2) * sg * sg);
+  R bmax = R(0);
+#pragma unroll
+  for (int m = 0; m < 6; ++m) { pi[m] *= i2s; bmax = fmax(bmax, fabs(pi[m])); }   // pi now holds b
+  const R A = R(1) + R(30) * bmax;
+  R zz[3] = {R(0), R(0), R(0)};
+  for (int t = 0; t < CE_TRIES; ++t) {
+    const uint4 w = philox(id, st.n, rd.rep, TAG_CE + 16u * (uint32_t)t, rd.key0, rd.key1);
+    R z3, U;
+    normal_pair(w.x, w.y, zz[0], zz[1]);
+    if (D == 3) {
+      normal_pair(w.z, w.w, zz[2], z3);
+      const uint4 w2 = philox(id, st.n, rd.rep, TAG_CE + 1u + 16u * (uint32_t)t, rd.key0, rd.key1);
+      U = sizeof(R) == 8 ? (R)unit24(w2.x) : (R)unit24f(w2.x);
+    } else {
+      U = sizeof(R) == 8 ? (R)unit24(w.z) : (R)unit24f(w.z);
+    }
+    const R q = pi[0] * zz[0] * zz[0] + pi[1] * zz[1] * zz[1] + R(2) * pi[3] * zz[0] * zz[1] +
+                (D == 3 ? pi[2] * zz[2] * zz[2] + R(2) * pi[4] * zz[0] * zz[2] + R(2) * pi[5] * zz[1] * zz[2] : R(0));
+    if (A * U <= R(1) + q) break;
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) C[a] = sg * zz[a];
+}
+
 // a4: kick (v += g) then drift r += v dt (Eq. 3, dt = 1, r in cell units so the
 // displacement is v r); a wall crossing reverses v and retraces the rest of
 // the step; x (and z) wrap periodically in the region.
@@ -285,14 +357,15 @@ template <int D, typename R> struct PassShared {
 };
 
 // RS: density resampling compiled in; AT: MPCD-AT collision (Eq. 6) instead of
-// SRD.  MPCD-AT needs the cell mean of the particles' random velocities
+// SRD; CE: the Chapman-Enskog redraw compiled in (the plain pass keeps only the
+// Maxwellian one).  MPCD-AT needs the cell mean of the particles' random velocities
 // before any particle can leave the collision; as the old relative velocity
 // plays no part in it, the binning pass draws each particle's random velocity
 // v_ran, adds v - v_ran to its cell sum and stores v_ran in place of v.  The
 // cell pass turns the sums into v_cm - <v_ran>, and the next pass adds that to
 // the stored v_ran: v_cm + v_ran - <v_ran> (virtual wall particles enter the
 // cell pass).
-template <int D, typename R, bool RS, bool AT>
+template <int D, typename R, bool RS, bool AT, bool CE>
 __device__ __forceinline__ void particle_item(const RepDev& rd, const StepInfo& st, const int2 bm,
                                               PassShared<D, R>& red) {
   using T4 = typename Vec4<R>::T;
@@ -375,14 +448,23 @@ __device__ __forceinline__ void particle_item(const RepDev& rd, const StepInfo& 
     if (!(RS && rd.resample) && outer) {
       R uf[3] = {R(0), R(0), R(0)};
       u_fine<D, R>(rd, X[p], Y[p], Z[p], uf);
-      const uint4 w = philox((alt ? rd.pid_alt : rd.pid)[j], st.n, rd.rep, TAG_RESAMPLE, rd.key0, rd.key1);
-      R z0, z1, z2, z3;
-      normal_pair(w.x, w.y, z0, z1);
-      normal_pair(w.z, w.w, z2, z3);
-      const R sg = Cst<R>::sig(rd);
-      v[p][0] = uf[0] + sg * z0;
-      v[p][1] = uf[1] + sg * z1;
-      if (D == 3) v[p][2] = uf[2] + sg * z2;
+      const uint32_t id = (alt ? rd.pid_alt : rd.pid)[j];
+      if (CE && rd.redraw == 1) {
+        R C[3];
+        ce_peculiar<D, R>(rd, st, X[p], Y[p], Z[p], id, C);
+        v[p][0] = uf[0] + C[0];
+        v[p][1] = uf[1] + C[1];
+        if (D == 3) v[p][2] = uf[2] + C[2];
+      } else {
+        const uint4 w = philox(id, st.n, rd.rep, TAG_RESAMPLE, rd.key0, rd.key1);
+        R z0, z1, z2, z3;
+        normal_pair(w.x, w.y, z0, z1);
+        normal_pair(w.z, w.w, z2, z3);
+        const R sg = Cst<R>::sig(rd);
+        v[p][0] = uf[0] + sg * z0;
+        v[p][1] = uf[1] + sg * z1;
+        if (D == 3) v[p][2] = uf[2] + sg * z2;
+      }
     }
     if (RS && fresh[p]) rd.pid[j] = PID_SPAWNED;
     else if (alt) rd.pid[j] = rd.pid_alt[j];
@@ -507,56 +589,65 @@ __device__ __forceinline__ void particle_item(const RepDev& rd, const StepInfo& 
   }
 }
 
-template <int D, typename R, bool RS, bool AT>
+template <int D, typename R, bool RS, bool AT, bool CE>
 __global__ void __launch_bounds__(256, 6) particle_pass(const RepDev* __restrict__ reps, const int2* __restrict__ bmap,
                                                      int nwork, const StepInfo* __restrict__ si, int k, int nrep) {
   __shared__ RepDev rd;
   __shared__ StepInfo st;
   __shared__ PassShared<D, R> red;
   for_each_item(bmap, nwork, reps, si, k, nrep, rd, st,
-                [&](const int2 bm) { particle_item<D, R, RS, AT>(rd, st, bm, red); });
+                [&](const int2 bm) { particle_item<D, R, RS, AT, CE>(rd, st, bm, red); });
 }
 
 // single-replica form (see for_each_item_one)
-template <int D, typename R, bool RS, bool AT>
+template <int D, typename R, bool RS, bool AT, bool CE>
 __global__ void __launch_bounds__(256, 6) particle_pass_one(const __grid_constant__ RepDev rd, int nwork,
                                                          const StepInfo* __restrict__ si, int k) {
   __shared__ StepInfo st;
   __shared__ PassShared<D, R> red;
   for_each_item_one([](int wi) { return make_int2(0, wi); }, nwork, si, k, st,
-                    [&](const int2 bm) { particle_item<D, R, RS, AT>(rd, st, bm, red); });
+                    [&](const int2 bm) { particle_item<D, R, RS, AT, CE>(rd, st, bm, red); });
 }
 
-template <int D, typename R, bool RS, bool AT>
+template <int D, typename R, bool RS, bool AT, bool CE>
 static void go_particles(const Launch& L, const int2* bmap, int nwork, int k) {
   if (L.nrep == 1 && L.host) {
-    static const int g1 = grid_cap(grid_for(particle_pass_one<D, R, RS, AT>, 256, 1 << 30));
-    particle_pass_one<D, R, RS, AT><<<g1 < nwork ? g1 : nwork, 256, 0, L.stream>>>(*L.host, nwork, L.si, k);
+    static const int g1 = grid_cap(grid_for(particle_pass_one<D, R, RS, AT, CE>, 256, 1 << 30));
+    particle_pass_one<D, R, RS, AT, CE><<<g1 < nwork ? g1 : nwork, 256, 0, L.stream>>>(*L.host, nwork, L.si, k);
     return;
   }
-  static const int g = grid_cap(grid_for(particle_pass<D, R, RS, AT>, 256, 1 << 30));
-  particle_pass<D, R, RS, AT><<<g < nwork ? g : nwork, 256, 0, L.stream>>>(L.reps, bmap, nwork, L.si, k, L.nrep);
+  static const int g = grid_cap(grid_for(particle_pass<D, R, RS, AT, CE>, 256, 1 << 30));
+  particle_pass<D, R, RS, AT, CE><<<g < nwork ? g : nwork, 256, 0, L.stream>>>(L.reps, bmap, nwork, L.si, k,
+                                                                            L.nrep);
 }
 
 template <int D, typename R>
-static void go_particles_mode(bool rs, bool at, const Launch& L, const int2* bmap, int nwork, int k) {
-  if (at) go_particles<D, R, false, true>(L, bmap, nwork, k);
-  else if (rs) go_particles<D, R, true, false>(L, bmap, nwork, k);
-  else go_particles<D, R, false, false>(L, bmap, nwork, k);
+static void go_particles_mode(bool rs, bool at, bool ce, const Launch& L, const int2* bmap, int nwork, int k) {
+  if (ce) {
+    if (at) go_particles<D, R, false, true, true>(L, bmap, nwork, k);
+    else go_particles<D, R, false, false, true>(L, bmap, nwork, k);
+  } else if (at) {
+    go_particles<D, R, false, true, false>(L, bmap, nwork, k);
+  } else if (rs) {
+    go_particles<D, R, true, false, false>(L, bmap, nwork, k);
+  } else {
+    go_particles<D, R, false, false, false>(L, bmap, nwork, k);
+  }
 }
 
 // rs: some replica of the handle uses density resampling (the pass then checks
 // each replica's mode; without it the resampling code is not compiled in);
-// at: the handle's replicas collide by MPCD-AT (never together with rs)
-cudaError_t launch_particles(int dim, int prec, bool rs, bool at, const Launch& L, const int2* bmap, int nwork,
-                             int k) {
+// at: the handle's replicas collide by MPCD-AT (never together with rs);
+// ce: some replica redraws by Chapman-Enskog (never together with rs)
+cudaError_t launch_particles(int dim, int prec, bool rs, bool at, bool ce, const Launch& L, const int2* bmap,
+                             int nwork, int k) {
   if (nwork == 0) return cudaSuccess;
   if (dim == 2) {
-    if (prec == P_FP64) go_particles_mode<2, double>(rs, at, L, bmap, nwork, k);
-    else go_particles_mode<2, float>(rs, at, L, bmap, nwork, k);
+    if (prec == P_FP64) go_particles_mode<2, double>(rs, at, ce, L, bmap, nwork, k);
+    else go_particles_mode<2, float>(rs, at, ce, L, bmap, nwork, k);
   } else {
-    if (prec == P_FP64) go_particles_mode<3, double>(rs, at, L, bmap, nwork, k);
-    else go_particles_mode<3, float>(rs, at, L, bmap, nwork, k);
+    if (prec == P_FP64) go_particles_mode<3, double>(rs, at, ce, L, bmap, nwork, k);
+    else go_particles_mode<3, float>(rs, at, ce, L, bmap, nwork, k);
   }
   return cudaGetLastError();
 }
@@ -901,7 +992,7 @@ __global__ void __launch_bounds__(256, 2) step_persistent(const RepDev* __restri
   for (int k = 0; k < kcount; ++k) {
     for_each_item(bm_lb, nb_lb, reps, si, k, nrep, rd, st, [&](const int4 bm) { lb_row<Q, S, V>(rd, st, bm); });
     if (!grid_barrier(bar, bar + 1, gridDim.x, err)) return;
-    for_each_item(bm_p, nb_p, reps, si, k, nrep, rd, st, [&](const int2 bm) { particle_item<D, R, false, false>(rd, st, bm, red); });
+    for_each_item(bm_p, nb_p, reps, si, k, nrep, rd, st, [&](const int2 bm) { particle_item<D, R, false, false, false>(rd, st, bm, red); });
     if (!grid_barrier(bar, bar + 1, gridDim.x, err)) return;
     for_each_item(bm_c, nb_c, reps, si, k, nrep, rd, st, [&](const int2 bm) { cell_item<Q, S>(rd, st, bm); });
     if (!grid_barrier(bar, bar + 1, gridDim.x, err)) return;
