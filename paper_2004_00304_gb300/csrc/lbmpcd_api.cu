@@ -294,8 +294,8 @@ static int build_maps(lbmpcd* h) {
     const long long nslot = d.resample ? (long long)d.cap : d.np;
     const long long npb = (nslot + PP_ITEM - 1) / PP_ITEM, ncb = (d.ncell + 256 * CPT - 1) / (256 * CPT), nbb = (d.nbuf + 255) / 256;
     for (long long b = 0; b < npb; ++b) pp.push_back(make_int2(r, (int)b));
+    for (long long b = 0; b < nbb; ++b) cc.push_back(make_int2(r, (int)(-1 - b)));   // a8 blocks first
     for (long long b = 0; b < ncb; ++b) cc.push_back(make_int2(r, (int)b));
-    for (long long b = 0; b < nbb; ++b) cc.push_back(make_int2(r, (int)(-1 - b)));
     for (int b = 0; b < d.ntile; ++b) tt.push_back(make_int2(r, b));
     if (d.resample) {
       const long long nouter = (long long)(d.xo_lo + (d.Wx - d.xo_hi)) * d.Hy * d.Wz;

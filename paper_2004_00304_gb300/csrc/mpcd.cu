@@ -839,33 +839,15 @@ __device__ __forceinline__ void cell_item(const RepDev& rd, const StepInfo& st, 
     return;
   }
   // a8: one thread per inner-buffer LB node.  The window sums are binary64;
-  // the equilibrium is evaluated in the kernel's precision.
+  // the equilibrium is evaluated in the kernel's precision.  Every load of
+  // the thread (frame, running sum, ring slot, the node's LB density) is
+  // issued before the first store, so that they make one round trip: these
+  // few blocks are the last to finish the pass.
   const long long b = (long long)(-1 - bm.y) * blockDim.x + threadIdx.x;
   if (b >= rd.nbuf) return;
   double* fr = rd.frame + 4 * b;
   double* ws = rd.wsum + 4 * b;
   double* rg = rd.ring + 4 * ((long long)(st.n % (uint32_t)rd.window) * rd.nbuf + b);
-  double W4[4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    const double x = fr[a];
-    W4[a] = ws[a] + (x - rg[a]);
-    ws[a] = W4[a];
-    rg[a] = x;
-    fr[a] = 0.0;
-  }
-  const uint32_t nf = min(st.n + 1u, (uint32_t)rd.window);
-  const R rdim = (D == 3) ? (R)(rd.r * rd.r * rd.r) : (R)(rd.r * rd.r);
-  const R M = (R)W4[0];
-  const R rho = M / ((R)rd.ppc * (R)Cst<R>::mass(rd) * rdim * (R)nf);
-  R u[3] = {R(0), R(0), R(0)};
-  if (M > R(0)) {
-    const R iM = R(1) / M;
-    u[0] = (R)W4[1] * iM; u[1] = (R)W4[2] * iM; u[2] = (R)W4[3] * iM;
-  }
-  double* wm = rd.wmean + 4 * b;
-  wm[0] = (double)rho; wm[1] = (double)u[0]; wm[2] = (double)u[1]; wm[3] = (double)u[2];
-  if (!(rd.feedback == 1 && st.n >= 1 && M > R(0))) return;
   long long t = b;
   int x, y, z;
   if (rd.strip) {
@@ -878,12 +860,32 @@ __device__ __forceinline__ void cell_item(const RepDev& rd, const StepInfo& st, 
     const int col = (int)(t % rd.n_in), side = (int)(t / rd.n_in);
     x = side == 0 ? rd.x0 + rd.n_out + col : rd.x1 - 1 - rd.n_out - col;
   }
-  S* dst = (S*)rd.f[(st.n & 1) ^ 1];
   const long long node = x + (long long)rd.nx * (y + (long long)rd.ny * z);
-  // equilibrium at the node's own LB density (this step's moment) and the
+  double xf[4], xw[4], xr[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) { xf[a] = fr[a]; xw[a] = ws[a]; xr[a] = rg[a]; }
+  const R rl = ((const R*)rd.rho)[node];
+  double W4[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) W4[a] = xw[a] + (xf[a] - xr[a]);
+#pragma unroll
+  for (int a = 0; a < 4; ++a) { ws[a] = W4[a]; rg[a] = xf[a]; fr[a] = 0.0; }
+  const uint32_t nf = min(st.n + 1u, (uint32_t)rd.window);
+  const R rdim = (D == 3) ? (R)(rd.r * rd.r * rd.r) : (R)(rd.r * rd.r);
+  const R M = (R)W4[0];
+  const R rho = M / ((R)rd.ppc * (R)Cst<R>::mass(rd) * rdim * (R)nf);
+  R u[3] = {R(0), R(0), R(0)};
+  if (M > R(0)) {
+    const R iM = R(1) / M;
+    u[0] = (R)W4[1] * iM; u[1] = (R)W4[2] * iM; u[2] = (R)W4[3] * iM;
+  }
+  double* wm = rd.wmean + 4 * b;
+  wm[0] = (double)rho; wm[1] = (double)u[0]; wm[2] = (double)u[1]; wm[3] = (double)u[2];
+  if (!(rd.feedback == 1 && st.n >= 1 && M > R(0))) return;
+  S* dst = (S*)rd.f[(st.n & 1) ^ 1];
+  // equilibrium at the node's own LB density (this step's moment, rl) and the
   // window-mean MPCD velocity: the MPCD density is reported, not imposed,
   // because the two fluids' equations of state differ (rho/3 versus n kT).
-  const R rl = ((const R*)rd.rho)[node];
   const R uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
@@ -902,13 +904,14 @@ __global__ void __launch_bounds__(256) cell_pass(const RepDev* __restrict__ reps
   for_each_item(bmap, nwork, reps, si, k, nrep, rd, st, [&](const int2 bm) { cell_item<Q, S>(rd, st, bm); });
 }
 
-// items: the cell blocks (0, b) of the replica, then its a8 blocks (0, -1 - b)
+// items: the a8 blocks (0, -1 - b) of the replica first (they finish last
+// when they start last), then its cell blocks (0, b)
 template <int Q, typename S>
 __global__ void __launch_bounds__(256) cell_pass_one(const __grid_constant__ RepDev rd, int nwork,
                                                      const StepInfo* __restrict__ si, int k) {
   __shared__ StepInfo st;
-  const int ncb = (int)((rd.ncell + 256 * CPT - 1) / (256 * CPT));
-  for_each_item_one([ncb](int wi) { return make_int2(0, wi < ncb ? wi : -1 - (wi - ncb)); }, nwork, si, k, st,
+  const int nbb = (int)((rd.nbuf + 255) / 256);
+  for_each_item_one([nbb](int wi) { return make_int2(0, wi < nbb ? -1 - wi : wi - nbb); }, nwork, si, k, st,
                     [&](const int2 bm) { cell_item<Q, S>(rd, st, bm); });
 }
 
