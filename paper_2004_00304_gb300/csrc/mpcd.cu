@@ -366,10 +366,10 @@ template <int D, typename R> struct PassShared {
 // the stored v_ran: v_cm + v_ran - <v_ran> (virtual wall particles enter the
 // cell pass).
 template <int D, typename R, bool RS, bool AT, bool CE>
-__device__ __forceinline__ void particle_item(const RepDev& rd, const StepInfo& st, const int2 bm,
-                                              PassShared<D, R>& red) {
+__device__ __forceinline__ void particle_item(const RepDev& rd, const StepInfo& st, const uint32_t start,
+                                              const uint32_t end, PassShared<D, R>& red) {
   using T4 = typename Vec4<R>::T;
-  const uint32_t j0 = (uint32_t)bm.y * PP_ITEM + threadIdx.x;
+  const uint32_t j0 = start + threadIdx.x;
   const bool alt = st.src_alt;
   const uint32_t* hsrc = alt ? rd.home_alt : rd.home;   // plain loads (see lb_row)
   int X[PPT], Y[PPT], Z[PPT];
@@ -378,7 +378,7 @@ __device__ __forceinline__ void particle_item(const RepDev& rd, const StepInfo& 
   // branch-free loads: a lane past the end reads the last particle and discards it
   void* const* offs = alt ? rd.off_alt : rd.off;
   void* const* vels = alt ? rd.vel_alt : rd.vel;
-  const uint32_t np32 = RS ? pool_end(rd) : (uint32_t)rd.np, last = np32 ? np32 - 1u : 0u;
+  const uint32_t np32 = min(RS ? pool_end(rd) : (uint32_t)rd.np, end), last = np32 ? np32 - 1u : 0u;
   // density resampling: removed particles (HOME_DEAD) are skipped, particles
   // created this step (PID_FRESH) are neither rotated nor removed
   bool fresh[PPT];
@@ -596,7 +596,7 @@ __global__ void __launch_bounds__(256, 6) particle_pass(const RepDev* __restrict
   __shared__ StepInfo st;
   __shared__ PassShared<D, R> red;
   for_each_item(bmap, nwork, reps, si, k, nrep, rd, st,
-                [&](const int2 bm) { particle_item<D, R, RS, AT, CE>(rd, st, bm, red); });
+                [&](const int2 bm) { particle_item<D, R, RS, AT, CE>(rd, st, (uint32_t)bm.y * PP_ITEM, ~0u, red); });
 }
 
 // single-replica form (see for_each_item_one)
@@ -605,8 +605,19 @@ __global__ void __launch_bounds__(256, 6) particle_pass_one(const __grid_constan
                                                          const StepInfo* __restrict__ si, int k) {
   __shared__ StepInfo st;
   __shared__ PassShared<D, R> red;
-  for_each_item_one([](int wi) { return make_int2(0, wi); }, nwork, si, k, st,
-                    [&](const int2 bm) { particle_item<D, R, RS, AT, CE>(rd, st, bm, red); });
+  {
+    const int* c = (const int*)(si + k);
+    int* d = (int*)&st;
+    for (int i = threadIdx.x; i < (int)(sizeof(StepInfo) / 4); i += blockDim.x) d[i] = c[i];
+    __syncthreads();
+  }
+  // an even share of the particles per block (a multiple of 32), walked in
+  // PP_ITEM chunks: every block ends with the same amount of work, where
+  // whole items left some blocks one item longer than the rest
+  const uint32_t np = RS ? pool_end(rd) : (uint32_t)rd.np;
+  const uint32_t per = ((np + gridDim.x - 1u) / gridDim.x + 31u) & ~31u;
+  const uint32_t b0 = blockIdx.x * per, b1 = min(np, b0 + per);
+  for (uint32_t s = b0; s < b1; s += PP_ITEM) particle_item<D, R, RS, AT, CE>(rd, st, s, b1, red);
 }
 
 template <int D, typename R, bool RS, bool AT, bool CE>
@@ -995,7 +1006,7 @@ __global__ void __launch_bounds__(256, 2) step_persistent(const RepDev* __restri
   for (int k = 0; k < kcount; ++k) {
     for_each_item(bm_lb, nb_lb, reps, si, k, nrep, rd, st, [&](const int4 bm) { lb_row<Q, S, V>(rd, st, bm); });
     if (!grid_barrier(bar, bar + 1, gridDim.x, err)) return;
-    for_each_item(bm_p, nb_p, reps, si, k, nrep, rd, st, [&](const int2 bm) { particle_item<D, R, false, false, false>(rd, st, bm, red); });
+    for_each_item(bm_p, nb_p, reps, si, k, nrep, rd, st, [&](const int2 bm) { particle_item<D, R, false, false, false>(rd, st, (uint32_t)bm.y * PP_ITEM, ~0u, red); });
     if (!grid_barrier(bar, bar + 1, gridDim.x, err)) return;
     for_each_item(bm_c, nb_c, reps, si, k, nrep, rd, st, [&](const int2 bm) { cell_item<Q, S>(rd, st, bm); });
     if (!grid_barrier(bar, bar + 1, gridDim.x, err)) return;
