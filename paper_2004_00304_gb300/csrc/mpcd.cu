@@ -745,20 +745,22 @@ cudaError_t launch_spawn(int dim, int prec, const Launch& L, const int2* bmap, i
 // ---------------------------------------------------------------------------
 // cell_pass: a7 cell part and a8.
 template <int Q, typename S>
-__device__ __forceinline__ void cell_item(const RepDev& rd, const StepInfo& st, const int2 bm) {
+__device__ __forceinline__ void cell_item(const RepDev& rd, const StepInfo& st, const int2 bm,
+                                          const long long start, const long long end) {
   using R = typename Store<S>::R;
   using T4 = typename Vec4<R>::T;
   using L = Lattice<Q>;
   constexpr int D = L::D;
   if (bm.y >= 0) {
-    // CPT cells per thread (c0 + 256 p): all accumulator loads first
-    const long long c0 = (long long)bm.y * (256 * CPT) + threadIdx.x;
+    // cells [start, end) (at most 256 CPT of them), CPT per thread (c0 + 256 p):
+    // all accumulator loads first
+    const long long c0 = start + threadIdx.x;
     uint32_t nn[CPT];
     R V[CPT][3];
 #pragma unroll
     for (int p = 0; p < CPT; ++p) {
       const long long c = c0 + 256 * p;
-      const long long cl = c < rd.ncell ? c : rd.ncell - 1;
+      const long long cl = c < end ? c : end - 1;
       if (sizeof(R) == 4) {
         const float4 g4 = rd.acc4[cl];
         nn[p] = (uint32_t)g4.x;
@@ -772,7 +774,7 @@ __device__ __forceinline__ void cell_item(const RepDev& rd, const StepInfo& st, 
 #pragma unroll
     for (int p = 0; p < CPT; ++p) {
       const long long c = c0 + 256 * p;
-      if (c >= rd.ncell) break;
+      if (c >= end) break;
       const uint32_t n = nn[p];
       R vc[3] = {R(0), R(0), R(0)}, rt[3] = {R(0), R(0), R(0)};
       if (n > 0) {
@@ -912,25 +914,40 @@ __global__ void __launch_bounds__(256) cell_pass(const RepDev* __restrict__ reps
                                                  int nwork, const StepInfo* __restrict__ si, int k, int nrep) {
   __shared__ RepDev rd;
   __shared__ StepInfo st;
-  for_each_item(bmap, nwork, reps, si, k, nrep, rd, st, [&](const int2 bm) { cell_item<Q, S>(rd, st, bm); });
+  for_each_item(bmap, nwork, reps, si, k, nrep, rd, st, [&](const int2 bm) {
+    cell_item<Q, S>(rd, st, bm, (long long)bm.y * (256 * CPT), rd.ncell);
+  });
 }
 
-// items: the a8 blocks (0, -1 - b) of the replica first (they finish last
-// when they start last), then its cell blocks (0, b)
+// the first blocks do the a8 items (they finish last when they start last);
+// every other block of the resident grid takes an even, contiguous share of
+// the collision cells, walked in chunks of 256 CPT
 template <int Q, typename S>
 __global__ void __launch_bounds__(256) cell_pass_one(const __grid_constant__ RepDev rd, int nwork,
                                                      const StepInfo* __restrict__ si, int k) {
   __shared__ StepInfo st;
+  {
+    const int* c = (const int*)(si + k);
+    int* d = (int*)&st;
+    for (int i = threadIdx.x; i < (int)(sizeof(StepInfo) / 4); i += blockDim.x) d[i] = c[i];
+    __syncthreads();
+  }
   const int nbb = (int)((rd.nbuf + 255) / 256);
-  for_each_item_one([nbb](int wi) { return make_int2(0, wi < nbb ? -1 - wi : wi - nbb); }, nwork, si, k, st,
-                    [&](const int2 bm) { cell_item<Q, S>(rd, st, bm); });
+  for (int b = blockIdx.x; b < nbb; b += gridDim.x) cell_item<Q, S>(rd, st, make_int2(0, -1 - b), 0, 0);
+  const int ncb = (int)gridDim.x > nbb ? (int)gridDim.x - nbb : (int)gridDim.x;
+  const int me = (int)gridDim.x > nbb ? (int)blockIdx.x - nbb : (int)blockIdx.x;
+  if (me < 0) return;
+  const long long per = ((rd.ncell + ncb - 1) / ncb + 31) & ~31LL;
+  const long long c0 = me * per, c1 = min(rd.ncell, c0 + per);
+  for (long long s = c0; s < c1; s += 256 * CPT) cell_item<Q, S>(rd, st, make_int2(0, 0), s, c1);
 }
 
 template <int Q, typename S>
 static void go_cells(const Launch& L, const int2* bmap, int nwork, int k) {
   if (L.nrep == 1 && L.host) {
     static const int g1 = grid_cap(grid_for(cell_pass_one<Q, S>, 256, 1 << 30));
-    cell_pass_one<Q, S><<<g1 < nwork ? g1 : nwork, 256, 0, L.stream>>>(*L.host, nwork, L.si, k);
+    // the whole resident grid: the kernel divides the cells evenly among its blocks
+    cell_pass_one<Q, S><<<g1, 256, 0, L.stream>>>(*L.host, nwork, L.si, k);
     return;
   }
   static const int g = grid_cap(grid_for(cell_pass<Q, S>, 256, 1 << 30));
@@ -1008,7 +1025,9 @@ __global__ void __launch_bounds__(256, 2) step_persistent(const RepDev* __restri
     if (!grid_barrier(bar, bar + 1, gridDim.x, err)) return;
     for_each_item(bm_p, nb_p, reps, si, k, nrep, rd, st, [&](const int2 bm) { particle_item<D, R, false, false, false>(rd, st, (uint32_t)bm.y * PP_ITEM, ~0u, red); });
     if (!grid_barrier(bar, bar + 1, gridDim.x, err)) return;
-    for_each_item(bm_c, nb_c, reps, si, k, nrep, rd, st, [&](const int2 bm) { cell_item<Q, S>(rd, st, bm); });
+    for_each_item(bm_c, nb_c, reps, si, k, nrep, rd, st, [&](const int2 bm) {
+      cell_item<Q, S>(rd, st, bm, (long long)bm.y * (256 * CPT), rd.ncell);
+    });
     if (!grid_barrier(bar, bar + 1, gridDim.x, err)) return;
   }
 }
