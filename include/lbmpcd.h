@@ -306,7 +306,7 @@ int lbmpcd_net_forward_noalloc(const float* theta_dev, const float* x_dev, int p
  * STATE (no replica with feedback = 2 and a region), INVALID_ARG, CUDA. */
 int lbmpcd_set_closure(lbmpcd* h, const float* theta, long long count, int src_on_device, int interval);
 
-/* Launch form of the step (batching; not in the paper).  mode 0
+/* Launch form of the step (batching of the step launches; not in the paper).  mode 0
  * (default): each step is three kernels (lb_pull, particle_pass, cell_pass)
  * over all replicas, 64 steps per captured CUDA graph.  mode 1: each chunk of
  * steps is one persistent cooperative kernel running the three phases per
