@@ -74,20 +74,28 @@ enum {
  *                                         in pool order, the same for every field read
  *                                         between two steps; PART_ID is the initial index
  *                                         or -3 for particles created by the resampling)
+ *  CELL_LIST [np] (int32)                 cell lists of the last binning: for the collision
+ *                                         cells in increasing id, the rows of the particle
+ *                                         fields (= particle ids without resampling) of its
+ *                                         particles in increasing order; cell c's entries
+ *                                         start at the sum of CELL_COUNT below c (assembled
+ *                                         on the host from PART_CELL)
  *  CLOSURE_IN [P][16][16][24] (double)    learned-closure network input of the last step
  *  CLOSURE_OUT [P][16][16][3] (double)    network output of the last step (with parameters)
  *  CLOSURE_TARGET [P][16][16][3] (double) moving averages of the strip fields (training target)
  *                                         -- the three CLOSURE fields exist with feedback = 2;
  *                                         P = 2 ceil(Hy/16) patches, see lbmpcd_set_closure
  * Collision cells: ncell = Wx (Hy+1) Wz, id = cx + Wx (cy + (Hy+1) cz), with
- * Wx = (x1-x0) refine, Hy = (ny-2) refine, Wz = nz refine (1 in 2D).
+ * Wx = (x1-x0) refine, Hy = (ny-2) refine (a near-wall strip: (y1-1) refine),
+ * Wz = nz refine (1 in 2D).
  * Inner buffer nodes: nbuf = 2 * floor(cw/2) * (ny-2) * nz, index
- * ((side * floor(cw/2) + col) * nz + z) * (ny-2) + (y-1). */
+ * ((side * floor(cw/2) + col) * nz + z) * (ny-2) + (y-1); for a near-wall
+ * strip floor(cw/2) * nz * nx, index (row * nz + z) * nx + x. */
 enum {
   LBMPCD_RHO = 0, LBMPCD_U = 1, LBMPCD_POPS = 2, LBMPCD_PART_POS = 3, LBMPCD_PART_VEL = 4,
   LBMPCD_PART_CELL = 5, LBMPCD_SHIFT = 6, LBMPCD_CELL_COUNT = 7, LBMPCD_WINDOW_MEAN = 8,
   LBMPCD_DIAG = 9, LBMPCD_PART_HOME = 10, LBMPCD_CELL_VCM = 11, LBMPCD_PART_ID = 12,
-  LBMPCD_CLOSURE_IN = 13, LBMPCD_CLOSURE_OUT = 14, LBMPCD_CLOSURE_TARGET = 15
+  LBMPCD_CLOSURE_IN = 13, LBMPCD_CLOSURE_OUT = 14, LBMPCD_CLOSURE_TARGET = 15, LBMPCD_CELL_LIST = 17
 };
 
 typedef struct lbmpcd lbmpcd; /* opaque handle */

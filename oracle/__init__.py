@@ -25,8 +25,8 @@ _lib = None
 
 FIELDS = dict(RHO=0, U=1, POPS=2, PART_POS=3, PART_VEL=4, PART_CELL=5, SHIFT=6,
               CELL_COUNT=7, WINDOW_MEAN=8, DIAG=9, PART_HOME=10, CELL_VCM=11, PART_ID=12,
-              CLOSURE_IN=13, CLOSURE_TARGET=15, PI=16)
-_INT_FIELDS = {"PART_CELL", "CELL_COUNT", "PART_HOME", "PART_ID"}
+              CLOSURE_IN=13, CLOSURE_TARGET=15, PI=16, CELL_LIST=17)
+_INT_FIELDS = {"PART_CELL", "CELL_COUNT", "PART_HOME", "PART_ID", "CELL_LIST"}
 
 
 def build(force: bool = False) -> str:

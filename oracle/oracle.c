@@ -984,6 +984,7 @@ long orc_field_size(const orc_sim* s, int field) {
     case ORC_CLOSURE_IN: return s->cl_on ? 2L * s->cl_npy * CL_W * CL_W * 3 * CL_FRAMES : -1;
     case ORC_CLOSURE_TARGET: return s->cl_on ? 2L * s->cl_npy * CL_W * CL_W * 3 : -1;
     case ORC_PI: return 6 * s->nnode;
+    case ORC_CELL_LIST: return s->np;
   }
   return -1;
 }
@@ -1029,6 +1030,13 @@ int orc_get_field(const orc_sim* s, int field, void* dst) {
       break;
     case ORC_WINDOW_MEAN: memcpy(D, s->wmean, sizeof(double) * n); break;
     case ORC_PI: memcpy(D, s->pi, sizeof(double) * n); break;
+    case ORC_CELL_LIST: {   /* for each cell in increasing order, its particles in increasing index */
+      long m = 0;
+      for (long c = 0; c < s->ncell; ++c)
+        for (long k = 0; k < s->np; ++k)
+          if (s->pcell[k] == c) I[m++] = (int)k;
+      break;
+    }
     case ORC_DIAG: diag(s, D); break;
     case ORC_CLOSURE_IN: memcpy(D, s->cl_x, sizeof(double) * n); break;
     case ORC_CLOSURE_TARGET:

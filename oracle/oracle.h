@@ -73,8 +73,10 @@ enum {
   ORC_PART_ID = 12,
   ORC_CLOSURE_IN = 13,      /* [P][16][16][24] network input of the last step */
   ORC_CLOSURE_TARGET = 15,  /* [P][16][16][3] moving averages, patch layout */
-  ORC_PI = 16               /* [6][nz][ny][nx] traceless kinematic non-equilibrium momentum flux
+  ORC_PI = 16,              /* [6][nz][ny][nx] traceless kinematic non-equilibrium momentum flux
                                (xx, yy, zz, xy, xz, yz) of the last LB step (redraw = 1) */
+  ORC_CELL_LIST = 17        /* [np] particle indices grouped by collision cell (increasing cell,
+                               then increasing index) */
 };
 
 orc_sim* orc_create(const orc_params* p, int replica);

@@ -25,8 +25,8 @@ D2Q9, D3Q19 = 9, 19
 FP64, FP32, FP16DEV = 0, 1, 2
 FIELDS = dict(RHO=0, U=1, POPS=2, PART_POS=3, PART_VEL=4, PART_CELL=5, SHIFT=6,
               CELL_COUNT=7, WINDOW_MEAN=8, DIAG=9, PART_HOME=10, CELL_VCM=11, PART_ID=12,
-              CLOSURE_IN=13, CLOSURE_OUT=14, CLOSURE_TARGET=15)
-INT_FIELDS = {"PART_CELL", "CELL_COUNT", "PART_HOME", "PART_ID"}
+              CLOSURE_IN=13, CLOSURE_OUT=14, CLOSURE_TARGET=15, CELL_LIST=17)
+INT_FIELDS = {"PART_CELL", "CELL_COUNT", "PART_HOME", "PART_ID", "CELL_LIST"}
 LAUNCH_LB_TMA = 1   # LBMPCD_LAUNCH_LB_TMA
 ERRORS = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "TIMEOUT", -5: "STATE", -6: "CAPACITY"}
 

@@ -638,18 +638,19 @@ static long long live_particles(lbmpcd* h, int r) {
 static long long field_elems(const lbmpcd* h, int r, int field) {
   const RepDev& d = h->rd[r];
   const bool pf = field == LBMPCD_PART_POS || field == LBMPCD_PART_VEL || field == LBMPCD_PART_HOME ||
-                  field == LBMPCD_PART_CELL || field == LBMPCD_PART_ID;
+                  field == LBMPCD_PART_CELL || field == LBMPCD_PART_ID || field == LBMPCD_CELL_LIST;
+  const bool scalar = field == LBMPCD_PART_CELL || field == LBMPCD_PART_ID || field == LBMPCD_CELL_LIST;
   if (pf && d.has_region && d.resample) {
     const long long n = live_particles(const_cast<lbmpcd*>(h), r);
     if (n < 0) return -1;
-    return (field == LBMPCD_PART_CELL || field == LBMPCD_PART_ID) ? n : 3 * n;
+    return scalar ? n : 3 * n;
   }
   switch (field) {
     case LBMPCD_RHO: return d.nnode;
     case LBMPCD_U: return 3 * d.nnode;
     case LBMPCD_POPS: return (long long)h->q * d.nnode;
     case LBMPCD_PART_POS: case LBMPCD_PART_VEL: case LBMPCD_PART_HOME: return d.has_region ? 3 * d.np : -1;
-    case LBMPCD_PART_CELL: case LBMPCD_PART_ID: return d.has_region ? d.np : -1;
+    case LBMPCD_PART_CELL: case LBMPCD_PART_ID: case LBMPCD_CELL_LIST: return d.has_region ? d.np : -1;
     case LBMPCD_SHIFT: return 3;
     case LBMPCD_CELL_COUNT: return d.has_region ? d.ncell : -1;
     case LBMPCD_CELL_VCM: return d.has_region ? 3 * d.ncell : -1;
@@ -661,7 +662,8 @@ static long long field_elems(const lbmpcd* h, int r, int field) {
   return -1;
 }
 static bool int_field(int f) {
-  return f == LBMPCD_PART_CELL || f == LBMPCD_CELL_COUNT || f == LBMPCD_PART_HOME || f == LBMPCD_PART_ID;
+  return f == LBMPCD_PART_CELL || f == LBMPCD_CELL_COUNT || f == LBMPCD_PART_HOME || f == LBMPCD_PART_ID ||
+         f == LBMPCD_CELL_LIST;
 }
 
 extern "C" long long lbmpcd_field_size(const lbmpcd* h, int replica, int field) {
@@ -690,6 +692,24 @@ extern "C" int lbmpcd_get_fields(lbmpcd* h, int replica, int field, void* dst, s
   if (bytes != (size_t)n * esz) return fail(h, LBMPCD_ERR_INVALID_ARG, "dst size does not match the field");
   if (h->maps_dirty) { int rc = build_maps(h); if (rc) return rc; }
   const RepDev& d = h->rd[replica];
+  if (field == LBMPCD_CELL_LIST) {
+    // stable counting sort of the particle rows by their collision cell (host)
+    std::vector<int32_t> cell((size_t)n), list((size_t)n);
+    std::vector<long long> start((size_t)d.ncell + 1, 0);
+    int rc = n ? lbmpcd_get_fields(h, replica, LBMPCD_PART_CELL, cell.data(), (size_t)n * 4, 0) : LBMPCD_OK;
+    if (rc) return rc;
+    for (long long j = 0; j < n; ++j) {
+      if (cell[j] < 0 || cell[j] >= d.ncell) return fail(h, LBMPCD_ERR_STATE, "particle without a collision cell");
+      ++start[cell[j] + 1];
+    }
+    for (long long c = 0; c < d.ncell; ++c) start[c + 1] += start[c];
+    for (long long j = 0; j < n; ++j) list[start[cell[j]]++] = (int32_t)j;
+    if (n == 0) return LBMPCD_OK;
+    CK(h, cudaMemcpyAsync(dst, list.data(), bytes, dst_on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost,
+                          h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return LBMPCD_OK;
+  }
   void* buf = dst;
   void* tmp = nullptr;
   if (!dst_on_device && n > 0) {

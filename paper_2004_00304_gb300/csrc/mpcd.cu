@@ -946,8 +946,12 @@ template <int Q, typename S>
 static void go_cells(const Launch& L, const int2* bmap, int nwork, int k) {
   if (L.nrep == 1 && L.host) {
     static const int g1 = grid_cap(grid_for(cell_pass_one<Q, S>, 256, 1 << 30));
-    // the whole resident grid: the kernel divides the cells evenly among its blocks
-    cell_pass_one<Q, S><<<g1, 256, 0, L.stream>>>(*L.host, nwork, L.si, k);
+    // the resident grid (at most one block per 256 cells besides the a8 blocks):
+    // the kernel divides the cells evenly among its blocks
+    const RepDev& h = *L.host;
+    const long long want = (h.nbuf + 255) / 256 + (h.ncell + 255) / 256;
+    const int g = (int)(want < g1 ? want : g1);
+    cell_pass_one<Q, S><<<g > 0 ? g : 1, 256, 0, L.stream>>>(h, nwork, L.si, k);
     return;
   }
   static const int g = grid_cap(grid_for(cell_pass<Q, S>, 256, 1 << 30));

@@ -284,3 +284,21 @@ def test_virtual_wall_particles():
     zs = np.array(zs)
     assert len(zs) > 100
     assert stats.kstest(zs, "norm").pvalue > 1e-4
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_cell_list_groups_particles_by_cell(dim):
+    """CELL_LIST is the stable grouping of particle indices by collision cell:
+    a permutation equal to a stable argsort of PART_CELL, with CELL_COUNT[c]
+    entries for cell c."""
+    cfg = inputs.small_2d() if dim == 2 else inputs.small_3d()
+    s = O.OracleSim(cfg["params"])
+    s.set_region(*cfg["region"])
+    s.step(3)
+    cells = s.get("PART_CELL")
+    lst = s.get("CELL_LIST")
+    assert np.array_equal(np.sort(lst), np.arange(len(cells)))
+    assert np.array_equal(lst, np.argsort(cells, kind="stable"))
+    cnt = s.get("CELL_COUNT")
+    assert np.array_equal(np.bincount(cells[lst], minlength=len(cnt)), cnt)
+    assert np.all(np.diff(cells[lst]) >= 0)
