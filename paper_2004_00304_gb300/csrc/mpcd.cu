@@ -589,8 +589,10 @@ __device__ __forceinline__ void particle_item(const RepDev& rd, const StepInfo& 
   }
 }
 
+// resident blocks per SM: 6 in 2D (40 registers, no spills); 5 in 3D, whose
+// state needs more registers (at 6 the 3D pass spilled and ran 13 % slower)
 template <int D, typename R, bool RS, bool AT, bool CE>
-__global__ void __launch_bounds__(256, 6) particle_pass(const RepDev* __restrict__ reps, const int2* __restrict__ bmap,
+__global__ void __launch_bounds__(256, D == 2 ? 6 : 5) particle_pass(const RepDev* __restrict__ reps, const int2* __restrict__ bmap,
                                                      int nwork, const StepInfo* __restrict__ si, int k, int nrep) {
   __shared__ RepDev rd;
   __shared__ StepInfo st;
@@ -601,7 +603,7 @@ __global__ void __launch_bounds__(256, 6) particle_pass(const RepDev* __restrict
 
 // single-replica form (see for_each_item_one)
 template <int D, typename R, bool RS, bool AT, bool CE>
-__global__ void __launch_bounds__(256, 6) particle_pass_one(const __grid_constant__ RepDev rd, int nwork,
+__global__ void __launch_bounds__(256, D == 2 ? 6 : 5) particle_pass_one(const __grid_constant__ RepDev rd, int nwork,
                                                          const StepInfo* __restrict__ si, int k) {
   __shared__ StepInfo st;
   __shared__ PassShared<D, R> red;

@@ -33,16 +33,22 @@ def _check(g, o):
         assert e <= 1e-12, (f, e)
 
 
-@pytest.mark.parametrize("case,bps", [("2d", 0), ("2d", 1), ("3d", 0)])
+@pytest.mark.parametrize("case,bps", [("2d", 0), ("2d", 1), ("3d", 0), ("2d_strip", 0), ("3d_strip", 0)])
 def test_persistent_matches_oracle(lb, case, bps):
     """70 steps = one 64-step chunk (sort + one persistent launch) and a
-    6-step remainder launch, then 3 more single steps."""
-    cfg = inputs.small_2d(precision=0, nx=72) if case == "2d" else inputs.small_3d(precision=0, nx=24)
+    6-step remainder launch, then 3 more single steps; also with a near-wall
+    strip as the MPCD region."""
+    cfg = inputs.small_2d(precision=0, nx=72) if case.startswith("2d") else inputs.small_3d(precision=0, nx=24)
     g = lb.Lbmpcd(cfg["params"])
-    g.set_region(0, *cfg["region"])
-    g.set_launch_mode(1, bps)
     o = O.OracleSim(cfg["params"])
-    o.set_region(*cfg["region"])
+    if case.endswith("strip"):
+        y1 = 8 if case.startswith("2d") else 6
+        g.set_strip(0, y1)
+        o.set_strip(y1)
+    else:
+        g.set_region(0, *cfg["region"])
+        o.set_region(*cfg["region"])
+    g.set_launch_mode(1, bps)
     g.step(70)
     o.step(70)
     _check(g, o)
