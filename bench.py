@@ -54,6 +54,28 @@ def ensemble_workload():
     return inputs.ensemble_replicas()
 
 
+def rank_params(params: dict, rank: int) -> dict:
+    """The channel of rank r under torchrun: the same workload with seed + 1000 r,
+    so that the ranks run independent replicas (no collective on the data path)."""
+    return dict(params, seed=params["seed"] + 1000 * rank)
+
+
+def max_over_ranks(value: float, world: int, device) -> float:
+    """The slowest rank's value (a MAX all-reduce; every rank calls it)."""
+    if world == 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(steps: int, world: int, seconds: float) -> float:
+    """Whole-job steps/s: the steps of all ranks over the slowest rank's time."""
+    return world * steps / seconds
+
+
 METRIC = "coupled_steps_per_s"
 UNIT = "steps/s"
 PROFILE_NOTE = os.path.join(ROOT, "profiles", "ncu_particle_pass_channel2048x512.md")
@@ -209,7 +231,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.Stream(device=dev)
-    params = dict(WORKLOAD["params"], seed=WORKLOAD["params"]["seed"] + 1000 * rank)
+    params = rank_params(WORKLOAD["params"], rank)
     p = WORKLOAD["params"]
     ab = algorithmic_bytes(p, WORKLOAD["region"])
 
@@ -250,10 +272,7 @@ def run_ours(args, rank, world, local_rank):
             launches = 6 * (args.steps // 64) + (2 if args.steps % 64 else 0)
         else:
             launches = 3 * args.steps + 5 * (args.steps // 64) + (1 if args.steps % 64 else 0)
-        t_max = torch.tensor([ms], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-        ms = float(t_max.item())
+        ms = max_over_ranks(ms, world, dev)
 
         # ---- per-kernel durations (events around every launch) ------------
         kprof = min(args.steps, 640)
@@ -280,12 +299,10 @@ def run_ours(args, rank, world, local_rank):
             torch.cuda.synchronize()
             t_e2e = time.perf_counter() - t0
             barrier()
-            tt = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
-            if world > 1:
-                dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t_e2e = max_over_ranks(t_e2e, world, dev)
             h2d = sum(t.numel() * t.element_size() for t in host_in.values())
             d2h = out_u.numel() * 8 + out_v.numel() * 8
-            e2e = {"value": world * args.steps / float(tt.item()), "unit": UNIT,
+            e2e = {"value": job_rate(args.steps, world, t_e2e), "unit": UNIT,
                    "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                    "note": "set_state of the full initial state from pinned host memory, K steps, "
                            "get_fields of U and particle velocities to pinned host memory"}
@@ -294,7 +311,7 @@ def run_ours(args, rank, world, local_rank):
 
     if rank != 0:
         return
-    steps_per_s = world * args.steps / (ms * 1e-3)
+    steps_per_s = job_rate(args.steps, world, ms * 1e-3)
     peaks = measured_peaks()
     hbm = float(peaks["hbm_gbs"]) if peaks else 6800.0
     step_bytes = ab["lb_pull"] + ab["particle_pass"] + ab["cell_pass"]
