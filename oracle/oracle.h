@@ -12,7 +12,10 @@
  *       D3Q19, half-way bounce-back walls (Sec. 3), Guo body force;
  *   a2  coarse->fine bilinear (trilinear) interpolation of u (Algorithm 2);
  *   a3  LB->MPCD Maxwellian redraw of outer-buffer particle velocities,
- *       Box-Muller normals (Sec. 2.3, Algorithm 1);
+ *       Box-Muller normals (Sec. 2.3, Algorithm 1), or with redraw = 1 the
+ *       Chapman-Enskog draw carrying the LB's non-equilibrium momentum flux
+ *       (the Enskog sampling Sec. 2.3 names); with resample_density = 1 the
+ *       outer-buffer particles are replaced instead;
  *   a4  MPCD streaming, Eq. 3, with body-force kick, bounce-back walls and
  *       periodic wrap inside the MPCD region (Sec. 2.3);
  *   a6  inner-buffer sampling of mass and momentum into a per-step frame;
@@ -22,6 +25,8 @@
  *       wall-cut cells;
  *   a8  MPCD->LB imposition of equilibrium populations built from the
  *       windowed cell moments on the inner buffer column.
+ * The MPCD region is a slab of whole columns with buffers at its x-ends, or
+ * (orc_set_strip) the near-wall strip of Sec. 3.3 with its buffer along y1.
  * With feedback = 2 (D2Q9 only; not in the paper) a8 is replaced by the
  * learned closure: each step records the instantaneous fine-cell fields of
  * the two 16-column strips at the region's x-edges, keeps the last 8 of them
