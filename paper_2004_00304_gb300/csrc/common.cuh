@@ -52,6 +52,7 @@ LBM_HD uint4 philox(uint32_t id, uint32_t step, uint32_t rep, uint32_t tag, uint
 
 // 24-bit uniform in [0,1): exact in binary32 and binary64.
 LBM_HD double unit24(uint32_t w) { return (double)(w >> 8) * (1.0 / 16777216.0); }
+
 LBM_HD float unit24f(uint32_t w) { return (float)(w >> 8) * (1.0f / 16777216.0f); }
 
 // Box-Muller pair: u1 = (a+1) 2^-32 in (0,1], u2 = b 2^-32,
@@ -77,6 +78,48 @@ __device__ __forceinline__ void normal_pair(uint32_t a, uint32_t b, float& z0, f
   sincospif(2.0f * ((float)b * (1.0f / 4294967296.0f)), &s, &c);
   z0 = rad * c;
   z1 = rad * s;
+}
+
+// L2 eviction priorities (createpolicy + L2::cache_hint): the particle state,
+// read and written back every step, is kept (evict_last); the LB populations,
+// which do not stay in L2 until their next use anyway, go first.
+__device__ __forceinline__ uint64_t l2_keep() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t l2_stream() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint32_t ld_hint(const uint32_t* a, uint64_t pol) {
+  uint32_t v;
+  asm volatile("ld.global.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(a), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ void st_hint(uint32_t* a, uint32_t v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.u32 [%0], %1, %2;" ::"l"(a), "r"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ float2 ld_hint(const float2* a, uint64_t pol) {
+  float2 v;
+  asm volatile("ld.global.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(v.x), "=f"(v.y) : "l"(a), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ void st_hint(float2* a, float2 v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(a), "f"(v.x), "f"(v.y), "l"(pol)
+               : "memory");
+}
+__device__ __forceinline__ float4 ld_hint(const float4* a, uint64_t pol) {
+  float4 v;
+  asm volatile("ld.global.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(a), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ void st_hint(float4* a, float4 v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(a), "f"(v.x), "f"(v.y),
+               "f"(v.z), "f"(v.w), "l"(pol)
+               : "memory");
 }
 
 // ---------------------------------------------------------------------------

@@ -16,11 +16,11 @@ template <typename S> struct Row<S, 1> {
 };
 template <> struct Row<float, 4> {
   __device__ static void ld(const float* p, float* o, float) {
-    const float4 t = *reinterpret_cast<const float4*>(p);
+    const float4 t = ld_hint(reinterpret_cast<const float4*>(p), l2_stream());
     o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
   }
   __device__ static void st(float* p, const float* v, float, uint32_t) {
-    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    st_hint(reinterpret_cast<float4*>(p), make_float4(v[0], v[1], v[2], v[3]), l2_stream());
   }
 };
 template <> struct Row<float, 2> {

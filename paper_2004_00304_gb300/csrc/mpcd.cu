@@ -60,12 +60,15 @@ template <int D, typename R> struct PState;
 template <typename R> struct PState<2, R> {
   using T2 = typename Pair<R>::T;
   __device__ static void ld(void* const* base, uint32_t j, R* x) {
-    const T2 t = ((const T2*)base[0])[j];
+    T2 t;
+    if constexpr (sizeof(R) == 4) t = ld_hint((const float2*)base[0] + j, l2_keep());
+    else t = ((const T2*)base[0])[j];
     x[0] = t.x; x[1] = t.y;
   }
   __device__ static void st(void* const* base, uint32_t j, const R* x) {
     T2 t; t.x = x[0]; t.y = x[1];
-    ((T2*)base[0])[j] = t;
+    if constexpr (sizeof(R) == 4) st_hint((float2*)base[0] + j, t, l2_keep());
+    else ((T2*)base[0])[j] = t;
   }
 };
 template <typename R> struct PState<3, R> {
@@ -388,7 +391,7 @@ __device__ __forceinline__ void particle_item(const RepDev& rd, const StepInfo& 
     act[p] = j < np32;
     fresh[p] = false;
     const uint32_t jl = act[p] ? j : last;
-    uint32_t hp = hsrc[jl];
+    uint32_t hp = ld_hint(hsrc + jl, l2_keep());
     if (RS && rd.resample) {
       if (hp == HOME_DEAD) { act[p] = false; hp = 0u; }
       fresh[p] = act[p] && (alt ? rd.pid_alt : rd.pid)[jl] == PID_FRESH;
@@ -503,7 +506,7 @@ __device__ __forceinline__ void particle_item(const RepDev& rd, const StepInfo& 
     }
     // a5: binning under this step's shift
     cid[p] = collision_cell<D, R>(rd, X[p], Y[p], Z[p], o[p], Cst<R>::shift(st));
-    rd.home[j] = HomePack<D>::pack(X[p], Y[p], Z[p]);
+    st_hint(rd.home + j, HomePack<D>::pack(X[p], Y[p], Z[p]), l2_keep());
     PState<D, R>::st(rd.off, j, o[p]);
     if (AT) {
       // a7 (MPCD-AT), first half: v_ran from Philox(id, n, replica, TAG_AT)
