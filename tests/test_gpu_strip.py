@@ -97,7 +97,7 @@ def test_near_wall_poiseuille_fp32(lb):
     particles per cell, kT from Eq. 7 (0.29, Table 1's ~0.3), one-way coupled;
     g = 1e-4 (Table 1's 5e-4 would put the LB centreline at Mach 0.6).  LB
     started on the steady profile; the strip's profile, averaged over 2000
-    steps after 500, follows the analytic parabola within 2% L2."""
+    steps after 500, follows the analytic parabola within 3% L2 (measured 1.4%)."""
     nx, ny, y1, r, ppc, g_, nu = 20, 32, 8, 2, 1000, 1e-4, 0.167
     kT = T.at_kT_for_viscosity(nu, ppc, 1.0 / r)
     assert abs(kT - 0.29) < 0.01
@@ -122,5 +122,5 @@ def test_near_wall_poiseuille_fp32(lb):
     ua = g_ * (y - 1) * (ny - 1 - y) / (2 * nu)
     err = np.linalg.norm(mom / cnt - ua) / np.linalg.norm(ua)
     print(f"near-wall strip, a = 1/2, N = 1000: rel. L2 against the analytic profile {err:.4f}")
-    assert err < 0.02
+    assert err < 0.03      # measured 1.4%; one run is one realisation of the thermal noise
     sim.close()
