@@ -161,6 +161,8 @@ struct orc_sim {
   long nbuf;                          /* inner-buffer LB nodes */
   double *frames;                     /* [W][nbuf][4] ring of per-step samples */
   double *wmean;                      /* [nbuf][4] rho_bar, u_bar of last step */
+  double *imp;                        /* [nbuf][4] imposition pending for the next LB update:
+                                         flag, u_bar (set by a8, applied by a1 of the next step) */
   long nframes;                       /* frames written so far */
   /* learned closure (feedback = 2): strips of CL_W fine columns per side */
   int cl_on, cl_npy;                  /* patches per side: ceil(Hy / 16) */
@@ -223,7 +225,7 @@ void orc_destroy(orc_sim* s) {
   if (!s) return;
   free(s->f); free(s->fn); free(s->rho); free(s->u); free(s->pi);
   free(s->home); free(s->off); free(s->vel); free(s->pcell);
-  free(s->cnt); free(s->sumv); free(s->vcm); free(s->vran); free(s->ranm); free(s->frames); free(s->wmean);
+  free(s->cnt); free(s->sumv); free(s->vcm); free(s->vran); free(s->ranm); free(s->frames); free(s->wmean); free(s->imp);
   free(s->cl_frame); free(s->cl_hist); free(s->cl_ema); free(s->cl_x);
   free(s);
 }
@@ -276,6 +278,7 @@ static int setup_region(orc_sim* s, int x0, int x1, int strip, int y1) {
   int W = p->window > 0 ? p->window : 1;
   s->frames = (double*)calloc((size_t)W * (s->nbuf > 0 ? s->nbuf : 1) * 4, sizeof(double));
   s->wmean = (double*)calloc((size_t)(s->nbuf > 0 ? s->nbuf : 1) * 4, sizeof(double));
+  s->imp = (double*)calloc((size_t)(s->nbuf > 0 ? s->nbuf : 1) * 4, sizeof(double));
   if (p->feedback == 2) {
     /* the closure needs two disjoint strips, 16 rows, an inner column inside
        the strip, LB nodes that do not straddle patches (r divides 16)
@@ -310,6 +313,24 @@ static int setup_region(orc_sim* s, int x0, int x1, int strip, int y1) {
   }
   s->nframes = 0;
   return 0;
+}
+
+/* LB node (x, y, z) of inner-buffer entry b: slab b = ((side n_in + col) nz
+ * + z)(ny - 2) + y - 1, col counted inwards from the region's edge; strip
+ * b = (row nz + z) nx + x, row counted down from the buffer's top. */
+static void buffer_node(const orc_sim* s, long b, int* x, int* y, int* z) {
+  const orc_params* p = &s->p;
+  long t = b;
+  if (s->strip) {
+    *x = (int)(t % p->nx); t /= p->nx;
+    *z = (int)(t % p->nz); t /= p->nz;
+    *y = s->y1 - 1 - s->n_out - (int)t;
+  } else {
+    *y = 1 + (int)(t % (p->ny - 2)); t /= (p->ny - 2);
+    *z = (int)(t % p->nz); t /= p->nz;
+    int col = (int)(t % s->n_in), side = (int)(t / s->n_in);
+    *x = side == 0 ? s->x0 + s->n_out + col : s->x1 - 1 - s->n_out - col;
+  }
 }
 
 /* ------------------------------------------------------------------------ */
@@ -380,6 +401,17 @@ static void lb_step(orc_sim* s) {
         s->f[i*s->nnode + nidx(s, x, 0, z)] = s->fn[i*s->nnode + nidx(s, x, 0, z)];
         s->f[i*s->nnode + nidx(s, x, p->ny-1, z)] = s->fn[i*s->nnode + nidx(s, x, p->ny-1, z)];
       }
+  /* a8 of the previous step, applied as the collision of the inner-buffer
+     nodes: their post-collision populations become f_eq(rho_LB, u_bar), rho_LB
+     the node's density of this update, u_bar the window mean a8 recorded */
+  for (long b = 0; b < s->nbuf; ++b) {
+    if (s->imp[4*b] == 0.0) continue;
+    int x, y, z;
+    buffer_node(s, b, &x, &y, &z);
+    double feq[19];
+    orc_feq(p->lattice, s->rho[nidx(s, x, y, z)], &s->imp[4*b+1], feq);
+    for (int i = 0; i < s->q; ++i) s->f[i * s->nnode + nidx(s, x, y, z)] = feq[i];
+  }
 }
 
 /* LB velocity with a ghost row behind each wall, u_ghost = -u_fluid, so that
@@ -801,13 +833,16 @@ static void collide_at(orc_sim* s) {
 }
 
 /* a8: on each inner-buffer LB node, rho_bar = rho0 M_W / (ppc m r^d W_n) and
- * u_bar = P_W / M_W from the last W_n = min(n+1, W) frames; the stored
- * post-collision populations become f_eq(rho_LB, u_bar) (Eq. 2), rho_LB being
- * the node's LB density of this step.  The MPCD density is reported, not
- * imposed: the two fluids have different equations of state (LB pressure
- * rho/3, MPCD pressure n kT), so MPCD density fluctuations imposed on the LB
- * become pressure gradients thousands of times too strong and the coupled
- * step diverges.  No imposition at the first step (n = 0). */
+ * u_bar = P_W / M_W from the last W_n = min(n+1, W) frames; the LB update of
+ * the next step (a1, lb_step) gives the node the post-collision populations
+ * f_eq(rho_LB, u_bar) (Eq. 2), rho_LB being the node's LB density of that
+ * update: the imposition acts as the collision rule of the inner-buffer
+ * nodes, since the frame of step n is complete only after step n's LB update.
+ * The MPCD density is reported, not imposed: the two fluids have different
+ * equations of state (LB pressure rho/3, MPCD pressure n kT), so MPCD density
+ * fluctuations imposed on the LB become pressure gradients thousands of times
+ * too strong and the coupled step diverges.  Nothing is imposed from the
+ * first step's window (n = 0). */
 static void impose(orc_sim* s) {
   const orc_params* p = &s->p;
   if (s->nbuf == 0) return;
@@ -824,23 +859,8 @@ static void impose(orc_sim* s) {
     double u[3] = {0, 0, 0};
     if (M > 0) { u[0] = P[0] / M; u[1] = P[1] / M; u[2] = P[2] / M; }
     s->wmean[4*b] = rho; s->wmean[4*b+1] = u[0]; s->wmean[4*b+2] = u[1]; s->wmean[4*b+3] = u[2];
-    if (!(p->feedback == 1 && s->step >= 1 && M > 0)) continue;
-    /* node coordinates of buffer entry b */
-    long t = b;
-    int x, y, z;
-    if (s->strip) {
-      x = (int)(t % p->nx); t /= p->nx;
-      z = (int)(t % p->nz); t /= p->nz;
-      y = s->y1 - 1 - s->n_out - (int)t;
-    } else {
-      y = 1 + (int)(t % (p->ny - 2)); t /= (p->ny - 2);
-      z = (int)(t % p->nz); t /= p->nz;
-      int col = (int)(t % s->n_in), side = (int)(t / s->n_in);
-      x = side == 0 ? s->x0 + s->n_out + col : s->x1 - 1 - s->n_out - col;
-    }
-    double feq[19];
-    orc_feq(p->lattice, s->rho[nidx(s, x, y, z)], u, feq);
-    for (int i = 0; i < s->q; ++i) s->f[i * s->nnode + nidx(s, x, y, z)] = feq[i];
+    s->imp[4*b] = (p->feedback == 1 && s->step >= 1 && M > 0) ? 1.0 : 0.0;
+    for (int a = 0; a < 3; ++a) s->imp[4*b+1+a] = u[a];
   }
 }
 

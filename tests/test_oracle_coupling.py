@@ -126,32 +126,36 @@ def test_window_is_mean_of_last_W_frames():
 
 
 def test_imposition_writes_equilibrium_of_window_mean():
-    """From the second step on, the inner-buffer populations are f_eq (Eq. 2)
-    at the node's LB density and the window-mean MPCD velocity: zeroth and
-    first moments equal rho_LB and rho_LB u_bar."""
+    """The window mean a8 records at step n is imposed by the LB update of
+    step n + 1: the inner-buffer populations after that update are f_eq
+    (Eq. 2) at the node's LB density of step n + 1 and the window-mean MPCD
+    velocity of step n, so their zeroth and first moments are rho_LB and
+    rho_LB u_bar.  Nothing is imposed from the window of step 0, so the first
+    imposed populations are those after step 2."""
     cfg = inputs.small_2d(feedback=1, window=3)
     p = cfg["params"]
     s = _sim(cfg)
     x0, x1 = cfg["region"]
     ny, nx = p["ny"], p["nx"]
-    for n in range(3):
+    c, _ = O.lattice(9)
+    wm_prev = None
+    for n in range(4):
         s.step(1)
         f = s.get("POPS").reshape(9, ny, nx)
-        wm = s.get("WINDOW_MEAN").reshape(-1, 4)
         rho = s.get("RHO").reshape(ny, nx)
-        c, _ = O.lattice(9)
         k = 0
         for xc in (x0 + 1, x1 - 2):
             for yy in range(1, ny - 1):
-                want = O.feq(9, rho[yy, xc], wm[k, 1:3])
-                if n > 0:
+                if n >= 2:
+                    want = O.feq(9, rho[yy, xc], wm_prev[k, 1:3])
                     assert abs(f[:, yy, xc].sum() - rho[yy, xc]) < 1e-14
-                    np.testing.assert_allclose(f[:, yy, xc] @ c[:, :2], rho[yy, xc] * wm[k, 1:3], atol=1e-16)
-                if n == 0:
-                    assert np.max(np.abs(f[:, yy, xc] - want)) > 1e-6
-                else:
+                    np.testing.assert_allclose(f[:, yy, xc] @ c[:, :2], rho[yy, xc] * wm_prev[k, 1:3], atol=1e-16)
                     np.testing.assert_allclose(f[:, yy, xc], want, rtol=0, atol=1e-15)
+                elif n == 1:
+                    want = O.feq(9, rho[yy, xc], wm_prev[k, 1:3])
+                    assert np.max(np.abs(f[:, yy, xc] - want)) > 1e-6
                 k += 1
+        wm_prev = s.get("WINDOW_MEAN").reshape(-1, 4)
 
 
 @pytest.mark.parametrize("case", ["2d", "3d"])

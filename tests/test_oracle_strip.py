@@ -117,26 +117,30 @@ def test_strip_sampling_counts_and_momentum(dim):
 
 
 def test_strip_imposition_on_the_inner_row():
-    """feedback = 1: from the second step on the inner-row populations are
-    f_eq(rho_LB, u_bar); no other row is touched by it."""
+    """feedback = 1: the window mean of step n is imposed on the inner row by
+    the LB update of step n + 1 (from the window of step 1 on): f_eq(rho_LB,
+    u_bar); no other row is touched by it."""
     cfg = inputs.small_2d(feedback=1, window=3)
     p = cfg["params"]
     ny, nx = p["ny"], p["nx"]
     y1 = 7
     s = _strip(cfg, y1)
     c, _ = O.lattice(9)
-    for n in range(3):
+    wm_prev = None
+    for n in range(4):
         s.step(1)
         f = s.get("POPS").reshape(9, ny, nx)
-        wm = s.get("WINDOW_MEAN").reshape(-1, 4)
         rho = s.get("RHO").reshape(ny, nx)
         for xx in range(0, nx, 5):
-            want = O.feq(9, rho[y1 - 2, xx], wm[xx, 1:3])
-            if n > 0:
+            if n >= 2:
+                want = O.feq(9, rho[y1 - 2, xx], wm_prev[xx, 1:3])
                 np.testing.assert_allclose(f[:, y1 - 2, xx], want, rtol=0, atol=1e-15)
-                np.testing.assert_allclose(f[:, y1 - 2, xx] @ c[:, :2], rho[y1 - 2, xx] * wm[xx, 1:3], atol=1e-16)
-            else:
+                np.testing.assert_allclose(f[:, y1 - 2, xx] @ c[:, :2], rho[y1 - 2, xx] * wm_prev[xx, 1:3],
+                                           atol=1e-16)
+            elif n == 1:
+                want = O.feq(9, rho[y1 - 2, xx], wm_prev[xx, 1:3])
                 assert np.max(np.abs(f[:, y1 - 2, xx] - want)) > 1e-6
+        wm_prev = s.get("WINDOW_MEAN").reshape(-1, 4)
 
 
 @pytest.mark.parametrize("dim", [2, 3])
