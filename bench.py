@@ -4,7 +4,9 @@ Workload: D2Q9 2048 x 512 channel (tau 0.8, g 1e-7, FP32 deviation storage),
 MPCD on the central 256 LB columns at refinement 2 (512 x 1020 cells, 10
 particles per cell, 5,222,400 particles), SRD 130 degrees, kT 1e-4, 2-column
 coupling buffers with the windowed MPCD -> LB feedback (W = 100).  One step =
-LB stream-collide + particle pass + cell pass.  Synthetic data only.
+LB stream-collide (whose launch also builds the previous step's collision-cell
+table and applies its MPCD -> LB imposition) + particle pass.  Synthetic data
+only.
 
 Prints one JSON line.  The device-timed value comes from CUDA events around
 lbmpcd_step(K) (graph replay) on the handle's stream, bracketed by a barrier
@@ -82,19 +84,41 @@ PROFILE_NOTE = os.path.join(ROOT, "profiles", "ncu_particle_pass_channel2048x512
 
 
 def algorithmic_bytes(p, region):
-    """Algorithmic HBM bytes per step of each kernel (FP32 storage, 2D).  MPCD-AT
-    reads each particle's id as well (its random velocity is keyed by it)."""
+    """Algorithmic HBM bytes per step of each kernel (FP32 storage, 2D): per LB
+    node 2 q 4 B (9 populations read and written), per particle its state read
+    and written (home 4 + offsets 8 + velocities 8, and the id 4 that keys the
+    MPCD-AT random velocity), per collision cell 2 (4 + 4 d) B = 24 B (count and
+    momentum sums written by the binning and read back for the table).  The
+    cell-table items run in the LB launch, so their bytes count there."""
     nx, ny, r, ppc = p["nx"], p["ny"], p["refine"], p["ppc"]
     fluid = nx * (ny - 2)
     Wx, Hy = (region[1] - region[0]) * r, (ny - 2) * r
     npart = Wx * Hy * ppc
     ncell = Wx * (Hy + 1)
     return dict(
-        lb_pull=72 * fluid,              # 9 populations read + 9 written, 4 B each
-        particle_pass=(44 if p.get("collision", 0) else 40) * npart,   # home 4 + offsets 8 + velocities 8,
-                                                                       # read and written (+ id 4 for MPCD-AT)
-        cell_pass=52 * ncell,            # accumulators read 12 + cleared 12, table written 16, read 12
+        lb_pull=72 * fluid + 24 * ncell,
+        particle_pass=(44 if p.get("collision", 0) else 40) * npart,
         fluid_nodes=fluid, particles=npart, cells=ncell)
+
+
+def step_launches(n0: int, last_sort: int, steps: int, mode: int, kchunk: int = 64):
+    """Kernel launches of lbmpcd_step(steps) from step n0 (the library's chunk
+    rule: chunks of 64 steps, then the powers of two below; a counting sort of
+    four kernels before a chunk once 64 steps have passed since the last one;
+    one prep kernel per chunk; two kernels per step, or one persistent kernel
+    per chunk).  Returns (launches, step count, last sort)."""
+    n, left, total = n0, steps, 0
+    while left > 0:
+        kc = kchunk
+        while kc > left:
+            kc //= 2
+        if n - last_sort >= kchunk:
+            total += 4
+            last_sort = n
+        total += 1 + (1 if mode == 1 else 2 * kc)
+        n += kc
+        left -= kc
+    return total, n, last_sort
 
 
 def measured_peaks():
@@ -171,11 +195,9 @@ def ncu_traffic_per_launch():
         return None
 
 
-def cpu_baseline(seconds: float = 12.0):
-    """The FP64 oracle, as it stands, on a bounded sample of the same workload:
-    a few full coupled steps of the whole 2048 x 512 system, single-threaded."""
+def _time_oracle(omp: bool, seconds: float):
     import oracle
-    s = oracle.OracleSim(WORKLOAD["params"])
+    s = oracle.OracleSim(WORKLOAD["params"], omp=omp)
     s.set_region(*WORKLOAD["region"])
     s.step(1)                       # warm-up
     t0 = time.perf_counter()
@@ -185,11 +207,24 @@ def cpu_baseline(seconds: float = 12.0):
         n += 1
         if time.perf_counter() - t0 > seconds:
             break
-    dt = time.perf_counter() - t0
-    return {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{n} full coupled steps of the {WORKLOAD['name']} workload (5.2M particles) after 1 "
-                      "warm-up step, "
-                      f"FP64, single thread, {dt:.1f} s"}
+    return n, time.perf_counter() - t0
+
+
+def cpu_baseline(seconds: float = 12.0):
+    """The FP64 oracle, as it stands, on a bounded sample of the same workload
+    (full coupled steps of the whole 2048 x 512 system): on all host cores
+    (its OpenMP build: LB nodes, particle streaming and redraw shared out, the
+    rest serial) and single-threaded."""
+    import oracle
+    n1, dt1 = _time_oracle(False, seconds)
+    nm, dtm = _time_oracle(True, seconds)
+    threads = oracle.num_threads(True)
+    return {"value": nm / dtm, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{nm} full coupled steps of the {WORKLOAD['name']} workload (5.2M particles) after 1 "
+                      f"warm-up step, FP64, {threads} threads (OpenMP over LB nodes, streaming and redraw), "
+                      f"{dtm:.1f} s",
+            "single_thread": {"value": n1 / dt1, "unit": UNIT, "cores": 1,
+                              "sample": f"{n1} full coupled steps, FP64, one thread, {dt1:.1f} s"}}
 
 
 def run_reference(args, rank, world):
@@ -253,6 +288,7 @@ def run_ours(args, rank, world, local_rank):
             host_in[nm] = t
         sim.step(args.warmup)
         stream.synchronize()
+        _, n_w, sort_w = step_launches(0, 0, args.warmup, launch["mode"])
 
         # ---- device-timed region: K steps of graph replay -----------------
         sampler = ClockSampler(local_rank) if rank == 0 else None
@@ -268,16 +304,13 @@ def run_ours(args, rank, world, local_rank):
         barrier()
         clocks = sampler.stop() if sampler else None
         ms = e0.elapsed_time(e1)
-        if launch["mode"] == 1:   # sort (4) + prep + one persistent kernel per chunk
-            launches = 6 * (args.steps // 64) + (2 if args.steps % 64 else 0)
-        else:
-            launches = 3 * args.steps + 5 * (args.steps // 64) + (1 if args.steps % 64 else 0)
+        launches, _, _ = step_launches(n_w, sort_w, args.steps, launch["mode"])
         ms = max_over_ranks(ms, world, dev)
 
         # ---- per-kernel durations (events around every launch) ------------
         kprof = min(args.steps, 640)
         phase_ms, nlaunch = sim.step_profiled(kprof)
-        per_launch = {k: phase_ms[k] / kprof for k in ("lb_pull", "particle_pass", "cell_pass")}
+        per_launch = {k: phase_ms[k] / kprof for k in ("lb_pull", "particle_pass")}
 
         # ---- e2e through the C ABI with host buffers ----------------------
         e2e = None
@@ -314,13 +347,13 @@ def run_ours(args, rank, world, local_rank):
     steps_per_s = job_rate(args.steps, world, ms * 1e-3)
     peaks = measured_peaks()
     hbm = float(peaks["hbm_gbs"]) if peaks else 6800.0
-    step_bytes = ab["lb_pull"] + ab["particle_pass"] + ab["cell_pass"]
+    step_bytes = ab["lb_pull"] + ab["particle_pass"]
     dom = "particle_pass"
     t_dom = per_launch[dom] * 1e-3
     achieved = ab[dom] / t_dom / 1e9
     traffic = ncu_traffic_per_launch() if not p.get("collision", 0) else None
     kernels = {}
-    for k in ("lb_pull", "particle_pass", "cell_pass"):
+    for k in ("lb_pull", "particle_pass"):
         t = per_launch[k] * 1e-3
         kernels[k] = {"us_per_launch": per_launch[k] * 1e3, "algorithmic_bytes": ab[k],
                       "achieved_gbs": ab[k] / t / 1e9 if t > 0 else None,
@@ -363,9 +396,9 @@ def run_slab3d(args):
     fluid = p["nx"] * (p["ny"] - 2) * p["nz"]
     Wx, Hy, Wz = (x1 - x0) * r, (p["ny"] - 2) * r, p["nz"] * r
     parts, cells = Wx * Hy * Wz * p["ppc"], Wx * (Hy + 1) * Wz
-    ab = dict(lb_pull=152 * fluid,          # 19 populations read + 19 written, 4 B each
-              particle_pass=56 * parts,     # home 4 + offsets 12 + velocities 12, read and written
-              cell_pass=64 * cells)         # accumulators read 16 + cleared 16, two table vectors written 32
+    ab = dict(lb_pull=152 * fluid + 32 * cells,   # 19 populations read + 19 written, 4 B each; cell
+                                                  # sums 2 (4 + 4 d) B, built in the same launch
+              particle_pass=56 * parts)           # home 4 + offsets 12 + velocities 12, read and written
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         sim = lb.Lbmpcd(p, stream=stream)
@@ -385,9 +418,9 @@ def run_slab3d(args):
     sps = args.steps / (ms * 1e-3)
     peaks = measured_peaks()
     hbm = float(peaks["hbm_gbs"]) if peaks else 6800.0
-    step_bytes = ab["lb_pull"] + ab["particle_pass"] + ab["cell_pass"]
+    step_bytes = ab["lb_pull"] + ab["particle_pass"]
     kernels = {}
-    for k in ("lb_pull", "particle_pass", "cell_pass"):
+    for k in ("lb_pull", "particle_pass"):
         t = phase_ms[k] / kprof * 1e-3
         kernels[k] = {"us_per_launch": t * 1e6, "algorithmic_bytes": ab[k], "achieved_gbs": ab[k] / t / 1e9,
                       "frac_of_measured_hbm": ab[k] / t / 1e9 / hbm}
@@ -448,7 +481,7 @@ def run_ensemble(args):
     cells = sum((r["region"][1] - r["region"][0]) * r["params"]["refine"] * ((r["params"]["ny"] - 2) * r["params"]["refine"] + 1)
                 for r in reps)
     pop_b = 36 if args.fp16 else 72
-    step_bytes = pop_b * nodes + 40 * parts + 52 * cells
+    step_bytes = pop_b * nodes + 40 * parts + 24 * cells
     peaks = measured_peaks()
     hbm = float(peaks["hbm_gbs"]) if peaks else 6800.0
     out = {"metric": METRIC, "value": sps, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,

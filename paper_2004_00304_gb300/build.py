@@ -26,7 +26,7 @@ SOURCES = {
     "closure.cu": [],
     "closure_coupling.cu": [],
 }
-HEADERS = ["common.cuh", "kernels.h", "tc_gemm.cuh", "net_fused.cuh", "lb_core.cuh"]
+HEADERS = ["common.cuh", "kernels.h", "tc_gemm.cuh", "net_fused.cuh", "lb_core.cuh", "cell_core.cuh"]
 
 
 def _nvcc() -> str:

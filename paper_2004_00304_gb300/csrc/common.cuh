@@ -226,7 +226,6 @@ struct RepDev {
   double* frame;           // [nbuf][4] this step's mass, momentum
   double* ring;            // [window][nbuf][4]
   double* wsum;            // [nbuf][4]
-  double* wmean;           // [nbuf][4] rho_bar, u_bar
   // learned closure (feedback = 2, 2D): strips of 16 fine columns per side,
   // strip cell c = (side Hy + row) 16 + xi
   int cl_on;               // strip sampling active
@@ -264,6 +263,7 @@ struct StepInfo {
   int pending;             // collision of step n-1 not yet applied to particles
   int write_moments;       // write rho/u on every node this step
   int src_alt;             // particle state of this step is in the *_alt (sorted) arrays
+  int cells;               // the collision-cell table of step n - 1 is still to be built (LB launch)
   double shift[3], prev[3];
   float shift_f[3], prev_f[3];   // the same shifts (exact in binary32)
 };

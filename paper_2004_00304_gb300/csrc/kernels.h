@@ -33,13 +33,16 @@ int lb_vector_width(int q, int prec, int nx);
 bool lb_tma_ok(int q, int prec, int vec);
 cudaError_t launch_lb(int q, int prec, int vec, bool tma, const Launch& L, const int4* bmap, int nblocks, int k);
 
-// prep: per-step records (shift, pending flag) for kcount steps.
-cudaError_t launch_prep(int dim, const Launch& L, StepInfo* si, int kcount, int sorted, uint32_t* d_step,
-                        int* d_pending, double* d_last_shift);
+// prep: per-step records (shift, pending flag) for kcount steps.  d_sorted[r]
+// (set by the sort, cleared here) says that replica r's current particle state
+// is the sorted copy in the *_alt arrays, which the chunk's first step reads.
+cudaError_t launch_prep(int dim, const Launch& L, StepInfo* si, int kcount, int* d_sorted, uint32_t* d_step,
+                        int* d_pending, int* d_cells, double* d_last_shift);
 
-// counting sort of the particles by home cell into the *_alt arrays.
+// counting sort of the particles by home cell into the *_alt arrays; sets
+// d_sorted[r] for every replica with a region.
 cudaError_t launch_sort(int dim, int prec, const Launch& L, const int2* bmap_p, int nb_p, const int2* bmap_t,
-                        int nb_t);
+                        int nb_t, int* d_sorted);
 
 // collision-cell table -> CELL_COUNT (field 7, int32) or CELL_VCM (field 11, [ncell][3] binary64).
 cudaError_t launch_tab_out(int dim, int prec, const RepDev& rd, int field, void* out, cudaStream_t st);
@@ -48,8 +51,12 @@ cudaError_t launch_tab_out(int dim, int prec, const RepDev& rd, int field, void*
 cudaError_t launch_particles(int dim, int prec, bool rs, bool at, bool ce, const Launch& L, const int2* bmap,
                              int nblocks, int k);
 
-// a7 cell part (v_cm, virtual particles, rotation draw) + a8 imposition.
-cudaError_t launch_cells(int q, int prec, const Launch& L, const int2* bmap, int nblocks, int k);
+// a7 cell part of step m (v_cm, virtual particles, rotation draw) for the
+// read-outs between calls (the step builds it inside the next LB launch).
+cudaError_t launch_cell_table(int q, int prec, const RepDev& rd, uint32_t m, bool shift_y_pos, cudaStream_t st);
+
+// WINDOW_MEAN after step m ([nbuf][4] binary64).
+cudaError_t launch_window_out(int dim, int prec, const RepDev& rd, uint32_t m, double* out, cudaStream_t st);
 
 // learned closure (feedback = 2): closure_in updates the strip ring and
 // moving averages (no parameters); closure_step does that, the network and
@@ -77,16 +84,18 @@ cudaError_t net_forward_resident(lbmpcd_net* n, int P, cudaStream_t st);
 ClosureNet net_closure(lbmpcd_net* n);
 int net_error(lbmpcd_net* n, cudaStream_t st);
 
-// persistent form of a chunk: kcount steps of lb_pull -> particle_pass ->
-// cell_pass in one cooperative launch with bounded grid barriers between
-// phases (bar: two zeroed words, err: set on a barrier timeout).  The LB map
-// has 256-thread row tiles.  blocks_per_sm <= 0 takes the occupancy limit.
+// persistent form of a chunk: kcount steps of lb_pull (with the cell-table
+// items) -> particle_pass in one cooperative launch with bounded grid
+// barriers between phases (bar: two zeroed words, err: set on a barrier
+// timeout, spin: polls before a barrier wait gives up, 0 for the default).
+// The LB map has 256-thread row tiles.  blocks_per_sm <= 0 takes the
+// occupancy limit.
 struct PersistentMaps {
   const int4* lb; int nb_lb;
   const int2* p; int nb_p;
-  const int2* c; int nb_c;
   unsigned* bar;
   int* err;
+  unsigned spin;
 };
 cudaError_t launch_persistent(int q, int prec, int vec, const Launch& L, int kcount, const PersistentMaps& m,
                               int blocks_per_sm, int* grid_out);

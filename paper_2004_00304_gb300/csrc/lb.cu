@@ -74,12 +74,16 @@ __device__ __forceinline__ void tl_copy(float* dst, const float* src, uint32_t b
 __device__ __forceinline__ void tl_issue(const RepDev* __restrict__ reps, const StepInfo* __restrict__ si, int k,
                                          int nrep, const int4 bm, float* stage, uint64_t* bar) {
   using L = Lattice<9>;
+  const uint32_t b = (uint32_t)__cvta_generic_to_shared(bar);
+  if (bm.y < 0) {   // a cell-table item: nothing to stage, complete the stage's phase
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(b) : "memory");
+    return;
+  }
   const RepDev& r = reps[bm.x];
   const int nx = r.nx, ny = r.ny, y = bm.z;
   const long long N = r.nnode;
   const float* src = (const float*)r.f[si[(long long)k * nrep + bm.x].n & 1];
   const int x0 = bm.y * TL_W, len = min(TL_W, nx - x0);
-  const uint32_t b = (uint32_t)__cvta_generic_to_shared(bar);
   asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(b),
                "r"((uint32_t)(9 * (len + 8) * 4))
                : "memory");
@@ -133,7 +137,11 @@ __global__ void __launch_bounds__(128) lb_pull_tma(const RepDev* __restrict__ re
       return;
     }
     const int x0 = bm.y * TL_W, len = min(TL_W, rd.nx - x0), xl = 4 * tid;
-    if (xl < len) {
+    if (bm.y < 0) {
+      if (st.cells)
+        cell_table_item<9, float>(rd, st.n - 1u, st.prev_f[1] > 0.0f, (long long)(-1 - bm.y) * blockDim.x * CPT,
+                                  rd.ncell);
+    } else if (xl < len) {
       const float* stage = tsm + s * 9 * TL_SEG;
       const int y = bm.z;
       float d[9][4];
@@ -151,7 +159,7 @@ __global__ void __launch_bounds__(128) lb_pull_tma(const RepDev* __restrict__ re
           d[i][0] = c.y; d[i][1] = c.z; d[i][2] = c.w; d[i][3] = seg[4];
         }
       }
-      lb_finish<9, float, 4>(rd, st, d, x0 + xl, rd.nx * y, y);
+      lb_finish<9, float, 4>(rd, st, d, x0 + xl, rd.nx * y, y, 0);
     }
     __syncthreads();   // every thread is done with stage s
     if (tid == 0) {

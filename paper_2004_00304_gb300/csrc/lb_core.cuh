@@ -1,7 +1,9 @@
 // lb_core.cuh -- the per-row LB update (a1) shared by the per-step lb_pull
-// kernel (lb.cu) and the persistent step kernel (mpcd.cu).
+// kernel (lb.cu) and the persistent step kernel (mpcd.cu).  The same launch
+// carries the collision-cell table of the previous step and its imposition
+// (cell_core.cuh).
 #pragma once
-#include "kernels.h"
+#include "cell_core.cuh"
 
 namespace lbm {
 
@@ -68,11 +70,12 @@ __device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 
 // Collision (BGK + Guo source, Eq. 1-2) of V consecutive nodes x0.. of the
-// row starting at node index `row`, whose arrived populations are d[i][v]; the
-// post-collision values go to the other buffer, rho / u where requested.
+// row (y, z) starting at node index `row`, whose arrived populations are
+// d[i][v]; the post-collision values go to the other buffer, rho / u where
+// requested.  Inner-buffer nodes take a8 of the previous step instead (below).
 template <int Q, typename S, int V>
 __device__ __forceinline__ void lb_finish(const RepDev& rd, const StepInfo& st, typename Store<S>::R (&d)[Q][V],
-                                          int x0, int row, int y) {
+                                          int x0, int row, int y, int z) {
   using L = Lattice<Q>;
   using R = typename Store<S>::R;
   const int nx = rd.nx;
@@ -150,6 +153,36 @@ __device__ __forceinline__ void lb_finish(const RepDev& rd, const StepInfo& st, 
       uv[2 * N + row + x] = mu[2][v];
     }
   }
+  // a8 of step m = n - 1 on the inner-buffer nodes: the window takes frame m
+  // (sampled by the particle pass of step m), and with feedback = 1 the node's
+  // post-collision populations become f_eq(rho_LB, u_bar) (Eq. 2) at its LB
+  // density of this update, written over the BGK values stored above (the
+  // populations are dead by now, which keeps this rare branch from adding to
+  // the row's register pressure); nothing is imposed from the window of step 0.
+  if (rd.nbuf > 0 && st.n >= 1u) {
+    const uint32_t m = st.n - 1u;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const long long b = inner_index(rd, x0 + v, y, z);
+      if (b < 0) continue;
+      double W4[4];
+      window_sums(rd, m, b, true, W4);
+      R rb, ub[3];
+      const R M = window_mean<L::D, R>(rd, m, W4, rb, ub);
+      if (rd.feedback == 1 && m >= 1u && M > R(0)) {
+        const R rl = mr[v];
+        const R uu = ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2];
+        const int node = row + x0 + v;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+          const R cu = L::cx(i) * ub[0] + L::cy(i) * ub[1] + L::cz(i) * ub[2];
+          const R dev = (R)L::w(i) * ((rl - R(1)) + rl * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu));
+          Store<S>::st(dst + i * N + node, dev, scale,
+                       sizeof(S) == 2 ? (mix32((uint32_t)node * 19u + (uint32_t)i + st.n * 0x632BE5ABu) | 1u) : 0u);
+        }
+      }
+    }
+  }
 }
 
 // One thread owns V consecutive nodes x0 .. x0+V-1 of one row (y, z); a
@@ -158,6 +191,11 @@ template <int Q, typename S, int V>
 __device__ __forceinline__ void lb_row(const RepDev& rd, const StepInfo& st, const int4 bm) {
   using L = Lattice<Q>;
   using R = typename Store<S>::R;
+  if (bm.y < 0) {   // item -1 - b: block b of blockDim CPT cells of the table of step n - 1
+    if (st.cells)
+      cell_table_item<Q, S>(rd, st.n - 1u, st.prev_f[1] > 0.0f, (long long)(-1 - bm.y) * blockDim.x * CPT, rd.ncell);
+    return;
+  }
   const int nx = rd.nx, ny = rd.ny, nz = rd.nz;
   const int y = bm.z, z = bm.w;
   const int tpr = nx / V;
@@ -222,7 +260,7 @@ __device__ __forceinline__ void lb_row(const RepDev& rd, const StepInfo& st, con
     }
   }
   if (!active) return;
-  lb_finish<Q, S, V>(rd, st, d, x0, row, y);
+  lb_finish<Q, S, V>(rd, st, d, x0, row, y, z);
 }
 
 }  // namespace lbm

@@ -4,9 +4,13 @@
 // allocations described by a RepDev record; one device table of these records
 // plus a block map per kernel family lets a single launch of each kernel
 // cover all replicas.  lbmpcd_step runs the per-step sequence
-//     lb_pull -> particle_pass -> cell_pass
-// in chunks of KCHUNK steps; each full chunk (a prep kernel plus the 3 kernels
-// per step) is captured once into a CUDA graph and replayed.  With the learned
+//     lb_pull -> particle_pass
+// (the LB launch of step n also builds the collision-cell table of step n - 1
+// and applies its MPCD -> LB imposition) in chunks of KCHUNK steps and, for what is left of a call, of the powers of
+// two below KCHUNK; each chunk length (a prep kernel plus the 3 kernels per
+// step) is captured once into a CUDA graph and replayed, so that calls of any
+// length run from graphs.  The particles are sorted by home cell whenever
+// KCHUNK steps have passed since the last sort, between chunks.  With the learned
 // closure (feedback = 2) each step adds one kernel: closure_in (sampling only)
 // or, with parameters loaded, closure_step (sampling, the network over the
 // patches of all replicas, imposition).
@@ -25,7 +29,8 @@
 using namespace lbm;
 
 namespace {
-constexpr int KCHUNK = 64;   // steps per captured graph (and per particle sort)
+constexpr int KCHUNK = 64;   // longest captured chunk; steps between particle sorts
+constexpr int NGRAPH = 7;    // chunk graphs of 1, 2, 4, ..., KCHUNK steps
 thread_local std::string g_create_error;
 }  // namespace
 
@@ -38,7 +43,7 @@ struct lbmpcd {
   std::vector<void*> allocs;                    // handle-wide
   RepDev* d_reps = nullptr;
   int4* bm_lb = nullptr;
-  int2 *bm_p = nullptr, *bm_c = nullptr, *bm_t = nullptr, *bm_cl = nullptr;
+  int2 *bm_p = nullptr, *bm_t = nullptr, *bm_cl = nullptr;
   int4* ptab = nullptr;                         // closure patches of the batch: (replica, side, py)
   int4* bm_lb256 = nullptr;                     // LB map with 256-thread row tiles (persistent kernel)
   int nb_lb256 = 0;
@@ -51,7 +56,8 @@ struct lbmpcd {
   int pers_bps = 0;                             // persistent blocks per SM (0: occupancy limit)
   bool pers_graph = true;                       // the persistent launch captures into a graph
   unsigned* d_bar = nullptr;                    // grid barrier: count, generation, error
-  int nb_lb = 0, nb_p = 0, nb_c = 0, nb_t = 0, nb_cl = 0, n_ptab = 0;
+  unsigned bar_spin = 0;                        // polls before a barrier wait gives up (0: default)
+  int nb_lb = 0, nb_p = 0, nb_t = 0, nb_cl = 0, n_ptab = 0;
   lbmpcd_net* net = nullptr;                    // learned closure, batch of all replicas' patches
   int cl_P = 0;                                 // patches in the batch
   bool cl_params = false;                       // parameters loaded: impose from the network
@@ -59,12 +65,17 @@ struct lbmpcd {
   StepInfo* d_si = nullptr;
   uint32_t* d_step = nullptr;
   int* d_pending = nullptr;
+  int* d_cells = nullptr;                       // per replica: the cell table of the last step is not built yet
   double* d_last_shift = nullptr;
   int* d_flag = nullptr;
   long long nstep = 0;
   bool maps_dirty = true;
   std::vector<char> pending;                    // host mirror of d_pending
-  cudaGraphExec_t graph = nullptr;
+  std::vector<char> cells;                      // host mirror of d_cells
+  cudaGraphExec_t graphs[NGRAPH] = {};          // chunk of 2^i steps
+  bool graphs_ready = false;
+  int* d_sorted = nullptr;                      // per replica: the sort ran since the last chunk
+  long long last_sort = 0;                      // step count at the last sort (the seeded state is sorted)
   std::string err;
 };
 
@@ -98,10 +109,17 @@ static void free_list(std::vector<void*>& list) {
   list.clear();
 }
 
+// the captured chunks hold the kernels' arguments: drop them when those change
+static void drop_graphs(lbmpcd* h) {
+  for (auto& g : h->graphs)
+    if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+  h->graphs_ready = false;
+}
+
 extern "C" void lbmpcd_destroy(lbmpcd* h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream); else cudaDeviceSynchronize();
-  if (h->graph) cudaGraphExecDestroy(h->graph);
+  drop_graphs(h);
   if (h->net) lbmpcd_net_destroy(h->net);
   for (auto& l : h->rep_allocs) free_list(l);
   free_list(h->allocs);
@@ -165,6 +183,7 @@ extern "C" int lbmpcd_create(const lbmpcd_params* params, int n_replicas, void* 
   h->rd.resize(n_replicas);
   h->rep_allocs.resize(n_replicas);
   h->pending.assign(n_replicas, 0);
+  h->cells.assign(n_replicas, 0);
   const size_t ss = store_size(h->prec), rs = real_size(h->prec);
   h->lbvec = 4;
   for (int r = 0; r < n_replicas; ++r) h->lbvec = std::min(h->lbvec, lb_vector_width(h->q, h->prec, params[r].nx));
@@ -211,6 +230,8 @@ extern "C" int lbmpcd_create(const lbmpcd_params* params, int n_replicas, void* 
   if (e == cudaSuccess) { e = dalloc(h->allocs, &tmp, sizeof(StepInfo) * KCHUNK * n_replicas); h->d_si = (StepInfo*)tmp; }
   if (e == cudaSuccess) { e = dalloc(h->allocs, &tmp, sizeof(uint32_t)); h->d_step = (uint32_t*)tmp; }
   if (e == cudaSuccess) { e = dalloc(h->allocs, &tmp, sizeof(int) * n_replicas); h->d_pending = (int*)tmp; }
+  if (e == cudaSuccess) { e = dalloc(h->allocs, &tmp, sizeof(int) * n_replicas); h->d_sorted = (int*)tmp; }
+  if (e == cudaSuccess) { e = dalloc(h->allocs, &tmp, sizeof(int) * n_replicas); h->d_cells = (int*)tmp; }
   if (e == cudaSuccess) { e = dalloc(h->allocs, &tmp, sizeof(double) * 3 * n_replicas); h->d_last_shift = (double*)tmp; }
   if (e == cudaSuccess) { e = dalloc(h->allocs, &tmp, sizeof(int) * 16); h->d_flag = (int*)tmp; }
   if (e == cudaSuccess) { e = dalloc(h->allocs, &tmp, sizeof(unsigned) * 4); h->d_bar = (unsigned*)tmp; }
@@ -225,9 +246,11 @@ extern "C" int lbmpcd_create(const lbmpcd_params* params, int n_replicas, void* 
 }
 
 // Block maps, one work item per entry, each replica's items contiguous:
-// LB (replica, tile, y, z); particles / sort (replica, block of PP_ITEM
-// particles); cells (replica, block of 256 CPT cells, or -1-b for block b of 256
-// inner-buffer nodes); sort tiles (replica, tile of SORT_TILE home cells).
+// LB (replica, tile, y, z), preceded by the replica's cell-table items
+// (replica, -1 - b, 0, 0) for block b of blockDim CPT collision cells (the
+// table of the previous step, built in the same launch); particles / sort
+// (replica, block of PP_ITEM particles); sort tiles (replica, tile of
+// SORT_TILE home cells).
 template <typename T>
 static int upload_map(lbmpcd* h, T** dst, int* cnt, const std::vector<T>& src) {
   if (*dst) {
@@ -278,10 +301,14 @@ static int build_maps(lbmpcd* h) {
   int rc0 = closure_batch(h);
   if (rc0) return rc0;
   std::vector<int4> lb;
-  std::vector<int2> pp, cc, tt, cl, sp;
+  std::vector<int2> pp, tt, cl, sp;
   std::vector<int4> pt, lb256;
   for (int r = 0; r < h->nrep; ++r) {
     const RepDev& d = h->rd[r];
+    if (d.has_region) {   // cell-table items first: their accumulators are still in L2
+      for (long long b = 0; b < (d.ncell + 128 * CPT - 1) / (128 * CPT); ++b) lb.push_back(make_int4(r, (int)(-1 - b), 0, 0));
+      for (long long b = 0; b < (d.ncell + 256 * CPT - 1) / (256 * CPT); ++b) lb256.push_back(make_int4(r, (int)(-1 - b), 0, 0));
+    }
     const int ntx = (d.nx / h->lbvec + 127) / 128;
     for (int z = 0; z < d.nz; ++z)
       for (int y = 1; y < d.ny - 1; ++y)
@@ -292,10 +319,8 @@ static int build_maps(lbmpcd* h) {
         for (int t = 0; t < ntx256; ++t) lb256.push_back(make_int4(r, t, y, z));
     if (!d.has_region) continue;
     const long long nslot = d.resample ? (long long)d.cap : d.np;
-    const long long npb = (nslot + PP_ITEM - 1) / PP_ITEM, ncb = (d.ncell + 256 * CPT - 1) / (256 * CPT), nbb = (d.nbuf + 255) / 256;
+    const long long npb = (nslot + PP_ITEM - 1) / PP_ITEM;
     for (long long b = 0; b < npb; ++b) pp.push_back(make_int2(r, (int)b));
-    for (long long b = 0; b < nbb; ++b) cc.push_back(make_int2(r, (int)(-1 - b)));   // a8 blocks first
-    for (long long b = 0; b < ncb; ++b) cc.push_back(make_int2(r, (int)b));
     for (int b = 0; b < d.ntile; ++b) tt.push_back(make_int2(r, b));
     if (d.resample) {
       const long long nouter = (long long)(d.xo_lo + (d.Wx - d.xo_hi)) * d.Hy * d.Wz;
@@ -310,7 +335,6 @@ static int build_maps(lbmpcd* h) {
   }
   int rc = upload_map(h, &h->bm_lb, &h->nb_lb, lb);
   if (!rc) rc = upload_map(h, &h->bm_p, &h->nb_p, pp);
-  if (!rc) rc = upload_map(h, &h->bm_c, &h->nb_c, cc);
   if (!rc) rc = upload_map(h, &h->bm_t, &h->nb_t, tt);
   if (!rc) rc = upload_map(h, &h->bm_cl, &h->nb_cl, cl);
   if (!rc) rc = upload_map(h, &h->ptab, &h->n_ptab, pt);
@@ -318,7 +342,7 @@ static int build_maps(lbmpcd* h) {
   if (!rc) rc = upload_map(h, &h->bm_s, &h->nb_s, sp);
   if (rc) return rc;
   CK(h, cudaMemcpy(h->d_reps, h->rd.data(), sizeof(RepDev) * h->nrep, cudaMemcpyHostToDevice));
-  if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
+  drop_graphs(h);
   h->maps_dirty = false;
   return LBMPCD_OK;
 }
@@ -432,7 +456,6 @@ extern "C" int lbmpcd_set_region(lbmpcd* h, int replica, const int lo[3], const 
   A(*(void**)&d.frame, nb4 * 8);
   A(*(void**)&d.ring, nb4 * 8 * (long long)p.window);
   A(*(void**)&d.wsum, nb4 * 8);
-  A(*(void**)&d.wmean, nb4 * 8);
   if (p.feedback == 2) {
     const long long ncl = 2LL * d.Hy * 16;
     A(*(void**)&d.cframe, 2 * ncl * 4 * 8);
@@ -462,19 +485,15 @@ extern "C" int lbmpcd_set_region(lbmpcd* h, int replica, const int lo[3], const 
   return LBMPCD_OK;
 }
 
-// One chunk of kcount steps.  Full (graph) chunks start with the counting
-// sort of the particles; the chunk's first particle pass reads the sorted copy.
+// One chunk of kcount steps (the sort, when due, runs before it: run_sort).
 static bool persistent(const lbmpcd* h) { return h->mode == 1 && h->nb_cl == 0; }
 
-static int run_chunk(lbmpcd* h, int kcount, bool sort) {
+static int run_chunk(lbmpcd* h, int kcount) {
   Launch L{h->d_reps, h->nrep, h->d_si, h->stream, h->d_flag + 8, h->rd.data()};
-  // density resampling compacts its particle pool at the start of every chunk
-  sort = (sort || h->nb_s > 0) && h->nb_p > 0;
-  if (sort) CK(h, launch_sort(h->dim, h->prec, L, h->bm_p, h->nb_p, h->bm_t, h->nb_t));
-  CK(h, launch_prep(h->dim, L, h->d_si, kcount, sort ? 1 : 0, h->d_step, h->d_pending, h->d_last_shift));
+  CK(h, launch_prep(h->dim, L, h->d_si, kcount, h->d_sorted, h->d_step, h->d_pending, h->d_cells,
+                    h->d_last_shift));
   if (persistent(h)) {
-    const PersistentMaps m{h->bm_lb256, h->nb_lb256, h->bm_p, h->nb_p, h->bm_c, h->nb_c, h->d_bar,
-                           (int*)(h->d_bar + 2)};
+    const PersistentMaps m{h->bm_lb256, h->nb_lb256, h->bm_p, h->nb_p, h->d_bar, (int*)(h->d_bar + 2), h->bar_spin};
     CK(h, launch_persistent(h->q, h->prec, h->lbvec, L, kcount, m, h->pers_bps, nullptr));
     return LBMPCD_OK;
   }
@@ -482,7 +501,6 @@ static int run_chunk(lbmpcd* h, int kcount, bool sort) {
     CK(h, launch_lb(h->q, h->prec, h->lbvec, h->lb_tma, L, h->bm_lb, h->nb_lb, k));
     if (h->nb_s) CK(h, launch_spawn(h->dim, h->prec, L, h->bm_s, h->nb_s, k));
     CK(h, launch_particles(h->dim, h->prec, h->nb_s > 0, h->at, h->ce, L, h->bm_p, h->nb_p, k));
-    CK(h, launch_cells(h->q, h->prec, L, h->bm_c, h->nb_c, k));
     if (h->nb_cl) {
       if (h->cl_params) CK(h, launch_closure_step(h->prec, L, h->ptab, h->n_ptab, k, net_closure(h->net)));
       else CK(h, launch_closure_in(L, h->bm_cl, h->nb_cl, k));
@@ -491,56 +509,97 @@ static int run_chunk(lbmpcd* h, int kcount, bool sort) {
   return LBMPCD_OK;
 }
 
+// The counting sort of the particles by home cell is due before a chunk when
+// KCHUNK steps have passed since the last one (it keeps the particles of a
+// warp in a few neighbouring cells; the seeded state is sorted); density
+// resampling compacts its particle pool with it before every chunk.
+static bool sort_due(const lbmpcd* h) {
+  if (h->nb_p == 0) return false;
+  return h->nb_s > 0 || h->nstep - h->last_sort >= KCHUNK;
+}
+
+static int run_sort(lbmpcd* h) {
+  Launch L{h->d_reps, h->nrep, h->d_si, h->stream, h->d_flag + 8, h->rd.data()};
+  CK(h, launch_sort(h->dim, h->prec, L, h->bm_p, h->nb_p, h->bm_t, h->nb_t, h->d_sorted));
+  h->last_sort = h->nstep;
+  return LBMPCD_OK;
+}
+
+// Capture the chunk of 2^i steps into graphs[i] on a capturing stream.
+static int capture_chunk(lbmpcd* h, int i) {
+  cudaGraph_t g = nullptr;
+  cudaStream_t cap = h->stream;
+  bool own = false;
+  if (!cap) { CK(h, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking)); own = true; }
+  if (own) CK(h, cudaDeviceSynchronize());
+  CK(h, cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+  cudaStream_t keep = h->stream;
+  h->stream = cap;
+  int rc = run_chunk(h, 1 << i);
+  h->stream = keep;
+  cudaError_t e = cudaStreamEndCapture(cap, &g);
+  if (!rc && e == cudaSuccess) {
+    e = cudaGraphInstantiate(&h->graphs[i], g, 0);
+    if (e != cudaSuccess) h->graphs[i] = nullptr;
+  }
+  if (g) cudaGraphDestroy(g);
+  if (own) cudaStreamDestroy(cap);
+  if (rc) return rc;
+  if (e != cudaSuccess || !h->graphs[i]) return cuda_fail(h, e != cudaSuccess ? e : cudaErrorUnknown, "graph capture");
+  return LBMPCD_OK;
+}
+
+// Every chunk length is captured at the first step after the maps were
+// (re)built, so that no later call pays for a capture.
+static int capture_all(lbmpcd* h) {
+  for (int i = 0; i < NGRAPH; ++i) {
+    const int rc = capture_chunk(h, i);
+    if (rc) {
+      drop_graphs(h);
+      if (!persistent(h)) return rc;
+      // the cooperative launch did not capture: launch the persistent chunks directly
+      cudaGetLastError();
+      h->pers_graph = false;
+      h->err.clear();
+      return LBMPCD_OK;
+    }
+  }
+  h->graphs_ready = true;
+  return LBMPCD_OK;
+}
+
+static int chunk_len(int left) {
+  int kc = KCHUNK;
+  while (kc > left) kc >>= 1;
+  return kc;
+}
+
+static int log2i(int v) { int i = 0; while ((1 << i) < v) ++i; return i; }
+
 extern "C" int lbmpcd_step(lbmpcd* h, int nsteps) {
   if (!h) return LBMPCD_ERR_INVALID_ARG;
   if (nsteps < 0) return fail(h, LBMPCD_ERR_INVALID_ARG, "nsteps < 0");
   if (h->maps_dirty) { int rc = build_maps(h); if (rc) return rc; }
+  const bool use_graph = !persistent(h) || h->pers_graph;
+  if (nsteps > 0 && use_graph && !h->graphs_ready) {
+    const int rc = capture_all(h);
+    if (rc) return rc;
+  }
   int left = nsteps;
-  while (left >= KCHUNK) {
-    const bool use_graph = !persistent(h) || h->pers_graph;
-    if (use_graph && !h->graph) {
-      cudaGraph_t g = nullptr;
-      cudaStream_t cap = h->stream;
-      bool own = false;
-      if (!cap) { CK(h, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking)); own = true; }
-      if (own) CK(h, cudaDeviceSynchronize());
-      CK(h, cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-      cudaStream_t keep = h->stream;
-      h->stream = cap;
-      int rc = run_chunk(h, KCHUNK, true);
-      h->stream = keep;
-      cudaError_t e = cudaStreamEndCapture(cap, &g);
-      if (!rc && e == cudaSuccess) {
-        e = cudaGraphInstantiate(&h->graph, g, 0);
-        if (e != cudaSuccess) h->graph = nullptr;
-      }
-      if (g) cudaGraphDestroy(g);
-      if (own) cudaStreamDestroy(cap);
-      if (rc || e != cudaSuccess || !h->graph) {
-        if (!persistent(h)) return rc ? rc : cuda_fail(h, e, "graph capture");
-        // the cooperative launch did not capture: launch the persistent chunks directly
-        cudaGetLastError();
-        h->pers_graph = false;
-        h->graph = nullptr;
-        continue;
-      }
-    }
-    if (use_graph) {
-      CK(h, cudaGraphLaunch(h->graph, h->stream));
+  while (left > 0) {
+    const int kc = chunk_len(left);
+    if (sort_due(h)) { const int rc = run_sort(h); if (rc) return rc; }
+    if (h->graphs_ready) {
+      CK(h, cudaGraphLaunch(h->graphs[log2i(kc)], h->stream));
     } else {
-      int rc = run_chunk(h, KCHUNK, true);
+      const int rc = run_chunk(h, kc);
       if (rc) return rc;
     }
-    left -= KCHUNK;
-    h->nstep += KCHUNK;
-  }
-  if (left > 0) {
-    int rc = run_chunk(h, left, false);
-    if (rc) return rc;
-    h->nstep += left;
+    left -= kc;
+    h->nstep += kc;
   }
   if (nsteps > 0)
-    for (int r = 0; r < h->nrep; ++r) h->pending[r] = h->rd[r].has_region ? 1 : 0;
+    for (int r = 0; r < h->nrep; ++r) h->pending[r] = h->cells[r] = h->rd[r].has_region ? 1 : 0;
   if (nsteps > 0 && h->cl_params) {   // a bounded wait inside a closure GEMM gave up
     const int rc = net_error(h->net, h->stream);
     if (rc) return fail(h, rc, "closure network: a tensor-core wait timed out");
@@ -580,7 +639,7 @@ extern "C" int lbmpcd_step_profiled(lbmpcd* h, int nsteps, double* phase_ms, lon
   int left = nsteps;
   cudaError_t e = cudaSuccess;
   while (left > 0 && e == cudaSuccess) {
-    const int kc = left < KCHUNK ? left : KCHUNK;
+    const int kc = chunk_len(left);
     int ie = 0;
     std::vector<int> phase;
     auto bracket = [&](int ph, auto&& fn) {
@@ -591,15 +650,16 @@ extern "C" int lbmpcd_step_profiled(lbmpcd* h, int nsteps, double* phase_ms, lon
       phase.push_back(ph);
       ++nl;
     };
-    const bool sort = (kc == KCHUNK || h->nb_s > 0) && h->nb_p > 0;
-    if (sort) bracket(4, [&] { return launch_sort(h->dim, h->prec, L, h->bm_p, h->nb_p, h->bm_t, h->nb_t); });
-    bracket(0, [&] { return launch_prep(h->dim, L, h->d_si, kc, sort ? 1 : 0, h->d_step, h->d_pending,
-                                        h->d_last_shift); });
+    if (sort_due(h)) {
+      bracket(4, [&] { return launch_sort(h->dim, h->prec, L, h->bm_p, h->nb_p, h->bm_t, h->nb_t, h->d_sorted); });
+      h->last_sort = h->nstep;
+    }
+    bracket(0, [&] { return launch_prep(h->dim, L, h->d_si, kc, h->d_sorted, h->d_step, h->d_pending,
+                                        h->d_cells, h->d_last_shift); });
     for (int k = 0; k < kc; ++k) {
       bracket(1, [&] { return launch_lb(h->q, h->prec, h->lbvec, h->lb_tma, L, h->bm_lb, h->nb_lb, k); });
       if (h->nb_s) bracket(2, [&] { return launch_spawn(h->dim, h->prec, L, h->bm_s, h->nb_s, k); });
       if (h->nb_p) bracket(2, [&] { return launch_particles(h->dim, h->prec, h->nb_s > 0, h->at, h->ce, L, h->bm_p, h->nb_p, k); });
-      if (h->nb_c) bracket(3, [&] { return launch_cells(h->q, h->prec, L, h->bm_c, h->nb_c, k); });
       if (h->nb_cl)
         bracket(5, [&] {
           return h->cl_params ? launch_closure_step(h->prec, L, h->ptab, h->n_ptab, k, net_closure(h->net))
@@ -619,7 +679,7 @@ extern "C" int lbmpcd_step_profiled(lbmpcd* h, int nsteps, double* phase_ms, lon
   for (auto& x : ev) cudaEventDestroy(x);
   if (e != cudaSuccess) rc = cuda_fail(h, e, "step_profiled");
   if (nsteps > 0)
-    for (int r = 0; r < h->nrep; ++r) h->pending[r] = h->rd[r].has_region ? 1 : 0;
+    for (int r = 0; r < h->nrep; ++r) h->pending[r] = h->cells[r] = h->rd[r].has_region ? 1 : 0;
   if (launches) *launches += nl;
   return rc;
 }
@@ -672,8 +732,25 @@ extern "C" long long lbmpcd_field_size(const lbmpcd* h, int replica, int field) 
   return n < 0 ? LBMPCD_ERR_INVALID_ARG : n;
 }
 
+// The collision-cell table of the last step, which the step builds only in
+// the next LB launch, for a read-out or the flush below.
+static int cells_if_pending(lbmpcd* h, int r) {
+  if (!h->cells[r] || !h->rd[r].has_region) return LBMPCD_OK;
+  double ls[3];
+  CK(h, cudaMemcpyAsync(ls, h->d_last_shift + 3 * r, sizeof(ls), cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  CK(h, launch_cell_table(h->q, h->prec, h->rd[r], (uint32_t)(h->nstep - 1), (float)ls[1] > 0.0f, h->stream));
+  CK(h, cudaMemsetAsync(h->d_cells + r, 0, sizeof(int), h->stream));
+  h->cells[r] = 0;
+  return LBMPCD_OK;
+}
+
+// Apply the collision of the last step to the particles (the step leaves it
+// to the next particle pass) before their state is read or replaced.
 static int flush_if_pending(lbmpcd* h, int r) {
   if (!h->pending[r] || !h->rd[r].has_region) return LBMPCD_OK;
+  const int rc = cells_if_pending(h, r);
+  if (rc) return rc;
   double ls[3];
   CK(h, cudaMemcpyAsync(ls, h->d_last_shift + 3 * r, sizeof(ls), cudaMemcpyDeviceToHost, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
@@ -738,10 +815,12 @@ extern "C" int lbmpcd_get_fields(lbmpcd* h, int replica, int field, void* dst, s
       break;
     case LBMPCD_CELL_COUNT:
     case LBMPCD_CELL_VCM:
-      e = launch_tab_out(h->dim, h->prec, d, field, buf, h->stream);
+      rc = cells_if_pending(h, replica);
+      if (!rc) e = launch_tab_out(h->dim, h->prec, d, field, buf, h->stream);
       break;
     case LBMPCD_WINDOW_MEAN:
-      e = cudaMemcpyAsync(buf, d.wmean, d.nbuf * 4 * 8, cudaMemcpyDeviceToDevice, h->stream);
+      if (h->nstep == 0) e = cudaMemsetAsync(buf, 0, d.nbuf * 4 * 8, h->stream);
+      else e = launch_window_out(h->dim, h->prec, d, (uint32_t)(h->nstep - 1), (double*)buf, h->stream);
       break;
     case LBMPCD_CLOSURE_IN:
       e = launch_closure_in_out(d, (uint32_t)(h->nstep - 1), (double*)buf, h->stream);
@@ -849,7 +928,14 @@ extern "C" int lbmpcd_set_closure(lbmpcd* h, const float* theta, long long count
     if (rc) return fail(h, rc, "loading the closure parameters");
     h->cl_params = true;
   }
-  if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }   // the step's kernels changed
+  drop_graphs(h);   // the step's kernels changed
+  return LBMPCD_OK;
+}
+
+extern "C" int lbmpcd_set_wait_limit(lbmpcd* h, unsigned polls) {
+  if (!h) return LBMPCD_ERR_INVALID_ARG;
+  h->bar_spin = polls;
+  drop_graphs(h);   // the persistent kernel takes the limit as an argument
   return LBMPCD_OK;
 }
 
@@ -867,7 +953,7 @@ extern "C" int lbmpcd_set_launch_mode(lbmpcd* h, int mode, int blocks_per_sm, in
   h->pers_bps = blocks_per_sm;
   h->lb_tma = (flags & LBMPCD_LAUNCH_LB_TMA) && lb_tma_ok(h->q, h->prec, h->lbvec);
   h->pers_graph = true;
-  if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
+  drop_graphs(h);
   return LBMPCD_OK;
 }
 

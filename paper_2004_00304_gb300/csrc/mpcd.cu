@@ -1,6 +1,6 @@
 // mpcd.cu -- the MPCD half of the coupled step and both coupling directions.
 //
-// Per step n the handle runs   lb_pull(n) -> particle_pass(n) -> cell_pass(n):
+// Per step n the handle runs   lb_pull(n) -> particle_pass(n):
 //   particle_pass  one thread per particle, structure-of-arrays state
 //                  (packed integer home cell, offsets, velocities):
 //                    a7(n-1)  rotate v about the v_cm of its collision cell
@@ -16,10 +16,11 @@
 //                    a5       binning under the step's random shift and a
 //                             warp-aggregated reduction (__match_any_sync
 //                             groups, one atomic per group and cell);
-//   cell_pass      one thread per collision cell: v_cm with virtual wall
-//                  particles, rotation draw (Eq. 4), accumulators cleared;
-//                  extra blocks run a8: window-mean MPCD velocity of the
-//                  inner buffer -> f_eq(rho_LB, u_bar) written into the LB buffer.
+//   lb_pull(n + 1) carries the cell half of a7(n) (v_cm with virtual wall
+//                  particles, rotation draw of Eq. 4, accumulators cleared)
+//                  as extra work items, and a8(n) (window-mean MPCD velocity
+//                  of the inner buffer -> f_eq(rho_LB, u_bar)) as the
+//                  collision of the inner-buffer nodes (cell_core.cuh).
 // The collision of the last step is applied lazily (flush) before particle
 // state is read out, so the visible state is always post-collision.
 // Every graph chunk starts with a counting sort of the particles by home cell
@@ -85,9 +86,11 @@ template <typename R> struct PState<3, R> {
 // ---------------------------------------------------------------------------
 // prep: one block; per (step k of the chunk, replica) the global step index,
 // the random shift of that step and of the previous one, and whether the
-// previous collision is still pending.
-__global__ void prep_steps(const RepDev* __restrict__ reps, int nrep, int dim, int kcount, int sorted,
-                           StepInfo* __restrict__ si, uint32_t* d_step, int* d_pending,
+// previous collision is still pending.  The sort, when one ran since the
+// last chunk, left d_sorted[r] = 1: the chunk's first step then reads the
+// sorted copy, and the flag is cleared for the next chunk.
+__global__ void prep_steps(const RepDev* __restrict__ reps, int nrep, int dim, int kcount, int* d_sorted,
+                           StepInfo* __restrict__ si, uint32_t* d_step, int* d_pending, int* d_cells,
                            double* d_last_shift) {
   const uint32_t n0 = *d_step;
   for (int idx = threadIdx.x; idx < kcount * nrep; idx += blockDim.x) {
@@ -96,8 +99,9 @@ __global__ void prep_steps(const RepDev* __restrict__ reps, int nrep, int dim, i
     StepInfo s;
     s.n = n0 + k;
     s.pending = (k == 0) ? d_pending[r] : 1;
+    s.cells = (k == 0) ? d_cells[r] : (rd.has_region ? 1 : 0);
     s.write_moments = (k == kcount - 1);
-    s.src_alt = (k == 0) && sorted && rd.has_region;
+    s.src_alt = (k == 0) && d_sorted[r] && rd.has_region;
     const uint4 w = philox(0u, s.n, rd.rep, TAG_SHIFT, rd.key0, rd.key1);
     s.shift[0] = unit24(w.x);
     s.shift[1] = unit24(w.y);
@@ -115,17 +119,20 @@ __global__ void prep_steps(const RepDev* __restrict__ reps, int nrep, int dim, i
   }
   __syncthreads();
   for (int r = threadIdx.x; r < nrep; r += blockDim.x) {
-    if (sorted && reps[r].resample) reps[r].pool[0] = reps[r].pool[2];   // the sort compacted the pool
+    if (d_sorted[r] && reps[r].resample) reps[r].pool[0] = reps[r].pool[2];   // the sort compacted the pool
+    d_sorted[r] = 0;
     const StepInfo& last = si[(kcount - 1) * nrep + r];
     for (int a = 0; a < 3; ++a) d_last_shift[3 * r + a] = last.shift[a];
     d_pending[r] = reps[r].has_region ? 1 : 0;
+    d_cells[r] = reps[r].has_region ? 1 : 0;
   }
   if (threadIdx.x == 0) *d_step = n0 + kcount;
 }
 
-cudaError_t launch_prep(int dim, const Launch& L, StepInfo* si, int kcount, int sorted, uint32_t* d_step,
-                        int* d_pending, double* d_last_shift) {
-  prep_steps<<<1, 256, 0, L.stream>>>(L.reps, L.nrep, dim, kcount, sorted, si, d_step, d_pending, d_last_shift);
+cudaError_t launch_prep(int dim, const Launch& L, StepInfo* si, int kcount, int* d_sorted, uint32_t* d_step,
+                        int* d_pending, int* d_cells, double* d_last_shift) {
+  prep_steps<<<1, 256, 0, L.stream>>>(L.reps, L.nrep, dim, kcount, d_sorted, si, d_step, d_pending, d_cells,
+                                      d_last_shift);
   return cudaGetLastError();
 }
 
@@ -748,248 +755,74 @@ cudaError_t launch_spawn(int dim, int prec, const Launch& L, const int2* bmap, i
 }
 
 // ---------------------------------------------------------------------------
-// cell_pass: a7 cell part and a8.
+// The collision-cell table of step m for the read-outs between calls (the
+// step itself builds it inside the next LB launch): every cell of one
+// replica, blocks of 256 CPT cells.
 template <int Q, typename S>
-__device__ __forceinline__ void cell_item(const RepDev& rd, const StepInfo& st, const int2 bm,
-                                          const long long start, const long long end) {
-  using R = typename Store<S>::R;
-  using T4 = typename Vec4<R>::T;
-  using L = Lattice<Q>;
-  constexpr int D = L::D;
-  if (bm.y >= 0) {
-    // cells [start, end) (at most 256 CPT of them), CPT per thread (c0 + 256 p):
-    // all accumulator loads first
-    const long long c0 = start + threadIdx.x;
-    uint32_t nn[CPT];
-    R V[CPT][3];
-#pragma unroll
-    for (int p = 0; p < CPT; ++p) {
-      const long long c = c0 + 256 * p;
-      const long long cl = c < end ? c : end - 1;
-      if (sizeof(R) == 4) {
-        const float4 g4 = rd.acc4[cl];
-        nn[p] = (uint32_t)g4.x;
-        V[p][0] = (R)g4.y; V[p][1] = (R)g4.z; V[p][2] = (R)g4.w;
-      } else {
-        nn[p] = rd.acc_n[cl];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) V[p][a] = a < D ? ((const R*)rd.acc_v[a])[cl] : R(0);
-      }
-    }
-#pragma unroll
-    for (int p = 0; p < CPT; ++p) {
-      const long long c = c0 + 256 * p;
-      if (c >= end) break;
-      const uint32_t n = nn[p];
-      R vc[3] = {R(0), R(0), R(0)}, rt[3] = {R(0), R(0), R(0)};
-      if (n > 0) {
-        const uint32_t ci = (uint32_t)c, row = ci / (uint32_t)rd.Wx;
-        const uint32_t cy = D == 2 ? row : row % (uint32_t)(rd.Hy + 1);
-        const bool cut = (cy == 0 || (cy == (uint32_t)rd.Hy && !rd.strip)) && st.shift_f[1] > 0.0f;
-        if (cut && (int)n < rd.ppc) {
-          // Lamura-type wall: ppc - n virtual particles at rest, summed momentum
-          // drawn from N(0, (ppc - n) m kT) per component.  MPCD-AT: they are
-          // members of the cell, so the sum of their random velocities (same
-          // law, TAG_AT_VIRT) is taken off as well: the sums hold v - v_ran.
-          const int nv = rd.ppc - (int)n;
-          const uint4 w = philox((uint32_t)c, st.n, rd.rep, TAG_VIRT, rd.key0, rd.key1);
-          R z[4];
-          normal_pair(w.x, w.y, z[0], z[1]);
-          normal_pair(w.z, w.w, z[2], z[3]);
-          const R sd = sqrt((R)nv * Cst<R>::kT_over_m(rd));
-#pragma unroll
-          for (int a = 0; a < D; ++a) V[p][a] += sd * z[a];
-          if (rd.collision == 1) {
-            const uint4 wa = philox((uint32_t)c, st.n, rd.rep, TAG_AT_VIRT, rd.key0, rd.key1);
-            normal_pair(wa.x, wa.y, z[0], z[1]);
-            normal_pair(wa.z, wa.w, z[2], z[3]);
-#pragma unroll
-            for (int a = 0; a < D; ++a) V[p][a] -= sd * z[a];
-          }
-#pragma unroll
-          for (int a = 0; a < D; ++a) vc[a] = V[p][a] / (R)rd.ppc;
-        } else {
-          const R inv_n = R(1) / (R)n;
-#pragma unroll
-          for (int a = 0; a < D; ++a) vc[a] = V[p][a] * inv_n;
-        }
-        if (rd.collision == 1) {
-          // MPCD-AT: no rotation; the table holds v_cm - <v_ran>
-        } else if (D == 2) {
-          const uint4 w = philox((uint32_t)c, st.n, rd.rep, TAG_SIGN, rd.key0, rd.key1);
-          rt[0] = (w.x >> 31) ? Cst<R>::sin_a(rd) : -Cst<R>::sin_a(rd);
-        } else {
-          const uint4 w = philox((uint32_t)c, st.n, rd.rep, TAG_AXIS, rd.key0, rd.key1);
-          if (sizeof(R) == 8) {
-            const double zc = 2.0 * unit24(w.x) - 1.0;
-            double sp, cp;
-            sincospi(2.0 * unit24(w.y), &sp, &cp);
-            const double rh = sqrt(1.0 - zc * zc);
-            rt[0] = (R)(rh * cp); rt[1] = (R)(rh * sp); rt[2] = (R)zc;
-          } else {
-            const float zc = 2.0f * unit24f(w.x) - 1.0f;
-            float sp, cp;
-            sincospif(2.0f * unit24f(w.y), &sp, &cp);
-            const float rh = sqrtf(1.0f - zc * zc);
-            rt[0] = (R)(rh * cp); rt[1] = (R)(rh * sp); rt[2] = (R)zc;
-          }
-        }
-      }
-      T4* tab = (T4*)rd.tab;
-      if (D == 2) {
-        T4 t; t.x = vc[0]; t.y = vc[1]; t.z = rt[0]; t.w = (R)n;
-        tab[c] = t;
-      } else {
-        T4 t0, t1;
-        t0.x = vc[0]; t0.y = vc[1]; t0.z = vc[2]; t0.w = (R)n;
-        t1.x = rt[0]; t1.y = rt[1]; t1.z = rt[2]; t1.w = R(0);
-        tab[2 * c] = t0;
-        tab[2 * c + 1] = t1;
-      }
-      if (sizeof(R) == 4) {
-        rd.acc4[c] = make_float4(0.f, 0.f, 0.f, 0.f);
-      } else {
-#pragma unroll
-        for (int a = 0; a < D; ++a) ((R*)rd.acc_v[a])[c] = R(0);
-        rd.acc_n[c] = 0u;
-      }
-    }
-    return;
-  }
-  // a8: one thread per inner-buffer LB node.  The window sums are binary64;
-  // the equilibrium is evaluated in the kernel's precision.  Every load of
-  // the thread (frame, running sum, ring slot, the node's LB density) is
-  // issued before the first store, so that they make one round trip: these
-  // few blocks are the last to finish the pass.
-  const long long b = (long long)(-1 - bm.y) * blockDim.x + threadIdx.x;
-  if (b >= rd.nbuf) return;
-  double* fr = rd.frame + 4 * b;
-  double* ws = rd.wsum + 4 * b;
-  double* rg = rd.ring + 4 * ((long long)(st.n % (uint32_t)rd.window) * rd.nbuf + b);
-  long long t = b;
-  int x, y, z;
-  if (rd.strip) {
-    x = (int)(t % rd.nx); t /= rd.nx;
-    z = (int)(t % rd.nz); t /= rd.nz;
-    y = rd.y1 - 1 - rd.n_out - (int)t;
-  } else {
-    y = 1 + (int)(t % (rd.ny - 2)); t /= (rd.ny - 2);
-    z = (int)(t % rd.nz); t /= rd.nz;
-    const int col = (int)(t % rd.n_in), side = (int)(t / rd.n_in);
-    x = side == 0 ? rd.x0 + rd.n_out + col : rd.x1 - 1 - rd.n_out - col;
-  }
-  const long long node = x + (long long)rd.nx * (y + (long long)rd.ny * z);
-  double xf[4], xw[4], xr[4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a) { xf[a] = fr[a]; xw[a] = ws[a]; xr[a] = rg[a]; }
-  const R rl = ((const R*)rd.rho)[node];
-  double W4[4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a) W4[a] = xw[a] + (xf[a] - xr[a]);
-#pragma unroll
-  for (int a = 0; a < 4; ++a) { ws[a] = W4[a]; rg[a] = xf[a]; fr[a] = 0.0; }
-  const uint32_t nf = min(st.n + 1u, (uint32_t)rd.window);
-  const R rdim = (D == 3) ? (R)(rd.r * rd.r * rd.r) : (R)(rd.r * rd.r);
-  const R M = (R)W4[0];
-  const R rho = M / ((R)rd.ppc * (R)Cst<R>::mass(rd) * rdim * (R)nf);
-  R u[3] = {R(0), R(0), R(0)};
-  if (M > R(0)) {
-    const R iM = R(1) / M;
-    u[0] = (R)W4[1] * iM; u[1] = (R)W4[2] * iM; u[2] = (R)W4[3] * iM;
-  }
-  double* wm = rd.wmean + 4 * b;
-  wm[0] = (double)rho; wm[1] = (double)u[0]; wm[2] = (double)u[1]; wm[3] = (double)u[2];
-  if (!(rd.feedback == 1 && st.n >= 1 && M > R(0))) return;
-  S* dst = (S*)rd.f[(st.n & 1) ^ 1];
-  // equilibrium at the node's own LB density (this step's moment, rl) and the
-  // window-mean MPCD velocity: the MPCD density is reported, not imposed,
-  // because the two fluids' equations of state differ (rho/3 versus n kT).
-  const R uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    const R cu = L::cx(i) * u[0] + L::cy(i) * u[1] + L::cz(i) * u[2];
-    const R dev = (R)L::w(i) * ((rl - R(1)) + rl * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu));
-    Store<S>::st(dst + i * rd.nnode + node, dev, rd.fp16_scale,
-                 sizeof(S) == 2 ? (mix32((uint32_t)node * 19u + (uint32_t)i + st.n * 0x632BE5ABu) | 1u) : 0u);
-  }
+__global__ void __launch_bounds__(256) cell_table_one(const __grid_constant__ RepDev rd, uint32_t m, int shift_y_pos) {
+  cell_table_item<Q, S>(rd, m, shift_y_pos != 0, (long long)blockIdx.x * 256 * CPT, rd.ncell);
 }
 
-template <int Q, typename S>
-__global__ void __launch_bounds__(256) cell_pass(const RepDev* __restrict__ reps, const int2* __restrict__ bmap,
-                                                 int nwork, const StepInfo* __restrict__ si, int k, int nrep) {
-  __shared__ RepDev rd;
-  __shared__ StepInfo st;
-  for_each_item(bmap, nwork, reps, si, k, nrep, rd, st, [&](const int2 bm) {
-    cell_item<Q, S>(rd, st, bm, (long long)bm.y * (256 * CPT), rd.ncell);
-  });
-}
-
-// the first blocks do the a8 items (they finish last when they start last);
-// every other block of the resident grid takes an even, contiguous share of
-// the collision cells, walked in chunks of 256 CPT
-template <int Q, typename S>
-__global__ void __launch_bounds__(256) cell_pass_one(const __grid_constant__ RepDev rd, int nwork,
-                                                     const StepInfo* __restrict__ si, int k) {
-  __shared__ StepInfo st;
-  {
-    const int* c = (const int*)(si + k);
-    int* d = (int*)&st;
-    for (int i = threadIdx.x; i < (int)(sizeof(StepInfo) / 4); i += blockDim.x) d[i] = c[i];
-    __syncthreads();
-  }
-  const int nbb = (int)((rd.nbuf + 255) / 256);
-  for (int b = blockIdx.x; b < nbb; b += gridDim.x) cell_item<Q, S>(rd, st, make_int2(0, -1 - b), 0, 0);
-  const int ncb = (int)gridDim.x > nbb ? (int)gridDim.x - nbb : (int)gridDim.x;
-  const int me = (int)gridDim.x > nbb ? (int)blockIdx.x - nbb : (int)blockIdx.x;
-  if (me < 0) return;
-  const long long per = ((rd.ncell + ncb - 1) / ncb + 31) & ~31LL;
-  const long long c0 = me * per, c1 = min(rd.ncell, c0 + per);
-  for (long long s = c0; s < c1; s += 256 * CPT) cell_item<Q, S>(rd, st, make_int2(0, 0), s, c1);
-}
-
-template <int Q, typename S>
-static void go_cells(const Launch& L, const int2* bmap, int nwork, int k) {
-  if (L.nrep == 1 && L.host) {
-    static const int g1 = grid_cap(grid_for(cell_pass_one<Q, S>, 256, 1 << 30));
-    // the resident grid (at most one block per 256 cells besides the a8 blocks):
-    // the kernel divides the cells evenly among its blocks
-    const RepDev& h = *L.host;
-    const long long want = (h.nbuf + 255) / 256 + (h.ncell + 255) / 256;
-    const int g = (int)(want < g1 ? want : g1);
-    cell_pass_one<Q, S><<<g > 0 ? g : 1, 256, 0, L.stream>>>(h, nwork, L.si, k);
-    return;
-  }
-  static const int g = grid_cap(grid_for(cell_pass<Q, S>, 256, 1 << 30));
-  cell_pass<Q, S><<<g < nwork ? g : nwork, 256, 0, L.stream>>>(L.reps, bmap, nwork, L.si, k, L.nrep);
-}
-
-cudaError_t launch_cells(int q, int prec, const Launch& L, const int2* bmap, int nblocks, int k) {
-  if (nblocks == 0) return cudaSuccess;
-#define LBM_CELLS(QQ, SS) go_cells<QQ, SS>(L, bmap, nblocks, k)
+cudaError_t launch_cell_table(int q, int prec, const RepDev& rd, uint32_t m, bool shift_y_pos, cudaStream_t st) {
+  const long long nb = (rd.ncell + 256 * CPT - 1) / (256 * CPT);
+  if (nb == 0) return cudaSuccess;
+  const int sp = shift_y_pos ? 1 : 0;
+#define LBM_CT(QQ, SS) cell_table_one<QQ, SS><<<(int)nb, 256, 0, st>>>(rd, m, sp)
   if (q == 9) {
-    if (prec == P_FP64) LBM_CELLS(9, double);
-    else if (prec == P_FP32) LBM_CELLS(9, float);
-    else LBM_CELLS(9, __half);
+    if (prec == P_FP64) LBM_CT(9, double);
+    else if (prec == P_FP32) LBM_CT(9, float);
+    else LBM_CT(9, __half);
   } else {
-    if (prec == P_FP64) LBM_CELLS(19, double);
-    else if (prec == P_FP32) LBM_CELLS(19, float);
-    else LBM_CELLS(19, __half);
+    if (prec == P_FP64) LBM_CT(19, double);
+    else if (prec == P_FP32) LBM_CT(19, float);
+    else LBM_CT(19, __half);
   }
-#undef LBM_CELLS
+#undef LBM_CT
+  return cudaGetLastError();
+}
+
+// WINDOW_MEAN after step m: rho_bar, u_bar of the last min(m + 1, W) frames
+// of every inner-buffer node, from the window state (frame m is folded in by
+// the next LB update, so it is added here without moving the window).
+template <int D, typename R>
+__global__ void window_out(const __grid_constant__ RepDev rd, uint32_t m, double* __restrict__ out) {
+  const long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (b >= rd.nbuf) return;
+  double W4[4];
+  window_sums(rd, m, b, false, W4);
+  R rho, u[3];
+  window_mean<D, R>(rd, m, W4, rho, u);
+  out[4 * b] = (double)rho;
+  out[4 * b + 1] = (double)u[0]; out[4 * b + 2] = (double)u[1]; out[4 * b + 3] = (double)u[2];
+}
+
+cudaError_t launch_window_out(int dim, int prec, const RepDev& rd, uint32_t m, double* out, cudaStream_t st) {
+  const int nb = (int)((rd.nbuf + 255) / 256);
+  if (nb == 0) return cudaSuccess;
+  if (dim == 2) {
+    if (prec == P_FP64) window_out<2, double><<<nb, 256, 0, st>>>(rd, m, out);
+    else window_out<2, float><<<nb, 256, 0, st>>>(rd, m, out);
+  } else {
+    if (prec == P_FP64) window_out<3, double><<<nb, 256, 0, st>>>(rd, m, out);
+    else window_out<3, float><<<nb, 256, 0, st>>>(rd, m, out);
+  }
   return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
 // Persistent form of a chunk: one cooperative launch runs kcount steps, each
-// as the three phases lb_pull -> particle_pass -> cell_pass over the same
-// block maps (the LB map with 256-thread row tiles), separated by a grid
-// barrier.  The barrier is a counter and a generation word in global memory;
-// every wait is bounded: after PB_SPIN polls a block records the failure in
-// *err and leaves the launch, so a stuck barrier ends the kernel instead of
-// hanging the GPU.  Co-residency of all blocks comes from the cooperative launch.
+// as the two phases lb_pull (with the cell-table items of the previous step)
+// -> particle_pass over the same block maps (the LB map with 256-thread row
+// tiles and 256 CPT-cell items), separated by a grid barrier.  The barrier is a counter and a generation word in global memory;
+// every wait is bounded: after `spin` polls (PB_SPIN unless the handle set
+// another limit) a block records the failure in *err and leaves the launch,
+// and a block that finds *err set leaves too, so a stuck barrier ends the
+// kernel instead of hanging the GPU.  Co-residency of all blocks comes from the
+// cooperative launch.
 constexpr unsigned PB_SPIN = 1u << 24;
 
-__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, unsigned nblocks, int* err) {
+__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, unsigned nblocks, int* err,
+                                             unsigned spin) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -1005,7 +838,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, uns
       const volatile unsigned* vg = gen;
       const volatile int* ve = err;
       while (*vg == g) {   // plain polling loads (L2), no atomic traffic on the word
-        if (++it >= PB_SPIN || *ve != 0) { ok = 0; break; }
+        if (++it >= spin || *ve != 0) { ok = 0; break; }
         __nanosleep(32);
       }
       if (!ok) atomicExch(err, 1);
@@ -1022,8 +855,7 @@ __global__ void __launch_bounds__(256, 2) step_persistent(const RepDev* __restri
                                                          const StepInfo* __restrict__ si, int kcount,
                                                          const int4* __restrict__ bm_lb, int nb_lb,
                                                          const int2* __restrict__ bm_p, int nb_p,
-                                                         const int2* __restrict__ bm_c, int nb_c,
-                                                         unsigned* bar, int* err) {
+                                                         unsigned* bar, int* err, unsigned spin) {
   constexpr int D = Q == 9 ? 2 : 3;
   using R = typename std::conditional<sizeof(S) == 8, double, float>::type;
   __shared__ RepDev rd;
@@ -1031,13 +863,9 @@ __global__ void __launch_bounds__(256, 2) step_persistent(const RepDev* __restri
   __shared__ PassShared<D, R> red;
   for (int k = 0; k < kcount; ++k) {
     for_each_item(bm_lb, nb_lb, reps, si, k, nrep, rd, st, [&](const int4 bm) { lb_row<Q, S, V>(rd, st, bm); });
-    if (!grid_barrier(bar, bar + 1, gridDim.x, err)) return;
+    if (!grid_barrier(bar, bar + 1, gridDim.x, err, spin)) return;
     for_each_item(bm_p, nb_p, reps, si, k, nrep, rd, st, [&](const int2 bm) { particle_item<D, R, false, false, false>(rd, st, (uint32_t)bm.y * PP_ITEM, ~0u, red); });
-    if (!grid_barrier(bar, bar + 1, gridDim.x, err)) return;
-    for_each_item(bm_c, nb_c, reps, si, k, nrep, rd, st, [&](const int2 bm) {
-      cell_item<Q, S>(rd, st, bm, (long long)bm.y * (256 * CPT), rd.ncell);
-    });
-    if (!grid_barrier(bar, bar + 1, gridDim.x, err)) return;
+    if (!grid_barrier(bar, bar + 1, gridDim.x, err, spin)) return;
   }
 }
 
@@ -1059,12 +887,13 @@ static cudaError_t go_persistent(const Launch& L, int kcount, const PersistentMa
   int nrep = L.nrep;
   const StepInfo* si = L.si;
   const int4* bl = m.lb;
-  const int2 *bp = m.p, *bc = m.c;
-  int nl = m.nb_lb, np = m.nb_p, nc = m.nb_c;
+  const int2* bp = m.p;
+  int nl = m.nb_lb, np = m.nb_p;
   unsigned* bar = m.bar;
   int* err = m.err;
+  unsigned spin = m.spin ? m.spin : PB_SPIN;
   void* args[] = {(void*)&reps, (void*)&nrep, (void*)&si, (void*)&kcount, (void*)&bl, (void*)&nl,
-                  (void*)&bp,   (void*)&np,   (void*)&bc, (void*)&nc,     (void*)&bar, (void*)&err};
+                  (void*)&bp,   (void*)&np,   (void*)&bar, (void*)&err, (void*)&spin};
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(256);
@@ -1379,12 +1208,13 @@ __global__ void __launch_bounds__(SORT_TILE) sort_scan_tiles(const RepDev* __res
   if (threadIdx.x == 0) rd.tsum[bm.y] = total;
 }
 
-__global__ void __launch_bounds__(1024) sort_scan_top(const RepDev* __restrict__ reps) {
+__global__ void __launch_bounds__(1024) sort_scan_top(const RepDev* __restrict__ reps, int* d_sorted) {
   __shared__ RepDev rd;
   __shared__ StepInfo unused;
   __shared__ uint32_t wt[33];
   load_block_records(rd, unused, reps, nullptr, blockIdx.x, 0, 0);
   if (!rd.has_region) return;
+  if (threadIdx.x == 0) d_sorted[blockIdx.x] = 1;   // read (and cleared) by the next prep
   uint32_t carry = 0;
   for (int base = 0; base < rd.ntile; base += blockDim.x) {
     const int t = base + threadIdx.x;
@@ -1430,13 +1260,13 @@ __global__ void __launch_bounds__(256) sort_scatter(const RepDev* __restrict__ r
 }
 
 cudaError_t launch_sort(int dim, int prec, const Launch& L, const int2* bmap_p, int nb_p, const int2* bmap_t,
-                        int nb_t) {
+                        int nb_t, int* d_sorted) {
   if (nb_p == 0) return cudaSuccess;
   static const int gc2 = grid_cap(grid_for(sort_count<2>, 256, 1 << 30)), gc3 = grid_cap(grid_for(sort_count<3>, 256, 1 << 30));
   if (dim == 2) sort_count<2><<<gc2 < nb_p ? gc2 : nb_p, 256, 0, L.stream>>>(L.reps, bmap_p, nb_p);
   else sort_count<3><<<gc3 < nb_p ? gc3 : nb_p, 256, 0, L.stream>>>(L.reps, bmap_p, nb_p);
   sort_scan_tiles<<<nb_t, SORT_TILE, 0, L.stream>>>(L.reps, bmap_t);
-  sort_scan_top<<<L.nrep, 1024, 0, L.stream>>>(L.reps);
+  sort_scan_top<<<L.nrep, 1024, 0, L.stream>>>(L.reps, d_sorted);
   static const int gs2 = grid_cap(grid_for(sort_scatter<2, float>, 256, 1 << 30));
   const int gs = nb_p < gs2 ? nb_p : gs2;
   if (dim == 2) {
