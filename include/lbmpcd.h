@@ -333,6 +333,17 @@ int lbmpcd_set_closure(lbmpcd* h, const float* theta, long long count, int src_o
 #define LBMPCD_LAUNCH_LB_TMA 1   /* flags: D2Q9 binary32 LB rows staged by bulk (TMA) copies */
 int lbmpcd_set_launch_mode(lbmpcd* h, int mode, int blocks_per_sm, int flags);
 
+/* Poll limit of the grid-barrier waits of the persistent launch form (mode 1;
+ * not a step of the paper's method): a block that has polled the barrier this
+ * many times without the other blocks arriving gives up, records the failure
+ * and leaves the launch, and every block that sees the record leaves at its
+ * next barrier, so lbmpcd_step returns LBMPCD_ERR_TIMEOUT instead of the GPU
+ * hanging.  polls = 0 restores the default (2^24 polls, seconds of waiting).
+ * A small limit makes the waits run out on purpose, which is how the tests
+ * drive this error path; the step's results are then invalid, the barrier
+ * words are reset and the handle can be stepped or destroyed as usual. */
+int lbmpcd_set_wait_limit(lbmpcd* h, unsigned polls);
+
 /* Time the launch forms {mode 0 with the default LB row width, with TMA rows
  * (where they apply), with one LB node per thread; mode 1 at the occupancy
  * limit and with one block per SM} for `steps` steps each (after a 64-step

@@ -83,6 +83,7 @@ def load_library(path: str = LIB_PATH):
     L.lbmpcd_net_forward_noalloc.argtypes = [vp, vp, ci, vp, vp]
     L.lbmpcd_set_closure.argtypes = [vp, vp, ll, ci, ci]
     L.lbmpcd_set_launch_mode.argtypes = [vp, ci, ci, ci]
+    L.lbmpcd_set_wait_limit.argtypes = [vp, ctypes.c_uint]
     L.lbmpcd_autotune.argtypes = [vp, ci, ctypes.POINTER(ci)]
     L.lbmpcd_net_destroy.restype = None
     L.lbmpcd_destroy.argtypes = [vp]
@@ -98,7 +99,7 @@ EXPORTED = ["lbmpcd_create", "lbmpcd_set_region", "lbmpcd_step", "lbmpcd_step_pr
             "lbmpcd_last_error", "lbmpcd_tc_gemm_bf16", "lbmpcd_net_num_params", "lbmpcd_net_create",
             "lbmpcd_net_get_params", "lbmpcd_net_set_params", "lbmpcd_net_forward", "lbmpcd_net_backward",
             "lbmpcd_net_train_step", "lbmpcd_net_destroy", "lbmpcd_net_forward_noalloc",
-            "lbmpcd_set_closure", "lbmpcd_set_launch_mode", "lbmpcd_autotune"]
+            "lbmpcd_set_closure", "lbmpcd_set_launch_mode", "lbmpcd_set_wait_limit", "lbmpcd_autotune"]
 
 
 def make_params(d: dict) -> lbmpcd_params:
@@ -231,10 +232,36 @@ def lbmpcd_tc_gemm_bf16(A, B, C, alpha=1.0, beta=0.0, err=None, stream=None):
 NET_STATIC_MAX_PATCHES = 8   # LBMPCD_NET_STATIC_MAX_PATCHES
 
 
+def _check_net_tensor(name, t, shape):
+    """A float32, contiguous CUDA tensor of the given shape (the C side only
+    sees its address, so a short or strided buffer would be read out of
+    bounds on the device)."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise ValueError(f"{name}: expected a torch tensor")
+    if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
+        raise ValueError(f"{name}: expected a contiguous float32 CUDA tensor")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name}: expected shape {tuple(shape)}, got {tuple(t.shape)}")
+
+
 def lbmpcd_net_forward_noalloc(theta, x, y, stream=None):
     """Network forward with the library's static scratch (no allocation):
     theta (n_params,) float32, x (P, 16, 16, 24) and y (P, 16, 16, 3) float32
-    CUDA tensors, P <= NET_STATIC_MAX_PATCHES."""
+    contiguous CUDA tensors on the current device, P <= NET_STATIC_MAX_PATCHES
+    (a larger P is passed on so that the library reports ERR_CAPACITY).
+    Raises ValueError for a tensor of the wrong type, shape or device."""
+    import torch
+    if not isinstance(x, torch.Tensor) or x.dim() != 4:
+        raise ValueError("x: expected a (P, 16, 16, 24) tensor")
+    P = int(x.shape[0])
+    _check_net_tensor("theta", theta, (int(load_library().lbmpcd_net_num_params()),))
+    _check_net_tensor("x", x, (P, 16, 16, 24))
+    _check_net_tensor("y", y, (P, 16, 16, 3))
+    cur = torch.cuda.current_device()
+    for name, t in (("theta", theta), ("x", x), ("y", y)):
+        if t.device.index != cur:
+            raise ValueError(f"{name}: on cuda:{t.device.index}, the current device is cuda:{cur}")
     sptr = getattr(stream, "cuda_stream", stream) or 0
     rc = load_library().lbmpcd_net_forward_noalloc(ctypes.c_void_p(theta.data_ptr()), ctypes.c_void_p(x.data_ptr()),
                                                     int(x.shape[0]), ctypes.c_void_p(y.data_ptr()),
@@ -336,6 +363,11 @@ class Lbmpcd:
         chunk.  lb_tma: TMA-staged LB rows (D2Q9 binary32)."""
         _check(self._h, load_library().lbmpcd_set_launch_mode(self._h, int(mode), int(blocks_per_sm),
                                                               LAUNCH_LB_TMA if lb_tma else 0))
+
+    def set_wait_limit(self, polls: int = 0):
+        """Polls before a grid-barrier wait of the persistent form gives up
+        (0: the library's default); lbmpcd_step then returns ERR_TIMEOUT."""
+        _check(self._h, load_library().lbmpcd_set_wait_limit(self._h, int(polls)))
 
     def autotune(self, steps: int = 256) -> dict:
         """Time the launch forms on a copy of this handle and keep the fastest."""

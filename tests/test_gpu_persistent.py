@@ -1,6 +1,7 @@
 """The persistent launch form (one cooperative kernel per chunk, grid barriers
-between the LB, particle and cell phases) and the autotuner, against the
-FP64 oracle (GPU).  Tolerances as in test_gpu_parity: 1e-12 relative in FP64,
+between the LB phase, which also builds the previous step's collision-cell
+table, and the particle phase) and the autotuner, against the FP64 oracle
+(GPU).  Tolerances as in test_gpu_parity: 1e-12 relative in FP64,
 integer results bit-exact."""
 import numpy as np
 import pytest
@@ -35,9 +36,9 @@ def _check(g, o):
 
 @pytest.mark.parametrize("case,bps", [("2d", 0), ("2d", 1), ("3d", 0), ("2d_strip", 0), ("3d_strip", 0)])
 def test_persistent_matches_oracle(lb, case, bps):
-    """70 steps = one 64-step chunk (sort + one persistent launch) and a
-    6-step remainder launch, then 3 more single steps; also with a near-wall
-    strip as the MPCD region."""
+    """70 steps = chunks of 64, 4 and 2 steps (the particle sort runs before
+    the 4-step chunk), then 3 more single steps; also with a near-wall strip
+    as the MPCD region."""
     cfg = inputs.small_2d(precision=0, nx=72) if case.startswith("2d") else inputs.small_3d(precision=0, nx=24)
     g = lb.Lbmpcd(cfg["params"])
     o = O.OracleSim(cfg["params"])
@@ -146,4 +147,34 @@ def test_lb_tma_coupled_fp32_matches_oracle(lb):
     assert rel_err(g.get("POPS"), o.get("POPS")) <= 1e-5
     g.step(147)
     assert np.all(np.isfinite(g.get("POPS")))
+    g.close()
+
+
+def test_barrier_wait_runs_out_and_handle_recovers(lb):
+    """A grid-barrier wait that runs out ends the persistent launch with
+    ERR_TIMEOUT instead of hanging the GPU: with a poll limit of 1 the first
+    block to reach a barrier gives up long before the other (at least one
+    per SM) arrive, records the failure, and every other block leaves at its
+    next barrier.  With the default limit restored the same handle steps
+    again without error, and a fresh handle still matches the oracle."""
+    cfg = inputs.small_2d(precision=0, nx=72)
+    g = lb.Lbmpcd(cfg["params"])
+    g.set_region(0, *cfg["region"])
+    g.set_launch_mode(1, 0)
+    g.set_wait_limit(1)
+    with pytest.raises(lb.LbmpcdError) as ei:
+        g.step(4)
+    assert ei.value.code == -4   # LBMPCD_ERR_TIMEOUT
+    g.set_wait_limit(0)
+    g.step(4)
+    assert np.all(np.isfinite(g.get("POPS")))
+    g.close()
+    g = lb.Lbmpcd(cfg["params"])
+    o = O.OracleSim(cfg["params"])
+    g.set_region(0, *cfg["region"])
+    o.set_region(*cfg["region"])
+    g.set_launch_mode(1, 0)
+    g.step(5)
+    o.step(5)
+    _check(g, o)
     g.close()
