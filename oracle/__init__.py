@@ -21,7 +21,9 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "_build", "liboracle.so")
+_SO_OMP = os.path.join(_HERE, "_build", "liboracle_omp.so")   # all-cores timing build
 _lib = None
+_lib_omp = None
 
 FIELDS = dict(RHO=0, U=1, POPS=2, PART_POS=3, PART_VEL=4, PART_CELL=5, SHIFT=6,
               CELL_COUNT=7, WINDOW_MEAN=8, DIAG=9, PART_HOME=10, CELL_VCM=11, PART_ID=12,
@@ -30,15 +32,19 @@ _INT_FIELDS = {"PART_CELL", "CELL_COUNT", "PART_HOME", "PART_ID", "CELL_LIST"}
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.c into _build/liboracle.so (plain gcc, no FMA contraction)."""
+    """Compile oracle.c into _build/liboracle.so (plain gcc, no FMA contraction),
+    the parity oracle, and _build/liboracle_omp.so, the same source with its
+    OpenMP pragmas enabled (LB nodes, particle streaming and redraw spread over
+    the host cores), used only to time the oracle on all cores."""
     src = os.path.join(_HERE, "oracle.c")
     os.makedirs(os.path.dirname(_SO), exist_ok=True)
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < max(
-            os.path.getmtime(src), os.path.getmtime(os.path.join(_HERE, "oracle.h"))):
-        tmp = _SO + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-                               "-shared", "-o", tmp, src, "-lm"])
-        os.replace(tmp, _SO)
+    newest = max(os.path.getmtime(src), os.path.getmtime(os.path.join(_HERE, "oracle.h")))
+    for so, extra in ((_SO, []), (_SO_OMP, ["-fopenmp"])):
+        if force or not os.path.exists(so) or os.path.getmtime(so) < newest:
+            tmp = so + f".{os.getpid()}.tmp"
+            subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC"] + extra +
+                                  ["-shared", "-o", tmp, src, "-lm"])
+            os.replace(tmp, so)
     return _SO
 
 
@@ -53,11 +59,12 @@ class Params(ctypes.Structure):
                 ("collision", ctypes.c_int), ("redraw", ctypes.c_int)]
 
 
-def lib():
-    global _lib
-    if _lib is None:
+def lib(omp: bool = False):
+    """The parity oracle, or with omp=True its all-cores timing build."""
+    global _lib, _lib_omp
+    if (_lib_omp if omp else _lib) is None:
         build()
-        L = ctypes.CDLL(_SO)
+        L = ctypes.CDLL(_SO_OMP if omp else _SO)
         vp = ctypes.c_void_p
         L.orc_create.restype = vp
         L.orc_create.argtypes = [ctypes.POINTER(Params), ctypes.c_int]
@@ -71,6 +78,8 @@ def lib():
         L.orc_destroy.argtypes = [vp]
         L.orc_num_particles.restype = ctypes.c_long
         L.orc_num_particles.argtypes = [vp]
+        L.orc_num_threads.restype = ctypes.c_int
+        L.orc_num_threads.argtypes = []
         L.orc_step_count.restype = ctypes.c_long
         L.orc_step_count.argtypes = [vp]
         L.orc_philox4x32_10.argtypes = [vp, vp, vp]
@@ -87,8 +96,16 @@ def lib():
         L.orc_closure_patches.restype = ctypes.c_long
         L.orc_closure_patches.argtypes = [vp]
         L.orc_closure_impose.argtypes = [vp, vp]
-        _lib = L
-    return _lib
+        if omp:
+            _lib_omp = L
+        else:
+            _lib = L
+    return _lib_omp if omp else _lib
+
+
+def num_threads(omp: bool = True) -> int:
+    """Threads the oracle's parallel loops use (1 for the parity build)."""
+    return int(lib(omp).orc_num_threads())
 
 
 def make_params(d: dict) -> Params:
@@ -117,54 +134,57 @@ def make_params(d: dict) -> Params:
 class OracleSim:
     """One replica of the coupled system, stepped by the FP64 oracle."""
 
-    def __init__(self, params: dict, replica: int = 0):
+    def __init__(self, params: dict, replica: int = 0, omp: bool = False):
+        """omp: run on the all-cores timing build (same arithmetic; the
+        per-node and per-particle loops are shared out among threads)."""
         self.params = dict(params)
         self._p = make_params(params)
-        self._h = lib().orc_create(ctypes.byref(self._p), int(replica))
+        self._L = lib(omp)
+        self._h = self._L.orc_create(ctypes.byref(self._p), int(replica))
         if not self._h:
             raise ValueError("oracle rejected the parameters")
 
     def __del__(self):
         h = getattr(self, "_h", None)
         if h:
-            lib().orc_destroy(h)
+            self._L.orc_destroy(h)
             self._h = None
 
     def set_region(self, x0: int, x1: int) -> None:
-        if lib().orc_set_region(self._h, int(x0), int(x1)) != 0:
+        if self._L.orc_set_region(self._h, int(x0), int(x1)) != 0:
             raise ValueError("bad region")
 
     def set_strip(self, y1: int) -> None:
         """Near-wall strip (Sec. 3.3): all columns, LB rows [1, y1), buffer along y1."""
-        if lib().orc_set_strip(self._h, int(y1)) != 0:
+        if self._L.orc_set_strip(self._h, int(y1)) != 0:
             raise ValueError("bad strip")
 
     def step(self, n: int = 1) -> None:
-        lib().orc_step(self._h, int(n))
+        self._L.orc_step(self._h, int(n))
 
     @property
     def num_particles(self) -> int:
-        return int(lib().orc_num_particles(self._h))
+        return int(self._L.orc_num_particles(self._h))
 
     @property
     def step_count(self) -> int:
-        return int(lib().orc_step_count(self._h))
+        return int(self._L.orc_step_count(self._h))
 
     def get(self, field: str) -> np.ndarray:
         fid = FIELDS[field]
-        n = int(lib().orc_field_size(self._h, fid))
+        n = int(self._L.orc_field_size(self._h, fid))
         out = np.empty(n, dtype=np.int32 if field in _INT_FIELDS else np.float64)
-        lib().orc_get_field(self._h, fid, out.ctypes.data)
+        self._L.orc_get_field(self._h, fid, out.ctypes.data)
         return out
 
     def u_fine(self, X: int, Y: int, Z: int = 0) -> np.ndarray:
         out = np.zeros(3)
-        lib().orc_u_fine(self._h, int(X), int(Y), int(Z), out.ctypes.data)
+        self._L.orc_u_fine(self._h, int(X), int(Y), int(Z), out.ctypes.data)
         return out
 
     @property
     def closure_patches(self) -> int:
-        return int(lib().orc_closure_patches(self._h))
+        return int(self._L.orc_closure_patches(self._h))
 
     def closure_impose(self, y) -> None:
         """a8 of the learned closure for the step just taken, from the network
@@ -172,7 +192,7 @@ class OracleSim:
         arr = np.ascontiguousarray(y, dtype=np.float64).ravel()
         if arr.size != self.closure_patches * 768:
             raise ValueError("closure output has the wrong size")
-        if lib().orc_closure_impose(self._h, arr.ctypes.data) != 0:
+        if self._L.orc_closure_impose(self._h, arr.ctypes.data) != 0:
             raise ValueError("no closure sampling on this replica")
 
     def set_closure(self, theta, interval: int = 1) -> None:
@@ -199,11 +219,11 @@ class OracleSim:
 
     def set(self, field: str, value) -> None:
         fid = FIELDS[field]
-        n = int(lib().orc_field_size(self._h, fid))
+        n = int(self._L.orc_field_size(self._h, fid))
         arr = np.ascontiguousarray(value, dtype=np.int32 if field in _INT_FIELDS else np.float64).ravel()
         if arr.size != n:
             raise ValueError(f"{field}: expected {n} elements, got {arr.size}")
-        if lib().orc_set_field(self._h, fid, arr.ctypes.data) != 0:
+        if self._L.orc_set_field(self._h, fid, arr.ctypes.data) != 0:
             raise ValueError(f"{field} cannot be set")
 
 

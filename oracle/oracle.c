@@ -30,6 +30,9 @@
  */
 #include "oracle.h"
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdlib.h>
 #include <string.h>
 
@@ -231,6 +234,15 @@ void orc_destroy(orc_sim* s) {
 }
 
 long orc_num_particles(const orc_sim* s) { return s->np; }
+
+/* threads the loops marked for OpenMP run on: 1 in the parity build */
+int orc_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
 long orc_step_count(const orc_sim* s) { return s->step; }
 
 /* Seed the MPCD region: exactly ppc particles in every cell, offsets uniform
@@ -343,6 +355,9 @@ static void buffer_node(const orc_sim* s, long b, int* x, int* y, int* z) {
 static void lb_step(orc_sim* s) {
   const orc_params* p = &s->p;
   const double cs2 = 1.0 / 3.0, tau = p->tau;
+  /* nodes are independent (each writes only its own populations and moments);
+     the pragma takes effect only in the all-cores timing build (-fopenmp) */
+#pragma omp parallel for collapse(2) schedule(static)
   for (int z = 0; z < p->nz; ++z)
     for (int y = 1; y < p->ny - 1; ++y)
       for (int x = 0; x < p->nx; ++x) {
@@ -588,6 +603,8 @@ static void ce_peculiar(const orc_sim* s, uint32_t id, long node, double sig, do
  * Chapman-Enskog draw above with redraw = 1). */
 static void resample(orc_sim* s) {
   double sig = sqrt(s->p.kT / s->p.mass);
+  /* particles are independent: each draws by its own index (timing build only) */
+#pragma omp parallel for schedule(static)
   for (long k = 0; k < s->np; ++k) {
     int X = s->home[3*k], Y = s->home[3*k+1], Z = s->home[3*k+2];
     if (!in_outer(s, X, Y)) continue;
@@ -615,6 +632,8 @@ static void stream(orc_sim* s) {
   const orc_params* p = &s->p;
   const double r = s->r;
   const double one_minus = 1.0 - 1.0 / 9007199254740992.0; /* largest double below 1 */
+  /* particles are independent (timing build only, as in lb_step) */
+#pragma omp parallel for schedule(static)
   for (long k = 0; k < s->np; ++k) {
     double* v = &s->vel[3*k];
     double* o = &s->off[3*k];

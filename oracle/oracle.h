@@ -94,6 +94,8 @@ int  orc_get_field(const orc_sim* s, int field, void* dst); /* double or int32 *
 int  orc_set_field(orc_sim* s, int field, const void* src);
 void orc_destroy(orc_sim* s);
 long orc_num_particles(const orc_sim* s);
+/* threads of the OpenMP loops (1 unless built with -fopenmp, for timing) */
+int orc_num_threads(void);
 long orc_step_count(const orc_sim* s);
 /* Closure patches per replica (0 unless feedback = 2 with a region). */
 long orc_closure_patches(const orc_sim* s);
