@@ -28,8 +28,10 @@ __global__ void __launch_bounds__(128, 5) lb_pull(const RepDev* __restrict__ rep
 // items from the block map (computing (tile, y, z) from the index takes
 // integer divisions that cost more than the load)
 template <int Q, typename S, int V>
-// 6 resident blocks per SM for D2Q9 (80 registers, no spills; 3 % faster than 5)
-__global__ void __launch_bounds__(128, Q == 9 ? 6 : 5) lb_pull_one(const __grid_constant__ RepDev rd, const int4* __restrict__ bmap,
+// 7 resident blocks per SM for D2Q9 (72 registers, one 4-byte spill): the 2040
+// row tiles of the 2048 x 512 channel take 1.92 rounds of the resident grid
+// instead of 2.24 (72.8 against 73.7 us per step; 5 per SM was slower still)
+__global__ void __launch_bounds__(128, Q == 9 ? 7 : 5) lb_pull_one(const __grid_constant__ RepDev rd, const int4* __restrict__ bmap,
                                                    int nwork, const StepInfo* __restrict__ si, int k) {
   __shared__ StepInfo st;
   for_each_item_one([bmap](int wi) { return bmap[wi]; }, nwork, si, k, st,
