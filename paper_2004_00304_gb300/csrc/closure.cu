@@ -17,11 +17,30 @@
 
 namespace lbm {
 
+// The dynamic shared-memory opt-in of a GEMM instantiation, set once on each
+// device (a function attribute holds for the device that is current when it
+// is set).
+template <int BN>
+static cudaError_t gemm_smem_optin() {
+  static std::mutex mu;
+  static bool done[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> g(mu);
+  if (!done[dev]) {
+    e = cudaFuncSetAttribute(tc_gemm_bf16<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_gemm_smem<BN>());
+    if (e != cudaSuccess) return e;
+    done[dev] = true;
+  }
+  return cudaSuccess;
+}
+
 template <int BN>
 static cudaError_t gemm_bn(const __nv_bfloat16* A, const __nv_bfloat16* B, float* C, int M, int N, int K, int ldc,
                            float alpha, float beta, int* err, cudaStream_t st) {
-  static const cudaError_t attr =
-      cudaFuncSetAttribute(tc_gemm_bf16<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_gemm_smem<BN>());
+  const cudaError_t attr = gemm_smem_optin<BN>();
   if (attr != cudaSuccess) return attr;
   dim3 grid(N / BN, M / tc::BM);
   tc_gemm_bf16<BN><<<grid, 128, tc_gemm_smem<BN>(), st>>>(A, B, C, M, N, K, ldc, alpha, beta, err);
