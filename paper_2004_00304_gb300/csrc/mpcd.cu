@@ -362,9 +362,207 @@ __device__ __forceinline__ void stream(const RepDev& rd, int& X, int& Y, int& Z,
 // are issued first, then their cell-table loads, before any arithmetic, so
 // they are in flight together instead of forming one dependent chain.
 // shared memory of particle_pass: staging of the warp-aggregated reduction
+// read-only (L1-cached) load of a cell-table entry: particles of one block are
+// sorted by home cell, so neighbouring threads read the same entries
+template <typename T> __device__ __forceinline__ T ld_ro(const T* p) {
+  if constexpr (std::is_same<T, float4>::value) return __ldg(p);
+  else return *p;
+}
+
 template <int D, typename R> struct PassShared {
   R sv[D][256];
 };
+
+// a7 of step n-1, particle side, from the entries of the particle's collision
+// cell in the table (2D: t0 = {v_cm, sin theta, n}; 3D: t0 = {v_cm, n},
+// t1 = {axis, 0}): v <- v_cm + R (v - v_cm) (Eq. 4), rotation by theta in 2D,
+// Rodrigues' formula about the axis in 3D.  MPCD-AT: v holds the particle's
+// random velocity and t0 v_cm - <v_ran>, so the collision is their sum.
+template <int D, typename R, bool AT, typename T4>
+__device__ __forceinline__ void collide_from_table(const RepDev& rd, const T4& t0, const T4& t1, R* v) {
+  const R ca = Cst<R>::cos_a(rd), sa = Cst<R>::sin_a(rd);
+  if (AT) {
+    v[0] += t0.x;
+    v[1] += t0.y;
+    if (D == 3) v[2] += t0.z;
+  } else if (D == 2) {
+    const R wx = v[0] - t0.x, wy = v[1] - t0.y;
+    v[0] = t0.x + (ca * wx - t0.z * wy);
+    v[1] = t0.y + (t0.z * wx + ca * wy);
+  } else {
+    const R vc[3] = {t0.x, t0.y, t0.z}, n[3] = {t1.x, t1.y, t1.z};
+    const R w[3] = {v[0] - vc[0], v[1] - vc[1], v[2] - vc[2]};
+    const R cr[3] = {n[1] * w[2] - n[2] * w[1], n[2] * w[0] - n[0] * w[2], n[0] * w[1] - n[1] * w[0]};
+    const R nw = n[0] * w[0] + n[1] * w[1] + n[2] * w[2];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) v[a] = vc[a] + (w[a] * ca + cr[a] * sa + n[a] * nw * (R(1) - ca));
+  }
+}
+
+constexpr uint32_t NO_CELL = 0xFFFFFFFFu;   // a particle that adds nothing to the cell sums
+
+// One particle j of step n after its collision of step n-1: a3' removal
+// (density resampling), a2 + a3 redraw in the outer buffer, a4 streaming, a6
+// inner-buffer sampling and the closure strips, a5 binning under this step's
+// shift, and the stores of its new state (MPCD-AT: with the random velocity of
+// this step's collision in place of v).  alt: the state was read from the
+// sorted copy; fresh: created by this step's spawn.  Returns the collision
+// cell, or NO_CELL for a removed particle.  v keeps what the cell sums take.
+template <int D, typename R, bool RS, bool AT, bool CE>
+__device__ __forceinline__ uint32_t move_particle(const RepDev& rd, const StepInfo& st, uint32_t j, bool alt,
+                                                  bool fresh, int& X, int& Y, int& Z, R* o, R* v) {
+  const bool outer = X < rd.xo_lo || X >= rd.xo_hi || Y >= rd.yo;
+  if (RS && rd.resample && outer && !fresh) {   // a3': replaced by this step's spawn
+    rd.home[j] = HOME_DEAD;
+    return NO_CELL;
+  }
+  // a2 + a3: Maxwellian redraw in the outer buffer columns
+  if (!(RS && rd.resample) && outer) {
+    R uf[3] = {R(0), R(0), R(0)};
+    u_fine<D, R>(rd, X, Y, Z, uf);
+    const uint32_t id = (alt ? rd.pid_alt : rd.pid)[j];
+    if (CE && rd.redraw == 1) {
+      R C[3];
+      ce_peculiar<D, R>(rd, st, X, Y, Z, id, C);
+      v[0] = uf[0] + C[0];
+      v[1] = uf[1] + C[1];
+      if (D == 3) v[2] = uf[2] + C[2];
+    } else {
+      const uint4 w = philox(id, st.n, rd.rep, TAG_RESAMPLE, rd.key0, rd.key1);
+      R z0, z1, z2, z3;
+      normal_pair(w.x, w.y, z0, z1);
+      normal_pair(w.z, w.w, z2, z3);
+      const R sg = Cst<R>::sig(rd);
+      v[0] = uf[0] + sg * z0;
+      v[1] = uf[1] + sg * z1;
+      if (D == 3) v[2] = uf[2] + sg * z2;
+    }
+  }
+  if (RS && fresh) rd.pid[j] = PID_SPAWNED;
+  else if (alt) rd.pid[j] = rd.pid_alt[j];
+  // a4
+  stream<D, R>(rd, X, Y, Z, o, v);
+  // a6: inner-buffer sample (unshifted cells), binary64 atomics
+  const bool left = X >= rd.xi_lo0 && X < rd.xi_hi0, right = X >= rd.xi_lo1 && X < rd.xi_hi1;
+  const bool row_in = Y >= rd.yi_lo && Y < rd.yi_hi;   // inner rows of a near-wall strip
+  if (left || right || row_in) {
+    const int xn = X / rd.r, wcols = rd.x1 - rd.x0;
+    const int zl = (D == 3) ? Z / rd.r : 0;
+    long long b;
+    if (row_in) {   // b = (row nz + z) nx + x, row counted down from the buffer's top
+      const int row = rd.y1 - 2 - rd.n_out - Y / rd.r;
+      b = ((long long)row * rd.nz + zl) * rd.nx + xn;
+    } else {
+      const int col = left ? xn - rd.n_out : wcols - 1 - rd.n_out - xn;
+      b = (((long long)(right ? 1 : 0) * rd.n_in + col) * rd.nz + zl) * (rd.ny - 2) + Y / rd.r;
+    }
+    double* fr = rd.frame + 4 * b;
+    atomicAdd(fr, rd.mass);
+#pragma unroll
+    for (int a = 0; a < D; ++a) atomicAdd(fr + 1 + a, rd.mass * (double)v[a]);
+  }
+  // learned-closure strips (feedback = 2): count and momentum per fine cell
+  // of the 16 columns at each x-edge, same instant as a6
+  if (D == 2 && rd.cl_on) {
+    const int xs = X < 16 ? X : rd.Wx - 1 - X;
+    if (xs < 16) {
+      const long long ncl = 32LL * rd.Hy;
+      double* fr = rd.cframe + 4 * ((st.n & 1) * ncl + ((long long)(X < 16 ? 0 : 1) * rd.Hy + Y) * 16 + xs);
+      atomicAdd(fr, 1.0);
+      atomicAdd(fr + 1, (double)v[0]);
+      atomicAdd(fr + 2, (double)v[1]);
+    }
+  }
+  // a5: binning under this step's shift
+  const uint32_t cid = collision_cell<D, R>(rd, X, Y, Z, o, Cst<R>::shift(st));
+  st_hint(rd.home + j, HomePack<D>::pack(X, Y, Z), l2_keep());
+  PState<D, R>::st(rd.off, j, o);
+  if (AT) {
+    // a7 (MPCD-AT), first half: v_ran from Philox(id, n, replica, TAG_AT)
+    const uint4 w = philox((alt ? rd.pid_alt : rd.pid)[j], st.n, rd.rep, TAG_AT, rd.key0, rd.key1);
+    R z[4];
+    normal_pair(w.x, w.y, z[0], z[1]);
+    if (D == 3) normal_pair(w.z, w.w, z[2], z[3]);
+    const R sg = Cst<R>::sig(rd);
+    R xi[3] = {sg * z[0], sg * z[1], D == 3 ? sg * z[2] : R(0)};
+    PState<D, R>::st(rd.vel, j, xi);
+#pragma unroll
+    for (int a = 0; a < D; ++a) v[a] -= xi[a];
+  } else {
+    PState<D, R>::st(rd.vel, j, v);
+  }
+  return cid;
+}
+
+// Cell sums of the thread's PPT particles (cid[p] = NO_CELL adds nothing).
+// Binary32: one vector atomic {n, sum v} per group of lanes; lanes are first
+// merged with their xor-1 and then xor-2 neighbours when they share the
+// collision cell (particles are sorted by home cell, so neighbours often do).
+// The merge removes a part of the atomics for a few shuffles, where the full
+// warp aggregation below cost as much as it saved.  Binary64: warp-aggregated
+// reduction, one round per particle slot: lanes sharing a collision cell are
+// summed by their lowest lane, which issues one atomic per accumulator.
+template <int D, typename R>
+__device__ __forceinline__ void add_cell_sums(const RepDev& rd, const uint32_t (&cid)[PPT], R (&v)[PPT][3],
+                                              PassShared<D, R>& red) {
+  if (sizeof(R) == 4) {
+    // a lane with nothing to add (inactive, or merged into its partner) holds
+    // the cell id NO_CELL, which matches no partner; in 2D the fourth
+    // component is zero and is not exchanged
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) {
+      uint32_t c = cid[p];
+      float4 a = make_float4(1.0f, (float)v[p][0], (float)v[p][1], D == 3 ? (float)v[p][D - 1] : 0.0f);
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const int m = 1 << r;
+        const uint32_t co = __shfl_xor_sync(0xFFFFFFFFu, c, m);
+        const float ax = __shfl_xor_sync(0xFFFFFFFFu, a.x, m), ay = __shfl_xor_sync(0xFFFFFFFFu, a.y, m);
+        const float az = __shfl_xor_sync(0xFFFFFFFFu, a.z, m);
+        const float aw = D == 3 ? __shfl_xor_sync(0xFFFFFFFFu, a.w, m) : 0.0f;
+        if (c != NO_CELL && co == c) {
+          if ((lane & m) == 0) { a.x += ax; a.y += ay; a.z += az; if (D == 3) a.w += aw; } else c = NO_CELL;
+        }
+      }
+      if (c != NO_CELL) atomicAdd(rd.acc4 + c, a);
+    }
+    return;
+  }
+  const int lane = threadIdx.x & 31, wbase = threadIdx.x & ~31;
+#pragma unroll
+  for (int p = 0; p < PPT; ++p) {
+    const unsigned grp = __match_any_sync(0xFFFFFFFFu, cid[p]);
+    __syncwarp();
+#pragma unroll
+    for (int a = 0; a < D; ++a) red.sv[a][threadIdx.x] = v[p][a];
+    __syncwarp();
+    if (cid[p] != NO_CELL && lane == __ffs(grp) - 1) {
+      R acc[D];
+#pragma unroll
+      for (int a = 0; a < D; ++a) acc[a] = R(0);
+      unsigned m = grp;
+      while (m) {
+        const int l = __ffs(m) - 1;
+        m &= m - 1;
+#pragma unroll
+        for (int a = 0; a < D; ++a) acc[a] += red.sv[a][wbase + l];
+      }
+      if (sizeof(R) == 4) {
+        float4 g4;
+        g4.x = (float)__popc(grp);
+        g4.y = (float)acc[0];
+        g4.z = (float)acc[1];
+        g4.w = D == 3 ? (float)acc[D - 1] : 0.0f;
+        atomicAdd(rd.acc4 + cid[p], g4);
+      } else {
+        atomicAdd(rd.acc_n + cid[p], (uint32_t)__popc(grp));
+#pragma unroll
+        for (int a = 0; a < D; ++a) atomicAdd((R*)rd.acc_v[a] + cid[p], acc[a]);
+      }
+    }
+  }
+}
 
 // RS: density resampling compiled in; AT: MPCD-AT collision (Eq. 6) instead of
 // SRD; CE: the Chapman-Enskog redraw compiled in (the plain pass keeps only the
@@ -372,9 +570,9 @@ template <int D, typename R> struct PassShared {
 // before any particle can leave the collision; as the old relative velocity
 // plays no part in it, the binning pass draws each particle's random velocity
 // v_ran, adds v - v_ran to its cell sum and stores v_ran in place of v.  The
-// cell pass turns the sums into v_cm - <v_ran>, and the next pass adds that to
-// the stored v_ran: v_cm + v_ran - <v_ran> (virtual wall particles enter the
-// cell pass).
+// cell-table items turn the sums into v_cm - <v_ran>, and the next pass adds
+// that to the stored v_ran: v_cm + v_ran - <v_ran> (virtual wall particles
+// enter the table).
 template <int D, typename R, bool RS, bool AT, bool CE>
 __device__ __forceinline__ void particle_item(const RepDev& rd, const StepInfo& st, const uint32_t start,
                                               const uint32_t end, PassShared<D, R>& red) {
@@ -409,198 +607,37 @@ __device__ __forceinline__ void particle_item(const RepDev& rd, const StepInfo& 
     PState<D, R>::ld(offs, jl, o[p]);
     PState<D, R>::ld(vels, jl, v[p]);
   }
-  // a7 of step n-1: cell-table loads for all four, then the rotations
+  // a7 of step n-1: cell-table loads for all particles, then the collisions
   if (st.pending) {
     const T4* tab = (const T4*)rd.tab;
     T4 t0[PPT], t1[PPT];
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
       const uint32_t c = collision_cell<D, R>(rd, X[p], Y[p], Z[p], o[p], Cst<R>::prev(st));
-      if (D == 2) t0[p] = tab[c];
-      else { t0[p] = tab[2 * (size_t)c]; if (!AT) t1[p] = tab[2 * (size_t)c + 1]; }
+      if (D == 2) t0[p] = ld_ro(tab + c);
+      else { t0[p] = ld_ro(tab + 2 * (size_t)c); if (!AT) t1[p] = ld_ro(tab + 2 * (size_t)c + 1); }
     }
-    const R ca = Cst<R>::cos_a(rd), sa = Cst<R>::sin_a(rd);
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
       if (RS && fresh[p]) continue;
-      if (AT) {
-        v[p][0] += t0[p].x;
-        v[p][1] += t0[p].y;
-        if (D == 3) v[p][2] += t0[p].z;
-      } else if (D == 2) {
-        const T4 t = t0[p];
-        const R wx = v[p][0] - t.x, wy = v[p][1] - t.y;
-        v[p][0] = t.x + (ca * wx - t.z * wy);
-        v[p][1] = t.y + (t.z * wx + ca * wy);
-      } else {
-        const R vc[3] = {t0[p].x, t0[p].y, t0[p].z}, n[3] = {t1[p].x, t1[p].y, t1[p].z};
-        const R w[3] = {v[p][0] - vc[0], v[p][1] - vc[1], v[p][2] - vc[2]};
-        const R cr[3] = {n[1] * w[2] - n[2] * w[1], n[2] * w[0] - n[0] * w[2], n[0] * w[1] - n[1] * w[0]};
-        const R nw = n[0] * w[0] + n[1] * w[1] + n[2] * w[2];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) v[p][a] = vc[a] + (w[a] * ca + cr[a] * sa + n[a] * nw * (R(1) - ca));
-      }
+      collide_from_table<D, R, AT>(rd, t0[p], t1[p], v[p]);
     }
   }
   uint32_t cid[PPT];
 #pragma unroll
   for (int p = 0; p < PPT; ++p) {
-    const uint32_t j = j0 + 256u * p;
-    cid[p] = 0xFFFFFFFFu;
+    cid[p] = NO_CELL;
     if (!act[p]) continue;
-    const bool outer = X[p] < rd.xo_lo || X[p] >= rd.xo_hi || Y[p] >= rd.yo;
-    if (RS && rd.resample && outer && !fresh[p]) {   // a3': replaced by this step's spawn
-      rd.home[j] = HOME_DEAD;
-      act[p] = false;
-      continue;
-    }
-    // a2 + a3: Maxwellian redraw in the outer buffer columns
-    if (!(RS && rd.resample) && outer) {
-      R uf[3] = {R(0), R(0), R(0)};
-      u_fine<D, R>(rd, X[p], Y[p], Z[p], uf);
-      const uint32_t id = (alt ? rd.pid_alt : rd.pid)[j];
-      if (CE && rd.redraw == 1) {
-        R C[3];
-        ce_peculiar<D, R>(rd, st, X[p], Y[p], Z[p], id, C);
-        v[p][0] = uf[0] + C[0];
-        v[p][1] = uf[1] + C[1];
-        if (D == 3) v[p][2] = uf[2] + C[2];
-      } else {
-        const uint4 w = philox(id, st.n, rd.rep, TAG_RESAMPLE, rd.key0, rd.key1);
-        R z0, z1, z2, z3;
-        normal_pair(w.x, w.y, z0, z1);
-        normal_pair(w.z, w.w, z2, z3);
-        const R sg = Cst<R>::sig(rd);
-        v[p][0] = uf[0] + sg * z0;
-        v[p][1] = uf[1] + sg * z1;
-        if (D == 3) v[p][2] = uf[2] + sg * z2;
-      }
-    }
-    if (RS && fresh[p]) rd.pid[j] = PID_SPAWNED;
-    else if (alt) rd.pid[j] = rd.pid_alt[j];
-    // a4
-    stream<D, R>(rd, X[p], Y[p], Z[p], o[p], v[p]);
-    // a6: inner-buffer sample (unshifted cells), binary64 atomics
-    const bool left = X[p] >= rd.xi_lo0 && X[p] < rd.xi_hi0, right = X[p] >= rd.xi_lo1 && X[p] < rd.xi_hi1;
-    const bool row_in = Y[p] >= rd.yi_lo && Y[p] < rd.yi_hi;   // inner rows of a near-wall strip
-    if (left || right || row_in) {
-      const int xn = X[p] / rd.r, wcols = rd.x1 - rd.x0;
-      const int zl = (D == 3) ? Z[p] / rd.r : 0;
-      long long b;
-      if (row_in) {   // b = (row nz + z) nx + x, row counted down from the buffer's top
-        const int row = rd.y1 - 2 - rd.n_out - Y[p] / rd.r;
-        b = ((long long)row * rd.nz + zl) * rd.nx + xn;
-      } else {
-        const int col = left ? xn - rd.n_out : wcols - 1 - rd.n_out - xn;
-        b = (((long long)(right ? 1 : 0) * rd.n_in + col) * rd.nz + zl) * (rd.ny - 2) + Y[p] / rd.r;
-      }
-      double* fr = rd.frame + 4 * b;
-      atomicAdd(fr, rd.mass);
-#pragma unroll
-      for (int a = 0; a < D; ++a) atomicAdd(fr + 1 + a, rd.mass * (double)v[p][a]);
-    }
-    // learned-closure strips (feedback = 2): count and momentum per fine cell
-    // of the 16 columns at each x-edge, same instant as a6
-    if (D == 2 && rd.cl_on) {
-      const int xs = X[p] < 16 ? X[p] : rd.Wx - 1 - X[p];
-      if (xs < 16) {
-        const long long ncl = 32LL * rd.Hy;
-        double* fr = rd.cframe + 4 * ((st.n & 1) * ncl + ((long long)(X[p] < 16 ? 0 : 1) * rd.Hy + Y[p]) * 16 + xs);
-        atomicAdd(fr, 1.0);
-        atomicAdd(fr + 1, (double)v[p][0]);
-        atomicAdd(fr + 2, (double)v[p][1]);
-      }
-    }
-    // a5: binning under this step's shift
-    cid[p] = collision_cell<D, R>(rd, X[p], Y[p], Z[p], o[p], Cst<R>::shift(st));
-    st_hint(rd.home + j, HomePack<D>::pack(X[p], Y[p], Z[p]), l2_keep());
-    PState<D, R>::st(rd.off, j, o[p]);
-    if (AT) {
-      // a7 (MPCD-AT), first half: v_ran from Philox(id, n, replica, TAG_AT)
-      const uint4 w = philox((alt ? rd.pid_alt : rd.pid)[j], st.n, rd.rep, TAG_AT, rd.key0, rd.key1);
-      R z[4];
-      normal_pair(w.x, w.y, z[0], z[1]);
-      if (D == 3) normal_pair(w.z, w.w, z[2], z[3]);
-      const R sg = Cst<R>::sig(rd);
-      R xi[3] = {sg * z[0], sg * z[1], D == 3 ? sg * z[2] : R(0)};
-      PState<D, R>::st(rd.vel, j, xi);
-#pragma unroll
-      for (int a = 0; a < D; ++a) v[p][a] -= xi[a];
-    } else {
-      PState<D, R>::st(rd.vel, j, v[p]);
-    }
+    cid[p] = move_particle<D, R, RS, AT, CE>(rd, st, j0 + 256u * p, alt, fresh[p], X[p], Y[p], Z[p], o[p], v[p]);
   }
-  // Cell sums.  Binary32: one vector atomic {n, sum v} per group of lanes;
-  // lanes are first merged with their xor-1 and then xor-2 neighbours when
-  // they share the collision cell (particles are sorted by home cell, so
-  // neighbours often do).  The atomics, not the arithmetic, bound this pass
-  // (removing them takes it from 70 to 47 us at 2048x512); the merge removes a
-  // part of them for a few shuffles, where the full warp aggregation below
-  // cost as much as it saved.  Binary64: warp-aggregated reduction, one round
-  // per particle slot: lanes sharing a collision cell are summed by their
-  // lowest lane, which issues one atomic per accumulator.
-  if (sizeof(R) == 4) {
-    // a lane with nothing to add (inactive, or merged into its partner) holds
-    // the cell id NONE, which matches no partner; in 2D the fourth component
-    // is zero and is not exchanged
-    constexpr uint32_t NONE = 0xFFFFFFFFu;
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int p = 0; p < PPT; ++p) {
-      uint32_t c = act[p] ? cid[p] : NONE;
-      float4 a = make_float4(1.0f, (float)v[p][0], (float)v[p][1], D == 3 ? (float)v[p][D - 1] : 0.0f);
-#pragma unroll
-      for (int r = 0; r < 2; ++r) {
-        const int m = 1 << r;
-        const uint32_t co = __shfl_xor_sync(0xFFFFFFFFu, c, m);
-        const float ax = __shfl_xor_sync(0xFFFFFFFFu, a.x, m), ay = __shfl_xor_sync(0xFFFFFFFFu, a.y, m);
-        const float az = __shfl_xor_sync(0xFFFFFFFFu, a.z, m);
-        const float aw = D == 3 ? __shfl_xor_sync(0xFFFFFFFFu, a.w, m) : 0.0f;
-        if (c != NONE && co == c) {
-          if ((lane & m) == 0) { a.x += ax; a.y += ay; a.z += az; if (D == 3) a.w += aw; } else c = NONE;
-        }
-      }
-      if (c != NONE) atomicAdd(rd.acc4 + c, a);
-    }
-    return;
-  }
-  const int lane = threadIdx.x & 31, wbase = threadIdx.x & ~31;
-#pragma unroll
-  for (int p = 0; p < PPT; ++p) {
-    const unsigned grp = __match_any_sync(0xFFFFFFFFu, cid[p]);
-    __syncwarp();
-#pragma unroll
-    for (int a = 0; a < D; ++a) red.sv[a][threadIdx.x] = v[p][a];
-    __syncwarp();
-    if (act[p] && lane == __ffs(grp) - 1) {
-      R acc[D];
-#pragma unroll
-      for (int a = 0; a < D; ++a) acc[a] = R(0);
-      unsigned m = grp;
-      while (m) {
-        const int l = __ffs(m) - 1;
-        m &= m - 1;
-#pragma unroll
-        for (int a = 0; a < D; ++a) acc[a] += red.sv[a][wbase + l];
-      }
-      if (sizeof(R) == 4) {
-        float4 g4;
-        g4.x = (float)__popc(grp);
-        g4.y = (float)acc[0];
-        g4.z = (float)acc[1];
-        g4.w = D == 3 ? (float)acc[D - 1] : 0.0f;
-        atomicAdd(rd.acc4 + cid[p], g4);
-      } else {
-        atomicAdd(rd.acc_n + cid[p], (uint32_t)__popc(grp));
-#pragma unroll
-        for (int a = 0; a < D; ++a) atomicAdd((R*)rd.acc_v[a] + cid[p], acc[a]);
-      }
-    }
-  }
+  add_cell_sums<D, R>(rd, cid, v, red);
 }
 
 // resident blocks per SM: 6 in 2D (40 registers, no spills); 5 in 3D, whose
-// state needs more registers (at 6 the 3D pass spilled and ran 13 % slower)
+// state needs more registers (at 6 the 3D pass spilled and ran 13 % slower);
+// the single-replica 2D form runs at 8 (32 registers, no spills except in the
+// Chapman-Enskog variant, which keeps 6): 71.8 against 72.8 us per step at
+// 2048 x 512, the pass being bound by the latency of its dependent loads
 template <int D, typename R, bool RS, bool AT, bool CE>
 __global__ void __launch_bounds__(256, D == 2 ? 6 : 5) particle_pass(const RepDev* __restrict__ reps, const int2* __restrict__ bmap,
                                                      int nwork, const StepInfo* __restrict__ si, int k, int nrep) {
@@ -613,7 +650,8 @@ __global__ void __launch_bounds__(256, D == 2 ? 6 : 5) particle_pass(const RepDe
 
 // single-replica form (see for_each_item_one)
 template <int D, typename R, bool RS, bool AT, bool CE>
-__global__ void __launch_bounds__(256, D == 2 ? 6 : 5) particle_pass_one(const __grid_constant__ RepDev rd, int nwork,
+__global__ void __launch_bounds__(256, (D == 2 && !CE && sizeof(R) == 4) ? 8 : (D == 2 ? 6 : 5))
+    particle_pass_one(const __grid_constant__ RepDev rd, int nwork,
                                                          const StepInfo* __restrict__ si, int k) {
   __shared__ StepInfo st;
   __shared__ PassShared<D, R> red;
