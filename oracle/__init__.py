@@ -188,7 +188,8 @@ class OracleSim:
 
     def closure_impose(self, y) -> None:
         """a8 of the learned closure for the step just taken, from the network
-        output y of shape (P, 16, 16, 3)."""
+        output y of shape (P, 16, 16, 3): the LB update of the next step
+        imposes it on the inner-buffer nodes."""
         arr = np.ascontiguousarray(y, dtype=np.float64).ravel()
         if arr.size != self.closure_patches * 768:
             raise ValueError("closure output has the wrong size")

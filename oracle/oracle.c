@@ -954,10 +954,11 @@ long orc_closure_patches(const orc_sim* s) { return s->cl_on ? 2L * s->cl_npy : 
 
 /* Imposition from the network output: on each inner-buffer LB node, u_bar =
  * sqrt(kT/m) times the mean predicted velocity over the node's r x r fine
- * cells (u_x mirrored back on the right side); the stored post-collision
- * populations become f_eq(rho_LB, u_bar), rho_LB the node's LB density of
- * the step (the MPCD density is not imposed, as in a8).  Fine cell (row, xi)
- * is read from patch min(row / 16, npy - 1) of its side. */
+ * cells (u_x mirrored back on the right side).  As for a8, the LB update of
+ * the next step gives the node the post-collision populations
+ * f_eq(rho_LB, u_bar), rho_LB its density of that update (the MPCD density
+ * is not imposed); this records u_bar for it.  Fine cell (row, xi) is read
+ * from patch min(row / 16, npy - 1) of its side. */
 int orc_closure_impose(orc_sim* s, const double* y) {
   const orc_params* p = &s->p;
   if (!s->cl_on) return -1;
@@ -975,14 +976,12 @@ int orc_closure_impose(orc_sim* s, const double* y) {
             long m = (pch * CL_W + (row - cl_row0(s, py))) * CL_W + xi;
             su[0] += y[3*m+1]; su[1] += y[3*m+2];
           }
-        double u[3];
-        u[0] = (side ? -1.0 : 1.0) * sig * su[0] / (double)(s->r * s->r);
-        u[1] = sig * su[1] / (double)(s->r * s->r);
-        u[2] = 0.0;
-        int x = side == 0 ? s->x0 + s->n_out + col : s->x1 - 1 - s->n_out - col;
-        double feq[19];
-        orc_feq(p->lattice, s->rho[nidx(s, x, yn, 0)], u, feq);
-        for (int i = 0; i < s->q; ++i) s->f[i * s->nnode + nidx(s, x, yn, 0)] = feq[i];
+        /* inner-buffer entry of the node (slab form, nz = 1) */
+        long bi = ((long)side * s->n_in + col) * (p->ny - 2) + (yn - 1);
+        s->imp[4*bi] = 1.0;
+        s->imp[4*bi+1] = (side ? -1.0 : 1.0) * sig * su[0] / (double)(s->r * s->r);
+        s->imp[4*bi+2] = sig * su[1] / (double)(s->r * s->r);
+        s->imp[4*bi+3] = 0.0;
       }
   return 0;
 }

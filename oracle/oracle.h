@@ -31,8 +31,8 @@
  * learned closure: each step records the instantaneous fine-cell fields of
  * the two 16-column strips at the region's x-edges, keeps the last 8 of them
  * and their exponential moving average, and lays them out as the network's
- * 16 x 16 patches; orc_closure_impose then imposes f_eq from a network
- * output that the caller computes (oracle/closure.py).
+ * 16 x 16 patches; orc_closure_impose then has the next LB update impose
+ * f_eq from a network output that the caller computes (oracle/closure.py).
  * All random numbers come from Philox4x32-10 keyed by (seed) with counter
  * (id, step, replica, tag); every floating-point step is IEEE binary64.
  */
@@ -100,8 +100,9 @@ long orc_step_count(const orc_sim* s);
 /* Closure patches per replica (0 unless feedback = 2 with a region). */
 long orc_closure_patches(const orc_sim* s);
 /* a8 of the learned closure for the step just completed: y [P][16][16][3]
- * is the network output in patch layout.  No-op before 8 frames exist.
- * Returns -1 if the replica has no closure sampling. */
+ * is the network output in patch layout; the LB update of the next step
+ * imposes it (as the windowed a8).  No-op before 8 frames exist.  Returns -1
+ * if the replica has no closure sampling. */
 int  orc_closure_impose(orc_sim* s, const double* y);
 
 /* building blocks exposed for the pin tests */
