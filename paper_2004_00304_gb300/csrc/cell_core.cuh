@@ -124,6 +124,57 @@ __device__ __forceinline__ void cell_table_item(const RepDev& rd, uint32_t m, bo
   }
 }
 
+// ---------------------------------------------------------------------------
+// Learned-closure strips (feedback = 2): the particle pass of step m adds 1
+// and v of every particle in a strip cell (the 16 fine columns nearest each
+// x-edge of the region) to half m & 1 of the frame; the LB launch of step
+// m + 1 turns it into the fields of step m, puts them in the 8-step ring and
+// the moving average (the training target) and clears the half for step m + 2.
+constexpr int CL_W = 16;                 // strip width and patch side, fine cells
+constexpr int CL_F = 8;                  // frames in the network input
+constexpr double CL_EMA_A = 1.0 / 500.0; // moving-average weight of the newest frame
+
+__device__ __forceinline__ int cl_row0(const RepDev& rd, int py) {
+  return py == rd.cl_npy - 1 ? rd.Hy - CL_W : CL_W * py;
+}
+
+// this step's fields of one strip cell from its frame {count, sum vx, sum vy}
+__device__ __forceinline__ void cl_phi(const RepDev& rd, const double* fr, int side, double phi[3]) {
+  const double n = fr[0];
+  phi[0] = n * rd.cl_inv_ppc - 1.0;
+  phi[1] = 0.0;
+  phi[2] = 0.0;
+  if (n > 0) {
+    const double s = rd.cl_inv_sig / n;
+    phi[1] = (side ? -fr[1] : fr[1]) * s;
+    phi[2] = fr[2] * s;
+  }
+}
+
+// ring slot n mod 8 and moving average of strip cell c
+__device__ __forceinline__ void cl_update(const RepDev& rd, uint32_t n, long long c, const double phi[3]) {
+  const long long ncl = 32LL * rd.Hy;
+  float* ring = rd.cring + ((long long)(n & (CL_F - 1)) * ncl + c) * 3;
+  double* e = rd.cema + 3 * c;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    ring[k] = (float)phi[k];
+    e[k] = n == 0 ? phi[k] : e[k] + (phi[k] - e[k]) * CL_EMA_A;
+  }
+}
+
+// Strip cells [start, end) of the frame of step m, one per thread.
+__device__ __forceinline__ void closure_fold_item(const RepDev& rd, uint32_t m, long long start, long long end) {
+  const long long ncl = 32LL * rd.Hy;
+  const long long c = start + threadIdx.x;
+  if (c >= end) return;
+  double* fr = rd.cframe + 4 * ((m & 1) * ncl + c);
+  double phi[3];
+  cl_phi(rd, fr, (int)(c / (16LL * rd.Hy)), phi);
+  cl_update(rd, m, c, phi);
+  fr[0] = 0.0; fr[1] = 0.0; fr[2] = 0.0;
+}
+
 // Index b of the inner-buffer LB node (x, y, z) in the window arrays, or -1:
 // slab  b = ((side n_in + col) nz + z)(ny - 2) + y - 1, col counted inwards
 //       from the region's edge (left: x = x0 + n_out + col, right:

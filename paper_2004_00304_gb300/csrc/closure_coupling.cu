@@ -3,88 +3,38 @@
 //
 // particle_pass(n) adds 1 and v of every particle whose home cell lies in a
 // strip (the 16 fine columns nearest each x-edge of the region, xi = distance
-// from the edge) to that cell's frame, half n & 1 of a double buffer.  After
-// cell_pass(n), per strip cell, the fields of step n are
+// from the edge) to that cell's frame, half n & 1 of a double buffer.  The
+// fields of step n per strip cell,
 //     phi_0 = n / ppc - 1,
 //     phi_1 = +-(sum v_x / n) / sqrt(kT/m)   (- on the right strip, seen in a mirror),
-//     phi_2 = (sum v_y / n) / sqrt(kT/m)     (velocities 0 in an empty cell);
-// they go into slot n mod 8 of a ring of the last 8 steps (binary32) and the
+//     phi_2 = (sum v_y / n) / sqrt(kT/m)     (velocities 0 in an empty cell),
+// go into slot n mod 8 of a ring of the last 8 steps (binary32) and the
 // moving average e <- e + (phi - e) / 500 (binary64, e = phi at n = 0), the
-// training target.  Patches: side-major, ceil(Hy/16) per side; patch py covers
-// rows 16 py .. 16 py + 15 except the last, which covers Hy - 16 .. Hy - 1 and
-// "owns" (updates, imposes) only its rows from 16 (npy - 1) on.
+// training target, by work items of the LB launch of step n + 1
+// (cell_core.cuh), which also clear the half.  Patches: side-major,
+// ceil(Hy/16) per side; patch py covers rows 16 py .. 16 py + 15 except the
+// last, which covers Hy - 16 .. Hy - 1 and "owns" only its rows from
+// 16 (npy - 1) on.
 //
-// Without network parameters closure_in does the per-cell update.  With
-// parameters closure_step does everything in one launch, one CTA per patch of
-// the batch: the update of the cells it owns and, on evaluation steps (n = n0,
-// n0 + K, n0 + 2K, ... for the inference interval K, n0 = max(7, the step at
-// which the parameters were loaded)), the network input built
-// from the ring straight into shared memory, the network (the tcgen05 layers
+// On evaluation steps (n = n0, n0 + K, n0 + 2K, ... for the inference
+// interval K, n0 = max(7, the step at which the parameters were loaded))
+// closure_step runs once after the particle pass, one CTA per patch of the
+// batch: the network input built from the ring (steps n - 7 .. n - 1) and the
+// frame of step n straight into shared memory, the network (the tcgen05 layers
 // of net_fused.cuh), the output and u_bar = sqrt(kT/m) times the mean
-// predicted velocity over each inner-buffer node's r x r cells; from n0 on
-// every step imposes f_eq(rho_LB, u_bar) with the latest u_bar on the
-// inner-buffer LB nodes whose rows the patch owns.
-#include "kernels.h"
+// predicted velocity over each inner-buffer node's r x r cells.  From the LB
+// update after the first evaluation on, every update gives the inner-buffer
+// nodes f_eq(rho_LB, u_bar) with the latest u_bar (lb_core.cuh), so the steps
+// between evaluations launch nothing for the closure.
+#include "cell_core.cuh"
 #include "net_fused.cuh"
 
 namespace lbm {
 
-constexpr int CL_W = 16;                 // strip width and patch side, fine cells
-constexpr int CL_F = 8;                  // frames in the network input
-constexpr double CL_EMA_A = 1.0 / 500.0; // moving-average weight of the newest frame
-
-__device__ __forceinline__ int cl_row0(const RepDev& rd, int py) {
-  return py == rd.cl_npy - 1 ? rd.Hy - CL_W : CL_W * py;
-}
-
-// this step's fields of one strip cell from its frame {count, sum vx, sum vy}
-__device__ __forceinline__ void cl_phi(const RepDev& rd, const double* fr, int side, double phi[3]) {
-  const double n = fr[0];
-  phi[0] = n * rd.cl_inv_ppc - 1.0;
-  phi[1] = 0.0;
-  phi[2] = 0.0;
-  if (n > 0) {
-    const double s = rd.cl_inv_sig / n;
-    phi[1] = (side ? -fr[1] : fr[1]) * s;
-    phi[2] = fr[2] * s;
-  }
-}
-
-// ring slot n mod 8 and moving average of strip cell c
-__device__ __forceinline__ void cl_update(const RepDev& rd, uint32_t n, long long c, const double phi[3]) {
-  const long long ncl = 32LL * rd.Hy;
-  float* ring = rd.cring + ((long long)(n & (CL_F - 1)) * ncl + c) * 3;
-  double* e = rd.cema + 3 * c;
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    ring[k] = (float)phi[k];
-    e[k] = n == 0 ? phi[k] : e[k] + (phi[k] - e[k]) * CL_EMA_A;
-  }
-}
-
-// sampling only (no parameters): one thread per strip cell
-__device__ __forceinline__ void closure_in_item(const RepDev& rd, const StepInfo& st, const int2 bm) {
-  const long long ncl = 32LL * rd.Hy;
-  const long long c = (long long)bm.y * blockDim.x + threadIdx.x;
-  if (c >= ncl) return;
-  double* fr = rd.cframe + 4 * ((st.n & 1) * ncl + c);
-  double phi[3];
-  cl_phi(rd, fr, (int)(c / (16LL * rd.Hy)), phi);
-  cl_update(rd, st.n, c, phi);
-  fr[0] = 0.0; fr[1] = 0.0; fr[2] = 0.0;
-  double* fo = rd.cframe + 4 * (((st.n + 1) & 1) * ncl + c);
-  fo[0] = 0.0; fo[1] = 0.0; fo[2] = 0.0;
-}
-
-__global__ void __launch_bounds__(256) closure_in(const RepDev* __restrict__ reps, const int2* __restrict__ bmap,
-                                                  int nwork, const StepInfo* __restrict__ si, int k, int nrep) {
-  __shared__ RepDev rd;
-  __shared__ StepInfo st;
-  for_each_item(bmap, nwork, reps, si, k, nrep, rd, st, [&](const int2 bm) { closure_in_item(rd, st, bm); });
-}
-
 // network input of one replica's patches after step n, [P][16][16][24]
-// binary64: frame f (oldest first) of step n - 7 + f is ring slot (n + 1 + f) mod 8
+// binary64: frame f (oldest first) of step n - 7 + f is ring slot (n + 1 + f)
+// mod 8 for f < 7; the newest, of step n, is still the frame the next LB
+// launch folds in, so its fields are formed here
 __global__ void closure_in_out(RepDev rd, uint32_t n, double* __restrict__ out) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= 2LL * rd.cl_npy * CL_W * CL_W) return;
@@ -93,40 +43,33 @@ __global__ void closure_in_out(RepDev rd, uint32_t n, double* __restrict__ out) 
   const long long ncl = 32LL * rd.Hy;
   const long long c = ((long long)side * rd.Hy + cl_row0(rd, py) + yy) * CL_W + xi;
 #pragma unroll
-  for (int f = 0; f < CL_F; ++f) {
+  for (int f = 0; f < CL_F - 1; ++f) {
     const float* r = rd.cring + ((long long)((n + 1u + (uint32_t)f) & (CL_F - 1)) * ncl + c) * 3;
 #pragma unroll
     for (int k = 0; k < 3; ++k) out[24 * i + 3 * f + k] = (double)r[k];
   }
+  double phi[3];
+  cl_phi(rd, rd.cframe + 4 * ((n & 1) * ncl + c), side, phi);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) out[24 * i + 3 * (CL_F - 1) + k] = (double)(float)phi[k];
 }
 
-// moving averages of one replica in patch layout [P][16][16][3], binary64
-__global__ void closure_target_out(RepDev rd, double* __restrict__ out) {
+// moving averages after step n of one replica in patch layout
+// [P][16][16][3], binary64: the stored average runs to step n - 1, the frame
+// of step n is added here as the next LB launch will
+__global__ void closure_target_out(RepDev rd, uint32_t n, double* __restrict__ out) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= 2LL * rd.cl_npy * CL_W * CL_W) return;
   const int p = (int)(i / (CL_W * CL_W)), yy = (int)((i / CL_W) % CL_W), xi = (int)(i % CL_W);
   const int side = p / rd.cl_npy, py = p % rd.cl_npy;
+  const long long ncl = 32LL * rd.Hy;
   const long long c = ((long long)side * rd.Hy + cl_row0(rd, py) + yy) * CL_W + xi;
+  double phi[3];
+  cl_phi(rd, rd.cframe + 4 * ((n & 1) * ncl + c), side, phi);
 #pragma unroll
-  for (int k = 0; k < 3; ++k) out[3 * i + k] = rd.cema[3 * c + k];
-}
-
-// f_eq(rho_LB, u) on one inner-buffer node, in the kernel's precision
-template <typename S>
-__device__ __forceinline__ void cl_impose_node(const RepDev& rd, uint32_t n, int x, int yn,
-                                               typename Store<S>::R ux, typename Store<S>::R uy) {
-  using R = typename Store<S>::R;
-  using L = Lattice<9>;
-  const long long node = x + (long long)rd.nx * yn;
-  S* dst = (S*)rd.f[(n & 1) ^ 1];
-  const R rl = ((const R*)rd.rho)[node];
-  const R uu = ux * ux + uy * uy;
-#pragma unroll
-  for (int i = 0; i < 9; ++i) {
-    const R cu = L::cx(i) * ux + L::cy(i) * uy;
-    const R dev = (R)L::w(i) * ((rl - R(1)) + rl * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu));
-    Store<S>::st(dst + i * rd.nnode + node, dev, rd.fp16_scale,
-                 sizeof(S) == 2 ? (mix32((uint32_t)node * 19u + (uint32_t)i + n * 0x632BE5ABu) | 1u) : 0u);
+  for (int k = 0; k < 3; ++k) {
+    const double e = rd.cema[3 * c + k];
+    out[3 * i + k] = n == 0 ? phi[k] : e + (phi[k] - e) * CL_EMA_A;
   }
 }
 
@@ -165,28 +108,7 @@ __global__ void __launch_bounds__(128, 1) closure_step(const RepDev* __restrict_
   const int nodes = (rows_end - own0) / rd.r;   // inner-buffer nodes per column whose rows this patch owns
   const uint32_t first = (uint32_t)rd.cl_first;
   const bool eval = n >= first && (n - first) % (uint32_t)rd.cl_interval == 0u;
-  if (!eval) {
-    // between evaluations: update the owned cells, impose the last prediction
-#pragma unroll
-    for (int t = 0; t < 2; ++t) {
-      const int m = 128 * t + 32 * warp + lane, row = row0 + (m >> 4);
-      if (row < own0) continue;
-      const long long c = ((long long)side * rd.Hy + row) * CL_W + (m & 15);
-      double phi[3];
-      cl_phi(rd, rd.cframe + 4 * ((n & 1) * ncl + c), side, phi);
-      cl_update(rd, n, c, phi);
-      double* fo = rd.cframe + 4 * (((n + 1) & 1) * ncl + c);
-      fo[0] = 0.0; fo[1] = 0.0; fo[2] = 0.0;
-    }
-    if (n > first)   // a prediction exists
-      for (int i = tid; i < nodes * rd.n_in; i += blockDim.x) {
-        const int col = i / nodes, yn = 1 + own0 / rd.r + i % nodes;
-        const double* u = rd.cl_u + 2 * (((long long)side * rd.n_in + col) * (rd.ny - 2) + (yn - 1));
-        const int x = side == 0 ? rd.x0 + rd.n_out + col : rd.x1 - 1 - rd.n_out - col;
-        cl_impose_node<S>(rd, n, x, yn, (R)u[0], (R)u[1]);
-      }
-    return;
-  }
+  if (!eval) return;   // launched on evaluation steps only (the chunk graphs disable the rest)
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s_addr(&tmem_base)),
@@ -209,8 +131,8 @@ __global__ void __launch_bounds__(128, 1) closure_step(const RepDev* __restrict_
   __syncthreads();   // zeros and barrier initialisation before anyone writes or waits
 
   // input: the 8 frames of this thread's two pixels (all loads first, so that
-  // they are in flight together); the owner of a cell also updates its ring
-  // slot and moving average and clears its next frame
+  // they are in flight together): steps n - 7 .. n - 1 from the ring, step n
+  // from its frame (folded into the ring by the next LB launch)
   float mean8[2][3];
   float v[2][3 * CL_F + 8];
   double fr[2][3];
@@ -238,11 +160,6 @@ __global__ void __launch_bounds__(128, 1) closure_step(const RepDev* __restrict_
     for (int q = 0; q < 3; ++q) v[t][3 * (CL_F - 1) + q] = (float)phi[q];
 #pragma unroll
     for (int q = 24; q < 32; ++q) v[t][q] = 0.0f;
-    if (row0 + (m >> 4) >= own0) {
-      cl_update(rd, n, cc[t], phi);
-      double* fo = rd.cframe + 4 * (((n + 1) & 1) * ncl + cc[t]);
-      fo[0] = 0.0; fo[1] = 0.0; fo[2] = 0.0;
-    }
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
       float s = 0.0f;
@@ -314,7 +231,8 @@ __global__ void __launch_bounds__(128, 1) closure_step(const RepDev* __restrict_
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   }
 
-  // imposition on the inner-buffer nodes whose fine rows this patch owns
+  // u_bar of the inner-buffer nodes whose fine rows this patch owns; the LB
+  // updates from step n + 1 on impose it
   if (!s_fail) {
     const float* s_y = reinterpret_cast<const float*>(sm);
     for (int i = tid; i < nodes * rd.n_in; i += blockDim.x) {
@@ -329,10 +247,8 @@ __global__ void __launch_bounds__(128, 1) closure_step(const RepDev* __restrict_
       const R scale = (R)rd.sig / (R)(rd.r * rd.r);
       const R ux = (side ? -su0 : su0) * scale, uy = su1 * scale;
       double* u = rd.cl_u + 2 * (((long long)side * rd.n_in + col) * (rd.ny - 2) + (yn - 1));
-      u[0] = (double)ux;   // imposed again until the next evaluation
+      u[0] = (double)ux;   // imposed until the next evaluation
       u[1] = (double)uy;
-      const int x = side == 0 ? rd.x0 + rd.n_out + col : rd.x1 - 1 - rd.n_out - col;
-      cl_impose_node<S>(rd, n, x, yn, ux, uy);
     }
   }
   if (s_fail && tid == 0) atomicExch(err, 1);
@@ -341,13 +257,6 @@ __global__ void __launch_bounds__(128, 1) closure_step(const RepDev* __restrict_
   if (warp == 0) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128u) : "memory");
   }
-}
-
-cudaError_t launch_closure_in(const Launch& L, const int2* bmap, int nwork, int k) {
-  if (nwork == 0) return cudaSuccess;
-  static const int g = grid_cap(grid_for(closure_in, 256, 1 << 30));
-  closure_in<<<g < nwork ? g : nwork, 256, 0, L.stream>>>(L.reps, bmap, nwork, L.si, k, L.nrep);
-  return cudaGetLastError();
 }
 
 template <typename S>
@@ -373,9 +282,9 @@ cudaError_t launch_closure_in_out(const RepDev& rd, uint32_t n, double* out, cud
   return cudaGetLastError();
 }
 
-cudaError_t launch_closure_target_out(const RepDev& rd, double* out, cudaStream_t st) {
+cudaError_t launch_closure_target_out(const RepDev& rd, uint32_t n, double* out, cudaStream_t st) {
   const long long np = 2LL * rd.cl_npy * CL_W * CL_W;
-  closure_target_out<<<(int)((np + 255) / 256), 256, 0, st>>>(rd, out);
+  closure_target_out<<<(int)((np + 255) / 256), 256, 0, st>>>(rd, n, out);
   return cudaGetLastError();
 }
 

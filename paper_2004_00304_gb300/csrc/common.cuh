@@ -235,9 +235,10 @@ struct RepDev {
   double cl_inv_ppc, cl_inv_sig;   // 1 / ppc, 1 / sqrt(kT/m)
   int cl_interval;                 // steps between network evaluations
   int cl_first;                    // first evaluation: max(7, step of the parameter load)
+  int cl_imp;                      // network loaded: the LB imposes cl_u after the first evaluation
   double* cl_u;                    // [nbuf][2] velocity imposed from the latest evaluation
   double* cframe;          // [2][2 Hy 16][4] count, sum vx, sum vy of step n in half n & 1
-                           // (binary64 atomics; the other half is cleared for step n + 1)
+                           // (binary64 atomics; folded and cleared by the LB launch of n + 1)
   float* cring;            // [8][2 Hy 16][3] fields of the last 8 steps
   double* cema;            // [2 Hy 16][3] moving averages (training target)
   float* cl_y;             // network output of the handle's batch [P][16][16][3]

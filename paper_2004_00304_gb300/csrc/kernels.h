@@ -58,9 +58,10 @@ cudaError_t launch_cell_table(int q, int prec, const RepDev& rd, uint32_t m, boo
 // WINDOW_MEAN after step m ([nbuf][4] binary64).
 cudaError_t launch_window_out(int dim, int prec, const RepDev& rd, uint32_t m, double* out, cudaStream_t st);
 
-// learned closure (feedback = 2): closure_in updates the strip ring and
-// moving averages (no parameters); closure_step does that, the network and
-// the imposition in one launch per step; readouts of input and target.
+// learned closure (feedback = 2): the LB launch folds the strip frames into
+// the ring and moving averages and imposes the latest prediction;
+// closure_step runs the network on evaluation steps; read-outs of input and
+// target after step n.
 struct NetMeta { long long woff[4], boff[4]; };
 struct ClosureNet {                 // what closure_step reads of the network
   const __nv_bfloat16* img;         // weight images (net_fused.cuh layout)
@@ -68,10 +69,9 @@ struct ClosureNet {                 // what closure_step reads of the network
   NetMeta meta;
   int* err;                         // set when a bounded wait gave up
 };
-cudaError_t launch_closure_in(const Launch& L, const int2* bmap, int nwork, int k);
 cudaError_t launch_closure_step(int prec, const Launch& L, const int4* ptab, int P, int k, const ClosureNet& cn);
 cudaError_t launch_closure_in_out(const RepDev& rd, uint32_t n, double* out, cudaStream_t st);
-cudaError_t launch_closure_target_out(const RepDev& rd, double* out, cudaStream_t st);
+cudaError_t launch_closure_target_out(const RepDev& rd, uint32_t n, double* out, cudaStream_t st);
 
 // the closure network (closure.cu) as the coupled step uses it: input and
 // output buffers of the handle's batch, weights cast once per parameter load,

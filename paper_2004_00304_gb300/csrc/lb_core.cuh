@@ -69,6 +69,39 @@ template <> struct Row<__half, 4> {
 __device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 
+// a8 of step m on inner-buffer node b (LB node index `node`, LB density rl of
+// this update): the window takes frame m (sampled by the particle pass of
+// step m), and with feedback = 1 the node's post-collision populations become
+// f_eq(rl, u_bar) (Eq. 2) with the window mean u_bar, written over the BGK
+// values its thread has stored; nothing is imposed from the window of step 0.
+// With the learned closure (feedback = 2) u_bar is the latest prediction
+// (cl_u), from the update after the first evaluation on.
+template <int Q, typename S>
+__device__ __noinline__ void a8_node(const RepDev& rd, uint32_t m, long long b, int node, typename Store<S>::R rl) {
+  using L = Lattice<Q>;
+  using R = typename Store<S>::R;
+  double W4[4];
+  window_sums(rd, m, b, true, W4);
+  R rb, ub[3];
+  const R M = window_mean<L::D, R>(rd, m, W4, rb, ub);
+  const bool net = rd.feedback == 2 && rd.cl_imp && m >= (uint32_t)rd.cl_first;
+  if (net) {
+    ub[0] = (R)rd.cl_u[2 * b];
+    ub[1] = (R)rd.cl_u[2 * b + 1];
+    ub[2] = R(0);
+  }
+  if (!((rd.feedback == 1 && m >= 1u && M > R(0)) || net)) return;
+  S* dst = (S*)rd.f[((m + 1u) & 1) ^ 1];
+  const R uu = ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const R cu = L::cx(i) * ub[0] + L::cy(i) * ub[1] + L::cz(i) * ub[2];
+    const R dev = (R)L::w(i) * ((rl - R(1)) + rl * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu));
+    Store<S>::st(dst + i * rd.nnode + node, dev, rd.fp16_scale,
+                 sizeof(S) == 2 ? (mix32((uint32_t)node * 19u + (uint32_t)i + (m + 1u) * 0x632BE5ABu) | 1u) : 0u);
+  }
+}
+
 // Collision (BGK + Guo source, Eq. 1-2) of V consecutive nodes x0.. of the
 // row (y, z) starting at node index `row`, whose arrived populations are
 // d[i][v]; the post-collision values go to the other buffer, rho / u where
@@ -153,34 +186,14 @@ __device__ __forceinline__ void lb_finish(const RepDev& rd, const StepInfo& st, 
       uv[2 * N + row + x] = mu[2][v];
     }
   }
-  // a8 of step m = n - 1 on the inner-buffer nodes: the window takes frame m
-  // (sampled by the particle pass of step m), and with feedback = 1 the node's
-  // post-collision populations become f_eq(rho_LB, u_bar) (Eq. 2) at its LB
-  // density of this update, written over the BGK values stored above (the
-  // populations are dead by now, which keeps this rare branch from adding to
-  // the row's register pressure); nothing is imposed from the window of step 0.
+  // a8 of step m = n - 1 on the inner-buffer nodes (a few lanes of a few
+  // rows; after the stores above, in a function of its own so that it does
+  // not add to the row's register allocation)
   if (rd.nbuf > 0 && st.n >= 1u) {
-    const uint32_t m = st.n - 1u;
 #pragma unroll
     for (int v = 0; v < V; ++v) {
       const long long b = inner_index(rd, x0 + v, y, z);
-      if (b < 0) continue;
-      double W4[4];
-      window_sums(rd, m, b, true, W4);
-      R rb, ub[3];
-      const R M = window_mean<L::D, R>(rd, m, W4, rb, ub);
-      if (rd.feedback == 1 && m >= 1u && M > R(0)) {
-        const R rl = mr[v];
-        const R uu = ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2];
-        const int node = row + x0 + v;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-          const R cu = L::cx(i) * ub[0] + L::cy(i) * ub[1] + L::cz(i) * ub[2];
-          const R dev = (R)L::w(i) * ((rl - R(1)) + rl * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu));
-          Store<S>::st(dst + i * N + node, dev, scale,
-                       sizeof(S) == 2 ? (mix32((uint32_t)node * 19u + (uint32_t)i + st.n * 0x632BE5ABu) | 1u) : 0u);
-        }
-      }
+      if (b >= 0) a8_node<Q, S>(rd, st.n - 1u, b, row + x0 + v, mr[v]);
     }
   }
 }
@@ -191,9 +204,15 @@ template <int Q, typename S, int V>
 __device__ __forceinline__ void lb_row(const RepDev& rd, const StepInfo& st, const int4 bm) {
   using L = Lattice<Q>;
   using R = typename Store<S>::R;
-  if (bm.y < 0) {   // item -1 - b: block b of blockDim CPT cells of the table of step n - 1
-    if (st.cells)
+  if (bm.y < 0) {
+    if (bm.z < 0) {   // item (-1 - b, -1): strip cells of block b, closure frame of step n - 1
+      if (st.n >= 1u) {
+        const long long c0 = (long long)(-1 - bm.y) * blockDim.x;
+        closure_fold_item(rd, st.n - 1u, c0, 32LL * rd.Hy);
+      }
+    } else if (st.cells) {   // item -1 - b: block b of blockDim CPT cells of the table of step n - 1
       cell_table_item<Q, S>(rd, st.n - 1u, st.prev_f[1] > 0.0f, (long long)(-1 - bm.y) * blockDim.x * CPT, rd.ncell);
+    }
     return;
   }
   const int nx = rd.nx, ny = rd.ny, nz = rd.nz;

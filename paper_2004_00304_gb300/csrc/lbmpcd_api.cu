@@ -43,7 +43,7 @@ struct lbmpcd {
   std::vector<void*> allocs;                    // handle-wide
   RepDev* d_reps = nullptr;
   int4* bm_lb = nullptr;
-  int2 *bm_p = nullptr, *bm_t = nullptr, *bm_cl = nullptr;
+  int2 *bm_p = nullptr, *bm_t = nullptr;
   int4* ptab = nullptr;                         // closure patches of the batch: (replica, side, py)
   int4* bm_lb256 = nullptr;                     // LB map with 256-thread row tiles (persistent kernel)
   int nb_lb256 = 0;
@@ -57,7 +57,8 @@ struct lbmpcd {
   bool pers_graph = true;                       // the persistent launch captures into a graph
   unsigned* d_bar = nullptr;                    // grid barrier: count, generation, error
   unsigned bar_spin = 0;                        // polls before a barrier wait gives up (0: default)
-  int nb_lb = 0, nb_p = 0, nb_t = 0, nb_cl = 0, n_ptab = 0;
+  int nb_lb = 0, nb_p = 0, nb_t = 0, n_ptab = 0;
+  bool has_cl = false;                          // some replica samples closure strips (feedback = 2)
   lbmpcd_net* net = nullptr;                    // learned closure, batch of all replicas' patches
   int cl_P = 0;                                 // patches in the batch
   bool cl_params = false;                       // parameters loaded: impose from the network
@@ -72,7 +73,10 @@ struct lbmpcd {
   bool maps_dirty = true;
   std::vector<char> pending;                    // host mirror of d_pending
   std::vector<char> cells;                      // host mirror of d_cells
-  cudaGraphExec_t graphs[NGRAPH] = {};          // chunk of 2^i steps
+  cudaGraphExec_t graphs[NGRAPH] = {};          // chunk of 2^i steps (no closure network)
+  cudaGraphExec_t g_eval = nullptr;             // one step with the closure network
+  cudaGraphExec_t g_period = nullptr;           // `period` steps, the network on every K-th from the first
+  int period = 0;                               // K floor(KCHUNK / K) for K <= KCHUNK, else 0
   bool graphs_ready = false;
   int* d_sorted = nullptr;                      // per replica: the sort ran since the last chunk
   long long last_sort = 0;                      // step count at the last sort (the seeded state is sorted)
@@ -111,8 +115,10 @@ static void free_list(std::vector<void*>& list) {
 
 // the captured chunks hold the kernels' arguments: drop them when those change
 static void drop_graphs(lbmpcd* h) {
-  for (auto& g : h->graphs)
-    if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+  for (auto* g : {&h->graphs[0], &h->graphs[1], &h->graphs[2], &h->graphs[3], &h->graphs[4], &h->graphs[5],
+                  &h->graphs[6], &h->g_eval, &h->g_period})
+    if (*g) { cudaGraphExecDestroy(*g); *g = nullptr; }
+  h->period = 0;
   h->graphs_ready = false;
 }
 
@@ -301,10 +307,17 @@ static int build_maps(lbmpcd* h) {
   int rc0 = closure_batch(h);
   if (rc0) return rc0;
   std::vector<int4> lb;
-  std::vector<int2> pp, tt, cl, sp;
+  std::vector<int2> pp, tt, sp;
   std::vector<int4> pt, lb256;
+  h->has_cl = false;
   for (int r = 0; r < h->nrep; ++r) {
     const RepDev& d = h->rd[r];
+    if (d.cl_on) {   // closure strip cells: the frame of the previous step folded into ring and average
+      const long long ncl = 32LL * d.Hy;
+      for (long long b = 0; b < (ncl + 127) / 128; ++b) lb.push_back(make_int4(r, (int)(-1 - b), -1, 0));
+      for (long long b = 0; b < (ncl + 255) / 256; ++b) lb256.push_back(make_int4(r, (int)(-1 - b), -1, 0));
+      h->has_cl = true;
+    }
     if (d.has_region) {   // cell-table items first: their accumulators are still in L2
       for (long long b = 0; b < (d.ncell + 128 * CPT - 1) / (128 * CPT); ++b) lb.push_back(make_int4(r, (int)(-1 - b), 0, 0));
       for (long long b = 0; b < (d.ncell + 256 * CPT - 1) / (256 * CPT); ++b) lb256.push_back(make_int4(r, (int)(-1 - b), 0, 0));
@@ -327,8 +340,6 @@ static int build_maps(lbmpcd* h) {
       for (long long b = 0; b < (nouter + 255) / 256; ++b) sp.push_back(make_int2(r, (int)b));
     }
     if (d.cl_on) {
-      const long long ncl = 2LL * d.Hy * 16;
-      for (long long b = 0; b < (ncl + 255) / 256; ++b) cl.push_back(make_int2(r, (int)b));
       for (int side = 0; side < 2; ++side)
         for (int py = 0; py < d.cl_npy; ++py) pt.push_back(make_int4(r, side, py, 0));   // batch order
     }
@@ -336,7 +347,6 @@ static int build_maps(lbmpcd* h) {
   int rc = upload_map(h, &h->bm_lb, &h->nb_lb, lb);
   if (!rc) rc = upload_map(h, &h->bm_p, &h->nb_p, pp);
   if (!rc) rc = upload_map(h, &h->bm_t, &h->nb_t, tt);
-  if (!rc) rc = upload_map(h, &h->bm_cl, &h->nb_cl, cl);
   if (!rc) rc = upload_map(h, &h->ptab, &h->n_ptab, pt);
   if (!rc) rc = upload_map(h, &h->bm_lb256, &h->nb_lb256, lb256);
   if (!rc) rc = upload_map(h, &h->bm_s, &h->nb_s, sp);
@@ -486,9 +496,31 @@ extern "C" int lbmpcd_set_region(lbmpcd* h, int replica, const int lo[3], const 
 }
 
 // One chunk of kcount steps (the sort, when due, runs before it: run_sort).
-static bool persistent(const lbmpcd* h) { return h->mode == 1 && h->nb_cl == 0; }
+static bool persistent(const lbmpcd* h) { return h->mode == 1 && !h->has_cl; }
 
-static int run_chunk(lbmpcd* h, int kcount) {
+// the closure network runs on step n (handle-wide: every closure replica
+// shares the first evaluation and the interval)
+static bool closure_eval(const lbmpcd* h, long long n) {
+  for (int r = 0; r < h->nrep; ++r) {
+    const RepDev& d = h->rd[r];
+    if (!d.cl_on) continue;
+    return n >= d.cl_first && (n - d.cl_first) % d.cl_interval == 0;
+  }
+  return false;
+}
+
+// Which steps of a chunk run the closure network: none, the first only, every
+// K-th from the first (the periodic graph), or as the step count says (a
+// chunk launched directly).
+enum { CL_NONE = 0, CL_FIRST = 1, CL_EVERY_K = 2, CL_BY_STEP = 3 };
+
+static int closure_interval(const lbmpcd* h) {
+  for (int r = 0; r < h->nrep; ++r)
+    if (h->rd[r].cl_on) return h->rd[r].cl_interval;
+  return 1;
+}
+
+static int run_chunk(lbmpcd* h, int kcount, int cl_mode) {
   Launch L{h->d_reps, h->nrep, h->d_si, h->stream, h->d_flag + 8, h->rd.data()};
   CK(h, launch_prep(h->dim, L, h->d_si, kcount, h->d_sorted, h->d_step, h->d_pending, h->d_cells,
                     h->d_last_shift));
@@ -501,9 +533,11 @@ static int run_chunk(lbmpcd* h, int kcount) {
     CK(h, launch_lb(h->q, h->prec, h->lbvec, h->lb_tma, L, h->bm_lb, h->nb_lb, k));
     if (h->nb_s) CK(h, launch_spawn(h->dim, h->prec, L, h->bm_s, h->nb_s, k));
     CK(h, launch_particles(h->dim, h->prec, h->nb_s > 0, h->at, h->ce, L, h->bm_p, h->nb_p, k));
-    if (h->nb_cl) {
-      if (h->cl_params) CK(h, launch_closure_step(h->prec, L, h->ptab, h->n_ptab, k, net_closure(h->net)));
-      else CK(h, launch_closure_in(L, h->bm_cl, h->nb_cl, k));
+    if (h->has_cl && h->cl_params) {
+      const bool net = cl_mode == CL_FIRST ? k == 0
+                     : cl_mode == CL_EVERY_K ? k % closure_interval(h) == 0
+                     : cl_mode == CL_BY_STEP ? closure_eval(h, h->nstep + k) : false;
+      if (net) CK(h, launch_closure_step(h->prec, L, h->ptab, h->n_ptab, k, net_closure(h->net)));
     }
   }
   return LBMPCD_OK;
@@ -525,8 +559,8 @@ static int run_sort(lbmpcd* h) {
   return LBMPCD_OK;
 }
 
-// Capture the chunk of 2^i steps into graphs[i] on a capturing stream.
-static int capture_chunk(lbmpcd* h, int i) {
+// Capture a chunk of kcount steps (closure network per cl_mode) into *out.
+static int capture_chunk(lbmpcd* h, int kcount, int cl_mode, cudaGraphExec_t* out) {
   cudaGraph_t g = nullptr;
   cudaStream_t cap = h->stream;
   bool own = false;
@@ -535,37 +569,59 @@ static int capture_chunk(lbmpcd* h, int i) {
   CK(h, cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
   cudaStream_t keep = h->stream;
   h->stream = cap;
-  int rc = run_chunk(h, 1 << i);
+  int rc = run_chunk(h, kcount, cl_mode);
   h->stream = keep;
   cudaError_t e = cudaStreamEndCapture(cap, &g);
   if (!rc && e == cudaSuccess) {
-    e = cudaGraphInstantiate(&h->graphs[i], g, 0);
-    if (e != cudaSuccess) h->graphs[i] = nullptr;
+    e = cudaGraphInstantiate(out, g, 0);
+    if (e != cudaSuccess) *out = nullptr;
   }
   if (g) cudaGraphDestroy(g);
   if (own) cudaStreamDestroy(cap);
   if (rc) return rc;
-  if (e != cudaSuccess || !h->graphs[i]) return cuda_fail(h, e != cudaSuccess ? e : cudaErrorUnknown, "graph capture");
+  if (e != cudaSuccess || !*out) return cuda_fail(h, e != cudaSuccess ? e : cudaErrorUnknown, "graph capture");
   return LBMPCD_OK;
 }
 
-// Every chunk length is captured at the first step after the maps were
-// (re)built, so that no later call pays for a capture.
+// Every graph is captured at the first step after the maps were (re)built,
+// so that no later call pays for a capture: the chunk lengths without the
+// closure network and, with it loaded, one evaluation step and the periodic
+// chunk (the network only where it runs: a disabled node in a graph still
+// cost ~3.5 us per step).
 static int capture_all(lbmpcd* h) {
-  for (int i = 0; i < NGRAPH; ++i) {
-    const int rc = capture_chunk(h, i);
-    if (rc) {
-      drop_graphs(h);
-      if (!persistent(h)) return rc;
-      // the cooperative launch did not capture: launch the persistent chunks directly
-      cudaGetLastError();
-      h->pers_graph = false;
-      h->err.clear();
-      return LBMPCD_OK;
+  int rc = LBMPCD_OK;
+  for (int i = 0; i < NGRAPH && !rc; ++i) rc = capture_chunk(h, 1 << i, CL_NONE, &h->graphs[i]);
+  if (!rc && h->has_cl && h->cl_params) {
+    rc = capture_chunk(h, 1, CL_FIRST, &h->g_eval);
+    const int K = closure_interval(h);
+    if (!rc && K <= KCHUNK) {
+      h->period = K * (KCHUNK / K);
+      rc = capture_chunk(h, h->period, CL_EVERY_K, &h->g_period);
     }
+  }
+  if (rc) {
+    drop_graphs(h);
+    if (!persistent(h)) return rc;
+    // the cooperative launch did not capture: launch the persistent chunks directly
+    cudaGetLastError();
+    h->pers_graph = false;
+    h->err.clear();
+    return LBMPCD_OK;
   }
   h->graphs_ready = true;
   return LBMPCD_OK;
+}
+
+// steps from n to the next step that runs the closure network (0: n does)
+static long long to_next_eval(const lbmpcd* h, long long n) {
+  for (int r = 0; r < h->nrep; ++r) {
+    const RepDev& d = h->rd[r];
+    if (!d.cl_on) continue;
+    if (n < d.cl_first) return d.cl_first - n;
+    const long long ph = (n - d.cl_first) % d.cl_interval;
+    return ph ? d.cl_interval - ph : 0;
+  }
+  return 1LL << 40;
 }
 
 static int chunk_len(int left) {
@@ -585,15 +641,24 @@ extern "C" int lbmpcd_step(lbmpcd* h, int nsteps) {
     const int rc = capture_all(h);
     if (rc) return rc;
   }
+  const bool net = h->has_cl && h->cl_params;
   int left = nsteps;
   while (left > 0) {
-    const int kc = chunk_len(left);
     if (sort_due(h)) { const int rc = run_sort(h); if (rc) return rc; }
-    if (h->graphs_ready) {
-      CK(h, cudaGraphLaunch(h->graphs[log2i(kc)], h->stream));
-    } else {
-      const int rc = run_chunk(h, kc);
+    int kc;
+    if (!h->graphs_ready) {
+      kc = chunk_len(left);
+      const int rc = run_chunk(h, kc, CL_BY_STEP);
       if (rc) return rc;
+    } else if (net && to_next_eval(h, h->nstep) == 0) {
+      // an evaluation step: the periodic chunk when it fits, else the single step
+      const bool per = h->g_period && left >= h->period;
+      kc = per ? h->period : 1;
+      CK(h, cudaGraphLaunch(per ? h->g_period : h->g_eval, h->stream));
+    } else {
+      const long long gap = net ? to_next_eval(h, h->nstep) : (long long)left;
+      kc = chunk_len((int)(gap < left ? gap : left));
+      CK(h, cudaGraphLaunch(h->graphs[log2i(kc)], h->stream));
     }
     left -= kc;
     h->nstep += kc;
@@ -660,11 +725,8 @@ extern "C" int lbmpcd_step_profiled(lbmpcd* h, int nsteps, double* phase_ms, lon
       bracket(1, [&] { return launch_lb(h->q, h->prec, h->lbvec, h->lb_tma, L, h->bm_lb, h->nb_lb, k); });
       if (h->nb_s) bracket(2, [&] { return launch_spawn(h->dim, h->prec, L, h->bm_s, h->nb_s, k); });
       if (h->nb_p) bracket(2, [&] { return launch_particles(h->dim, h->prec, h->nb_s > 0, h->at, h->ce, L, h->bm_p, h->nb_p, k); });
-      if (h->nb_cl)
-        bracket(5, [&] {
-          return h->cl_params ? launch_closure_step(h->prec, L, h->ptab, h->n_ptab, k, net_closure(h->net))
-                              : launch_closure_in(L, h->bm_cl, h->nb_cl, k);
-        });
+      if (h->has_cl && h->cl_params && closure_eval(h, h->nstep + k))
+        bracket(5, [&] { return launch_closure_step(h->prec, L, h->ptab, h->n_ptab, k, net_closure(h->net)); });
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     for (size_t i = 0; i < phase.size() && e == cudaSuccess; ++i) {
@@ -823,13 +885,15 @@ extern "C" int lbmpcd_get_fields(lbmpcd* h, int replica, int field, void* dst, s
       else e = launch_window_out(h->dim, h->prec, d, (uint32_t)(h->nstep - 1), (double*)buf, h->stream);
       break;
     case LBMPCD_CLOSURE_IN:
-      e = launch_closure_in_out(d, (uint32_t)(h->nstep - 1), (double*)buf, h->stream);
+      if (h->nstep == 0) e = cudaMemsetAsync(buf, 0, (size_t)n * 8, h->stream);
+      else e = launch_closure_in_out(d, (uint32_t)(h->nstep - 1), (double*)buf, h->stream);
       break;
     case LBMPCD_CLOSURE_OUT:
       e = launch_real_out(P_FP32, net_output(h->net) + (long long)d.cl_p0 * 256 * 3, n, (double*)buf, h->stream);
       break;
     case LBMPCD_CLOSURE_TARGET:
-      e = launch_closure_target_out(d, (double*)buf, h->stream);
+      if (h->nstep == 0) e = cudaMemsetAsync(buf, 0, (size_t)n * 8, h->stream);
+      else e = launch_closure_target_out(d, (uint32_t)(h->nstep - 1), (double*)buf, h->stream);
       break;
     case LBMPCD_DIAG: {
       double* o = (double*)buf;
@@ -909,13 +973,15 @@ extern "C" int lbmpcd_set_closure(lbmpcd* h, const float* theta, long long count
   if (theta && count != lbmpcd_net_num_params())
     return fail(h, LBMPCD_ERR_INVALID_ARG, "parameter count does not match the closure network");
   if (theta && interval < 1) return fail(h, LBMPCD_ERR_INVALID_ARG, "interval must be >= 1");
-  if (theta)
-    for (int r = 0; r < h->nrep; ++r)
-      if (h->rd[r].cl_on) {
+  for (int r = 0; r < h->nrep; ++r)
+    if (h->rd[r].cl_on) {
+      if (theta) {
         h->rd[r].cl_interval = interval;
         h->rd[r].cl_first = (int)std::max<long long>(7, h->nstep);
-        h->maps_dirty = true;
       }
+      h->rd[r].cl_imp = theta ? 1 : 0;   // the LB imposes the prediction once one exists
+      h->maps_dirty = true;
+    }
   if (h->maps_dirty) { int rc = build_maps(h); if (rc) return rc; }
   if (!theta) {
     h->cl_params = false;

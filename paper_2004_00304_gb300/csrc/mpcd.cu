@@ -407,7 +407,8 @@ constexpr uint32_t NO_CELL = 0xFFFFFFFFu;   // a particle that adds nothing to t
 // shift, and the stores of its new state (MPCD-AT: with the random velocity of
 // this step's collision in place of v).  alt: the state was read from the
 // sorted copy; fresh: created by this step's spawn.  Returns the collision
-// cell, or NO_CELL for a removed particle.  v keeps what the cell sums take.
+// cell, or NO_CELL for a removed particle.  v keeps what the cell sums take
+// (with SRD the velocity of the sampling instant, which add_strip_sums uses).
 template <int D, typename R, bool RS, bool AT, bool CE>
 __device__ __forceinline__ uint32_t move_particle(const RepDev& rd, const StepInfo& st, uint32_t j, bool alt,
                                                   bool fresh, int& X, int& Y, int& Z, R* o, R* v) {
@@ -461,9 +462,10 @@ __device__ __forceinline__ uint32_t move_particle(const RepDev& rd, const StepIn
 #pragma unroll
     for (int a = 0; a < D; ++a) atomicAdd(fr + 1 + a, rd.mass * (double)v[a]);
   }
-  // learned-closure strips (feedback = 2): count and momentum per fine cell
-  // of the 16 columns at each x-edge, same instant as a6
-  if (D == 2 && rd.cl_on) {
+  // learned-closure strips (feedback = 2), same instant as a6: with MPCD-AT
+  // (whose v is replaced below) count and momentum per strip cell here; with
+  // SRD the caller sums them per warp (add_strip_sums)
+  if (D == 2 && AT && rd.cl_on) {
     const int xs = X < 16 ? X : rd.Wx - 1 - X;
     if (xs < 16) {
       const long long ncl = 32LL * rd.Hy;
@@ -564,6 +566,44 @@ __device__ __forceinline__ void add_cell_sums(const RepDev& rd, const uint32_t (
   }
 }
 
+// Learned-closure strip frame (feedback = 2, SRD): count and momentum per
+// strip cell (the 16 fine columns at each x-edge of the region) of the moved
+// particles (home X, Y after streaming, velocity v of the sampling instant;
+// cid NO_CELL: nothing to add), binary64 atomics into half n & 1.  Particles
+// are sorted by home cell and strip cells are home cells, so lanes are first
+// merged with their xor-1 and xor-2 neighbours of the same cell; only warps
+// holding a strip particle (an eighth of them on the benchmark channels) take
+// this path.
+template <typename R>
+__device__ __forceinline__ void add_strip_sums(const RepDev& rd, const StepInfo& st, const uint32_t (&cid)[PPT],
+                                               const int (&X)[PPT], const int (&Y)[PPT], const R (&v)[PPT][3]) {
+  const long long ncl = 32LL * rd.Hy;
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int p = 0; p < PPT; ++p) {
+    const int xs = X[p] < 16 ? X[p] : rd.Wx - 1 - X[p];
+    int c = (cid[p] != NO_CELL && xs < 16) ? ((X[p] < 16 ? 0 : 1) * rd.Hy + Y[p]) * 16 + xs : -1;
+    if (!__any_sync(0xFFFFFFFFu, c >= 0)) continue;
+    double a0 = c >= 0 ? 1.0 : 0.0, a1 = (double)v[p][0], a2 = (double)v[p][1];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int m = 1 << r;
+      const int co = __shfl_xor_sync(0xFFFFFFFFu, c, m);
+      const double b0 = __shfl_xor_sync(0xFFFFFFFFu, a0, m), b1 = __shfl_xor_sync(0xFFFFFFFFu, a1, m);
+      const double b2 = __shfl_xor_sync(0xFFFFFFFFu, a2, m);
+      if (c >= 0 && co == c) {
+        if ((lane & m) == 0) { a0 += b0; a1 += b1; a2 += b2; } else c = -1;
+      }
+    }
+    if (c >= 0) {
+      double* fr = rd.cframe + 4 * ((st.n & 1) * ncl + c);
+      atomicAdd(fr, a0);
+      atomicAdd(fr + 1, a1);
+      atomicAdd(fr + 2, a2);
+    }
+  }
+}
+
 // RS: density resampling compiled in; AT: MPCD-AT collision (Eq. 6) instead of
 // SRD; CE: the Chapman-Enskog redraw compiled in (the plain pass keeps only the
 // Maxwellian one).  MPCD-AT needs the cell mean of the particles' random velocities
@@ -630,6 +670,7 @@ __device__ __forceinline__ void particle_item(const RepDev& rd, const StepInfo& 
     if (!act[p]) continue;
     cid[p] = move_particle<D, R, RS, AT, CE>(rd, st, j0 + 256u * p, alt, fresh[p], X[p], Y[p], Z[p], o[p], v[p]);
   }
+  if (D == 2 && !AT && rd.cl_on) add_strip_sums<R>(rd, st, cid, X, Y, v);
   add_cell_sums<D, R>(rd, cid, v, red);
 }
 
