@@ -233,7 +233,12 @@ int lbmpcd_tc_gemm_bf16(const void* A, const void* B, float* C, int M, int N, in
 /* The learned closure network (not in the paper; the MPCD->LB feedback of
  * the coupled step may use it in place of the long averaging window): a
  * 3x3 convolutional net 24 -> 64 -> 64 -> 64 -> 3 channels on 16 x 16 patches
- * of MPCD cells, ReLU between layers, plus the mean of its 8 input frames;
+ * of MPCD cells, ReLU between layers; the output is the mean of its 8 input
+ * frames plus the last layer's output less that output's mean over the 16
+ * rows of each patch column (per field), so that every column mean of every
+ * predicted field is that of the 8-frame mean and the closure cannot add or
+ * drain mass or momentum on average in any column of the coupling strip (the
+ * head's bias therefore has no effect and a zero gradient);
  * bf16 weights and activations, fp32 accumulation, every contraction on the
  * tcgen05 tensor cores.  Tensors are fp32, NHWC, device pointers: input
  * x[P][16][16][24] (frame f, field c at channel 3f + c: density deviation

@@ -10,9 +10,16 @@ statement of the learned coupling): input one 16 x 16 patch of MPCD cells with
 24 channels = 8 consecutive instantaneous frames x {density deviation
 n/ppc - 1, u_x / sqrt(kT/m), u_y / sqrt(kT/m)} (frame f, field c at channel
 3 f + c); three 3 x 3 convolutions with 64 channels and ReLU, a linear 3 x 3
-convolution to 3 channels, zero padding; the output is added to the mean of
-the 8 input frames, so the network learns a correction to the plain short
-window.  Layout NHWC; weights W[l] of shape (cout, 3, 3, cin), biases b[l].
+convolution to 3 channels, zero padding; the last layer's output, less its
+mean over the 16 rows of each patch column (per channel), is added to the
+mean of the 8 input frames.  The network thus learns a correction to the
+plain short window that redistributes each field along y within a patch
+column but leaves the column's mean that of the 8-frame mean: fed back into
+the flow, the closure cannot add or drain mass or momentum on average in any
+column of the coupling strip, whatever its fit.  (Unconstrained, an
+MSE-trained correction shrinks the predicted velocities towards the training
+set's mean, most at the patch edges where the zero padding starts, and the
+coupling loop amplifies that.)  Layout NHWC; weights W[l] of shape (cout, 3, 3, cin), biases b[l].
 
 Loss: mean squared error over all output values.
 """
@@ -71,20 +78,26 @@ def conv3x3(x: np.ndarray, W: np.ndarray, b: np.ndarray) -> np.ndarray:
     return out
 
 
-def forward(theta: np.ndarray, x: np.ndarray, emulate_bf16: bool = False):
+def forward(theta: np.ndarray, x: np.ndarray, emulate_bf16: bool = False, jitter=None):
     """Network output (P,16,16,3) and the per-layer cache for backward.
     emulate_bf16 rounds weights and stored activations to bf16 where the
-    CUDA path stores them in bf16 (inputs, hidden activations, weights)."""
+    CUDA path stores them in bf16 (inputs, hidden activations, weights).
+    jitter, if given, is applied to every layer's pre-activations z (a test
+    uses it to measure how far rounding-order-sized changes of z move the
+    bf16 and ReLU decisions downstream)."""
     r = bf16 if emulate_bf16 else (lambda a: a)
     layers = unpack(theta)
     a = r(x)
     cache = []
     for li, (W, b) in enumerate(layers):
         z = conv3x3(a, r(W), b)
+        if jitter is not None:
+            z = jitter(z)
         cache.append((a, z))
         a = r(np.maximum(z, 0.0)) if li < len(layers) - 1 else z
+    centred = a - a.mean(axis=1, keepdims=True)      # over y in each patch column
     mean8 = x.reshape(*x.shape[:3], 8, 3).mean(axis=3)
-    return a + mean8, cache
+    return centred + mean8, cache
 
 
 def loss(theta, x, t, emulate_bf16=False) -> float:
@@ -92,13 +105,15 @@ def loss(theta, x, t, emulate_bf16=False) -> float:
     return float(np.mean((y - t) ** 2))
 
 
-def backward(theta: np.ndarray, x: np.ndarray, t: np.ndarray, emulate_bf16: bool = False):
-    """Loss and its gradient with respect to the flat parameter vector."""
+def backward(theta: np.ndarray, x: np.ndarray, t: np.ndarray, emulate_bf16: bool = False, jitter=None):
+    """Loss and its gradient with respect to the flat parameter vector
+    (jitter: as in forward)."""
     r = bf16 if emulate_bf16 else (lambda a: a)
     layers = unpack(theta)
-    y, cache = forward(theta, x, emulate_bf16)
+    y, cache = forward(theta, x, emulate_bf16, jitter)
     L = float(np.mean((y - t) ** 2))
-    d = 2.0 * (y - t) / y.size                     # dL/dy, and dL/dz of the last (linear) layer
+    d = 2.0 * (y - t) / y.size                     # dL/dy
+    d = d - d.mean(axis=1, keepdims=True)          # dL/dz of the last (linear) layer: through the centring
     grads = [None] * len(layers)
     for li in range(len(layers) - 1, -1, -1):
         W, b = layers[li]

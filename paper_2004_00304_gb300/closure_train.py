@@ -44,6 +44,21 @@ def poiseuille(y, ny: int, tau: float, g: float):
     return g / (2.0 * nu) * (y - 1.0) * (ny - 1.0 - y)
 
 
+def matched_tau(ppc: float, kT: float, alpha: float, refine: int, mass: float = 1.0) -> float:
+    """LB relaxation time whose kinematic viscosity (tau - 1/2) / 3 equals that
+    of the 2D SRD fluid of the coupled region (kinetic-theory form: kinetic
+    part kT dt / m (M / (s (1 - cos 2 alpha)) - 1/2), collisional part
+    a^2 (1 - cos alpha) s / (12 M dt), s = M - 1 + e^-M, cell size a =
+    1 / refine, dt = 1).  With it the coupled channel's steady state is the
+    analytic Poiseuille profile of that viscosity."""
+    M = float(ppc)
+    s = M - 1.0 + math.exp(-M)
+    a = 1.0 / refine
+    kin = kT / mass * (M / (s * (1.0 - math.cos(2.0 * alpha))) - 0.5)
+    col = a * a * (1.0 - math.cos(alpha)) * s / (12.0 * M)
+    return 0.5 + 3.0 * (kin + col)
+
+
 def training_channels(n: int, seed: int, ny_choices=(64, 128, 256, 512), g_range=(1e-7, 1e-6),
                       umax: float = 0.05, **kw) -> list:
     """n channels: Ny drawn from ny_choices, g log-uniform in g_range and
@@ -141,7 +156,9 @@ def train(X, T, steps: int, batch: int = 32, lr: float = 1e-3, seed: int = 0, th
 
 def init_params(seed: int) -> np.ndarray:
     """He-normal weights, zero biases, the last layer scaled by 0.1 (the
-    network starts close to the plain 8-frame mean it corrects)."""
+    network starts close to the plain 8-frame mean it corrects; the
+    correction is centred along y in each patch column, so the column means
+    stay those of the 8-frame mean)."""
     rng = np.random.default_rng(seed)
     parts = []
     layers = [(24, 64), (64, 64), (64, 64), (64, 3)]

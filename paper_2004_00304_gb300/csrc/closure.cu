@@ -145,7 +145,8 @@ __global__ void k_im2colT(const __nv_bfloat16* __restrict__ a, int M, int Mpad, 
   colT[t] = v;
 }
 
-// z += b; hidden layers: a = bf16(relu(z)); last layer: y = z + mean of the 8 input frames
+// z += b; hidden layers: a = bf16(relu(z)); last layer: y = z + mean of the 8
+// input frames (k_center then takes z's column means off y)
 __global__ void k_epilogue(float* __restrict__ z, const float* __restrict__ theta, NetLayer L, int M, int last,
                            __nv_bfloat16* a, const float* __restrict__ x32, float* y) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -160,6 +161,36 @@ __global__ void k_epilogue(float* __restrict__ z, const float* __restrict__ thet
 #pragma unroll
     for (int f = 0; f < 8; ++f) s += x32[(long long)m * 24 + 3 * f + c];
     y[i] = v + 0.125f * s;
+  }
+}
+
+// dst[m][c] -= mean of src[.][c] over the 16 rows of m's patch column (pixel
+// m = 16 y + x of patch m / 256; same patch and x), c < 3: the centring of the
+// last layer's output (forward) and of dL/dy (backward: the centring is its
+// own adjoint).  One block of 256 threads per patch: warp w holds rows 2w and
+// 2w + 1, lanes l and l ^ 16 the same column.  Each thread reads and writes
+// only its own row, so dst may be src.
+__global__ void __launch_bounds__(256) k_center(float* dst, int dstride, const float* src, int sstride) {
+  __shared__ float part[8][16][3];
+  const long long m = (long long)blockIdx.x * 256 + threadIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float v[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    v[c] = src[m * sstride + c];
+    v[c] += __shfl_xor_sync(0xFFFFFFFFu, v[c], 16);
+  }
+  if (lane < 16) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) part[warp][lane][c] = v[c];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    float s = 0.0f;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) s += part[w][lane & 15][c];
+    dst[m * dstride + c] -= s * (1.0f / 16.0f);
   }
 }
 
@@ -393,6 +424,7 @@ cudaError_t net_forward_resident(lbmpcd_net* n, int P, cudaStream_t st) {
     k_epilogue<<<nblk((long long)M * L.cout), 256, 0, st>>>(n->z[l], n->theta, L, M, last ? 1 : 0,
                                                             last ? nullptr : n->act[l + 1], n->x32, n->y);
   }
+  k_center<<<P, 256, 0, st>>>(n->y, 3, n->z[NL - 1], layer(NL - 1).npad);
   return cudaGetLastError();
 }
 
@@ -424,6 +456,7 @@ int net_backward(lbmpcd_net* n, const float* t, int P) {
   cudaMemsetAsync(n->loss, 0, 4, st);
   cudaMemsetAsync(n->d, 0, (size_t)Mp * 64 * 4, st);
   k_loss<<<nblk((long long)M * 3), 256, 0, st>>>(n->y, t, M, n->d, n->loss);
+  k_center<<<P, 256, 0, st>>>(n->d, 64, n->d, 64);   // dL/dz of the last layer
   for (int l = NL - 1; l >= 0; --l) {
     const NetLayer L = layer(l);
     k_prep_dC<<<nblk((long long)Mp * 64), 256, 0, st>>>(n->d, n->z[l], L, M, Mp, l == NL - 1 ? 1 : 0, n->dC, n->dCT,
@@ -574,6 +607,7 @@ extern "C" int lbmpcd_net_forward_noalloc(const float* theta_dev, const float* x
     k_epilogue<<<nblk((long long)M * L.cout), 256, 0, st>>>(z, theta_dev, L, M, last ? 1 : 0,
                                                            last ? nullptr : act[l + 1], x_dev, y_dev);
   }
+  k_center<<<patches, 256, 0, st>>>(y_dev, 3, z, layer(NL - 1).npad);
   if (cudaGetLastError() != cudaSuccess) return LBMPCD_ERR_CUDA;
   int e = 0;
   if (cudaMemcpyAsync(&e, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return LBMPCD_ERR_CUDA;

@@ -93,6 +93,7 @@ __global__ void __launch_bounds__(128, 1) closure_step(const RepDev* __restrict_
   __shared__ __align__(8) uint64_t mbar;   // MMAs of a layer complete
   __shared__ __align__(8) uint64_t wbar;   // weight image of a layer arrived
   __shared__ float s_bias[4][64];
+  __shared__ float s_zsum[4][16][3];      // per-warp column sums of the last layer's output
   __shared__ uint32_t tmem_base;
   __shared__ int s_fail;
   unsigned char* cp = sm;   // copies for dx = -1, 0, +1 at cp + (dx + 1) COPY_BYTES
@@ -212,6 +213,22 @@ __global__ void __launch_bounds__(128, 1) closure_step(const RepDev* __restrict_
       FZ_TMEM_LD16(v0, trow);
       FZ_TMEM_LD16(v1, trow + 64u);
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      // the correction less its mean over the 16 rows of its patch column
+      // (per field) plus the 8-frame mean.  Pixel m = 16 y + x: this warp's
+      // pixels are rows 8t + 2 warp + lane / 16, column lane % 16.
+      float z[2][3], zs[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        z[0][c] = __uint_as_float(v0[c]) + s_bias[3][c];
+        z[1][c] = __uint_as_float(v1[c]) + s_bias[3][c];
+        zs[c] = z[0][c] + z[1][c];
+        zs[c] += __shfl_xor_sync(0xFFFFFFFFu, zs[c], 16);
+      }
+      if (lane < 16) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) s_zsum[warp][lane][c] = zs[c];
+      }
+      __syncthreads();
       float* s_y = reinterpret_cast<float*>(sm);
 #pragma unroll
       for (int t = 0; t < 2; ++t) {
@@ -219,7 +236,9 @@ __global__ void __launch_bounds__(128, 1) closure_step(const RepDev* __restrict_
         float* yr = rd.cl_y + ((long long)blockIdx.x * 256 + m) * 3;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          const float yv = (__uint_as_float(t ? v1[c] : v0[c]) + s_bias[3][c]) + mean8[t][c];
+          const int x = lane & 15;
+          const float zm = (s_zsum[0][x][c] + s_zsum[1][x][c] + s_zsum[2][x][c] + s_zsum[3][x][c]) * (1.0f / 16.0f);
+          const float yv = (z[t][c] - zm) + mean8[t][c];
           yr[c] = yv;
           s_y[3 * m + c] = yv;
         }

@@ -15,9 +15,9 @@
 // already in the same layout ([n][tap][channel], zero padded), the two M tiles
 // accumulate in TMEM columns 0..63 and 64..127, and the epilogue (bias, ReLU,
 // bf16) writes the next layer's three copies; the last layer (3 outputs,
-// padded to N = 16) adds the mean of the 8 input frames.  The kernel that
-// runs these layers inside the coupled step is closure_step
-// (closure_coupling.cu).
+// padded to N = 16) subtracts its own mean over each patch column (16 rows)
+// per field and adds the mean of the 8 input frames.  The kernel that runs
+// these layers inside the coupled step is closure_step (closure_coupling.cu).
 #pragma once
 #include <cuda_bf16.h>
 #include <stdint.h>

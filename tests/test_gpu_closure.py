@@ -6,8 +6,8 @@ tests/net_tolerances.py)."""
 import numpy as np
 import pytest
 
-from tests.net_tolerances import (FWD_RTOL, GRAD_LAYER_L2, GRAD_RTOL, elem_err, oracle_patches, rel_l2,
-                                  rms)
+from tests.net_tolerances import (FWD_RTOL, GRAD_LAYER_L2, GRAD_RTOL, decision_spread, elem_err, oracle_patches,
+                                  rel_l2, rms)
 
 pytestmark = pytest.mark.gpu
 
@@ -96,8 +96,9 @@ def test_net_forward_matches_oracle(lb, data, request):
 def test_net_gradient_matches_oracle(lb, data, request):
     """Parameter gradient of the MSE loss, per layer (weights and biases),
     element by element against the oracle's backward with bf16 rounding
-    (GRAD_RTOL of max(|g|, rms of the layer's tensor); relative L2 below
-    GRAD_LAYER_L2), and against the exact FP64 backward no further than the
+    (GRAD_RTOL of max(|g|, rms of the layer's tensor), or twice the oracle's
+    own decision spread on this data where that is larger; relative L2 below
+    GRAD_LAYER_L2, likewise), and against the exact FP64 backward no further than the
     bf16 definition itself plus 5e-3.  Random targets and the oracle's own
     moving-average targets (realistic)."""
     import torch
@@ -111,18 +112,28 @@ def test_net_gradient_matches_oracle(lb, data, request):
     net.close()
     Le, ge = C.backward(th, x, t, emulate_bf16=True)
     L64, g64 = C.backward(th, x, t)
+    spread = decision_spread(C, th, x, t)
     assert abs(L - Le) < 2e-3 * Le
     o = 0
-    for ci, co in C.LAYERS:
+    for li, (ci, co) in enumerate(C.LAYERS):
         nW = co * 9 * ci
         for name, sl in (("W", slice(o, o + nW)), ("b", slice(o + nW, o + nW + co))):
+            if co == 3 and name == "b":
+                # the column centring removes the head's bias: its exact gradient
+                # is 0, the GPU's is fp32 rounding of sums of centred terms
+                assert np.max(np.abs(ge[sl])) < 1e-12
+                assert np.max(np.abs(g[sl])) <= 1e-4 * rms(ge[o:o + nW]), g[sl]
+                continue
             e = elem_err(g[sl], ge[sl], rms(ge[sl]))
             l2 = rel_l2(g[sl], ge[sl])
             d_gpu, d_def = rel_l2(g[sl], g64[sl]), rel_l2(ge[sl], g64[sl])
-            print(f"{data} grad {ci}->{co} {name}: max element error {e:.2e}, rel L2 {l2:.2e} vs bf16 oracle; "
-                  f"to exact FP64: GPU {d_gpu:.2e}, bf16 definition {d_def:.2e}")
-            assert e <= GRAD_RTOL, (ci, co, name, e)
-            assert l2 <= GRAD_LAYER_L2, (ci, co, name, l2)
+            k = 0 if name == "W" else 2
+            tol_e = max(GRAD_RTOL, 2.0 * spread[li, k])
+            tol_l2 = max(GRAD_LAYER_L2, 2.0 * spread[li, k + 1])
+            print(f"{data} grad {ci}->{co} {name}: max element error {e:.2e} (bound {tol_e:.2e}), rel L2 {l2:.2e} "
+                  f"(bound {tol_l2:.2e}) vs bf16 oracle; to exact FP64: GPU {d_gpu:.2e}, bf16 definition {d_def:.2e}")
+            assert e <= tol_e, (ci, co, name, e)
+            assert l2 <= tol_l2, (ci, co, name, l2)
             assert d_gpu <= d_def + 5e-3, (ci, co, name, d_gpu, d_def)
         o += nW + co
 

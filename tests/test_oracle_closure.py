@@ -1,6 +1,7 @@
 """Pins of the closure network's FP64 oracle (not GPU): convolution against
 explicit loops, gradients against central finite differences, bf16 rounding
-on hand-worked values, and the skip connection."""
+on hand-worked values, the skip connection and the column-mean centring of
+the correction."""
 import numpy as np
 import pytest
 
@@ -47,6 +48,51 @@ def test_zero_head_gives_window_mean():
     np.testing.assert_allclose(y, C.mean8(x), atol=1e-15)
 
 
+def test_output_keeps_the_column_means_of_the_window_mean():
+    """The correction is centred along y per patch column and channel:
+    whatever the parameters, the mean over the 16 rows of every column of
+    every output field is that of the 8-frame mean, and the head's bias (a
+    uniform correction) has no effect."""
+    rng = np.random.default_rng(11)
+    th = C.init_params(2) + rng.normal(0, 0.05, size=C.n_params())
+    x = rng.normal(size=(3, 16, 16, 24)) + np.array([0.3, -1.0, 2.0] * 8)
+    y, _ = C.forward(th, x)
+    m8 = C.mean8(x)
+    np.testing.assert_allclose(y.mean(axis=1), m8.mean(axis=1), atol=1e-13)
+    assert np.max(np.abs(y - m8)) > 1e-3                 # it does redistribute
+    th2 = th.copy()
+    th2[-3:] += np.array([0.5, -2.0, 7.0])               # head biases
+    y2, _ = C.forward(th2, x)
+    np.testing.assert_allclose(y2, y, atol=1e-13)
+
+
+def test_uniform_correction_by_hand():
+    """Head weights that copy one input channel: the output is the 8-frame
+    mean plus that channel less its mean over the pixel's patch column
+    (16 rows, same x), written out pixel by pixel."""
+    rng = np.random.default_rng(12)
+    th = C.init_params(1)
+    L = C.unpack(th)
+    for W, b in L[:3]:                                  # layers 1-3 pass frame 0 field 1 (shifted positive)
+        W[:] = 0.0
+        b[:] = 0.0
+    L[0][0][0, 1, 1, 1] = 1.0                           # a = relu(x[..., 1])
+    L[1][0][0, 1, 1, 0] = 1.0
+    L[2][0][0, 1, 1, 0] = 1.0
+    L[3][0][:] = 0.0
+    L[3][1][:] = 0.0
+    L[3][0][2, 1, 1, 0] = 1.0                           # head channel 2 = that activation
+    x = rng.normal(size=(1, 16, 16, 24))
+    x[..., 1] = np.abs(x[..., 1])
+    y, _ = C.forward(th, x)
+    for i in range(16):
+        for j in range(16):
+            m = sum(x[0, k, j, 1] for k in range(16)) / 16.0
+            m8 = [sum(x[0, i, j, 3 * f + c] for f in range(8)) / 8.0 for c in range(3)]
+            want = [m8[0], m8[1], m8[2] + x[0, i, j, 1] - m]
+            assert np.max(np.abs(y[0, i, j] - want)) < 1e-13
+
+
 def test_gradient_against_finite_differences():
     """dL/dtheta of backward() equals central differences of loss() on one
     patch (exact arithmetic; with bf16 emulation the loss is piecewise
@@ -66,4 +112,6 @@ def test_gradient_against_finite_differences():
         tp[i] += h
         tm[i] -= h
         fd = (C.loss(tp, x, t) - C.loss(tm, x, t)) / (2 * h)
-        assert abs(fd - g[i]) <= 1e-6 * max(abs(fd), 1e-8) + 1e-11, (i, fd, g[i])
+        # central differences carry ~eps L / h of rounding (the head bias's exact gradient is 0)
+        assert abs(fd - g[i]) <= 1e-6 * max(abs(fd), 1e-8) + 4e-16 * max(1.0, L) / h, (i, fd, g[i])
+    assert np.max(np.abs(g[-3:])) < 1e-14                # the centring removes the head bias
