@@ -495,19 +495,19 @@ def run_ensemble(args):
     print(json.dumps(out), flush=True)
 
 
-def _ensemble_profile_error(lb, CT, cfg, mode, theta, replicas, burn, steps, every):
+def _ensemble_running_means(lb, CT, cfg, mode, theta, replicas, burn, steps, every, seed0=0):
     """Running means over time and `replicas` channels (distinct seeds, one
     handle) of (a) the velocity imposed on the two inner-buffer columns (the
     MPCD -> LB feedback, from the populations there) and (b) the x-averaged
-    LB velocity profile, against the steady Poiseuille profile: relative L2
-    errors after each sample, samples `every` steps apart from `burn` steps
-    on."""
+    LB velocity profile, after each sample; samples `every` steps apart from
+    `burn` steps on.  Returns numpy arrays [samples][ny - 2][2] and
+    [samples][ny - 2]."""
     import numpy as np
     import torch
     name, fb, window, K = mode
     p0, (x0, x1) = cfg["params"], cfg["region"]
     nx, ny = p0["nx"], p0["ny"]
-    ps = [dict(p0, feedback=fb, window=window, seed=p0["seed"] + 7919 * r) for r in range(replicas)]
+    ps = [dict(p0, feedback=fb, window=window, seed=p0["seed"] + seed0 + 7919 * r) for r in range(replicas)]
     sim = lb.Lbmpcd(ps)
     for r in range(replicas):
         sim.set_region(r, x0, x1)
@@ -515,17 +515,16 @@ def _ensemble_profile_error(lb, CT, cfg, mode, theta, replicas, burn, steps, eve
     if fb == 2:
         sim.set_closure(theta, interval=K)
     sim.step(burn)
-    yc = np.arange(1, ny - 1) + 0.5
-    u_ref = torch.tensor(CT.poiseuille(yc, ny, p0["tau"], p0["force"][0]), device="cuda")
     cols = [x0 + 1, x1 - 2]                      # inner-buffer columns (coupling width 2)
     cxs = torch.tensor([0, 1, 0, -1, 0, 1, -1, -1, 1], dtype=torch.float64, device="cuda")
     uf = torch.empty(3 * ny * nx, dtype=torch.float64, device="cuda")
     pops = torch.empty(9 * ny * nx, dtype=torch.float64, device="cuda")
+    S = steps // every
     acc_lb = torch.zeros(ny - 2, dtype=torch.float64, device="cuda")
     acc_imp = torch.zeros(ny - 2, 2, dtype=torch.float64, device="cuda")
-    e_imp, e_lb = [], []
-    rel = lambda a, b: float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
-    for k in range(steps // every):
+    m_lb = torch.empty(S, ny - 2, dtype=torch.float64, device="cuda")
+    m_imp = torch.empty(S, ny - 2, 2, dtype=torch.float64, device="cuda")
+    for k in range(S):
         sim.step(every)
         for r in range(replicas):
             sim.get("U", r, out=uf)
@@ -533,11 +532,17 @@ def _ensemble_profile_error(lb, CT, cfg, mode, theta, replicas, burn, steps, eve
             sim.get("POPS", r, out=pops)
             f = pops.view(9, ny, nx)[:, 1:ny - 1, cols]
             acc_imp += (cxs[:, None, None] * f).sum(0) / f.sum(0)
-        n = (k + 1) * replicas
-        e_lb.append(rel(acc_lb / n, u_ref))
-        e_imp.append(rel(acc_imp / n, u_ref[:, None].expand(-1, 2)))
+        m_lb[k] = acc_lb / ((k + 1) * replicas)
+        m_imp[k] = acc_imp / ((k + 1) * replicas)
     sim.close()
-    return np.asarray(e_imp), np.asarray(e_lb)
+    return m_imp.cpu().numpy(), m_lb.cpu().numpy()
+
+
+def _rel_err(a, b):
+    """Relative L2 distance per sample: a, b [samples][...]."""
+    import numpy as np
+    ax = tuple(range(1, a.ndim))
+    return np.sqrt(((a - b) ** 2).sum(axis=ax) / (b ** 2).sum(axis=ax))
 
 
 def _time_to(errs, every, tol=0.01):
@@ -561,14 +566,20 @@ def run_closure(args):
     closure (inference every step and every 8 steps).
 
     Speed: steps/s of one channel, CUDA events around `steps` steps.
-    Accuracy and time to solution: 8 replicas (distinct seeds) start from
-    the Poiseuille profile and run 1000 steps; then, every 10 steps for 5000
-    steps, the running mean over time and replicas of the velocity imposed
-    on the inner-buffer columns (the averaged MPCD -> LB feedback) and of the
-    x-averaged LB profile are compared with that profile.  A mode's time to
+    Accuracy and time to solution: every mode runs 8 replicas (distinct
+    seeds) from the Poiseuille profile for 1000 steps; then, every 10 steps
+    for 5000 steps, the running mean over time and replicas of the velocity
+    imposed on the inner-buffer columns (the averaged MPCD -> LB feedback)
+    and of the x-averaged LB profile is taken.  The judge of a mode's error
+    is the plain W = 100 coupling: an independent 16-replica W = 100 run over
+    the same window, whose running means at the same times are the
+    reference (the MPCD mean at the buffer differs from the analytic profile
+    by ~1 % and drifts slowly, the same in every mode).  A mode's time to
     solution is the number of channel-steps (steps x replicas) after which
-    the imposed-profile error stays at or below 1 %, over its measured
-    single-channel step rate (null if it is above 1 % at the end)."""
+    its imposed-profile error against that reference stays at or below 1 %,
+    over its measured single-channel step rate (null if it is above 1 % at
+    the end); the errors against the analytic profile are given beside.
+    """
     import numpy as np
     import torch
     import __graft_entry__
@@ -594,6 +605,9 @@ def run_closure(args):
     modes = [("plain_W100", 1, 100, 0), ("plain_W8", 1, 8, 0), ("closure_K1", 2, 100, 1), ("closure_K8", 2, 100, 8)]
     runs = {}
     peaks = measured_peaks()
+    R, burn, n_acc, every = 8, 1000, 5000, 10
+    ref_imp, ref_lb = _ensemble_running_means(lb, CT, cfg, modes[0], None, 16, burn, n_acc, every, seed0=100_000)
+    u_ref = CT.poiseuille(np.arange(1, ny - 1) + 0.5, ny, p0["tau"], p0["force"][0])
     for name, fb, window, K in modes:
         pm = dict(p0, feedback=fb, window=window)
         sim = lb.Lbmpcd([pm])
@@ -619,12 +633,14 @@ def run_closure(args):
                                    "roofline": {"bound": "tensor", "achieved": flops / t_launch / 1e12, "peak": peak,
                                                 "unit": "TFLOP/s", "frac": flops / t_launch / 1e12 / peak}}
         sim.close()
-        R, burn, n_acc, every = 8, 1000, 5000, 10
-        e_imp, e_lb = _ensemble_profile_error(lb, CT, cfg, (name, fb, window, K), theta, R, burn, n_acc, every)
+        im, ml = _ensemble_running_means(lb, CT, cfg, (name, fb, window, K), theta, R, burn, n_acc, every)
+        e_imp, e_lb = _rel_err(im, ref_imp), _rel_err(ml, ref_lb)
         steps_to = _time_to(e_imp, every)
         pick = lambda e: {str((k + 1) * every): float(e[k]) for k in (0, 9, 49, 99, 249, 499) if k < e.size}
         run["ensemble"] = {"replicas": R, "burn_in": burn, "sample_every": every,
-                           "imposed_err_at_steps": pick(e_imp), "lb_err_at_steps": pick(e_lb),
+                           "imposed_err_vs_W100_ref": pick(e_imp), "lb_err_vs_W100_ref": pick(e_lb),
+                           "imposed_err_vs_poiseuille": pick(_rel_err(im, np.broadcast_to(u_ref[None, :, None], im.shape))),
+                           "lb_err_vs_poiseuille": pick(_rel_err(ml, np.broadcast_to(u_ref[None, :], ml.shape))),
                            "steps_to_1pct_imposed": steps_to, "steps_to_1pct_lb": _time_to(e_lb, every),
                            "seconds_to_1pct": None if steps_to is None else steps_to * R / run["steps_per_s"]}
         runs[name] = run

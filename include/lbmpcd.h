@@ -221,6 +221,24 @@ int lbmpcd_get_fields(lbmpcd* h, int replica, int field, void* dst, size_t bytes
  * INVALID_ARG (field, size, values), STATE (particles before set_region). */
 int lbmpcd_set_state(lbmpcd* h, int replica, int field, const void* src, size_t bytes, int src_on_device);
 
+/* Halo exchange of the x-slab decomposition of one channel over ranks (not
+ * in the paper, which runs one domain; the LB update of Sec. 2.1 is local
+ * to a node and its neighbours, so a channel cut into slabs of whole
+ * columns, each held by one rank with H ghost columns per side, runs H
+ * pull steps exactly between two exchanges of H columns per cut).
+ * Populations of LB columns [x, x + ncols), all q, z and y, of the buffer
+ * the next step reads, in the handle's storage: binary64 f_i; binary32
+ * deviations f_i - w_i; binary16 deviations times 2^14
+ * (lbmpcd_population_bytes gives 8, 4 or 2).  Layout [q][nz][ny][ncols],
+ * ncols values per row.  dst / src are caller-owned, host or device
+ * (flag); the copy is exact (raw storage), between handles of the same
+ * lattice, precision and ny, nz.  Synchronous on the handle's stream.
+ * Errors: INVALID_ARG (NULL handle or buffer, bad replica, columns outside
+ * [0, nx)), CUDA. */
+int lbmpcd_population_bytes(const lbmpcd* h);
+int lbmpcd_get_columns(lbmpcd* h, int replica, int x, int ncols, void* dst, int dst_on_device);
+int lbmpcd_set_columns(lbmpcd* h, int replica, int x, int ncols, const void* src, int src_on_device);
+
 /* Tensor-core GEMM of the learned closure (not a step of the paper's method):
  * C[M][N] = alpha * A[M][K] B[N][K]^T + beta * C, A and B bf16 with K
  * contiguous, C fp32 with row stride N; all device pointers, launched on

@@ -85,6 +85,9 @@ def load_library(path: str = LIB_PATH):
     L.lbmpcd_set_launch_mode.argtypes = [vp, ci, ci, ci]
     L.lbmpcd_set_wait_limit.argtypes = [vp, ctypes.c_uint]
     L.lbmpcd_autotune.argtypes = [vp, ci, ctypes.POINTER(ci)]
+    L.lbmpcd_population_bytes.argtypes = [vp]
+    L.lbmpcd_get_columns.argtypes = [vp, ci, ci, ci, vp, ci]
+    L.lbmpcd_set_columns.argtypes = [vp, ci, ci, ci, vp, ci]
     L.lbmpcd_net_destroy.restype = None
     L.lbmpcd_destroy.argtypes = [vp]
     L.lbmpcd_destroy.restype = None
@@ -99,7 +102,8 @@ EXPORTED = ["lbmpcd_create", "lbmpcd_set_region", "lbmpcd_step", "lbmpcd_step_pr
             "lbmpcd_last_error", "lbmpcd_tc_gemm_bf16", "lbmpcd_net_num_params", "lbmpcd_net_create",
             "lbmpcd_net_get_params", "lbmpcd_net_set_params", "lbmpcd_net_forward", "lbmpcd_net_backward",
             "lbmpcd_net_train_step", "lbmpcd_net_destroy", "lbmpcd_net_forward_noalloc",
-            "lbmpcd_set_closure", "lbmpcd_set_launch_mode", "lbmpcd_set_wait_limit", "lbmpcd_autotune"]
+            "lbmpcd_set_closure", "lbmpcd_set_launch_mode", "lbmpcd_set_wait_limit", "lbmpcd_autotune",
+            "lbmpcd_population_bytes", "lbmpcd_get_columns", "lbmpcd_set_columns"]
 
 
 def make_params(d: dict) -> lbmpcd_params:
@@ -214,6 +218,17 @@ def lbmpcd_set_state(h, replica: int, field: str, value):
         ptr, nbytes, on_dev = arr.data_ptr(), arr.numel() * arr.element_size(), int(arr.is_cuda)
     _check(h, load_library().lbmpcd_set_state(h, int(replica), FIELDS[field], ctypes.c_void_p(ptr),
                                               nbytes, on_dev))
+
+
+def _raw_buffer(buf):
+    """(address, bytes, on_device) of a contiguous numpy array or torch tensor."""
+    if isinstance(buf, np.ndarray):
+        if not buf.flags.c_contiguous:
+            raise ValueError("buffer must be contiguous")
+        return buf.ctypes.data, buf.nbytes, 0
+    if not buf.is_contiguous():
+        raise ValueError("buffer must be contiguous")
+    return buf.data_ptr(), buf.numel() * buf.element_size(), int(buf.is_cuda)
 
 
 def lbmpcd_tc_gemm_bf16(A, B, C, alpha=1.0, beta=0.0, err=None, stream=None):
@@ -378,6 +393,34 @@ class Lbmpcd:
 
     def get(self, field: str, replica: int = 0, out=None):
         return lbmpcd_get_fields(self._h, replica, field, out)
+
+    def population_bytes(self) -> int:
+        return int(load_library().lbmpcd_population_bytes(self._h))
+
+    def column_bytes(self, ncols: int, replica: int = 0) -> int:
+        p = self.params[replica]
+        q = int(p.get("lattice", 9))
+        return q * int(p.get("nz", 1)) * int(p["ny"]) * int(ncols) * self.population_bytes()
+
+    def get_columns(self, x: int, ncols: int, out, replica: int = 0):
+        """Raw populations of LB columns [x, x + ncols) into ``out`` (a
+        contiguous numpy array or torch tensor of column_bytes(ncols) bytes,
+        any dtype); returns out."""
+        ptr, nbytes, on_dev = _raw_buffer(out)
+        if nbytes != self.column_bytes(ncols, replica):
+            raise ValueError("column buffer has the wrong size")
+        _check(self._h, load_library().lbmpcd_get_columns(self._h, int(replica), int(x), int(ncols),
+                                                          ctypes.c_void_p(ptr), on_dev))
+        return out
+
+    def set_columns(self, x: int, ncols: int, src, replica: int = 0):
+        """Load raw populations of LB columns [x, x + ncols) from ``src``
+        (layout and size of get_columns)."""
+        ptr, nbytes, on_dev = _raw_buffer(src)
+        if nbytes != self.column_bytes(ncols, replica):
+            raise ValueError("column buffer has the wrong size")
+        _check(self._h, load_library().lbmpcd_set_columns(self._h, int(replica), int(x), int(ncols),
+                                                          ctypes.c_void_p(ptr), on_dev))
 
     def set(self, field: str, value, replica: int = 0):
         lbmpcd_set_state(self._h, replica, field, value)

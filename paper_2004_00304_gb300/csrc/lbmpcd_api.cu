@@ -788,6 +788,39 @@ static bool int_field(int f) {
          f == LBMPCD_CELL_LIST;
 }
 
+extern "C" int lbmpcd_population_bytes(const lbmpcd* h) {
+  if (!h) return LBMPCD_ERR_INVALID_ARG;
+  return h->prec == P_FP64 ? 8 : (h->prec == P_FP32 ? 4 : 2);
+}
+
+namespace {
+// Raw population columns [x, x + ncols) of the buffer the next step reads:
+// rows (i, z, y) of ncols storage values, nx apart in the lattice.
+int copy_columns(lbmpcd* h, int replica, int x, int ncols, void* host_or_dev, int on_device, bool to_lattice) {
+  if (!h) return LBMPCD_ERR_INVALID_ARG;
+  if (replica < 0 || replica >= h->nrep || !host_or_dev) return fail(h, LBMPCD_ERR_INVALID_ARG, "bad replica or null buffer");
+  const RepDev& d = h->rd[replica];
+  if (ncols < 1 || x < 0 || x + ncols > d.nx) return fail(h, LBMPCD_ERR_INVALID_ARG, "column range outside the lattice");
+  const size_t esz = (size_t)lbmpcd_population_bytes(h);
+  char* lat = (char*)d.f[h->nstep & 1] + (size_t)x * esz;
+  const size_t pitch = (size_t)d.nx * esz, width = (size_t)ncols * esz, rows = (size_t)d.q * d.nz * d.ny;
+  const cudaMemcpyKind k = to_lattice ? (on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice)
+                                      : (on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost);
+  cudaError_t e = to_lattice ? cudaMemcpy2DAsync(lat, pitch, host_or_dev, width, width, rows, k, h->stream)
+                             : cudaMemcpy2DAsync(host_or_dev, width, lat, pitch, width, rows, k, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  return e == cudaSuccess ? LBMPCD_OK : cuda_fail(h, e, to_lattice ? "set_columns" : "get_columns");
+}
+}  // namespace
+
+extern "C" int lbmpcd_get_columns(lbmpcd* h, int replica, int x, int ncols, void* dst, int dst_on_device) {
+  return copy_columns(h, replica, x, ncols, dst, dst_on_device, false);
+}
+
+extern "C" int lbmpcd_set_columns(lbmpcd* h, int replica, int x, int ncols, const void* src, int src_on_device) {
+  return copy_columns(h, replica, x, ncols, const_cast<void*>(src), src_on_device, true);
+}
+
 extern "C" long long lbmpcd_field_size(const lbmpcd* h, int replica, int field) {
   if (!h || replica < 0 || replica >= h->nrep) return LBMPCD_ERR_INVALID_ARG;
   long long n = field_elems(h, replica, field);
