@@ -545,6 +545,60 @@ def _rel_err(a, b):
     return np.sqrt(((a - b) ** 2).sum(axis=ax) / (b ** 2).sum(axis=ax))
 
 
+def _startup_profile(yw, t, H, g, nu, terms=200):
+    """Plane Poiseuille flow started from rest under a constant force g: the
+    steady parabola minus its decaying odd sine modes (yw from the wall,
+    channel height H, kinematic viscosity nu)."""
+    import numpy as np
+    u = g * yw * (H - yw) / (2 * nu)
+    for n in range(1, 2 * terms, 2):
+        u = u - 4 * g * H * H / (nu * np.pi ** 3 * n ** 3) * np.sin(n * np.pi * yw / H) * \
+            np.exp(-(n * np.pi / H) ** 2 * nu * t)
+    return u
+
+
+def _transient_imposed_error(lb, CT, cfg, mode, theta, replicas, steps, every):
+    """`replicas` channels (distinct seeds, one handle) start from rest under
+    the force; every `every` steps the velocity imposed on the two
+    inner-buffer columns, averaged over the replicas (no time average: the
+    flow is changing), is compared with the start-up solution at that time.
+    Returns (relative L2 errors per sample, device seconds of the steps)."""
+    import numpy as np
+    import torch
+    name, fb, window, K = mode
+    p0, (x0, x1) = cfg["params"], cfg["region"]
+    nx, ny = p0["nx"], p0["ny"]
+    ps = [dict(p0, feedback=fb, window=window, seed=p0["seed"] + 7919 * r) for r in range(replicas)]
+    sim = lb.Lbmpcd(ps)
+    for r in range(replicas):
+        sim.set_region(r, x0, x1)
+    if fb == 2:
+        sim.set_closure(theta, interval=K)
+    nu = (p0["tau"] - 0.5) / 3.0
+    yw = np.arange(1, ny - 1) + 0.5 - 1.0
+    cols = [x0 + 1, x1 - 2]
+    cxs = torch.tensor([0, 1, 0, -1, 0, 1, -1, -1, 1], dtype=torch.float64, device="cuda")
+    pops = torch.empty(9 * ny * nx, dtype=torch.float64, device="cuda")
+    errs, t_dev = [], 0.0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for k in range(steps // every):
+        e0.record()
+        sim.step(every)
+        e1.record()
+        torch.cuda.synchronize()
+        t_dev += e0.elapsed_time(e1) * 1e-3
+        acc = torch.zeros(ny - 2, 2, dtype=torch.float64, device="cuda")
+        for r in range(replicas):
+            sim.get("POPS", r, out=pops)
+            f = pops.view(9, ny, nx)[:, 1:ny - 1, cols]
+            acc += (cxs[:, None, None] * f).sum(0) / f.sum(0)
+        u = (acc / replicas).cpu().numpy()
+        ua = _startup_profile(yw, (k + 1) * every, ny - 2, p0["force"][0], nu)
+        errs.append(float(np.linalg.norm(u - ua[:, None]) / np.linalg.norm(np.repeat(ua[:, None], 2, 1))))
+    sim.close()
+    return np.asarray(errs), t_dev
+
+
 def _time_to(errs, every, tol=0.01):
     """Steps after which the running-mean error stays at or below tol (None if
     it is above tol at the last sample)."""
@@ -579,6 +633,16 @@ def run_closure(args):
     its imposed-profile error against that reference stays at or below 1 %,
     over its measured single-channel step rate (null if it is above 1 % at
     the end); the errors against the analytic profile are given beside.
+
+    Transient (surrogate_speedup_to_1pct): 64 replicas of a 256 x 64 channel
+    start from rest under g = 3.2e-6; every 50 steps the replica-mean
+    velocity imposed on the inner-buffer columns is compared with the
+    start-up solution of plane Poiseuille flow at that time (the viscosities
+    matched, the coupled channel is one fluid).  A window of W steps lags the
+    accelerating flow by ~W/2 steps; the closure's 8 frames by ~4.  Time to
+    solution = steps until the error stays at or below 1 %, times the
+    handle's measured step time; the speedup is W = 100's over the
+    closure's at K = 8.
     """
     import numpy as np
     import torch
@@ -644,6 +708,21 @@ def run_closure(args):
                            "steps_to_1pct_imposed": steps_to, "steps_to_1pct_lb": _time_to(e_lb, every),
                            "seconds_to_1pct": None if steps_to is None else steps_to * R / run["steps_per_s"]}
         runs[name] = run
+    # start-up transient: 64 replicas of a 256 x 64 channel from rest, where a
+    # window's lag (W / 2 steps) costs accuracy while the flow accelerates
+    tcfg = CT.channel(64, 3.2e-6, seed=9, nx=256, region_cols=32, tau=tau)
+    transient = {"workload": "64 replicas, 256x64 D2Q9, MPCD central 32 columns at r = 2, g = 3.2e-6, from rest",
+                 "replicas": 64, "steps": 6000, "sample_every": 50}
+    tmodes = [("plain_W8", 1, 8, 0), ("plain_W25", 1, 25, 0), ("plain_W100", 1, 100, 0),
+              ("closure_K1", 2, 100, 1), ("closure_K8", 2, 100, 8)]
+    for name, fb, window, K in tmodes:
+        errs, t_dev = _transient_imposed_error(lb, CT, tcfg, (name, fb, window, K), theta, 64, 6000, 50)
+        steps_to = _time_to(errs, 50)
+        transient[name] = {"imposed_err_at_steps": {str((k + 1) * 50): float(errs[k]) for k in (1, 9, 19, 39, 59, 79, 99, 119)},
+                           "mean_err_last_half": float(errs[errs.size // 2:].mean()),
+                           "steps_to_1pct": steps_to, "step_s": t_dev / 6000,
+                           "seconds_to_1pct": None if steps_to is None else steps_to * t_dev / 6000}
+    tw, tc = transient["plain_W100"]["seconds_to_1pct"], transient["closure_K8"]["seconds_to_1pct"]
     t_w, t_c = runs["plain_W100"]["ensemble"]["seconds_to_1pct"], runs["closure_K8"]["ensemble"]["seconds_to_1pct"]
     out = {"metric": METRIC, "value": runs["closure_K8"]["steps_per_s"], "unit": UNIT, "n_gpus": 1,
            "steps": args.steps, "warmup": max(args.warmup, 1000),
@@ -659,7 +738,11 @@ def run_closure(args):
                        "heldout": {k: [float(v) for v in ev[k]] for k in ("rmse_net", "rmse_mean8", "gain")},
                        "in_loop": runs,
                        "step_time_over_plain_W100": runs["plain_W100"]["steps_per_s"] / runs["closure_K8"]["steps_per_s"],
-                       "surrogate_speedup_to_1pct": (t_w / t_c) if (t_w and t_c) else None}}
+                       "transient": transient,
+                       "transient_err_W100_over_K8": transient["plain_W100"]["mean_err_last_half"] /
+                                                     transient["closure_K8"]["mean_err_last_half"],
+                       "surrogate_speedup_to_1pct": (tw / tc) if (tw and tc) else None,
+                       "surrogate_speedup_to_1pct_steady": (t_w / t_c) if (t_w and t_c) else None}}
     print(json.dumps(out), flush=True)
 
 
