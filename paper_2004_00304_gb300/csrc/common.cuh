@@ -324,17 +324,26 @@ LBM_HD uint32_t mix32(uint32_t x) {
   return x;
 }
 
-// binary32 -> binary16 with stochastic rounding: round up with probability
-// (y - down) / (up - down), so that the stored value is unbiased and updates
-// far below one binary16 ulp (the per-step body-force increments) still
-// accumulate.  h = 0 selects round-to-nearest (used when loading a state).
+// binary32 -> binary16 with stochastic rounding: round up (in magnitude)
+// with probability (|y| - down) / (up - down), so that the stored value is
+// unbiased and updates far below one binary16 ulp (the per-step body-force
+// increments) still accumulate.  For y in binary16's normal range the 13
+// low mantissa bits that binary16 drops are exactly that fraction; adding 13
+// uniform random bits to them and truncating toward zero rounds up with
+// exactly that probability (the carry moves into the kept bits, or the
+// exponent).  Below 2^-14 (binary16 subnormals: deviations under 2^-28 at the
+// 2^14 scale) more bits are dropped and the rounding leans toward zero.
+// h = 0 selects round-to-nearest (used when loading a state); h's top 13
+// bits are the random bits.
 __device__ __forceinline__ __half sr_half(float y, uint32_t h) {
   if (h == 0u) return __float2half_rn(y);
-  const __half lo = __float2half_rd(y), hi = __float2half_ru(y);
-  const float flo = __half2float(lo), gap = __half2float(hi) - flo;
-  const float u = (float)(h >> 8) * (1.0f / 16777216.0f);
-  return (gap > 0.0f && u * gap < y - flo) ? hi : lo;
+  return __float2half_rz(__uint_as_float(__float_as_uint(y) + (h >> 19)));
 }
+
+// next word of the stochastic-rounding stream of one thread (a 32-bit linear
+// congruential step, Numerical Recipes' constants; its top bits are the ones
+// sr_half uses); never 0, which would select round-to-nearest
+__device__ __forceinline__ uint32_t sr_next(uint32_t h) { return (h * 1664525u + 1013904223u) | 1u; }
 
 template <> struct Store<double> {
   using R = double;
@@ -367,16 +376,26 @@ __device__ __forceinline__ void load_block_records(RepDev& srd, StepInfo& sst, c
   __syncthreads();
 }
 
-// Grid-stride walk over a block map: a block processes work items blockIdx.x,
-// blockIdx.x + gridDim.x, ...; the replica's records are reloaded into shared
-// memory only when the replica changes (the map lists each replica's items
-// contiguously).  The body runs with the records of its item's replica.
-template <typename Item, typename Body>
+// Walk over a block map.  Grid-stride (CONTIG = false): block b processes
+// items b, b + gridDim.x, ...; contiguous (CONTIG = true): the items
+// [b per, (b + 1) per), per = ceil(nwork / gridDim.x).  The map lists each
+// replica's items contiguously and a block reloads the replica's records into
+// shared memory only when the replica changes: with the contiguous split a
+// block of the particle pass meets one replica or a few, where the
+// grid-stride walk changed replica on almost every item of an ensemble of
+// small replicas (a barrier and a dependent load each).  The LB launch keeps
+// the grid-stride walk, so that its cell-table items, listed first, run first
+// on every SM.  The body runs with the records of its item's replica.
+template <bool CONTIG = false, typename Item, typename Body>
 __device__ __forceinline__ void for_each_item(const Item* __restrict__ bmap, int nwork, const RepDev* reps,
                                               const StepInfo* si, int k, int nrep, RepDev& rd, StepInfo& st,
                                               Body&& body) {
   int cur = -1;
-  for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
+  const int per = CONTIG ? (nwork + (int)gridDim.x - 1) / (int)gridDim.x : 1;
+  const int w0 = CONTIG ? (int)blockIdx.x * per : (int)blockIdx.x;
+  const int w1 = CONTIG ? min(nwork, w0 + per) : nwork;
+  const int dw = CONTIG ? 1 : (int)gridDim.x;
+  for (int wi = w0; wi < w1; wi += dw) {
     const Item bm = bmap[wi];
     if (bm.x != cur) {
       __syncthreads();
@@ -384,6 +403,24 @@ __device__ __forceinline__ void for_each_item(const Item* __restrict__ bmap, int
       cur = bm.x;
     }
     body(bm);
+  }
+}
+
+// The same walks with the records read in place from global memory (through
+// the read-only path; they do not change during a launch) instead of staged
+// in shared memory: no barrier when the replica changes.  The body receives
+// the item's records.
+template <bool CONTIG = false, typename Item, typename Body>
+__device__ __forceinline__ void for_each_item_direct(const Item* __restrict__ bmap, int nwork,
+                                                     const RepDev* __restrict__ reps,
+                                                     const StepInfo* __restrict__ si, int k, int nrep, Body&& body) {
+  const int per = CONTIG ? (nwork + (int)gridDim.x - 1) / (int)gridDim.x : 1;
+  const int w0 = CONTIG ? (int)blockIdx.x * per : (int)blockIdx.x;
+  const int w1 = CONTIG ? min(nwork, w0 + per) : nwork;
+  const int dw = CONTIG ? 1 : (int)gridDim.x;
+  for (int wi = w0; wi < w1; wi += dw) {
+    const Item bm = bmap[wi];
+    body(reps[bm.x], si[(long long)k * nrep + bm.x], bm);
   }
 }
 

@@ -17,11 +17,10 @@
 namespace lbm {
 
 template <int Q, typename S, int V>
-__global__ void __launch_bounds__(128, 5) lb_pull(const RepDev* __restrict__ reps, const int4* __restrict__ bmap,
+__global__ void __launch_bounds__(128, Q == 9 ? 7 : 5) lb_pull(const RepDev* __restrict__ reps, const int4* __restrict__ bmap,
                                                int nwork, const StepInfo* __restrict__ si, int k, int nrep) {
-  __shared__ RepDev rd;
-  __shared__ StepInfo st;
-  for_each_item(bmap, nwork, reps, si, k, nrep, rd, st, [&](const int4 bm) { lb_row<Q, S, V>(rd, st, bm); });
+  for_each_item_direct(bmap, nwork, reps, si, k, nrep,
+                       [&](const RepDev& rd, const StepInfo& st, const int4 bm) { lb_row<Q, S, V>(rd, st, bm); });
 }
 
 // single-replica form (see for_each_item_one)

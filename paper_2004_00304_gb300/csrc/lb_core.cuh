@@ -42,7 +42,7 @@ template <> struct Row<__half, 2> {
   __device__ static void st(__half* p, const float* v, float sc, uint32_t h) {
     __half2 t;
     t.x = sr_half(v[0] * sc, h);
-    t.y = sr_half(v[1] * sc, h ? mix32(h + 1u) : 0u);
+    t.y = sr_half(v[1] * sc, h ? sr_next(h) : 0u);
     *reinterpret_cast<__half2*>(p) = t;
   }
 };
@@ -55,10 +55,11 @@ template <> struct Row<__half, 4> {
   }
   __device__ static void st(__half* p, const float* v, float sc, uint32_t h) {
     __half2 a, b;
+    const uint32_t h1 = h ? sr_next(h) : 0u, h2 = h ? sr_next(h1) : 0u, h3 = h ? sr_next(h2) : 0u;
     a.x = sr_half(v[0] * sc, h);
-    a.y = sr_half(v[1] * sc, h ? mix32(h + 1u) : 0u);
-    b.x = sr_half(v[2] * sc, h ? mix32(h + 2u) : 0u);
-    b.y = sr_half(v[3] * sc, h ? mix32(h + 3u) : 0u);
+    a.y = sr_half(v[1] * sc, h1);
+    b.x = sr_half(v[2] * sc, h2);
+    b.y = sr_half(v[3] * sc, h3);
     uint2 t;
     t.x = *reinterpret_cast<const uint32_t*>(&a);
     t.y = *reinterpret_cast<const uint32_t*>(&b);
@@ -160,9 +161,14 @@ __device__ __forceinline__ void lb_finish(const RepDev& rd, const StepInfo& st, 
   }
   // random bits of the binary16 stochastic rounding: per node, population, step
   const uint32_t hb = sizeof(S) == 2 ? mix32((uint32_t)(row + x0) * 0x9E3779B1u ^ (st.n * 0x632BE5ABu + rd.rep)) : 0u;
+  // one stream of rounding words per thread, V words per population (the
+  // first from the node's hash, the rest from sr_next)
+  uint32_t hs = hb;
 #pragma unroll
-  for (int i = 0; i < Q; ++i)
-    Row<S, V>::st(dst + i * N + row + x0, d[i], scale, hb ? (mix32(hb + 0x27D4EB2Fu * (uint32_t)i) | 1u) : 0u);
+  for (int i = 0; i < Q; ++i) {
+    if (sizeof(S) == 2) hs = sr_next(hs + (uint32_t)V * 0x9E3779B9u);
+    Row<S, V>::st(dst + i * N + row + x0, d[i], scale, sizeof(S) == 2 ? hs : 0u);
+  }
 
   // rho, u: every node on request; otherwise the columns the coupling reads
   // (x0-1 .. x0+cw and x1-cw-1 .. x1, periodic in x), or for a near-wall strip
@@ -198,8 +204,12 @@ __device__ __forceinline__ void lb_finish(const RepDev& rd, const StepInfo& st, 
   }
 }
 
-// One thread owns V consecutive nodes x0 .. x0+V-1 of one row (y, z); a
-// work item (replica, tile, y, z) is one block-wide tile of a row.
+// One thread owns V consecutive nodes x0 .. x0+V-1 of one row (y, z).  A
+// work item (replica, tile, y, z | k << 24) is one block-wide tile of a row
+// (k = 0), or, for rows of tpr = nx / V < blockDim threads (tpr a power of
+// two dividing blockDim), the 2^k = blockDim / tpr rows y, y + 1, ... with
+// tpr threads each, so that narrow replicas do not leave most of a block
+// idle.
 template <int Q, typename S, int V>
 __device__ __forceinline__ void lb_row(const RepDev& rd, const StepInfo& st, const int4 bm) {
   using L = Lattice<Q>;
@@ -216,10 +226,14 @@ __device__ __forceinline__ void lb_row(const RepDev& rd, const StepInfo& st, con
     return;
   }
   const int nx = rd.nx, ny = rd.ny, nz = rd.nz;
-  const int y = bm.z, z = bm.w;
+  const int z = bm.w & 0xFFFFFF, rlog = bm.w >> 24;
   const int tpr = nx / V;
-  const int tx = bm.y * blockDim.x + threadIdx.x;
-  const bool active = tx < tpr;
+  const int lt = rlog ? __ffs(tpr) - 1 : 0;             // tpr = 2^lt when rows share the block
+  const int tx = rlog ? (int)threadIdx.x & (tpr - 1) : bm.y * (int)blockDim.x + (int)threadIdx.x;
+  const int yr = bm.z + (rlog ? (int)threadIdx.x >> lt : 0);
+  const bool row_ok = yr < ny - 1;
+  const int y = row_ok ? yr : ny - 2;                    // rows past the last fluid row load a valid one
+  const bool active = tx < tpr && row_ok;
   const int lane = threadIdx.x & 31;
   const int x0 = tx * V;
   const int par = st.n & 1;
@@ -257,24 +271,32 @@ __device__ __forceinline__ void lb_row(const RepDev& rd, const StepInfo& st, con
     if (V > 1 && L::cx(i) > 0) edge[i] = Store<S>::ld(rp + xprev, inv);
     if (V > 1 && L::cx(i) < 0) edge[i] = Store<S>::ld(rp + xnext, inv);
   }
-  // phase 2: shift the rows with cx != 0 by one node through the neighbour lanes
+  // phase 2: shift the rows with cx != 0 by one node through the neighbour
+  // lanes.  Every lane takes part in every shuffle: the lanes of one warp may
+  // hold different rows (multi-row items), of which some read a bounce-back
+  // row that is not shifted.
   if (V > 1) {
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
+      if (L::cx(i) == 0) continue;
       const int sy = y - L::cy(i);
-      if (L::cx(i) == 0 || sy == 0 || sy == ny - 1) continue;
+      const bool shift = !((sy == 0) | (sy == ny - 1));
       if (L::cx(i) > 0) {                    // source x - 1: previous lane's last node
         R prev = __shfl_up_sync(0xFFFFFFFFu, d[i][V - 1], 1);
-        if (lane == 0) prev = edge[i];
+        if (lane == 0 || tx == 0) prev = edge[i];
+        if (shift) {
 #pragma unroll
-        for (int v = V - 1; v > 0; --v) d[i][v] = d[i][v - 1];
-        d[i][0] = prev;
+          for (int v = V - 1; v > 0; --v) d[i][v] = d[i][v - 1];
+          d[i][0] = prev;
+        }
       } else {                               // source x + 1: next lane's first node
         R next = __shfl_down_sync(0xFFFFFFFFu, d[i][0], 1);
         if (lane == 31 || tx + 1 >= tpr) next = edge[i];
+        if (shift) {
 #pragma unroll
-        for (int v = 0; v < V - 1; ++v) d[i][v] = d[i][v + 1];
-        d[i][V - 1] = next;
+          for (int v = 0; v < V - 1; ++v) d[i][v] = d[i][v + 1];
+          d[i][V - 1] = next;
+        }
       }
     }
   }

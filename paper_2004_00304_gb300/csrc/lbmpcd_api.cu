@@ -322,14 +322,21 @@ static int build_maps(lbmpcd* h) {
       for (long long b = 0; b < (d.ncell + 128 * CPT - 1) / (128 * CPT); ++b) lb.push_back(make_int4(r, (int)(-1 - b), 0, 0));
       for (long long b = 0; b < (d.ncell + 256 * CPT - 1) / (256 * CPT); ++b) lb256.push_back(make_int4(r, (int)(-1 - b), 0, 0));
     }
-    const int ntx = (d.nx / h->lbvec + 127) / 128;
-    for (int z = 0; z < d.nz; ++z)
-      for (int y = 1; y < d.ny - 1; ++y)
-        for (int t = 0; t < ntx; ++t) lb.push_back(make_int4(r, t, y, z));
-    const int ntx256 = (d.nx / h->lbvec + 255) / 256;
-    for (int z = 0; z < d.nz; ++z)
-      for (int y = 1; y < d.ny - 1; ++y)
-        for (int t = 0; t < ntx256; ++t) lb256.push_back(make_int4(r, t, y, z));
+    // row items for blocks of bd threads: tiles of one row, or 2^k whole rows
+    // per item where a row has tpr = nx / vec threads, tpr a power of two
+    // below bd (not for the TMA-staged form, which stages one row per item)
+    auto rows = [&](std::vector<int4>& out, int bd) {
+      const int tpr = d.nx / h->lbvec;
+      int k = 0;
+      if (!h->lb_tma && tpr < bd && (tpr & (tpr - 1)) == 0)
+        while ((tpr << (k + 1)) <= bd) ++k;
+      const int ntx = k ? 1 : (tpr + bd - 1) / bd;
+      for (int z = 0; z < d.nz; ++z)
+        for (int y = 1; y < d.ny - 1; y += 1 << k)
+          for (int t = 0; t < ntx; ++t) out.push_back(make_int4(r, t, y, z | (k << 24)));
+    };
+    rows(lb, 128);
+    rows(lb256, 256);
     if (!d.has_region) continue;
     const long long nslot = d.resample ? (long long)d.cap : d.np;
     const long long npb = (nslot + PP_ITEM - 1) / PP_ITEM;
@@ -1050,7 +1057,9 @@ extern "C" int lbmpcd_set_launch_mode(lbmpcd* h, int mode, int blocks_per_sm, in
                     "nor the Chapman-Enskog redraw");
   h->mode = mode;
   h->pers_bps = blocks_per_sm;
-  h->lb_tma = (flags & LBMPCD_LAUNCH_LB_TMA) && lb_tma_ok(h->q, h->prec, h->lbvec);
+  const bool tma = (flags & LBMPCD_LAUNCH_LB_TMA) && lb_tma_ok(h->q, h->prec, h->lbvec);
+  if (tma != h->lb_tma) h->maps_dirty = true;   // the TMA form takes single-row items
+  h->lb_tma = tma;
   h->pers_graph = true;
   drop_graphs(h);
   return LBMPCD_OK;

@@ -685,8 +685,8 @@ __global__ void __launch_bounds__(256, D == 2 ? 6 : 5) particle_pass(const RepDe
   __shared__ RepDev rd;
   __shared__ StepInfo st;
   __shared__ PassShared<D, R> red;
-  for_each_item(bmap, nwork, reps, si, k, nrep, rd, st,
-                [&](const int2 bm) { particle_item<D, R, RS, AT, CE>(rd, st, (uint32_t)bm.y * PP_ITEM, ~0u, red); });
+  for_each_item<true>(bmap, nwork, reps, si, k, nrep, rd, st,
+                      [&](const int2 bm) { particle_item<D, R, RS, AT, CE>(rd, st, (uint32_t)bm.y * PP_ITEM, ~0u, red); });
 }
 
 // single-replica form (see for_each_item_one)
