@@ -338,22 +338,36 @@ int lbmpcd_net_forward_noalloc(const float* theta_dev, const float* x_dev, int p
 int lbmpcd_set_closure(lbmpcd* h, const float* theta, long long count, int src_on_device, int interval);
 
 /* Launch form of the step (batching of the step launches; not in the paper).  mode 0
- * (default): each step is three kernels (lb_pull, particle_pass, cell_pass)
- * over all replicas, 64 steps per captured CUDA graph.  mode 1: each chunk of
- * steps is one persistent cooperative kernel running the three phases per
+ * (default): per-kernel launches over all replicas, captured once into CUDA
+ * graphs of 1, 2, 4, ..., 64 steps.  By default mode 0 runs the overlapped
+ * form: the LB update of step n + 1, which needs only the populations of
+ * step n, runs beside the particle pass of step n (launched as a
+ * programmatic dependent of the pass, taking its row tiles from a work
+ * counter, with the pass capped at blocks_per_sm blocks per SM -- 0 = the
+ * occupancy limit, where the LB blocks take the SMs the pass's blocks leave
+ * as they finish), and a third launch per step builds the
+ * collision-cell table and applies the MPCD->LB imposition of step n.  The
+ * learned closure, density resampling, the Chapman-Enskog redraw and the
+ * TMA-staged LB rows run the serial form instead (one LB launch carrying
+ * the previous step's table and imposition, then the particle pass), as does
+ * every run with flags & LBMPCD_LAUNCH_SERIAL.  mode 1: each chunk of steps is
+ * one persistent cooperative kernel running the LB and particle phases per
  * step with a grid barrier between phases (bounded waits: a barrier that
  * times out ends the launch and lbmpcd_step returns ERR_TIMEOUT), captured
  * into the chunk's graph when the driver allows the capture, launched
- * directly otherwise; lbmpcd_step then synchronises the stream at its end.
- * blocks_per_sm: persistent blocks per SM (0 = the occupancy limit).  Results
- * are those of mode 0 (same per-step records, same kernels' item code).  Mode 1
- * is not available with the learned closure (INVALID_ARG); lbmpcd_step_profiled
- * always launches per kernel.  flags: LBMPCD_LAUNCH_LB_TMA runs the LB update
- * of D2Q9 binary32 channels (4 nodes per thread) with its source rows staged in
- * shared memory by bulk (TMA) copies, three rows ahead per block; ignored for
- * other lattices and precisions.  A bounded wait in that kernel that gives up
- * is reported by the next lbmpcd_get_fields as ERR_TIMEOUT. */
+ * directly otherwise; lbmpcd_step then synchronises the stream at its end;
+ * blocks_per_sm: persistent blocks per SM (0 = the occupancy limit).  Every
+ * form computes the same results (same per-step records, same item code,
+ * the same operations in the same order per element).  Mode 1 is not
+ * available with the learned closure, density resampling, MPCD-AT or the
+ * Chapman-Enskog redraw (INVALID_ARG).  flags: LBMPCD_LAUNCH_LB_TMA runs the
+ * LB update of D2Q9 binary32 channels (4 nodes per thread) with its source
+ * rows staged in shared memory by bulk (TMA) copies, three rows ahead per
+ * block; ignored for other lattices and precisions.  A bounded wait in that
+ * kernel that gives up is reported by the next lbmpcd_get_fields as
+ * ERR_TIMEOUT. */
 #define LBMPCD_LAUNCH_LB_TMA 1   /* flags: D2Q9 binary32 LB rows staged by bulk (TMA) copies */
+#define LBMPCD_LAUNCH_SERIAL 2   /* flags: mode 0 without the overlapped form */
 int lbmpcd_set_launch_mode(lbmpcd* h, int mode, int blocks_per_sm, int flags);
 
 /* Poll limit of the grid-barrier waits of the persistent launch form (mode 1;
@@ -367,9 +381,11 @@ int lbmpcd_set_launch_mode(lbmpcd* h, int mode, int blocks_per_sm, int flags);
  * words are reset and the handle can be stepped or destroyed as usual. */
 int lbmpcd_set_wait_limit(lbmpcd* h, unsigned polls);
 
-/* Time the launch forms {mode 0 with the default LB row width, with TMA rows
- * (where they apply), with one LB node per thread; mode 1 at the occupancy
- * limit and with one block per SM} for `steps` steps each (after a 64-step
+/* Time the launch forms {mode 0 with the default LB row width (overlapped,
+ * with the particle pass at the occupancy limit, 6 and 7 blocks per SM where
+ * the overlapped form applies, and serial), with TMA rows (where they apply), with
+ * one LB node per thread; mode 1 at the occupancy limit and with one block per
+ * SM} for `steps` steps each (after a 64-step
  * warm-up) on a fresh copy of the handle built from the same parameters and
  * regions -- the handle's own state is not touched -- and keep the fastest.
  * choice (may be NULL) receives {mode, blocks_per_sm, LB nodes per thread,

@@ -28,6 +28,7 @@ FIELDS = dict(RHO=0, U=1, POPS=2, PART_POS=3, PART_VEL=4, PART_CELL=5, SHIFT=6,
               CLOSURE_IN=13, CLOSURE_OUT=14, CLOSURE_TARGET=15, CELL_LIST=17)
 INT_FIELDS = {"PART_CELL", "CELL_COUNT", "PART_HOME", "PART_ID", "CELL_LIST"}
 LAUNCH_LB_TMA = 1   # LBMPCD_LAUNCH_LB_TMA
+LAUNCH_SERIAL = 2   # LBMPCD_LAUNCH_SERIAL
 ERRORS = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "TIMEOUT", -5: "STATE", -6: "CAPACITY"}
 
 
@@ -373,11 +374,13 @@ class Lbmpcd:
     def set_closure(self, theta, interval: int = 1):
         lbmpcd_set_closure(self._h, theta, interval)
 
-    def set_launch_mode(self, mode: int, blocks_per_sm: int = 0, lb_tma: bool = False):
-        """0: per-kernel launches in 64-step graphs; 1: one persistent kernel per
-        chunk.  lb_tma: TMA-staged LB rows (D2Q9 binary32)."""
-        _check(self._h, load_library().lbmpcd_set_launch_mode(self._h, int(mode), int(blocks_per_sm),
-                                                              LAUNCH_LB_TMA if lb_tma else 0))
+    def set_launch_mode(self, mode: int, blocks_per_sm: int = 0, lb_tma: bool = False, serial: bool = False):
+        """0: per-kernel launches in 64-step graphs (overlapped unless serial;
+        blocks_per_sm caps the particle pass there); 1: one persistent kernel
+        per chunk (blocks_per_sm: its blocks per SM).  lb_tma: TMA-staged LB
+        rows (D2Q9 binary32)."""
+        flags = (LAUNCH_LB_TMA if lb_tma else 0) | (LAUNCH_SERIAL if serial else 0)
+        _check(self._h, load_library().lbmpcd_set_launch_mode(self._h, int(mode), int(blocks_per_sm), flags))
 
     def set_wait_limit(self, polls: int = 0):
         """Polls before a grid-barrier wait of the persistent form gives up
@@ -389,7 +392,7 @@ class Lbmpcd:
         out = (ctypes.c_int * 5)()
         _check(self._h, load_library().lbmpcd_autotune(self._h, int(steps), out))
         return dict(mode=out[0], blocks_per_sm=out[1], lb_nodes_per_thread=out[2], lb_tma=bool(out[3] & LAUNCH_LB_TMA),
-                    candidates=out[4])
+                    serial=bool(out[3] & LAUNCH_SERIAL), candidates=out[4])
 
     def get(self, field: str, replica: int = 0, out=None):
         return lbmpcd_get_fields(self._h, replica, field, out)

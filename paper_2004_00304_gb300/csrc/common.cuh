@@ -2,6 +2,7 @@
 // the counter-based generator, uniform/normal maps, lattice tables, the
 // per-replica descriptor and the per-step record read by every kernel.
 #pragma once
+#include <utility>
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 #include <stdint.h>
@@ -166,8 +167,8 @@ struct RepDev {
   float fp16_scale;        // binary16 deviation scale 2^k (1 for the other storages)
   float fp16_inv;
   void* f[2];              // populations [q][nnode], ping-pong by step parity
-  void* rho;               // [nnode]
-  void* u;                 // [3][nnode]
+  void* rho;               // [2][nnode]     by step parity (rho_of)
+  void* u;                 // [2][3][nnode]  by step parity (u_of)
   // MPCD region, cell units: [0,Wx) x [0,Hy) x [0,Wz)
   int has_region, x0, x1, Wx, Hy, Wz, r, n_out, n_in, cw, ppc, feedback, window;
   double kT, mass, sig;    // sig = sqrt(kT / m)
@@ -246,6 +247,16 @@ struct RepDev {
 
 constexpr int SORT_TILE = 1024;
 
+// rho and u of the LB update of step n: two copies, by step parity, so that
+// the particle pass of step n reads them while the LB update of step n + 1
+// writes the other copy
+template <typename R> __device__ __forceinline__ R* rho_of(const RepDev& rd, uint32_t n) {
+  return (R*)rd.rho + (long long)(n & 1u) * rd.nnode;
+}
+template <typename R> __device__ __forceinline__ R* u_of(const RepDev& rd, uint32_t n) {
+  return (R*)rd.u + (long long)(n & 1u) * 3 * rd.nnode;
+}
+
 // end of the particle slots in use: the pool end with density resampling,
 // the fixed count otherwise
 __device__ __forceinline__ uint32_t pool_end(const RepDev& rd) {
@@ -265,6 +276,8 @@ struct StepInfo {
   int write_moments;       // write rho/u on every node this step
   int src_alt;             // particle state of this step is in the *_alt (sorted) arrays
   int cells;               // the collision-cell table of step n - 1 is still to be built (LB launch)
+  int lb_a8;               // the LB launch of step n applies a8 of step n - 1 on the inner-buffer nodes
+                           // (otherwise a launch after the particle pass of step n - 1 does)
   double shift[3], prev[3];
   float shift_f[3], prev_f[3];   // the same shifts (exact in binary32)
 };
@@ -361,6 +374,32 @@ template <> struct Store<__half> {
   __device__ static void st(__half* p, float v, float scale, uint32_t h = 0) { *p = sr_half(v * scale, h); }
 };
 
+// Programmatic dependent launch: a kernel launched after this one with the
+// programmatic-serialization attribute may start once every block of this
+// one has passed allow_dependent_launch; such a kernel calls
+// wait_for_prerequisite before it ends, so that it completes only after this
+// one has (and sees its writes).  Both are no-ops without such a launch.
+__device__ __forceinline__ void allow_dependent_launch() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void wait_for_prerequisite() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Launch with or without the programmatic-serialization attribute (pdl).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), int grid, int block, cudaStream_t st, bool pdl,
+                              Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
 // Copy a block's descriptor and step record to shared memory (all threads
 // call it; it ends with a barrier).  si == nullptr skips the step record.
 __device__ __forceinline__ void load_block_records(RepDev& srd, StepInfo& sst, const RepDev* reps,
@@ -452,10 +491,8 @@ inline int grid_cap(int resident) {
   return mode ? (1 << 30) : resident;
 }
 
-// Blocks to launch for nwork items: enough to fill every SM at the kernel's
-// occupancy, never more than the items.
-template <typename K>
-inline int grid_for(K kernel, int threads, int nwork) {
+// streaming multiprocessors of the current device (read once)
+inline int sm_count() {
   static int sms = 0;
   if (!sms) {
     int dev = 0;
@@ -463,6 +500,14 @@ inline int grid_for(K kernel, int threads, int nwork) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (sms <= 0) sms = 1;
   }
+  return sms;
+}
+
+// Blocks to launch for nwork items: enough to fill every SM at the kernel's
+// occupancy, never more than the items.
+template <typename K>
+inline int grid_for(K kernel, int threads, int nwork) {
+  const int sms = sm_count();
   int occ = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, 0) != cudaSuccess || occ < 1) occ = 1;
   const long long cap = (long long)occ * sms;

@@ -33,11 +33,22 @@ int lb_vector_width(int q, int prec, int nx);
 bool lb_tma_ok(int q, int prec, int vec);
 cudaError_t launch_lb(int q, int prec, int vec, bool tma, const Launch& L, const int4* bmap, int nblocks, int k);
 
+// The overlapped form of a step (the LB update of step n + 1 runs beside the
+// particle pass of step n, which it does not depend on):
+// launch_lb_rows: the LB row items of step slot k, launched as a programmatic
+// dependent of the particle pass just launched on the same stream (it starts
+// while the pass runs, takes its rows from the work counter ctr[k], and ends
+// only after the pass has); launch_lb_items: a kernel over a map of non-row
+// LB items (closure strip frame, collision-cell table, a8) of step slot k,
+// after both (pdl: as a programmatic dependent of the rows just launched).
+cudaError_t launch_lb_rows(int q, int prec, int vec, const Launch& L, const int4* bmap, int nwork, int k, int* ctr);
+cudaError_t launch_lb_items(int q, int prec, const Launch& L, const int4* bmap, int nwork, int k, bool pdl);
+
 // prep: per-step records (shift, pending flag) for kcount steps.  d_sorted[r]
 // (set by the sort, cleared here) says that replica r's current particle state
 // is the sorted copy in the *_alt arrays, which the chunk's first step reads.
 cudaError_t launch_prep(int dim, const Launch& L, StepInfo* si, int kcount, int* d_sorted, uint32_t* d_step,
-                        int* d_pending, int* d_cells, double* d_last_shift);
+                        int* d_pending, int* d_cells, double* d_last_shift, int overlap, int* ctr);
 
 // counting sort of the particles by home cell into the *_alt arrays; sets
 // d_sorted[r] for every replica with a region.
@@ -47,9 +58,10 @@ cudaError_t launch_sort(int dim, int prec, const Launch& L, const int2* bmap_p, 
 // collision-cell table -> CELL_COUNT (field 7, int32) or CELL_VCM (field 11, [ncell][3] binary64).
 cudaError_t launch_tab_out(int dim, int prec, const RepDev& rd, int field, void* out, cudaStream_t st);
 
-// a7(n-1) + a2 + a3 + a4 + a6 + a5 over every particle.
+// a7(n-1) + a2 + a3 + a4 + a6 + a5 over every particle; bps > 0 caps the
+// blocks per SM (the overlapped form), 0 takes the occupancy limit.
 cudaError_t launch_particles(int dim, int prec, bool rs, bool at, bool ce, const Launch& L, const int2* bmap,
-                             int nblocks, int k);
+                             int nblocks, int k, int bps, bool pdl = false);
 
 // a7 cell part of step m (v_cm, virtual particles, rotation draw) for the
 // read-outs between calls (the step builds it inside the next LB launch).

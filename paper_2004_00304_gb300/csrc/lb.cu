@@ -37,6 +37,112 @@ __global__ void __launch_bounds__(128, Q == 9 ? 7 : 5) lb_pull_one(const __grid_
                     [&](const int4 bm) { lb_row<Q, S, V>(rd, st, bm); });
 }
 
+// LB rows of the overlapped form: items taken from the counter ctr[k] (one
+// atomic per item, the next one fetched while the current one runs), so that
+// the blocks that start beside the particle pass take as many rows as they
+// can and the rest start when the pass ends; each block ends with the
+// programmatic-dependency wait for the pass it was launched after.
+template <typename Body>
+__device__ __forceinline__ void rows_from_counter(const int4* __restrict__ bmap, int nwork, int* ctr, Body&& body) {
+  __shared__ int s_next[2];
+  if (threadIdx.x == 0) s_next[0] = atomicAdd(ctr, 1);
+  __syncthreads();
+  for (int it = 0;; ++it) {
+    const int wi = s_next[it & 1];
+    if (wi >= nwork) break;
+    if (threadIdx.x == 0) s_next[(it + 1) & 1] = atomicAdd(ctr, 1);
+    body(bmap[wi]);
+    __syncthreads();
+  }
+  allow_dependent_launch();   // the table / a8 launch may start its blocks now
+  wait_for_prerequisite();
+}
+
+#ifndef LBM_ROWS_MINB
+#define LBM_ROWS_MINB 7
+#endif
+template <int Q, typename S, int V>
+__global__ void __launch_bounds__(128, Q == 9 ? LBM_ROWS_MINB : 5) lb_rows_one(const __grid_constant__ RepDev rd,
+                                                   const int4* __restrict__ bmap, int nwork,
+                                                   const StepInfo* __restrict__ si, int k, int* ctr) {
+  __shared__ StepInfo st;
+  {
+    const int* c = (const int*)(si + k);
+    int* d = (int*)&st;
+    for (int i = threadIdx.x; i < (int)(sizeof(StepInfo) / 4); i += blockDim.x) d[i] = c[i];
+  }
+  rows_from_counter(bmap, nwork, ctr + k, [&](const int4 bm) { lb_row<Q, S, V>(rd, st, bm); });
+}
+
+template <int Q, typename S, int V>
+__global__ void __launch_bounds__(128, Q == 9 ? 7 : 5) lb_rows(const RepDev* __restrict__ reps,
+                                               const int4* __restrict__ bmap, int nwork,
+                                               const StepInfo* __restrict__ si, int k, int nrep, int* ctr) {
+  rows_from_counter(bmap, nwork, ctr + k, [&](const int4 bm) {
+    lb_row<Q, S, V>(reps[bm.x], si[(long long)k * nrep + bm.x], bm);
+  });
+}
+
+template <int Q, typename S, int V>
+static cudaError_t go_lb_rows(const Launch& L, const int4* bmap, int nwork, int k, int* ctr) {
+  if (nwork == 0) return cudaSuccess;
+  if (L.nrep == 1 && L.host) {
+    static const int g1 = grid_for(lb_rows_one<Q, S, V>, 128, 1 << 30);
+    return launch_pdl(lb_rows_one<Q, S, V>, g1 < nwork ? g1 : nwork, 128, L.stream, true, *L.host, bmap, nwork,
+                      L.si, k, ctr);
+  }
+  static const int g = grid_for(lb_rows<Q, S, V>, 128, 1 << 30);
+  return launch_pdl(lb_rows<Q, S, V>, g < nwork ? g : nwork, 128, L.stream, true, L.reps, bmap, nwork, L.si, k,
+                    L.nrep, ctr);
+}
+
+// The table / a8 launch of the overlapped form (items of lb_item only, so
+// without the row code's registers).  Launched as a programmatic dependent of
+// the LB rows (pdl), its blocks may be placed while the particle pass still
+// runs; they wait for the rows (which wait for the pass) before any work,
+// and let the next particle pass be placed at once.
+#ifndef LBM_ITEMS_MINB
+#define LBM_ITEMS_MINB 8
+#endif
+template <int Q, typename S>
+__global__ void __launch_bounds__(128, LBM_ITEMS_MINB) lb_items_one(const __grid_constant__ RepDev rd,
+                                                    const int4* __restrict__ bmap, int nwork,
+                                                    const StepInfo* __restrict__ si, int k) {
+  __shared__ StepInfo st;
+  wait_for_prerequisite();
+  allow_dependent_launch();
+  {
+    const int* c = (const int*)(si + k);
+    int* d = (int*)&st;
+    for (int i = threadIdx.x; i < (int)(sizeof(StepInfo) / 4); i += blockDim.x) d[i] = c[i];
+    __syncthreads();
+  }
+  for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) lb_item<Q, S>(rd, st, bmap[wi]);
+}
+
+template <int Q, typename S>
+__global__ void __launch_bounds__(128, LBM_ITEMS_MINB) lb_items(const RepDev* __restrict__ reps,
+                                                const int4* __restrict__ bmap, int nwork,
+                                                const StepInfo* __restrict__ si, int k, int nrep) {
+  wait_for_prerequisite();
+  allow_dependent_launch();
+  for (int wi = blockIdx.x; wi < nwork; wi += gridDim.x) {
+    const int4 bm = bmap[wi];
+    lb_item<Q, S>(reps[bm.x], si[(long long)k * nrep + bm.x], bm);
+  }
+}
+
+template <int Q, typename S>
+static cudaError_t go_lb_items(const Launch& L, const int4* bmap, int nwork, int k, bool pdl) {
+  if (nwork == 0) return cudaSuccess;
+  if (L.nrep == 1 && L.host) {
+    static const int g1 = grid_for(lb_items_one<Q, S>, 128, 1 << 30);
+    return launch_pdl(lb_items_one<Q, S>, g1 < nwork ? g1 : nwork, 128, L.stream, pdl, *L.host, bmap, nwork, L.si, k);
+  }
+  static const int g = grid_for(lb_items<Q, S>, 128, 1 << 30);
+  return launch_pdl(lb_items<Q, S>, g < nwork ? g : nwork, 128, L.stream, pdl, L.reps, bmap, nwork, L.si, k, L.nrep);
+}
+
 template <int Q, typename S, int V>
 static cudaError_t go_lb(const Launch& L, const int4* bmap, int nwork, int k) {
   if (nwork == 0) return cudaSuccess;
@@ -206,6 +312,30 @@ cudaError_t launch_lb(int q, int prec, int vec, bool tma, const Launch& L, const
   if (prec == P_FP64) return go_lb<19, double, 1>(L, bmap, nblocks, k);
   if (prec == P_FP32) return vec == 2 ? go_lb<19, float, 2>(L, bmap, nblocks, k) : go_lb<19, float, 1>(L, bmap, nblocks, k);
   return vec == 2 ? go_lb<19, __half, 2>(L, bmap, nblocks, k) : go_lb<19, __half, 1>(L, bmap, nblocks, k);
+}
+
+cudaError_t launch_lb_rows(int q, int prec, int vec, const Launch& L, const int4* bmap, int nwork, int k, int* ctr) {
+  if (q == 9) {
+    if (prec == P_FP64) return go_lb_rows<9, double, 1>(L, bmap, nwork, k, ctr);
+    if (prec == P_FP32)
+      return vec == 4 ? go_lb_rows<9, float, 4>(L, bmap, nwork, k, ctr) : go_lb_rows<9, float, 1>(L, bmap, nwork, k, ctr);
+    return vec == 4 ? go_lb_rows<9, __half, 4>(L, bmap, nwork, k, ctr) : go_lb_rows<9, __half, 1>(L, bmap, nwork, k, ctr);
+  }
+  if (prec == P_FP64) return go_lb_rows<19, double, 1>(L, bmap, nwork, k, ctr);
+  if (prec == P_FP32)
+    return vec == 2 ? go_lb_rows<19, float, 2>(L, bmap, nwork, k, ctr) : go_lb_rows<19, float, 1>(L, bmap, nwork, k, ctr);
+  return vec == 2 ? go_lb_rows<19, __half, 2>(L, bmap, nwork, k, ctr) : go_lb_rows<19, __half, 1>(L, bmap, nwork, k, ctr);
+}
+
+cudaError_t launch_lb_items(int q, int prec, const Launch& L, const int4* bmap, int nwork, int k, bool pdl) {
+  if (q == 9) {
+    if (prec == P_FP64) return go_lb_items<9, double>(L, bmap, nwork, k, pdl);
+    if (prec == P_FP32) return go_lb_items<9, float>(L, bmap, nwork, k, pdl);
+    return go_lb_items<9, __half>(L, bmap, nwork, k, pdl);
+  }
+  if (prec == P_FP64) return go_lb_items<19, double>(L, bmap, nwork, k, pdl);
+  if (prec == P_FP32) return go_lb_items<19, float>(L, bmap, nwork, k, pdl);
+  return go_lb_items<19, __half>(L, bmap, nwork, k, pdl);
 }
 
 // ---- copy-out / copy-in of populations and LB-side diagnostics ------------

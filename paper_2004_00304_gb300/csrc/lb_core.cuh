@@ -184,8 +184,8 @@ __device__ __forceinline__ void lb_finish(const RepDev& rd, const StepInfo& st, 
       want = da <= rd.cw + 1 || db <= rd.cw + 1;
     }
     if (want) {
-      R* rh = (R*)rd.rho;
-      R* uv = (R*)rd.u;
+      R* rh = rho_of<R>(rd, st.n);
+      R* uv = u_of<R>(rd, st.n);
       rh[row + x] = mr[v];
       uv[row + x] = mu[0][v];
       uv[N + row + x] = mu[1][v];
@@ -194,8 +194,9 @@ __device__ __forceinline__ void lb_finish(const RepDev& rd, const StepInfo& st, 
   }
   // a8 of step m = n - 1 on the inner-buffer nodes (a few lanes of a few
   // rows; after the stores above, in a function of its own so that it does
-  // not add to the row's register allocation)
-  if (rd.nbuf > 0 && st.n >= 1u) {
+  // not add to the row's register allocation), unless a8 items of a launch
+  // after this one apply it (the overlapped form, below)
+  if (rd.nbuf > 0 && st.n >= 1u && st.lb_a8) {
 #pragma unroll
     for (int v = 0; v < V; ++v) {
       const long long b = inner_index(rd, x0 + v, y, z);
@@ -204,25 +205,70 @@ __device__ __forceinline__ void lb_finish(const RepDev& rd, const StepInfo& st, 
   }
 }
 
+// LB node index of inner-buffer node b (the inverse of inner_index).
+__device__ __forceinline__ long long inner_node(const RepDev& rd, long long b) {
+  if (rd.strip) {
+    const int x = (int)(b % rd.nx);
+    const long long t = b / rd.nx;
+    const int z = (int)(t % rd.nz), row = (int)(t / rd.nz);
+    const int y = rd.y1 - 1 - rd.n_out - row;
+    return x + (long long)rd.nx * (y + (long long)rd.ny * z);
+  }
+  const int y = 1 + (int)(b % (rd.ny - 2));
+  const long long t = b / (rd.ny - 2);
+  const int z = (int)(t % rd.nz);
+  const long long t2 = t / rd.nz;
+  const int col = (int)(t2 % rd.n_in), side = (int)(t2 / rd.n_in);
+  const int x = side ? rd.x1 - 1 - rd.n_out - col : rd.x0 + rd.n_out + col;
+  return x + (long long)rd.nx * (y + (long long)rd.ny * z);
+}
+
+// a8 of step m as a work item of its own (the overlapped form, where the LB
+// update of step m + 1 runs beside the particle pass of step m): inner-buffer
+// node b takes frame m into the window and, with feedback, gets f_eq(rho_LB,
+// u_bar) over the post-collision populations the update of step m + 1 wrote,
+// rho_LB being that update's density of the node.  The same arithmetic as the
+// in-launch form.
+template <int Q, typename S>
+__device__ __forceinline__ void a8_item(const RepDev& rd, uint32_t m, long long b) {
+  using R = typename Store<S>::R;
+  if (b >= rd.nbuf) return;
+  const long long node = inner_node(rd, b);
+  a8_node<Q, S>(rd, m, b, (int)node, rho_of<R>(rd, m + 1u)[node]);
+}
+
 // One thread owns V consecutive nodes x0 .. x0+V-1 of one row (y, z).  A
 // work item (replica, tile, y, z | k << 24) is one block-wide tile of a row
 // (k = 0), or, for rows of tpr = nx / V < blockDim threads (tpr a power of
 // two dividing blockDim), the 2^k = blockDim / tpr rows y, y + 1, ... with
 // tpr threads each, so that narrow replicas do not leave most of a block
 // idle.
+// A work item other than an LB row (bm.y < 0), of block b = -1 - bm.y: the
+// strip cells of the closure frame (bm.z = -1), the collision-cell table
+// (bm.z = 0, blockDim CPT cells) or the a8 imposition of the inner-buffer
+// nodes (bm.z = -2).  bm.w = 0: of step n - 1, in the LB launch of step n;
+// bm.w = 1: of step n, in a launch after the particle pass of step n (the
+// overlapped form).
+template <int Q, typename S>
+__device__ __forceinline__ void lb_item(const RepDev& rd, const StepInfo& st, const int4 bm) {
+  const long long blk = -1 - bm.y;
+  const bool now = bm.w != 0;
+  const uint32_t m = now ? st.n : st.n - 1u;
+  if (bm.z == -1) {
+    if (now || st.n >= 1u) closure_fold_item(rd, m, blk * blockDim.x, 32LL * rd.Hy);
+  } else if (bm.z == -2) {
+    a8_item<Q, S>(rd, st.n, blk * blockDim.x + threadIdx.x);
+  } else if (now || st.cells) {
+    cell_table_item<Q, S>(rd, m, (now ? st.shift_f[1] : st.prev_f[1]) > 0.0f, blk * blockDim.x * CPT, rd.ncell);
+  }
+}
+
 template <int Q, typename S, int V>
 __device__ __forceinline__ void lb_row(const RepDev& rd, const StepInfo& st, const int4 bm) {
   using L = Lattice<Q>;
   using R = typename Store<S>::R;
   if (bm.y < 0) {
-    if (bm.z < 0) {   // item (-1 - b, -1): strip cells of block b, closure frame of step n - 1
-      if (st.n >= 1u) {
-        const long long c0 = (long long)(-1 - bm.y) * blockDim.x;
-        closure_fold_item(rd, st.n - 1u, c0, 32LL * rd.Hy);
-      }
-    } else if (st.cells) {   // item -1 - b: block b of blockDim CPT cells of the table of step n - 1
-      cell_table_item<Q, S>(rd, st.n - 1u, st.prev_f[1] > 0.0f, (long long)(-1 - bm.y) * blockDim.x * CPT, rd.ncell);
-    }
+    lb_item<Q, S>(rd, st, bm);
     return;
   }
   const int nx = rd.nx, ny = rd.ny, nz = rd.nz;

@@ -47,6 +47,14 @@ struct lbmpcd {
   int4* ptab = nullptr;                         // closure patches of the batch: (replica, side, py)
   int4* bm_lb256 = nullptr;                     // LB map with 256-thread row tiles (persistent kernel)
   int nb_lb256 = 0;
+  // overlapped form: LB row items alone; the items of the launch after the
+  // particle pass of step n (closure strip frame, table and a8 of step n),
+  // without a8 for the last step of a chunk
+  int4 *bm_rows = nullptr, *bm_c = nullptr, *bm_c_last = nullptr;
+  int nb_rows = 0, nb_c = 0, nb_c_last = 0;
+  bool serial = false;                          // overlapped form switched off (LBMPCD_LAUNCH_SERIAL)
+  int ov_bps = 0;                               // particle-pass blocks per SM in the overlapped form (0: default)
+  int* d_ctr = nullptr;                         // [KCHUNK] work counters of the overlapped LB rows
   int2* bm_s = nullptr;                         // outer-buffer cells of the density resampling
   int nb_s = 0;
   int mode = 0;                                 // 0: per-kernel launches in graphs, 1: persistent
@@ -221,9 +229,9 @@ extern "C" int lbmpcd_create(const lbmpcd_params* params, int n_replicas, void* 
     std::vector<void*>& L = h->allocs;
     e = dalloc(L, &d.f[0], h->q * d.nnode * ss);
     if (e == cudaSuccess) e = dalloc(L, &d.f[1], h->q * d.nnode * ss);
-    if (e == cudaSuccess) e = dalloc(L, &d.rho, d.nnode * rs);
-    if (e == cudaSuccess) e = dalloc(L, &d.u, 3 * d.nnode * rs);
-    if (e == cudaSuccess) e = launch_fill_real(h->prec, d.rho, d.nnode, 1.0, nullptr);   // rho0 = 1
+    if (e == cudaSuccess) e = dalloc(L, &d.rho, 2 * d.nnode * rs);   // two copies by step parity
+    if (e == cudaSuccess) e = dalloc(L, &d.u, 2 * 3 * d.nnode * rs);
+    if (e == cudaSuccess) e = launch_fill_real(h->prec, d.rho, 2 * d.nnode, 1.0, nullptr);   // rho0 = 1
     if (e != cudaSuccess) {
       int code = e == cudaErrorMemoryAllocation ? LBMPCD_ERR_OOM : LBMPCD_ERR_CUDA;
       std::string m = std::string("allocating LB arrays: ") + cudaGetErrorString(e);
@@ -241,6 +249,7 @@ extern "C" int lbmpcd_create(const lbmpcd_params* params, int n_replicas, void* 
   if (e == cudaSuccess) { e = dalloc(h->allocs, &tmp, sizeof(double) * 3 * n_replicas); h->d_last_shift = (double*)tmp; }
   if (e == cudaSuccess) { e = dalloc(h->allocs, &tmp, sizeof(int) * 16); h->d_flag = (int*)tmp; }
   if (e == cudaSuccess) { e = dalloc(h->allocs, &tmp, sizeof(unsigned) * 4); h->d_bar = (unsigned*)tmp; }
+  if (e == cudaSuccess) { e = dalloc(h->allocs, &tmp, sizeof(int) * KCHUNK); h->d_ctr = (int*)tmp; }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     std::string m = std::string("allocating handle arrays: ") + cudaGetErrorString(e);
@@ -308,7 +317,7 @@ static int build_maps(lbmpcd* h) {
   if (rc0) return rc0;
   std::vector<int4> lb;
   std::vector<int2> pp, tt, sp;
-  std::vector<int4> pt, lb256;
+  std::vector<int4> pt, lb256, rows_only, cit, cit_last;
   h->has_cl = false;
   for (int r = 0; r < h->nrep; ++r) {
     const RepDev& d = h->rd[r];
@@ -321,6 +330,17 @@ static int build_maps(lbmpcd* h) {
     if (d.has_region) {   // cell-table items first: their accumulators are still in L2
       for (long long b = 0; b < (d.ncell + 128 * CPT - 1) / (128 * CPT); ++b) lb.push_back(make_int4(r, (int)(-1 - b), 0, 0));
       for (long long b = 0; b < (d.ncell + 256 * CPT - 1) / (256 * CPT); ++b) lb256.push_back(make_int4(r, (int)(-1 - b), 0, 0));
+      // the overlapped form's items of step n after its particle pass (bm.w = 1):
+      // a8 of the inner-buffer nodes first (the longest chain of dependent
+      // loads) and only in the map for steps that are not the last of their
+      // chunk; strip frame and table in both maps
+      for (long long b = 0; b < (d.nbuf + 127) / 128; ++b) cit.push_back(make_int4(r, (int)(-1 - b), -2, 1));
+      for (auto* m : {&cit, &cit_last}) {
+        if (d.cl_on)
+          for (long long b = 0; b < (32LL * d.Hy + 127) / 128; ++b) m->push_back(make_int4(r, (int)(-1 - b), -1, 1));
+        for (long long b = 0; b < (d.ncell + 128 * CPT - 1) / (128 * CPT); ++b)
+          m->push_back(make_int4(r, (int)(-1 - b), 0, 1));
+      }
     }
     // row items for blocks of bd threads: tiles of one row, or 2^k whole rows
     // per item where a row has tpr = nx / vec threads, tpr a power of two
@@ -337,6 +357,7 @@ static int build_maps(lbmpcd* h) {
     };
     rows(lb, 128);
     rows(lb256, 256);
+    rows(rows_only, 128);
     if (!d.has_region) continue;
     const long long nslot = d.resample ? (long long)d.cap : d.np;
     const long long npb = (nslot + PP_ITEM - 1) / PP_ITEM;
@@ -357,6 +378,9 @@ static int build_maps(lbmpcd* h) {
   if (!rc) rc = upload_map(h, &h->ptab, &h->n_ptab, pt);
   if (!rc) rc = upload_map(h, &h->bm_lb256, &h->nb_lb256, lb256);
   if (!rc) rc = upload_map(h, &h->bm_s, &h->nb_s, sp);
+  if (!rc) rc = upload_map(h, &h->bm_rows, &h->nb_rows, rows_only);
+  if (!rc) rc = upload_map(h, &h->bm_c, &h->nb_c, cit);
+  if (!rc) rc = upload_map(h, &h->bm_c_last, &h->nb_c_last, cit_last);
   if (rc) return rc;
   CK(h, cudaMemcpy(h->d_reps, h->rd.data(), sizeof(RepDev) * h->nrep, cudaMemcpyHostToDevice));
   drop_graphs(h);
@@ -505,6 +529,58 @@ extern "C" int lbmpcd_set_region(lbmpcd* h, int replica, const int lo[3], const 
 // One chunk of kcount steps (the sort, when due, runs before it: run_sort).
 static bool persistent(const lbmpcd* h) { return h->mode == 1 && !h->has_cl; }
 
+// The overlapped form of the per-kernel launches: the LB update of step n + 1
+// needs only the populations of step n, so it runs beside the particle pass
+// of step n (a programmatic dependent of the pass, on the pass's stream, with
+// the pass capped at ov_bps blocks per SM so that LB blocks fit beside it);
+// the table and a8 of step n, which need both, follow in a launch of their
+// own.  A chunk is L(n0); then per step P(n) with L(n + 1) beside it, then
+// the table and a8 of step n; the last step's a8 is left to the next chunk's
+// first LB launch, as in the serial form.  Not with the learned closure
+// (its network runs between the pass and the table), density resampling (its
+// spawn runs before the pass) or the Chapman-Enskog redraw (the pass reads
+// the populations the LB update of step n + 1 overwrites), nor with the
+// TMA-staged LB rows.
+static bool overlapped(const lbmpcd* h) {
+  return h->mode == 0 && !h->serial && !h->has_cl && h->nb_s == 0 && !h->ce && !h->lb_tma && h->nb_p > 0;
+}
+
+// particle-pass blocks per SM in the overlapped form: the handle's setting,
+// else the occupancy limit (the LB blocks then take the SMs the pass leaves
+// as its blocks finish: measured faster on the 2048 x 512 channel than
+// capping the pass at 7 or 6 blocks per SM to make room for them)
+static int ov_blocks(const lbmpcd* h) { return h->pers_bps > 0 ? h->pers_bps : 0; }
+
+// Programmatic dependencies inside an overlapped chunk: bit 0, the table / a8
+// launch after the LB rows (its blocks are placed while the pass ends); bit
+// 1, the next particle pass after that launch.
+#ifndef LBM_OV_PDL
+#define LBM_OV_PDL 3
+#endif
+
+// The kernels of one overlapped chunk of kcount steps (after its prep);
+// around(phase, fn) wraps each launch group (the profiled form brackets them
+// with events, which also makes each group wait for the previous one).
+template <typename Around>
+static cudaError_t overlapped_chunk(lbmpcd* h, const Launch& L, int kcount, Around&& around) {
+  cudaError_t e = around(1, [&] { return launch_lb(h->q, h->prec, h->lbvec, false, L, h->bm_lb, h->nb_lb, 0); });
+  for (int k = 0; k < kcount && e == cudaSuccess; ++k) {
+    const bool last = k + 1 == kcount;
+    e = around(2, [&] {
+      cudaError_t x = launch_particles(h->dim, h->prec, false, h->at, false, L, h->bm_p, h->nb_p, k, ov_blocks(h),
+                                       k > 0 && (LBM_OV_PDL & 2));
+      if (x == cudaSuccess && !last) x = launch_lb_rows(h->q, h->prec, h->lbvec, L, h->bm_rows, h->nb_rows, k + 1, h->d_ctr);
+      return x;
+    });
+    if (e == cudaSuccess)
+      e = around(3, [&] {
+        return launch_lb_items(h->q, h->prec, L, last ? h->bm_c_last : h->bm_c, last ? h->nb_c_last : h->nb_c, k,
+                               !last && (LBM_OV_PDL & 1));
+      });
+  }
+  return e;
+}
+
 // the closure network runs on step n (handle-wide: every closure replica
 // shares the first evaluation and the interval)
 static bool closure_eval(const lbmpcd* h, long long n) {
@@ -529,8 +605,13 @@ static int closure_interval(const lbmpcd* h) {
 
 static int run_chunk(lbmpcd* h, int kcount, int cl_mode) {
   Launch L{h->d_reps, h->nrep, h->d_si, h->stream, h->d_flag + 8, h->rd.data()};
+  const bool ov = overlapped(h);
   CK(h, launch_prep(h->dim, L, h->d_si, kcount, h->d_sorted, h->d_step, h->d_pending, h->d_cells,
-                    h->d_last_shift));
+                    h->d_last_shift, ov ? 1 : 0, ov ? h->d_ctr : nullptr));
+  if (ov) {
+    CK(h, overlapped_chunk(h, L, kcount, [](int, auto&& fn) { return fn(); }));
+    return LBMPCD_OK;
+  }
   if (persistent(h)) {
     const PersistentMaps m{h->bm_lb256, h->nb_lb256, h->bm_p, h->nb_p, h->d_bar, (int*)(h->d_bar + 2), h->bar_spin};
     CK(h, launch_persistent(h->q, h->prec, h->lbvec, L, kcount, m, h->pers_bps, nullptr));
@@ -539,7 +620,7 @@ static int run_chunk(lbmpcd* h, int kcount, int cl_mode) {
   for (int k = 0; k < kcount; ++k) {
     CK(h, launch_lb(h->q, h->prec, h->lbvec, h->lb_tma, L, h->bm_lb, h->nb_lb, k));
     if (h->nb_s) CK(h, launch_spawn(h->dim, h->prec, L, h->bm_s, h->nb_s, k));
-    CK(h, launch_particles(h->dim, h->prec, h->nb_s > 0, h->at, h->ce, L, h->bm_p, h->nb_p, k));
+    CK(h, launch_particles(h->dim, h->prec, h->nb_s > 0, h->at, h->ce, L, h->bm_p, h->nb_p, k, 0));
     if (h->has_cl && h->cl_params) {
       const bool net = cl_mode == CL_FIRST ? k == 0
                      : cl_mode == CL_EVERY_K ? k % closure_interval(h) == 0
@@ -671,7 +752,10 @@ extern "C" int lbmpcd_step(lbmpcd* h, int nsteps) {
     h->nstep += kc;
   }
   if (nsteps > 0)
-    for (int r = 0; r < h->nrep; ++r) h->pending[r] = h->cells[r] = h->rd[r].has_region ? 1 : 0;
+    for (int r = 0; r < h->nrep; ++r) {
+      h->pending[r] = h->rd[r].has_region ? 1 : 0;
+      h->cells[r] = h->rd[r].has_region && !overlapped(h) ? 1 : 0;   // the overlapped form builds the last table
+    }
   if (nsteps > 0 && h->cl_params) {   // a bounded wait inside a closure GEMM gave up
     const int rc = net_error(h->net, h->stream);
     if (rc) return fail(h, rc, "closure network: a tensor-core wait timed out");
@@ -726,12 +810,24 @@ extern "C" int lbmpcd_step_profiled(lbmpcd* h, int nsteps, double* phase_ms, lon
       bracket(4, [&] { return launch_sort(h->dim, h->prec, L, h->bm_p, h->nb_p, h->bm_t, h->nb_t, h->d_sorted); });
       h->last_sort = h->nstep;
     }
+    const bool ov = overlapped(h);
     bracket(0, [&] { return launch_prep(h->dim, L, h->d_si, kc, h->d_sorted, h->d_step, h->d_pending,
-                                        h->d_cells, h->d_last_shift); });
-    for (int k = 0; k < kc; ++k) {
+                                        h->d_cells, h->d_last_shift, ov ? 1 : 0, ov ? h->d_ctr : nullptr); });
+    if (ov) {
+      // phase 1: the chunk's first LB launch; 2: each particle pass with the
+      // LB update of the next step beside it (one bracket: they overlap);
+      // 3: the table and a8 launch of each step
+      int inner = 0;
+      overlapped_chunk(h, L, kc, [&](int ph, auto&& fn) {
+        bracket(ph, [&] { return fn(); });
+        if (ph == 2 && inner++ + 1 < kc) ++nl;   // the LB rows launched inside the bracket
+        return e;
+      });
+    }
+    for (int k = 0; k < kc && !ov; ++k) {
       bracket(1, [&] { return launch_lb(h->q, h->prec, h->lbvec, h->lb_tma, L, h->bm_lb, h->nb_lb, k); });
       if (h->nb_s) bracket(2, [&] { return launch_spawn(h->dim, h->prec, L, h->bm_s, h->nb_s, k); });
-      if (h->nb_p) bracket(2, [&] { return launch_particles(h->dim, h->prec, h->nb_s > 0, h->at, h->ce, L, h->bm_p, h->nb_p, k); });
+      if (h->nb_p) bracket(2, [&] { return launch_particles(h->dim, h->prec, h->nb_s > 0, h->at, h->ce, L, h->bm_p, h->nb_p, k, 0); });
       if (h->has_cl && h->cl_params && closure_eval(h, h->nstep + k))
         bracket(5, [&] { return launch_closure_step(h->prec, L, h->ptab, h->n_ptab, k, net_closure(h->net)); });
     }
@@ -748,7 +844,10 @@ extern "C" int lbmpcd_step_profiled(lbmpcd* h, int nsteps, double* phase_ms, lon
   for (auto& x : ev) cudaEventDestroy(x);
   if (e != cudaSuccess) rc = cuda_fail(h, e, "step_profiled");
   if (nsteps > 0)
-    for (int r = 0; r < h->nrep; ++r) h->pending[r] = h->cells[r] = h->rd[r].has_region ? 1 : 0;
+    for (int r = 0; r < h->nrep; ++r) {
+      h->pending[r] = h->rd[r].has_region ? 1 : 0;
+      h->cells[r] = h->rd[r].has_region && !overlapped(h) ? 1 : 0;
+    }
   if (launches) *launches += nl;
   return rc;
 }
@@ -900,8 +999,13 @@ extern "C" int lbmpcd_get_fields(lbmpcd* h, int replica, int field, void* dst, s
   const int parity = (int)(h->nstep & 1);
   double ls[3] = {0, 0, 0};
   switch (field) {
-    case LBMPCD_RHO: e = launch_real_out(h->prec, d.rho, d.nnode, (double*)buf, h->stream); break;
-    case LBMPCD_U: e = launch_real_out(h->prec, d.u, 3 * d.nnode, (double*)buf, h->stream); break;
+    case LBMPCD_RHO: case LBMPCD_U: {   // the copy of the last LB update (parity of step nstep - 1)
+      const long long mp = h->nstep > 0 ? ((h->nstep - 1) & 1) : 0;
+      const size_t rs = real_size(h->prec);
+      e = field == LBMPCD_RHO ? launch_real_out(h->prec, (char*)d.rho + mp * d.nnode * rs, d.nnode, (double*)buf, h->stream)
+                              : launch_real_out(h->prec, (char*)d.u + mp * 3 * d.nnode * rs, 3 * d.nnode, (double*)buf, h->stream);
+      break;
+    }
     case LBMPCD_POPS: e = launch_pops_out(h->q, h->prec, d, parity, (double*)buf, h->stream); break;
     case LBMPCD_PART_POS: case LBMPCD_PART_VEL: case LBMPCD_PART_HOME: case LBMPCD_PART_CELL:
     case LBMPCD_PART_ID:
@@ -1047,7 +1151,7 @@ extern "C" int lbmpcd_set_wait_limit(lbmpcd* h, unsigned polls) {
 
 extern "C" int lbmpcd_set_launch_mode(lbmpcd* h, int mode, int blocks_per_sm, int flags) {
   if (!h) return LBMPCD_ERR_INVALID_ARG;
-  if (mode < 0 || mode > 1 || blocks_per_sm < 0 || (flags & ~LBMPCD_LAUNCH_LB_TMA))
+  if (mode < 0 || mode > 1 || blocks_per_sm < 0 || (flags & ~(LBMPCD_LAUNCH_LB_TMA | LBMPCD_LAUNCH_SERIAL)))
     return fail(h, LBMPCD_ERR_INVALID_ARG, "mode must be 0 or 1, flags a set of LBMPCD_LAUNCH_*");
   if (mode == 1)
     for (int r = 0; r < h->nrep; ++r)
@@ -1060,6 +1164,7 @@ extern "C" int lbmpcd_set_launch_mode(lbmpcd* h, int mode, int blocks_per_sm, in
   const bool tma = (flags & LBMPCD_LAUNCH_LB_TMA) && lb_tma_ok(h->q, h->prec, h->lbvec);
   if (tma != h->lb_tma) h->maps_dirty = true;   // the TMA form takes single-row items
   h->lb_tma = tma;
+  h->serial = (flags & LBMPCD_LAUNCH_SERIAL) != 0;
   h->pers_graph = true;
   drop_graphs(h);
   return LBMPCD_OK;
@@ -1078,6 +1183,11 @@ extern "C" int lbmpcd_autotune(lbmpcd* h, int steps, int* choice) {
   struct Cand { int mode, bps, vec, flags; };
   const int vdef = h->lbvec;
   std::vector<Cand> cands = {{0, 0, vdef, 0}};
+  if (!closure) {   // the overlapped form at other particle-pass shares of the SMs, and the serial form
+    cands.push_back({0, 6, vdef, 0});
+    cands.push_back({0, 7, vdef, 0});
+    cands.push_back({0, 0, vdef, LBMPCD_LAUNCH_SERIAL});
+  }
   if (lb_tma_ok(h->q, h->prec, vdef)) cands.push_back({0, 0, vdef, LBMPCD_LAUNCH_LB_TMA});
   if (vdef != 1) cands.push_back({0, 0, 1, 0});
   if (!closure) {

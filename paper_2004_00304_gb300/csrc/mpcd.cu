@@ -86,13 +86,20 @@ template <typename R> struct PState<3, R> {
 // ---------------------------------------------------------------------------
 // prep: one block; per (step k of the chunk, replica) the global step index,
 // the random shift of that step and of the previous one, and whether the
-// previous collision is still pending.  The sort, when one ran since the
+// previous collision is still pending.  overlap: the chunk runs the
+// overlapped form (the LB update of step n + 1 beside the particle pass of
+// step n, a launch after both for the table and a8 of step n): only the
+// chunk's first LB launch applies a8 of the step before it, and the chunk
+// leaves the table of its last step built; its work counters (ctr, one per
+// step) start at zero.  The sort, when one ran since the
 // last chunk, left d_sorted[r] = 1: the chunk's first step then reads the
 // sorted copy, and the flag is cleared for the next chunk.
 __global__ void prep_steps(const RepDev* __restrict__ reps, int nrep, int dim, int kcount, int* d_sorted,
                            StepInfo* __restrict__ si, uint32_t* d_step, int* d_pending, int* d_cells,
-                           double* d_last_shift) {
+                           double* d_last_shift, int overlap, int* ctr) {
   const uint32_t n0 = *d_step;
+  if (ctr)
+    for (int k = threadIdx.x; k < kcount; k += blockDim.x) ctr[k] = 0;
   for (int idx = threadIdx.x; idx < kcount * nrep; idx += blockDim.x) {
     const int k = idx / nrep, r = idx % nrep;
     const RepDev& rd = reps[r];
@@ -101,6 +108,7 @@ __global__ void prep_steps(const RepDev* __restrict__ reps, int nrep, int dim, i
     s.pending = (k == 0) ? d_pending[r] : 1;
     s.cells = (k == 0) ? d_cells[r] : (rd.has_region ? 1 : 0);
     s.write_moments = (k == kcount - 1);
+    s.lb_a8 = overlap ? (k == 0) : 1;
     s.src_alt = (k == 0) && d_sorted[r] && rd.has_region;
     const uint4 w = philox(0u, s.n, rd.rep, TAG_SHIFT, rd.key0, rd.key1);
     s.shift[0] = unit24(w.x);
@@ -124,15 +132,15 @@ __global__ void prep_steps(const RepDev* __restrict__ reps, int nrep, int dim, i
     const StepInfo& last = si[(kcount - 1) * nrep + r];
     for (int a = 0; a < 3; ++a) d_last_shift[3 * r + a] = last.shift[a];
     d_pending[r] = reps[r].has_region ? 1 : 0;
-    d_cells[r] = reps[r].has_region ? 1 : 0;
+    d_cells[r] = reps[r].has_region && !overlap ? 1 : 0;
   }
   if (threadIdx.x == 0) *d_step = n0 + kcount;
 }
 
 cudaError_t launch_prep(int dim, const Launch& L, StepInfo* si, int kcount, int* d_sorted, uint32_t* d_step,
-                        int* d_pending, int* d_cells, double* d_last_shift) {
+                        int* d_pending, int* d_cells, double* d_last_shift, int overlap, int* ctr) {
   prep_steps<<<1, 256, 0, L.stream>>>(L.reps, L.nrep, dim, kcount, d_sorted, si, d_step, d_pending, d_cells,
-                                      d_last_shift);
+                                      d_last_shift, overlap, ctr);
   return cudaGetLastError();
 }
 
@@ -190,22 +198,23 @@ __device__ __forceinline__ void rotate(const RepDev& rd, uint32_t c, R* v) {
 // LB velocity at node (x,y,z) with periodic x, z and the wall ghost
 // u(0) = -u(1), u(ny-1) = -u(ny-2) that puts u = 0 on the half-way walls.
 template <typename R>
-__device__ __forceinline__ R u_node(const RepDev& rd, int a, int x, int y, int z) {
+__device__ __forceinline__ R u_node(const RepDev& rd, uint32_t n, int a, int x, int y, int z) {
   x = wrap(x, rd.nx);
   z = wrap(z, rd.nz);
   R sgn = R(1);
   if (y <= 0) { y = 1; sgn = R(-1); }
   if (y >= rd.ny - 1) { y = rd.ny - 2; sgn = R(-1); }
-  const R* u = (const R*)rd.u;
+  const R* u = u_of<R>(rd, n);
   return sgn * u[a * rd.nnode + x + (long long)rd.nx * (y + (long long)rd.ny * z)];
 }
 
 // a2: bilinear (2D) / trilinear (3D) interpolation of the LB velocity, known
-// at node centres, to the centre of MPCD cell (X,Y,Z) (Algorithm 2).  In the
+// at node centres (the LB update of step n), to the centre of MPCD cell
+// (X,Y,Z) (Algorithm 2).  In the
 // kernel's precision: for refinement ratios that are powers of two the
 // positions and weights are exact in binary32.
 template <int D, typename R>
-__device__ void u_fine(const RepDev& rd, int X, int Y, int Z, R* out) {
+__device__ void u_fine(const RepDev& rd, uint32_t n, int X, int Y, int Z, R* out) {
   const R r = Cst<R>::r(rd);
   const R px = (R)rd.x0 + ((R)X + R(0.5)) / r - R(0.5);
   const R py = R(1) + ((R)Y + R(0.5)) / r - R(0.5);
@@ -219,7 +228,7 @@ __device__ void u_fine(const RepDev& rd, int X, int Y, int Z, R* out) {
         for (int dk = 0; dk < (D == 3 ? 2 : 1); ++dk) {
           R wgt = (di ? tx : R(1) - tx) * (dj ? ty : R(1) - ty);
           if (D == 3) wgt *= (dk ? tz : R(1) - tz);
-          acc += wgt * u_node<R>(rd, a, i0 + di, j0 + dj, k0 + dk);
+          acc += wgt * u_node<R>(rd, n, a, i0 + di, j0 + dj, k0 + dk);
         }
     out[a] = acc;
   }
@@ -420,7 +429,7 @@ __device__ __forceinline__ uint32_t move_particle(const RepDev& rd, const StepIn
   // a2 + a3: Maxwellian redraw in the outer buffer columns
   if (!(RS && rd.resample) && outer) {
     R uf[3] = {R(0), R(0), R(0)};
-    u_fine<D, R>(rd, X, Y, Z, uf);
+    u_fine<D, R>(rd, st.n, X, Y, Z, uf);
     const uint32_t id = (alt ? rd.pid_alt : rd.pid)[j];
     if (CE && rd.redraw == 1) {
       R C[3];
@@ -685,6 +694,8 @@ __global__ void __launch_bounds__(256, D == 2 ? 6 : 5) particle_pass(const RepDe
   __shared__ RepDev rd;
   __shared__ StepInfo st;
   __shared__ PassShared<D, R> red;
+  wait_for_prerequisite();    // launched as a programmatic dependent: the table of step n - 1 is complete
+  allow_dependent_launch();   // the LB update of step n + 1 may start beside this pass
   for_each_item<true>(bmap, nwork, reps, si, k, nrep, rd, st,
                       [&](const int2 bm) { particle_item<D, R, RS, AT, CE>(rd, st, (uint32_t)bm.y * PP_ITEM, ~0u, red); });
 }
@@ -696,6 +707,8 @@ __global__ void __launch_bounds__(256, (D == 2 && !CE && sizeof(R) == 4) ? 8 : (
                                                          const StepInfo* __restrict__ si, int k) {
   __shared__ StepInfo st;
   __shared__ PassShared<D, R> red;
+  wait_for_prerequisite();    // launched as a programmatic dependent: the table of step n - 1 is complete
+  allow_dependent_launch();   // the LB update of step n + 1 may start beside this pass
   {
     const int* c = (const int*)(si + k);
     int* d = (int*)&st;
@@ -711,29 +724,34 @@ __global__ void __launch_bounds__(256, (D == 2 && !CE && sizeof(R) == 4) ? 8 : (
   for (uint32_t s = b0; s < b1; s += PP_ITEM) particle_item<D, R, RS, AT, CE>(rd, st, s, b1, red);
 }
 
+// bps > 0: that many blocks per SM at most (the overlapped form leaves room
+// for the LB update beside the pass), else the occupancy limit
 template <int D, typename R, bool RS, bool AT, bool CE>
-static void go_particles(const Launch& L, const int2* bmap, int nwork, int k) {
+static void go_particles(const Launch& L, const int2* bmap, int nwork, int k, int bps, bool pdl) {
+  const int cap = bps > 0 ? bps * sm_count() : 1 << 30;
   if (L.nrep == 1 && L.host) {
     static const int g1 = grid_cap(grid_for(particle_pass_one<D, R, RS, AT, CE>, 256, 1 << 30));
-    particle_pass_one<D, R, RS, AT, CE><<<g1 < nwork ? g1 : nwork, 256, 0, L.stream>>>(*L.host, nwork, L.si, k);
+    const int g = min(min(g1, cap), nwork);
+    launch_pdl(particle_pass_one<D, R, RS, AT, CE>, g, 256, L.stream, pdl, *L.host, nwork, L.si, k);
     return;
   }
-  static const int g = grid_cap(grid_for(particle_pass<D, R, RS, AT, CE>, 256, 1 << 30));
-  particle_pass<D, R, RS, AT, CE><<<g < nwork ? g : nwork, 256, 0, L.stream>>>(L.reps, bmap, nwork, L.si, k,
-                                                                            L.nrep);
+  static const int gm = grid_cap(grid_for(particle_pass<D, R, RS, AT, CE>, 256, 1 << 30));
+  const int g = min(min(gm, cap), nwork);
+  launch_pdl(particle_pass<D, R, RS, AT, CE>, g, 256, L.stream, pdl, L.reps, bmap, nwork, L.si, k, L.nrep);
 }
 
 template <int D, typename R>
-static void go_particles_mode(bool rs, bool at, bool ce, const Launch& L, const int2* bmap, int nwork, int k) {
+static void go_particles_mode(bool rs, bool at, bool ce, const Launch& L, const int2* bmap, int nwork, int k,
+                              int bps, bool pdl) {
   if (ce) {
-    if (at) go_particles<D, R, false, true, true>(L, bmap, nwork, k);
-    else go_particles<D, R, false, false, true>(L, bmap, nwork, k);
+    if (at) go_particles<D, R, false, true, true>(L, bmap, nwork, k, bps, pdl);
+    else go_particles<D, R, false, false, true>(L, bmap, nwork, k, bps, pdl);
   } else if (at) {
-    go_particles<D, R, false, true, false>(L, bmap, nwork, k);
+    go_particles<D, R, false, true, false>(L, bmap, nwork, k, bps, pdl);
   } else if (rs) {
-    go_particles<D, R, true, false, false>(L, bmap, nwork, k);
+    go_particles<D, R, true, false, false>(L, bmap, nwork, k, bps, pdl);
   } else {
-    go_particles<D, R, false, false, false>(L, bmap, nwork, k);
+    go_particles<D, R, false, false, false>(L, bmap, nwork, k, bps, pdl);
   }
 }
 
@@ -742,14 +760,14 @@ static void go_particles_mode(bool rs, bool at, bool ce, const Launch& L, const 
 // at: the handle's replicas collide by MPCD-AT (never together with rs);
 // ce: some replica redraws by Chapman-Enskog (never together with rs)
 cudaError_t launch_particles(int dim, int prec, bool rs, bool at, bool ce, const Launch& L, const int2* bmap,
-                             int nwork, int k) {
+                             int nwork, int k, int bps, bool pdl) {
   if (nwork == 0) return cudaSuccess;
   if (dim == 2) {
-    if (prec == P_FP64) go_particles_mode<2, double>(rs, at, ce, L, bmap, nwork, k);
-    else go_particles_mode<2, float>(rs, at, ce, L, bmap, nwork, k);
+    if (prec == P_FP64) go_particles_mode<2, double>(rs, at, ce, L, bmap, nwork, k, bps, pdl);
+    else go_particles_mode<2, float>(rs, at, ce, L, bmap, nwork, k, bps, pdl);
   } else {
-    if (prec == P_FP64) go_particles_mode<3, double>(rs, at, ce, L, bmap, nwork, k);
-    else go_particles_mode<3, float>(rs, at, ce, L, bmap, nwork, k);
+    if (prec == P_FP64) go_particles_mode<3, double>(rs, at, ce, L, bmap, nwork, k, bps, pdl);
+    else go_particles_mode<3, float>(rs, at, ce, L, bmap, nwork, k, bps, pdl);
   }
   return cudaGetLastError();
 }
@@ -776,7 +794,7 @@ __device__ __forceinline__ void spawn_item(const RepDev& rd, const StepInfo& st,
   const int X = xi < nl ? xi : rd.xo_hi + (xi - nl);
   const uint32_t c = (uint32_t)(X + (long long)rd.Wx * (Y + (long long)rd.Hy * Z));
   const long long node = (rd.x0 + X / rd.r) + (long long)rd.nx * ((1 + Y / rd.r) + (long long)rd.ny * (D == 3 ? Z / rd.r : 0));
-  const double x = (double)rd.ppc * (double)((const R*)rd.rho)[node];
+  const double x = (double)rd.ppc * (double)rho_of<R>(rd, st.n)[node];
   const uint4 wd = philox(c, st.n, rd.rep, TAG_DENSITY, rd.key0, rd.key1);
   const double fl = floor(x);
   const uint32_t nmax = (uint32_t)(SPAWN_MAX * rd.ppc);
@@ -785,7 +803,7 @@ __device__ __forceinline__ void spawn_item(const RepDev& rd, const StepInfo& st,
   uint32_t n = nn > (long long)nmax ? nmax : (uint32_t)nn;
   if (n == 0) return;
   R uf[3] = {R(0), R(0), R(0)};
-  u_fine<D, R>(rd, X, Y, Z, uf);
+  u_fine<D, R>(rd, st.n, X, Y, Z, uf);
   const uint32_t base = atomicAdd(rd.pool, n);
   const bool alt = st.src_alt;
   uint32_t* home = alt ? rd.home_alt : rd.home;
