@@ -104,7 +104,7 @@ def algorithmic_bytes(p, region):
 
 def step_launches(n0: int, last_sort: int, steps: int, mode: int, kchunk: int = 64, overlapped: bool = False):
     """Kernel launches of lbmpcd_step(steps) from step n0 (the library's chunk
-    rule: chunks of 64 steps, then the powers of two below; a counting sort of
+    rule: chunks of 64 steps, then one of the rest; a counting sort of
     four kernels before a chunk once 64 steps have passed since the last one;
     one prep kernel per chunk; two kernels per step, or in the overlapped form
     one LB launch per chunk and three kernels per step but the last (particle
@@ -112,9 +112,7 @@ def step_launches(n0: int, last_sort: int, steps: int, mode: int, kchunk: int = 
     chunk).  Returns (launches, step count, last sort)."""
     n, left, total = n0, steps, 0
     while left > 0:
-        kc = kchunk
-        while kc > left:
-            kc //= 2
+        kc = min(kchunk, left)
         if n - last_sort >= kchunk:
             total += 4
             last_sort = n
@@ -125,15 +123,8 @@ def step_launches(n0: int, last_sort: int, steps: int, mode: int, kchunk: int = 
 
 
 def n_chunks(steps: int, kchunk: int = 64) -> int:
-    """Chunks of lbmpcd_step(steps): 64 steps, then the powers of two below."""
-    n, left = 0, steps
-    while left > 0:
-        kc = kchunk
-        while kc > left:
-            kc //= 2
-        left -= kc
-        n += 1
-    return n
+    """Chunks of lbmpcd_step(steps): 64 steps each, then the rest."""
+    return -(-steps // kchunk)
 
 
 def measured_peaks():
@@ -303,13 +294,16 @@ def run_ours(args, rank, world, local_rank):
             host_in[nm] = t
         # the overlapped form (the default per-kernel form where it applies)
         ov = launch["mode"] == 0 and not launch.get("serial") and not launch.get("lb_tma")
+        # the clock sampler starts before the warm-up steps, so that the timed
+        # steps follow the warm-up without an idle gap (an idle GPU takes some
+        # microseconds to come back to full speed)
+        sampler = ClockSampler(local_rank) if rank == 0 else None
+        time.sleep(0.3 if sampler else 0)
         sim.step(args.warmup)
         stream.synchronize()
         _, n_w, sort_w = step_launches(0, 0, args.warmup, launch["mode"], overlapped=ov)
 
         # ---- device-timed region: K steps of graph replay -----------------
-        sampler = ClockSampler(local_rank) if rank == 0 else None
-        time.sleep(0.3 if sampler else 0)
         barrier()
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)

@@ -339,7 +339,8 @@ int lbmpcd_set_closure(lbmpcd* h, const float* theta, long long count, int src_o
 
 /* Launch form of the step (batching of the step launches; not in the paper).  mode 0
  * (default): per-kernel launches over all replicas, captured once into CUDA
- * graphs of 1, 2, 4, ..., 64 steps.  By default mode 0 runs the overlapped
+ * graphs of 1, 2, 3, ..., 64 steps (a call replays one graph per 64 steps
+ * and one for the rest).  By default mode 0 runs the overlapped
  * form: the LB update of step n + 1, which needs only the populations of
  * step n, runs beside the particle pass of step n (launched as a
  * programmatic dependent of the pass, taking its row tiles from a work

@@ -3,17 +3,17 @@
 // A handle owns R replicas.  Every replica's arrays are separate device
 // allocations described by a RepDev record; one device table of these records
 // plus a block map per kernel family lets a single launch of each kernel
-// cover all replicas.  lbmpcd_step runs the per-step sequence
-//     lb_pull -> particle_pass
-// (the LB launch of step n also builds the collision-cell table of step n - 1
-// and applies its MPCD -> LB imposition) in chunks of KCHUNK steps and, for what is left of a call, of the powers of
-// two below KCHUNK; each chunk length (a prep kernel plus the 3 kernels per
-// step) is captured once into a CUDA graph and replayed, so that calls of any
-// length run from graphs.  The particles are sorted by home cell whenever
-// KCHUNK steps have passed since the last sort, between chunks.  With the learned
-// closure (feedback = 2) each step adds one kernel: closure_in (sampling only)
-// or, with parameters loaded, closure_step (sampling, the network over the
-// patches of all replicas, imposition).
+// cover all replicas.  lbmpcd_step runs the steps in chunks of KCHUNK steps
+// and one chunk of what is left of a call; every chunk length (a prep kernel
+// plus the step kernels) is captured once into a CUDA graph and replayed.
+// The step kernels are, in the serial form, lb_pull (which also builds the
+// collision-cell table of step n - 1 and applies its MPCD -> LB imposition)
+// then particle_pass; in the overlapped form (the default where it applies)
+// the LB rows of step n + 1 run beside the particle pass of step n and a
+// third launch builds the table and applies the imposition of step n.  The
+// particles are sorted by home cell whenever KCHUNK steps have passed since
+// the last sort, between chunks.  With the learned closure (feedback = 2) the
+// network runs as one more kernel (closure_step) on its evaluation steps.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>
@@ -30,7 +30,7 @@ using namespace lbm;
 
 namespace {
 constexpr int KCHUNK = 64;   // longest captured chunk; steps between particle sorts
-constexpr int NGRAPH = 7;    // chunk graphs of 1, 2, 4, ..., KCHUNK steps
+constexpr int NGRAPH = KCHUNK;   // chunk graphs of 1, 2, 3, ..., KCHUNK steps
 thread_local std::string g_create_error;
 }  // namespace
 
@@ -81,7 +81,7 @@ struct lbmpcd {
   bool maps_dirty = true;
   std::vector<char> pending;                    // host mirror of d_pending
   std::vector<char> cells;                      // host mirror of d_cells
-  cudaGraphExec_t graphs[NGRAPH] = {};          // chunk of 2^i steps (no closure network)
+  cudaGraphExec_t graphs[NGRAPH] = {};          // chunk of i + 1 steps (no closure network)
   cudaGraphExec_t g_eval = nullptr;             // one step with the closure network
   cudaGraphExec_t g_period = nullptr;           // `period` steps, the network on every K-th from the first
   int period = 0;                               // K floor(KCHUNK / K) for K <= KCHUNK, else 0
@@ -123,8 +123,9 @@ static void free_list(std::vector<void*>& list) {
 
 // the captured chunks hold the kernels' arguments: drop them when those change
 static void drop_graphs(lbmpcd* h) {
-  for (auto* g : {&h->graphs[0], &h->graphs[1], &h->graphs[2], &h->graphs[3], &h->graphs[4], &h->graphs[5],
-                  &h->graphs[6], &h->g_eval, &h->g_period})
+  for (auto& g : h->graphs)
+    if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+  for (auto* g : {&h->g_eval, &h->g_period})
     if (*g) { cudaGraphExecDestroy(*g); *g = nullptr; }
   h->period = 0;
   h->graphs_ready = false;
@@ -678,7 +679,7 @@ static int capture_chunk(lbmpcd* h, int kcount, int cl_mode, cudaGraphExec_t* ou
 // cost ~3.5 us per step).
 static int capture_all(lbmpcd* h) {
   int rc = LBMPCD_OK;
-  for (int i = 0; i < NGRAPH && !rc; ++i) rc = capture_chunk(h, 1 << i, CL_NONE, &h->graphs[i]);
+  for (int i = 0; i < NGRAPH && !rc; ++i) rc = capture_chunk(h, i + 1, CL_NONE, &h->graphs[i]);
   if (!rc && h->has_cl && h->cl_params) {
     rc = capture_chunk(h, 1, CL_FIRST, &h->g_eval);
     const int K = closure_interval(h);
@@ -712,13 +713,9 @@ static long long to_next_eval(const lbmpcd* h, long long n) {
   return 1LL << 40;
 }
 
-static int chunk_len(int left) {
-  int kc = KCHUNK;
-  while (kc > left) kc >>= 1;
-  return kc;
-}
-
-static int log2i(int v) { int i = 0; while ((1 << i) < v) ++i; return i; }
+// a call is cut into chunks of KCHUNK steps and one of the rest (each
+// chunk one graph replay; the first LB launch of a chunk is not overlapped)
+static int chunk_len(int left) { return left < KCHUNK ? left : KCHUNK; }
 
 extern "C" int lbmpcd_step(lbmpcd* h, int nsteps) {
   if (!h) return LBMPCD_ERR_INVALID_ARG;
@@ -746,7 +743,7 @@ extern "C" int lbmpcd_step(lbmpcd* h, int nsteps) {
     } else {
       const long long gap = net ? to_next_eval(h, h->nstep) : (long long)left;
       kc = chunk_len((int)(gap < left ? gap : left));
-      CK(h, cudaGraphLaunch(h->graphs[log2i(kc)], h->stream));
+      CK(h, cudaGraphLaunch(h->graphs[kc - 1], h->stream));
     }
     left -= kc;
     h->nstep += kc;
