@@ -192,6 +192,42 @@ int lbmpcd_create(const lbmpcd_params* params, int n_replicas, void* cuda_stream
  * narrower than 2 coupling widths, cell index range too large), OOM, CUDA. */
 int lbmpcd_set_region(lbmpcd* h, int replica, const int lo[3], const int hi[3]);
 
+/* A piece of a slab region divided over x-slabs of one channel (Sec. 3.1.1:
+ * larger systems call for a parallel implementation; one handle per slab).
+ * lo / hi: the whole region in this handle's LB columns, which may extend
+ * beyond [0, nx) (the region is cut by the slab); the particles, the cells,
+ * the coupling buffers and the periodic wrap in x are those of the whole
+ * region, in its own cell coordinates.  [own_lo, own_hi) (inside [0, nx)):
+ * the LB columns this handle owns, the only ones whose inner-buffer nodes it
+ * imposes on (a8).  [keep_lo, keep_hi): the region cell columns (modulo the
+ * region's width Wx = (hi[0] - lo[0]) r, a range of at most Wx) whose
+ * particles this handle keeps: its own columns and the ghost columns around
+ * them.  The whole region is seeded exactly as lbmpcd_set_region seeds it
+ * (same particle ids, positions and velocities) and the particles outside
+ * the kept columns are removed, so a set of pieces holds the undivided run's
+ * particles.  Particles are pooled (lbmpcd_set_particles replaces them);
+ * their read-outs list the live particles with their ids (PART_ID).  Not for
+ * near-wall strips, the learned closure, density resampling, MPCD-AT or the
+ * Chapman-Enskog redraw, nor the persistent launch form (INVALID_ARG).
+ * Errors: as lbmpcd_set_region, plus INVALID_ARG for an empty owned range or
+ * kept range. */
+int lbmpcd_set_region_piece(lbmpcd* h, int replica, const int lo[3], const int hi[3], int own_lo, int own_hi,
+                            int keep_lo, int keep_hi);
+
+/* Replace the pooled particles of a replica (a region piece) by n given ones,
+ * host arrays: home cell (X, Y, Z) int32 [n][3] in region cells, offsets in
+ * [0, 1) and velocities binary64 [n][3] (the read-out layouts of PART_HOME,
+ * PART_POS and PART_VEL), ids int32 [n] (PART_ID); the state is taken as
+ * after the collision of the last step (a pending collision of the particles
+ * replaced is applied to them first, and the collision-cell table built).
+ * Used by the x-slab driver to hand particles between the pieces of a
+ * divided region (Sec. 3.1.1).  Errors: INVALID_ARG (bad replica, count,
+ * null array; a home cell outside the region or an offset outside [0, 1):
+ * that particle is dropped), STATE (not a pooled replica), CAPACITY (n above
+ * the pool), CUDA. */
+int lbmpcd_set_particles(lbmpcd* h, int replica, long long n, const int* home, const double* off, const double* vel,
+                         const int* pid);
+
 /* Advance every replica by nsteps coupled time steps (one step = LB
  * stream-collide, interpolation + Maxwellian redraw in the outer buffer, MPCD
  * streaming, inner-buffer sampling, random-shift binning, SRD collision,

@@ -63,6 +63,8 @@ def load_library(path: str = LIB_PATH):
     vp, ci, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
     L.lbmpcd_create.argtypes = [ctypes.POINTER(lbmpcd_params), ci, vp, ctypes.POINTER(vp)]
     L.lbmpcd_set_region.argtypes = [vp, ci, ctypes.POINTER(ci), ctypes.POINTER(ci)]
+    L.lbmpcd_set_region_piece.argtypes = [vp, ci, ctypes.POINTER(ci), ctypes.POINTER(ci), ci, ci, ci, ci]
+    L.lbmpcd_set_particles.argtypes = [vp, ci, ctypes.c_longlong, vp, vp, vp, vp]
     L.lbmpcd_step.argtypes = [vp, ci]
     L.lbmpcd_get_fields.argtypes = [vp, ci, ci, vp, sz, ci]
     L.lbmpcd_set_state.argtypes = [vp, ci, ci, vp, sz, ci]
@@ -104,7 +106,8 @@ EXPORTED = ["lbmpcd_create", "lbmpcd_set_region", "lbmpcd_step", "lbmpcd_step_pr
             "lbmpcd_net_get_params", "lbmpcd_net_set_params", "lbmpcd_net_forward", "lbmpcd_net_backward",
             "lbmpcd_net_train_step", "lbmpcd_net_destroy", "lbmpcd_net_forward_noalloc",
             "lbmpcd_set_closure", "lbmpcd_set_launch_mode", "lbmpcd_set_wait_limit", "lbmpcd_autotune",
-            "lbmpcd_population_bytes", "lbmpcd_get_columns", "lbmpcd_set_columns"]
+            "lbmpcd_population_bytes", "lbmpcd_get_columns", "lbmpcd_set_columns", "lbmpcd_set_region_piece",
+            "lbmpcd_set_particles"]
 
 
 def make_params(d: dict) -> lbmpcd_params:
@@ -154,6 +157,31 @@ def lbmpcd_set_region(h, replica: int, lo, hi):
     lo3 = (ctypes.c_int * 3)(*[int(v) for v in lo])
     hi3 = (ctypes.c_int * 3)(*[int(v) for v in hi])
     _check(h, load_library().lbmpcd_set_region(h, int(replica), lo3, hi3))
+
+
+def lbmpcd_set_region_piece(h, replica: int, lo, hi, own, keep):
+    """A piece of a region divided over x-slabs: lo / hi the whole region in
+    this handle's LB columns (may reach beyond the lattice), own = (own_lo,
+    own_hi) the owned LB columns, keep = (keep_lo, keep_hi) the region cell
+    columns (mod the region's width) whose particles the handle keeps."""
+    lo3 = (ctypes.c_int * 3)(*[int(v) for v in lo])
+    hi3 = (ctypes.c_int * 3)(*[int(v) for v in hi])
+    _check(h, load_library().lbmpcd_set_region_piece(h, int(replica), lo3, hi3, int(own[0]), int(own[1]),
+                                                     int(keep[0]), int(keep[1])))
+
+
+def lbmpcd_set_particles(h, replica: int, home, off, vel, pid):
+    """Replace the pooled particles of a region piece (home int32 [n][3],
+    offsets and velocities binary64 [n][3], ids int32 [n], host arrays)."""
+    home = np.ascontiguousarray(home, dtype=np.int32).reshape(-1, 3)
+    off = np.ascontiguousarray(off, dtype=np.float64).reshape(-1, 3)
+    vel = np.ascontiguousarray(vel, dtype=np.float64).reshape(-1, 3)
+    pid = np.ascontiguousarray(pid, dtype=np.int32).reshape(-1)
+    n = pid.size
+    if not (home.shape[0] == off.shape[0] == vel.shape[0] == n):
+        raise ValueError("home, off, vel and pid must describe the same particles")
+    _check(h, load_library().lbmpcd_set_particles(h, int(replica), n, home.ctypes.data, off.ctypes.data,
+                                                  vel.ctypes.data, pid.ctypes.data))
 
 
 def lbmpcd_step(h, nsteps: int):
@@ -358,6 +386,13 @@ class Lbmpcd:
     def set_region(self, replica: int, x0: int, x1: int):
         p = self.params[replica]
         lbmpcd_set_region(self._h, replica, (x0, 0, 0), (x1, p["ny"], p.get("nz", 1)))
+
+    def set_region_piece(self, replica: int, x0: int, x1: int, own, keep):
+        p = self.params[replica]
+        lbmpcd_set_region_piece(self._h, replica, (x0, 0, 0), (x1, p["ny"], p.get("nz", 1)), own, keep)
+
+    def set_particles(self, replica: int, home, off, vel, pid):
+        lbmpcd_set_particles(self._h, replica, home, off, vel, pid)
 
     def set_strip(self, replica: int, y1: int):
         """Near-wall strip (Sec. 3.3): all columns, LB rows [1, y1), coupling

@@ -186,10 +186,16 @@ struct RepDev {
   // near-wall strip (Sec. 3.3): region = all columns x LB rows [1, y1); outer
   // buffer rows Y >= yo (Hy when there is no strip), inner rows [yi_lo, yi_hi)
   int strip, y1, yo, yi_lo, yi_hi;
-  // density resampling: particles live in a pool of cap slots; pool[0] is
-  // its end, pool[1] an overflow flag, pool[2] the live count of the last
-  // sort or compaction; ltile scratch of the readout compaction
+  // pooled particles (density resampling, or a piece of a region divided
+  // over x-slabs): particles live in a pool of cap slots, a removed one
+  // marked HOME_DEAD; pool[0] is its end, pool[1] an overflow flag, pool[2]
+  // the live count of the last sort or compaction; ltile scratch of the
+  // readout compaction.  resample: density resampling (a3') itself.
+  int pooled;
   int resample;
+  // LB columns whose inner-buffer nodes this handle imposes on (a8): all of
+  // them, or for a piece of a divided region the columns the handle owns
+  int own_lo, own_hi;
   // collision rule: 0 SRD (Eq. 4), 1 MPCD-AT (Eq. 6)
   int collision;
   // outer-buffer redraw: 0 Maxwellian, 1 Chapman-Enskog
@@ -257,10 +263,10 @@ template <typename R> __device__ __forceinline__ R* u_of(const RepDev& rd, uint3
   return (R*)rd.u + (long long)(n & 1u) * 3 * rd.nnode;
 }
 
-// end of the particle slots in use: the pool end with density resampling,
-// the fixed count otherwise
+// end of the particle slots in use: the pool end for pooled particles, the
+// fixed count otherwise
 __device__ __forceinline__ uint32_t pool_end(const RepDev& rd) {
-  if (!rd.resample) return (uint32_t)rd.np;
+  if (!rd.pooled) return (uint32_t)rd.np;
   const uint32_t e = *(volatile const uint32_t*)rd.pool;
   return e < rd.cap ? e : rd.cap;
 }

@@ -118,6 +118,14 @@ cudaError_t launch_persistent(int q, int prec, int vec, const Launch& L, int kco
 cudaError_t launch_spawn(int dim, int prec, const Launch& L, const int2* bmap, int nwork, int k);
 cudaError_t launch_live_index(const RepDev& rd, cudaStream_t st);
 
+// pieces of a region divided over x-slabs: keep the particles of home cell
+// columns [lo, hi) mod Wx (the others removed); replace the pooled particles
+// by n given ones (device arrays: home [n][3] int32, offsets and velocities
+// [n][3] binary64, ids [n] int32; *bad set for a value out of range).
+cudaError_t launch_keep_columns(int dim, const RepDev& rd, int lo, int hi, cudaStream_t st);
+cudaError_t launch_pool_in(int dim, int prec, const RepDev& rd, long long n, const int* home, const double* off,
+                           const double* vel, const int* pid, int* bad, cudaStream_t st);
+
 // apply the pending collision of the last step to every particle of a replica.
 cudaError_t launch_flush(int dim, int prec, const RepDev* rd_dev, const RepDev& rd, const double* last_shift,
                          cudaStream_t st);

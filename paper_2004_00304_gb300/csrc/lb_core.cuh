@@ -200,27 +200,27 @@ __device__ __forceinline__ void lb_finish(const RepDev& rd, const StepInfo& st, 
 #pragma unroll
     for (int v = 0; v < V; ++v) {
       const long long b = inner_index(rd, x0 + v, y, z);
-      if (b >= 0) a8_node<Q, S>(rd, st.n - 1u, b, row + x0 + v, mr[v]);
+      if (b >= 0 && x0 + v >= rd.own_lo && x0 + v < rd.own_hi) a8_node<Q, S>(rd, st.n - 1u, b, row + x0 + v, mr[v]);
     }
   }
 }
 
-// LB node index of inner-buffer node b (the inverse of inner_index).
-__device__ __forceinline__ long long inner_node(const RepDev& rd, long long b) {
+// LB column, row and z of inner-buffer node b (the inverse of inner_index);
+// for a piece of a divided region the column may lie outside the lattice.
+__device__ __forceinline__ void inner_xyz(const RepDev& rd, long long b, int& x, int& y, int& z) {
   if (rd.strip) {
-    const int x = (int)(b % rd.nx);
+    x = (int)(b % rd.nx);
     const long long t = b / rd.nx;
-    const int z = (int)(t % rd.nz), row = (int)(t / rd.nz);
-    const int y = rd.y1 - 1 - rd.n_out - row;
-    return x + (long long)rd.nx * (y + (long long)rd.ny * z);
+    z = (int)(t % rd.nz);
+    y = rd.y1 - 1 - rd.n_out - (int)(t / rd.nz);
+    return;
   }
-  const int y = 1 + (int)(b % (rd.ny - 2));
+  y = 1 + (int)(b % (rd.ny - 2));
   const long long t = b / (rd.ny - 2);
-  const int z = (int)(t % rd.nz);
+  z = (int)(t % rd.nz);
   const long long t2 = t / rd.nz;
   const int col = (int)(t2 % rd.n_in), side = (int)(t2 / rd.n_in);
-  const int x = side ? rd.x1 - 1 - rd.n_out - col : rd.x0 + rd.n_out + col;
-  return x + (long long)rd.nx * (y + (long long)rd.ny * z);
+  x = side ? rd.x1 - 1 - rd.n_out - col : rd.x0 + rd.n_out + col;
 }
 
 // a8 of step m as a work item of its own (the overlapped form, where the LB
@@ -228,12 +228,16 @@ __device__ __forceinline__ long long inner_node(const RepDev& rd, long long b) {
 // node b takes frame m into the window and, with feedback, gets f_eq(rho_LB,
 // u_bar) over the post-collision populations the update of step m + 1 wrote,
 // rho_LB being that update's density of the node.  The same arithmetic as the
-// in-launch form.
+// in-launch form.  A piece of a divided region imposes on the columns it owns
+// only.
 template <int Q, typename S>
 __device__ __forceinline__ void a8_item(const RepDev& rd, uint32_t m, long long b) {
   using R = typename Store<S>::R;
   if (b >= rd.nbuf) return;
-  const long long node = inner_node(rd, b);
+  int x, y, z;
+  inner_xyz(rd, b, x, y, z);
+  if (x < rd.own_lo || x >= rd.own_hi) return;
+  const long long node = x + (long long)rd.nx * (y + (long long)rd.ny * z);
   a8_node<Q, S>(rd, m, b, (int)node, rho_of<R>(rd, m + 1u)[node]);
 }
 

@@ -360,7 +360,7 @@ static int build_maps(lbmpcd* h) {
     rows(lb256, 256);
     rows(rows_only, 128);
     if (!d.has_region) continue;
-    const long long nslot = d.resample ? (long long)d.cap : d.np;
+    const long long nslot = d.pooled ? (long long)d.cap : d.np;
     const long long npb = (nslot + PP_ITEM - 1) / PP_ITEM;
     for (long long b = 0; b < npb; ++b) pp.push_back(make_int2(r, (int)b));
     for (int b = 0; b < d.ntile; ++b) tt.push_back(make_int2(r, b));
@@ -389,7 +389,9 @@ static int build_maps(lbmpcd* h) {
   return LBMPCD_OK;
 }
 
-extern "C" int lbmpcd_set_region(lbmpcd* h, int replica, const int lo[3], const int hi[3]) {
+// piece = {own_lo, own_hi, keep_lo, keep_hi} for a piece of a region divided
+// over x-slabs (lbmpcd_set_region_piece), else null
+static int set_region_impl(lbmpcd* h, int replica, const int lo[3], const int hi[3], const int* piece) {
   if (!h) return LBMPCD_ERR_INVALID_ARG;
   if (replica < 0 || replica >= h->nrep || !lo || !hi) return fail(h, LBMPCD_ERR_INVALID_ARG, "bad replica or null bounds");
   if (h->nstep > 0) return fail(h, LBMPCD_ERR_STATE, "set_region must precede the first step");
@@ -410,8 +412,17 @@ extern "C" int lbmpcd_set_region(lbmpcd* h, int replica, const int lo[3], const 
       return fail(h, LBMPCD_ERR_INVALID_ARG, "near-wall strip not taller than its coupling buffer");
     if (p.feedback == 2 || p.resample_density)
       return fail(h, LBMPCD_ERR_INVALID_ARG, "a near-wall strip runs neither the learned closure nor density resampling");
-  } else if (x0 < 0 || x1 > p.nx || x1 - x0 < 2 * p.coupling_width || x1 <= x0) {
+  } else if ((!piece && (x0 < 0 || x1 > p.nx)) || x1 - x0 < 2 * p.coupling_width || x1 <= x0) {
     return fail(h, LBMPCD_ERR_INVALID_ARG, "region columns out of range or narrower than two coupling widths");
+  }
+  if (piece) {
+    if (strip) return fail(h, LBMPCD_ERR_INVALID_ARG, "a near-wall strip is not divided into pieces");
+    if (p.feedback == 2 || p.resample_density || p.redraw == 1 || p.collision == 1)
+      return fail(h, LBMPCD_ERR_INVALID_ARG,
+                  "a piece of a region runs neither the learned closure, density resampling, the Chapman-Enskog "
+                  "redraw nor MPCD-AT");
+    if (piece[0] < 0 || piece[1] > p.nx || piece[0] >= piece[1] || x0 < -(1 << 20) || x1 > (1 << 20))
+      return fail(h, LBMPCD_ERR_INVALID_ARG, "owned columns of a piece must be a non-empty range of the lattice");
   }
   d.x0 = x0; d.x1 = x1;
   d.strip = strip ? 1 : 0; d.y1 = y1;
@@ -442,6 +453,8 @@ extern "C" int lbmpcd_set_region(lbmpcd* h, int replica, const int lo[3], const 
   // density resampling: a pool with room for KCHUNK + 1 steps of new particles
   // at twice the mean rate (the pool is compacted at the start of every chunk)
   long long cap = d.np;
+  if (piece && (piece[2] >= piece[3] || piece[3] - piece[2] > d.Wx || piece[2] <= -d.Wx || piece[3] > 2 * d.Wx))
+    return fail(h, LBMPCD_ERR_INVALID_ARG, "kept cell columns of a piece must be a non-empty range of at most the region's width");
   if (p.resample_density) {
     const long long nouter = (long long)(d.xo_lo + (d.Wx - d.xo_hi)) * d.Hy * d.Wz;
     if ((double)d.nhome * SPAWN_MAX * p.ppc >= 4294967296.0)
@@ -474,10 +487,11 @@ extern "C" int lbmpcd_set_region(lbmpcd* h, int replica, const int lo[3], const 
     }
   }
   A(*(void**)&d.rank, cap * 4);
-  if (p.resample_density) {
+  if (p.resample_density || piece) {
     A(*(void**)&d.pool, 4 * 4);
     A(*(void**)&d.ltile, ((cap + SORT_TILE - 1) / SORT_TILE) * 4);
-    d.resample = 1;
+    d.pooled = 1;
+    d.resample = p.resample_density ? 1 : 0;
     d.cap = (uint32_t)cap;
     const uint32_t init[4] = {(uint32_t)d.np, 0u, (uint32_t)d.np, 0u};
     if (e == cudaSuccess) e = cudaMemcpy(d.pool, init, sizeof(init), cudaMemcpyHostToDevice);
@@ -512,6 +526,8 @@ extern "C" int lbmpcd_set_region(lbmpcd* h, int replica, const int lo[3], const 
                 std::string("allocating region arrays: ") + cudaGetErrorString(e));
   }
   d.has_region = 1;
+  d.own_lo = piece ? piece[0] : 0;
+  d.own_hi = piece ? piece[1] : p.nx;
   if (p.feedback == 2) {
     d.cl_on = 1;
     d.cl_npy = (d.Hy + 15) / 16;
@@ -523,8 +539,21 @@ extern "C" int lbmpcd_set_region(lbmpcd* h, int replica, const int lo[3], const 
   int rc = build_maps(h);
   if (rc) return rc;
   CK(h, launch_init_particles(h->dim, h->prec, h->d_reps + replica, d, h->stream));
+  // a piece keeps the particles of the whole region's seeding (same ids,
+  // positions and velocities as the undivided run) in its kept cell columns
+  if (piece) CK(h, launch_keep_columns(h->dim, d, piece[2], piece[3], h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
   return LBMPCD_OK;
+}
+
+extern "C" int lbmpcd_set_region(lbmpcd* h, int replica, const int lo[3], const int hi[3]) {
+  return set_region_impl(h, replica, lo, hi, nullptr);
+}
+
+extern "C" int lbmpcd_set_region_piece(lbmpcd* h, int replica, const int lo[3], const int hi[3], int own_lo,
+                                       int own_hi, int keep_lo, int keep_hi) {
+  const int pc[4] = {own_lo, own_hi, keep_lo, keep_hi};
+  return set_region_impl(h, replica, lo, hi, pc);
 }
 
 // One chunk of kcount steps (the sort, when due, runs before it: run_sort).
@@ -542,6 +571,14 @@ static bool persistent(const lbmpcd* h) { return h->mode == 1 && !h->has_cl; }
 // spawn runs before the pass) or the Chapman-Enskog redraw (the pass reads
 // the populations the LB update of step n + 1 overwrites), nor with the
 // TMA-staged LB rows.
+// some replica keeps its particles in a pool (density resampling or a region
+// piece): the particle pass is compiled with the pool handling
+static bool pooled_any(const lbmpcd* h) {
+  for (int r = 0; r < h->nrep; ++r)
+    if (h->rd[r].pooled) return true;
+  return false;
+}
+
 static bool overlapped(const lbmpcd* h) {
   return h->mode == 0 && !h->serial && !h->has_cl && h->nb_s == 0 && !h->ce && !h->lb_tma && h->nb_p > 0;
 }
@@ -568,7 +605,7 @@ static cudaError_t overlapped_chunk(lbmpcd* h, const Launch& L, int kcount, Arou
   for (int k = 0; k < kcount && e == cudaSuccess; ++k) {
     const bool last = k + 1 == kcount;
     e = around(2, [&] {
-      cudaError_t x = launch_particles(h->dim, h->prec, false, h->at, false, L, h->bm_p, h->nb_p, k, ov_blocks(h),
+      cudaError_t x = launch_particles(h->dim, h->prec, pooled_any(h), h->at, false, L, h->bm_p, h->nb_p, k, ov_blocks(h),
                                        k > 0 && (LBM_OV_PDL & 2));
       if (x == cudaSuccess && !last) x = launch_lb_rows(h->q, h->prec, h->lbvec, L, h->bm_rows, h->nb_rows, k + 1, h->d_ctr);
       return x;
@@ -621,7 +658,7 @@ static int run_chunk(lbmpcd* h, int kcount, int cl_mode) {
   for (int k = 0; k < kcount; ++k) {
     CK(h, launch_lb(h->q, h->prec, h->lbvec, h->lb_tma, L, h->bm_lb, h->nb_lb, k));
     if (h->nb_s) CK(h, launch_spawn(h->dim, h->prec, L, h->bm_s, h->nb_s, k));
-    CK(h, launch_particles(h->dim, h->prec, h->nb_s > 0, h->at, h->ce, L, h->bm_p, h->nb_p, k, 0));
+    CK(h, launch_particles(h->dim, h->prec, pooled_any(h), h->at, h->ce, L, h->bm_p, h->nb_p, k, 0));
     if (h->has_cl && h->cl_params) {
       const bool net = cl_mode == CL_FIRST ? k == 0
                      : cl_mode == CL_EVERY_K ? k % closure_interval(h) == 0
@@ -824,7 +861,7 @@ extern "C" int lbmpcd_step_profiled(lbmpcd* h, int nsteps, double* phase_ms, lon
     for (int k = 0; k < kc && !ov; ++k) {
       bracket(1, [&] { return launch_lb(h->q, h->prec, h->lbvec, h->lb_tma, L, h->bm_lb, h->nb_lb, k); });
       if (h->nb_s) bracket(2, [&] { return launch_spawn(h->dim, h->prec, L, h->bm_s, h->nb_s, k); });
-      if (h->nb_p) bracket(2, [&] { return launch_particles(h->dim, h->prec, h->nb_s > 0, h->at, h->ce, L, h->bm_p, h->nb_p, k, 0); });
+      if (h->nb_p) bracket(2, [&] { return launch_particles(h->dim, h->prec, pooled_any(h), h->at, h->ce, L, h->bm_p, h->nb_p, k, 0); });
       if (h->has_cl && h->cl_params && closure_eval(h, h->nstep + k))
         bracket(5, [&] { return launch_closure_step(h->prec, L, h->ptab, h->n_ptab, k, net_closure(h->net)); });
     }
@@ -865,7 +902,7 @@ static long long field_elems(const lbmpcd* h, int r, int field) {
   const bool pf = field == LBMPCD_PART_POS || field == LBMPCD_PART_VEL || field == LBMPCD_PART_HOME ||
                   field == LBMPCD_PART_CELL || field == LBMPCD_PART_ID || field == LBMPCD_CELL_LIST;
   const bool scalar = field == LBMPCD_PART_CELL || field == LBMPCD_PART_ID || field == LBMPCD_CELL_LIST;
-  if (pf && d.has_region && d.resample) {
+  if (pf && d.has_region && d.pooled) {
     const long long n = live_particles(const_cast<lbmpcd*>(h), r);
     if (n < 0) return -1;
     return scalar ? n : 3 * n;
@@ -915,6 +952,51 @@ int copy_columns(lbmpcd* h, int replica, int x, int ncols, void* host_or_dev, in
   return e == cudaSuccess ? LBMPCD_OK : cuda_fail(h, e, to_lattice ? "set_columns" : "get_columns");
 }
 }  // namespace
+
+static int flush_if_pending(lbmpcd* h, int r);
+
+extern "C" int lbmpcd_set_particles(lbmpcd* h, int replica, long long n, const int* home, const double* off,
+                                    const double* vel, const int* pid) {
+  if (!h) return LBMPCD_ERR_INVALID_ARG;
+  if (replica < 0 || replica >= h->nrep || n < 0 || (n > 0 && (!home || !off || !vel || !pid)))
+    return fail(h, LBMPCD_ERR_INVALID_ARG, "bad replica, count or null array");
+  RepDev& d = h->rd[replica];
+  if (!d.has_region || !d.pooled) return fail(h, LBMPCD_ERR_STATE, "set_particles needs pooled particles (a region piece)");
+  if (n > (long long)d.cap) return fail(h, LBMPCD_ERR_CAPACITY, "more particles than the pool holds");
+  if (h->maps_dirty) { int rc = build_maps(h); if (rc) return rc; }
+  int rc = flush_if_pending(h, replica);   // the table of the last step built, its accumulators cleared
+  if (rc) return rc;
+  // one device buffer: offsets and velocities (binary64) first, so that
+  // every array starts aligned to its element size whatever n is
+  void* tmp = nullptr;
+  const size_t bh = (size_t)n * 3 * 4, bo = (size_t)n * 3 * 8, bp = (size_t)n * 4;
+  if (n > 0) CK(h, cudaMalloc(&tmp, 2 * bo + bh + bp));
+  char* t = (char*)tmp;
+  double* t_off = (double*)t;
+  double* t_vel = (double*)(t + bo);
+  int* t_home = (int*)(t + 2 * bo);
+  int* t_pid = (int*)(t + 2 * bo + bh);
+  cudaError_t e = cudaSuccess;
+  if (n > 0) {
+    e = cudaMemcpyAsync(t_off, off, bo, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(t_vel, vel, bo, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(t_home, home, bh, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(t_pid, pid, bp, cudaMemcpyHostToDevice, h->stream);
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->d_flag, 0, sizeof(int), h->stream);
+  if (e == cudaSuccess && n > 0)
+    e = launch_pool_in(h->dim, h->prec, d, n, t_home, t_off, t_vel, t_pid, h->d_flag, h->stream);
+  const uint32_t pool[4] = {(uint32_t)n, 0u, (uint32_t)n, 0u};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d.pool, pool, sizeof(pool), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->d_sorted + replica, 0, sizeof(int), h->stream);
+  int bad = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, h->d_flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (tmp) cudaFree(tmp);
+  if (e != cudaSuccess) return cuda_fail(h, e, "set_particles");
+  if (bad) return fail(h, LBMPCD_ERR_INVALID_ARG, "particle home cell or offset out of range (removed)");
+  return LBMPCD_OK;
+}
 
 extern "C" int lbmpcd_get_columns(lbmpcd* h, int replica, int x, int ncols, void* dst, int dst_on_device) {
   return copy_columns(h, replica, x, ncols, dst, dst_on_device, false);
@@ -1072,8 +1154,9 @@ extern "C" int lbmpcd_set_state(lbmpcd* h, int replica, int field, const void* s
   const RepDev& d = h->rd[replica];
   const bool lbf = field == LBMPCD_POPS || field == LBMPCD_U;
   if (!lbf && !d.has_region) return fail(h, LBMPCD_ERR_STATE, "particles need a region first");
-  if (!lbf && d.resample)
-    return fail(h, LBMPCD_ERR_INVALID_ARG, "particle state cannot be loaded with density resampling");
+  if (!lbf && d.pooled)
+    return fail(h, LBMPCD_ERR_INVALID_ARG,
+                "particle state of pooled particles (density resampling, a region piece) is loaded by lbmpcd_set_particles");
   const long long n = field_elems(h, replica, field);
   const size_t esz = int_field(field) ? 4 : 8;
   if (bytes != (size_t)n * esz) return fail(h, LBMPCD_ERR_INVALID_ARG, "src size does not match the field");
@@ -1152,7 +1235,7 @@ extern "C" int lbmpcd_set_launch_mode(lbmpcd* h, int mode, int blocks_per_sm, in
     return fail(h, LBMPCD_ERR_INVALID_ARG, "mode must be 0 or 1, flags a set of LBMPCD_LAUNCH_*");
   if (mode == 1)
     for (int r = 0; r < h->nrep; ++r)
-      if (h->rd[r].cl_on || h->rd[r].resample || h->at || h->ce)
+      if (h->rd[r].cl_on || h->rd[r].pooled || h->at || h->ce)
         return fail(h, LBMPCD_ERR_INVALID_ARG,
                     "the persistent form runs neither the learned closure, the density resampling, MPCD-AT "
                     "nor the Chapman-Enskog redraw");
@@ -1176,7 +1259,7 @@ extern "C" int lbmpcd_autotune(lbmpcd* h, int steps, int* choice) {
   if (!h) return LBMPCD_ERR_INVALID_ARG;
   if (steps < 1) return fail(h, LBMPCD_ERR_INVALID_ARG, "steps must be >= 1");
   bool closure = false;
-  for (int r = 0; r < h->nrep; ++r) closure = closure || h->rd[r].cl_on || h->rd[r].resample || h->at || h->ce;
+  for (int r = 0; r < h->nrep; ++r) closure = closure || h->rd[r].cl_on || h->rd[r].pooled || h->at || h->ce;
   struct Cand { int mode, bps, vec, flags; };
   const int vdef = h->lbvec;
   std::vector<Cand> cands = {{0, 0, vdef, 0}};

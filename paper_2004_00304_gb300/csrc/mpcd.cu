@@ -127,7 +127,7 @@ __global__ void prep_steps(const RepDev* __restrict__ reps, int nrep, int dim, i
   }
   __syncthreads();
   for (int r = threadIdx.x; r < nrep; r += blockDim.x) {
-    if (d_sorted[r] && reps[r].resample) reps[r].pool[0] = reps[r].pool[2];   // the sort compacted the pool
+    if (d_sorted[r] && reps[r].pooled) reps[r].pool[0] = reps[r].pool[2];   // the sort compacted the pool
     d_sorted[r] = 0;
     const StepInfo& last = si[(kcount - 1) * nrep + r];
     for (int a = 0; a < 3; ++a) d_last_shift[3 * r + a] = last.shift[a];
@@ -646,9 +646,9 @@ __device__ __forceinline__ void particle_item(const RepDev& rd, const StepInfo& 
     fresh[p] = false;
     const uint32_t jl = act[p] ? j : last;
     uint32_t hp = ld_hint(hsrc + jl, l2_keep());
-    if (RS && rd.resample) {
+    if (RS && rd.pooled) {
       if (hp == HOME_DEAD) { act[p] = false; hp = 0u; }
-      fresh[p] = act[p] && (alt ? rd.pid_alt : rd.pid)[jl] == PID_FRESH;
+      fresh[p] = act[p] && rd.resample && (alt ? rd.pid_alt : rd.pid)[jl] == PID_FRESH;
     }
     HomePack<D>::unpack(hp, X[p], Y[p], Z[p]);
 #pragma unroll
@@ -1043,7 +1043,7 @@ __global__ void flush_collision(const RepDev* __restrict__ rdp, double s0, doubl
 
 cudaError_t launch_flush(int dim, int prec, const RepDev* rd_dev, const RepDev& rd, const double* ls,
                          cudaStream_t st) {
-  const int nb = (int)(((rd.resample ? (long long)rd.cap : rd.np) + 255) / 256);
+  const int nb = (int)(((rd.pooled ? (long long)rd.cap : rd.np) + 255) / 256);
   if (nb == 0) return cudaSuccess;
   if (dim == 2) {
     if (prec == P_FP64) flush_collision<2, double><<<nb, 256, 0, st>>>(rd_dev, ls[0], ls[1], ls[2]);
@@ -1108,8 +1108,8 @@ __global__ void part_out(RepDev rd, int field, double s0, double s1, double s2, 
   const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (j >= pool_end(rd)) return;
   const uint32_t hp = rd.home[j];
-  if (rd.resample && hp == HOME_DEAD) return;
-  const long long id = rd.resample ? (long long)rd.rank[j] : (long long)rd.pid[j];
+  if (rd.pooled && hp == HOME_DEAD) return;
+  const long long id = rd.pooled ? (long long)rd.rank[j] : (long long)rd.pid[j];
   int X, Y, Z;
   HomePack<D>::unpack(hp, X, Y, Z);
   if (field == F_POS || field == F_VEL) {
@@ -1126,7 +1126,7 @@ __global__ void part_out(RepDev rd, int field, double s0, double s1, double s2, 
     const R s[3] = {(R)s0, (R)s1, (R)s2};
     ((int*)out)[id] = (int)collision_cell<D, R>(rd, X, Y, Z, of, s);
   } else {
-    ((int*)out)[id] = rd.resample ? (int)rd.pid[j] : (int)id;
+    ((int*)out)[id] = rd.pooled ? (int)rd.pid[j] : (int)id;
   }
 }
 
@@ -1158,7 +1158,7 @@ __global__ void part_in(RepDev rd, int field, const void* in, int* bad) {
 
 cudaError_t launch_part_out(int dim, int prec, const RepDev& rd, int field, const double* ls, void* out,
                             cudaStream_t st) {
-  const int nb = (int)(((rd.resample ? (long long)rd.cap : rd.np) + 255) / 256);
+  const int nb = (int)(((rd.pooled ? (long long)rd.cap : rd.np) + 255) / 256);
   if (nb == 0) return cudaSuccess;
   if (dim == 2) {
     if (prec == P_FP64) part_out<2, double><<<nb, 256, 0, st>>>(rd, field, ls[0], ls[1], ls[2], out);
@@ -1184,6 +1184,72 @@ cudaError_t launch_part_in(int dim, int prec, const RepDev& rd, int field, const
   return cudaGetLastError();
 }
 
+// A piece of a region divided over x-slabs keeps the particles whose home
+// cell column X lies in [lo, hi) modulo the region's width Wx; the others
+// are removed (HOME_DEAD; the next sort compacts the pool).
+template <int D>
+__global__ void keep_columns(RepDev rd, int lo, int hi) {
+  const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (j >= pool_end(rd)) return;
+  const uint32_t hp = rd.home[j];
+  if (hp == HOME_DEAD) return;
+  int X, Y, Z;
+  HomePack<D>::unpack(hp, X, Y, Z);
+  const int dx = wrap(X - lo, rd.Wx);
+  if (dx >= hi - lo) rd.home[j] = HOME_DEAD;
+}
+
+cudaError_t launch_keep_columns(int dim, const RepDev& rd, int lo, int hi, cudaStream_t st) {
+  const int nb = (int)(((long long)rd.cap + 255) / 256);
+  if (nb == 0) return cudaSuccess;
+  if (dim == 2) keep_columns<2><<<nb, 256, 0, st>>>(rd, lo, hi);
+  else keep_columns<3><<<nb, 256, 0, st>>>(rd, lo, hi);
+  return cudaGetLastError();
+}
+
+// Pooled particles replaced by n given ones (home cells int32 [n][3],
+// offsets and velocities binary64 [n][3], ids int32 [n]) in slots 0 .. n-1,
+// all in the sorted order the caller gives; the pool ends at n.  A home cell
+// outside the region, or an offset outside [0, 1), sets *bad and the slot is
+// written as removed (HOME_DEAD).
+template <int D, typename R>
+__global__ void pool_in(RepDev rd, long long n, const int* __restrict__ home, const double* __restrict__ off,
+                        const double* __restrict__ vel, const int* __restrict__ pid, int* bad) {
+  const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const int X = home[3 * j], Y = home[3 * j + 1], Z = D == 3 ? home[3 * j + 2] : 0;
+  R o[3], v[3];
+  bool ok = X >= 0 && X < rd.Wx && Y >= 0 && Y < rd.Hy && Z >= 0 && Z < rd.Wz;
+  for (int a = 0; a < 3; ++a) {
+    o[a] = (R)off[3 * j + a];
+    v[a] = (R)vel[3 * j + a];
+    if (a < D && !(o[a] >= R(0) && o[a] < R(1))) ok = false;
+  }
+  if (!ok) {
+    rd.home[j] = HOME_DEAD;
+    atomicExch(bad, 1);
+    return;
+  }
+  rd.home[j] = HomePack<D>::pack(X, Y, Z);
+  rd.pid[j] = (uint32_t)pid[j];
+  PState<D, R>::st(rd.off, (uint32_t)j, o);
+  PState<D, R>::st(rd.vel, (uint32_t)j, v);
+}
+
+cudaError_t launch_pool_in(int dim, int prec, const RepDev& rd, long long n, const int* home, const double* off,
+                           const double* vel, const int* pid, int* bad, cudaStream_t st) {
+  const int nb = (int)((n + 255) / 256);
+  if (nb == 0) return cudaSuccess;
+  if (dim == 2) {
+    if (prec == P_FP64) pool_in<2, double><<<nb, 256, 0, st>>>(rd, n, home, off, vel, pid, bad);
+    else pool_in<2, float><<<nb, 256, 0, st>>>(rd, n, home, off, vel, pid, bad);
+  } else {
+    if (prec == P_FP64) pool_in<3, double><<<nb, 256, 0, st>>>(rd, n, home, off, vel, pid, bad);
+    else pool_in<3, float><<<nb, 256, 0, st>>>(rd, n, home, off, vel, pid, bad);
+  }
+  return cudaGetLastError();
+}
+
 // particle count, momentum and kinetic energy (binary64) into out[4..8].
 template <int D, typename R>
 __global__ void part_diag(RepDev rd, double* out) {
@@ -1191,7 +1257,7 @@ __global__ void part_diag(RepDev rd, double* out) {
   const long long end = pool_end(rd);
   for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < end;
        j += (long long)gridDim.x * blockDim.x) {
-    if (rd.resample && rd.home[j] == HOME_DEAD) continue;
+    if (rd.pooled && rd.home[j] == HOME_DEAD) continue;
     cnt += 1.0;
     R vv[3] = {R(0), R(0), R(0)};
     PState<D, R>::ld(rd.vel, (uint32_t)j, vv);
@@ -1210,7 +1276,7 @@ __global__ void part_diag(RepDev rd, double* out) {
 }
 
 cudaError_t launch_diag_particles(int dim, int prec, const RepDev& rd, double* out9, cudaStream_t st) {
-  const long long nslots = rd.resample ? (long long)rd.cap : rd.np;
+  const long long nslots = rd.pooled ? (long long)rd.cap : rd.np;
   if (nslots == 0) return cudaSuccess;
   long long g = (nslots + 255) / 256;
   const int nb = (int)(g < 1024 ? g : 1024);
@@ -1322,7 +1388,7 @@ __global__ void __launch_bounds__(1024) sort_scan_top(const RepDev* __restrict__
     carry += total;
     __syncthreads();
   }
-  if (threadIdx.x == 0 && rd.resample) rd.pool[2] = carry;   // live particles after the sort
+  if (threadIdx.x == 0 && rd.pooled) rd.pool[2] = carry;   // live particles after the sort
 }
 
 template <int D, typename R>

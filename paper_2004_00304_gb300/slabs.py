@@ -13,15 +13,30 @@ driver therefore takes `halo` steps, exchanges `halo` columns per cut in each
 direction (raw population storage, lbmpcd_get_columns / lbmpcd_set_columns),
 and repeats: one exchange every `halo` steps instead of one per step.
 
-The MPCD region is not divided: plan_slabs places every cut outside the
-region and its `margin` LB columns on either side (room for the buffers'
-interpolation stencils), so that the rank that holds the region runs the
-coupled step of the undivided channel on it, particles, cell table and
-coupling buffers included.  The cuts balance a per-column cost (LB bytes per
-column, plus the particles' and cells' bytes in the region's columns); since
-the region's slab cannot be cut, the step time of N ranks is at least that
-slab's share, so the strong-scaling gain is bounded by total cost / region
-cost (1.45 for the 2048 x 512 channel with its 256-column region).
+The MPCD region is either kept whole or divided.  Kept whole (the default),
+plan_slabs places every cut outside the region and its `margin` LB columns on
+either side (room for the buffers' interpolation stencils), so that the rank
+that holds the region runs the coupled step of the undivided channel on it,
+particles, cell table and coupling buffers included; the strong-scaling gain
+is then bounded by total cost / region cost (1.45 for the 2048 x 512 channel
+with its 256-column region).  Divided (split_region=True), cuts may fall
+inside the region, but not within `halo` columns of its coupling buffers
+(the imposition of a buffer node must not reach another slab's ghost
+columns): each slab holding region columns runs a region piece
+(lbmpcd_set_region_piece) that owns the region's cell columns inside the slab
+and keeps, besides its own particles, those of `ghost` LB columns on each
+side (modulo the region's periodic width).  Its cells, table and coupling
+are those of the whole region, the imposition is applied on its own columns
+only.  After every step each piece hands the particles it owned before the
+step (in their new state, after the collision of the step) to every piece,
+and each piece keeps those of its columns (lbmpcd_set_particles), ghosts
+refreshed from their owners: the owner computed the step from complete
+cells (a particle's collision cell is its home cell or the next one, and it
+moves less than a cell per step, so one step of ghost columns suffices) and
+from its own LB columns.  The hand-over is every step, not every `halo`
+steps, because a particle may cross the region's periodic wrap from one
+outer buffer into the other, where its next redraw needs the LB velocity of
+the far end, which only the piece holding that end has.
 
 Exchanges: DistExchanger (torch.distributed point-to-point, gloo on host
 tensors or NCCL on device tensors) between processes, one rank each;
@@ -54,7 +69,8 @@ def column_costs(params: dict, region=None) -> np.ndarray:
     return cost
 
 
-def plan_slabs(nx: int, nranks: int, cost=None, region=None, halo: int = 4, margin: int = 2) -> list:
+def plan_slabs(nx: int, nranks: int, cost=None, region=None, halo: int = 4, margin: int = 2,
+               split_region: bool = False, cw: int = 2) -> list:
     """Cut positions X_0 < X_1 < ... < X_nranks = X_0 + nx of contiguous slabs
     of the periodic channel (slab r = columns [X_r, X_r+1) mod nx) that
     minimise the largest slab cost (`cost` per column, default uniform),
@@ -69,7 +85,20 @@ def plan_slabs(nx: int, nranks: int, cost=None, region=None, halo: int = 4, marg
         raise ValueError("one cost per column")
     shift = 0
     items = []                                        # (first column, width, cost), from column `shift` on
-    if region is not None:
+    if region is not None and split_region:
+        # the region may be cut, but not within `halo` columns of its coupling
+        # buffers: [x0 - halo, x0 + cw + halo) and [x1 - cw - halo, x1 + halo)
+        # are each indivisible
+        x0, x1 = region
+        a0, a1, b0, b1 = x0 - halo, x0 + cw + halo, x1 - cw - halo, x1 + halo
+        if a0 < 0 or b1 > nx or a1 > b0:
+            raise ValueError("region, its buffers and their halos must lie inside the channel, the two ends apart")
+        shift = a0
+        items.append((a0, a1 - a0, float(c[a0:a1].sum())))
+        items += [(x, 1, float(c[x])) for x in range(a1, b0)]
+        items.append((b0, b1 - b0, float(c[b0:b1].sum())))
+        items += [(x, 1, float(c[x % nx])) for x in range(b1, a0 + nx)]
+    elif region is not None:
         blo, bhi = region[0] - margin, region[1] + margin
         if blo < 0 or bhi > nx or region[1] <= region[0]:
             raise ValueError("region and its margins must lie inside the channel")
@@ -132,7 +161,7 @@ class SlabChannel:
     None (set on the rank whose slab holds it)."""
 
     def __init__(self, params: dict, cuts, rank: int, region=None, halo: int = 4, make_engine=None,
-                 device: str = "cuda", stream=None):
+                 device: str = "cuda", stream=None, ghost=None):
         self.rank, self.world, self.halo = int(rank), len(cuts) - 1, int(halo)
         self.X0, self.X1 = int(cuts[rank]), int(cuts[rank + 1])
         self.w = self.X1 - self.X0
@@ -148,14 +177,80 @@ class SlabChannel:
         nx = int(params["nx"])
         rel = None if region is None else (region[0] - self.X0) % nx      # region start inside the slab
         self.has_region = rel is not None and rel + (region[1] - region[0]) <= self.w
+        self.piece = None
+        self._own_ids = None
         if self.has_region:
             self.sim.set_region(0, rel + self.halo, rel + (region[1] - region[0]) + self.halo)
+        elif region is not None:
+            self._set_piece(region, rel, ghost)
         self.since = 0                                 # steps since the ghost columns were exact
         self.device = device
         nb = self.sim.column_bytes(self.halo)
         import torch
         self._buf = {k: torch.empty(nb, dtype=torch.uint8, device=device)
                      for k in ("send_left", "send_right", "recv_left", "recv_right")}
+
+    def _set_piece(self, region, rel, ghost) -> None:
+        """This slab holds part of a region that plan_slabs(split_region=True)
+        divided: a region piece owning the region's columns inside the slab,
+        keeping also the particles of `ghost` LB columns (default: enough for
+        `halo` steps, 2 halo + 1 cells) on each side, modulo the region's
+        periodic width."""
+        x0g, x1g = region
+        wlb = x1g - x0g
+        if rel >= self.w + self.halo:                  # the region lies left of the slab's start
+            rel -= int(self.global_params["nx"])
+        lo = max(self.halo, rel + self.halo)
+        hi = min(self.halo + self.w, rel + self.halo + wlb)
+        if lo >= hi:
+            return                                     # no region column in this slab
+        r = int(self.global_params.get("refine", 1))
+        g = int(ghost) if ghost is not None else -(-(2 * self.halo + 1) // r)
+        c0, c1 = (lo - rel - self.halo) * r, (hi - rel - self.halo) * r     # owned region cell columns
+        wx = wlb * r
+        k0, k1 = c0 - g * r, c1 + g * r
+        if k1 - k0 > wx:
+            k0, k1 = 0, wx
+        self.sim.set_region_piece(0, rel + self.halo, rel + self.halo + wlb, (lo, hi), (k0, k1))
+        self.piece = dict(own=(c0, c1), keep=(k0, k1), wx=wx)
+        home = self.sim.get("PART_HOME").reshape(-1, 3)
+        pid = self.sim.get("PART_ID").reshape(-1)
+        self._own_ids = pid[(home[:, 0] >= c0) & (home[:, 0] < c1)]   # owned before the first step
+
+    def particles_out(self):
+        """The particles this piece owned at the last hand-over (home cell
+        column in its own columns then), in their current state after the
+        collision of the last step, as (home [n][3], offsets [n][3],
+        velocities [n][3], ids [n]).  The piece that owned a particle at the
+        last hand-over computed its step from complete cells and from its own
+        LB columns, also when the particle crossed into another piece's
+        columns or, through the region's periodic wrap, into the far outer
+        buffer during the step."""
+        if self.piece is None:
+            return None
+        home = self.sim.get("PART_HOME").reshape(-1, 3)
+        off = self.sim.get("PART_POS").reshape(-1, 3)
+        vel = self.sim.get("PART_VEL").reshape(-1, 3)
+        pid = self.sim.get("PART_ID").reshape(-1)
+        m = np.isin(pid, self._own_ids)
+        return home[m], off[m], vel[m], pid[m]
+
+    def particles_in(self, owned) -> None:
+        """Replace this piece's particles by those of `owned` (the owned sets
+        of every piece, concatenated) in its kept columns, ordered by home
+        cell; the ones in its own columns are its owned set until the next
+        hand-over."""
+        if self.piece is None:
+            return
+        home, off, vel, pid = owned
+        k0, k1 = self.piece["keep"]
+        c0, c1 = self.piece["own"]
+        wx = self.piece["wx"]
+        m = ((home[:, 0] - k0) % wx) < (k1 - k0)
+        key = home[m, 0] + wx * (home[m, 1] + 1048576 * home[m, 2])
+        o = np.argsort(key, kind="stable")
+        self.sim.set_particles(0, home[m][o], off[m][o], vel[m][o], pid[m][o])
+        self._own_ids = pid[(home[:, 0] >= c0) & (home[:, 0] < c1)]
 
     def global_columns(self) -> np.ndarray:
         """Global columns of the local lattice, ghosts included (mod nx)."""
@@ -223,6 +318,14 @@ class DistExchanger:
         self.rank = dist.get_rank(group)
         self.world = dist.get_world_size(group)
 
+    def gather(self, obj):
+        """Every rank's `obj` (host data), in rank order."""
+        if self.world == 1:
+            return [obj]
+        out = [None] * self.world
+        self.dist.all_gather_object(out, obj, group=self.group)
+        return out
+
     def exchange(self, send_left, send_right, recv_left, recv_right):
         if self.world == 1:
             recv_left.copy_(send_right)
@@ -241,32 +344,57 @@ class DistExchanger:
         return recv_left, recv_right
 
 
+def _concat(parts):
+    """The owned particle sets of all pieces (None for slabs without one) as
+    one set."""
+    parts = [p for p in parts if p is not None]
+    if not parts:
+        return None
+    return tuple(np.concatenate([p[i] for p in parts]) for i in range(4))
+
+
 def run_dist(slab: SlabChannel, steps: int, ex: DistExchanger) -> None:
     """`steps` steps of this rank's slab, exchanging with the other ranks (all
-    ranks call it with the same `steps`)."""
+    ranks call it with the same `steps`): the LB ghost columns every `halo`
+    steps; with a divided region also the particles after every step (one
+    all-gather of the pieces' owned particles, each piece keeping those of
+    its kept columns).  A particle may cross the region's periodic wrap from
+    one outer buffer into the other, where the next step redraws it from the
+    LB columns of the far end, which only the piece there holds: so the
+    particles change hands every step."""
+    pieces = ex.gather(slab.piece is not None)
+    divided = any(pieces)
     while steps > 0:
-        k = min(steps, slab.halo - slab.since)
-        if k == 0:
+        if slab.since == slab.halo:
             sl, sr = slab.halo_out()
             rl, rr = ex.exchange(sl, sr, slab._buf["recv_left"], slab._buf["recv_right"])
             slab.halo_in(rl, rr)
-            continue
+        k = 1 if divided else min(steps, slab.halo - slab.since)
         slab.advance(k)
         steps -= k
+        if divided:
+            every = ex.gather(slab.particles_out())
+            if slab.piece is not None:
+                slab.particles_in(_concat(every))
 
 
 def run_local(slabs, steps: int) -> None:
     """`steps` steps of all slabs of one channel held by this process (rank
-    order), exchanging in memory: the ranks of one channel emulated in lock
-    step, with every copy ordered by the host."""
+    order), exchanging in memory as run_dist does: the ranks of one channel
+    emulated in lock step, with every copy ordered by the host."""
     W = len(slabs)
+    divided = any(s.piece is not None for s in slabs)
     while steps > 0:
-        k = min(steps, slabs[0].halo - slabs[0].since)
-        if k == 0:
+        if slabs[0].since == slabs[0].halo:
             outs = [s.halo_out() for s in slabs]          # each slab's own send buffers
             for r, s in enumerate(slabs):
                 s.halo_in(outs[(r - 1) % W][1], outs[(r + 1) % W][0])
-            continue
+        k = 1 if divided else min(steps, slabs[0].halo - slabs[0].since)
         for s in slabs:
             s.advance(k)
         steps -= k
+        if divided:
+            owned = _concat([s.particles_out() for s in slabs])
+            for s in slabs:
+                if s.piece is not None:
+                    s.particles_in(owned)

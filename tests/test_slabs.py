@@ -157,3 +157,136 @@ def test_gloo_ranks_match_the_undivided_oracle(tmp_path, world, halo, steps):
     holders = [r for r in range(world) if (tmp_path / f"vel{r}.npy").exists()]
     assert len(holders) == 1
     assert np.array_equal(np.load(tmp_path / f"vel{holders[0]}.npy"), ref.get("PART_VEL"))
+
+
+class PieceEngine:
+    """A stand-in engine for the particle hand-over of a divided region (test
+    side, no method physics): the whole region is seeded with one particle
+    per cell, id = cell index, and every step moves every particle one cell
+    to the right (periodic in the region), so that particles cross the cuts
+    and change owner; the LB columns are zeros."""
+
+    def __init__(self, params):
+        self.p = dict(params)
+        self.q, self.nz, self.ny = int(self.p["lattice"]), int(self.p.get("nz", 1)), int(self.p["ny"])
+        self.r = int(self.p.get("refine", 1))
+
+    def set_region_piece(self, replica, x0, x1, own, keep):
+        self.wx, self.hy = (x1 - x0) * self.r, (self.ny - 2) * self.r
+        self.own, self.keep = own, keep
+        home, off, vel, pid = seeded(self.wx, self.hy)
+        m = ((home[:, 0] - keep[0]) % self.wx) < (keep[1] - keep[0])
+        self.set_particles(0, home[m], off[m], vel[m], pid[m])
+
+    def set_particles(self, replica, home, off, vel, pid):
+        self.home, self.off, self.vel, self.pid = (np.array(a) for a in (home, off, vel, pid))
+
+    def get(self, field, replica=0, out=None):
+        return {"PART_HOME": self.home, "PART_POS": self.off, "PART_VEL": self.vel, "PART_ID": self.pid}[field]
+
+    def step(self, k):
+        self.home = self.home.copy()
+        self.home[:, 0] = (self.home[:, 0] + k) % self.wx
+
+    def column_bytes(self, n):
+        return self.q * self.nz * self.ny * n * 8
+
+    def get_columns(self, x, n, out):
+        return out
+
+    def set_columns(self, x, n, src):
+        pass
+
+    def close(self):
+        pass
+
+
+def seeded(wx, hy):
+    X, Y = np.meshgrid(np.arange(wx), np.arange(hy))
+    home = np.stack([X.ravel(), Y.ravel(), np.zeros(X.size, int)], 1).astype(np.int32)
+    pid = (home[:, 0] + wx * home[:, 1]).astype(np.int32)
+    off = np.full((pid.size, 3), 0.25)
+    vel = np.stack([pid * 1e-3, -pid * 1e-3, np.zeros(pid.size)], 1)
+    return home, off, vel, pid
+
+
+def _divided(world, halo):
+    cfg = inputs.small_2d(feedback=1)
+    p, region = cfg["params"], cfg["region"]
+    cuts = S.plan_slabs(p["nx"], world, S.column_costs(p, region), region, halo=halo, split_region=True,
+                        cw=p["coupling_width"])
+    return p, region, cuts
+
+
+def test_plan_may_cut_the_region_away_from_its_buffers():
+    p, region, cuts = _divided(3, 2)
+    x0, x1 = region
+    assert len(cuts) == 4 and cuts[-1] - cuts[0] == p["nx"]
+    inner = [c % p["nx"] for c in cuts[1:-1]]
+    assert any(x0 < c < x1 for c in inner)                 # the region is divided
+    for c in cuts[:-1]:                                   # no cut within halo of a coupling buffer
+        c %= p["nx"]
+        assert not (x0 - 2 < c < x0 + 2 + 2) and not (x1 - 2 - 2 < c < x1 + 2)
+    with pytest.raises(ValueError):
+        S.plan_slabs(p["nx"], 2, region=(1, 30), halo=4, split_region=True)
+
+
+@pytest.mark.parametrize("world,halo,steps", [(2, 2, 9), (3, 2, 11), (3, 4, 13)])
+def test_pieces_hand_particles_over(world, halo, steps):
+    """Slabs emulated in one process with a divided region: after steps that
+    cross several LB exchanges, the pieces' owned particles are exactly the
+    whole region's particles, each owned once, and every piece holds exactly
+    the particles of its kept columns (modulo the region's width)."""
+    p, region, cuts = _divided(world, halo)
+    sl = [S.SlabChannel(p, cuts, r, region=region, halo=halo, make_engine=PieceEngine, device="cpu")
+          for r in range(world)]
+    pieces = [s for s in sl if s.piece is not None]
+    assert len(pieces) >= 2
+    S.run_local(sl, steps)
+    wx = pieces[0].piece["wx"]
+    home, off, vel, pid = seeded(wx, (p["ny"] - 2) * p["refine"])
+    home = home.copy()
+    home[:, 0] = (home[:, 0] + steps) % wx
+    got = S._concat([s.particles_out() for s in sl])
+    o = np.argsort(got[3])
+    assert np.array_equal(got[3][o], np.sort(pid))
+    assert np.array_equal(got[0][o], home[np.argsort(pid)])
+    assert np.array_equal(got[2][o], vel[np.argsort(pid)])
+    for s in pieces:                                      # handed over after every step: the kept columns
+        k0, k1 = s.piece["keep"]
+        want = np.sort(pid[((home[:, 0] - k0) % wx) < (k1 - k0)])
+        assert np.array_equal(np.sort(s.sim.pid), want)
+
+
+def _piece_rank_main(rank, world, port, p, region, cuts, halo, steps, out_dir):
+    import torch.distributed as dist
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    try:
+        sl = S.SlabChannel(p, cuts, rank, region=region, halo=halo, make_engine=PieceEngine, device="cpu")
+        S.run_dist(sl, steps, S.DistExchanger())
+        own = sl.particles_out()
+        if own is not None:
+            np.save(os.path.join(out_dir, f"home{rank}.npy"), own[0])
+            np.save(os.path.join(out_dir, f"pid{rank}.npy"), own[3])
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+def test_gloo_pieces_hand_particles_over(tmp_path):
+    """The same hand-over between two gloo ranks (one all-gather of the owned
+    particles per exchange): their owned sets partition the region's
+    particles, at the positions the undivided motion gives."""
+    import torch.multiprocessing as mp
+    world, halo, steps = 2, 2, 9
+    p, region, cuts = _divided(world, halo)
+    mp.spawn(_piece_rank_main, args=(world, _free_port(), p, region, cuts, halo, steps, str(tmp_path)),
+             nprocs=world, join=True)
+    wx = (region[1] - region[0]) * p["refine"]
+    home, off, vel, pid = seeded(wx, (p["ny"] - 2) * p["refine"])
+    home[:, 0] = (home[:, 0] + steps) % wx
+    pids = np.concatenate([np.load(tmp_path / f"pid{r}.npy") for r in range(world)])
+    homes = np.concatenate([np.load(tmp_path / f"home{r}.npy") for r in range(world)])
+    o = np.argsort(pids)
+    assert np.array_equal(pids[o], np.sort(pid))
+    assert np.array_equal(homes[o], home[np.argsort(pid)])
