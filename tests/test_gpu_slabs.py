@@ -71,8 +71,8 @@ def _owned_particles(sl):
     return home[o], off[o], vel[o], pid[o]
 
 
-@pytest.mark.parametrize("world,halo,steps", [(2, 2, 13), (3, 2, 11), (3, 4, 19)])
-def test_fp64_divided_region_matches_the_undivided_channel(lb, world, halo, steps):
+@pytest.mark.parametrize("dim,world,halo,steps", [(2, 2, 2, 13), (2, 3, 2, 11), (2, 3, 4, 19), (3, 2, 2, 7)])
+def test_fp64_divided_region_matches_the_undivided_channel(lb, dim, world, halo, steps):
     """The MPCD region cut between slabs: each slab's handle holds a region
     piece (its own cell columns plus ghost columns, particles handed over at
     every halo exchange, the imposition on its own columns only).  Against
@@ -82,8 +82,9 @@ def test_fp64_divided_region_matches_the_undivided_channel(lb, world, halo, step
     of the pieces' own particles, by id) within 1e-12; each particle owned
     by exactly one piece."""
     from paper_2004_00304_gb300 import slabs as S
-    cfg = inputs.small_2d(feedback=1)
+    cfg = inputs.small_2d(feedback=1) if dim == 2 else inputs.small_3d(feedback=1)
     p, region = cfg["params"], cfg["region"]
+    q, nz = p["lattice"], p.get("nz", 1)
     P0 = _initial_pops(p)
     cuts = S.plan_slabs(p["nx"], world, S.column_costs(p, region), region, halo=halo, split_region=True,
                         cw=p["coupling_width"])
@@ -98,7 +99,7 @@ def test_fp64_divided_region_matches_the_undivided_channel(lb, world, halo, step
     assert npiece == world or (world > 1 and npiece >= 2), cuts
     S.run_local(sl, steps)
     nx = p["nx"]
-    R = one.get("POPS").reshape(9, 1, p["ny"], nx)
+    R = one.get("POPS").reshape(q, nz, p["ny"], nx)
     scale = np.max(np.abs(R))
     for r, s in enumerate(sl):
         got = s.interior("POPS")
@@ -118,7 +119,7 @@ def test_fp64_divided_region_matches_the_undivided_channel(lb, world, halo, step
     r_, wx = p["refine"], (region[1] - region[0]) * p["refine"]
     n_out = (p["coupling_width"] + 1) // 2
     inner = (home[:, 0] >= n_out * r_) & (home[:, 0] < wx - n_out * r_)
-    assert inner.sum() > 0.8 * n
+    assert inner.sum() > 0.5 * n
     assert np.max(np.abs(vel[inner] - v1[inner])) <= 1e-12 * max(1.0, np.max(np.abs(v1)))
     one.close()
     for s in sl:
