@@ -88,6 +88,8 @@ struct lbmpcd {
   bool graphs_ready = false;
   int* d_sorted = nullptr;                      // per replica: the sort ran since the last chunk
   long long last_sort = 0;                      // step count at the last sort (the seeded state is sorted)
+  void* stage = nullptr;                        // device staging buffer of the host-side set / get calls
+  size_t stage_cap = 0;
   std::string err;
 };
 
@@ -97,6 +99,30 @@ static int fail(lbmpcd* h, int code, const std::string& msg) {
 }
 static int cuda_fail(lbmpcd* h, cudaError_t e, const char* where) {
   return fail(h, LBMPCD_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+// The device buffer through which host arrays are set and read, kept by the
+// handle and grown to the largest request: an allocation and a release per
+// call cost milliseconds for the particle fields, and every cudaFree waits
+// for the whole device.  Only the handle's stream uses it; the stream is
+// synchronised first, so that no copy of an earlier call that returned early
+// on an error is still in flight.
+static cudaError_t staging(lbmpcd* h, size_t bytes, void** out) {
+  cudaError_t s = cudaStreamSynchronize(h->stream);
+  if (s != cudaSuccess) return s;
+  if (bytes > h->stage_cap) {
+    if (h->stage) {
+      cudaError_t e = cudaFree(h->stage);
+      h->stage = nullptr;
+      h->stage_cap = 0;
+      if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = cudaMalloc(&h->stage, bytes);
+    if (e != cudaSuccess) { h->stage = nullptr; return e; }
+    h->stage_cap = bytes;
+  }
+  *out = h->stage;
+  return cudaSuccess;
 }
 #define CK(h, call)                                            \
   do {                                                         \
@@ -138,6 +164,7 @@ extern "C" void lbmpcd_destroy(lbmpcd* h) {
   if (h->net) lbmpcd_net_destroy(h->net);
   for (auto& l : h->rep_allocs) free_list(l);
   free_list(h->allocs);
+  if (h->stage) cudaFree(h->stage);
   delete h;
 }
 
@@ -970,7 +997,7 @@ extern "C" int lbmpcd_set_particles(lbmpcd* h, int replica, long long n, const i
   // every array starts aligned to its element size whatever n is
   void* tmp = nullptr;
   const size_t bh = (size_t)n * 3 * 4, bo = (size_t)n * 3 * 8, bp = (size_t)n * 4;
-  if (n > 0) CK(h, cudaMalloc(&tmp, 2 * bo + bh + bp));
+  if (n > 0) CK(h, staging(h, 2 * bo + bh + bp, &tmp));
   char* t = (char*)tmp;
   double* t_off = (double*)t;
   double* t_vel = (double*)(t + bo);
@@ -992,7 +1019,6 @@ extern "C" int lbmpcd_set_particles(lbmpcd* h, int replica, long long n, const i
   int bad = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, h->d_flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-  if (tmp) cudaFree(tmp);
   if (e != cudaSuccess) return cuda_fail(h, e, "set_particles");
   if (bad) return fail(h, LBMPCD_ERR_INVALID_ARG, "particle home cell or offset out of range (removed)");
   return LBMPCD_OK;
@@ -1070,7 +1096,7 @@ extern "C" int lbmpcd_get_fields(lbmpcd* h, int replica, int field, void* dst, s
   void* buf = dst;
   void* tmp = nullptr;
   if (!dst_on_device && n > 0) {
-    CK(h, cudaMalloc(&tmp, bytes));
+    CK(h, staging(h, bytes, &tmp));
     buf = tmp;
   }
   int rc = LBMPCD_OK;
@@ -1135,11 +1161,9 @@ extern "C" int lbmpcd_get_fields(lbmpcd* h, int replica, int field, void* dst, s
     e = cudaMemcpyAsync(&kerr, h->d_flag + 8, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
   if (rc == LBMPCD_OK && e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (rc == LBMPCD_OK && e == cudaSuccess && kerr) {
-    if (tmp) cudaFree(tmp);
     cudaMemset(h->d_flag + 8, 0, sizeof(int));
     return fail(h, LBMPCD_ERR_TIMEOUT, "a bounded wait in the TMA-staged LB kernel gave up; results invalid");
   }
-  if (tmp) cudaFree(tmp);
   if (rc) return rc;
   if (e != cudaSuccess) return cuda_fail(h, e, "get_fields");
   return LBMPCD_OK;
@@ -1165,9 +1189,9 @@ extern "C" int lbmpcd_set_state(lbmpcd* h, int replica, int field, const void* s
   const void* buf = src;
   void* tmp = nullptr;
   if (!src_on_device) {
-    CK(h, cudaMalloc(&tmp, bytes));
+    CK(h, staging(h, bytes, &tmp));
     cudaError_t e = cudaMemcpyAsync(tmp, src, bytes, cudaMemcpyHostToDevice, h->stream);
-    if (e != cudaSuccess) { cudaFree(tmp); return cuda_fail(h, e, "set_state copy"); }
+    if (e != cudaSuccess) return cuda_fail(h, e, "set_state copy");
     buf = tmp;
   }
   cudaError_t e = cudaSuccess;
@@ -1183,7 +1207,6 @@ extern "C" int lbmpcd_set_state(lbmpcd* h, int replica, int field, const void* s
   if (e == cudaSuccess && !lbf)
     e = cudaMemcpyAsync(&bad, h->d_flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-  if (tmp) cudaFree(tmp);
   if (e != cudaSuccess) return cuda_fail(h, e, "set_state");
   if (bad) return fail(h, LBMPCD_ERR_INVALID_ARG, "particle positions out of range (state partly written)");
   return LBMPCD_OK;
