@@ -81,14 +81,12 @@ __device__ __forceinline__ void normal_pair(uint32_t a, uint32_t b, float& z0, f
   z1 = rad * s;
 }
 
-// L2 eviction priorities (createpolicy + L2::cache_hint): the particle state,
-// read and written back every step, is kept (evict_last); the LB populations,
-// which do not stay in L2 until their next use anyway, go first.
-__device__ __forceinline__ uint64_t l2_keep() {
-  uint64_t p;
-  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
+// L2 eviction priority for data streamed once per step (createpolicy +
+// L2::cache_hint, evict_first): the particle state, and the LB populations
+// as they are read.  The populations an LB update writes keep the normal
+// priority, so that they are still in L2 when the next update reads them
+// (the particle state, which would crowd them out, goes first), and so do
+// the cell table and sums, which every particle touches.
 __device__ __forceinline__ uint64_t l2_stream() {
   uint64_t p;
   asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
@@ -116,11 +114,6 @@ __device__ __forceinline__ float4 ld_hint(const float4* a, uint64_t pol) {
   asm volatile("ld.global.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
                : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(a), "l"(pol));
   return v;
-}
-__device__ __forceinline__ void st_hint(float4* a, float4 v, uint64_t pol) {
-  asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(a), "f"(v.x), "f"(v.y),
-               "f"(v.z), "f"(v.w), "l"(pol)
-               : "memory");
 }
 
 // ---------------------------------------------------------------------------

@@ -22,7 +22,7 @@ template <> struct Row<float, 4> {
     o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
   }
   __device__ static void st(float* p, const float* v, float, uint32_t) {
-    st_hint(reinterpret_cast<float4*>(p), make_float4(v[0], v[1], v[2], v[3]), l2_stream());
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
   }
 };
 template <> struct Row<float, 2> {

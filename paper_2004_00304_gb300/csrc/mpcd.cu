@@ -62,13 +62,13 @@ template <typename R> struct PState<2, R> {
   using T2 = typename Pair<R>::T;
   __device__ static void ld(void* const* base, uint32_t j, R* x) {
     T2 t;
-    if constexpr (sizeof(R) == 4) t = ld_hint((const float2*)base[0] + j, l2_keep());
+    if constexpr (sizeof(R) == 4) t = ld_hint((const float2*)base[0] + j, l2_stream());
     else t = ((const T2*)base[0])[j];
     x[0] = t.x; x[1] = t.y;
   }
   __device__ static void st(void* const* base, uint32_t j, const R* x) {
     T2 t; t.x = x[0]; t.y = x[1];
-    if constexpr (sizeof(R) == 4) st_hint((float2*)base[0] + j, t, l2_keep());
+    if constexpr (sizeof(R) == 4) st_hint((float2*)base[0] + j, t, l2_stream());
     else ((T2*)base[0])[j] = t;
   }
 };
@@ -486,7 +486,7 @@ __device__ __forceinline__ uint32_t move_particle(const RepDev& rd, const StepIn
   }
   // a5: binning under this step's shift
   const uint32_t cid = collision_cell<D, R>(rd, X, Y, Z, o, Cst<R>::shift(st));
-  st_hint(rd.home + j, HomePack<D>::pack(X, Y, Z), l2_keep());
+  st_hint(rd.home + j, HomePack<D>::pack(X, Y, Z), l2_stream());
   PState<D, R>::st(rd.off, j, o);
   if (AT) {
     // a7 (MPCD-AT), first half: v_ran from Philox(id, n, replica, TAG_AT)
@@ -645,7 +645,7 @@ __device__ __forceinline__ void particle_item(const RepDev& rd, const StepInfo& 
     act[p] = j < np32;
     fresh[p] = false;
     const uint32_t jl = act[p] ? j : last;
-    uint32_t hp = ld_hint(hsrc + jl, l2_keep());
+    uint32_t hp = ld_hint(hsrc + jl, l2_stream());
     if (RS && rd.pooled) {
       if (hp == HOME_DEAD) { act[p] = false; hp = 0u; }
       fresh[p] = act[p] && rd.resample && (alt ? rd.pid_alt : rd.pid)[jl] == PID_FRESH;
