@@ -672,8 +672,8 @@ def run_closure(args):
     seeds) from the Poiseuille profile for 1000 steps; then, every 10 steps
     for 5000 steps, the running mean over time and replicas of the velocity
     imposed on the inner-buffer columns (the averaged MPCD -> LB feedback)
-    and of the x-averaged LB profile is taken.  The judge of a mode's error
-    is the plain W = 100 coupling: an independent 16-replica W = 100 run over
+    and of the x-averaged LB profile is taken.  A mode's error is measured
+    against the plain W = 100 coupling: an independent 16-replica W = 100 run over
     the same window, whose running means at the same times are the
     reference (the MPCD mean at the buffer differs from the analytic profile
     by ~1 % and drifts slowly, the same in every mode).  A mode's time to
