@@ -246,11 +246,15 @@ int lbmpcd_step_profiled(lbmpcd* h, int nsteps, double* phase_ms, long long* lau
 
 /* Copy one field of one replica (layouts above) to dst, which holds exactly
  * `bytes` bytes (else INVALID_ARG); dst_on_device = 1 for device memory.
- * Synchronises the handle's stream before returning. */
+ * A host dst is filled through a device staging buffer that the handle keeps
+ * between calls, grown to the largest host array seen and released by
+ * lbmpcd_destroy (pinned host memory copies fastest).  Synchronises the
+ * handle's stream before returning. */
 int lbmpcd_get_fields(lbmpcd* h, int replica, int field, void* dst, size_t bytes, int dst_on_device);
 
 /* Load POPS, PART_POS, PART_VEL or PART_HOME of one replica from src (same
- * layouts and element types as get_fields; particle arrays in id order), or
+ * layouts and element types as get_fields; particle arrays in id order; a
+ * host src goes through the handle's staging buffer, as for get_fields), or
  * start the LB from a velocity field: U [3][nz][ny][nx] sets the populations
  * of every node to f_eq(rho0 = 1, u) (Eq. 2).
  * Positions must satisfy 0 <= offset < 1 and lie inside the region.  Errors:

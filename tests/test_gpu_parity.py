@@ -280,6 +280,39 @@ def test_set_state_round_trip_and_step(lb):
     assert rel_err(g.get("PART_VEL"), o.get("PART_VEL")) <= 1e-12
 
 
+def test_host_calls_of_changing_sizes(lb):
+    """Host-side set / get calls of growing and shrinking sizes, from pageable
+    and pinned host memory (the handle keeps one staging buffer between
+    calls), return what the first calls returned and load what they are given."""
+    import torch
+    cfg = inputs.small_2d(precision=0)
+    g, o = pair(lb, cfg)
+    g.step(2)
+    o.step(2)
+    rho0, vel0, pops0, shift0 = g.get("RHO"), g.get("PART_VEL"), g.get("POPS"), g.get("SHIFT")
+    assert vel0.size > pops0.size > rho0.size > shift0.size
+    assert rel_err(vel0, o.get("PART_VEL")) <= 1e-12
+    # small after large, large after small
+    assert np.array_equal(g.get("RHO"), rho0)
+    assert np.array_equal(g.get("PART_VEL"), vel0)
+    assert np.array_equal(g.get("SHIFT"), shift0)
+    assert np.array_equal(g.get("POPS"), pops0)
+    # pinned host buffers, out and in
+    t = torch.empty(pops0.size, dtype=torch.float64, pin_memory=True)
+    g.get("POPS", out=t.numpy())
+    assert np.array_equal(t.numpy(), pops0)
+    v = inputs.random_velocities(o.num_particles, 2, 0.02, seed=12)
+    g.set("PART_VEL", torch.from_numpy(v).pin_memory())
+    o.set("PART_VEL", v)
+    g.set("POPS", t)
+    assert rel_err(g.get("POPS"), pops0) <= 1e-15
+    assert np.array_equal(g.get("PART_VEL"), o.get("PART_VEL"))
+    g.step(2)
+    o.step(2)
+    assert np.array_equal(g.get("PART_HOME"), o.get("PART_HOME"))
+    assert rel_err(g.get("PART_VEL"), o.get("PART_VEL")) <= 1e-12
+
+
 def test_replicas_in_one_handle(lb):
     """Three uneven replicas in one handle match three separate oracles."""
     cfgs = [inputs.small_2d(precision=0, seed=31),
