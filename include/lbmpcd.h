@@ -331,7 +331,9 @@ void lbmpcd_net_destroy(lbmpcd_net* net);
  *    batches: call once per slice of at most that many patches); NULL
  *    pointers or patches < 1: ERR_INVALID_ARG.
  *  - Runs on `stream` (a cudaStream_t, may be NULL) and synchronises it
- *    before returning; a bounded wait that gave up returns ERR_TIMEOUT.
+ *    before returning, so it cannot be called while that stream is being
+ *    captured into a graph (the call then fails with ERR_CUDA); a bounded
+ *    wait that gave up returns ERR_TIMEOUT.
  *  - The scratch's error word must be zero when the GEMMs start: each call
  *    clears it itself, first on its stream.  Nothing else in the scratch is
  *    read before the call writes it, so no state carries between calls.
