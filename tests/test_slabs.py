@@ -273,20 +273,22 @@ def _piece_rank_main(rank, world, port, p, region, cuts, halo, steps, out_dir):
         dist.destroy_process_group()
 
 
-def test_gloo_pieces_hand_particles_over(tmp_path):
-    """The same hand-over between two gloo ranks (one all-gather of the owned
-    particles per exchange): their owned sets partition the region's
-    particles, at the positions the undivided motion gives."""
+@pytest.mark.parametrize("world,halo,steps", [(2, 2, 9), (3, 2, 11)])
+def test_gloo_pieces_hand_particles_over(tmp_path, world, halo, steps):
+    """The same hand-over between gloo ranks (one all-gather of the owned
+    particles per step): their owned sets partition the region's particles,
+    at the positions the undivided motion gives."""
     import torch.multiprocessing as mp
-    world, halo, steps = 2, 2, 9
     p, region, cuts = _divided(world, halo)
     mp.spawn(_piece_rank_main, args=(world, _free_port(), p, region, cuts, halo, steps, str(tmp_path)),
              nprocs=world, join=True)
     wx = (region[1] - region[0]) * p["refine"]
     home, off, vel, pid = seeded(wx, (p["ny"] - 2) * p["refine"])
     home[:, 0] = (home[:, 0] + steps) % wx
-    pids = np.concatenate([np.load(tmp_path / f"pid{r}.npy") for r in range(world)])
-    homes = np.concatenate([np.load(tmp_path / f"home{r}.npy") for r in range(world)])
+    holders = [r for r in range(world) if (tmp_path / f"pid{r}.npy").exists()]
+    assert len(holders) >= 2
+    pids = np.concatenate([np.load(tmp_path / f"pid{r}.npy") for r in holders])
+    homes = np.concatenate([np.load(tmp_path / f"home{r}.npy") for r in holders])
     o = np.argsort(pids)
     assert np.array_equal(pids[o], np.sort(pid))
     assert np.array_equal(homes[o], home[np.argsort(pid)])
